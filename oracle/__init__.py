@@ -1,0 +1,280 @@
+"""CPU FP64 oracle for the uniaxial-cloak ray tracer -- TEST INFRASTRUCTURE ONLY.
+
+A ctypes front end over ``libcloak_oracle.so`` (plain C, FP64; source in
+``cloak_oracle.c``).  Only the tests, the smoke check and the CPU-baseline leg
+of the benchmark may import this package.  The renderer never routes through it.
+
+Each wrapper names the passage of Halimeh & Wegener (arXiv:1209.6038) it
+follows; the C source carries the detail.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RADIAL, AZIMUTHAL, TEST_CONST = 0, 1, 100
+ORDINARY, EXTRAORDINARY = 0, 1
+RK4, DP45 = 0, 1
+STATUS = {0: "MISSED", 1: "EXITED", 2: "HIT_METAL_EXITED", 3: "NO_TRANSMISSION", 4: "TIR",
+          5: "STEP_LIMIT", 6: "SINGULAR", 7: "METAL_CAP"}
+
+RECORD_DTYPE = np.dtype([("exit_pos", "<f8", 3), ("exit_dir", "<f8", 3), ("tof", "<f8"), ("weight", "<f8"),
+                         ("tile_id", "<i4"), ("status", "<i4"), ("steps", "<i4"), ("mode", "<i4")])
+assert RECORD_DTYPE.itemsize == 80
+
+
+class _Cloak(C.Structure):
+    _fields_ = [("variant", C.c_int), ("R1", C.c_double), ("R2", C.c_double), ("H", C.c_double),
+                ("eps_o_test", C.c_double), ("eps_e_test", C.c_double), ("c_test", C.c_double * 3),
+                ("scene_seed", C.c_uint64)]
+
+
+class _Integ(C.Structure):
+    _fields_ = [("kind", C.c_int), ("h_or_tol", C.c_double), ("max_steps", C.c_long)]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("eye", C.c_double * 3), ("target", C.c_double * 3), ("up", C.c_double * 3),
+                ("hfov_deg", C.c_double), ("width", C.c_int), ("height", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        dp = C.POINTER(C.c_double)
+        L.orc_splitmix64.restype = C.c_uint64
+        L.orc_splitmix64.argtypes = [C.c_uint64]
+        L.orc_uniform.restype = C.c_double
+        L.orc_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32]
+        L.orc_permittivity.argtypes = [C.POINTER(_Cloak), dp, dp, dp, dp, dp]
+        L.orc_aux_matrix.argtypes = [C.POINTER(_Cloak), dp, dp, dp]
+        L.orc_eq8_accel.argtypes = [dp, dp, dp, dp]
+        L.orc_eq2_accel.argtypes = [C.c_double, dp, dp, dp]
+        L.orc_rhs.argtypes = [C.POINTER(_Cloak), C.c_int, dp, dp]
+        L.orc_refract_into.restype = C.c_int
+        L.orc_refract_into.argtypes = [C.POINTER(_Cloak), C.c_int, dp, dp, dp, dp, dp]
+        L.orc_mode_fields.argtypes = [C.POINTER(_Cloak), C.c_int, dp, dp, dp, dp, dp]
+        L.orc_transmission_in.restype = C.c_int
+        L.orc_transmission_in.argtypes = [C.POINTER(_Cloak), dp, dp, dp, dp]
+        L.orc_transmission_out.restype = C.c_int
+        L.orc_transmission_out.argtypes = [C.POINTER(_Cloak), C.c_int, dp, dp, dp, dp]
+        L.orc_rk4_step.argtypes = [C.POINTER(_Cloak), C.c_int, dp, C.c_double, dp]
+        L.orc_dp45_step.argtypes = [C.POINTER(_Cloak), C.c_int, dp, C.c_double, dp, dp]
+        L.orc_trace_ray.restype = C.c_int
+        L.orc_trace_ray.argtypes = [C.POINTER(_Cloak), C.POINTER(_Integ), C.c_int, dp, dp, C.c_void_p,
+                                    dp, C.c_long, C.POINTER(C.c_long)]
+        L.orc_trace_rays.argtypes = [C.POINTER(_Cloak), C.POINTER(_Integ), C.c_int, dp, C.c_long, C.c_void_p,
+                                     C.c_int]
+        L.orc_camera_ray.argtypes = [C.POINTER(_Camera), C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, dp, dp]
+        L.orc_shade.restype = C.c_int
+        L.orc_shade.argtypes = [C.POINTER(_Cloak), dp, dp, dp]
+        L.orc_render.argtypes = [C.POINTER(_Cloak), C.POINTER(_Integ), C.POINTER(_Camera), C.c_int, C.c_int,
+                                 C.c_uint64, C.POINTER(C.c_int64), C.c_long, dp, C.c_void_p, C.c_int]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _vec(x, n=3):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(n))
+    return a
+
+
+class Cloak:
+    """Cloak geometry and material: Eq. 14 (radial) or Eq. 15 (azimuthal), or a
+    homogeneous uniaxial test medium (Eq. 1 with a fixed optic axis)."""
+
+    def __init__(self, variant=RADIAL, R1=0.5, R2=1.0, H=2.0, eps_o=1.0, eps_e=1.0, c_hat=(0, 0, 1),
+                 scene_seed=0):
+        self.s = _Cloak(variant, R1, R2, H, eps_o, eps_e, (C.c_double * 3)(*c_hat), scene_seed)
+
+    @property
+    def ref(self):
+        return C.byref(self.s)
+
+
+class Integrator:
+    """RK4 at fixed step h (Sect. 4) or Dormand-Prince 5(4) at tolerance tol."""
+
+    def __init__(self, kind=RK4, h_or_tol=1e-3, max_steps=2_000_000):
+        self.s = _Integ(kind, h_or_tol, max_steps)
+
+    @property
+    def ref(self):
+        return C.byref(self.s)
+
+
+class Camera:
+    def __init__(self, eye, target=(0, 0, 0), up=(0, 0, 1), hfov_deg=60.0, width=128, height=96):
+        self.s = _Camera((C.c_double * 3)(*eye), (C.c_double * 3)(*target), (C.c_double * 3)(*up), hfov_deg,
+                         width, height)
+        self.width, self.height = width, height
+
+    @property
+    def ref(self):
+        return C.byref(self.s)
+
+
+def splitmix64(z: int) -> int:
+    return int(lib().orc_splitmix64(z & 0xFFFFFFFFFFFFFFFF))
+
+
+def uniform(seed, pixel, sample, dim) -> float:
+    return float(lib().orc_uniform(seed, pixel, sample, dim))
+
+
+def permittivity(cloak: Cloak, x):
+    x = _vec(x)
+    eps = np.zeros(9)
+    eo, ee = C.c_double(), C.c_double()
+    ch = np.zeros(3)
+    lib().orc_permittivity(cloak.ref, _dp(x), _dp(eps), C.byref(eo), C.byref(ee), _dp(ch))
+    return eps.reshape(3, 3), eo.value, ee.value, ch
+
+
+def aux_matrix(cloak: Cloak, x):
+    """Eq. 7: M and dM[k, i, j] = d M_ij / d x_k."""
+    x = _vec(x)
+    M = np.zeros(9)
+    dM = np.zeros(27)
+    lib().orc_aux_matrix(cloak.ref, _dp(x), _dp(M), _dp(dM))
+    return M.reshape(3, 3), dM.reshape(3, 3, 3)
+
+
+def eq8_accel(M, dM, v):
+    M = np.ascontiguousarray(M, dtype=np.float64).reshape(9)
+    dM = np.ascontiguousarray(dM, dtype=np.float64).reshape(27)
+    v = _vec(v)
+    a = np.zeros(3)
+    lib().orc_eq8_accel(_dp(M), _dp(dM), _dp(v), _dp(a))
+    return a
+
+
+def eq2_accel(n, gradn, v):
+    g = _vec(gradn)
+    v = _vec(v)
+    a = np.zeros(3)
+    lib().orc_eq2_accel(float(n), _dp(g), _dp(v), _dp(a))
+    return a
+
+
+def rhs(cloak: Cloak, mode, y):
+    y = _vec(y, 6)
+    dy = np.zeros(6)
+    lib().orc_rhs(cloak.ref, mode, _dp(y), _dp(dy))
+    return dy
+
+
+def refract_into(cloak: Cloak, mode, x, n, kt):
+    """Sect. 3, Eqs. 9-11: inward wave of the mode with tangential wave vector kt.
+    Returns (k, v) or None when the mode is evanescent."""
+    x, n, kt = _vec(x), _vec(n), _vec(kt)
+    k = np.zeros(3)
+    v = np.zeros(3)
+    ok = lib().orc_refract_into(cloak.ref, mode, _dp(x), _dp(n), _dp(kt), _dp(k), _dp(v))
+    return (k, v) if ok else None
+
+
+def mode_fields(cloak: Cloak, mode, x, k):
+    """Sect. 3 field directions (D, E, H) of the propagating wave with wave vector k."""
+    x, k = _vec(x), _vec(k)
+    D, E, H = np.zeros(3), np.zeros(3), np.zeros(3)
+    lib().orc_mode_fields(cloak.ref, mode, _dp(x), _dp(k), _dp(D), _dp(E), _dp(H))
+    return D, E, H
+
+
+def transmission_in(cloak: Cloak, x, n, d):
+    """Eq. 12 vacuum -> medium: dict of T_o^s, T_o^p, T_e^s, T_e^p, R^s, R^p, T_o, T_e."""
+    x, n, d = _vec(x), _vec(n), _vec(d)
+    out = np.zeros(8)
+    ok = lib().orc_transmission_in(cloak.ref, _dp(x), _dp(n), _dp(d), _dp(out))
+    keys = ["To_s", "To_p", "Te_s", "Te_p", "R_s", "R_p", "To", "Te"]
+    return dict(zip(keys, out)) if ok else None
+
+
+def transmission_out(cloak: Cloak, mode, x, n, k):
+    """Eq. 12 medium -> vacuum: (ok, T, R_o, R_e); ok False on total internal reflection."""
+    x, n, k = _vec(x), _vec(n), _vec(k)
+    out = np.zeros(4)
+    ok = lib().orc_transmission_out(cloak.ref, mode, _dp(x), _dp(n), _dp(k), _dp(out))
+    return bool(ok), out[0], out[1], out[2]
+
+
+def rk4_step(cloak: Cloak, mode, y, h):
+    y = _vec(y, 6)
+    o = np.zeros(6)
+    lib().orc_rk4_step(cloak.ref, mode, _dp(y), float(h), _dp(o))
+    return o
+
+
+def dp45_step(cloak: Cloak, mode, y, h):
+    y = _vec(y, 6)
+    o = np.zeros(6)
+    e = np.zeros(6)
+    lib().orc_dp45_step(cloak.ref, mode, _dp(y), float(h), _dp(o), _dp(e))
+    return o, e
+
+
+def trace_ray(cloak: Cloak, integ: Integrator, mode, o, d, path_cap=0):
+    """One ray through entry split, integration, exit refraction and shading.
+    Returns (record, path) where path rows are (t, x, y, z, vx, vy, vz)."""
+    o, d = _vec(o), _vec(d)
+    rec = np.zeros(1, dtype=RECORD_DTYPE)
+    path = np.zeros((max(path_cap, 1), 7))
+    plen = C.c_long(0)
+    lib().orc_trace_ray(cloak.ref, integ.ref, mode, _dp(o), _dp(d), rec.ctypes.data_as(C.c_void_p),
+                        _dp(path) if path_cap > 0 else None, path_cap, C.byref(plen))
+    return rec[0], path[: min(plen.value, path_cap)]
+
+
+def trace_rays(cloak: Cloak, integ: Integrator, mode, rays, nthreads=None):
+    rays = np.ascontiguousarray(rays, dtype=np.float64).reshape(-1, 6)
+    n = rays.shape[0]
+    recs = np.zeros(n, dtype=RECORD_DTYPE)
+    lib().orc_trace_rays(cloak.ref, integ.ref, mode, _dp(rays), n, recs.ctypes.data_as(C.c_void_p),
+                         nthreads or os.cpu_count() or 1)
+    return recs
+
+
+def camera_ray(cam: Camera, i, j, s, spp, seed):
+    o = np.zeros(3)
+    d = np.zeros(3)
+    lib().orc_camera_ray(cam.ref, i, j, s, spp, seed, _dp(o), _dp(d))
+    return o, d
+
+
+def shade(cloak: Cloak, p, d):
+    p, d = _vec(p), _vec(d)
+    rgb = np.zeros(3)
+    tile = lib().orc_shade(cloak.ref, _dp(p), _dp(d), _dp(rgb))
+    return tile, rgb
+
+
+def render(cloak: Cloak, integ: Integrator, cam: Camera, mode, spp=1, seed=0, pixels=None, nthreads=None,
+           records=True):
+    """Whole image (or a pixel subset, flat indices j*W+i): RGBA = mean over samples of
+    weight * colour (alpha = mean weight) and per-sample records."""
+    if pixels is None:
+        npix = cam.width * cam.height
+        pix_ptr = None
+    else:
+        pixels = np.ascontiguousarray(pixels, dtype=np.int64)
+        npix = pixels.shape[0]
+        pix_ptr = pixels.ctypes.data_as(C.POINTER(C.c_int64))
+    rgba = np.zeros((npix, 4))
+    recs = np.zeros(npix * spp, dtype=RECORD_DTYPE) if records else None
+    lib().orc_render(cloak.ref, integ.ref, cam.ref, mode, spp, seed, pix_ptr, npix, _dp(rgba),
+                     recs.ctypes.data_as(C.c_void_p) if records else None, nthreads or os.cpu_count() or 1)
+    return rgba, recs

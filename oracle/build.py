@@ -1,0 +1,28 @@
+"""Build the CPU FP64 oracle (test infrastructure only) into oracle/libcloak_oracle.so.
+
+Plain gcc, no tuning flags: -O2, no fast-math, no FMA contraction, OpenMP for
+the per-ray loops.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "cloak_oracle.c")
+LIB = os.path.join(HERE, "libcloak_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
+        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "cloak_oracle.h"))
+    ):
+        return LIB
+    cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-Wall", "-o", LIB + ".tmp", SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))

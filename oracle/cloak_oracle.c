@@ -1,0 +1,925 @@
+/*
+ * cloak_oracle.c -- plain CPU FP64 oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * A slow, literal statement of the method of Halimeh & Wegener,
+ * arXiv:1209.6038, used to check the CUDA renderer.  It follows the paper's
+ * steps in its own notation: the Cartesian permittivity tensor of Eq. 14 / 15,
+ * the auxiliary matrix of Eq. 7 by explicit 3x3 inversion, the equations of
+ * motion Eq. 2 and Eq. 8 written term by term, the Sect. 3 interface through
+ * Eqs. 9-11 (angle of refraction found by bisection), the transmission
+ * coefficients of Eq. 12 from a 4x4 field-continuity solve, and classical
+ * fourth-order Runge-Kutta (Sect. 4).  No blocking, fusion or algebraic
+ * simplification beyond what those formulas state.
+ *
+ * Readings where the paper is silent are marked "Reading:".
+ */
+#include "cloak_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------ */
+/* small linear algebra                                                */
+/* ------------------------------------------------------------------ */
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double a[3], const double b[3], double o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+static void matvec3(const double A[9], const double x[3], double y[3]) {
+    for (int i = 0; i < 3; ++i) y[i] = A[3 * i] * x[0] + A[3 * i + 1] * x[1] + A[3 * i + 2] * x[2];
+}
+static void matmul3(const double A[9], const double B[9], double C[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+            C[3 * i + j] = s;
+        }
+}
+/* inverse of a general 3x3 matrix by the adjugate */
+static void inv3(const double A[9], double B[9]) {
+    double c00 = A[4] * A[8] - A[5] * A[7];
+    double c01 = A[5] * A[6] - A[3] * A[8];
+    double c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    double id = 1.0 / det;
+    B[0] = c00 * id;
+    B[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    B[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    B[3] = c01 * id;
+    B[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    B[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    B[6] = c02 * id;
+    B[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+}
+/* some unit vector perpendicular to n */
+static void any_perp(const double n[3], double t[3]) {
+    double ax[3] = {1.0, 0.0, 0.0};
+    if (fabs(n[0]) > 0.9) { ax[0] = 0.0; ax[1] = 1.0; }
+    cross3(n, ax, t);
+    double l = norm3(t);
+    for (int i = 0; i < 3; ++i) t[i] /= l;
+}
+
+static cplx cdot3(const cplx a[3], const cplx b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void ccross3(const cplx a[3], const cplx b[3], cplx o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double cnorm2(const cplx a[3]) {
+    return creal(a[0] * conj(a[0]) + a[1] * conj(a[1]) + a[2] * conj(a[2]));
+}
+/* normal component of the time-averaged Poynting vector, n . Re(E x H*) (factor 1/2 dropped) */
+static double normal_flux(const double n[3], const cplx E[3], const cplx H[3]) {
+    cplx Hc[3] = {conj(H[0]), conj(H[1]), conj(H[2])}, S[3];
+    ccross3(E, Hc, S);
+    return n[0] * creal(S[0]) + n[1] * creal(S[1]) + n[2] * creal(S[2]);
+}
+/* Gaussian elimination with partial pivoting, 4x4 complex, in place; returns 0 if singular */
+static int solve4(cplx A[4][4], cplx b[4], cplx x[4]) {
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (cabs(A[r][col]) > cabs(A[piv][col])) piv = r;
+        if (cabs(A[piv][col]) == 0.0) return 0;
+        if (piv != col) {
+            for (int k = 0; k < 4; ++k) { cplx t = A[col][k]; A[col][k] = A[piv][k]; A[piv][k] = t; }
+            cplx t = b[col]; b[col] = b[piv]; b[piv] = t;
+        }
+        for (int r = col + 1; r < 4; ++r) {
+            cplx f = A[r][col] / A[col][col];
+            for (int k = col; k < 4; ++k) A[r][k] -= f * A[col][k];
+            b[r] -= f * b[col];
+        }
+    }
+    for (int r = 3; r >= 0; --r) {
+        cplx s = b[r];
+        for (int k = r + 1; k < 4; ++k) s -= A[r][k] * x[k];
+        x[r] = s / A[r][r];
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* splitmix64 (Steele, Lea & Flood, OOPSLA 2014), counter-based use     */
+/* ------------------------------------------------------------------ */
+uint64_t orc_splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+/* Reading: uniform in [0,1) from the top 53 bits of a hash chain over
+   (seed, pixel, sample, dimension). */
+double orc_uniform(uint64_t seed, uint64_t pixel, uint32_t sample, uint32_t dim) {
+    uint64_t h = orc_splitmix64(seed);
+    h = orc_splitmix64(h ^ pixel);
+    h = orc_splitmix64(h ^ (((uint64_t)sample << 8) | (uint64_t)dim));
+    return (double)(h >> 11) * 0x1.0p-53;
+}
+
+/* ------------------------------------------------------------------ */
+/* material: Eq. 14 / Eq. 15 in cylindrical components                 */
+/* ------------------------------------------------------------------ */
+/* Cylindrical components (eps'_r, eps'_theta, eps'_z) at radius r and their
+   r-derivatives.  a = R1, b = R2. */
+static void cyl_eps(const orc_cloak *c, double r, double e[3], double de[3]) {
+    double a = c->R1, b = c->R2;
+    double K = (b / (b - a)) * (b / (b - a));
+    double q = (r - a) / r;
+    double er = q * q * K;                      /* ((r-a)/r)^2 (b/(b-a))^2 */
+    double der = 2.0 * q * (a / (r * r)) * K;   /* d/dr of the above */
+    e[0] = er;
+    de[0] = der;
+    e[1] = K; /* eps'_theta = (b/(b-a))^2 in both Eq. 14 and Eq. 15 */
+    de[1] = 0.0;
+    if (c->variant == ORC_RADIAL) { e[2] = K; de[2] = 0.0; }   /* Eq. 14 */
+    else { e[2] = er; de[2] = der; }                            /* Eq. 15 */
+}
+static void cyl_basis(const double x[3], double *r, double rh[3], double th[3]) {
+    *r = hypot(x[0], x[1]);
+    rh[0] = x[0] / *r; rh[1] = x[1] / *r; rh[2] = 0.0;
+    th[0] = -x[1] / *r; th[1] = x[0] / *r; th[2] = 0.0;
+}
+
+/* Cartesian permittivity tensor (Eq. 1 rotated to the lab frame), with the
+   ordinary/extraordinary values and the optic axis c-hat. */
+void orc_permittivity(const orc_cloak *c, const double x[3], double eps[9], double *eps_o, double *eps_e,
+                      double chat[3]) {
+    if (c->variant == ORC_TEST_CONST) {
+        double l = norm3(c->c_test);
+        for (int i = 0; i < 3; ++i) chat[i] = c->c_test[i] / l;
+        *eps_o = c->eps_o_test;
+        *eps_e = c->eps_e_test;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                eps[3 * i + j] = (i == j ? *eps_o : 0.0) + (*eps_e - *eps_o) * chat[i] * chat[j];
+        return;
+    }
+    double r, rh[3], th[3], zh[3] = {0, 0, 1}, e[3], de[3];
+    cyl_basis(x, &r, rh, th);
+    cyl_eps(c, r, e, de);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            eps[3 * i + j] = e[0] * rh[i] * rh[j] + e[1] * th[i] * th[j] + e[2] * zh[i] * zh[j];
+    if (c->variant == ORC_RADIAL) {          /* optic axis r-hat: eps_e = eps'_r, eps_o = eps'_theta = eps'_z */
+        *eps_e = e[0]; *eps_o = e[1];
+        for (int i = 0; i < 3; ++i) chat[i] = rh[i];
+    } else {                                 /* optic axis theta-hat: eps_e = eps'_theta, eps_o = eps'_r = eps'_z */
+        *eps_e = e[1]; *eps_o = e[0];
+        for (int i = 0; i < 3; ++i) chat[i] = th[i];
+    }
+}
+
+/* Eq. 7: M = n_o^2 n_e^2 eps^{-1} and its Cartesian gradient.
+   dM[9*k + 3*i + j] = d M_ij / d x_k. */
+void orc_aux_matrix(const orc_cloak *c, const double x[3], double M[9], double dM[27]) {
+    double eps[9], eo, ee, ch[3], ie[9];
+    orc_permittivity(c, x, eps, &eo, &ee, ch);
+    inv3(eps, ie);
+    double P = eo * ee; /* n_o^2 n_e^2 */
+    for (int i = 0; i < 9; ++i) M[i] = P * ie[i];
+    if (c->variant == ORC_TEST_CONST) {
+        memset(dM, 0, 27 * sizeof(double));
+        return;
+    }
+    double r, rh[3], th[3], zh[3] = {0, 0, 1}, e[3], de[3];
+    cyl_basis(x, &r, rh, th);
+    cyl_eps(c, r, e, de);
+    double deo, dee; /* d eps_o / dr, d eps_e / dr */
+    if (c->variant == ORC_RADIAL) { dee = de[0]; deo = de[1]; }
+    else { dee = de[1]; deo = de[0]; }
+    for (int k = 0; k < 3; ++k) {
+        /* derivatives of the basis along x_k: d rh = th_k th / r, d th = -th_k rh / r, d zh = 0 */
+        double drh[3], dth[3];
+        for (int i = 0; i < 3; ++i) { drh[i] = th[k] * th[i] / r; dth[i] = -th[k] * rh[i] / r; }
+        double deps[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                deps[3 * i + j] = de[0] * rh[k] * rh[i] * rh[j] + e[0] * (drh[i] * rh[j] + rh[i] * drh[j]) +
+                                  de[1] * rh[k] * th[i] * th[j] + e[1] * (dth[i] * th[j] + th[i] * dth[j]) +
+                                  de[2] * rh[k] * zh[i] * zh[j];
+        double dP = (deo * ee + eo * dee) * rh[k];
+        double t1[9], t2[9];
+        matmul3(ie, deps, t1);
+        matmul3(t1, ie, t2); /* eps^{-1} (d eps) eps^{-1} */
+        for (int i = 0; i < 9; ++i) dM[9 * k + i] = dP * ie[i] - P * t2[i];
+    }
+}
+
+/* Eq. 8: dv/dt = (1/2) M^{-1} [ v (grad M) v - 2 ((grad M) . v) v ].
+   Reading: component i of "v (grad M) v" is v^T (d_i M) v; "((grad M) . v) v"
+   is sum_l v_l (d_l M) v. */
+void orc_eq8_accel(const double M[9], const double dM[27], const double v[3], double a[3]) {
+    double g[3], h[3], w[3], Mi[9];
+    for (int i = 0; i < 3; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) s += v[j] * dM[9 * i + 3 * j + k] * v[k];
+        g[i] = s;
+    }
+    for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l)
+            for (int k = 0; k < 3; ++k) s += v[l] * dM[9 * l + 3 * j + k] * v[k];
+        h[j] = s;
+    }
+    for (int i = 0; i < 3; ++i) w[i] = g[i] - 2.0 * h[i];
+    inv3(M, Mi);
+    matvec3(Mi, w, a);
+    for (int i = 0; i < 3; ++i) a[i] *= 0.5;
+}
+
+/* Eq. 2: dv/dt = ( |v|^2 grad n - 2 (grad n . v) v ) / n. */
+void orc_eq2_accel(double n, const double gn[3], const double v[3], double a[3]) {
+    double vv = dot3(v, v), gv = dot3(gn, v);
+    for (int i = 0; i < 3; ++i) a[i] = (vv * gn[i] - 2.0 * gv * v[i]) / n;
+}
+
+/* right-hand side of the first-order system y = (x, v): dx/dt = v, dv/dt = Eq. 2 (o) or Eq. 8 (e) */
+void orc_rhs(const orc_cloak *c, int mode, const double y[6], double dy[6]) {
+    const double *x = y, *v = y + 3;
+    dy[0] = v[0]; dy[1] = v[1]; dy[2] = v[2];
+    if (mode == ORC_EXTRAORDINARY) {
+        double M[9], dM[27];
+        orc_aux_matrix(c, x, M, dM);
+        orc_eq8_accel(M, dM, v, dy + 3);
+    } else {
+        double gn[3] = {0, 0, 0}, n;
+        if (c->variant == ORC_TEST_CONST) {
+            n = sqrt(c->eps_o_test);
+        } else {
+            double r, rh[3], th[3], e[3], de[3];
+            cyl_basis(x, &r, rh, th);
+            cyl_eps(c, r, e, de);
+            double eo = (c->variant == ORC_RADIAL) ? e[1] : e[0];
+            double deo = (c->variant == ORC_RADIAL) ? de[1] : de[0];
+            n = sqrt(eo);                       /* n_o = sqrt(eps_o) */
+            for (int i = 0; i < 3; ++i) gn[i] = deo / (2.0 * n) * rh[i];
+        }
+        orc_eq2_accel(n, gn, v, dy + 3);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sect. 3: refraction into the medium (Eqs. 9-11)                      */
+/* ------------------------------------------------------------------ */
+/* Eq. 9 with Eq. 10: index seen by the extraordinary wave whose wave vector
+   makes angle phi with -n-hat inside the plane of incidence (unit tangent t).
+   Eq. 10 gives the angle of D_e with c-hat through its sine; only its sine and
+   cosine squared enter Eq. 9, so the arcsin is not taken. */
+static double eq9_index(double no, double ne, const double ch[3], const double t[3], const double n[3], double phi) {
+    double s = dot3(ch, t) * sin(phi) - dot3(ch, n) * cos(phi);
+    double s2 = s * s, c2 = 1.0 - s2;
+    return no * ne / sqrt(no * no * c2 + ne * ne * s2);
+}
+
+/* The propagating wave of `mode` inside the medium at face point x (outward
+   normal n) whose tangential wave vector is kt, travelling inward.
+   Returns 1 with k and v = M^{-1} k (Eq. 6), or 0 if the mode has no real
+   angle of refraction in [0, pi/2] (evanescent). */
+int orc_refract_into(const orc_cloak *c, int mode, const double x[3], const double n[3], const double kt[3],
+                     double k[3], double v[3]) {
+    double eps[9], eo, ee, ch[3];
+    orc_permittivity(c, x, eps, &eo, &ee, ch);
+    double no = sqrt(eo), ne = sqrt(ee);
+    double st = norm3(kt); /* n_i sin(phi_i), left side of Eq. 11 */
+    double t[3];
+    if (st > 0.0) for (int i = 0; i < 3; ++i) t[i] = kt[i] / st;
+    else any_perp(n, t);
+    if (mode == ORC_ORDINARY) {
+        double s = st / no; /* Eq. 11: n_o sin(phi_o) = n_i sin(phi_i) */
+        if (s > 1.0) return 0;
+        double phi = asin(s);
+        for (int i = 0; i < 3; ++i) k[i] = no * (t[i] * sin(phi) - n[i] * cos(phi)); /* |k_o| = n_o */
+        for (int i = 0; i < 3; ++i) v[i] = k[i] / eo; /* Eq. 6 with M = n_o^2 I */
+        return 1;
+    }
+    /* Eq. 11 for the extraordinary wave: n(phi) sin(phi) = st, root in [0, pi/2] by bisection */
+    double phi;
+    if (st == 0.0) {
+        phi = 0.0;
+    } else {
+        double hi = 0.5 * M_PI, lo = 0.0;
+        if (eq9_index(no, ne, ch, t, n, hi) * sin(hi) - st < 0.0) return 0;
+        for (int it = 0; it < 400; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (eq9_index(no, ne, ch, t, n, mid) * sin(mid) - st < 0.0) lo = mid;
+            else hi = mid;
+        }
+        phi = 0.5 * (lo + hi);
+    }
+    double nn = eq9_index(no, ne, ch, t, n, phi); /* |k_e| = n(phi_e) */
+    for (int i = 0; i < 3; ++i) k[i] = nn * (t[i] * sin(phi) - n[i] * cos(phi));
+    double M[9], dM[27], Mi[9];
+    orc_aux_matrix(c, x, M, dM);
+    inv3(M, Mi);
+    matvec3(Mi, k, v); /* Eq. 6 */
+    return 1;
+}
+
+/* Wave vector (possibly complex) of the inward wave of `mode` with tangential kt.
+   Propagating: Eqs. 9-11 (above).  Evanescent -- Reading: the paper is silent;
+   the normal component q solves the dispersion relation |k|^2 = eps_o (o) or
+   k^T M^{-1} k = 1 (e) with the branch that decays into the medium. */
+static void inward_wave(const orc_cloak *c, int mode, const double x[3], const double n[3], const double kt[3],
+                        cplx k[3]) {
+    double kr[3], vr[3];
+    if (orc_refract_into(c, mode, x, n, kt, kr, vr)) {
+        for (int i = 0; i < 3; ++i) k[i] = kr[i];
+        return;
+    }
+    double eps[9], eo, ee, ch[3];
+    orc_permittivity(c, x, eps, &eo, &ee, ch);
+    cplx q;
+    if (mode == ORC_ORDINARY) {
+        q = -csqrt(eo - dot3(kt, kt));
+    } else {
+        double M[9], dM[27], Mi[9], Mn[3], Mk[3];
+        orc_aux_matrix(c, x, M, dM);
+        inv3(M, Mi);
+        matvec3(Mi, n, Mn);
+        matvec3(Mi, kt, Mk);
+        double A = dot3(n, Mn), B = dot3(n, Mk), C = dot3(kt, Mk) - 1.0;
+        q = (-B - csqrt(B * B - A * C)) / A;
+    }
+    for (int i = 0; i < 3; ++i) k[i] = kt[i] + q * n[i];
+}
+
+/* Field directions of a plane wave of `mode` in the medium (Sect. 3):
+   D_o is perpendicular to the ordinary main section, D_e lies in the
+   extraordinary main section and is perpendicular to k; E = eps^{-1} D,
+   H = k x E (mu = 1, omega = c0 = 1).
+   Reading: when k is parallel to c-hat the two modes are degenerate and
+   D_o is taken along z-hat x k (x-hat x k if that vanishes too). */
+static void mode_fields(int mode, const cplx k[3], const double eps[9], const double ch[3], cplx E[3], cplx H[3]) {
+    cplx c3[3] = {ch[0], ch[1], ch[2]}, Do[3], D[3];
+    ccross3(c3, k, Do);
+    if (cnorm2(Do) < 1e-20 * cnorm2(k)) {
+        cplx z3[3] = {0, 0, 1};
+        ccross3(z3, k, Do);
+        if (cnorm2(Do) < 1e-20 * cnorm2(k)) {
+            cplx x3[3] = {1, 0, 0};
+            ccross3(x3, k, Do);
+        }
+        if (mode == ORC_EXTRAORDINARY) ccross3(k, Do, D);
+        else for (int i = 0; i < 3; ++i) D[i] = Do[i];
+    } else if (mode == ORC_ORDINARY) {
+        for (int i = 0; i < 3; ++i) D[i] = Do[i];
+    } else {
+        cplx kk = cdot3(k, k), ck = cdot3(c3, k);
+        for (int i = 0; i < 3; ++i) D[i] = kk * c3[i] - ck * k[i];
+    }
+    double ie[9];
+    inv3(eps, ie);
+    for (int i = 0; i < 3; ++i) E[i] = ie[3 * i] * D[0] + ie[3 * i + 1] * D[1] + ie[3 * i + 2] * D[2];
+    ccross3(k, E, H);
+}
+
+/* Field directions (D, E, H) of a propagating wave of `mode` with real wave
+   vector k at point x (for tests of the Sect. 3 / Sect. 5 field rules). */
+void orc_mode_fields(const orc_cloak *c, int mode, const double x[3], const double k[3], double D[3], double E[3],
+                     double H[3]) {
+    double eps[9], eo, ee, ch[3];
+    orc_permittivity(c, x, eps, &eo, &ee, ch);
+    cplx ck[3] = {k[0], k[1], k[2]}, cE[3], cH[3];
+    mode_fields(mode, ck, eps, ch, cE, cH);
+    for (int i = 0; i < 3; ++i) { E[i] = creal(cE[i]); H[i] = creal(cH[i]); }
+    matvec3(eps, E, D);
+}
+
+/* s and p unit polarisations of a real vacuum wave k at a face with normal n */
+static void vacuum_basis(const double k[3], const double n[3], double s[3], double p[3]) {
+    cross3(k, n, s);
+    double l = norm3(s);
+    if (l < 1e-12) any_perp(n, s);
+    else for (int i = 0; i < 3; ++i) s[i] /= l;
+    cross3(s, k, p);
+}
+
+/* Eq. 12 at a vacuum -> medium face.  Incident unit vacuum direction d
+   (d . n < 0), outward normal n, face point x.  out = {T_o^s, T_o^p, T_e^s,
+   T_e^p, R^s, R^p, T_o (unpolarised), T_e (unpolarised)}. */
+int orc_transmission_in(const orc_cloak *c, const double x[3], const double n[3], const double d[3], double out[8]) {
+    double eps[9], eo, ee, ch[3];
+    orc_permittivity(c, x, eps, &eo, &ee, ch);
+    double dn = dot3(d, n), kt[3], kr[3];
+    for (int i = 0; i < 3; ++i) { kt[i] = d[i] - dn * n[i]; kr[i] = d[i] - 2.0 * dn * n[i]; }
+    cplx ko[3], ke[3], Eo[3], Ho[3], Ee[3], He[3];
+    inward_wave(c, ORC_ORDINARY, x, n, kt, ko);
+    inward_wave(c, ORC_EXTRAORDINARY, x, n, kt, ke);
+    mode_fields(ORC_ORDINARY, ko, eps, ch, Eo, Ho);
+    mode_fields(ORC_EXTRAORDINARY, ke, eps, ch, Ee, He);
+    double s[3], pi[3], pr[3];
+    vacuum_basis(d, n, s, pi);
+    cross3(s, kr, pr); /* reflected wave: same s, p = s x k_r */
+    double t1[3], t2[3];
+    for (int i = 0; i < 3; ++i) t1[i] = s[i];
+    cross3(n, s, t2);
+    cplx ckr[3] = {kr[0], kr[1], kr[2]}, cd[3] = {d[0], d[1], d[2]};
+    cplx Ers[3] = {s[0], s[1], s[2]}, Erp[3] = {pr[0], pr[1], pr[2]}, Hrs[3], Hrp[3];
+    ccross3(ckr, Ers, Hrs);
+    ccross3(ckr, Erp, Hrp);
+    for (int pol = 0; pol < 2; ++pol) {
+        cplx Ei[3], Hi[3];
+        for (int i = 0; i < 3; ++i) Ei[i] = pol == 0 ? s[i] : pi[i];
+        ccross3(cd, Ei, Hi);
+        /* tangential continuity of E and H: incident + reflected = transmitted */
+        const cplx *cols_E[4] = {Ers, Erp, Eo, Ee}, *cols_H[4] = {Hrs, Hrp, Ho, He};
+        double sign[4] = {1, 1, -1, -1};
+        cplx A[4][4], b[4], u[4];
+        for (int col = 0; col < 4; ++col) {
+            cplx t1c[3] = {t1[0], t1[1], t1[2]}, t2c[3] = {t2[0], t2[1], t2[2]};
+            A[0][col] = sign[col] * cdot3(cols_E[col], t1c);
+            A[1][col] = sign[col] * cdot3(cols_E[col], t2c);
+            A[2][col] = sign[col] * cdot3(cols_H[col], t1c);
+            A[3][col] = sign[col] * cdot3(cols_H[col], t2c);
+        }
+        cplx t1c[3] = {t1[0], t1[1], t1[2]}, t2c[3] = {t2[0], t2[1], t2[2]};
+        b[0] = -cdot3(Ei, t1c); b[1] = -cdot3(Ei, t2c);
+        b[2] = -cdot3(Hi, t1c); b[3] = -cdot3(Hi, t2c);
+        if (!solve4(A, b, u)) return 0;
+        double fi = fabs(normal_flux(n, Ei, Hi));
+        double To = cabs(u[2]) * cabs(u[2]) * fabs(normal_flux(n, Eo, Ho)) / fi;
+        double Te = cabs(u[3]) * cabs(u[3]) * fabs(normal_flux(n, Ee, He)) / fi;
+        cplx Er[3], Hr[3];
+        for (int i = 0; i < 3; ++i) { Er[i] = u[0] * Ers[i] + u[1] * Erp[i]; Hr[i] = u[0] * Hrs[i] + u[1] * Hrp[i]; }
+        double R = fabs(normal_flux(n, Er, Hr)) / fi;
+        out[0 + pol] = To;
+        out[2 + pol] = Te;
+        out[4 + pol] = R;
+    }
+    out[6] = 0.5 * (out[0] + out[1]); /* unpolarised light: mean over s and p */
+    out[7] = 0.5 * (out[2] + out[3]);
+    return 1;
+}
+
+/* Eq. 12 at a medium -> vacuum face (Sect. 3, last paragraph): incident
+   wave of `mode` with real wave vector k, one refracted vacuum wave and two
+   reflected waves (o and e) in the medium.  out = {T, R_o, R_e, 0}.
+   Returns 0 for total internal reflection (|k_t| > 1). */
+int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const double n[3], const double k[3],
+                         double out[4]) {
+    double eps[9], eo, ee, ch[3];
+    orc_permittivity(c, x, eps, &eo, &ee, ch);
+    double kn = dot3(k, n), kt[3];
+    for (int i = 0; i < 3; ++i) kt[i] = k[i] - kn * n[i];
+    double kt2 = dot3(kt, kt);
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    if (kt2 > 1.0) return 0;
+    double kv[3];
+    for (int i = 0; i < 3; ++i) kv[i] = kt[i] + sqrt(1.0 - kt2) * n[i];
+    double s[3], p[3];
+    vacuum_basis(kv, n, s, p);
+    cplx ckv[3] = {kv[0], kv[1], kv[2]};
+    cplx Es[3] = {s[0], s[1], s[2]}, Ep[3] = {p[0], p[1], p[2]}, Hs[3], Hp[3];
+    ccross3(ckv, Es, Hs);
+    ccross3(ckv, Ep, Hp);
+    cplx kro[3], kre[3], Ero[3], Hro[3], Ere[3], Hre[3], ck[3] = {k[0], k[1], k[2]}, Em[3], Hm[3];
+    inward_wave(c, ORC_ORDINARY, x, n, kt, kro);
+    inward_wave(c, ORC_EXTRAORDINARY, x, n, kt, kre);
+    mode_fields(ORC_ORDINARY, kro, eps, ch, Ero, Hro);
+    mode_fields(ORC_EXTRAORDINARY, kre, eps, ch, Ere, Hre);
+    mode_fields(mode, ck, eps, ch, Em, Hm);
+    double t1[3], t2[3];
+    for (int i = 0; i < 3; ++i) t1[i] = s[i];
+    cross3(n, s, t2);
+    cplx t1c[3] = {t1[0], t1[1], t1[2]}, t2c[3] = {t2[0], t2[1], t2[2]};
+    /* tangential continuity: incident + reflected (medium side) = transmitted (vacuum side) */
+    const cplx *cols_E[4] = {Es, Ep, Ero, Ere}, *cols_H[4] = {Hs, Hp, Hro, Hre};
+    double sign[4] = {1, 1, -1, -1};
+    cplx A[4][4], b[4], u[4];
+    for (int col = 0; col < 4; ++col) {
+        A[0][col] = sign[col] * cdot3(cols_E[col], t1c);
+        A[1][col] = sign[col] * cdot3(cols_E[col], t2c);
+        A[2][col] = sign[col] * cdot3(cols_H[col], t1c);
+        A[3][col] = sign[col] * cdot3(cols_H[col], t2c);
+    }
+    b[0] = cdot3(Em, t1c); b[1] = cdot3(Em, t2c);
+    b[2] = cdot3(Hm, t1c); b[3] = cdot3(Hm, t2c);
+    if (!solve4(A, b, u)) return 0;
+    double fi = fabs(normal_flux(n, Em, Hm));
+    cplx Et[3], Ht[3];
+    for (int i = 0; i < 3; ++i) { Et[i] = u[0] * Es[i] + u[1] * Ep[i]; Ht[i] = u[0] * Hs[i] + u[1] * Hp[i]; }
+    out[0] = fabs(normal_flux(n, Et, Ht)) / fi;
+    out[1] = cabs(u[2]) * cabs(u[2]) * fabs(normal_flux(n, Ero, Hro)) / fi;
+    out[2] = cabs(u[3]) * cabs(u[3]) * fabs(normal_flux(n, Ere, Hre)) / fi;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* integrators                                                          */
+/* ------------------------------------------------------------------ */
+/* classical fourth-order Runge-Kutta (Sect. 4) */
+void orc_rk4_step(const orc_cloak *c, int mode, const double y[6], double h, double out[6]) {
+    double k1[6], k2[6], k3[6], k4[6], t[6];
+    orc_rhs(c, mode, y, k1);
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+    orc_rhs(c, mode, t, k2);
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+    orc_rhs(c, mode, t, k3);
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + h * k3[i];
+    orc_rhs(c, mode, t, k4);
+    for (int i = 0; i < 6; ++i) out[i] = y[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+/* Dormand & Prince (1980) 5(4) pair: out = fifth-order solution, err = its
+   difference from the embedded fourth-order solution. */
+void orc_dp45_step(const orc_cloak *c, int mode, const double y[6], double h, double out[6], double err[6]) {
+    static const double a[7][6] = {
+        {0, 0, 0, 0, 0, 0},
+        {1.0 / 5, 0, 0, 0, 0, 0},
+        {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+        {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+        {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+        {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+        {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+    static const double b5[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0};
+    static const double b4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200,
+                                 187.0 / 2100, 1.0 / 40};
+    double k[7][6], t[6];
+    orc_rhs(c, mode, y, k[0]);
+    for (int s = 1; s < 7; ++s) {
+        for (int i = 0; i < 6; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < s; ++j) acc += a[s][j] * k[j][i];
+            t[i] = y[i] + h * acc;
+        }
+        orc_rhs(c, mode, t, k[s]);
+    }
+    for (int i = 0; i < 6; ++i) {
+        double s5 = 0.0, s4 = 0.0;
+        for (int j = 0; j < 7; ++j) { s5 += b5[j] * k[j][i]; s4 += b4[j] * k[j][i]; }
+        out[i] = y[i] + h * s5;
+        err[i] = h * (s5 - s4);
+    }
+}
+
+static void step_solution(const orc_cloak *c, const orc_integrator *in, int mode, const double y[6], double h,
+                          double out[6]) {
+    if (in->kind == ORC_RK4) orc_rk4_step(c, mode, y, h, out);
+    else { double e[6]; orc_dp45_step(c, mode, y, h, out, e); }
+}
+
+/* ------------------------------------------------------------------ */
+/* geometry                                                             */
+/* ------------------------------------------------------------------ */
+/* event functions: positive once the surface has been crossed */
+enum { EV_LATERAL = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_METAL = 3 };
+static double event_value(const orc_cloak *c, int ev, const double y[6]) {
+    switch (ev) {
+    case EV_LATERAL: return hypot(y[0], y[1]) - c->R2;
+    case EV_TOP: return y[2] - 0.5 * c->H;
+    case EV_BOTTOM: return -y[2] - 0.5 * c->H;
+    default: return c->R1 - hypot(y[0], y[1]);
+    }
+}
+
+/* Reading (the paper is silent): the crossing inside a step y_n -> y_{n+1} is
+   the s in (0, h] at which one step of size s of the same integrator from
+   y_n lands on the surface; found by bisection to machine resolution.
+   The returned s is on the far side (exits) or the near side (metal). */
+static double crossing(const orc_cloak *c, const orc_integrator *in, int mode, const double y[6], double h, int ev) {
+    double lo = 0.0, hi = h, t[6];
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        step_solution(c, in, mode, y, mid, t);
+        if (event_value(c, ev, t) > 0.0) hi = mid;
+        else lo = mid;
+    }
+    return ev == EV_METAL ? lo : hi;
+}
+
+/* first entry of the ray o + s d into the finite cylinder r <= R2, |z| <= H/2 */
+static int hit_cylinder(const orc_cloak *c, const double o[3], const double d[3], double p[3], double n[3],
+                        int *face) {
+    double best = INFINITY;
+    *face = -1;
+    double A = d[0] * d[0] + d[1] * d[1], B = o[0] * d[0] + o[1] * d[1],
+           C = o[0] * o[0] + o[1] * o[1] - c->R2 * c->R2;
+    if (A > 0.0) {
+        double disc = B * B - A * C;
+        if (disc >= 0.0) {
+            double s = (-B - sqrt(disc)) / A; /* nearer root: where the ray enters the infinite cylinder */
+            if (s > 0.0 && fabs(o[2] + s * d[2]) <= 0.5 * c->H) { best = s; *face = EV_LATERAL; }
+        }
+    }
+    for (int cap = 0; cap < 2; ++cap) {
+        double zc = cap == 0 ? 0.5 * c->H : -0.5 * c->H;
+        if (d[2] == 0.0) continue;
+        if ((cap == 0 && d[2] >= 0.0) || (cap == 1 && d[2] <= 0.0)) continue; /* must approach from outside */
+        double s = (zc - o[2]) / d[2];
+        double px = o[0] + s * d[0], py = o[1] + s * d[1];
+        if (s > 0.0 && px * px + py * py <= c->R2 * c->R2 && s < best) { best = s; *face = cap == 0 ? EV_TOP : EV_BOTTOM; }
+    }
+    if (*face < 0) return 0;
+    for (int i = 0; i < 3; ++i) p[i] = o[i] + best * d[i];
+    if (*face == EV_LATERAL) {
+        double r = hypot(p[0], p[1]);
+        n[0] = p[0] / r; n[1] = p[1] / r; n[2] = 0.0;
+    } else {
+        n[0] = n[1] = 0.0;
+        n[2] = *face == EV_TOP ? 1.0 : -1.0;
+    }
+    return 1;
+}
+
+static void face_normal(int ev, const double x[3], double n[3]) {
+    if (ev == EV_LATERAL) {
+        double r = hypot(x[0], x[1]);
+        n[0] = x[0] / r; n[1] = x[1] / r; n[2] = 0.0;
+    } else {
+        n[0] = n[1] = 0.0;
+        n[2] = ev == EV_TOP ? 1.0 : -1.0;
+    }
+}
+
+/* wave vector of the mode from the ray velocity: k = M v (Eq. 6) */
+static void wave_vector(const orc_cloak *c, int mode, const double x[3], const double v[3], double k[3]) {
+    if (mode == ORC_EXTRAORDINARY) {
+        double M[9], dM[27];
+        orc_aux_matrix(c, x, M, dM);
+        matvec3(M, v, k);
+    } else {
+        double eps[9], eo, ee, ch[3];
+        orc_permittivity(c, x, eps, &eo, &ee, ch);
+        for (int i = 0; i < 3; ++i) k[i] = eo * v[i];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* procedural room (stands in for the missing scene of the paper)       */
+/* ------------------------------------------------------------------ */
+/* Reading: axis-aligned box x, y in [-10, 10], z in [-H/2, -H/2 + 10];
+   walls and floor checkered with 8 tiles per unit, per-tile tint from
+   splitmix64(scene seed, face, i, j); constant ceiling. */
+int orc_shade(const orc_cloak *c, const double p[3], const double d[3], double rgb[3]) {
+    const double L = 10.0, z0 = -0.5 * c->H, z1 = z0 + 10.0;
+    double best = INFINITY, s;
+    int face = -1;
+    if (d[0] > 0.0) { s = (L - p[0]) / d[0]; if (s < best) { best = s; face = 0; } }
+    else if (d[0] < 0.0) { s = (-L - p[0]) / d[0]; if (s < best) { best = s; face = 1; } }
+    if (d[1] > 0.0) { s = (L - p[1]) / d[1]; if (s < best) { best = s; face = 2; } }
+    else if (d[1] < 0.0) { s = (-L - p[1]) / d[1]; if (s < best) { best = s; face = 3; } }
+    if (d[2] < 0.0) { s = (z0 - p[2]) / d[2]; if (s < best) { best = s; face = 4; } }
+    else if (d[2] > 0.0) { s = (z1 - p[2]) / d[2]; if (s < best) { best = s; face = 5; } }
+    if (face < 0) { rgb[0] = rgb[1] = rgb[2] = 0.0; return -1; }
+    if (face == 5) { rgb[0] = 0.55; rgb[1] = 0.55; rgb[2] = 0.6; return 5 << 20; }
+    double q[3];
+    for (int i = 0; i < 3; ++i) q[i] = p[i] + best * d[i];
+    double u, v;
+    int nu = 160, nv;
+    if (face <= 1) { u = q[1] + L; v = q[2] - z0; nv = 80; }
+    else if (face <= 3) { u = q[0] + L; v = q[2] - z0; nv = 80; }
+    else { u = q[0] + L; v = q[1] + L; nv = 160; }
+    int i = (int)floor(u * 8.0), j = (int)floor(v * 8.0);
+    if (i < 0) i = 0;
+    if (i > nu - 1) i = nu - 1;
+    if (j < 0) j = 0;
+    if (j > nv - 1) j = nv - 1;
+    uint64_t h = orc_splitmix64(c->scene_seed);
+    h = orc_splitmix64(h ^ (uint64_t)face);
+    h = orc_splitmix64(h ^ (uint64_t)i);
+    h = orc_splitmix64(h ^ (uint64_t)j);
+    double base = ((i + j) & 1) ? 0.25 : 0.85;
+    for (int ch = 0; ch < 3; ++ch) rgb[ch] = base * (0.6 + 0.4 * (double)((h >> (8 * ch)) & 255u) / 255.0);
+    return (face << 20) | (i << 10) | j;
+}
+
+/* ------------------------------------------------------------------ */
+/* one ray: entry split, integration, exit refraction, shading          */
+/* ------------------------------------------------------------------ */
+static void path_push(double *path, long cap, long *len, double t, const double y[6]) {
+    if (!path || *len >= cap) { if (len) ++*len; return; }
+    double *p = path + 7 * (*len);
+    p[0] = t;
+    for (int i = 0; i < 6; ++i) p[1 + i] = y[i];
+    ++*len;
+}
+
+static void finish_vacuum(const orc_cloak *c, const double p[3], const double d[3], orc_record *rec) {
+    double rgb[3];
+    for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = p[i]; rec->exit_dir[i] = d[i]; }
+    rec->tile_id = orc_shade(c, p, d, rgb);
+}
+
+int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const double o[3], const double d[3],
+                  orc_record *rec, double *path, long path_cap, long *path_len) {
+    memset(rec, 0, sizeof(*rec));
+    rec->mode = mode;
+    rec->tile_id = -1;
+    long plen = 0;
+    if (path_len) *path_len = 0;
+    double p[3], n[3];
+    int face;
+    if (!hit_cylinder(c, o, d, p, n, &face)) {
+        rec->status = ORC_MISSED;
+        rec->weight = 1.0;
+        finish_vacuum(c, o, d, rec);
+        return rec->status;
+    }
+    if (face != EV_LATERAL && c->R1 > 0.0 && hypot(p[0], p[1]) <= c->R1) {
+        /* metal end disc seen from outside: mirror, reflectance 1 */
+        double dr[3], dn = dot3(d, n);
+        for (int i = 0; i < 3; ++i) dr[i] = d[i] - 2.0 * dn * n[i];
+        rec->status = ORC_METAL_CAP;
+        rec->weight = 1.0;
+        finish_vacuum(c, p, dr, rec);
+        return rec->status;
+    }
+    /* entry double refraction (Sect. 3) */
+    double dn = dot3(d, n), kt[3], k0[3], v0[3];
+    for (int i = 0; i < 3; ++i) kt[i] = d[i] - dn * n[i];
+    if (!orc_refract_into(c, mode, p, n, kt, k0, v0)) {
+        rec->status = ORC_NO_TRANSMISSION;
+        for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = p[i]; rec->exit_dir[i] = d[i]; }
+        return rec->status;
+    }
+    double x_in[3] = {p[0], p[1], p[2]}, n_in[3] = {n[0], n[1], n[2]};
+    double y[6] = {p[0], p[1], p[2], v0[0], v0[1], v0[2]}, y1[6], t = 0.0;
+    path_push(path, path_cap, &plen, t, y);
+    double h = in->kind == ORC_RK4 ? in->h_or_tol : 1e-3, tol = in->h_or_tol;
+    int metal = 0, steps = 0;
+    const int nev = c->R1 > 0.0 ? 4 : 3;
+    for (;;) {
+        if (steps >= in->max_steps || (in->kind == ORC_DP45 && h < 1e-14)) {
+            rec->status = ORC_STEP_LIMIT;
+            rec->steps = steps;
+            for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = y[i]; rec->exit_dir[i] = d[i]; }
+            rec->tof = t;
+            if (path_len) *path_len = plen;
+            return rec->status;
+        }
+        double fac = 1.0;
+        if (in->kind == ORC_RK4) {
+            orc_rk4_step(c, mode, y, h, y1);
+            ++steps;
+        } else {
+            double e[6];
+            orc_dp45_step(c, mode, y, h, y1, e);
+            ++steps;
+            /* error norm: max_i |e_i| / (tol + tol max(|y_i|, |y1_i|)) */
+            double err = 0.0;
+            int bad = 0;
+            for (int i = 0; i < 6; ++i) {
+                double sc = tol + tol * fmax(fabs(y[i]), fabs(y1[i]));
+                double q = fabs(e[i]) / sc;
+                if (q != q) bad = 1;
+                else if (q > err) err = q;
+            }
+            if (bad) err = NAN;
+            if (!(err <= 1.0)) {
+                h *= isfinite(err) ? fmax(0.2, 0.9 * pow(err, -0.2)) : 0.2;
+                continue;
+            }
+            fac = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
+        }
+        /* surfaces crossed by this step; the earliest crossing wins */
+        int ev_hit = -1;
+        double s_hit = INFINITY;
+        for (int ev = 0; ev < nev; ++ev) {
+            if (event_value(c, ev, y1) > 0.0) {
+                double s = crossing(c, in, mode, y, h, ev);
+                if (s < s_hit) { s_hit = s; ev_hit = ev; }
+            }
+        }
+        if (ev_hit < 0) {
+            for (int i = 0; i < 6; ++i) y[i] = y1[i];
+            t += h;
+            h *= fac;
+            path_push(path, path_cap, &plen, t, y);
+            continue;
+        }
+        step_solution(c, in, mode, y, s_hit, y1);
+        for (int i = 0; i < 6; ++i) y[i] = y1[i];
+        t += s_hit;
+        h *= fac;
+        path_push(path, path_cap, &plen, t, y);
+        if (ev_hit == EV_METAL) {
+            if (c->variant == ORC_RADIAL && mode == ORC_ORDINARY) {
+                /* Sect. 4: c-hat parallel to the metal normal, single mirror ray with equal angles */
+                double nm[3], r = hypot(y[0], y[1]);
+                nm[0] = y[0] / r; nm[1] = y[1] / r; nm[2] = 0.0;
+                double vn = dot3(y + 3, nm);
+                for (int i = 0; i < 3; ++i) y[3 + i] -= 2.0 * vn * nm[i];
+                metal = 1;
+                path_push(path, path_cap, &plen, t, y);
+                continue;
+            }
+            rec->status = ORC_SINGULAR;
+            rec->steps = steps;
+            rec->tof = t;
+            for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = y[i]; rec->exit_dir[i] = d[i]; }
+            if (path_len) *path_len = plen;
+            return rec->status;
+        }
+        /* exit refraction (Sect. 3): keep k_t, vacuum k_n = +sqrt(1 - |k_t|^2) */
+        double xo[3] = {y[0], y[1], y[2]}, no[3], kx[3], ktx[3];
+        face_normal(ev_hit, xo, no);
+        wave_vector(c, mode, xo, y + 3, kx);
+        double kn = dot3(kx, no);
+        for (int i = 0; i < 3; ++i) ktx[i] = kx[i] - kn * no[i];
+        double kt2 = dot3(ktx, ktx);
+        rec->steps = steps;
+        rec->tof = t;
+        if (path_len) *path_len = plen;
+        if (kt2 > 1.0) {
+            rec->status = ORC_TIR;
+            for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = xo[i]; rec->exit_dir[i] = d[i]; }
+            return rec->status;
+        }
+        double dout[3];
+        for (int i = 0; i < 3; ++i) dout[i] = ktx[i] + sqrt(1.0 - kt2) * no[i];
+        /* Eq. 12 along the physical direction of light: from the room into the
+           cloak at the exit point, and out of the cloak towards the camera at the
+           entry point.  Unpolarised source: mean over s and p. */
+        double Tin[8], Tout[4], mdout[3], mk0[3];
+        for (int i = 0; i < 3; ++i) { mdout[i] = -dout[i]; mk0[i] = -k0[i]; }
+        double w = 0.0;
+        if (orc_transmission_in(c, xo, no, mdout, Tin) && orc_transmission_out(c, mode, x_in, n_in, mk0, Tout))
+            w = (mode == ORC_ORDINARY ? Tin[6] : Tin[7]) * Tout[0];
+        rec->weight = w;
+        rec->status = metal ? ORC_HIT_METAL_EXITED : ORC_EXITED;
+        finish_vacuum(c, xo, dout, rec);
+        return rec->status;
+    }
+}
+
+void orc_trace_rays(const orc_cloak *c, const orc_integrator *in, int mode, const double *rays, long n,
+                    orc_record *recs, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nthreads)
+    for (long i = 0; i < n; ++i) {
+        const double *r = rays + 6 * i;
+        orc_trace_ray(c, in, mode, r, r + 3, recs + i, NULL, 0, NULL);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* camera and render                                                    */
+/* ------------------------------------------------------------------ */
+/* Pinhole camera; horizontal field of view; row 0 at the top.  One sample per
+   pixel goes through the pixel centre; more samples are jittered with
+   orc_uniform(seed, pixel, sample, 0 / 1). */
+void orc_camera_ray(const orc_camera *cam, int i, int j, int s, int spp, uint64_t seed, double o[3], double d[3]) {
+    double w[3], u[3], v[3];
+    for (int k = 0; k < 3; ++k) w[k] = cam->target[k] - cam->eye[k];
+    double l = norm3(w);
+    for (int k = 0; k < 3; ++k) w[k] /= l;
+    cross3(w, cam->up, u);
+    l = norm3(u);
+    for (int k = 0; k < 3; ++k) u[k] /= l;
+    cross3(u, w, v);
+    double tx = tan(0.5 * cam->hfov_deg * M_PI / 180.0);
+    double ty = tx * (double)cam->height / (double)cam->width;
+    double xi1 = 0.5, xi2 = 0.5;
+    if (spp > 1) {
+        uint64_t pix = (uint64_t)j * (uint64_t)cam->width + (uint64_t)i;
+        xi1 = orc_uniform(seed, pix, (uint32_t)s, 0);
+        xi2 = orc_uniform(seed, pix, (uint32_t)s, 1);
+    }
+    double px = (2.0 * (i + xi1) / cam->width - 1.0) * tx;
+    double py = (1.0 - 2.0 * (j + xi2) / cam->height) * ty;
+    for (int k = 0; k < 3; ++k) d[k] = w[k] + px * u[k] + py * v[k];
+    l = norm3(d);
+    for (int k = 0; k < 3; ++k) { d[k] /= l; o[k] = cam->eye[k]; }
+}
+
+void orc_render(const orc_cloak *c, const orc_integrator *in, const orc_camera *cam, int mode, int spp,
+                uint64_t seed, const int64_t *pixels, long npix, double *rgba, orc_record *recs, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    long total = pixels ? npix : (long)cam->width * cam->height;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+    for (long idx = 0; idx < total; ++idx) {
+        long pix = pixels ? (long)pixels[idx] : idx;
+        int i = (int)(pix % cam->width), j = (int)(pix / cam->width);
+        double acc[4] = {0, 0, 0, 0};
+        for (int s = 0; s < spp; ++s) {
+            double o[3], d[3], rgb[3];
+            orc_record rec;
+            orc_camera_ray(cam, i, j, s, spp, seed, o, d);
+            orc_trace_ray(c, in, mode, o, d, &rec, NULL, 0, NULL);
+            if (rec.tile_id >= 0) orc_shade(c, rec.exit_pos, rec.exit_dir, rgb);
+            else rgb[0] = rgb[1] = rgb[2] = 0.0;
+            for (int k = 0; k < 3; ++k) acc[k] += rec.weight * rgb[k];
+            acc[3] += rec.weight;
+            if (recs) recs[idx * spp + s] = rec;
+        }
+        if (rgba)
+            for (int k = 0; k < 4; ++k) rgba[4 * idx + k] = acc[k] / spp;
+    }
+}
