@@ -1,0 +1,136 @@
+/*
+ * cloak.h -- C ABI of the GB300 (sm_103a) renderer for light rays through the
+ * non-magnetic uniaxial cylindrical invisibility cloaks of Halimeh & Wegener,
+ * "Photorealistic ray tracing of free-space invisibility cloaks made of
+ * uniaxial dielectrics" (arXiv:1209.6038).
+ *
+ * Conventions (all entry points):
+ *   - Units c0 = omega = 1: a vacuum ray has |k| = |v| = 1, time t is the
+ *     integration variable of Eq. 2 / Eq. 8 and also the time of flight.
+ *   - The cylinder axis is +z.  The cloak shell is R1 <= r <= R2,
+ *     |z| <= height/2; a metal cylinder fills r <= R1, |z| <= height/2.
+ *   - Device buffers are allocated and owned by the caller; the library
+ *     writes them asynchronously on the caller's CUDA stream (`cuda_stream`
+ *     is a cudaStream_t passed as void*, NULL = legacy default stream).
+ *   - The library owns only the handle and its internal scratch memory.
+ *   - Every call returns CLOAK_OK or an error code and never aborts; the
+ *     reason of the last failure on the calling thread is returned by
+ *     cloak_last_error().  Argument errors are detected before any launch;
+ *     launch errors are reported as CLOAK_ECUDA.
+ *   - A handle is not thread-safe: serialise calls on one handle.
+ */
+#ifndef CLOAK_H
+#define CLOAK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cloak cloak_t; /* opaque handle */
+
+/* cloak variants */
+enum {
+    CLOAK_RADIAL = 0,                /* Eq. 14: optic axis along r-hat (Sect. 4) */
+    CLOAK_AZIMUTHAL = 1,             /* Eq. 15: optic axis along theta-hat (Sect. 4) */
+    CLOAK_TEST_UNIAXIAL_CONST = 100  /* homogeneous uniaxial medium of Eq. 1 with a fixed optic axis
+                                        filling r <= R2 (requires R1 = 0); for interface tests */
+};
+/* polarization mode traced through the medium (Sect. 2) */
+enum { CLOAK_POL_ORDINARY = 0, CLOAK_POL_EXTRAORDINARY = 1 };
+/* integrators for Eq. 2 / Eq. 8 */
+enum {
+    CLOAK_RK4 = 0,  /* classical fourth-order Runge-Kutta at a fixed step h in t (Sect. 4) */
+    CLOAK_DP45 = 1  /* Dormand-Prince 5(4), adaptive, tolerance tol */
+};
+/* arithmetic of the integrator */
+enum {
+    CLOAK_FP64 = 0,  /* all of the path in FP64 */
+    CLOAK_MIXED = 1  /* RK stepping in FP32 with FP64 state accumulation; FP64 near r = R1 and for
+                        the interface and exit root solves */
+};
+/* kernel schedule */
+enum {
+    CLOAK_SCHED_PLAIN = 0,     /* one thread per pixel, whole path in one kernel (FP64 comparator) */
+    CLOAK_SCHED_WAVEFRONT = 1  /* camera/entry, compacted integration and exit/shade stages */
+};
+/* return codes */
+enum { CLOAK_OK = 0, CLOAK_EINVAL = 1, CLOAK_ENOMEM = 2, CLOAK_ECUDA = 3, CLOAK_ETIMEOUT = 4, CLOAK_ESTATE = 5 };
+/* per-ray status in cloak_record.status */
+enum {
+    CLOAK_RAY_MISSED = 0,           /* the camera ray never meets the cylinder */
+    CLOAK_RAY_EXITED = 1,           /* went through the cloak and left it */
+    CLOAK_RAY_HIT_METAL_EXITED = 2, /* mirrored at r = R1 (radial ordinary rays, Sect. 4), then left */
+    CLOAK_RAY_NO_TRANSMISSION = 3,  /* the chosen mode is evanescent at the entry face */
+    CLOAK_RAY_TIR = 4,              /* total internal reflection at the exit face (weight 0) */
+    CLOAK_RAY_STEP_LIMIT = 5,       /* max_steps reached or adaptive step below 1e-14 */
+    CLOAK_RAY_SINGULAR = 6,         /* reached r = R1 in a mode without a mirror rule */
+    CLOAK_RAY_METAL_CAP = 7         /* mirrored off a metal end disc (r <= R1) from outside */
+};
+
+/* 80-byte per-ray (per-sample) result */
+typedef struct cloak_record {
+    double exit_pos[3]; /* start point of the final vacuum ray */
+    double exit_dir[3]; /* unit direction of the final vacuum ray */
+    double tof;         /* time spent inside the cloak */
+    double weight;      /* T_in * T_out from Eq. 12 along the physical direction of light
+                           (unpolarised source); 1 for rays that miss or hit a metal disc */
+    int32_t tile_id;    /* (face << 20) | (i << 10) | j of the room tile hit, -1 for none */
+    int32_t status;     /* CLOAK_RAY_* */
+    int32_t steps;      /* integrator step attempts */
+    int32_t mode;       /* CLOAK_POL_* traced */
+} cloak_record;
+
+/* Create a cloak.  variant: CLOAK_RADIAL / CLOAK_AZIMUTHAL (Eqs. 14, 15 with
+ * a = R1, b = R2; needs 0 < R1 < R2) or CLOAK_TEST_UNIAXIAL_CONST (needs
+ * R1 = 0).  height > 0.  Defaults: camera at (5,0,0) looking at the origin,
+ * 60 deg horizontal field of view, 128x96; RK4 with h = 1e-3, FP64,
+ * max_steps = 1e6; plain schedule; room seed 0.
+ * Returns NULL on error (see cloak_last_error()).  Needs a current CUDA device. */
+cloak_t *cloak_create(int variant, double R1, double R2, double height);
+/* Release the handle and its scratch memory (synchronises the device). NULL is ignored. */
+void cloak_destroy(cloak_t *h);
+/* Message of the last failed call on this thread ("" if none).  Owned by the library. */
+const char *cloak_last_error(void);
+
+/* Pinhole camera: eye, look-at target, up vector (host arrays of 3 doubles),
+ * horizontal field of view in degrees (0 < hfov < 180), image size in pixels
+ * (width, height >= 1, width*height <= 2^31 - 1).  Row 0 is the top row. */
+int cloak_camera_set(cloak_t *h, const double eye[3], const double target[3], const double up[3], double hfov_deg,
+                     int width, int height);
+/* Integrator (Sect. 4 and its adaptive form): kind CLOAK_RK4 with h_or_tol = step h > 0, or CLOAK_DP45
+ * with h_or_tol = tolerance > 0 (error norm max_i |err_i| / (tol + tol max(|y_i|, |y_i'|)), safety 0.9,
+ * step factor in [0.2, 5], initial step 1e-3).  precision CLOAK_FP64 or CLOAK_MIXED.
+ * max_steps >= 1 bounds the step attempts of one ray. */
+int cloak_set_integrator(cloak_t *h, int kind, double h_or_tol, int precision, long max_steps);
+/* Medium of CLOAK_TEST_UNIAXIAL_CONST (Eq. 1): eps_o, eps_e > 0, optic axis c_hat (host, 3 doubles,
+ * nonzero; normalised internally).  CLOAK_ESTATE for other variants. */
+int cloak_set_test_medium(cloak_t *h, double eps_o, double eps_e, const double c_hat[3]);
+/* Seed of the procedural room that stands in for the paper's scenery (checkered walls and floor,
+ * 8 tiles per unit, box x,y in [-10,10], z in [-height/2, -height/2 + 10]). */
+int cloak_set_scene_seed(cloak_t *h, unsigned long long seed);
+/* Kernel schedule (CLOAK_SCHED_*).  packet: threads per block of the integration stage
+ * (32..1024, multiple of 32, 0 = default); steps_per_round: reserved (0). */
+int cloak_set_schedule(cloak_t *h, int schedule, int packet, int steps_per_round);
+
+/* Render one image of the chosen polarization (Sect. 4): dev_rgba is float4[width*height]
+ * (bytes >= 16*width*height), RGB = mean over the spp samples of weight * colour, A = mean weight.
+ * spp >= 1; one sample goes through the pixel centre, more samples are jittered from
+ * splitmix64(seed, pixel, sample, dim).  polarization: CLOAK_POL_*. */
+int cloak_render(cloak_t *h, int polarization, int spp, unsigned long long seed, void *dev_rgba, size_t bytes,
+                 void *cuda_stream);
+/* As cloak_render, but writes one cloak_record per sample: dev_records is
+ * cloak_record[width*height*spp] (sample s of pixel p at p*spp + s). */
+int cloak_render_records(cloak_t *h, int polarization, int spp, unsigned long long seed, void *dev_records,
+                         size_t bytes, void *cuda_stream);
+/* Trace n >= 0 arbitrary rays without a camera: dev_rays is double[n][6] (origin xyz, unit direction
+ * xyz; origins outside the cylinder), dev_records is cloak_record[n].  Both device memory. */
+int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long n, void *dev_records,
+                     void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLOAK_H */

@@ -1,0 +1,212 @@
+"""Thin Python binding of the C ABI in include/cloak.h (argument marshalling only).
+
+The functions carry the C names; every step of the rendering path runs in the
+CUDA kernels of libcloak.so.  Device buffers are torch tensors; the current
+torch stream is passed as the CUDA stream.  Loading fails loudly when the
+library has not been built -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcloak.so")
+
+RADIAL, AZIMUTHAL, TEST_UNIAXIAL_CONST = 0, 1, 100
+POL_ORDINARY, POL_EXTRAORDINARY = 0, 1
+RK4, DP45 = 0, 1
+FP64, MIXED = 0, 1
+SCHED_PLAIN, SCHED_WAVEFRONT = 0, 1
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
+RAY_STATUS = {0: "MISSED", 1: "EXITED", 2: "HIT_METAL_EXITED", 3: "NO_TRANSMISSION", 4: "TIR",
+              5: "STEP_LIMIT", 6: "SINGULAR", 7: "METAL_CAP"}
+
+RECORD_DTYPE = np.dtype([("exit_pos", "<f8", 3), ("exit_dir", "<f8", 3), ("tof", "<f8"), ("weight", "<f8"),
+                         ("tile_id", "<i4"), ("status", "<i4"), ("steps", "<i4"), ("mode", "<i4")])
+RECORD_BYTES = 80
+
+# name -> (restype, argtypes) of every entry point declared in include/cloak.h
+_d3 = C.POINTER(C.c_double)
+SIGNATURES = {
+    "cloak_create": (C.c_void_p, [C.c_int, C.c_double, C.c_double, C.c_double]),
+    "cloak_destroy": (None, [C.c_void_p]),
+    "cloak_last_error": (C.c_char_p, []),
+    "cloak_camera_set": (C.c_int, [C.c_void_p, _d3, _d3, _d3, C.c_double, C.c_int, C.c_int]),
+    "cloak_set_integrator": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_long]),
+    "cloak_set_test_medium": (C.c_int, [C.c_void_p, C.c_double, C.c_double, _d3]),
+    "cloak_set_scene_seed": (C.c_int, [C.c_void_p, C.c_ulonglong]),
+    "cloak_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "cloak_render": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "cloak_render_records": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
+                                       C.c_void_p]),
+    "cloak_trace_rays": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
+}
+
+_lib = None
+
+
+class CloakError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cloak error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load libcloak.so and declare the signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it first (python -c 'import __graft_entry__ as g; "
+                               "g.build()'); there is no CPU fallback")
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise CloakError(rc, load().cloak_last_error().decode())
+    return rc
+
+
+def _vec3(v):
+    return (C.c_double * 3)(*[float(x) for x in v])
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------ C names
+def cloak_create(variant, R1, R2, height):
+    h = load().cloak_create(variant, R1, R2, height)
+    if not h:
+        raise CloakError(EINVAL, load().cloak_last_error().decode())
+    return C.c_void_p(h)
+
+
+def cloak_destroy(h):
+    load().cloak_destroy(h)
+
+
+def cloak_last_error():
+    return load().cloak_last_error().decode()
+
+
+def cloak_camera_set(h, eye, target, up, hfov_deg, width, height):
+    return _check(load().cloak_camera_set(h, _vec3(eye), _vec3(target), _vec3(up), hfov_deg, width, height))
+
+
+def cloak_set_integrator(h, kind, h_or_tol, precision=FP64, max_steps=1_000_000):
+    return _check(load().cloak_set_integrator(h, kind, h_or_tol, precision, max_steps))
+
+
+def cloak_set_test_medium(h, eps_o, eps_e, c_hat):
+    return _check(load().cloak_set_test_medium(h, eps_o, eps_e, _vec3(c_hat)))
+
+
+def cloak_set_scene_seed(h, seed):
+    return _check(load().cloak_set_scene_seed(h, seed))
+
+
+def cloak_set_schedule(h, schedule, packet=0, steps_per_round=0):
+    return _check(load().cloak_set_schedule(h, schedule, packet, steps_per_round))
+
+
+def cloak_render(h, polarization, spp, seed, rgba, stream=None):
+    """rgba: float32 CUDA tensor with >= 4*W*H elements."""
+    return _check(load().cloak_render(h, polarization, spp, seed, C.c_void_p(rgba.data_ptr()),
+                                      rgba.numel() * rgba.element_size(), _stream_ptr(stream)))
+
+
+def cloak_render_records(h, polarization, spp, seed, records, stream=None):
+    """records: uint8 (or any) CUDA tensor of >= 80*W*H*spp bytes."""
+    return _check(load().cloak_render_records(h, polarization, spp, seed, C.c_void_p(records.data_ptr()),
+                                              records.numel() * records.element_size(), _stream_ptr(stream)))
+
+
+def cloak_trace_rays(h, polarization, rays, n, records, stream=None):
+    """rays: float64 CUDA tensor (n, 6); records: CUDA tensor of >= 80*n bytes."""
+    if records.numel() * records.element_size() < RECORD_BYTES * n or rays.numel() < 6 * n:
+        raise CloakError(EINVAL, "buffer too small")
+    return _check(load().cloak_trace_rays(h, polarization, C.c_void_p(rays.data_ptr()), n,
+                                          C.c_void_p(records.data_ptr()), _stream_ptr(stream)))
+
+
+# ------------------------------------------------------------------ convenience
+def records_to_numpy(buf) -> np.ndarray:
+    """Copy a device record buffer to a structured numpy array (cloak_record layout)."""
+    return buf.cpu().numpy().view(np.uint8).view(RECORD_DTYPE)
+
+
+class Cloak:
+    """Owning wrapper around a cloak_t handle."""
+
+    def __init__(self, variant=RADIAL, R1=0.5, R2=1.0, height=2.0):
+        self.h = cloak_create(variant, R1, R2, height)
+        self.width, self.height = 128, 96
+
+    def close(self):
+        if self.h is not None:
+            cloak_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def camera(self, eye, target=(0, 0, 0), up=(0, 0, 1), hfov_deg=60.0, width=128, height=96):
+        cloak_camera_set(self.h, eye, target, up, hfov_deg, width, height)
+        self.width, self.height = width, height
+        return self
+
+    def integrator(self, kind=RK4, h_or_tol=1e-3, precision=FP64, max_steps=1_000_000):
+        cloak_set_integrator(self.h, kind, h_or_tol, precision, max_steps)
+        return self
+
+    def schedule(self, schedule=SCHED_PLAIN, packet=0, steps_per_round=0):
+        cloak_set_schedule(self.h, schedule, packet, steps_per_round)
+        return self
+
+    def test_medium(self, eps_o, eps_e, c_hat):
+        cloak_set_test_medium(self.h, eps_o, eps_e, c_hat)
+        return self
+
+    def scene_seed(self, seed):
+        cloak_set_scene_seed(self.h, seed)
+        return self
+
+    def render(self, polarization, spp=1, seed=0, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.height, self.width, 4), dtype=torch.float32, device="cuda")
+        cloak_render(self.h, polarization, spp, seed, out, stream)
+        return out
+
+    def render_records(self, polarization, spp=1, seed=0, out=None, stream=None):
+        import torch
+        n = self.width * self.height * spp
+        if out is None:
+            out = torch.empty(n * RECORD_BYTES, dtype=torch.uint8, device="cuda")
+        cloak_render_records(self.h, polarization, spp, seed, out, stream)
+        return out
+
+    def trace_rays(self, polarization, rays, out=None, stream=None):
+        import torch
+        rays = rays.to(device="cuda", dtype=torch.float64).contiguous()
+        n = rays.shape[0]
+        if out is None:
+            out = torch.empty(max(n, 1) * RECORD_BYTES, dtype=torch.uint8, device="cuda")
+        cloak_trace_rays(self.h, polarization, rays, n, out, stream)
+        return out

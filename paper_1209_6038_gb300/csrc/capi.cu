@@ -1,0 +1,275 @@
+// capi.cu -- the C ABI of include/cloak.h: handle lifetime, argument checks, launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+struct cloak {
+    int variant;
+    double R1, R2, H;
+    double eo_t, ee_t, c_t[3];
+    unsigned long long scene_seed;
+    double eye[3], target[3], up[3], hfov;
+    int W, Hp;
+    int integ;
+    double h_or_tol;
+    int precision;
+    long max_steps;
+    int schedule, packet, steps_per_round;
+    int device;
+};
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+static int cuda_fail(cudaError_t e, const char *where) {
+    return fail(CLOAK_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+static bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+// Camera frame and material constants for the kernels.
+static int make_params(const cloak *h, ck::Params &p) {
+    memset(&p, 0, sizeof(p));
+    p.variant = h->variant == CLOAK_RADIAL ? ck::V_RADIAL : h->variant == CLOAK_AZIMUTHAL ? ck::V_AZIMUTHAL : ck::V_TEST;
+    p.R1 = h->R1;
+    p.R2 = h->R2;
+    p.H = h->H;
+    p.halfH = 0.5 * h->H;
+    double kk = h->R2 / (h->R2 - h->R1);
+    p.K = kk * kk;
+    p.invK = 1.0 / p.K;
+    p.R1x2 = 2.0 * h->R1;
+    p.eo_t = h->eo_t;
+    p.ee_t = h->ee_t;
+    double cl = std::sqrt(h->c_t[0] * h->c_t[0] + h->c_t[1] * h->c_t[1] + h->c_t[2] * h->c_t[2]);
+    for (int i = 0; i < 3; ++i) p.c_t[i] = h->c_t[i] / cl;
+    p.scene_seed = h->scene_seed;
+    p.integ = h->integ == CLOAK_RK4 ? ck::I_RK4 : ck::I_DP45;
+    p.h_or_tol = h->h_or_tol;
+    p.max_steps = h->max_steps;
+    double w[3], u[3], v[3];
+    for (int i = 0; i < 3; ++i) w[i] = h->target[i] - h->eye[i];
+    double l = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (!(l > 0)) return fail(CLOAK_EINVAL, "camera eye and target coincide");
+    for (int i = 0; i < 3; ++i) w[i] /= l;
+    u[0] = w[1] * h->up[2] - w[2] * h->up[1];
+    u[1] = w[2] * h->up[0] - w[0] * h->up[2];
+    u[2] = w[0] * h->up[1] - w[1] * h->up[0];
+    l = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (!(l > 1e-300)) return fail(CLOAK_EINVAL, "camera up vector is parallel to the view direction");
+    for (int i = 0; i < 3; ++i) u[i] /= l;
+    v[0] = u[1] * w[2] - u[2] * w[1];
+    v[1] = u[2] * w[0] - u[0] * w[2];
+    v[2] = u[0] * w[1] - u[1] * w[0];
+    for (int i = 0; i < 3; ++i) {
+        p.eye[i] = h->eye[i];
+        p.fw[i] = w[i];
+        p.rt[i] = u[i];
+        p.up[i] = v[i];
+    }
+    p.tx = std::tan(0.5 * h->hfov * M_PI / 180.0);
+    p.ty = p.tx * (double)h->Hp / (double)h->W;
+    p.W = h->W;
+    p.Hp = h->Hp;
+    return CLOAK_OK;
+}
+
+static int use_device(const cloak *h) {
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return CLOAK_OK;
+}
+
+extern "C" {
+
+const char *cloak_last_error(void) { return g_err.c_str(); }
+
+cloak_t *cloak_create(int variant, double R1, double R2, double height) {
+    if (variant != CLOAK_RADIAL && variant != CLOAK_AZIMUTHAL && variant != CLOAK_TEST_UNIAXIAL_CONST) {
+        fail(CLOAK_EINVAL, "unknown variant %d", variant);
+        return nullptr;
+    }
+    if (!(std::isfinite(R1) && std::isfinite(R2) && std::isfinite(height) && height > 0 && R2 > 0)) {
+        fail(CLOAK_EINVAL, "geometry must be finite with R2 > 0 and height > 0");
+        return nullptr;
+    }
+    if (variant == CLOAK_TEST_UNIAXIAL_CONST ? (R1 != 0.0) : !(R1 > 0 && R1 < R2)) {
+        fail(CLOAK_EINVAL, variant == CLOAK_TEST_UNIAXIAL_CONST ? "test medium needs R1 = 0" : "need 0 < R1 < R2");
+        return nullptr;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "cudaGetDevice");
+        return nullptr;
+    }
+    cloak *h = new (std::nothrow) cloak();
+    if (!h) {
+        fail(CLOAK_ENOMEM, "out of host memory");
+        return nullptr;
+    }
+    h->variant = variant;
+    h->R1 = R1;
+    h->R2 = R2;
+    h->H = height;
+    h->eo_t = h->ee_t = 1.0;
+    h->c_t[0] = 0; h->c_t[1] = 0; h->c_t[2] = 1;
+    h->scene_seed = 0;
+    h->eye[0] = 5; h->eye[1] = 0; h->eye[2] = 0;
+    h->target[0] = h->target[1] = h->target[2] = 0;
+    h->up[0] = 0; h->up[1] = 0; h->up[2] = 1;
+    h->hfov = 60.0;
+    h->W = 128;
+    h->Hp = 96;
+    h->integ = CLOAK_RK4;
+    h->h_or_tol = 1e-3;
+    h->precision = CLOAK_FP64;
+    h->max_steps = 1000000;
+    h->schedule = CLOAK_SCHED_PLAIN;
+    h->packet = 0;
+    h->steps_per_round = 0;
+    h->device = dev;
+    g_err.clear();
+    return h;
+}
+
+void cloak_destroy(cloak_t *h) {
+    if (!h) return;
+    delete h;
+}
+
+int cloak_camera_set(cloak_t *h, const double eye[3], const double target[3], const double up[3], double hfov_deg,
+                     int width, int height) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (!eye || !target || !up) return fail(CLOAK_EINVAL, "null camera vector");
+    if (!finite3(eye) || !finite3(target) || !finite3(up)) return fail(CLOAK_EINVAL, "camera vectors must be finite");
+    if (!(hfov_deg > 0 && hfov_deg < 180)) return fail(CLOAK_EINVAL, "hfov must be in (0, 180) degrees");
+    if (width < 1 || height < 1 || (long long)width * height > 2147483647LL)
+        return fail(CLOAK_EINVAL, "image size %dx%d out of range", width, height);
+    cloak tmp = *h;
+    for (int i = 0; i < 3; ++i) { tmp.eye[i] = eye[i]; tmp.target[i] = target[i]; tmp.up[i] = up[i]; }
+    tmp.hfov = hfov_deg;
+    tmp.W = width;
+    tmp.Hp = height;
+    ck::Params p;
+    int rc = make_params(&tmp, p);
+    if (rc != CLOAK_OK) return rc;
+    *h = tmp;
+    return CLOAK_OK;
+}
+
+int cloak_set_integrator(cloak_t *h, int kind, double h_or_tol, int precision, long max_steps) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (kind != CLOAK_RK4 && kind != CLOAK_DP45) return fail(CLOAK_EINVAL, "unknown integrator %d", kind);
+    if (!(std::isfinite(h_or_tol) && h_or_tol > 0)) return fail(CLOAK_EINVAL, "step / tolerance must be > 0");
+    if (precision != CLOAK_FP64 && precision != CLOAK_MIXED) return fail(CLOAK_EINVAL, "unknown precision %d", precision);
+    if (max_steps < 1 || max_steps > 2000000000L) return fail(CLOAK_EINVAL, "max_steps out of range");
+    h->integ = kind;
+    h->h_or_tol = h_or_tol;
+    h->precision = precision;
+    h->max_steps = max_steps;
+    return CLOAK_OK;
+}
+
+int cloak_set_test_medium(cloak_t *h, double eps_o, double eps_e, const double c_hat[3]) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (h->variant != CLOAK_TEST_UNIAXIAL_CONST) return fail(CLOAK_ESTATE, "not a test-medium handle");
+    if (!c_hat || !finite3(c_hat)) return fail(CLOAK_EINVAL, "optic axis must be finite");
+    double l = std::sqrt(c_hat[0] * c_hat[0] + c_hat[1] * c_hat[1] + c_hat[2] * c_hat[2]);
+    if (!(l > 0) || !(eps_o > 0) || !(eps_e > 0) || !std::isfinite(eps_o) || !std::isfinite(eps_e))
+        return fail(CLOAK_EINVAL, "need eps_o, eps_e > 0 and a nonzero optic axis");
+    h->eo_t = eps_o;
+    h->ee_t = eps_e;
+    for (int i = 0; i < 3; ++i) h->c_t[i] = c_hat[i];
+    return CLOAK_OK;
+}
+
+int cloak_set_scene_seed(cloak_t *h, unsigned long long seed) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    h->scene_seed = seed;
+    return CLOAK_OK;
+}
+
+int cloak_set_schedule(cloak_t *h, int schedule, int packet, int steps_per_round) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (schedule != CLOAK_SCHED_PLAIN && schedule != CLOAK_SCHED_WAVEFRONT)
+        return fail(CLOAK_EINVAL, "unknown schedule %d", schedule);
+    if (packet != 0 && (packet < 32 || packet > 1024 || packet % 32))
+        return fail(CLOAK_EINVAL, "packet must be 0 or a multiple of 32 in [32, 1024]");
+    if (steps_per_round < 0) return fail(CLOAK_EINVAL, "steps_per_round must be >= 0");
+    h->schedule = schedule;
+    h->packet = packet;
+    h->steps_per_round = steps_per_round;
+    return CLOAK_OK;
+}
+
+int cloak_render(cloak_t *h, int polarization, int spp, unsigned long long seed, void *dev_rgba, size_t bytes,
+                 void *cuda_stream) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (polarization != CLOAK_POL_ORDINARY && polarization != CLOAK_POL_EXTRAORDINARY)
+        return fail(CLOAK_EINVAL, "unknown polarization %d", polarization);
+    if (spp < 1 || spp > 65536) return fail(CLOAK_EINVAL, "spp must be in [1, 65536]");
+    size_t need = (size_t)h->W * h->Hp * 16;
+    if (!dev_rgba) return fail(CLOAK_EINVAL, "null output buffer");
+    if (bytes < need) return fail(CLOAK_EINVAL, "output buffer holds %zu bytes, needs %zu", bytes, need);
+    ck::Params p;
+    int rc = make_params(h, p);
+    if (rc) return rc;
+    if ((rc = use_device(h))) return rc;
+    cudaError_t e = ck::launch_render_plain(p, polarization, spp, seed, (float4 *)dev_rgba, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "render launch");
+    return CLOAK_OK;
+}
+
+int cloak_render_records(cloak_t *h, int polarization, int spp, unsigned long long seed, void *dev_records,
+                         size_t bytes, void *cuda_stream) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (polarization != CLOAK_POL_ORDINARY && polarization != CLOAK_POL_EXTRAORDINARY)
+        return fail(CLOAK_EINVAL, "unknown polarization %d", polarization);
+    if (spp < 1 || spp > 65536) return fail(CLOAK_EINVAL, "spp must be in [1, 65536]");
+    size_t need = (size_t)h->W * h->Hp * spp * sizeof(cloak_record);
+    if (!dev_records) return fail(CLOAK_EINVAL, "null output buffer");
+    if (bytes < need) return fail(CLOAK_EINVAL, "record buffer holds %zu bytes, needs %zu", bytes, need);
+    ck::Params p;
+    int rc = make_params(h, p);
+    if (rc) return rc;
+    if ((rc = use_device(h))) return rc;
+    cudaError_t e = ck::launch_records_plain(p, polarization, spp, seed, (cloak_record *)dev_records,
+                                             (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "records launch");
+    return CLOAK_OK;
+}
+
+int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long n, void *dev_records,
+                     void *cuda_stream) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (polarization != CLOAK_POL_ORDINARY && polarization != CLOAK_POL_EXTRAORDINARY)
+        return fail(CLOAK_EINVAL, "unknown polarization %d", polarization);
+    if (n < 0) return fail(CLOAK_EINVAL, "n must be >= 0");
+    if (n == 0) return CLOAK_OK;
+    if (!dev_rays || !dev_records) return fail(CLOAK_EINVAL, "null buffer");
+    ck::Params p;
+    int rc = make_params(h, p);
+    if (rc) return rc;
+    if ((rc = use_device(h))) return rc;
+    cudaError_t e = ck::launch_trace_rays(p, polarization, dev_rays, n, (cloak_record *)dev_records,
+                                          (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "trace launch");
+    return CLOAK_OK;
+}
+
+}  // extern "C"

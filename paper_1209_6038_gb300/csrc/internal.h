@@ -1,0 +1,49 @@
+// internal.h -- declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "cloak.h"
+#include "physics.cuh"
+
+namespace ck {
+
+template <int V>
+cudaError_t launch_render_plain_v(const Params &p, int mode, int spp, unsigned long long seed, float4 *out,
+                                  cudaStream_t st);
+template <int V>
+cudaError_t launch_records_plain_v(const Params &p, int mode, int spp, unsigned long long seed, cloak_record *out,
+                                   cudaStream_t st);
+template <int V>
+cudaError_t launch_trace_rays_v(const Params &p, int mode, const double *rays, long long n, cloak_record *out,
+                                cudaStream_t st);
+extern template cudaError_t launch_render_plain_v<0>(const Params &, int, int, unsigned long long, float4 *, cudaStream_t);
+extern template cudaError_t launch_render_plain_v<1>(const Params &, int, int, unsigned long long, float4 *, cudaStream_t);
+extern template cudaError_t launch_render_plain_v<2>(const Params &, int, int, unsigned long long, float4 *, cudaStream_t);
+extern template cudaError_t launch_records_plain_v<0>(const Params &, int, int, unsigned long long, cloak_record *, cudaStream_t);
+extern template cudaError_t launch_records_plain_v<1>(const Params &, int, int, unsigned long long, cloak_record *, cudaStream_t);
+extern template cudaError_t launch_records_plain_v<2>(const Params &, int, int, unsigned long long, cloak_record *, cudaStream_t);
+extern template cudaError_t launch_trace_rays_v<0>(const Params &, int, const double *, long long, cloak_record *, cudaStream_t);
+extern template cudaError_t launch_trace_rays_v<1>(const Params &, int, const double *, long long, cloak_record *, cudaStream_t);
+extern template cudaError_t launch_trace_rays_v<2>(const Params &, int, const double *, long long, cloak_record *, cudaStream_t);
+
+inline cudaError_t launch_render_plain(const Params &p, int mode, int spp, unsigned long long seed, float4 *out,
+                                cudaStream_t st) {
+    if (p.variant == V_RADIAL) return launch_render_plain_v<0>(p, mode, spp, seed, out, st);
+    if (p.variant == V_AZIMUTHAL) return launch_render_plain_v<1>(p, mode, spp, seed, out, st);
+    return launch_render_plain_v<2>(p, mode, spp, seed, out, st);
+}
+inline cudaError_t launch_records_plain(const Params &p, int mode, int spp, unsigned long long seed, cloak_record *out,
+                                 cudaStream_t st) {
+    if (p.variant == V_RADIAL) return launch_records_plain_v<0>(p, mode, spp, seed, out, st);
+    if (p.variant == V_AZIMUTHAL) return launch_records_plain_v<1>(p, mode, spp, seed, out, st);
+    return launch_records_plain_v<2>(p, mode, spp, seed, out, st);
+}
+inline cudaError_t launch_trace_rays(const Params &p, int mode, const double *rays, long long n, cloak_record *out,
+                              cudaStream_t st) {
+    if (p.variant == V_RADIAL) return launch_trace_rays_v<0>(p, mode, rays, n, out, st);
+    if (p.variant == V_AZIMUTHAL) return launch_trace_rays_v<1>(p, mode, rays, n, out, st);
+    return launch_trace_rays_v<2>(p, mode, rays, n, out, st);
+}
+
+}  // namespace ck

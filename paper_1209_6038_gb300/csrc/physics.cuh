@@ -1,0 +1,621 @@
+// physics.cuh -- device-side physics of the uniaxial cylindrical cloaks
+// (Halimeh & Wegener, arXiv:1209.6038), written for sm_103a.
+//
+// Formulation used on the GPU (equivalent to the paper's equations, chosen for
+// few FP64 operations per evaluation):
+//   * Eq. 7 with Eq. 14 / 15: in the cylindrical frame (r, theta, z) the
+//     auxiliary matrix is diagonal, M = diag(K, f, g) with f = K((r-R1)/r)^2,
+//     K = (R2/(R2-R1))^2 and g = f (radial, Eq. 14) or g = K (azimuthal,
+//     Eq. 15).  The ordinary ray sees M_o = eps_o I with eps_o = K (radial) or
+//     f (azimuthal).
+//   * Eq. 8 (and Eq. 2 as its special case M = n^2 I) for a diagonal
+//     M = diag(A(r), B(r), G(r)) with A = K constant reduces to
+//       a_r = [ B' v_t^2/2 + G' v_z^2/2 - (A - B) v_t^2 / r ] / A  (+ -A' v_r^2/2A)
+//       a_t = -(B'/B) v_r v_t,   a_z = -(G'/G) v_r v_z
+//     with B'/B = f'/f = 2 R1 / (r (r - R1)).
+//   * Sect. 3 entry refraction: tangential k is conserved and the normal
+//     component q solves (n^T M^-1 n) q^2 + 2 (n^T M^-1 k_t) q + k_t^T M^-1 k_t - 1 = 0
+//     (the extraordinary index surface of Eq. 9), root with inward ray velocity.
+//   * Eq. 12 transmission from the 4x4 continuity system of tangential E, H.
+#pragma once
+
+#include <cstdint>
+
+#include "cloak.h"
+
+namespace ck {
+
+enum { V_RADIAL = 0, V_AZIMUTHAL = 1, V_TEST = 2 };
+enum { M_ORD = 0, M_EXT = 1 };
+enum { I_RK4 = 0, I_DP45 = 1 };
+
+struct Params {
+    int variant;  // V_*
+    double R1, R2, H, halfH, K, invK, R1x2;
+    double eo_t, ee_t, c_t[3];  // homogeneous test medium
+    unsigned long long scene_seed;
+    int integ;
+    double h_or_tol;
+    long long max_steps;
+    // camera
+    double eye[3], fw[3], rt[3], up[3], tx, ty;
+    int W, Hp;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
+    return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+}
+
+// splitmix64 mixing step (Steele, Lea & Flood 2014)
+__device__ __forceinline__ uint64_t sm64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ double jitter(uint64_t seed, uint64_t pix, uint32_t s, uint32_t dim) {
+    uint64_t h = sm64(sm64(sm64(seed) ^ pix) ^ ((uint64_t(s) << 8) | dim));
+    return double(h >> 11) * 0x1.0p-53;
+}
+
+// ------------------------------------------------------------------ material
+// Local uniaxial material (eps_o, eps_e, optic axis c) at x (Eqs. 1, 14, 15).
+__device__ __forceinline__ void local_material(const Params &p, const double x[3], double &eo, double &ee,
+                                               double c[3]) {
+    if (p.variant == V_TEST) {
+        eo = p.eo_t;
+        ee = p.ee_t;
+        c[0] = p.c_t[0]; c[1] = p.c_t[1]; c[2] = p.c_t[2];
+        return;
+    }
+    double r = hypot(x[0], x[1]);
+    double q = (r - p.R1) / r;
+    double f = p.K * q * q;
+    double cx = x[0] / r, cy = x[1] / r;
+    if (p.variant == V_RADIAL) {
+        eo = p.K; ee = f;
+        c[0] = cx; c[1] = cy; c[2] = 0.0;
+    } else {
+        eo = f; ee = p.K;
+        c[0] = -cy; c[1] = cx; c[2] = 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ equation of motion
+// dv/dt of Eq. 8 (extraordinary) or Eq. 2 (ordinary) at (x, v); cylindrical closed form.
+template <int VAR, int MODE, typename T>
+__device__ __forceinline__ void accel(T R1, T K, T invK, T x, T y, T vx, T vy, T vz, T &ax, T &ay, T &az) {
+    if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD)) {  // homogeneous: straight lines (Sect. 4)
+        ax = T(0); ay = T(0); az = T(0);
+        return;
+    }
+    T r2 = x * x + y * y;
+    T ir = T(1) / sqrt(r2);
+    T r = r2 * ir;
+    T cx = x * ir, cy = y * ir;
+    T vr = vx * cx + vy * cy;
+    T vt = vy * cx - vx * cy;
+    T u = r - R1;
+    T g = T(2) * R1 * ir / u;  // f'/f
+    T ar, at, azz;
+    if (MODE == M_EXT) {
+        T q = u * ir;
+        T f = K * q * q;
+        T fp = f * g;  // f'
+        T vt2 = vt * vt;
+        at = -g * vr * vt;
+        if (VAR == V_RADIAL) {  // M = diag(K, f, f)
+            ar = (T(0.5) * fp * (vt2 + vz * vz) - (K - f) * vt2 * ir) * invK;
+            azz = -g * vr * vz;
+        } else {  // M = diag(K, f, K)
+            ar = (T(0.5) * fp * vt2 - (K - f) * vt2 * ir) * invK;
+            azz = T(0);
+        }
+    } else {  // azimuthal ordinary: M = f I, Eq. 2 with n = sqrt(f)
+        T hg = T(0.5) * g;
+        ar = hg * (vt * vt + vz * vz - vr * vr);
+        at = -g * vr * vt;
+        azz = -g * vr * vz;
+    }
+    ax = ar * cx - at * cy;
+    ay = ar * cy + at * cx;
+    az = azz;
+}
+
+template <int VAR, int MODE>
+__device__ __forceinline__ void rhs(const Params &p, const double y[6], double dy[6]) {
+    dy[0] = y[3]; dy[1] = y[4]; dy[2] = y[5];
+    accel<VAR, MODE, double>(p.R1, p.K, p.invK, y[0], y[1], y[3], y[4], y[5], dy[3], dy[4], dy[5]);
+}
+
+// ------------------------------------------------------------------ integrators
+template <int VAR, int MODE>
+__device__ __forceinline__ void rk4_step(const Params &p, const double y[6], double h, double out[6]) {
+    double k[6], acc[6], t[6];
+    rhs<VAR, MODE>(p, y, k);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { acc[i] = k[i]; t[i] = fma(0.5 * h, k[i], y[i]); }
+    rhs<VAR, MODE>(p, t, k);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, k[i], acc[i]); t[i] = fma(0.5 * h, k[i], y[i]); }
+    rhs<VAR, MODE>(p, t, k);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, k[i], acc[i]); t[i] = fma(h, k[i], y[i]); }
+    rhs<VAR, MODE>(p, t, k);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out[i] = fma(h * (1.0 / 6.0), acc[i] + k[i], y[i]);
+}
+
+// Dormand-Prince 5(4) tableau (Dormand & Prince 1980)
+struct DP {
+    static constexpr double a21 = 1.0 / 5;
+    static constexpr double a31 = 3.0 / 40, a32 = 9.0 / 40;
+    static constexpr double a41 = 44.0 / 45, a42 = -56.0 / 15, a43 = 32.0 / 9;
+    static constexpr double a51 = 19372.0 / 6561, a52 = -25360.0 / 2187, a53 = 64448.0 / 6561, a54 = -212.0 / 729;
+    static constexpr double a61 = 9017.0 / 3168, a62 = -355.0 / 33, a63 = 46732.0 / 5247, a64 = 49.0 / 176,
+                            a65 = -5103.0 / 18656;
+    static constexpr double b1 = 35.0 / 384, b3 = 500.0 / 1113, b4 = 125.0 / 192, b5 = -2187.0 / 6784,
+                            b6 = 11.0 / 84;
+    // e = b5th - b4th
+    static constexpr double e1 = 35.0 / 384 - 5179.0 / 57600, e3 = 500.0 / 1113 - 7571.0 / 16695,
+                            e4 = 125.0 / 192 - 393.0 / 640, e5 = -2187.0 / 6784 + 92097.0 / 339200,
+                            e6 = 11.0 / 84 - 187.0 / 2100, e7 = -1.0 / 40;
+};
+
+// Fifth-order solution of one DP step of size h from y with first stage k1 = f(y).
+// If err != nullptr also returns k7 = f(out) and the embedded error estimate.
+template <int VAR, int MODE>
+__device__ __forceinline__ void dp45_step(const Params &p, const double y[6], const double k1[6], double h,
+                                          double out[6], double *err, double *k7) {
+    double k2[6], k3[6], k4[6], k5[6], k6[6], t[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = fma(h, DP::a21 * k1[i], y[i]);
+    rhs<VAR, MODE>(p, t, k2);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = fma(h, DP::a31 * k1[i] + DP::a32 * k2[i], y[i]);
+    rhs<VAR, MODE>(p, t, k3);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = fma(h, DP::a41 * k1[i] + DP::a42 * k2[i] + DP::a43 * k3[i], y[i]);
+    rhs<VAR, MODE>(p, t, k4);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        t[i] = fma(h, DP::a51 * k1[i] + DP::a52 * k2[i] + DP::a53 * k3[i] + DP::a54 * k4[i], y[i]);
+    rhs<VAR, MODE>(p, t, k5);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        t[i] = fma(h, DP::a61 * k1[i] + DP::a62 * k2[i] + DP::a63 * k3[i] + DP::a64 * k4[i] + DP::a65 * k5[i],
+                   y[i]);
+    rhs<VAR, MODE>(p, t, k6);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        out[i] = fma(h, DP::b1 * k1[i] + DP::b3 * k3[i] + DP::b4 * k4[i] + DP::b5 * k5[i] + DP::b6 * k6[i], y[i]);
+    if (err) {
+        rhs<VAR, MODE>(p, out, k7);
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            err[i] = h * (DP::e1 * k1[i] + DP::e3 * k3[i] + DP::e4 * k4[i] + DP::e5 * k5[i] + DP::e6 * k6[i] +
+                          DP::e7 * k7[i]);
+    }
+}
+
+// ------------------------------------------------------------------ surfaces
+enum { EV_LAT = 0, EV_TOP = 1, EV_BOT = 2, EV_METAL = 3 };
+__device__ __forceinline__ double event_g(const Params &p, int ev, const double y[6]) {
+    switch (ev) {
+    case EV_LAT: return hypot(y[0], y[1]) - p.R2;
+    case EV_TOP: return y[2] - p.halfH;
+    case EV_BOT: return -y[2] - p.halfH;
+    default: return p.R1 - hypot(y[0], y[1]);
+    }
+}
+
+// One step of size s from y with the integrator's own update (RK4, or the DP
+// fifth-order solution given k1 = f(y)).
+template <int VAR, int MODE, int INTEG>
+__device__ __forceinline__ void flow(const Params &p, const double y[6], const double k1[6], double s, double out[6]) {
+    if (INTEG == I_RK4) rk4_step<VAR, MODE>(p, y, s, out);
+    else dp45_step<VAR, MODE>(p, y, k1, s, out, nullptr, nullptr);
+}
+
+// Root s* in (0, h] of g(flow_s(y)) for a surface crossed by the step (g(0) <= 0 < g(h)):
+// Illinois-modified regula falsi with bisection safeguard, to machine resolution.
+// Returns the end of the final bracket beyond the surface (exits) or before it (metal).
+template <int VAR, int MODE, int INTEG>
+__device__ double crossing(const Params &p, const double y[6], const double k1[6], double h, double ghi, int ev) {
+    double lo = 0.0, hi = h, glo = event_g(p, ev, y), t[6];
+    if (!(glo <= 0.0)) glo = 0.0;
+    int side = 0;
+    for (int it = 0; it < 200; ++it) {
+        if (hi - lo <= 4.0e-16 * hi) break;
+        double s;
+        if (it < 60 && ghi > glo) s = (lo * ghi - hi * glo) / (ghi - glo);
+        else s = 0.5 * (lo + hi);
+        if (!(s > lo && s < hi)) s = 0.5 * (lo + hi);
+        if (!(s > lo && s < hi)) break;
+        flow<VAR, MODE, INTEG>(p, y, k1, s, t);
+        double gs = event_g(p, ev, t);
+        if (gs > 0.0) {
+            hi = s; ghi = gs;
+            if (side == 1) glo *= 0.5;
+            side = 1;
+        } else {
+            lo = s; glo = gs;
+            if (side == -1) ghi *= 0.5;
+            side = -1;
+        }
+    }
+    return ev == EV_METAL ? lo : hi;
+}
+
+// First entry of o + s d into the finite cylinder r <= R2, |z| <= H/2.
+// face: EV_LAT / EV_TOP / EV_BOT, or -1 for a miss.
+__device__ __forceinline__ int cylinder_entry(const Params &p, const double o[3], const double d[3], double pt[3],
+                                              double n[3]) {
+    double best = 1e300;
+    int face = -1;
+    double a = d[0] * d[0] + d[1] * d[1];
+    double b = o[0] * d[0] + o[1] * d[1];
+    double c = o[0] * o[0] + o[1] * o[1] - p.R2 * p.R2;
+    if (a > 0.0) {
+        double disc = b * b - a * c;
+        if (disc >= 0.0) {
+            double sq = sqrt(disc);
+            // nearer root of a s^2 + 2 b s + c = 0 in cancellation-free form
+            double s = (b < 0.0) ? c / (-b + sq) : (-b - sq) / a;
+            if (s > 0.0 && fabs(o[2] + s * d[2]) <= p.halfH) { best = s; face = EV_LAT; }
+        }
+    }
+    if (d[2] < 0.0) {
+        double s = (p.halfH - o[2]) / d[2];
+        double px = o[0] + s * d[0], py = o[1] + s * d[1];
+        if (s > 0.0 && px * px + py * py <= p.R2 * p.R2 && s < best) { best = s; face = EV_TOP; }
+    } else if (d[2] > 0.0) {
+        double s = (-p.halfH - o[2]) / d[2];
+        double px = o[0] + s * d[0], py = o[1] + s * d[1];
+        if (s > 0.0 && px * px + py * py <= p.R2 * p.R2 && s < best) { best = s; face = EV_BOT; }
+    }
+    if (face < 0) return -1;
+    for (int i = 0; i < 3; ++i) pt[i] = o[i] + best * d[i];
+    if (face == EV_LAT) {
+        double r = hypot(pt[0], pt[1]);
+        n[0] = pt[0] / r; n[1] = pt[1] / r; n[2] = 0.0;
+    } else {
+        n[0] = 0.0; n[1] = 0.0; n[2] = face == EV_TOP ? 1.0 : -1.0;
+    }
+    return face;
+}
+
+__device__ __forceinline__ void face_normal(int ev, const double x[3], double n[3]) {
+    if (ev == EV_LAT) {
+        double r = hypot(x[0], x[1]);
+        n[0] = x[0] / r; n[1] = x[1] / r; n[2] = 0.0;
+    } else {
+        n[0] = 0.0; n[1] = 0.0; n[2] = ev == EV_TOP ? 1.0 : -1.0;
+    }
+}
+
+// ------------------------------------------------------------------ interface (Sect. 3)
+// Inward wave of the mode with tangential wave vector kt at a face with outward normal n.
+// Returns false if the mode is evanescent; else wave vector k and ray velocity v = M^-1 k (Eq. 6).
+__device__ __forceinline__ bool refract_in(int mode, double eo, double ee, const double c[3], const double n[3],
+                                           const double kt[3], double k[3], double v[3]) {
+    double kt2 = dot3(kt, kt);
+    if (mode == M_ORD) {
+        double a = eo - kt2;
+        if (a < 0.0) return false;
+        double q = -sqrt(a);
+        double ie = 1.0 / eo;
+        for (int i = 0; i < 3; ++i) { k[i] = fma(q, n[i], kt[i]); v[i] = k[i] * ie; }
+        return true;
+    }
+    double iee = 1.0 / ee, dl = 1.0 / eo - iee;
+    double cn = dot3(c, n), ckt = dot3(c, kt);
+    double A = fma(dl * cn, cn, iee);
+    double B = dl * cn * ckt;
+    double C = fma(iee, kt2, fma(dl * ckt, ckt, -1.0));
+    double disc = B * B - A * C;
+    if (disc < 0.0) return false;
+    double sq = sqrt(disc);
+    double q;
+    if (B > 0.0) q = (-B - sq) / A;
+    else q = (-B + sq) > 0.0 ? C / (-B + sq) : 0.0;
+    for (int i = 0; i < 3; ++i) k[i] = fma(q, n[i], kt[i]);
+    double ck_ = dot3(c, k);
+    for (int i = 0; i < 3; ++i) v[i] = fma(iee, k[i], dl * ck_ * c[i]);
+    return true;
+}
+
+// k = M v for the mode (Eq. 6 inverted)
+__device__ __forceinline__ void wave_from_velocity(int mode, double eo, double ee, const double c[3],
+                                                   const double v[3], double k[3]) {
+    if (mode == M_ORD) {
+        for (int i = 0; i < 3; ++i) k[i] = eo * v[i];
+    } else {
+        double cv = dot3(c, v);
+        for (int i = 0; i < 3; ++i) k[i] = fma(ee, v[i], (eo - ee) * cv * c[i]);
+    }
+}
+
+// ---- complex helpers for Eq. 12
+struct cx {
+    double re, im;
+};
+__device__ __forceinline__ cx C(double a, double b = 0.0) { return cx{a, b}; }
+__device__ __forceinline__ cx operator+(cx a, cx b) { return cx{a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cx operator-(cx a, cx b) { return cx{a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cx operator*(cx a, cx b) {
+    return cx{fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ cx operator*(double s, cx a) { return cx{s * a.re, s * a.im}; }
+__device__ __forceinline__ cx cdiv(cx a, cx b) {
+    double d = b.re * b.re + b.im * b.im;
+    return cx{(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+__device__ __forceinline__ double cabs2(cx a) { return a.re * a.re + a.im * a.im; }
+__device__ __forceinline__ cx cdot(const cx a[3], const cx b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+__device__ __forceinline__ void ccross(const cx a[3], const cx b[3], cx o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ double vnorm2(const cx a[3]) { return cabs2(a[0]) + cabs2(a[1]) + cabs2(a[2]); }
+// n . Re(E x conj(H))
+__device__ __forceinline__ double flux_n(const double n[3], const cx E[3], const cx H[3]) {
+    double s = 0.0;
+    const int i1[3] = {1, 2, 0}, i2[3] = {2, 0, 1};
+    for (int i = 0; i < 3; ++i) {
+        // Re(E_a conj(H_b) - E_b conj(H_a))
+        int a = i1[i], b = i2[i];
+        double re = (E[a].re * H[b].re + E[a].im * H[b].im) - (E[b].re * H[a].re + E[b].im * H[a].im);
+        s += n[i] * re;
+    }
+    return s;
+}
+
+// Inward wave (possibly evanescent: decaying into the medium) of the mode with tangential kt.
+__device__ __forceinline__ void inward_wave_c(int mode, double eo, double ee, const double c[3], const double n[3],
+                                              const double kt[3], cx k[3]) {
+    double kr[3], vr[3];
+    if (refract_in(mode, eo, ee, c, n, kt, kr, vr)) {
+        for (int i = 0; i < 3; ++i) k[i] = C(kr[i]);
+        return;
+    }
+    cx q;
+    if (mode == M_ORD) {
+        q = C(0.0, -sqrt(dot3(kt, kt) - eo));
+    } else {
+        double iee = 1.0 / ee, dl = 1.0 / eo - iee;
+        double cn = dot3(c, n), ckt = dot3(c, kt);
+        double A = fma(dl * cn, cn, iee), B = dl * cn * ckt, Cc = iee * dot3(kt, kt) + dl * ckt * ckt - 1.0;
+        q = C(-B / A, -sqrt(A * Cc - B * B) / A);
+    }
+    for (int i = 0; i < 3; ++i) k[i] = C(kt[i]) + q * C(n[i]);
+}
+
+// Field directions of a plane wave of the mode (Sect. 3): D_o perpendicular to the ordinary
+// main section, D_e in the extraordinary main section and perpendicular to k; E = eps^-1 D,
+// H = k x E.  Degenerate k parallel to c: D_o along z x k (x x k if that vanishes too).
+__device__ __forceinline__ void wave_fields(int mode, double eo, double ee, const double c[3], const cx k[3],
+                                            cx E[3], cx H[3]) {
+    cx cc[3] = {C(c[0]), C(c[1]), C(c[2])}, Do[3], D[3];
+    ccross(cc, k, Do);
+    double kk2 = vnorm2(k);
+    if (vnorm2(Do) < 1e-20 * kk2) {
+        cx z3[3] = {C(0), C(0), C(1)};
+        ccross(z3, k, Do);
+        if (vnorm2(Do) < 1e-20 * kk2) {
+            cx x3[3] = {C(1), C(0), C(0)};
+            ccross(x3, k, Do);
+        }
+        if (mode == M_EXT) ccross(k, Do, D);
+        else for (int i = 0; i < 3; ++i) D[i] = Do[i];
+    } else if (mode == M_ORD) {
+        for (int i = 0; i < 3; ++i) D[i] = Do[i];
+    } else {
+        cx kk = cdot(k, k), ckk = cdot(cc, k);
+        for (int i = 0; i < 3; ++i) D[i] = kk * cc[i] - ckk * k[i];
+    }
+    // eps^-1 = I/eo + (1/ee - 1/eo) c c^T
+    double ieo = 1.0 / eo, dl = 1.0 / ee - ieo;
+    cx cD = cdot(cc, D);
+    for (int i = 0; i < 3; ++i) E[i] = ieo * D[i] + (dl * c[i]) * cD;
+    ccross(k, E, H);
+}
+
+__device__ __forceinline__ void unit_perp(const double n[3], double t[3]) {
+    // any unit vector perpendicular to n
+    double a[3] = {0.0, 0.0, 0.0};
+    int m = fabs(n[0]) < fabs(n[1]) ? (fabs(n[0]) < fabs(n[2]) ? 0 : 2) : (fabs(n[1]) < fabs(n[2]) ? 1 : 2);
+    a[m] = 1.0;
+    t[0] = n[1] * a[2] - n[2] * a[1];
+    t[1] = n[2] * a[0] - n[0] * a[2];
+    t[2] = n[0] * a[1] - n[1] * a[0];
+    double l = sqrt(dot3(t, t));
+    for (int i = 0; i < 3; ++i) t[i] /= l;
+}
+
+__device__ __forceinline__ void s_basis(const double k[3], const double n[3], double s[3]) {
+    s[0] = k[1] * n[2] - k[2] * n[1];
+    s[1] = k[2] * n[0] - k[0] * n[2];
+    s[2] = k[0] * n[1] - k[1] * n[0];
+    double l = sqrt(dot3(s, s));
+    if (l < 1e-12) unit_perp(n, s);
+    else for (int i = 0; i < 3; ++i) s[i] /= l;
+}
+
+// Solve the complex 4x4 system A X = B for NR right-hand sides (Gaussian elimination, partial pivoting).
+template <int NR>
+__device__ bool csolve4(cx A[4][4], cx B[4][NR]) {
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        double best = cabs2(A[col][col]);
+        for (int r = col + 1; r < 4; ++r) {
+            double v = cabs2(A[r][col]);
+            if (v > best) { best = v; piv = r; }
+        }
+        if (best == 0.0) return false;
+        if (piv != col) {
+            for (int k = 0; k < 4; ++k) { cx t = A[col][k]; A[col][k] = A[piv][k]; A[piv][k] = t; }
+            for (int k = 0; k < NR; ++k) { cx t = B[col][k]; B[col][k] = B[piv][k]; B[piv][k] = t; }
+        }
+        for (int r = col + 1; r < 4; ++r) {
+            cx f = cdiv(A[r][col], A[col][col]);
+            for (int k = col; k < 4; ++k) A[r][k] = A[r][k] - f * A[col][k];
+            for (int k = 0; k < NR; ++k) B[r][k] = B[r][k] - f * B[col][k];
+        }
+    }
+    for (int r = 3; r >= 0; --r)
+        for (int k = 0; k < NR; ++k) {
+            cx s = B[r][k];
+            for (int j = r + 1; j < 4; ++j) s = s - A[r][j] * B[j][k];
+            B[r][k] = cdiv(s, A[r][r]);
+        }
+    return true;
+}
+
+// Eq. 12, vacuum -> medium, unpolarised light (mean over s and p): transmission into `mode`.
+static __device__ __noinline__ double transmission_in(int mode, double eo, double ee, const double c[3], const double n[3],
+                                               const double d[3]) {
+    double dn = dot3(d, n), kt[3], kr[3];
+    for (int i = 0; i < 3; ++i) { kt[i] = d[i] - dn * n[i]; kr[i] = d[i] - 2.0 * dn * n[i]; }
+    cx ko[3], ke[3], Eo[3], Ho[3], Ee[3], He[3];
+    inward_wave_c(M_ORD, eo, ee, c, n, kt, ko);
+    inward_wave_c(M_EXT, eo, ee, c, n, kt, ke);
+    wave_fields(M_ORD, eo, ee, c, ko, Eo, Ho);
+    wave_fields(M_EXT, eo, ee, c, ke, Ee, He);
+    double s[3], pi[3], pr[3], t2[3];
+    s_basis(d, n, s);
+    pi[0] = s[1] * d[2] - s[2] * d[1]; pi[1] = s[2] * d[0] - s[0] * d[2]; pi[2] = s[0] * d[1] - s[1] * d[0];
+    pr[0] = s[1] * kr[2] - s[2] * kr[1]; pr[1] = s[2] * kr[0] - s[0] * kr[2]; pr[2] = s[0] * kr[1] - s[1] * kr[0];
+    t2[0] = n[1] * s[2] - n[2] * s[1]; t2[1] = n[2] * s[0] - n[0] * s[2]; t2[2] = n[0] * s[1] - n[1] * s[0];
+    // columns: reflected s, reflected p, -o, -e ; rows: E.t1, E.t2, H.t1, H.t2 with t1 = s
+    cx Ers[3] = {C(s[0]), C(s[1]), C(s[2])}, Erp[3] = {C(pr[0]), C(pr[1]), C(pr[2])}, Hrs[3], Hrp[3];
+    cx ckr[3] = {C(kr[0]), C(kr[1]), C(kr[2])};
+    ccross(ckr, Ers, Hrs);
+    ccross(ckr, Erp, Hrp);
+    cx ct1[3] = {C(s[0]), C(s[1]), C(s[2])}, ct2[3] = {C(t2[0]), C(t2[1]), C(t2[2])};
+    const cx *colE[4] = {Ers, Erp, Eo, Ee}, *colH[4] = {Hrs, Hrp, Ho, He};
+    cx A[4][4], B[4][2];
+    for (int j = 0; j < 4; ++j) {
+        double sg = j < 2 ? 1.0 : -1.0;
+        A[0][j] = sg * cdot(colE[j], ct1);
+        A[1][j] = sg * cdot(colE[j], ct2);
+        A[2][j] = sg * cdot(colH[j], ct1);
+        A[3][j] = sg * cdot(colH[j], ct2);
+    }
+    cx cd[3] = {C(d[0]), C(d[1]), C(d[2])};
+    double fin[2];
+    for (int pol = 0; pol < 2; ++pol) {
+        const double *e = pol == 0 ? s : pi;
+        cx Ei[3] = {C(e[0]), C(e[1]), C(e[2])}, Hi[3];
+        ccross(cd, Ei, Hi);
+        B[0][pol] = -1.0 * cdot(Ei, ct1);
+        B[1][pol] = -1.0 * cdot(Ei, ct2);
+        B[2][pol] = -1.0 * cdot(Hi, ct1);
+        B[3][pol] = -1.0 * cdot(Hi, ct2);
+        fin[pol] = fabs(flux_n(n, Ei, Hi));
+    }
+    if (!csolve4<2>(A, B)) return 0.0;
+    const cx *Em = mode == M_ORD ? Eo : Ee, *Hm = mode == M_ORD ? Ho : He;
+    int row = mode == M_ORD ? 2 : 3;
+    double fm = fabs(flux_n(n, Em, Hm));
+    return 0.5 * (cabs2(B[row][0]) * fm / fin[0] + cabs2(B[row][1]) * fm / fin[1]);
+}
+
+// Eq. 12, medium -> vacuum (Sect. 3, last paragraph): fraction of the incident mode's normal
+// energy flux carried by the refracted vacuum wave.  0 for total internal reflection.
+static __device__ __noinline__ double transmission_out(int mode, double eo, double ee, const double c[3],
+                                                const double n[3], const double k[3]) {
+    double kn = dot3(k, n), kt[3];
+    for (int i = 0; i < 3; ++i) kt[i] = k[i] - kn * n[i];
+    double kt2 = dot3(kt, kt);
+    if (kt2 > 1.0) return 0.0;
+    double kv[3], s[3], pv[3], t2[3];
+    double qn = sqrt(1.0 - kt2);
+    for (int i = 0; i < 3; ++i) kv[i] = fma(qn, n[i], kt[i]);
+    s_basis(kv, n, s);
+    pv[0] = s[1] * kv[2] - s[2] * kv[1]; pv[1] = s[2] * kv[0] - s[0] * kv[2]; pv[2] = s[0] * kv[1] - s[1] * kv[0];
+    t2[0] = n[1] * s[2] - n[2] * s[1]; t2[1] = n[2] * s[0] - n[0] * s[2]; t2[2] = n[0] * s[1] - n[1] * s[0];
+    cx ckv[3] = {C(kv[0]), C(kv[1]), C(kv[2])};
+    cx Es[3] = {C(s[0]), C(s[1]), C(s[2])}, Ep[3] = {C(pv[0]), C(pv[1]), C(pv[2])}, Hs[3], Hp[3];
+    ccross(ckv, Es, Hs);
+    ccross(ckv, Ep, Hp);
+    cx kro[3], kre[3], Ero[3], Hro[3], Ere[3], Hre[3], Em[3], Hm[3];
+    inward_wave_c(M_ORD, eo, ee, c, n, kt, kro);
+    inward_wave_c(M_EXT, eo, ee, c, n, kt, kre);
+    wave_fields(M_ORD, eo, ee, c, kro, Ero, Hro);
+    wave_fields(M_EXT, eo, ee, c, kre, Ere, Hre);
+    cx ck3[3] = {C(k[0]), C(k[1]), C(k[2])};
+    wave_fields(mode, eo, ee, c, ck3, Em, Hm);
+    cx ct1[3] = {C(s[0]), C(s[1]), C(s[2])}, ct2[3] = {C(t2[0]), C(t2[1]), C(t2[2])};
+    const cx *colE[4] = {Es, Ep, Ero, Ere}, *colH[4] = {Hs, Hp, Hro, Hre};
+    cx A[4][4], B[4][1];
+    for (int j = 0; j < 4; ++j) {
+        double sg = j < 2 ? 1.0 : -1.0;
+        A[0][j] = sg * cdot(colE[j], ct1);
+        A[1][j] = sg * cdot(colE[j], ct2);
+        A[2][j] = sg * cdot(colH[j], ct1);
+        A[3][j] = sg * cdot(colH[j], ct2);
+    }
+    B[0][0] = cdot(Em, ct1);
+    B[1][0] = cdot(Em, ct2);
+    B[2][0] = cdot(Hm, ct1);
+    B[3][0] = cdot(Hm, ct2);
+    double fm = fabs(flux_n(n, Em, Hm));
+    if (!csolve4<1>(A, B)) return 0.0;
+    cx Et[3], Ht[3];
+    for (int i = 0; i < 3; ++i) { Et[i] = B[0][0] * Es[i] + B[1][0] * Ep[i]; Ht[i] = B[0][0] * Hs[i] + B[1][0] * Hp[i]; }
+    return fabs(flux_n(n, Et, Ht)) / fm;
+}
+
+// ------------------------------------------------------------------ room and camera
+// Procedural room: box x, y in [-10, 10], z in [-H/2, -H/2 + 10]; checkered walls and floor with
+// 8 tiles per unit and splitmix64-hashed tints; constant ceiling.  Returns the tile id.
+__device__ __forceinline__ int room_hit(const Params &p, const double o[3], const double d[3], float rgb[3]) {
+    const double Lb = 10.0, z0 = -p.halfH, z1 = z0 + 10.0;
+    double best = 1e300, s;
+    int face = -1;
+    if (d[0] > 0.0) { s = (Lb - o[0]) / d[0]; if (s < best) { best = s; face = 0; } }
+    else if (d[0] < 0.0) { s = (-Lb - o[0]) / d[0]; if (s < best) { best = s; face = 1; } }
+    if (d[1] > 0.0) { s = (Lb - o[1]) / d[1]; if (s < best) { best = s; face = 2; } }
+    else if (d[1] < 0.0) { s = (-Lb - o[1]) / d[1]; if (s < best) { best = s; face = 3; } }
+    if (d[2] < 0.0) { s = (z0 - o[2]) / d[2]; if (s < best) { best = s; face = 4; } }
+    else if (d[2] > 0.0) { s = (z1 - o[2]) / d[2]; if (s < best) { best = s; face = 5; } }
+    if (face < 0) { rgb[0] = rgb[1] = rgb[2] = 0.f; return -1; }
+    if (face == 5) { rgb[0] = 0.55f; rgb[1] = 0.55f; rgb[2] = 0.6f; return 5 << 20; }
+    double qx = o[0] + best * d[0], qy = o[1] + best * d[1], qz = o[2] + best * d[2];
+    double u, v;
+    int nv;
+    if (face <= 1) { u = qy + Lb; v = qz - z0; nv = 80; }
+    else if (face <= 3) { u = qx + Lb; v = qz - z0; nv = 80; }
+    else { u = qx + Lb; v = qy + Lb; nv = 160; }
+    int i = (int)floor(u * 8.0), j = (int)floor(v * 8.0);
+    i = min(max(i, 0), 159);
+    j = min(max(j, 0), nv - 1);
+    uint64_t h = sm64(sm64(sm64(sm64(p.scene_seed) ^ uint64_t(face)) ^ uint64_t(i)) ^ uint64_t(j));
+    float base = ((i + j) & 1) ? 0.25f : 0.85f;
+    for (int c = 0; c < 3; ++c) rgb[c] = base * (0.6f + 0.4f * float((h >> (8 * c)) & 255u) / 255.0f);
+    return (face << 20) | (i << 10) | j;
+}
+
+__device__ __forceinline__ void camera_ray(const Params &p, int i, int j, int s, int spp, uint64_t seed, double o[3],
+                                           double d[3]) {
+    double xi1 = 0.5, xi2 = 0.5;
+    if (spp > 1) {
+        uint64_t pix = uint64_t(j) * uint64_t(p.W) + uint64_t(i);
+        xi1 = jitter(seed, pix, s, 0);
+        xi2 = jitter(seed, pix, s, 1);
+    }
+    double px = (2.0 * (i + xi1) / p.W - 1.0) * p.tx;
+    double py = (1.0 - 2.0 * (j + xi2) / p.Hp) * p.ty;
+    double l2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        d[k] = p.fw[k] + px * p.rt[k] + py * p.up[k];
+        l2 += d[k] * d[k];
+    }
+    double il = 1.0 / sqrt(l2);
+    for (int k = 0; k < 3; ++k) { d[k] *= il; o[k] = p.eye[k]; }
+}
+
+}  // namespace ck
