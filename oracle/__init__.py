@@ -57,6 +57,7 @@ def lib():
         L.orc_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32]
         L.orc_permittivity.argtypes = [C.POINTER(_Cloak), dp, dp, dp, dp, dp]
         L.orc_aux_matrix.argtypes = [C.POINTER(_Cloak), dp, dp, dp]
+        L.orc_aux_inverse.argtypes = [C.POINTER(_Cloak), dp, dp]
         L.orc_eq8_accel.argtypes = [dp, dp, dp, dp]
         L.orc_eq2_accel.argtypes = [C.c_double, dp, dp, dp]
         L.orc_rhs.argtypes = [C.POINTER(_Cloak), C.c_int, dp, dp]
@@ -153,8 +154,17 @@ def aux_matrix(cloak: Cloak, x):
     return M.reshape(3, 3), dM.reshape(3, 3, 3)
 
 
-def eq8_accel(M, dM, v):
-    M = np.ascontiguousarray(M, dtype=np.float64).reshape(9)
+def aux_inverse(cloak: Cloak, x):
+    """Eq. 7 inverted: M^{-1} = eps / (n_o^2 n_e^2)."""
+    x = _vec(x)
+    Mi = np.zeros(9)
+    lib().orc_aux_inverse(cloak.ref, _dp(x), _dp(Mi))
+    return Mi.reshape(3, 3)
+
+
+def eq8_accel(Minv, dM, v):
+    """Eq. 8 given M^{-1} and the gradient of M."""
+    M = np.ascontiguousarray(Minv, dtype=np.float64).reshape(9)
     dM = np.ascontiguousarray(dM, dtype=np.float64).reshape(27)
     v = _vec(v)
     a = np.zeros(3)

@@ -4,7 +4,7 @@
  * A slow, literal statement of the method of Halimeh & Wegener,
  * arXiv:1209.6038, used to check the CUDA renderer.  It follows the paper's
  * steps in its own notation: the Cartesian permittivity tensor of Eq. 14 / 15,
- * the auxiliary matrix of Eq. 7 by explicit 3x3 inversion, the equations of
+ * the auxiliary matrix of Eq. 7 from the principal-frame inverse permittivity, the equations of
  * motion Eq. 2 and Eq. 8 written term by term, the Sect. 3 interface through
  * Eqs. 9-11 (angle of refraction found by bisection), the transmission
  * coefficients of Eq. 12 from a 4x4 field-continuity solve, and classical
@@ -37,31 +37,6 @@ static void cross3(const double a[3], const double b[3], double o[3]) {
 static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
 static void matvec3(const double A[9], const double x[3], double y[3]) {
     for (int i = 0; i < 3; ++i) y[i] = A[3 * i] * x[0] + A[3 * i + 1] * x[1] + A[3 * i + 2] * x[2];
-}
-static void matmul3(const double A[9], const double B[9], double C[9]) {
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
-            C[3 * i + j] = s;
-        }
-}
-/* inverse of a general 3x3 matrix by the adjugate */
-static void inv3(const double A[9], double B[9]) {
-    double c00 = A[4] * A[8] - A[5] * A[7];
-    double c01 = A[5] * A[6] - A[3] * A[8];
-    double c02 = A[3] * A[7] - A[4] * A[6];
-    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
-    double id = 1.0 / det;
-    B[0] = c00 * id;
-    B[1] = (A[2] * A[7] - A[1] * A[8]) * id;
-    B[2] = (A[1] * A[5] - A[2] * A[4]) * id;
-    B[3] = c01 * id;
-    B[4] = (A[0] * A[8] - A[2] * A[6]) * id;
-    B[5] = (A[2] * A[3] - A[0] * A[5]) * id;
-    B[6] = c02 * id;
-    B[7] = (A[1] * A[6] - A[0] * A[7]) * id;
-    B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
 }
 /* some unit vector perpendicular to n */
 static void any_perp(const double n[3], double t[3]) {
@@ -183,12 +158,35 @@ void orc_permittivity(const orc_cloak *c, const double x[3], double eps[9], doub
     }
 }
 
+/* Inverse permittivity in the lab frame.  eps is diagonal in its own frame
+   (Eq. 1; the cylindrical frame of Eq. 14 / 15), so its inverse is the sum of
+   the reciprocal principal values times the projectors -- no numerical
+   inversion (which would lose ~eps_max/eps_min of relative precision near
+   r = R1, where one principal value tends to zero). */
+static void inv_permittivity(const orc_cloak *c, const double x[3], double ie[9]) {
+    if (c->variant == ORC_TEST_CONST) {
+        double l = norm3(c->c_test), ch[3];
+        for (int i = 0; i < 3; ++i) ch[i] = c->c_test[i] / l;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                ie[3 * i + j] = (i == j ? 1.0 / c->eps_o_test : 0.0) +
+                                (1.0 / c->eps_e_test - 1.0 / c->eps_o_test) * ch[i] * ch[j];
+        return;
+    }
+    double r, rh[3], th[3], zh[3] = {0, 0, 1}, e[3], de[3];
+    cyl_basis(x, &r, rh, th);
+    cyl_eps(c, r, e, de);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            ie[3 * i + j] = rh[i] * rh[j] / e[0] + th[i] * th[j] / e[1] + zh[i] * zh[j] / e[2];
+}
+
 /* Eq. 7: M = n_o^2 n_e^2 eps^{-1} and its Cartesian gradient.
    dM[9*k + 3*i + j] = d M_ij / d x_k. */
 void orc_aux_matrix(const orc_cloak *c, const double x[3], double M[9], double dM[27]) {
     double eps[9], eo, ee, ch[3], ie[9];
     orc_permittivity(c, x, eps, &eo, &ee, ch);
-    inv3(eps, ie);
+    inv_permittivity(c, x, ie);
     double P = eo * ee; /* n_o^2 n_e^2 */
     for (int i = 0; i < 9; ++i) M[i] = P * ie[i];
     if (c->variant == ORC_TEST_CONST) {
@@ -205,25 +203,31 @@ void orc_aux_matrix(const orc_cloak *c, const double x[3], double M[9], double d
         /* derivatives of the basis along x_k: d rh = th_k th / r, d th = -th_k rh / r, d zh = 0 */
         double drh[3], dth[3];
         for (int i = 0; i < 3; ++i) { drh[i] = th[k] * th[i] / r; dth[i] = -th[k] * rh[i] / r; }
-        double deps[9];
+        double die[9]; /* d(eps^{-1}) / dx_k */
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j)
-                deps[3 * i + j] = de[0] * rh[k] * rh[i] * rh[j] + e[0] * (drh[i] * rh[j] + rh[i] * drh[j]) +
-                                  de[1] * rh[k] * th[i] * th[j] + e[1] * (dth[i] * th[j] + th[i] * dth[j]) +
-                                  de[2] * rh[k] * zh[i] * zh[j];
+                die[3 * i + j] = -de[0] / (e[0] * e[0]) * rh[k] * rh[i] * rh[j] +
+                                 (drh[i] * rh[j] + rh[i] * drh[j]) / e[0] -
+                                 de[1] / (e[1] * e[1]) * rh[k] * th[i] * th[j] +
+                                 (dth[i] * th[j] + th[i] * dth[j]) / e[1] -
+                                 de[2] / (e[2] * e[2]) * rh[k] * zh[i] * zh[j];
         double dP = (deo * ee + eo * dee) * rh[k];
-        double t1[9], t2[9];
-        matmul3(ie, deps, t1);
-        matmul3(t1, ie, t2); /* eps^{-1} (d eps) eps^{-1} */
-        for (int i = 0; i < 9; ++i) dM[9 * k + i] = dP * ie[i] - P * t2[i];
+        for (int i = 0; i < 9; ++i) dM[9 * k + i] = dP * ie[i] + P * die[i];
     }
+}
+
+/* Eq. 7 inverted: M^{-1} = eps / (n_o^2 n_e^2). */
+void orc_aux_inverse(const orc_cloak *c, const double x[3], double Mi[9]) {
+    double eps[9], eo, ee, ch[3];
+    orc_permittivity(c, x, eps, &eo, &ee, ch);
+    for (int i = 0; i < 9; ++i) Mi[i] = eps[i] / (eo * ee);
 }
 
 /* Eq. 8: dv/dt = (1/2) M^{-1} [ v (grad M) v - 2 ((grad M) . v) v ].
    Reading: component i of "v (grad M) v" is v^T (d_i M) v; "((grad M) . v) v"
    is sum_l v_l (d_l M) v. */
-void orc_eq8_accel(const double M[9], const double dM[27], const double v[3], double a[3]) {
-    double g[3], h[3], w[3], Mi[9];
+void orc_eq8_accel(const double Mi[9], const double dM[27], const double v[3], double a[3]) {
+    double g[3], h[3], w[3];
     for (int i = 0; i < 3; ++i) {
         double s = 0.0;
         for (int j = 0; j < 3; ++j)
@@ -237,7 +241,6 @@ void orc_eq8_accel(const double M[9], const double dM[27], const double v[3], do
         h[j] = s;
     }
     for (int i = 0; i < 3; ++i) w[i] = g[i] - 2.0 * h[i];
-    inv3(M, Mi);
     matvec3(Mi, w, a);
     for (int i = 0; i < 3; ++i) a[i] *= 0.5;
 }
@@ -253,9 +256,10 @@ void orc_rhs(const orc_cloak *c, int mode, const double y[6], double dy[6]) {
     const double *x = y, *v = y + 3;
     dy[0] = v[0]; dy[1] = v[1]; dy[2] = v[2];
     if (mode == ORC_EXTRAORDINARY) {
-        double M[9], dM[27];
+        double M[9], dM[27], Mi[9];
         orc_aux_matrix(c, x, M, dM);
-        orc_eq8_accel(M, dM, v, dy + 3);
+        orc_aux_inverse(c, x, Mi);
+        orc_eq8_accel(Mi, dM, v, dy + 3);
     } else {
         double gn[3] = {0, 0, 0}, n;
         if (c->variant == ORC_TEST_CONST) {
@@ -324,9 +328,8 @@ int orc_refract_into(const orc_cloak *c, int mode, const double x[3], const doub
     }
     double nn = eq9_index(no, ne, ch, t, n, phi); /* |k_e| = n(phi_e) */
     for (int i = 0; i < 3; ++i) k[i] = nn * (t[i] * sin(phi) - n[i] * cos(phi));
-    double M[9], dM[27], Mi[9];
-    orc_aux_matrix(c, x, M, dM);
-    inv3(M, Mi);
+    double Mi[9];
+    orc_aux_inverse(c, x, Mi);
     matvec3(Mi, k, v); /* Eq. 6 */
     return 1;
 }
@@ -348,9 +351,8 @@ static void inward_wave(const orc_cloak *c, int mode, const double x[3], const d
     if (mode == ORC_ORDINARY) {
         q = -csqrt(eo - dot3(kt, kt));
     } else {
-        double M[9], dM[27], Mi[9], Mn[3], Mk[3];
-        orc_aux_matrix(c, x, M, dM);
-        inv3(M, Mi);
+        double Mi[9], Mn[3], Mk[3];
+        orc_aux_inverse(c, x, Mi);
         matvec3(Mi, n, Mn);
         matvec3(Mi, kt, Mk);
         double A = dot3(n, Mn), B = dot3(n, Mk), C = dot3(kt, Mk) - 1.0;
@@ -365,7 +367,7 @@ static void inward_wave(const orc_cloak *c, int mode, const double x[3], const d
    H = k x E (mu = 1, omega = c0 = 1).
    Reading: when k is parallel to c-hat the two modes are degenerate and
    D_o is taken along z-hat x k (x-hat x k if that vanishes too). */
-static void mode_fields(int mode, const cplx k[3], const double eps[9], const double ch[3], cplx E[3], cplx H[3]) {
+static void mode_fields(int mode, const cplx k[3], const double ie[9], const double ch[3], cplx E[3], cplx H[3]) {
     cplx c3[3] = {ch[0], ch[1], ch[2]}, Do[3], D[3];
     ccross3(c3, k, Do);
     if (cnorm2(Do) < 1e-20 * cnorm2(k)) {
@@ -383,8 +385,6 @@ static void mode_fields(int mode, const cplx k[3], const double eps[9], const do
         cplx kk = cdot3(k, k), ck = cdot3(c3, k);
         for (int i = 0; i < 3; ++i) D[i] = kk * c3[i] - ck * k[i];
     }
-    double ie[9];
-    inv3(eps, ie);
     for (int i = 0; i < 3; ++i) E[i] = ie[3 * i] * D[0] + ie[3 * i + 1] * D[1] + ie[3 * i + 2] * D[2];
     ccross3(k, E, H);
 }
@@ -396,7 +396,9 @@ void orc_mode_fields(const orc_cloak *c, int mode, const double x[3], const doub
     double eps[9], eo, ee, ch[3];
     orc_permittivity(c, x, eps, &eo, &ee, ch);
     cplx ck[3] = {k[0], k[1], k[2]}, cE[3], cH[3];
-    mode_fields(mode, ck, eps, ch, cE, cH);
+    double ie[9];
+    inv_permittivity(c, x, ie);
+    mode_fields(mode, ck, ie, ch, cE, cH);
     for (int i = 0; i < 3; ++i) { E[i] = creal(cE[i]); H[i] = creal(cH[i]); }
     matvec3(eps, E, D);
 }
@@ -421,8 +423,10 @@ int orc_transmission_in(const orc_cloak *c, const double x[3], const double n[3]
     cplx ko[3], ke[3], Eo[3], Ho[3], Ee[3], He[3];
     inward_wave(c, ORC_ORDINARY, x, n, kt, ko);
     inward_wave(c, ORC_EXTRAORDINARY, x, n, kt, ke);
-    mode_fields(ORC_ORDINARY, ko, eps, ch, Eo, Ho);
-    mode_fields(ORC_EXTRAORDINARY, ke, eps, ch, Ee, He);
+    double ie[9];
+    inv_permittivity(c, x, ie);
+    mode_fields(ORC_ORDINARY, ko, ie, ch, Eo, Ho);
+    mode_fields(ORC_EXTRAORDINARY, ke, ie, ch, Ee, He);
     double s[3], pi[3], pr[3];
     vacuum_basis(d, n, s, pi);
     cross3(s, kr, pr); /* reflected wave: same s, p = s x k_r */
@@ -491,9 +495,11 @@ int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const 
     cplx kro[3], kre[3], Ero[3], Hro[3], Ere[3], Hre[3], ck[3] = {k[0], k[1], k[2]}, Em[3], Hm[3];
     inward_wave(c, ORC_ORDINARY, x, n, kt, kro);
     inward_wave(c, ORC_EXTRAORDINARY, x, n, kt, kre);
-    mode_fields(ORC_ORDINARY, kro, eps, ch, Ero, Hro);
-    mode_fields(ORC_EXTRAORDINARY, kre, eps, ch, Ere, Hre);
-    mode_fields(mode, ck, eps, ch, Em, Hm);
+    double ie[9];
+    inv_permittivity(c, x, ie);
+    mode_fields(ORC_ORDINARY, kro, ie, ch, Ero, Hro);
+    mode_fields(ORC_EXTRAORDINARY, kre, ie, ch, Ere, Hre);
+    mode_fields(mode, ck, ie, ch, Em, Hm);
     double t1[3], t2[3];
     for (int i = 0; i < 3; ++i) t1[i] = s[i];
     cross3(n, s, t2);

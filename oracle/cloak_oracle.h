@@ -81,7 +81,8 @@ double orc_uniform(uint64_t seed, uint64_t pixel, uint32_t sample, uint32_t dim)
 void orc_permittivity(const orc_cloak *c, const double x[3], double eps[9],
                       double *eps_o, double *eps_e, double chat[3]);
 void orc_aux_matrix(const orc_cloak *c, const double x[3], double M[9], double dM[27]);
-void orc_eq8_accel(const double M[9], const double dM[27], const double v[3], double a[3]);
+void orc_aux_inverse(const orc_cloak *c, const double x[3], double Minv[9]);
+void orc_eq8_accel(const double Minv[9], const double dM[27], const double v[3], double a[3]);
 void orc_eq2_accel(double n, const double gradn[3], const double v[3], double a[3]);
 void orc_rhs(const orc_cloak *c, int mode, const double y[6], double dy[6]);
 

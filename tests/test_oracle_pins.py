@@ -125,6 +125,7 @@ def test_aux_matrix_structure(variant):
         t = np.cross(ch, [0.1, 0.2, 0.9])
         t /= np.linalg.norm(t)
         np.testing.assert_allclose(M @ t, ee * t, atol=1e-12)
+        np.testing.assert_allclose(M @ O.aux_inverse(c, x), np.eye(3), atol=1e-13)
 
 
 @pytest.mark.parametrize("variant", [O.RADIAL, O.AZIMUTHAL])
@@ -155,7 +156,8 @@ def test_eq8_reduces_to_eq2_for_isotropic_M():
         v = rng.normal(size=3)
         M = n * n * np.eye(3)
         dM = np.stack([2 * n * gn[k] * np.eye(3) for k in range(3)])
-        np.testing.assert_allclose(O.eq8_accel(M, dM, v), O.eq2_accel(n, gn, v), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(O.eq8_accel(np.linalg.inv(M), dM, v), O.eq2_accel(n, gn, v), rtol=1e-12,
+                                   atol=1e-12)
 
 
 @pytest.mark.parametrize("variant", [O.RADIAL, O.AZIMUTHAL])
@@ -574,3 +576,42 @@ def test_inplane_weights_closed_form(p):
     Ts, Tp, t = fresnel(i, 2.0)
     rec, _ = trace(O.Cloak(O.RADIAL), O.ORDINARY, o, d)
     assert rec["weight"] == pytest.approx(0.5 * Ts * Ts, abs=1e-12)
+
+
+@pytest.mark.parametrize("which,variant,mode,L,kz,tol", [
+    ("radial_e", O.RADIAL, O.EXTRAORDINARY, 1e-3, 0.003, 2e-9),
+    ("radial_e", O.RADIAL, O.EXTRAORDINARY, -2e-3, -0.004, 2e-9),
+    ("azim_o", O.AZIMUTHAL, O.ORDINARY, 2e-4, 0.02, 2e-9),
+    ("azim_o", O.AZIMUTHAL, O.ORDINARY, -3e-3, 0.1, 2e-9),
+])
+def test_near_axis_closed_form(which, variant, mode, L, kz, tol):
+    """Rays passing within ~1e-3 of the inner radius, where f = K((r-R1)/r)^2 -> 0
+    and one principal value of eps and M vanishes: the oracle must stay accurate
+    there.  The entry height is chosen so that the path is centred in z."""
+    tof, dth, dz = quad_exit(L, kz, which)
+    assert abs(dz) < 1.9
+    z0 = -0.5 * dz
+    o, d, p = make_ray(L, kz, theta0=1.1, z0=z0)
+    pos, dexp = exit_from_angles(1.1, z0, dth, dz, L, kz)
+    rec, _ = trace(O.Cloak(variant), mode, o, d, O.DP45, 1e-12)
+    assert O.STATUS[rec["status"]] == "EXITED"
+    assert angle(rec["exit_dir"], dexp) < tol
+    assert np.abs(rec["exit_pos"] - pos).max() < tol
+    assert rec["tof"] == pytest.approx(tof, abs=tol)
+
+
+@pytest.mark.parametrize("L,kz,tol", [(-3e-3, 0.1, 1e-10), (2e-4, 0.02, 1e-8)])
+def test_near_axis_azimuthal_extraordinary(L, kz, tol):
+    """Azimuthal e-ray with impact parameter down to 2e-4: the ray speed near the
+    turning point grows like 1/L (superluminal region, Sect. 6)."""
+    c = O.Cloak(O.AZIMUTHAL)
+    U, Kp = R2 - R1, K - kz * kz
+    root = math.sqrt(Kp * U * U - L * L)
+    dth = math.copysign(2 * math.acos(abs(L) / (U * math.sqrt(Kp))), L)
+    dz = 2 * kz * root / Kp
+    o, d, p = make_ray(L, kz, theta0=0.3, z0=-0.5 * dz)
+    pos, dexp = exit_from_angles(0.3, -0.5 * dz, dth, dz, L, kz)
+    rec, _ = trace(c, O.EXTRAORDINARY, o, d, O.DP45, 1e-12)
+    assert O.STATUS[rec["status"]] == "EXITED"
+    assert angle(rec["exit_dir"], dexp) < tol
+    assert rec["tof"] == pytest.approx(2 * K * root / Kp, abs=tol)
