@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the uniaxial-cloak renderer on one node.
+
+A step renders every image of the full workload: radial and azimuthal cloaks
+(Eqs. 14, 15) x ordinary and extraordinary light x camera elevations 0/20/45 deg,
+1920x1080 pixels, 4 jittered samples per pixel, Dormand-Prince 5(4) at tolerance
+1e-9 in FP64 -- 99.5 million camera rays.  The value is traced camera rays per
+second (whole job).  Also reported: the plain FP64 path (one thread per pixel),
+the roofline of the dominant kernel against the FP64 ALU peak, the CPU FP64
+oracle on a bounded sample of the same workload (and the exit-direction error
+against it), an end-to-end number through the public API with the images copied
+to pinned host memory, and the SM clocks seen during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "traced rays/s at 1920x1080 vs plain FP64 GPU integrator; max exit-dir err"
+UNIT = "rays/s"
+
+# FP64 ALU peak derived from the GB300 unit counts and clock: 152 SMs x 2070 MHz x
+# 4 FP64 flop per clock per SM (two DFMA) = 1.26 TFLOP/s (nominal FP64 figure 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+FP32_PEAK_TFLOPS = 152 * 2.070e9 * 256 / 1e12
+
+# Algorithmic FP64 flops per integrator step attempt, counted from the source formulas
+# (FMA = 2 flops, division and square root = 1 flop each):
+#   RHS of Eq. 8 / Eq. 2 in closed cylindrical form: radial-e 41, azimuthal-e 37,
+#   azimuthal-o 33, radial-o 0 (straight lines, Sect. 4).
+#   DP5(4) attempt: 6 new RHS + stage combinations (348) + error norm (30).
+#   RK4 step: 4 RHS + combinations (102).
+RHS_FLOPS = {(0, 0): 0, (0, 1): 41, (1, 0): 33, (1, 1): 37}
+DP45_FIXED, RK4_FIXED = 378, 102
+
+
+def flops_per_step(variant, mode, integ):
+    r = RHS_FLOPS[(variant, mode)]
+    return 6 * r + DP45_FIXED if integ == 1 else 4 * r + RK4_FIXED
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ reference arm (the CPU oracle)
+def sample_pixels(w, img_index, n, seed=12345):
+    import numpy as np
+    rng = np.random.default_rng(seed + img_index)
+    return np.sort(rng.choice(w.width * w.height, n, replace=False))
+
+
+def run_oracle_sample(w, pix_per_image, nthreads, seed=12345):
+    """The CPU FP64 oracle on a seeded pixel sample of every image; returns (rays, seconds, records)."""
+    import oracle as O
+    from paper_1209_6038_gb300 import inputs
+    recs = []
+    t0 = time.perf_counter()
+    for idx, (v, m, e) in enumerate(w.images):
+        eye, tgt, up = inputs.camera_pose(e)
+        pix = sample_pixels(w, idx, pix_per_image, seed)
+        integ = O.Integrator(O.DP45 if w.integrator == "dp45" else O.RK4, w.h_or_tol, w.max_steps)
+        _, rec = O.render(O.Cloak(v), integ, O.Camera(eye, tgt, up, w.hfov_deg, w.width, w.height), m, w.spp,
+                          w.seed, pixels=pix, nthreads=nthreads)
+        recs.append(rec)
+    dt = time.perf_counter() - t0
+    return pix_per_image * w.spp * len(w.images), dt, recs
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import build as obuild
+    obuild.build()
+    from paper_1209_6038_gb300 import inputs
+    w = inputs.FULL
+    cores = os.cpu_count() or 1
+    per_image = args.ref_pixels
+    for _ in range(args.warmup):
+        run_oracle_sample(w, max(8, per_image // 8), cores, seed=999)
+    times, nrays = [], 0
+    for k in range(args.steps):
+        n, dt, _ = run_oracle_sample(w, per_image, cores, seed=12345 + 100 * k)
+        times.append(dt)
+        nrays += n
+    total = sum(times)
+    value = nrays / total
+    sample = (f"{per_image} seeded pixels x {w.spp} spp from each of the {len(w.images)} images per step "
+              f"({per_image * w.spp * len(w.images)} rays/step)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(w):
+    return {"workload": w.name, "width": w.width, "height": w.height, "spp": w.spp,
+            "images": len(w.images), "variants": ["radial", "azimuthal"][: len(w.variants)],
+            "polarizations": ["ordinary", "extraordinary"][: len(w.pols)], "elevations_deg": list(w.elevations),
+            "integrator": w.integrator, "tol": w.h_or_tol, "camera_distance": 5.0, "hfov_deg": w.hfov_deg,
+            "geometry": {"R1": 0.5, "R2": 1.0, "height": 2.0}, "scene": "procedural checkerboard room, seed 0",
+            "parallelism": "one process per GPU, every rank renders the full workload (replicas)",
+            "l2": "256 MiB buffer written between timed steps"}
+
+
+# ------------------------------------------------------------------ native arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--ref-pixels", type=int, default=1000, help="oracle pixels per image per step")
+    ap.add_argument("--cpu-pixels", type=int, default=1000, help="oracle pixels per image for cpu_baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1209_6038_gb300 import build as pbuild
+    if rank == 0:
+        pbuild.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_1209_6038_gb300 import cloak as ck
+    from paper_1209_6038_gb300 import inputs
+    ck.load()
+    w = inputs.FULL
+    stream = torch.cuda.current_stream()
+
+    def make_handles(schedule):
+        hs = {}
+        for v in w.variants:
+            for e in w.elevations:
+                eye, tgt, up = inputs.camera_pose(e)
+                c = ck.Cloak(v).camera(eye, tgt, up, w.hfov_deg, w.width, w.height)
+                c.integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol, ck.FP64, w.max_steps)
+                c.schedule(schedule)
+                hs[(v, e)] = c
+        return hs
+
+    imgs = [torch.empty((w.height, w.width, 4), dtype=torch.float32, device="cuda") for _ in w.images]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(hs):
+        for i, (v, m, e) in enumerate(w.images):
+            hs[(v, e)].render(m, w.spp, w.seed, out=imgs[i])
+
+    def timed(hs, warmup, steps, sampler=None):
+        for _ in range(warmup):
+            step(hs)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms = []
+        ctx = sampler if sampler is not None else _Null()
+        with ctx:
+            for _ in range(steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step(hs)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        tot = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+        return float(tot.item()) / steps, ms
+
+    sched = ck.SCHED_PLAIN
+    hs = make_handles(sched)
+    sampler = ClockSampler(local)
+    ms_step, ms_list = timed(hs, args.warmup, args.steps, sampler)
+    rays_step = w.rays
+    value = ws * rays_step / (ms_step / 1e3)
+    clocks = sampler.summary()
+    launches_per_step = len(w.images)  # one render kernel per image on the plain schedule
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(w),
+           "schedule": "plain", "clocks": clocks, "gpu_launches": launches_per_step * args.steps}
+
+    if rank == 0:
+        # ---- records pass (untimed): step counts for the roofline, sampled rays for the error
+        rec_buf = torch.empty(w.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
+        flops = 0.0
+        steps_total = 0
+        status_hist = np.zeros(8, np.int64)
+        gpu_samples = []
+        for idx, (v, m, e) in enumerate(w.images):
+            hs[(v, e)].render_records(m, w.spp, w.seed, out=rec_buf)
+            i32 = rec_buf.view(torch.int32).view(-1, 20)   # cloak_record: tile_id, status, steps at 16, 17, 18
+            status = i32[:, 17].long()
+            steps_img = int(i32[:, 18].long().sum().item())
+            steps_total += steps_img
+            flops += steps_img * flops_per_step(v, m, 1 if w.integrator == "dp45" else 0)
+            status_hist += torch.bincount(status, minlength=8).cpu().numpy()[:8]
+            pix = sample_pixels(w, idx, args.cpu_pixels)
+            sel = torch.from_numpy((pix[:, None] * w.spp + np.arange(w.spp)[None, :]).reshape(-1)).cuda()
+            gpu_samples.append(ck.records_to_numpy(rec_buf.view(-1, ck.RECORD_BYTES)[sel].reshape(-1)))
+        del rec_buf
+        achieved = flops / (ms_step / 1e3) / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                           "peak_source": "derived: 152 SM x 2.07 GHz x 4 FP64 flop/clk/SM",
+                           "kernel": "k_render_plain (12 launches per step)"}
+        out["work"] = {"integrator_steps_per_step": steps_total, "fp64_flops_per_step": flops,
+                       "status_hist": {ck.RAY_STATUS[i]: int(status_hist[i]) for i in range(8)}}
+
+        # ---- CPU oracle on a bounded sample, and the exit-direction error against it
+        cores = os.cpu_count() or 1
+        nr, dt, orecs = run_oracle_sample(w, args.cpu_pixels, cores)
+        g = np.concatenate(gpu_samples)
+        o = np.concatenate(orecs)
+        fin = np.isin(o["status"], [0, 1, 2, 7]) & (g["status"] == o["status"])
+        cr = np.linalg.norm(np.cross(g["exit_dir"][fin], o["exit_dir"][fin]), axis=-1)
+        dtp = np.sum(g["exit_dir"][fin] * o["exit_dir"][fin], axis=-1)
+        err = np.arctan2(cr, dtp)
+        px_g = (g["tile_id"] != o["tile_id"]) | (g["status"] != o["status"])
+        px_diff = px_g.reshape(-1, w.spp).any(1)
+        out["cpu_baseline"] = {"value": nr / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{args.cpu_pixels} seeded pixels x {w.spp} spp from each of the "
+                                         f"{len(w.images)} images ({nr} rays), {dt:.1f} s"}
+        out["accuracy_vs_oracle"] = {"max_exit_dir_err_rad": float(err.max(initial=0)),
+                                     "p999_exit_dir_err_rad": float(np.quantile(err, 0.999)) if len(err) else 0.0,
+                                     "rays_over_1e-9_rad": int((err > 1e-9).sum()), "rays_compared": int(fin.sum()),
+                                     "status_mismatch": int((g["status"] != o["status"]).sum()),
+                                     "pixels_tile_or_status_differs_frac": float(px_diff.mean())}
+
+    # ---- end to end through the public API: render and copy every image to pinned host memory
+    if not args.no_e2e:
+        host = [torch.empty_like(im, device="cpu").pin_memory() for im in imgs]
+        for _ in range(1):
+            step(hs)
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step(hs)
+            for hb, im in zip(host, imgs):
+                hb.copy_(im, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        e2e = ws * rays_step / (statistics.mean(e2e_ms) / 1e3)
+        out["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0,
+                      "d2h_bytes_per_step": sum(im.numel() * 4 for im in imgs),
+                      "note": "inputs are camera and integrator parameters passed by value as kernel arguments; "
+                              "outputs are the 12 float4 images copied to pinned host memory"}
+
+    for c in hs.values():
+        c.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+if __name__ == "__main__":
+    sys.exit(main())

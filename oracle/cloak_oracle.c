@@ -596,8 +596,10 @@ static double event_value(const orc_cloak *c, int ev, const double y[6]) {
 
 /* Reading (the paper is silent): the crossing inside a step y_n -> y_{n+1} is
    the s in (0, h] at which one step of size s of the same integrator from
-   y_n lands on the surface; found by bisection to machine resolution.
-   The returned s is on the far side (exits) or the near side (metal). */
+   y_n lands on the surface, namely the root that bisection of [0, h]
+   converges to (this selects one root when a coarse step crosses the
+   surface more than once).  The returned s is on the far side (exits) or the
+   near side (metal). */
 static double crossing(const orc_cloak *c, const orc_integrator *in, int mode, const double y[6], double h, int ev) {
     double lo = 0.0, hi = h, t[6];
     for (int it = 0; it < 400; ++it) {

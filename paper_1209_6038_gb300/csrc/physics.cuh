@@ -218,13 +218,25 @@ __device__ __forceinline__ void flow(const Params &p, const double y[6], const d
     else dp45_step<VAR, MODE>(p, y, k1, s, out, nullptr, nullptr);
 }
 
-// Root s* in (0, h] of g(flow_s(y)) for a surface crossed by the step (g(0) <= 0 < g(h)):
-// Illinois-modified regula falsi with bisection safeguard, to machine resolution.
+// Root s* in (0, h] of g(flow_s(y)) for a surface crossed by the step (g(0) <= 0 < g(h)).
+// When a coarse step crosses the surface more than once, the root is the one that
+// bisection of [0, h] converges to: the first BISECT_PREFIX halvings are plain
+// bisection (same midpoints as a pure bisection, so the same root is selected), then
+// Illinois-modified regula falsi finishes inside the remaining bracket.
 // Returns the end of the final bracket beyond the surface (exits) or before it (metal).
+constexpr int BISECT_PREFIX = 12;
 template <int VAR, int MODE, int INTEG>
 __device__ double crossing(const Params &p, const double y[6], const double k1[6], double h, double ghi, int ev) {
     double lo = 0.0, hi = h, glo = event_g(p, ev, y), t[6];
     if (!(glo <= 0.0)) glo = 0.0;
+    for (int it = 0; it < BISECT_PREFIX; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        flow<VAR, MODE, INTEG>(p, y, k1, mid, t);
+        double gm = event_g(p, ev, t);
+        if (gm > 0.0) { hi = mid; ghi = gm; }
+        else { lo = mid; glo = gm; }
+    }
     int side = 0;
     for (int it = 0; it < 200; ++it) {
         if (hi - lo <= 4.0e-16 * hi) break;
