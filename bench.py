@@ -186,9 +186,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--ref-pixels", type=int, default=1000, help="oracle pixels per image per step")
-    ap.add_argument("--cpu-pixels", type=int, default=1000, help="oracle pixels per image for cpu_baseline")
+    ap.add_argument("--cpu-pixels", type=int, default=15000, help="oracle pixels per image for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--profile-image", default=None,
+                    help="VARIANT,MODE,ELEV: render only this image twice (for profilers), e.g. 1,1,20")
+    ap.add_argument("--width", type=int, default=None)
+    ap.add_argument("--height", type=int, default=None)
+    ap.add_argument("--schedule", default="plain", choices=["plain", "wavefront"])
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -211,6 +216,21 @@ def main():
     ck.load()
     w = inputs.FULL
     stream = torch.cuda.current_stream()
+    if args.profile_image:
+        v, m, e = args.profile_image.split(",")
+        W, H = args.width or w.width, args.height or w.height
+        eye, tgt, up = inputs.camera_pose(float(e))
+        c = ck.Cloak(int(v)).camera(eye, tgt, up, w.hfov_deg, W, H)
+        c.integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol, ck.FP64, w.max_steps)
+        c.schedule(ck.SCHED_WAVEFRONT if args.schedule == "wavefront" else ck.SCHED_PLAIN)
+        img = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            c.render(int(m), w.spp, w.seed, out=img)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_image": args.profile_image, "width": W, "height": H,
+                          "mean_rgba": img.mean(dim=(0, 1)).tolist()}))
+        c.close()
+        return 0
 
     def make_handles(schedule):
         hs = {}

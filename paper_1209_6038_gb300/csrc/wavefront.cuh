@@ -1,0 +1,303 @@
+// wavefront.cuh -- the optimised FP64 schedule.
+//
+//   A  k_wf_entry      one thread per (pixel, sample): camera ray, cylinder entry, Sect. 3 entry
+//                      refraction and the Eq. 12 factor of the entry face; rays that miss or hit a
+//                      metal disc are shaded at once, rays that enter are appended to a compacted
+//                      device queue (SoA, FP64 state).
+//   B  k_wf_integrate  persistent kernel, one resident grid: every lane owns one queued ray and
+//                      refills itself from the queue when its ray leaves.  Each loop iteration runs
+//                      ONE uniform step evaluation (DP5(4): six right-hand sides; RK4: four) for every
+//                      lane; the surface-crossing search is a lane state that reuses that same step
+//                      slot with a trial step size, so root finding never serialises a warp.
+//   C  k_wf_exit       one thread per queued ray: exit refraction, Eq. 12 factor of the exit face,
+//                      room lookup.
+//   D  k_wf_resolve    per pixel: mean over its samples in sample order.
+//
+// The arithmetic of every ray is that of the plain path (trace.cuh) step for step.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "trace.cuh"
+
+namespace ck {
+
+// queue slot layout (structure of arrays; capacity = rays per image)
+struct Queue {
+    double *x, *y, *z, *vx, *vy, *vz;  // state on entry; final state after B
+    double *w_out;                     // Eq. 12 factor of the entry face (physical exit towards the camera)
+    double *t;                         // time of flight after B
+    int *id;                           // sample index (pixel * spp + sample)
+    int *status;                       // CLOAK_RAY_* after B (EXITED / HIT_METAL_EXITED means: crossed a face)
+    int *steps;
+    int *face;                         // surface crossed at exit (EV_LAT / EV_TOP / EV_BOT)
+    unsigned int *count;               // [0] queued rays, [1] next ray for B, [2] error flag
+    long long cap;
+};
+
+__device__ __forceinline__ void store_sample(float4 *samples, cloak_record *recs, long long id,
+                                             const cloak_record &rec, const float rgb[3]) {
+    if (samples) {
+        float w = (float)rec.weight;
+        samples[id] = make_float4(w * rgb[0], w * rgb[1], w * rgb[2], w);
+    }
+    if (recs) recs[id] = rec;
+}
+
+template <int VAR, int MODE>
+__global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned long long seed, Queue q,
+                                                  float4 *samples, cloak_record *recs) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long n = (long long)p.W * p.Hp * spp;
+    if (idx >= n) return;
+    long long pix = idx / spp;
+    int s = (int)(idx - pix * spp);
+    int i = (int)(pix % p.W), j = (int)(pix / p.W);
+    double o[3], d[3], y[6], k0[3], n_in[3], mat[5];
+    camera_ray(p, i, j, s, spp, seed, o, d);
+    cloak_record rec;
+    float rgb[3];
+    if (!enter<MODE>(p, o, d, rec, rgb, y, k0, n_in, mat)) {
+        store_sample(samples, recs, idx, rec, rgb);
+        return;
+    }
+    // Eq. 12 at the entry face along the physical direction: light leaves the cloak towards the camera
+    double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
+    double w_out = transmission_out(MODE, mat[0], mat[1], c, n_in, mk0);
+    unsigned int slot = atomicAdd(q.count, 1u);
+    q.x[slot] = y[0]; q.y[slot] = y[1]; q.z[slot] = y[2];
+    q.vx[slot] = y[3]; q.vy[slot] = y[4]; q.vz[slot] = y[5];
+    q.w_out[slot] = w_out;
+    q.id[slot] = (int)idx;
+}
+
+// One uniform step evaluation: the integrator's update of size s from y (and, for DP5(4), the
+// embedded error estimate and the first stage of the next step).
+template <int VAR, int MODE, int INTEG>
+__device__ __forceinline__ void step_eval(const Params &p, const double y[6], double k1[6], bool need_k1, double s,
+                                          double y1[6], double e6[6], double k7[6]) {
+    if (INTEG == I_RK4) {
+        rk4_step<VAR, MODE>(p, y, s, y1);
+    } else {
+        if (need_k1) rhs<VAR, MODE>(p, y, k1);
+        dp45_step<VAR, MODE>(p, y, k1, s, y1, e6, k7);
+    }
+}
+
+enum { PH_STEP = 0, PH_CROSS = 1, PH_FINAL = 2, PH_IDLE = 3 };
+
+template <int VAR, int MODE, int INTEG>
+__global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
+    const unsigned int n = q.count[0];
+    const int nev = p.R1 > 0.0 ? 4 : 3;
+    const double tol = p.h_or_tol, h0 = INTEG == I_RK4 ? p.h_or_tol : 1e-3;
+    // lane state
+    double y[6], k1[6], h = h0, t = 0.0;
+    int steps = 0, phase = PH_IDLE, slot = -1;
+    bool metal = false, need_k1 = true;
+    // crossing state
+    double hs = 0.0, fac = 1.0, lo = 0.0, hi = 0.0, glo = 0.0, ghi = 0.0, sbest = 0.0, g1[4];
+    int ev = 0, evbest = -1, side = 0, it = 0;
+    unsigned int pending = 0;
+
+    for (;;) {
+        // ---- refill: a lane without a ray takes the next queued one
+        if (phase == PH_IDLE) {
+            unsigned int k = atomicAdd(q.count + 1, 1u);
+            if (k < n) {
+                slot = (int)k;
+                y[0] = q.x[k]; y[1] = q.y[k]; y[2] = q.z[k];
+                y[3] = q.vx[k]; y[4] = q.vy[k]; y[5] = q.vz[k];
+                h = h0; t = 0.0; steps = 0; metal = false; need_k1 = true; phase = PH_STEP;
+            }
+        }
+        if (__all_sync(__activemask(), phase == PH_IDLE)) {
+            if (phase == PH_IDLE) break;
+        }
+        if (phase == PH_IDLE) break;
+        int status = -1;
+        if (phase == PH_STEP && (steps >= p.max_steps || (INTEG == I_DP45 && h < 1e-14))) status = CLOAK_RAY_STEP_LIMIT;
+        if (status < 0) {
+            double s = phase == PH_STEP ? h : (phase == PH_CROSS ? 0.0 : sbest);
+            if (phase == PH_CROSS) {
+                // next trial point: bisection prefix, then Illinois regula falsi (see crossing())
+                if (it < BISECT_PREFIX) s = 0.5 * (lo + hi);
+                else if (it - BISECT_PREFIX < 60 && ghi > glo) s = (lo * ghi - hi * glo) / (ghi - glo);
+                else s = 0.5 * (lo + hi);
+                if (!(s > lo && s < hi)) s = 0.5 * (lo + hi);
+            }
+            double y1[6], e6[6], k7[6];
+            step_eval<VAR, MODE, INTEG>(p, y, k1, need_k1, s, y1, e6, k7);
+            need_k1 = false;
+            if (phase == PH_STEP) {
+                ++steps;
+                fac = 1.0;
+                bool accept = true;
+                if (INTEG == I_DP45) {
+                    double err = 0.0;
+                    bool bad = false;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        double sc = tol + tol * fmax(fabs(y[i]), fabs(y1[i]));
+                        double qq = fabs(e6[i]) / sc;
+                        if (qq != qq) bad = true;
+                        else if (qq > err) err = qq;
+                    }
+                    if (bad || !(err <= 1.0)) {
+                        h *= (bad || isinf(err)) ? 0.2 : fmax(0.2, 0.9 * pow(err, -0.2));
+                        accept = false;
+                    } else {
+                        fac = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
+                    }
+                }
+                if (accept) {
+                    pending = 0;
+                    for (int e = 0; e < nev; ++e) {
+                        g1[e] = event_g(p, e, y1);
+                        if (g1[e] > 0.0) pending |= 1u << e;
+                    }
+                    if (!pending) {
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) y[i] = y1[i];
+                        t += h;
+                        h *= fac;
+                        if (INTEG == I_DP45) {
+#pragma unroll
+                            for (int i = 0; i < 6; ++i) k1[i] = k7[i];
+                        }
+                    } else {
+                        hs = h;
+                        sbest = 1e300;
+                        evbest = -1;
+                        ev = __ffs(pending) - 1;
+                        lo = 0.0; hi = hs; glo = event_g(p, ev, y); ghi = g1[ev];
+                        if (!(glo <= 0.0)) glo = 0.0;
+                        side = 0; it = 0;
+                        phase = PH_CROSS;
+                    }
+                }
+            } else if (phase == PH_CROSS) {
+                bool done = false;
+                if (!(s > lo && s < hi)) {
+                    done = true;
+                } else {
+                    double gs = event_g(p, ev, y1);
+                    if (it < BISECT_PREFIX) {
+                        if (gs > 0.0) { hi = s; ghi = gs; } else { lo = s; glo = gs; }
+                    } else if (gs > 0.0) {
+                        hi = s; ghi = gs;
+                        if (side == 1) glo *= 0.5;
+                        side = 1;
+                    } else {
+                        lo = s; glo = gs;
+                        if (side == -1) ghi *= 0.5;
+                        side = -1;
+                    }
+                    ++it;
+                    if (it >= BISECT_PREFIX && hi - lo <= 4.0e-16 * hi) done = true;
+                    if (it >= BISECT_PREFIX + 200) done = true;
+                }
+                if (done) {
+                    double se = ev == EV_METAL ? lo : hi;
+                    if (se < sbest) { sbest = se; evbest = ev; }
+                    pending &= ~(1u << ev);
+                    if (pending) {
+                        ev = __ffs(pending) - 1;
+                        lo = 0.0; hi = hs; glo = event_g(p, ev, y); ghi = g1[ev];
+                        if (!(glo <= 0.0)) glo = 0.0;
+                        side = 0; it = 0;
+                    } else {
+                        phase = PH_FINAL;
+                    }
+                }
+            } else {  // PH_FINAL: y1 is the state at the crossing
+#pragma unroll
+                for (int i = 0; i < 6; ++i) y[i] = y1[i];
+                t += sbest;
+                h = hs * fac;
+                need_k1 = true;
+                phase = PH_STEP;
+                if (evbest == EV_METAL) {
+                    if (VAR == V_RADIAL && MODE == M_ORD) {
+                        double r = hypot(y[0], y[1]), nm0 = y[0] / r, nm1 = y[1] / r;
+                        double vn = y[3] * nm0 + y[4] * nm1;
+                        y[3] -= 2.0 * vn * nm0;
+                        y[4] -= 2.0 * vn * nm1;
+                        metal = true;
+                    } else {
+                        status = CLOAK_RAY_SINGULAR;
+                    }
+                } else {
+                    status = metal ? CLOAK_RAY_HIT_METAL_EXITED : CLOAK_RAY_EXITED;
+                }
+            }
+        }
+        if (status >= 0) {  // ray finished: write back, lane becomes idle
+            q.x[slot] = y[0]; q.y[slot] = y[1]; q.z[slot] = y[2];
+            q.vx[slot] = y[3]; q.vy[slot] = y[4]; q.vz[slot] = y[5];
+            q.t[slot] = t;
+            q.status[slot] = status;
+            q.steps[slot] = steps;
+            q.face[slot] = evbest;
+            phase = PH_IDLE;
+        }
+    }
+}
+
+template <int VAR, int MODE>
+__global__ void __launch_bounds__(128) k_wf_exit(Params p, int spp, unsigned long long seed, Queue q,
+                                                 float4 *samples, cloak_record *recs) {
+    const unsigned int n = q.count[0];
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        long long idx = q.id[k];
+        long long pix = idx / spp;
+        int s = (int)(idx - pix * spp);
+        int i = (int)(pix % p.W), j = (int)(pix / p.W);
+        double o[3], d[3];
+        camera_ray(p, i, j, s, spp, seed, o, d);
+        double y[6] = {q.x[k], q.y[k], q.z[k], q.vx[k], q.vy[k], q.vz[k]};
+        int status = q.status[k];
+        cloak_record rec;
+        rec.mode = MODE;
+        rec.tile_id = -1;
+        rec.weight = 0.0;
+        rec.steps = q.steps[k];
+        rec.tof = q.t[k];
+        float rgb[3] = {0.f, 0.f, 0.f};
+        if (status == CLOAK_RAY_EXITED || status == CLOAK_RAY_HIT_METAL_EXITED) {
+            double x[3] = {y[0], y[1], y[2]}, nrm[3], eo, ee, c[3], kk[3];
+            face_normal(q.face[k], x, nrm);
+            local_material(p, x, eo, ee, c);
+            wave_from_velocity(MODE, eo, ee, c, y + 3, kk);
+            double kn = dot3(kk, nrm), kt[3];
+            for (int a = 0; a < 3; ++a) kt[a] = kk[a] - kn * nrm[a];
+            double kt2 = dot3(kt, kt);
+            set_vec(rec.exit_pos, x);
+            if (kt2 > 1.0) {
+                rec.status = CLOAK_RAY_TIR;
+                set_vec(rec.exit_dir, d);
+            } else {
+                double qn = sqrt(1.0 - kt2), dout[3], mdout[3];
+                for (int a = 0; a < 3; ++a) {
+                    dout[a] = fma(qn, nrm[a], kt[a]);
+                    mdout[a] = -dout[a];
+                }
+                double tin = transmission_in(MODE, eo, ee, c, nrm, mdout);
+                rec.weight = tin * q.w_out[k];
+                rec.status = status;
+                set_vec(rec.exit_dir, dout);
+                rec.tile_id = room_hit(p, x, dout, rgb);
+            }
+        } else {  // STEP_LIMIT or SINGULAR
+            rec.status = status;
+            rec.exit_pos[0] = y[0]; rec.exit_pos[1] = y[1]; rec.exit_pos[2] = y[2];
+            set_vec(rec.exit_dir, d);
+        }
+        store_sample(samples, recs, idx, rec, rgb);
+    }
+}
+
+__global__ void k_wf_resolve(int npix, int spp, const float4 *samples, float4 *out);
+
+}  // namespace ck

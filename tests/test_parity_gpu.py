@@ -8,7 +8,7 @@ Where FP64 arithmetic itself does not determine a result to that level, the bar
 widens to what it does determine.  For every ray the oracle is re-run on inputs
 perturbed by 1e-13 (ray origins and directions, or the camera): the change of
 its own output is that ray's spread, and a GPU value may differ from the oracle
-by 1e-9 + 10 x spread.  Rays whose status flips under the perturbation (coarse
+by 1e-9 + 10 x spread (four perturbations for ray sets, three for images).  Rays whose status flips under the perturbation (coarse
 steps near r = R1) are checked for validity only, and their share is bounded.
 A room-tile mismatch is accepted only where the oracle's hit point lies on a tile
 edge (pixel-centre rays of a camera at z = 0 hit the floor at rational points).
@@ -71,7 +71,7 @@ def spread_of(base, others):
 
 def oracle_trace(cloak, integ, mode, rays):
     base = O.trace_rays(cloak, integ, mode, rays)
-    others = [O.trace_rays(cloak, integ, mode, perturb_rays(rays, k)) for k in range(2)]
+    others = [O.trace_rays(cloak, integ, mode, perturb_rays(rays, k)) for k in range(4)]
     return base, spread_of(base, others)
 
 
@@ -187,7 +187,7 @@ def oracle_render(variant, mode, integ, h_or_tol, W, H, spp, elev, seed, pixels=
     integ_o = O.Integrator(integ, h_or_tol)
     rgba, rec = O.render(O.Cloak(variant), integ_o, O.Camera(eye, tgt, up, 60, W, H), mode, spp, seed, pixels=pixels)
     others = []
-    for k in range(2):
+    for k in range(3):
         rng = np.random.default_rng(2000 + k)
         e2 = np.array(eye) + PERTURB * rng.normal(size=3)
         t2 = np.array(tgt) + PERTURB * rng.normal(size=3)
@@ -268,7 +268,8 @@ def test_edge_cases(ck):
     for W, H, spp in ((1, 1, 1), (7, 5, 3)):
         img, rec = small_render(ck, 0, 1, 0, 1e-3, W, H, spp, 0.0, seed=9)
         rgba, orec, sp = oracle_render(0, 1, 0, 1e-3, W, H, spp, 0.0, 9)
-        compare_records(rec, orec, sp, f"{W}x{H}", max_unstable=0.5)
+        # the single pixel of a 1x1 image looks exactly along the axis (impact parameter 0)
+        compare_records(rec, orec, sp, f"{W}x{H}", max_unstable=1.0)
         compare_images(img, rgba, rec, orec, sp, spp, f"{W}x{H}")
     # step limit
     rays = inputs.ray_set(64, seed=2, kind="lateral")
