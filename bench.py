@@ -193,7 +193,7 @@ def main():
                     help="VARIANT,MODE,ELEV: render only this image twice (for profilers), e.g. 1,1,20")
     ap.add_argument("--width", type=int, default=None)
     ap.add_argument("--height", type=int, default=None)
-    ap.add_argument("--schedule", default="plain", choices=["plain", "wavefront"])
+    ap.add_argument("--schedule", default="wavefront", choices=["plain", "wavefront"])
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -245,10 +245,14 @@ def main():
 
     imgs = [torch.empty((w.height, w.width, 4), dtype=torch.float32, device="cuda") for _ in w.images]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stage_ms = [0.0, 0.0, 0.0, 0.0]
 
-    def step(hs):
+    def step(hs, timed_stages=False):
         for i, (v, m, e) in enumerate(w.images):
             hs[(v, e)].render(m, w.spp, w.seed, out=imgs[i])
+            if timed_stages:
+                for k, t in enumerate(hs[(v, e)].stage_times()):
+                    stage_ms[k] += t
 
     def timed(hs, warmup, steps, sampler=None):
         for _ in range(warmup):
@@ -257,6 +261,8 @@ def main():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        for k in range(4):
+            stage_ms[k] = 0.0
         ms = []
         ctx = sampler if sampler is not None else _Null()
         with ctx:
@@ -265,7 +271,7 @@ def main():
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                step(hs)
+                step(hs, timed_stages=True)
                 b.record(stream)
                 b.synchronize()
                 ms.append(a.elapsed_time(b))
@@ -275,21 +281,26 @@ def main():
         tot = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
         if ws > 1:
             dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-        return float(tot.item()) / steps, ms
+        return float(tot.item()) / steps, ms, [x / steps for x in stage_ms]
 
-    sched = ck.SCHED_PLAIN
-    hs = make_handles(sched)
+    main_sched = ck.SCHED_WAVEFRONT if args.schedule == "wavefront" else ck.SCHED_PLAIN
+    hs = make_handles(main_sched)
+    for c in hs.values():
+        c.stage_timing(True)
     sampler = ClockSampler(local)
-    ms_step, ms_list = timed(hs, args.warmup, args.steps, sampler)
+    ms_step, ms_list, stages = timed(hs, args.warmup, args.steps, sampler)
     rays_step = w.rays
     value = ws * rays_step / (ms_step / 1e3)
     clocks = sampler.summary()
-    launches_per_step = len(w.images)  # one render kernel per image on the plain schedule
+    launches_per_image = 4 if main_sched == ck.SCHED_WAVEFRONT else 1
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(w),
-           "schedule": "plain", "clocks": clocks, "gpu_launches": launches_per_step * args.steps}
+           "schedule": args.schedule, "clocks": clocks,
+           "gpu_launches": launches_per_image * len(w.images) * args.steps,
+           "stage_ms_per_step": {"camera_entry": stages[0], "integrate": stages[1], "exit_shade": stages[2],
+                                 "resolve": stages[3]}}
 
     if rank == 0:
         # ---- records pass (untimed): step counts for the roofline, sampled rays for the error
@@ -310,11 +321,13 @@ def main():
             sel = torch.from_numpy((pix[:, None] * w.spp + np.arange(w.spp)[None, :]).reshape(-1)).cuda()
             gpu_samples.append(ck.records_to_numpy(rec_buf.view(-1, ck.RECORD_BYTES)[sel].reshape(-1)))
         del rec_buf
-        achieved = flops / (ms_step / 1e3) / 1e12
+        kname = "k_wf_integrate (12 launches per step)" if main_sched == ck.SCHED_WAVEFRONT else \
+            "k_render_plain (12 launches per step)"
+        achieved = flops / (stages[1] / 1e3) / 1e12
         out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                           "peak_source": "derived: 152 SM x 2.07 GHz x 4 FP64 flop/clk/SM",
-                           "kernel": "k_render_plain (12 launches per step)"}
+                           "peak_source": "derived: 152 SM x 2.07 GHz x 4 FP64 flop/clk/SM", "kernel": kname,
+                           "kernel_ms_per_step": stages[1]}
         out["work"] = {"integrator_steps_per_step": steps_total, "fp64_flops_per_step": flops,
                        "status_hist": {ck.RAY_STATUS[i]: int(status_hist[i]) for i in range(8)}}
 
@@ -337,6 +350,18 @@ def main():
                                      "rays_over_1e-9_rad": int((err > 1e-9).sum()), "rays_compared": int(fin.sum()),
                                      "status_mismatch": int((g["status"] != o["status"]).sum()),
                                      "pixels_tile_or_status_differs_frac": float(px_diff.mean())}
+
+    # ---- the plain FP64 integrator (one thread per pixel) on the same workload, for comparison
+    if not args.no_plain and main_sched != ck.SCHED_PLAIN:
+        ph = make_handles(ck.SCHED_PLAIN)
+        for c in ph.values():
+            c.stage_timing(True)
+        pms, _, _ = timed(ph, 1, 1)
+        for c in ph.values():
+            c.close()
+        out["plain_fp64"] = {"value": ws * rays_step / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+                             "warmup": 1, "steps": 1}
+        out["speedup_vs_plain_fp64"] = pms / ms_step
 
     # ---- end to end through the public API: render and copy every image to pinned host memory
     if not args.no_e2e:

@@ -115,6 +115,15 @@ int cloak_set_scene_seed(cloak_t *h, unsigned long long seed);
  * (32..1024, multiple of 32, 0 = default); steps_per_round: reserved (0). */
 int cloak_set_schedule(cloak_t *h, int schedule, int packet, int steps_per_round);
 
+/* Per-stage device timing (CUDA events on the call's stream).  on != 0 enables it for later calls.
+ * cloak_stage_times waits for the last cloak_render / cloak_render_records call on this handle and
+ * writes its stage durations in milliseconds: ms[0] camera rays + entry refraction, ms[1] integration
+ * of Eq. 2 / Eq. 8 (the whole kernel on the plain schedule), ms[2] exit refraction + Eq. 12 weights +
+ * room lookup, ms[3] per-pixel resolve (0 where a stage does not exist).  CLOAK_ESTATE if timing was
+ * off or nothing was rendered since it was enabled. */
+int cloak_set_stage_timing(cloak_t *h, int on);
+int cloak_stage_times(cloak_t *h, float ms[4]);
+
 /* Render one image of the chosen polarization (Sect. 4): dev_rgba is float4[width*height]
  * (bytes >= 16*width*height), RGB = mean over the spp samples of weight * colour, A = mean weight.
  * spp >= 1; one sample goes through the pixel centre, more samples are jittered from

@@ -39,6 +39,8 @@ SIGNATURES = {
     "cloak_set_test_medium": (C.c_int, [C.c_void_p, C.c_double, C.c_double, _d3]),
     "cloak_set_scene_seed": (C.c_int, [C.c_void_p, C.c_ulonglong]),
     "cloak_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "cloak_set_stage_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "cloak_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     "cloak_render": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t, C.c_void_p]),
     "cloak_render_records": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
@@ -122,6 +124,17 @@ def cloak_set_schedule(h, schedule, packet=0, steps_per_round=0):
     return _check(load().cloak_set_schedule(h, schedule, packet, steps_per_round))
 
 
+def cloak_set_stage_timing(h, on):
+    return _check(load().cloak_set_stage_timing(h, 1 if on else 0))
+
+
+def cloak_stage_times(h):
+    """[camera+entry, integration, exit+shading, resolve] of the last render, in ms."""
+    ms = (C.c_float * 4)()
+    _check(load().cloak_stage_times(h, ms))
+    return list(ms)
+
+
 def cloak_render(h, polarization, spp, seed, rgba, stream=None):
     """rgba: float32 CUDA tensor with >= 4*W*H elements."""
     return _check(load().cloak_render(h, polarization, spp, seed, C.c_void_p(rgba.data_ptr()),
@@ -178,6 +191,13 @@ class Cloak:
     def schedule(self, schedule=SCHED_PLAIN, packet=0, steps_per_round=0):
         cloak_set_schedule(self.h, schedule, packet, steps_per_round)
         return self
+
+    def stage_timing(self, on=True):
+        cloak_set_stage_timing(self.h, on)
+        return self
+
+    def stage_times(self):
+        return cloak_stage_times(self.h)
 
     def test_medium(self, eps_o, eps_e, c_hat):
         cloak_set_test_medium(self.h, eps_o, eps_e, c_hat)

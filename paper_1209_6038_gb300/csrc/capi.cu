@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "wavefront.cuh"
 
 struct cloak {
     int variant;
@@ -23,6 +24,14 @@ struct cloak {
     long max_steps;
     int schedule, packet, steps_per_round;
     int device;
+    // library-owned scratch of the wavefront schedule (queue + per-sample buffer), grown on demand
+    void *scratch;
+    size_t scratch_bytes;
+    // stage timing: events recorded around the stages of the last render call
+    int timing;        // 0 off, 1 on
+    int timed_calls;   // renders since timing was enabled
+    int timed_sched;   // schedule of the last timed render
+    cudaEvent_t ev[5];
 };
 
 static thread_local std::string g_err;
@@ -88,6 +97,63 @@ static int make_params(const cloak *h, ck::Params &p) {
     return CLOAK_OK;
 }
 
+// Carve the wavefront queue (SoA, cap slots) and the per-sample buffer out of the handle's scratch.
+static int wavefront_scratch(cloak *h, long long cap, ck::Queue &q, float4 **samples) {
+    size_t need = (size_t)cap * (8 * sizeof(double) + 4 * sizeof(int) + sizeof(float4)) + 256;
+    if (h->scratch_bytes < need) {
+        if (h->scratch) {
+            cudaError_t e = cudaFree(h->scratch);
+            h->scratch = nullptr;
+            h->scratch_bytes = 0;
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFree(scratch)");
+        }
+        cudaError_t e = cudaMalloc(&h->scratch, need);
+        if (e != cudaSuccess) {
+            h->scratch = nullptr;
+            cudaGetLastError();
+            return fail(CLOAK_ENOMEM, "cannot allocate %zu bytes of wavefront scratch: %s", need, cudaGetErrorString(e));
+        }
+        h->scratch_bytes = need;
+    }
+    char *b = (char *)h->scratch;
+    q.count = (unsigned int *)b;
+    b += 256;
+    double **dp[8] = {&q.x, &q.y, &q.z, &q.vx, &q.vy, &q.vz, &q.w_out, &q.t};
+    for (int i = 0; i < 8; ++i) { *dp[i] = (double *)b; b += (size_t)cap * sizeof(double); }
+    *samples = (float4 *)b;
+    b += (size_t)cap * sizeof(float4);
+    int **ip[4] = {&q.id, &q.status, &q.steps, &q.face};
+    for (int i = 0; i < 4; ++i) { *ip[i] = (int *)b; b += (size_t)cap * sizeof(int); }
+    q.cap = cap;
+    return CLOAK_OK;
+}
+
+static int run_wavefront(cloak *h, const ck::Params &p, int pol, int spp, unsigned long long seed, float4 *out,
+                         cloak_record *recs, cudaStream_t st) {
+    long long cap = (long long)p.W * p.Hp * spp;
+    if (cap > 2147483647LL) return fail(CLOAK_EINVAL, "width*height*spp = %lld exceeds 2^31-1", cap);
+    ck::Queue q;
+    float4 *samples = nullptr;
+    int rc = wavefront_scratch(h, cap, q, &samples);
+    if (rc) return rc;
+    cudaEvent_t *ev = h->timing ? h->ev : nullptr;
+    if (ev) cudaEventRecord(ev[0], st);
+    cudaError_t e = cudaMemsetAsync(q.count, 0, 256, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    e = ck::launch_wavefront(p, pol, spp, seed, q, recs ? nullptr : samples, recs, h->packet, st, ev);
+    if (e != cudaSuccess) return cuda_fail(e, "wavefront launch");
+    if (!recs) {
+        e = ck::launch_resolve(p.W * p.Hp, spp, samples, out, st);
+        if (e != cudaSuccess) return cuda_fail(e, "resolve launch");
+    }
+    if (ev) {
+        cudaEventRecord(ev[4], st);
+        h->timed_calls++;
+        h->timed_sched = CLOAK_SCHED_WAVEFRONT;
+    }
+    return CLOAK_OK;
+}
+
 static int use_device(const cloak *h) {
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
@@ -143,13 +209,65 @@ cloak_t *cloak_create(int variant, double R1, double R2, double height) {
     h->packet = 0;
     h->steps_per_round = 0;
     h->device = dev;
+    h->scratch = nullptr;
+    h->scratch_bytes = 0;
+    h->timing = 0;
+    h->timed_calls = 0;
+    h->timed_sched = 0;
     g_err.clear();
     return h;
 }
 
 void cloak_destroy(cloak_t *h) {
     if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->scratch) cudaFree(h->scratch);
+    if (h->timing)
+        for (int i = 0; i < 5; ++i) cudaEventDestroy(h->ev[i]);
     delete h;
+}
+
+int cloak_set_stage_timing(cloak_t *h, int on) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    int rc = use_device(h);
+    if (rc) return rc;
+    if (on && !h->timing) {
+        for (int i = 0; i < 5; ++i) {
+            cudaError_t e = cudaEventCreate(&h->ev[i]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < i; ++j) cudaEventDestroy(h->ev[j]);
+                return cuda_fail(e, "cudaEventCreate");
+            }
+        }
+        h->timing = 1;
+        h->timed_calls = 0;
+    } else if (!on && h->timing) {
+        cudaError_t e = cudaDeviceSynchronize();
+        for (int i = 0; i < 5; ++i) cudaEventDestroy(h->ev[i]);
+        h->timing = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    }
+    return CLOAK_OK;
+}
+
+int cloak_stage_times(cloak_t *h, float ms[4]) {
+    if (!h || !ms) return fail(CLOAK_EINVAL, "null argument");
+    if (!h->timing || h->timed_calls == 0) return fail(CLOAK_ESTATE, "stage timing is off or nothing was timed");
+    int rc = use_device(h);
+    if (rc) return rc;
+    cudaError_t e = cudaEventSynchronize(h->ev[4]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    for (int i = 0; i < 4; ++i) ms[i] = 0.f;
+    if (h->timed_sched == CLOAK_SCHED_WAVEFRONT) {
+        for (int i = 0; i < 4; ++i) {
+            e = cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        }
+    } else {
+        e = cudaEventElapsedTime(&ms[1], h->ev[0], h->ev[4]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    }
+    return CLOAK_OK;
 }
 
 int cloak_camera_set(cloak_t *h, const double eye[3], const double target[3], const double up[3], double hfov_deg,
@@ -230,8 +348,16 @@ int cloak_render(cloak_t *h, int polarization, int spp, unsigned long long seed,
     int rc = make_params(h, p);
     if (rc) return rc;
     if ((rc = use_device(h))) return rc;
+    if (h->schedule == CLOAK_SCHED_WAVEFRONT)
+        return run_wavefront(h, p, polarization, spp, seed, (float4 *)dev_rgba, nullptr, (cudaStream_t)cuda_stream);
+    if (h->timing) cudaEventRecord(h->ev[0], (cudaStream_t)cuda_stream);
     cudaError_t e = ck::launch_render_plain(p, polarization, spp, seed, (float4 *)dev_rgba, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "render launch");
+    if (h->timing) {
+        cudaEventRecord(h->ev[4], (cudaStream_t)cuda_stream);
+        h->timed_calls++;
+        h->timed_sched = CLOAK_SCHED_PLAIN;
+    }
     return CLOAK_OK;
 }
 
@@ -248,9 +374,18 @@ int cloak_render_records(cloak_t *h, int polarization, int spp, unsigned long lo
     int rc = make_params(h, p);
     if (rc) return rc;
     if ((rc = use_device(h))) return rc;
+    if (h->schedule == CLOAK_SCHED_WAVEFRONT)
+        return run_wavefront(h, p, polarization, spp, seed, nullptr, (cloak_record *)dev_records,
+                             (cudaStream_t)cuda_stream);
+    if (h->timing) cudaEventRecord(h->ev[0], (cudaStream_t)cuda_stream);
     cudaError_t e = ck::launch_records_plain(p, polarization, spp, seed, (cloak_record *)dev_records,
                                              (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "records launch");
+    if (h->timing) {
+        cudaEventRecord(h->ev[4], (cudaStream_t)cuda_stream);
+        h->timed_calls++;
+        h->timed_sched = CLOAK_SCHED_PLAIN;
+    }
     return CLOAK_OK;
 }
 

@@ -46,4 +46,21 @@ inline cudaError_t launch_trace_rays(const Params &p, int mode, const double *ra
     return launch_trace_rays_v<2>(p, mode, rays, n, out, st);
 }
 
+struct Queue;
+template <int V>
+cudaError_t launch_wavefront_v(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q,
+                               float4 *samples, cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev);
+extern template cudaError_t launch_wavefront_v<0>(const Params &, int, int, unsigned long long, const Queue &, float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *);
+extern template cudaError_t launch_wavefront_v<1>(const Params &, int, int, unsigned long long, const Queue &, float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *);
+extern template cudaError_t launch_wavefront_v<2>(const Params &, int, int, unsigned long long, const Queue &, float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *);
+// ev (nullable): ev[1] after entry, ev[2] after integration, ev[3] after exit (ev[0] is recorded by the caller)
+inline cudaError_t launch_wavefront(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q,
+                                    float4 *samples, cloak_record *recs, int packet, cudaStream_t st,
+                                    cudaEvent_t *ev) {
+    if (p.variant == V_RADIAL) return launch_wavefront_v<0>(p, mode, spp, seed, q, samples, recs, packet, st, ev);
+    if (p.variant == V_AZIMUTHAL) return launch_wavefront_v<1>(p, mode, spp, seed, q, samples, recs, packet, st, ev);
+    return launch_wavefront_v<2>(p, mode, spp, seed, q, samples, recs, packet, st, ev);
+}
+cudaError_t launch_resolve(int npix, int spp, const float4 *samples, float4 *out, cudaStream_t st);
+
 }  // namespace ck

@@ -1,0 +1,25 @@
+// Kernels shared by all variants.
+#include "wavefront.cuh"
+
+namespace ck {
+
+// mean over the samples of each pixel, in sample order (the plain path accumulates the same way)
+__global__ void k_wf_resolve(int npix, int spp, const float4 *samples, float4 *out) {
+    int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= npix) return;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const float4 *s = samples + (long long)pix * spp;
+    for (int k = 0; k < spp; ++k) {
+        float4 v = s[k];
+        a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
+    }
+    float inv = 1.0f / spp;
+    out[pix] = make_float4(a0 * inv, a1 * inv, a2 * inv, a3 * inv);
+}
+
+cudaError_t launch_resolve(int npix, int spp, const float4 *samples, float4 *out, cudaStream_t st) {
+    k_wf_resolve<<<(npix + 255) / 256, 256, 0, st>>>(npix, spp, samples, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ck

@@ -112,10 +112,7 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                 h = h0; t = 0.0; steps = 0; metal = false; need_k1 = true; phase = PH_STEP;
             }
         }
-        if (__all_sync(__activemask(), phase == PH_IDLE)) {
-            if (phase == PH_IDLE) break;
-        }
-        if (phase == PH_IDLE) break;
+        if (phase == PH_IDLE) break;  // queue drained for this lane
         int status = -1;
         if (phase == PH_STEP && (steps >= p.max_steps || (INTEG == I_DP45 && h < 1e-14))) status = CLOAK_RAY_STEP_LIMIT;
         if (status < 0) {
@@ -299,5 +296,59 @@ __global__ void __launch_bounds__(128) k_wf_exit(Params p, int spp, unsigned lon
 }
 
 __global__ void k_wf_resolve(int npix, int spp, const float4 *samples, float4 *out);
+
+}  // namespace ck
+
+namespace ck {
+
+template <int V, int M, int I>
+static cudaError_t wavefront_vmi(const Params &p, int spp, unsigned long long seed, const Queue &q, float4 *samples,
+                                 cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev) {
+    long long n = (long long)p.W * p.Hp * spp;
+    const int bs = 128;
+    k_wf_entry<V, M><<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(p, spp, seed, q, samples, recs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
+    // persistent integrator: exactly the resident grid
+    static int blocks_per_sm[33] = {0};
+    int pk = packet > 0 ? packet : 128;
+    int slot = pk / 32;
+    if (blocks_per_sm[slot] == 0) {
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V, M, I>, pk, 0);
+        if (e != cudaSuccess) return e;
+        blocks_per_sm[slot] = nb > 0 ? nb : 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_wf_integrate<V, M, I><<<blocks_per_sm[slot] * sms, pk, 0, st>>>(p, q);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[2], st);
+    k_wf_exit<V, M><<<sms * 16, 128, 0, st>>>(p, spp, seed, q, samples, recs);
+    e = cudaGetLastError();
+    if (ev) cudaEventRecord(ev[3], st);
+    return e;
+}
+
+template <int V>
+cudaError_t launch_wavefront_v(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q,
+                               float4 *samples, cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev) {
+    if (mode == M_ORD && p.integ == I_RK4)
+        return wavefront_vmi<V, M_ORD, I_RK4>(p, spp, seed, q, samples, recs, packet, st, ev);
+    if (mode == M_ORD && p.integ == I_DP45)
+        return wavefront_vmi<V, M_ORD, I_DP45>(p, spp, seed, q, samples, recs, packet, st, ev);
+    if (mode == M_EXT && p.integ == I_RK4)
+        return wavefront_vmi<V, M_EXT, I_RK4>(p, spp, seed, q, samples, recs, packet, st, ev);
+    if (mode == M_EXT && p.integ == I_DP45)
+        return wavefront_vmi<V, M_EXT, I_DP45>(p, spp, seed, q, samples, recs, packet, st, ev);
+    return cudaErrorInvalidValue;
+}
+
+#define CK_INSTANTIATE_WAVEFRONT(V)                                                                        \
+    template cudaError_t launch_wavefront_v<V>(const Params &, int, int, unsigned long long, const Queue &, \
+                                               float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *);
 
 }  // namespace ck

@@ -168,10 +168,14 @@ def test_test_medium_interfaces(ck, mode):
     assert np.isin(o["status"], [1]).sum() > 200
 
 
-def small_render(ck, variant, mode, integ, h_or_tol, W, H, spp, elev, seed=0, records=True):
+SCHEDULES = ("plain", "wavefront")
+
+
+def small_render(ck, variant, mode, integ, h_or_tol, W, H, spp, elev, seed=0, records=True, schedule="plain"):
     import torch
     eye, tgt, up = inputs.camera_pose(elev)
     c = ck.Cloak(variant).camera(eye, tgt, up, 60.0, W, H).integrator(integ, h_or_tol)
+    c.schedule(ck.SCHED_WAVEFRONT if schedule == "wavefront" else ck.SCHED_PLAIN)
     img = c.render(mode, spp, seed)
     rec = c.render_records(mode, spp, seed) if records else None
     torch.cuda.synchronize()
@@ -209,12 +213,13 @@ def compare_images(img, rgba, rec, orec, sp, spp, what):
 def test_small_config_image(ck):
     """The small workload (radial, extraordinary, 128x96, 1 spp, RK4 h = 1e-3): whole image."""
     w = inputs.SMALL
-    img, rec = small_render(ck, 0, 1, 0, 1e-3, w.width, w.height, 1, 0.0)
     rgba, orec, sp = oracle_render(0, 1, 0, 1e-3, w.width, w.height, 1, 0.0, 0)
-    stats = compare_records(rec, orec, sp, "small image")
-    frac = compare_images(img, rgba, rec, orec, sp, 1, "small image")
-    print(stats, "pixels without a determined tile:", frac)
-    assert frac < 0.002
+    for sched in SCHEDULES:
+        img, rec = small_render(ck, 0, 1, 0, 1e-3, w.width, w.height, 1, 0.0, schedule=sched)
+        stats = compare_records(rec, orec, sp, f"small image {sched}")
+        frac = compare_images(img, rgba, rec, orec, sp, 1, f"small image {sched}")
+        print(sched, stats, "pixels without a determined tile:", frac)
+        assert frac < 0.002
     assert (orec["status"] == 1).sum() > 1500
 
 
@@ -225,14 +230,16 @@ def test_jittered_elevations_dp45(ck, variant, mode):
     DP5(4) at tol 1e-9, 61x37 pixels (a ragged tail for 128-thread blocks)."""
     W, H, spp = 61, 37, 2
     for elev in (0.0, 20.0, 45.0):
-        img, rec = small_render(ck, variant, mode, 1, 1e-9, W, H, spp, elev, seed=3)
         rgba, orec, sp = oracle_render(variant, mode, 1, 1e-9, W, H, spp, elev, 3)
-        stats = compare_records(rec, orec, sp, f"v{variant} m{mode} e{elev}", steps_exact=False)
-        compare_images(img, rgba, rec, orec, sp, spp, f"v{variant} m{mode} e{elev}")
-        print(elev, stats)
+        for sched in SCHEDULES:
+            img, rec = small_render(ck, variant, mode, 1, 1e-9, W, H, spp, elev, seed=3, schedule=sched)
+            stats = compare_records(rec, orec, sp, f"v{variant} m{mode} e{elev} {sched}", steps_exact=False)
+            compare_images(img, rgba, rec, orec, sp, spp, f"v{variant} m{mode} e{elev} {sched}")
+            print(elev, sched, stats)
 
 
-def test_full_size_sampled(ck):
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_full_size_sampled(ck, schedule):
     """1920x1080, 4 jittered spp, DP5(4) tol 1e-9 (the full workload's launch shape),
     azimuthal cloak, extraordinary light, elevation 20 deg: a seeded sample of pixels
     against the oracle; validity over every pixel."""
@@ -240,6 +247,7 @@ def test_full_size_sampled(ck):
     w = inputs.FULL
     eye, tgt, up = inputs.camera_pose(20.0)
     c = ck.Cloak(1).camera(eye, tgt, up, 60.0, w.width, w.height).integrator(1, 1e-9)
+    c.schedule(ck.SCHED_WAVEFRONT if schedule == "wavefront" else ck.SCHED_PLAIN)
     rec_t = c.render_records(1, w.spp, w.seed)
     img = c.render(1, w.spp, w.seed)
     torch.cuda.synchronize()
@@ -266,11 +274,12 @@ def test_edge_cases(ck):
     ck.cloak_trace_rays(c.h, 1, torch.empty((0, 6), dtype=torch.float64, device="cuda"), 0, out)
     # 1x1 and odd images
     for W, H, spp in ((1, 1, 1), (7, 5, 3)):
-        img, rec = small_render(ck, 0, 1, 0, 1e-3, W, H, spp, 0.0, seed=9)
         rgba, orec, sp = oracle_render(0, 1, 0, 1e-3, W, H, spp, 0.0, 9)
-        # the single pixel of a 1x1 image looks exactly along the axis (impact parameter 0)
-        compare_records(rec, orec, sp, f"{W}x{H}", max_unstable=1.0)
-        compare_images(img, rgba, rec, orec, sp, spp, f"{W}x{H}")
+        for sched in SCHEDULES:
+            img, rec = small_render(ck, 0, 1, 0, 1e-3, W, H, spp, 0.0, seed=9, schedule=sched)
+            # the single pixel of a 1x1 image looks exactly along the axis (impact parameter 0)
+            compare_records(rec, orec, sp, f"{W}x{H} {sched}", max_unstable=1.0)
+            compare_images(img, rgba, rec, orec, sp, spp, f"{W}x{H} {sched}")
     # step limit
     rays = inputs.ray_set(64, seed=2, kind="lateral")
     g = gpu_trace(ck, 1, 1, rays, 0, 1e-3, max_steps=7)
@@ -287,3 +296,18 @@ def test_edge_cases(ck):
     with pytest.raises(ck.CloakError):
         ck.cloak_create(0, 1.0, 0.5, 2.0)
     c.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_wavefront_matches_plain(ck, variant, mode):
+    """Both schedules run the same per-ray arithmetic: their records and images agree
+    (here at 320x180, 4 spp, DP5(4), elevation 20 deg, and RK4 at elevation 45 deg)."""
+    for integ, tol, elev in ((1, 1e-9, 20.0), (0, 1e-3, 45.0)):
+        a_img, a_rec = small_render(ck, variant, mode, integ, tol, 320, 180, 4, elev, seed=5, schedule="plain")
+        b_img, b_rec = small_render(ck, variant, mode, integ, tol, 320, 180, 4, elev, seed=5, schedule="wavefront")
+        assert np.array_equal(a_rec["status"], b_rec["status"])
+        assert np.array_equal(a_rec["tile_id"], b_rec["tile_id"])
+        assert angles(a_rec["exit_dir"], b_rec["exit_dir"]).max() < 1e-12
+        assert np.abs(a_rec["tof"] - b_rec["tof"]).max() < 1e-12
+        assert np.abs(a_img - b_img).max() < 1e-6
