@@ -1,0 +1,315 @@
+// integrator.cuh -- the persistent integration kernel of the wavefront schedule, templated on a
+// stepper that fixes the arithmetic:
+//
+//   Stepper64     FP64 throughout (the arithmetic of the plain path, step for step).
+//   StepperMixed  right-hand sides of Eq. 2 / Eq. 8 and the stage combinations in FP32; the state
+//                 (x, v) accumulated as float-float (TwoSum, Knuth 1969), so rounding does not build
+//                 up over thousands of steps; whole steps in FP64 where r < R1 + 0.02 (f -> 0 at
+//                 R1 makes FP32 lose the relative precision of r - R1); step control in FP32.
+//
+// Each lane owns one queued ray and refills from the queue when it finishes.  Every loop iteration
+// runs ONE uniform step evaluation for all lanes; the surface-crossing search (bisection prefix,
+// then Illinois regula falsi, see crossing() in physics.cuh) reuses that slot with a trial size.
+#pragma once
+
+#include "physics.cuh"
+
+namespace ck {
+
+struct Queue;
+
+// ------------------------------------------------------------------ FP64 stepper
+template <int VAR, int MODE, int INTEG>
+struct Stepper64 {
+    typedef double real;
+    double y[6], k1[6], y1[6], e6[6], k7[6];
+    bool need_k1;
+
+    __device__ __forceinline__ void load(const double *x, const double *yy, const double *z, const double *vx,
+                                         const double *vy, const double *vz, int k) {
+        y[0] = x[k]; y[1] = yy[k]; y[2] = z[k];
+        y[3] = vx[k]; y[4] = vy[k]; y[5] = vz[k];
+        need_k1 = true;
+    }
+    __device__ __forceinline__ void eval(const Params &p, double s) {
+        if (INTEG == I_RK4) {
+            rk4_step<VAR, MODE>(p, y, s, y1);
+        } else {
+            if (need_k1) rhs<VAR, MODE>(p, y, k1);
+            need_k1 = false;
+            dp45_step<VAR, MODE>(p, y, k1, s, y1, e6, k7);
+        }
+    }
+    // DP5(4) error norm; NaN if any component is NaN
+    __device__ __forceinline__ double err(double tol) const {
+        double e = 0.0;
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double sc = tol + tol * fmax(fabs(y[i]), fabs(y1[i]));
+            double q = fabs(e6[i]) / sc;
+            if (q != q) bad = true;
+            else if (q > e) e = q;
+        }
+        return bad ? __longlong_as_double(0x7ff8000000000000ll) : e;
+    }
+    __device__ __forceinline__ double g_start(const Params &p, int ev) const { return event_g(p, ev, y); }
+    __device__ __forceinline__ double g_end(const Params &p, int ev) const { return event_g(p, ev, y1); }
+    __device__ __forceinline__ void take_step() {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y[i] = y1[i];
+        if (INTEG == I_DP45) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) k1[i] = k7[i];  // first stage of the next step (FSAL)
+        }
+    }
+    __device__ __forceinline__ void take_crossing() {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y[i] = y1[i];
+        need_k1 = true;
+    }
+    __device__ __forceinline__ void mirror() {  // Sect. 4: single mirror ray at the metal cylinder
+        double r = hypot(y[0], y[1]), nm0 = y[0] / r, nm1 = y[1] / r;
+        double vn = y[3] * nm0 + y[4] * nm1;
+        y[3] -= 2.0 * vn * nm0;
+        y[4] -= 2.0 * vn * nm1;
+        need_k1 = true;
+    }
+    __device__ __forceinline__ void state(double out[6]) const {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) out[i] = y[i];
+    }
+    static __device__ __forceinline__ double rpow(double x, double e) { return pow(x, e); }
+};
+
+// ------------------------------------------------------------------ mixed stepper
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (hi, lo) + d  ->  renormalised (hi', lo')
+__device__ __forceinline__ void ff_add(float hi, float lo, float d, float &oh, float &ol) {
+    float s, e;
+    two_sum(hi, d, s, e);
+    e += lo;
+    oh = s + e;
+    ol = e - (oh - s);
+}
+
+// dv/dt of Eq. 8 / Eq. 2 in FP32 with the fast reciprocal square root and division
+template <int VAR, int MODE>
+__device__ __forceinline__ void accel_f32(float R1, float K, float invK, float x, float y, float vx, float vy, float vz,
+                                          float &ax, float &ay, float &az) {
+    if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD)) {
+        ax = 0.f; ay = 0.f; az = 0.f;
+        return;
+    }
+    float r2 = x * x + y * y;
+    float ir = rsqrtf(r2);
+    float r = r2 * ir;
+    float cx = x * ir, cy = y * ir;
+    float vr = vx * cx + vy * cy;
+    float vt = vy * cx - vx * cy;
+    float u = r - R1;
+    float g = __fdividef(2.f * R1 * ir, u);  // f'/f
+    float ar, at, azz;
+    if (MODE == M_EXT) {
+        float q = u * ir;
+        float f = K * q * q;
+        float fp = f * g;
+        float vt2 = vt * vt;
+        at = -g * vr * vt;
+        if (VAR == V_RADIAL) {
+            ar = (0.5f * fp * (vt2 + vz * vz) - (K - f) * vt2 * ir) * invK;
+            azz = -g * vr * vz;
+        } else {
+            ar = (0.5f * fp * vt2 - (K - f) * vt2 * ir) * invK;
+            azz = 0.f;
+        }
+    } else {
+        float hg = 0.5f * g;
+        ar = hg * (vt * vt + vz * vz - vr * vr);
+        at = -g * vr * vt;
+        azz = -g * vr * vz;
+    }
+    ax = ar * cx - at * cy;
+    ay = ar * cy + at * cx;
+    az = azz;
+}
+
+template <int VAR, int MODE>
+__device__ __forceinline__ void rhs_f32(const Params &p, const float t[6], float d[6]) {
+    d[0] = t[3]; d[1] = t[4]; d[2] = t[5];
+    accel_f32<VAR, MODE>((float)p.R1, (float)p.K, (float)p.invK, t[0], t[1], t[3], t[4], t[5], d[3], d[4], d[5]);
+}
+
+constexpr double MIXED_FP64_BAND = 0.02;  // FP64 steps for r < R1 + 0.02
+
+template <int VAR, int MODE, int INTEG>
+struct StepperMixed {
+    typedef float real;
+    float yh[6], yl[6], k1[6];  // state (float-float) and first stage
+    float y1h[6], y1l[6], e6[6], k7[6];
+    bool need_k1;
+
+    __device__ __forceinline__ void load(const double *x, const double *yy, const double *z, const double *vx,
+                                         const double *vy, const double *vz, int k) {
+        double v[6] = {x[k], yy[k], z[k], vx[k], vy[k], vz[k]};
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            yh[i] = (float)v[i];
+            yl[i] = (float)(v[i] - (double)yh[i]);
+        }
+        need_k1 = true;
+    }
+    __device__ __forceinline__ bool island(const Params &p) const {
+        if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD)) return false;
+        float x = yh[0] + yl[0], y = yh[1] + yl[1];
+        float lim = (float)(p.R1 + MIXED_FP64_BAND);
+        return x * x + y * y < lim * lim;
+    }
+    __device__ __forceinline__ void eval(const Params &p, float s) {
+        if (island(p)) {  // FP64 step from the float-float state
+            double y[6], yo[6], e[6], kk1[6], kk7[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) y[i] = (double)yh[i] + (double)yl[i];
+            if (INTEG == I_RK4) {
+                rk4_step<VAR, MODE>(p, y, (double)s, yo);
+            } else {
+                rhs<VAR, MODE>(p, y, kk1);
+                dp45_step<VAR, MODE>(p, y, kk1, (double)s, yo, e, kk7);
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                y1h[i] = (float)yo[i];
+                y1l[i] = (float)(yo[i] - (double)y1h[i]);
+                if (INTEG == I_DP45) { e6[i] = (float)e[i]; k7[i] = (float)kk7[i]; }
+            }
+            need_k1 = true;
+            return;
+        }
+        float t[6], k2[6], k3[6], k4[6], k5[6], k6[6];
+        if (INTEG == I_RK4) {
+            float acc[6], kk[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) t[i] = yh[i] + yl[i];
+            rhs_f32<VAR, MODE>(p, t, kk);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) { acc[i] = kk[i]; t[i] = yh[i] + fmaf(0.5f * s, kk[i], yl[i]); }
+            rhs_f32<VAR, MODE>(p, t, kk);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) { acc[i] = fmaf(2.f, kk[i], acc[i]); t[i] = yh[i] + fmaf(0.5f * s, kk[i], yl[i]); }
+            rhs_f32<VAR, MODE>(p, t, kk);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) { acc[i] = fmaf(2.f, kk[i], acc[i]); t[i] = yh[i] + fmaf(s, kk[i], yl[i]); }
+            rhs_f32<VAR, MODE>(p, t, kk);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) ff_add(yh[i], yl[i], s * (1.f / 6.f) * (acc[i] + kk[i]), y1h[i], y1l[i]);
+            return;
+        }
+        if (need_k1) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) t[i] = yh[i] + yl[i];
+            rhs_f32<VAR, MODE>(p, t, k1);
+            need_k1 = false;
+        }
+        const float a21 = (float)DP::a21, a31 = (float)DP::a31, a32 = (float)DP::a32, a41 = (float)DP::a41,
+                    a42 = (float)DP::a42, a43 = (float)DP::a43, a51 = (float)DP::a51, a52 = (float)DP::a52,
+                    a53 = (float)DP::a53, a54 = (float)DP::a54, a61 = (float)DP::a61, a62 = (float)DP::a62,
+                    a63 = (float)DP::a63, a64 = (float)DP::a64, a65 = (float)DP::a65, b1 = (float)DP::b1,
+                    b3 = (float)DP::b3, b4 = (float)DP::b4, b5 = (float)DP::b5, b6 = (float)DP::b6,
+                    c1 = (float)DP::e1, c3 = (float)DP::e3, c4 = (float)DP::e4, c5 = (float)DP::e5,
+                    c6 = (float)DP::e6, c7 = (float)DP::e7;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) t[i] = yh[i] + fmaf(s, a21 * k1[i], yl[i]);
+        rhs_f32<VAR, MODE>(p, t, k2);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) t[i] = yh[i] + fmaf(s, a31 * k1[i] + a32 * k2[i], yl[i]);
+        rhs_f32<VAR, MODE>(p, t, k3);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) t[i] = yh[i] + fmaf(s, a41 * k1[i] + a42 * k2[i] + a43 * k3[i], yl[i]);
+        rhs_f32<VAR, MODE>(p, t, k4);
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            t[i] = yh[i] + fmaf(s, a51 * k1[i] + a52 * k2[i] + a53 * k3[i] + a54 * k4[i], yl[i]);
+        rhs_f32<VAR, MODE>(p, t, k5);
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            t[i] = yh[i] + fmaf(s, a61 * k1[i] + a62 * k2[i] + a63 * k3[i] + a64 * k4[i] + a65 * k5[i], yl[i]);
+        rhs_f32<VAR, MODE>(p, t, k6);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            float d = s * (b1 * k1[i] + b3 * k3[i] + b4 * k4[i] + b5 * k5[i] + b6 * k6[i]);
+            ff_add(yh[i], yl[i], d, y1h[i], y1l[i]);
+            t[i] = y1h[i] + y1l[i];
+        }
+        rhs_f32<VAR, MODE>(p, t, k7);
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            e6[i] = s * (c1 * k1[i] + c3 * k3[i] + c4 * k4[i] + c5 * k5[i] + c6 * k6[i] + c7 * k7[i]);
+    }
+    __device__ __forceinline__ float err(float tol) const {
+        float e = 0.f;
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            float sc = tol + tol * fmaxf(fabsf(yh[i]), fabsf(y1h[i]));
+            float q = __fdividef(fabsf(e6[i]), sc);
+            if (q != q) bad = true;
+            else if (q > e) e = q;
+        }
+        return bad ? __int_as_float(0x7fc00000) : e;
+    }
+    static __device__ __forceinline__ float gval(const Params &p, int ev, const float h[6], const float l[6]) {
+        float x = h[0] + l[0], y = h[1] + l[1], z = h[2] + l[2];
+        switch (ev) {
+        case EV_LAT: return sqrtf(x * x + y * y) - (float)p.R2;
+        case EV_TOP: return z - (float)p.halfH;
+        case EV_BOT: return -z - (float)p.halfH;
+        default: return (float)p.R1 - sqrtf(x * x + y * y);
+        }
+    }
+    __device__ __forceinline__ float g_start(const Params &p, int ev) const { return gval(p, ev, yh, yl); }
+    __device__ __forceinline__ float g_end(const Params &p, int ev) const { return gval(p, ev, y1h, y1l); }
+    __device__ __forceinline__ void take_step() {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) { yh[i] = y1h[i]; yl[i] = y1l[i]; }
+        if (INTEG == I_DP45 && !need_k1) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) k1[i] = k7[i];
+        }
+    }
+    __device__ __forceinline__ void take_crossing() {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) { yh[i] = y1h[i]; yl[i] = y1l[i]; }
+        need_k1 = true;
+    }
+    __device__ __forceinline__ void mirror() {
+        double y[6];
+        state(y);
+        double r = hypot(y[0], y[1]), nm0 = y[0] / r, nm1 = y[1] / r;
+        double vn = y[3] * nm0 + y[4] * nm1;
+        y[3] -= 2.0 * vn * nm0;
+        y[4] -= 2.0 * vn * nm1;
+#pragma unroll
+        for (int i = 3; i < 6; ++i) {
+            yh[i] = (float)y[i];
+            yl[i] = (float)(y[i] - (double)yh[i]);
+        }
+        need_k1 = true;
+    }
+    __device__ __forceinline__ void state(double out[6]) const {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) out[i] = (double)yh[i] + (double)yl[i];
+    }
+    static __device__ __forceinline__ float rpow(float x, float e) { return __powf(x, e); }
+};
+
+// ------------------------------------------------------------------ the persistent loop
+enum { PH_STEP = 0, PH_CROSS = 1, PH_FINAL = 2, PH_IDLE = 3 };
+
+template <int VAR, int MODE, int INTEG, class S>
+__device__ __forceinline__ void integrate_loop(const Params &p, const Queue &q);
+
+}  // namespace ck

@@ -35,6 +35,7 @@ struct Params {
     double eo_t, ee_t, c_t[3];  // homogeneous test medium
     unsigned long long scene_seed;
     int integ;
+    int precision;  // 0 FP64, 1 mixed (wavefront schedule only)
     double h_or_tol;
     long long max_steps;
     // camera

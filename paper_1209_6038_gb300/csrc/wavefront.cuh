@@ -9,6 +9,7 @@
 //                      ONE uniform step evaluation (DP5(4): six right-hand sides; RK4: four) for every
 //                      lane; the surface-crossing search is a lane state that reuses that same step
 //                      slot with a trial step size, so root finding never serialises a warp.
+//                      FP64 or mixed arithmetic (integrator.cuh).
 //   C  k_wf_exit       one thread per queued ray: exit refraction, Eq. 12 factor of the exit face,
 //                      room lookup.
 //   D  k_wf_resolve    per pixel: mean over its samples in sample order.
@@ -18,6 +19,9 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "integrator.cuh"
 #include "internal.h"
 #include "trace.cuh"
 
@@ -72,32 +76,21 @@ __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned lo
     q.id[slot] = (int)idx;
 }
 
-// One uniform step evaluation: the integrator's update of size s from y (and, for DP5(4), the
-// embedded error estimate and the first stage of the next step).
-template <int VAR, int MODE, int INTEG>
-__device__ __forceinline__ void step_eval(const Params &p, const double y[6], double k1[6], bool need_k1, double s,
-                                          double y1[6], double e6[6], double k7[6]) {
-    if (INTEG == I_RK4) {
-        rk4_step<VAR, MODE>(p, y, s, y1);
-    } else {
-        if (need_k1) rhs<VAR, MODE>(p, y, k1);
-        dp45_step<VAR, MODE>(p, y, k1, s, y1, e6, k7);
-    }
-}
-
-enum { PH_STEP = 0, PH_CROSS = 1, PH_FINAL = 2, PH_IDLE = 3 };
-
-template <int VAR, int MODE, int INTEG>
+template <int VAR, int MODE, int INTEG, int PREC>
 __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
+    typedef typename std::conditional<PREC == 0, Stepper64<VAR, MODE, INTEG>, StepperMixed<VAR, MODE, INTEG>>::type S;
+    typedef typename S::real R;
+    S st;
     const unsigned int n = q.count[0];
     const int nev = p.R1 > 0.0 ? 4 : 3;
-    const double tol = p.h_or_tol, h0 = INTEG == I_RK4 ? p.h_or_tol : 1e-3;
+    const R tol = (R)p.h_or_tol, h0 = INTEG == I_RK4 ? (R)p.h_or_tol : (R)1e-3;
+    const R conv = sizeof(R) == 8 ? (R)4.0e-16 : (R)2.4e-7;  // bracket resolution of the crossing search
     // lane state
-    double y[6], k1[6], h = h0, t = 0.0;
+    R h = h0, t = 0;
     int steps = 0, phase = PH_IDLE, slot = -1;
-    bool metal = false, need_k1 = true;
+    bool metal = false;
     // crossing state
-    double hs = 0.0, fac = 1.0, lo = 0.0, hi = 0.0, glo = 0.0, ghi = 0.0, sbest = 0.0, g1[4];
+    R hs = 0, fac = 1, lo = 0, hi = 0, glo = 0, ghi = 0, sbest = 0, g1[4];
     int ev = 0, evbest = -1, side = 0, it = 0;
     unsigned int pending = 0;
 
@@ -107,69 +100,53 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
             unsigned int k = atomicAdd(q.count + 1, 1u);
             if (k < n) {
                 slot = (int)k;
-                y[0] = q.x[k]; y[1] = q.y[k]; y[2] = q.z[k];
-                y[3] = q.vx[k]; y[4] = q.vy[k]; y[5] = q.vz[k];
-                h = h0; t = 0.0; steps = 0; metal = false; need_k1 = true; phase = PH_STEP;
+                st.load(q.x, q.y, q.z, q.vx, q.vy, q.vz, (int)k);
+                h = h0; t = 0; steps = 0; metal = false; phase = PH_STEP;
             }
         }
         if (phase == PH_IDLE) break;  // queue drained for this lane
         int status = -1;
-        if (phase == PH_STEP && (steps >= p.max_steps || (INTEG == I_DP45 && h < 1e-14))) status = CLOAK_RAY_STEP_LIMIT;
+        if (phase == PH_STEP && (steps >= p.max_steps || (INTEG == I_DP45 && h < (R)1e-14))) status = CLOAK_RAY_STEP_LIMIT;
         if (status < 0) {
-            double s = phase == PH_STEP ? h : (phase == PH_CROSS ? 0.0 : sbest);
+            R s = phase == PH_STEP ? h : sbest;
             if (phase == PH_CROSS) {
                 // next trial point: bisection prefix, then Illinois regula falsi (see crossing())
-                if (it < BISECT_PREFIX) s = 0.5 * (lo + hi);
+                if (it < BISECT_PREFIX) s = (R)0.5 * (lo + hi);
                 else if (it - BISECT_PREFIX < 60 && ghi > glo) s = (lo * ghi - hi * glo) / (ghi - glo);
-                else s = 0.5 * (lo + hi);
-                if (!(s > lo && s < hi)) s = 0.5 * (lo + hi);
+                else s = (R)0.5 * (lo + hi);
+                if (!(s > lo && s < hi)) s = (R)0.5 * (lo + hi);
             }
-            double y1[6], e6[6], k7[6];
-            step_eval<VAR, MODE, INTEG>(p, y, k1, need_k1, s, y1, e6, k7);
-            need_k1 = false;
+            st.eval(p, s);
             if (phase == PH_STEP) {
                 ++steps;
-                fac = 1.0;
+                fac = 1;
                 bool accept = true;
                 if (INTEG == I_DP45) {
-                    double err = 0.0;
-                    bool bad = false;
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        double sc = tol + tol * fmax(fabs(y[i]), fabs(y1[i]));
-                        double qq = fabs(e6[i]) / sc;
-                        if (qq != qq) bad = true;
-                        else if (qq > err) err = qq;
-                    }
-                    if (bad || !(err <= 1.0)) {
-                        h *= (bad || isinf(err)) ? 0.2 : fmax(0.2, 0.9 * pow(err, -0.2));
+                    R err = st.err(tol);
+                    if (!(err <= (R)1)) {
+                        h *= (isnan(err) || isinf(err)) ? (R)0.2 : fmax((R)0.2, (R)0.9 * S::rpow(err, (R)-0.2));
                         accept = false;
                     } else {
-                        fac = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
+                        fac = err == (R)0 ? (R)5 : fmin((R)5, fmax((R)0.2, (R)0.9 * S::rpow(err, (R)-0.2)));
                     }
                 }
                 if (accept) {
                     pending = 0;
                     for (int e = 0; e < nev; ++e) {
-                        g1[e] = event_g(p, e, y1);
-                        if (g1[e] > 0.0) pending |= 1u << e;
+                        g1[e] = st.g_end(p, e);
+                        if (g1[e] > (R)0) pending |= 1u << e;
                     }
                     if (!pending) {
-#pragma unroll
-                        for (int i = 0; i < 6; ++i) y[i] = y1[i];
+                        st.take_step();
                         t += h;
                         h *= fac;
-                        if (INTEG == I_DP45) {
-#pragma unroll
-                            for (int i = 0; i < 6; ++i) k1[i] = k7[i];
-                        }
                     } else {
                         hs = h;
-                        sbest = 1e300;
+                        sbest = (R)1e30;
                         evbest = -1;
                         ev = __ffs(pending) - 1;
-                        lo = 0.0; hi = hs; glo = event_g(p, ev, y); ghi = g1[ev];
-                        if (!(glo <= 0.0)) glo = 0.0;
+                        lo = 0; hi = hs; glo = st.g_start(p, ev); ghi = g1[ev];
+                        if (!(glo <= (R)0)) glo = 0;
                         side = 0; it = 0;
                         phase = PH_CROSS;
                     }
@@ -179,48 +156,43 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                 if (!(s > lo && s < hi)) {
                     done = true;
                 } else {
-                    double gs = event_g(p, ev, y1);
+                    R gs = st.g_end(p, ev);
                     if (it < BISECT_PREFIX) {
-                        if (gs > 0.0) { hi = s; ghi = gs; } else { lo = s; glo = gs; }
-                    } else if (gs > 0.0) {
+                        if (gs > (R)0) { hi = s; ghi = gs; } else { lo = s; glo = gs; }
+                    } else if (gs > (R)0) {
                         hi = s; ghi = gs;
-                        if (side == 1) glo *= 0.5;
+                        if (side == 1) glo *= (R)0.5;
                         side = 1;
                     } else {
                         lo = s; glo = gs;
-                        if (side == -1) ghi *= 0.5;
+                        if (side == -1) ghi *= (R)0.5;
                         side = -1;
                     }
                     ++it;
-                    if (it >= BISECT_PREFIX && hi - lo <= 4.0e-16 * hi) done = true;
+                    if (it >= BISECT_PREFIX && hi - lo <= conv * hi) done = true;
                     if (it >= BISECT_PREFIX + 200) done = true;
                 }
                 if (done) {
-                    double se = ev == EV_METAL ? lo : hi;
+                    R se = ev == EV_METAL ? lo : hi;
                     if (se < sbest) { sbest = se; evbest = ev; }
                     pending &= ~(1u << ev);
                     if (pending) {
                         ev = __ffs(pending) - 1;
-                        lo = 0.0; hi = hs; glo = event_g(p, ev, y); ghi = g1[ev];
-                        if (!(glo <= 0.0)) glo = 0.0;
+                        lo = 0; hi = hs; glo = st.g_start(p, ev); ghi = g1[ev];
+                        if (!(glo <= (R)0)) glo = 0;
                         side = 0; it = 0;
                     } else {
                         phase = PH_FINAL;
                     }
                 }
-            } else {  // PH_FINAL: y1 is the state at the crossing
-#pragma unroll
-                for (int i = 0; i < 6; ++i) y[i] = y1[i];
+            } else {  // PH_FINAL: the evaluation landed on the crossing
+                st.take_crossing();
                 t += sbest;
                 h = hs * fac;
-                need_k1 = true;
                 phase = PH_STEP;
                 if (evbest == EV_METAL) {
                     if (VAR == V_RADIAL && MODE == M_ORD) {
-                        double r = hypot(y[0], y[1]), nm0 = y[0] / r, nm1 = y[1] / r;
-                        double vn = y[3] * nm0 + y[4] * nm1;
-                        y[3] -= 2.0 * vn * nm0;
-                        y[4] -= 2.0 * vn * nm1;
+                        st.mirror();
                         metal = true;
                     } else {
                         status = CLOAK_RAY_SINGULAR;
@@ -231,9 +203,11 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
             }
         }
         if (status >= 0) {  // ray finished: write back, lane becomes idle
+            double y[6];
+            st.state(y);
             q.x[slot] = y[0]; q.y[slot] = y[1]; q.z[slot] = y[2];
             q.vx[slot] = y[3]; q.vy[slot] = y[4]; q.vz[slot] = y[5];
-            q.t[slot] = t;
+            q.t[slot] = (double)t;
             q.status[slot] = status;
             q.steps[slot] = steps;
             q.face[slot] = evbest;
@@ -301,8 +275,8 @@ __global__ void k_wf_resolve(int npix, int spp, const float4 *samples, float4 *o
 
 namespace ck {
 
-template <int V, int M, int I>
-static cudaError_t wavefront_vmi(const Params &p, int spp, unsigned long long seed, const Queue &q, float4 *samples,
+template <int V, int M, int I, int PREC>
+static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long seed, const Queue &q, float4 *samples,
                                  cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev) {
     long long n = (long long)p.W * p.Hp * spp;
     const int bs = 128;
@@ -316,14 +290,14 @@ static cudaError_t wavefront_vmi(const Params &p, int spp, unsigned long long se
     int slot = pk / 32;
     if (blocks_per_sm[slot] == 0) {
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V, M, I>, pk, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V, M, I, PREC>, pk, 0);
         if (e != cudaSuccess) return e;
         blocks_per_sm[slot] = nb > 0 ? nb : 1;
     }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_wf_integrate<V, M, I><<<blocks_per_sm[slot] * sms, pk, 0, st>>>(p, q);
+    k_wf_integrate<V, M, I, PREC><<<blocks_per_sm[slot] * sms, pk, 0, st>>>(p, q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);
@@ -331,6 +305,13 @@ static cudaError_t wavefront_vmi(const Params &p, int spp, unsigned long long se
     e = cudaGetLastError();
     if (ev) cudaEventRecord(ev[3], st);
     return e;
+}
+
+template <int V, int M, int I>
+static cudaError_t wavefront_vmi(const Params &p, int spp, unsigned long long seed, const Queue &q, float4 *samples,
+                                 cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev) {
+    if (p.precision == 1) return wavefront_vmip<V, M, I, 1>(p, spp, seed, q, samples, recs, packet, st, ev);
+    return wavefront_vmip<V, M, I, 0>(p, spp, seed, q, samples, recs, packet, st, ev);
 }
 
 template <int V>

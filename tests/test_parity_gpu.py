@@ -171,10 +171,11 @@ def test_test_medium_interfaces(ck, mode):
 SCHEDULES = ("plain", "wavefront")
 
 
-def small_render(ck, variant, mode, integ, h_or_tol, W, H, spp, elev, seed=0, records=True, schedule="plain"):
+def small_render(ck, variant, mode, integ, h_or_tol, W, H, spp, elev, seed=0, records=True, schedule="plain",
+                 precision=0):
     import torch
     eye, tgt, up = inputs.camera_pose(elev)
-    c = ck.Cloak(variant).camera(eye, tgt, up, 60.0, W, H).integrator(integ, h_or_tol)
+    c = ck.Cloak(variant).camera(eye, tgt, up, 60.0, W, H).integrator(integ, h_or_tol, precision)
     c.schedule(ck.SCHED_WAVEFRONT if schedule == "wavefront" else ck.SCHED_PLAIN)
     img = c.render(mode, spp, seed)
     rec = c.render_records(mode, spp, seed) if records else None
@@ -301,13 +302,14 @@ def test_edge_cases(ck):
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_wavefront_matches_plain(ck, variant, mode):
-    """Both schedules run the same per-ray arithmetic: their records and images agree
-    (here at 320x180, 4 spp, DP5(4), elevation 20 deg, and RK4 at elevation 45 deg)."""
+    """Both schedules run the same per-ray arithmetic (up to the compiler's FMA contraction in
+    different inlining contexts): statuses and tiles agree exactly, exit directions within the
+    FP64 bar (here at 320x180, 4 spp, DP5(4), elevation 20 deg, and RK4 at elevation 45 deg)."""
     for integ, tol, elev in ((1, 1e-9, 20.0), (0, 1e-3, 45.0)):
         a_img, a_rec = small_render(ck, variant, mode, integ, tol, 320, 180, 4, elev, seed=5, schedule="plain")
         b_img, b_rec = small_render(ck, variant, mode, integ, tol, 320, 180, 4, elev, seed=5, schedule="wavefront")
         assert np.array_equal(a_rec["status"], b_rec["status"])
         assert np.array_equal(a_rec["tile_id"], b_rec["tile_id"])
-        assert angles(a_rec["exit_dir"], b_rec["exit_dir"]).max() < 1e-12
-        assert np.abs(a_rec["tof"] - b_rec["tof"]).max() < 1e-12
+        assert angles(a_rec["exit_dir"], b_rec["exit_dir"]).max() < TOL_DIR
+        assert np.abs(a_rec["tof"] - b_rec["tof"]).max() < TOL_ABS
         assert np.abs(a_img - b_img).max() < 1e-6
