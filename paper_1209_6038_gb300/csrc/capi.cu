@@ -62,6 +62,8 @@ static int make_params(const cloak *h, ck::Params &p) {
     p.K = kk * kk;
     p.invK = 1.0 / p.K;
     p.R1x2 = 2.0 * h->R1;
+    p.R1sq = h->R1 * h->R1;
+    p.R2sq = h->R2 * h->R2;
     p.eo_t = h->eo_t;
     p.ee_t = h->ee_t;
     double cl = std::sqrt(h->c_t[0] * h->c_t[0] + h->c_t[1] * h->c_t[1] + h->c_t[2] * h->c_t[2]);

@@ -4,8 +4,9 @@
 //   Stepper64     FP64 throughout (the arithmetic of the plain path, step for step).
 //   StepperMixed  right-hand sides of Eq. 2 / Eq. 8 and the stage combinations in FP32; the state
 //                 (x, v) accumulated as float-float (TwoSum, Knuth 1969), so rounding does not build
-//                 up over thousands of steps; whole steps in FP64 where r < R1 + 0.02 (f -> 0 at
-//                 R1 makes FP32 lose the relative precision of r - R1); step control in FP32.
+//                 up over thousands of steps, and stage positions kept as float-float so r - R1 is
+//                 formed without cancellation; whole steps in FP64 where r < R1 + 0.02 (where
+//                 f -> 0); step control in FP32.
 //
 // Each lane owns one queued ray and refills from the queue when it finishes.  Every loop iteration
 // runs ONE uniform step evaluation for all lanes; the surface-crossing search (bisection prefix,
@@ -40,19 +41,8 @@ struct Stepper64 {
             dp45_step<VAR, MODE>(p, y, k1, s, y1, e6, k7);
         }
     }
-    // DP5(4) error norm; NaN if any component is NaN
-    __device__ __forceinline__ double err(double tol) const {
-        double e = 0.0;
-        bool bad = false;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            double sc = tol + tol * fmax(fabs(y[i]), fabs(y1[i]));
-            double q = fabs(e6[i]) / sc;
-            if (q != q) bad = true;
-            else if (q > e) e = q;
-        }
-        return bad ? __longlong_as_double(0x7ff8000000000000ll) : e;
-    }
+    // DP5(4) step control (physics.cuh: dp_control); fac is the next-step factor
+    __device__ __forceinline__ bool control(double tol, double &fac) const { return dp_control(y, y1, e6, tol, fac); }
     __device__ __forceinline__ double g_start(const Params &p, int ev) const { return event_g(p, ev, y); }
     __device__ __forceinline__ double g_end(const Params &p, int ev) const { return event_g(p, ev, y1); }
     __device__ __forceinline__ void take_step() {
@@ -79,7 +69,6 @@ struct Stepper64 {
 #pragma unroll
         for (int i = 0; i < 6; ++i) out[i] = y[i];
     }
-    static __device__ __forceinline__ double rpow(double x, double e) { return pow(x, e); }
 };
 
 // ------------------------------------------------------------------ mixed stepper
@@ -97,21 +86,31 @@ __device__ __forceinline__ void ff_add(float hi, float lo, float d, float &oh, f
     ol = e - (oh - s);
 }
 
-// dv/dt of Eq. 8 / Eq. 2 in FP32 with the fast reciprocal square root and division
+// dv/dt of Eq. 8 / Eq. 2 in FP32 with the fast reciprocal square root and division.  The position
+// comes as float-float (xh + xl, yh + yl) so that u = r - R1 keeps its relative precision close to
+// the inner radius: r^2 is formed exactly (TwoProd / TwoSum) and u = (r^2 - R1^2) / (r + R1) with
+// R1^2 as float-float (r^2 - R1^2 is then free of cancellation error).
 template <int VAR, int MODE>
-__device__ __forceinline__ void accel_f32(float R1, float K, float invK, float x, float y, float vx, float vy, float vz,
-                                          float &ax, float &ay, float &az) {
+__device__ __forceinline__ void accel_f32(float R1, float R1sq_h, float R1sq_l, float K, float invK, float xh, float xl,
+                                          float yh, float yl, float vx, float vy, float vz, float &ax, float &ay,
+                                          float &az) {
     if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD)) {
         ax = 0.f; ay = 0.f; az = 0.f;
         return;
     }
-    float r2 = x * x + y * y;
+    float px = xh * xh, ex = fmaf(xh, xh, -px);
+    float py = yh * yh, ey = fmaf(yh, yh, -py);
+    float r2h, r2l;
+    two_sum(px, py, r2h, r2l);
+    r2l += ex + ey + 2.f * (xh * xl + yh * yl);
+    float r2 = r2h + r2l;
     float ir = rsqrtf(r2);
     float r = r2 * ir;
+    float x = xh + xl, y = yh + yl;
     float cx = x * ir, cy = y * ir;
     float vr = vx * cx + vy * cy;
     float vt = vy * cx - vx * cy;
-    float u = r - R1;
+    float u = __fdividef((r2h - R1sq_h) + (r2l - R1sq_l), r + R1);
     float g = __fdividef(2.f * R1 * ir, u);  // f'/f
     float ar, at, azz;
     if (MODE == M_EXT) {
@@ -138,10 +137,13 @@ __device__ __forceinline__ void accel_f32(float R1, float K, float invK, float x
     az = azz;
 }
 
+// t: stage point (float), tl: low parts of its x and y
 template <int VAR, int MODE>
-__device__ __forceinline__ void rhs_f32(const Params &p, const float t[6], float d[6]) {
+__device__ __forceinline__ void rhs_f32(const Params &p, const float t[6], const float tl[2], float d[6]) {
     d[0] = t[3]; d[1] = t[4]; d[2] = t[5];
-    accel_f32<VAR, MODE>((float)p.R1, (float)p.K, (float)p.invK, t[0], t[1], t[3], t[4], t[5], d[3], d[4], d[5]);
+    float R1sq_h = (float)p.R1sq, R1sq_l = (float)(p.R1sq - (double)R1sq_h);
+    accel_f32<VAR, MODE>((float)p.R1, R1sq_h, R1sq_l, (float)p.K, (float)p.invK, t[0], tl[0], t[1], tl[1], t[3], t[4],
+                         t[5], d[3], d[4], d[5]);
 }
 
 constexpr double MIXED_FP64_BAND = 0.02;  // FP64 steps for r < R1 + 0.02
@@ -169,6 +171,13 @@ struct StepperMixed {
         float lim = (float)(p.R1 + MIXED_FP64_BAND);
         return x * x + y * y < lim * lim;
     }
+    // stage point y + d: x, y as float-float (t, tl), the rest in FP32
+    __device__ __forceinline__ void stage(const float d[6], float t[6], float tl[2]) const {
+        ff_add(yh[0], yl[0], d[0], t[0], tl[0]);
+        ff_add(yh[1], yl[1], d[1], t[1], tl[1]);
+#pragma unroll
+        for (int i = 2; i < 6; ++i) t[i] = yh[i] + (yl[i] + d[i]);
+    }
     __device__ __forceinline__ void eval(const Params &p, float s) {
         if (island(p)) {  // FP64 step from the float-float state
             double y[6], yo[6], e[6], kk1[6], kk7[6];
@@ -189,29 +198,32 @@ struct StepperMixed {
             need_k1 = true;
             return;
         }
-        float t[6], k2[6], k3[6], k4[6], k5[6], k6[6];
+        float t[6], tl[2], d[6], k2[6], k3[6], k4[6], k5[6], k6[6];
         if (INTEG == I_RK4) {
             float acc[6], kk[6];
+            const float z6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            stage(z6, t, tl);
+            rhs_f32<VAR, MODE>(p, t, tl, kk);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) t[i] = yh[i] + yl[i];
-            rhs_f32<VAR, MODE>(p, t, kk);
+            for (int i = 0; i < 6; ++i) { acc[i] = kk[i]; d[i] = 0.5f * s * kk[i]; }
+            stage(d, t, tl);
+            rhs_f32<VAR, MODE>(p, t, tl, kk);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) { acc[i] = kk[i]; t[i] = yh[i] + fmaf(0.5f * s, kk[i], yl[i]); }
-            rhs_f32<VAR, MODE>(p, t, kk);
+            for (int i = 0; i < 6; ++i) { acc[i] = fmaf(2.f, kk[i], acc[i]); d[i] = 0.5f * s * kk[i]; }
+            stage(d, t, tl);
+            rhs_f32<VAR, MODE>(p, t, tl, kk);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) { acc[i] = fmaf(2.f, kk[i], acc[i]); t[i] = yh[i] + fmaf(0.5f * s, kk[i], yl[i]); }
-            rhs_f32<VAR, MODE>(p, t, kk);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) { acc[i] = fmaf(2.f, kk[i], acc[i]); t[i] = yh[i] + fmaf(s, kk[i], yl[i]); }
-            rhs_f32<VAR, MODE>(p, t, kk);
+            for (int i = 0; i < 6; ++i) { acc[i] = fmaf(2.f, kk[i], acc[i]); d[i] = s * kk[i]; }
+            stage(d, t, tl);
+            rhs_f32<VAR, MODE>(p, t, tl, kk);
 #pragma unroll
             for (int i = 0; i < 6; ++i) ff_add(yh[i], yl[i], s * (1.f / 6.f) * (acc[i] + kk[i]), y1h[i], y1l[i]);
             return;
         }
         if (need_k1) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) t[i] = yh[i] + yl[i];
-            rhs_f32<VAR, MODE>(p, t, k1);
+            const float z6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            stage(z6, t, tl);
+            rhs_f32<VAR, MODE>(p, t, tl, k1);
             need_k1 = false;
         }
         const float a21 = (float)DP::a21, a31 = (float)DP::a31, a32 = (float)DP::a32, a41 = (float)DP::a41,
@@ -222,44 +234,55 @@ struct StepperMixed {
                     c1 = (float)DP::e1, c3 = (float)DP::e3, c4 = (float)DP::e4, c5 = (float)DP::e5,
                     c6 = (float)DP::e6, c7 = (float)DP::e7;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) t[i] = yh[i] + fmaf(s, a21 * k1[i], yl[i]);
-        rhs_f32<VAR, MODE>(p, t, k2);
+        for (int i = 0; i < 6; ++i) d[i] = s * (a21 * k1[i]);
+        stage(d, t, tl);
+        rhs_f32<VAR, MODE>(p, t, tl, k2);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) t[i] = yh[i] + fmaf(s, a31 * k1[i] + a32 * k2[i], yl[i]);
-        rhs_f32<VAR, MODE>(p, t, k3);
+        for (int i = 0; i < 6; ++i) d[i] = s * (a31 * k1[i] + a32 * k2[i]);
+        stage(d, t, tl);
+        rhs_f32<VAR, MODE>(p, t, tl, k3);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) t[i] = yh[i] + fmaf(s, a41 * k1[i] + a42 * k2[i] + a43 * k3[i], yl[i]);
-        rhs_f32<VAR, MODE>(p, t, k4);
+        for (int i = 0; i < 6; ++i) d[i] = s * (a41 * k1[i] + a42 * k2[i] + a43 * k3[i]);
+        stage(d, t, tl);
+        rhs_f32<VAR, MODE>(p, t, tl, k4);
 #pragma unroll
-        for (int i = 0; i < 6; ++i)
-            t[i] = yh[i] + fmaf(s, a51 * k1[i] + a52 * k2[i] + a53 * k3[i] + a54 * k4[i], yl[i]);
-        rhs_f32<VAR, MODE>(p, t, k5);
+        for (int i = 0; i < 6; ++i) d[i] = s * (a51 * k1[i] + a52 * k2[i] + a53 * k3[i] + a54 * k4[i]);
+        stage(d, t, tl);
+        rhs_f32<VAR, MODE>(p, t, tl, k5);
 #pragma unroll
-        for (int i = 0; i < 6; ++i)
-            t[i] = yh[i] + fmaf(s, a61 * k1[i] + a62 * k2[i] + a63 * k3[i] + a64 * k4[i] + a65 * k5[i], yl[i]);
-        rhs_f32<VAR, MODE>(p, t, k6);
+        for (int i = 0; i < 6; ++i) d[i] = s * (a61 * k1[i] + a62 * k2[i] + a63 * k3[i] + a64 * k4[i] + a65 * k5[i]);
+        stage(d, t, tl);
+        rhs_f32<VAR, MODE>(p, t, tl, k6);
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            float d = s * (b1 * k1[i] + b3 * k3[i] + b4 * k4[i] + b5 * k5[i] + b6 * k6[i]);
-            ff_add(yh[i], yl[i], d, y1h[i], y1l[i]);
-            t[i] = y1h[i] + y1l[i];
+            float dd = s * (b1 * k1[i] + b3 * k3[i] + b4 * k4[i] + b5 * k5[i] + b6 * k6[i]);
+            ff_add(yh[i], yl[i], dd, y1h[i], y1l[i]);
+            t[i] = y1h[i];
         }
-        rhs_f32<VAR, MODE>(p, t, k7);
+        tl[0] = y1l[0];
+        tl[1] = y1l[1];
+#pragma unroll
+        for (int i = 2; i < 6; ++i) t[i] = y1h[i] + y1l[i];
+        rhs_f32<VAR, MODE>(p, t, tl, k7);
 #pragma unroll
         for (int i = 0; i < 6; ++i)
             e6[i] = s * (c1 * k1[i] + c3 * k3[i] + c4 * k4[i] + c5 * k5[i] + c6 * k6[i] + c7 * k7[i]);
     }
-    __device__ __forceinline__ float err(float tol) const {
-        float e = 0.f;
-        bool bad = false;
+    __device__ __forceinline__ bool control(float tol, float &fac) const {
+        bool acc = true, bad = false;
+        float fe = 0.f;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             float sc = tol + tol * fmaxf(fabsf(yh[i]), fabsf(y1h[i]));
-            float q = __fdividef(fabsf(e6[i]), sc);
-            if (q != q) bad = true;
-            else if (q > e) e = q;
+            float ae = fabsf(e6[i]);
+            if (ae != ae) bad = true;
+            if (!(ae <= sc)) acc = false;
+            fe = fmaxf(fe, __fdividef(ae, sc));
         }
-        return bad ? __int_as_float(0x7fc00000) : e;
+        if (bad) { fac = 0.2f; return false; }
+        fac = fe == 0.f ? 5.f : fminf(5.f, fmaxf(0.2f, 0.9f * __powf(fe, -0.2f)));
+        if (!(fe < 3.0e38f)) fac = 0.2f;
+        return acc;
     }
     static __device__ __forceinline__ float gval(const Params &p, int ev, const float h[6], const float l[6]) {
         float x = h[0] + l[0], y = h[1] + l[1], z = h[2] + l[2];
@@ -303,7 +326,6 @@ struct StepperMixed {
 #pragma unroll
         for (int i = 0; i < 6; ++i) out[i] = (double)yh[i] + (double)yl[i];
     }
-    static __device__ __forceinline__ float rpow(float x, float e) { return __powf(x, e); }
 };
 
 // ------------------------------------------------------------------ the persistent loop

@@ -31,7 +31,7 @@ enum { I_RK4 = 0, I_DP45 = 1 };
 
 struct Params {
     int variant;  // V_*
-    double R1, R2, H, halfH, K, invK, R1x2;
+    double R1, R2, H, halfH, K, invK, R1x2, R1sq, R2sq;
     double eo_t, ee_t, c_t[3];  // homogeneous test medium
     unsigned long long scene_seed;
     int integ;
@@ -92,7 +92,7 @@ __device__ __forceinline__ void accel(T R1, T K, T invK, T x, T y, T vx, T vy, T
         return;
     }
     T r2 = x * x + y * y;
-    T ir = T(1) / sqrt(r2);
+    T ir = rsqrt(r2);
     T r = r2 * ir;
     T cx = x * ir, cy = y * ir;
     T vr = vx * cx + vy * cy;
@@ -200,14 +200,38 @@ __device__ __forceinline__ void dp45_step(const Params &p, const double y[6], co
     }
 }
 
+// DP5(4) step control: accept iff |e_i| <= tol + tol max(|y_i|, |y1_i|) for every component
+// (decided in FP64); the step factor 0.9 err^(-1/5), clamped to [0.2, 5], is evaluated in FP32
+// (it only sets the next step size).  NaN -> reject with factor 0.2.
+__device__ __forceinline__ bool dp_control(const double y[6], const double y1[6], const double e6[6], double tol,
+                                           double &fac) {
+    bool acc = true, bad = false;
+    float fe = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double sc = tol + tol * fmax(fabs(y[i]), fabs(y1[i]));
+        double ae = fabs(e6[i]);
+        if (ae != ae) bad = true;
+        if (!(ae <= sc)) acc = false;
+        fe = fmaxf(fe, __fdividef((float)ae, (float)sc));
+    }
+    if (bad) { fac = 0.2; return false; }
+    float f = fe == 0.f ? 5.f : fminf(5.f, fmaxf(0.2f, 0.9f * __powf(fe, -0.2f)));
+    if (!(fe < 3.0e38f)) f = 0.2f;
+    fac = (double)f;
+    return acc;
+}
+
 // ------------------------------------------------------------------ surfaces
 enum { EV_LAT = 0, EV_TOP = 1, EV_BOT = 2, EV_METAL = 3 };
+// Event functions: positive once the surface has been crossed.  The radial surfaces use r^2 - R^2,
+// which has the same roots and signs as r - R and needs no square root.
 __device__ __forceinline__ double event_g(const Params &p, int ev, const double y[6]) {
     switch (ev) {
-    case EV_LAT: return hypot(y[0], y[1]) - p.R2;
+    case EV_LAT: return fma(y[0], y[0], y[1] * y[1]) - p.R2sq;
     case EV_TOP: return y[2] - p.halfH;
     case EV_BOT: return -y[2] - p.halfH;
-    default: return p.R1 - hypot(y[0], y[1]);
+    default: return p.R1sq - fma(y[0], y[0], y[1] * y[1]);
     }
 }
 
@@ -221,16 +245,20 @@ __device__ __forceinline__ void flow(const Params &p, const double y[6], const d
 
 // Root s* in (0, h] of g(flow_s(y)) for a surface crossed by the step (g(0) <= 0 < g(h)).
 // When a coarse step crosses the surface more than once, the root is the one that
-// bisection of [0, h] converges to: the first BISECT_PREFIX halvings are plain
-// bisection (same midpoints as a pure bisection, so the same root is selected), then
-// Illinois-modified regula falsi finishes inside the remaining bracket.
+// bisection of [0, h] converges to: the first halvings are plain bisection (same
+// midpoints as a pure bisection, so the same root is selected), then Illinois-modified
+// regula falsi finishes inside the remaining bracket.
 // Returns the end of the final bracket beyond the surface (exits) or before it (metal).
-constexpr int BISECT_PREFIX = 12;
+// Halvings before regula falsi: 12 for fixed-step RK4 (coarse steps can cross a surface more than
+// once), 4 for the error-controlled DP5(4) steps.  Bracket resolution: 1e-13 of the step (FP64).
+template <int INTEG>
+__device__ __forceinline__ constexpr int bisect_prefix() { return INTEG == I_RK4 ? 12 : 4; }
+constexpr double CROSS_REL_TOL = 1e-13;
 template <int VAR, int MODE, int INTEG>
 __device__ double crossing(const Params &p, const double y[6], const double k1[6], double h, double ghi, int ev) {
     double lo = 0.0, hi = h, glo = event_g(p, ev, y), t[6];
     if (!(glo <= 0.0)) glo = 0.0;
-    for (int it = 0; it < BISECT_PREFIX; ++it) {
+    for (int it = 0; it < bisect_prefix<INTEG>(); ++it) {
         double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
         flow<VAR, MODE, INTEG>(p, y, k1, mid, t);
@@ -240,7 +268,7 @@ __device__ double crossing(const Params &p, const double y[6], const double k1[6
     }
     int side = 0;
     for (int it = 0; it < 200; ++it) {
-        if (hi - lo <= 4.0e-16 * hi) break;
+        if (hi - lo <= CROSS_REL_TOL * hi) break;
         double s;
         if (it < 60 && ghi > glo) s = (lo * ghi - hi * glo) / (ghi - glo);
         else s = 0.5 * (lo + hi);

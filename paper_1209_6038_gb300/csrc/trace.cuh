@@ -120,20 +120,10 @@ __device__ void trace_ray(const Params &p, const double o[3], const double d[3],
             double e6[6];
             dp45_step<VAR, MODE>(p, y, k1, h, y1, e6, k7);
             ++steps;
-            double err = 0.0;
-            bool bad = false;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                double sc = tol + tol * fmax(fabs(y[i]), fabs(y1[i]));
-                double q = fabs(e6[i]) / sc;
-                if (q != q) bad = true;
-                else if (q > err) err = q;
-            }
-            if (bad || !(err <= 1.0)) {
-                h *= (bad || isinf(err)) ? 0.2 : fmax(0.2, 0.9 * pow(err, -0.2));
+            if (!dp_control(y, y1, e6, tol, fac)) {
+                h *= fmin(fac, 1.0);
                 continue;
             }
-            fac = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
         }
         int evh = -1;
         double sh = 1e300;

@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     const unsigned int n = q.count[0];
     const int nev = p.R1 > 0.0 ? 4 : 3;
     const R tol = (R)p.h_or_tol, h0 = INTEG == I_RK4 ? (R)p.h_or_tol : (R)1e-3;
-    const R conv = sizeof(R) == 8 ? (R)4.0e-16 : (R)2.4e-7;  // bracket resolution of the crossing search
+    const R conv = sizeof(R) == 8 ? (R)CROSS_REL_TOL : (R)2.4e-7;  // bracket resolution of the crossing search
+    constexpr int prefix = bisect_prefix<INTEG>();
     // lane state
     R h = h0, t = 0;
     int steps = 0, phase = PH_IDLE, slot = -1;
@@ -111,8 +112,8 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
             R s = phase == PH_STEP ? h : sbest;
             if (phase == PH_CROSS) {
                 // next trial point: bisection prefix, then Illinois regula falsi (see crossing())
-                if (it < BISECT_PREFIX) s = (R)0.5 * (lo + hi);
-                else if (it - BISECT_PREFIX < 60 && ghi > glo) s = (lo * ghi - hi * glo) / (ghi - glo);
+                if (it < prefix) s = (R)0.5 * (lo + hi);
+                else if (it - prefix < 60 && ghi > glo) s = (lo * ghi - hi * glo) / (ghi - glo);
                 else s = (R)0.5 * (lo + hi);
                 if (!(s > lo && s < hi)) s = (R)0.5 * (lo + hi);
             }
@@ -122,12 +123,10 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                 fac = 1;
                 bool accept = true;
                 if (INTEG == I_DP45) {
-                    R err = st.err(tol);
-                    if (!(err <= (R)1)) {
-                        h *= (isnan(err) || isinf(err)) ? (R)0.2 : fmax((R)0.2, (R)0.9 * S::rpow(err, (R)-0.2));
+                    if (!st.control(tol, fac)) {
+                        h *= fmin(fac, (R)1);
+                        fac = 1;
                         accept = false;
-                    } else {
-                        fac = err == (R)0 ? (R)5 : fmin((R)5, fmax((R)0.2, (R)0.9 * S::rpow(err, (R)-0.2)));
                     }
                 }
                 if (accept) {
@@ -157,7 +156,7 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                     done = true;
                 } else {
                     R gs = st.g_end(p, ev);
-                    if (it < BISECT_PREFIX) {
+                    if (it < prefix) {
                         if (gs > (R)0) { hi = s; ghi = gs; } else { lo = s; glo = gs; }
                     } else if (gs > (R)0) {
                         hi = s; ghi = gs;
@@ -169,8 +168,8 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                         side = -1;
                     }
                     ++it;
-                    if (it >= BISECT_PREFIX && hi - lo <= conv * hi) done = true;
-                    if (it >= BISECT_PREFIX + 200) done = true;
+                    if (it >= prefix && hi - lo <= conv * hi) done = true;
+                    if (it >= prefix + 200) done = true;
                 }
                 if (done) {
                     R se = ev == EV_METAL ? lo : hi;
