@@ -48,8 +48,11 @@ enum {
 /* arithmetic of the integrator */
 enum {
     CLOAK_FP64 = 0,  /* all of the path in FP64 */
-    CLOAK_MIXED = 1  /* RK stepping in FP32 with FP64 state accumulation; FP64 near r = R1 and for
-                        the interface and exit root solves */
+    CLOAK_MIXED = 1,   /* RK stepping in FP32 (right-hand sides, stage combinations, step control) with
+                          float-float state accumulation; whole steps in FP64 where r < R1 + 0.02; entry
+                          and exit interface solves in FP64 (wavefront schedule only) */
+    CLOAK_MIXED_FF = 2 /* as CLOAK_MIXED without the FP64 band: stage positions in float-float keep
+                          r - R1 accurate down to the inner radius */
 };
 /* kernel schedule */
 enum {

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libcloak.so")
 RADIAL, AZIMUTHAL, TEST_UNIAXIAL_CONST = 0, 1, 100
 POL_ORDINARY, POL_EXTRAORDINARY = 0, 1
 RK4, DP45 = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_FF = 0, 1, 2
 SCHED_PLAIN, SCHED_WAVEFRONT = 0, 1
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
 RAY_STATUS = {0: "MISSED", 1: "EXITED", 2: "HIT_METAL_EXITED", 3: "NO_TRANSMISSION", 4: "TIR",

@@ -70,7 +70,8 @@ static int make_params(const cloak *h, ck::Params &p) {
     for (int i = 0; i < 3; ++i) p.c_t[i] = h->c_t[i] / cl;
     p.scene_seed = h->scene_seed;
     p.integ = h->integ == CLOAK_RK4 ? ck::I_RK4 : ck::I_DP45;
-    p.precision = h->precision == CLOAK_MIXED ? 1 : 0;
+    p.precision = h->precision == CLOAK_MIXED ? 1 : h->precision == CLOAK_MIXED_FF ? 2 : 0;
+    p.mixed_band = h->precision == CLOAK_MIXED ? 0.02 : 0.0;
     p.h_or_tol = h->h_or_tol;
     p.max_steps = h->max_steps;
     double w[3], u[3], v[3];
@@ -297,7 +298,8 @@ int cloak_set_integrator(cloak_t *h, int kind, double h_or_tol, int precision, l
     if (!h) return fail(CLOAK_EINVAL, "null handle");
     if (kind != CLOAK_RK4 && kind != CLOAK_DP45) return fail(CLOAK_EINVAL, "unknown integrator %d", kind);
     if (!(std::isfinite(h_or_tol) && h_or_tol > 0)) return fail(CLOAK_EINVAL, "step / tolerance must be > 0");
-    if (precision != CLOAK_FP64 && precision != CLOAK_MIXED) return fail(CLOAK_EINVAL, "unknown precision %d", precision);
+    if (precision != CLOAK_FP64 && precision != CLOAK_MIXED && precision != CLOAK_MIXED_FF)
+        return fail(CLOAK_EINVAL, "unknown precision %d", precision);
     if (max_steps < 1 || max_steps > 2000000000L) return fail(CLOAK_EINVAL, "max_steps out of range");
     h->integ = kind;
     h->h_or_tol = h_or_tol;
@@ -353,7 +355,7 @@ int cloak_render(cloak_t *h, int polarization, int spp, unsigned long long seed,
     if ((rc = use_device(h))) return rc;
     if (h->schedule == CLOAK_SCHED_WAVEFRONT)
         return run_wavefront(h, p, polarization, spp, seed, (float4 *)dev_rgba, nullptr, (cudaStream_t)cuda_stream);
-    if (h->precision == CLOAK_MIXED) return fail(CLOAK_EINVAL, "mixed precision needs the wavefront schedule");
+    if (h->precision != CLOAK_FP64) return fail(CLOAK_EINVAL, "mixed precision needs the wavefront schedule");
     if (h->timing) cudaEventRecord(h->ev[0], (cudaStream_t)cuda_stream);
     cudaError_t e = ck::launch_render_plain(p, polarization, spp, seed, (float4 *)dev_rgba, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "render launch");
@@ -381,7 +383,7 @@ int cloak_render_records(cloak_t *h, int polarization, int spp, unsigned long lo
     if (h->schedule == CLOAK_SCHED_WAVEFRONT)
         return run_wavefront(h, p, polarization, spp, seed, nullptr, (cloak_record *)dev_records,
                              (cudaStream_t)cuda_stream);
-    if (h->precision == CLOAK_MIXED) return fail(CLOAK_EINVAL, "mixed precision needs the wavefront schedule");
+    if (h->precision != CLOAK_FP64) return fail(CLOAK_EINVAL, "mixed precision needs the wavefront schedule");
     if (h->timing) cudaEventRecord(h->ev[0], (cudaStream_t)cuda_stream);
     cudaError_t e = ck::launch_records_plain(p, polarization, spp, seed, (cloak_record *)dev_records,
                                              (cudaStream_t)cuda_stream);

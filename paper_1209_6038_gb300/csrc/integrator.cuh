@@ -146,7 +146,6 @@ __device__ __forceinline__ void rhs_f32(const Params &p, const float t[6], const
                          t[5], d[3], d[4], d[5]);
 }
 
-constexpr double MIXED_FP64_BAND = 0.02;  // FP64 steps for r < R1 + 0.02
 
 template <int VAR, int MODE, int INTEG>
 struct StepperMixed {
@@ -168,7 +167,8 @@ struct StepperMixed {
     __device__ __forceinline__ bool island(const Params &p) const {
         if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD)) return false;
         float x = yh[0] + yl[0], y = yh[1] + yl[1];
-        float lim = (float)(p.R1 + MIXED_FP64_BAND);
+        if (!(p.mixed_band > 0.0)) return false;
+        float lim = (float)(p.R1 + p.mixed_band);
         return x * x + y * y < lim * lim;
     }
     // stage point y + d: x, y as float-float (t, tl), the rest in FP32

@@ -35,7 +35,8 @@ struct Params {
     double eo_t, ee_t, c_t[3];  // homogeneous test medium
     unsigned long long scene_seed;
     int integ;
-    int precision;  // 0 FP64, 1 mixed (wavefront schedule only)
+    int precision;  // 0 FP64, 1 mixed, 2 mixed without the FP64 band (wavefront schedule only)
+    double mixed_band;  // FP64 steps where r < R1 + mixed_band (mixed precision)
     double h_or_tol;
     long long max_steps;
     // camera

@@ -309,7 +309,7 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
 template <int V, int M, int I>
 static cudaError_t wavefront_vmi(const Params &p, int spp, unsigned long long seed, const Queue &q, float4 *samples,
                                  cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev) {
-    if (p.precision == 1) return wavefront_vmip<V, M, I, 1>(p, spp, seed, q, samples, recs, packet, st, ev);
+    if (p.precision != 0) return wavefront_vmip<V, M, I, 1>(p, spp, seed, q, samples, recs, packet, st, ev);
     return wavefront_vmip<V, M, I, 0>(p, spp, seed, q, samples, recs, packet, st, ev);
 }
 
