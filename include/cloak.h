@@ -142,6 +142,22 @@ int cloak_render_records(cloak_t *h, int polarization, int spp, unsigned long lo
 int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long n, void *dev_records,
                      void *cuda_stream);
 
+/* Allocation-free render.  The paper has no counterpart: this is a service for callers that may not
+ * allocate device memory -- processes whose device memory is owned entirely by another allocator
+ * (a framework's caching pool), latency-critical render loops that cannot afford the device-wide
+ * synchronisation of cudaMalloc / cudaFree, or programs that must not grow their footprint after
+ * start-up.  It renders exactly like cloak_render on the wavefront schedule (the handle's camera,
+ * integrator and precision), but its queue and per-sample buffer live in one fixed device array
+ * inside the library (96 MiB + 256 B, held on every GPU that loads the library until the process
+ * exits) instead of handle scratch, and it calls no cudaMalloc, cudaFree or allocating routine.
+ * Limit: width*height*spp <= 1048576 samples, else CLOAK_EINVAL before any launch.  The caller still
+ * passes the output (dev_rgba, float4[width*height], bytes >= 16*width*height).  The first call on a
+ * device resolves the array's device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array, which keeps the last call's contents: calls whose GPU
+ * work overlaps (other streams, other threads, other handles) race on it and must be serialised. */
+int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsigned long long seed, void *dev_rgba,
+                         size_t bytes, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,8 @@ SIGNATURES = {
     "cloak_render_records": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
     "cloak_trace_rays": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
+    "cloak_render_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
+                                       C.c_void_p]),
 }
 
 _lib = None
@@ -153,6 +155,12 @@ def cloak_trace_rays(h, polarization, rays, n, records, stream=None):
         raise CloakError(EINVAL, "buffer too small")
     return _check(load().cloak_trace_rays(h, polarization, C.c_void_p(rays.data_ptr()), n,
                                           C.c_void_p(records.data_ptr()), _stream_ptr(stream)))
+
+
+def cloak_render_noalloc(h, polarization, spp, seed, rgba, stream=None):
+    """Allocation-free render (fixed library-owned device array; at most 1048576 samples per call)."""
+    return _check(load().cloak_render_noalloc(h, polarization, spp, seed, C.c_void_p(rgba.data_ptr()),
+                                              rgba.numel() * rgba.element_size(), _stream_ptr(stream)))
 
 
 # ------------------------------------------------------------------ convenience

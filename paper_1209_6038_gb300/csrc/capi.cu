@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -415,3 +416,75 @@ int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free render (cloak_render_noalloc).  The wavefront queue and per-sample buffer live in
+// a fixed file-scope device array instead of handle scratch, for callers that may not allocate
+// device memory.  The array is part of this module: every GPU that loads the library holds it until
+// the process exits.  Host code must not use the array's name as a device address; its address is
+// resolved once per device with cudaGetSymbolAddress and passed to the kernels.
+// ---------------------------------------------------------------------------------------------
+static constexpr long long NOALLOC_MAX_SAMPLES = 1LL << 20;  // width * height * spp
+static constexpr size_t NOALLOC_SLOT_BYTES = 8 * sizeof(double) + 4 * sizeof(int) + sizeof(float4);
+static constexpr size_t NOALLOC_BYTES = 256 + (size_t)NOALLOC_MAX_SAMPLES * NOALLOC_SLOT_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+static constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+// Device address of the array on the current device (resolved on the first call per device).
+static int noalloc_scratch_ptr(int dev, void **out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(CLOAK_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return CLOAK_OK;
+}
+
+extern "C" int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsigned long long seed, void *dev_rgba,
+                                    size_t bytes, void *cuda_stream) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (polarization != CLOAK_POL_ORDINARY && polarization != CLOAK_POL_EXTRAORDINARY)
+        return fail(CLOAK_EINVAL, "unknown polarization %d", polarization);
+    if (spp < 1 || spp > 65536) return fail(CLOAK_EINVAL, "spp must be in [1, 65536]");
+    if (!dev_rgba) return fail(CLOAK_EINVAL, "null output buffer");
+    size_t need = (size_t)h->W * h->Hp * 16;
+    if (bytes < need) return fail(CLOAK_EINVAL, "output buffer holds %zu bytes, needs %zu", bytes, need);
+    long long cap = (long long)h->W * h->Hp * spp;
+    if (cap > NOALLOC_MAX_SAMPLES)
+        return fail(CLOAK_EINVAL, "width*height*spp = %lld exceeds the no-alloc limit of %lld samples", cap,
+                    NOALLOC_MAX_SAMPLES);
+    ck::Params p;
+    int rc = make_params(h, p);
+    if (rc) return rc;
+    if ((rc = use_device(h))) return rc;
+    void *base = nullptr;
+    if ((rc = noalloc_scratch_ptr(h->device, &base))) return rc;
+    // same layout as the handle scratch of the wavefront schedule
+    char *b = (char *)base;
+    ck::Queue q;
+    q.count = (unsigned int *)b;
+    b += 256;
+    double **dp[8] = {&q.x, &q.y, &q.z, &q.vx, &q.vy, &q.vz, &q.w_out, &q.t};
+    for (int i = 0; i < 8; ++i) { *dp[i] = (double *)b; b += (size_t)cap * sizeof(double); }
+    float4 *samples = (float4 *)b;
+    b += (size_t)cap * sizeof(float4);
+    int **ip[4] = {&q.id, &q.status, &q.steps, &q.face};
+    for (int i = 0; i < 4; ++i) { *ip[i] = (int *)b; b += (size_t)cap * sizeof(int); }
+    q.cap = cap;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the queue counters must start at zero; everything else is written before it is read
+    cudaError_t e = cudaMemsetAsync(q.count, 0, 256, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    e = ck::launch_wavefront(p, polarization, spp, seed, q, samples, nullptr, h->packet, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "wavefront launch");
+    e = ck::launch_resolve(p.W * p.Hp, spp, samples, (float4 *)dev_rgba, st);
+    if (e != cudaSuccess) return cuda_fail(e, "resolve launch");
+    return CLOAK_OK;
+}
