@@ -796,6 +796,21 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
             }
             fac = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
         }
+        /* Reading: a DP5(4) step whose end points both lie outside the metal cylinder while its
+           chord passes inside r < R1 is retried with the step shortened to the chord's closest
+           approach.  (Sect. 4: all radial ordinary rays reach the metal; they travel on straight
+           lines, along which the error estimate vanishes and the step grows without bound.) */
+        if (in->kind == ORC_DP45 && c->R1 > 0.0 && event_value(c, EV_METAL, y1) <= 0.0) {
+            double dx = y1[0] - y[0], dy = y1[1] - y[1], dd = dx * dx + dy * dy;
+            if (dd > 0.0) {
+                double sc = -(y[0] * dx + y[1] * dy) / dd;
+                double mx = y[0] + sc * dx, my = y[1] + sc * dy;
+                if (sc > 0.0 && sc < 1.0 && mx * mx + my * my < c->R1 * c->R1) {
+                    h *= sc;
+                    continue;
+                }
+            }
+        }
         /* surfaces crossed by this step; the earliest crossing wins */
         int ev_hit = -1;
         double s_hit = INFINITY;

@@ -615,3 +615,17 @@ def test_near_axis_azimuthal_extraordinary(L, kz, tol):
     assert O.STATUS[rec["status"]] == "EXITED"
     assert angle(rec["exit_dir"], dexp) < tol
     assert rec["tof"] == pytest.approx(2 * K * root / Kp, abs=tol)
+
+
+def test_all_radial_ordinary_rays_reach_metal_with_dp45():
+    """Sect. 4: every radial ordinary ray that enters laterally reaches the metal cylinder --
+    also with the adaptive integrator, whose steps grow without bound on these straight rays."""
+    rng = np.random.default_rng(9)
+    c = O.Cloak(O.RADIAL)
+    for _ in range(40):
+        L = rng.uniform(-0.97, 0.97)
+        kz = rng.uniform(-0.1, 0.1)
+        o, d, p = make_ray(L, kz, theta0=rng.uniform(0, 6.28), z0=0.0)
+        for tol in (1e-9, 1e-6):
+            rec, _ = trace(c, O.ORDINARY, o, d, O.DP45, tol)
+            assert O.STATUS[rec["status"]] == "HIT_METAL_EXITED", (L, kz, tol)
