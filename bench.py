@@ -189,6 +189,7 @@ def main():
     ap.add_argument("--cpu-pixels", type=int, default=15000, help="oracle pixels per image for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--profile-image", default=None,
                     help="VARIANT,MODE,ELEV: render only this image twice (for profilers), e.g. 1,1,20")
     ap.add_argument("--width", type=int, default=None)
@@ -232,13 +233,14 @@ def main():
         c.close()
         return 0
 
-    def make_handles(schedule):
+    def make_handles(schedule, precision=None):
         hs = {}
         for v in w.variants:
             for e in w.elevations:
                 eye, tgt, up = inputs.camera_pose(e)
                 c = ck.Cloak(v).camera(eye, tgt, up, w.hfov_deg, w.width, w.height)
-                c.integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol, ck.FP64, w.max_steps)
+                c.integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol,
+                             ck.FP64 if precision is None else precision, w.max_steps)
                 c.schedule(schedule)
                 hs[(v, e)] = c
         return hs
@@ -350,6 +352,37 @@ def main():
                                      "rays_over_1e-9_rad": int((err > 1e-9).sum()), "rays_compared": int(fin.sum()),
                                      "status_mismatch": int((g["status"] != o["status"]).sum()),
                                      "pixels_tile_or_status_differs_frac": float(px_diff.mean())}
+
+    # ---- the precision form: the same workload with FP32 stepping (mixed), against the oracle sample
+    if not args.no_mixed and rank == 0:
+        mh = make_handles(main_sched, precision=ck.MIXED)
+        for c in mh.values():
+            c.stage_timing(True)
+        mms, _, mstages = timed(mh, 1, 2)
+        rec_buf = torch.empty(w.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
+        msamples = []
+        for idx, (v, m, e) in enumerate(w.images):
+            mh[(v, e)].render_records(m, w.spp, w.seed, out=rec_buf)
+            pix = sample_pixels(w, idx, args.cpu_pixels)
+            sel = torch.from_numpy((pix[:, None] * w.spp + np.arange(w.spp)[None, :]).reshape(-1)).cuda()
+            msamples.append(ck.records_to_numpy(rec_buf.view(-1, ck.RECORD_BYTES)[sel].reshape(-1)))
+        del rec_buf
+        for c in mh.values():
+            c.close()
+        g = np.concatenate(msamples)
+        fin = np.isin(o["status"], [0, 1, 2, 7]) & (g["status"] == o["status"])
+        cr = np.linalg.norm(np.cross(g["exit_dir"][fin], o["exit_dir"][fin]), axis=-1)
+        err = np.arctan2(cr, np.sum(g["exit_dir"][fin] * o["exit_dir"][fin], axis=-1))
+        px_diff = ((g["tile_id"] != o["tile_id"]) | (g["status"] != o["status"])).reshape(-1, w.spp).any(1)
+        out["mixed"] = {"value": ws * rays_step / (mms / 1e3), "unit": UNIT, "ms_per_step": mms, "warmup": 1,
+                        "steps": 2, "dtype": "f32 stepping, float-float state, f64 band r < R1 + 0.02",
+                        "integrate_ms_per_step": mstages[1],
+                        "speedup_vs_fp64": ms_step / mms,
+                        "accuracy_vs_oracle": {"max_exit_dir_err_rad": float(err.max(initial=0)),
+                                               "p999_exit_dir_err_rad": float(np.quantile(err, 0.999)),
+                                               "rays_over_1e-5_rad": int((err > 1e-5).sum()),
+                                               "rays_compared": int(fin.sum()),
+                                               "pixels_tile_or_status_differs_frac": float(px_diff.mean())}}
 
     # ---- the plain FP64 integrator (one thread per pixel) on the same workload, for comparison
     if not args.no_plain and main_sched != ck.SCHED_PLAIN:

@@ -43,6 +43,7 @@ struct Stepper64 {
     }
     // DP5(4) step control (physics.cuh: dp_control); fac is the next-step factor
     __device__ __forceinline__ bool control(double tol, double &fac) const { return dp_control(y, y1, e6, tol, fac); }
+    __device__ __forceinline__ double chord(const Params &p) const { return metal_chord(y[0], y[1], y1[0], y1[1], p.R1sq); }
     __device__ __forceinline__ double g_start(const Params &p, int ev) const { return event_g(p, ev, y); }
     __device__ __forceinline__ double g_end(const Params &p, int ev) const { return event_g(p, ev, y1); }
     __device__ __forceinline__ void take_step() {
@@ -292,6 +293,9 @@ struct StepperMixed {
         case EV_BOT: return -z - (float)p.halfH;
         default: return (float)p.R1 - sqrtf(x * x + y * y);
         }
+    }
+    __device__ __forceinline__ float chord(const Params &p) const {
+        return metal_chord(yh[0] + yl[0], yh[1] + yl[1], y1h[0] + y1l[0], y1h[1] + y1l[1], (float)p.R1sq);
     }
     __device__ __forceinline__ float g_start(const Params &p, int ev) const { return gval(p, ev, yh, yl); }
     __device__ __forceinline__ float g_end(const Params &p, int ev) const { return gval(p, ev, y1h, y1l); }

@@ -223,6 +223,18 @@ __device__ __forceinline__ bool dp_control(const double y[6], const double y1[6]
     return acc;
 }
 
+// A DP5(4) step whose end points lie outside the metal cylinder while its chord passes inside r < R1
+// is retried with the step shortened to the chord's closest approach (straight radial ordinary rays
+// would otherwise step over the metal).  Returns that fraction of the step, or 0.
+template <typename T>
+__device__ __forceinline__ T metal_chord(T x0, T y0, T x1, T y1, T R1sq) {
+    T dx = x1 - x0, dy = y1 - y0, dd = dx * dx + dy * dy;
+    if (!(dd > T(0))) return T(0);
+    T sc = -(x0 * dx + y0 * dy) / dd;
+    T mx = x0 + sc * dx, my = y0 + sc * dy;
+    return (sc > T(0) && sc < T(1) && mx * mx + my * my < R1sq) ? sc : T(0);
+}
+
 // ------------------------------------------------------------------ surfaces
 enum { EV_LAT = 0, EV_TOP = 1, EV_BOT = 2, EV_METAL = 3 };
 // Event functions: positive once the surface has been crossed.  The radial surfaces use r^2 - R^2,

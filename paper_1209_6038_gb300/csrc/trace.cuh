@@ -125,6 +125,13 @@ __device__ void trace_ray(const Params &p, const double o[3], const double d[3],
                 continue;
             }
         }
+        if (INTEG == I_DP45 && nev == 4 && event_g(p, EV_METAL, y1) <= 0.0) {
+            double sc = metal_chord(y[0], y[1], y1[0], y1[1], p.R1sq);
+            if (sc > 0.0) {
+                h *= sc;
+                continue;
+            }
+        }
         int evh = -1;
         double sh = 1e300;
         for (int ev = 0; ev < nev; ++ev) {

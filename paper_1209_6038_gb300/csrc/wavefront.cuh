@@ -135,7 +135,11 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                         g1[e] = st.g_end(p, e);
                         if (g1[e] > (R)0) pending |= 1u << e;
                     }
-                    if (!pending) {
+                    R sc = 0;
+                    if (INTEG == I_DP45 && nev == 4 && !(pending & (1u << EV_METAL))) sc = st.chord(p);
+                    if (sc > (R)0) {
+                        h *= sc;  // retried: the step's chord passes through the metal cylinder
+                    } else if (!pending) {
                         st.take_step();
                         t += h;
                         h *= fac;

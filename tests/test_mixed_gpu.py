@@ -1,26 +1,29 @@
 """Mixed-precision path (FP32 right-hand sides and stage combinations, float-float state,
 FP64 steps within 0.02 of the inner radius, FP64 interface solves) against the FP64 oracle.
 
-Bar: exit direction within 1e-5 rad of the oracle (plus 10x the oracle's own spread under
-1e-13 input perturbations, as in the FP64 tests), and at least 99.9% of sampled pixels with
-the same room tile and status in every sample.
+Bar: exit direction within 1e-5 rad of the oracle, and at least 99.9% of sampled pixels with the
+same room tile and status in every sample.  As in the FP64 tests the bar widens where the problem
+itself amplifies rounding: the oracle's own change under 1e-13 input perturbations (its spread),
+scaled to FP32 rounding (2^-24 / 1e-13), times 10, is added per ray -- e.g. near-grazing exits
+through a cap, where the exit direction is 1/sqrt(1 - |k_t|^2) times more sensitive than k.
 """
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_1209_6038_gb300 import inputs
-from test_parity_gpu import angles, ck, oracle_render, small_render  # noqa: F401
+from test_parity_gpu import PERTURB, angles, ck, oracle_render, small_render  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 TOL_MIXED = 1e-5
+FP32_OVER_PROBE = 2.0 ** -24 / PERTURB
 
 
 def mixed_errors(rec, orec, sp):
     same = rec["status"] == orec["status"]
     fin = same & np.isin(orec["status"], [0, 1, 2, 7]) & ~sp["unstable"]
     err = angles(rec["exit_dir"][fin], orec["exit_dir"][fin])
-    lim = TOL_MIXED + 10 * sp["dir"][fin]
+    lim = TOL_MIXED + 10 * FP32_OVER_PROBE * sp["dir"][fin]
     return err, lim, same
 
 
