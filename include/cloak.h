@@ -148,7 +148,7 @@ int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long 
  * synchronisation of cudaMalloc / cudaFree, or programs that must not grow their footprint after
  * start-up.  It renders exactly like cloak_render on the wavefront schedule (the handle's camera,
  * integrator and precision), but its queue and per-sample buffer live in one fixed device array
- * inside the library (96 MiB + 256 B, held on every GPU that loads the library until the process
+ * inside the library (104 MiB + 1 KiB, held on every GPU that loads the library until the process
  * exits) instead of handle scratch, and it calls no cudaMalloc, cudaFree or allocating routine.
  * Limit: width*height*spp <= 1048576 samples, else CLOAK_EINVAL before any launch.  The caller still
  * passes the output (dev_rgba, float4[width*height], bytes >= 16*width*height).  The first call on a

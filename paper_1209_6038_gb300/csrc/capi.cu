@@ -104,7 +104,7 @@ static int make_params(const cloak *h, ck::Params &p) {
 
 // Carve the wavefront queue (SoA, cap slots) and the per-sample buffer out of the handle's scratch.
 static int wavefront_scratch(cloak *h, long long cap, ck::Queue &q, float4 **samples) {
-    size_t need = (size_t)cap * (8 * sizeof(double) + 4 * sizeof(int) + sizeof(float4)) + 256;
+    size_t need = ck::queue_bytes(cap);
     if (h->scratch_bytes < need) {
         if (h->scratch) {
             cudaError_t e = cudaFree(h->scratch);
@@ -120,16 +120,7 @@ static int wavefront_scratch(cloak *h, long long cap, ck::Queue &q, float4 **sam
         }
         h->scratch_bytes = need;
     }
-    char *b = (char *)h->scratch;
-    q.count = (unsigned int *)b;
-    b += 256;
-    double **dp[8] = {&q.x, &q.y, &q.z, &q.vx, &q.vy, &q.vz, &q.w_out, &q.t};
-    for (int i = 0; i < 8; ++i) { *dp[i] = (double *)b; b += (size_t)cap * sizeof(double); }
-    *samples = (float4 *)b;
-    b += (size_t)cap * sizeof(float4);
-    int **ip[4] = {&q.id, &q.status, &q.steps, &q.face};
-    for (int i = 0; i < 4; ++i) { *ip[i] = (int *)b; b += (size_t)cap * sizeof(int); }
-    q.cap = cap;
+    ck::carve_queue((char *)h->scratch, cap, q, samples);
     return CLOAK_OK;
 }
 
@@ -143,7 +134,7 @@ static int run_wavefront(cloak *h, const ck::Params &p, int pol, int spp, unsign
     if (rc) return rc;
     cudaEvent_t *ev = h->timing ? h->ev : nullptr;
     if (ev) cudaEventRecord(ev[0], st);
-    cudaError_t e = cudaMemsetAsync(q.count, 0, 256, st);
+    cudaError_t e = cudaMemsetAsync(q.count, 0, ck::QUEUE_HEADER_BYTES, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     e = ck::launch_wavefront(p, pol, spp, seed, q, recs ? nullptr : samples, recs, h->packet, st, ev);
     if (e != cudaSuccess) return cuda_fail(e, "wavefront launch");
@@ -425,8 +416,7 @@ int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long 
 // resolved once per device with cudaGetSymbolAddress and passed to the kernels.
 // ---------------------------------------------------------------------------------------------
 static constexpr long long NOALLOC_MAX_SAMPLES = 1LL << 20;  // width * height * spp
-static constexpr size_t NOALLOC_SLOT_BYTES = 8 * sizeof(double) + 4 * sizeof(int) + sizeof(float4);
-static constexpr size_t NOALLOC_BYTES = 256 + (size_t)NOALLOC_MAX_SAMPLES * NOALLOC_SLOT_BYTES;
+static constexpr size_t NOALLOC_BYTES = ck::QUEUE_HEADER_BYTES + (size_t)NOALLOC_MAX_SAMPLES * ck::QUEUE_SLOT_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 static constexpr int NOALLOC_MAX_DEVICES = 64;
@@ -467,20 +457,12 @@ extern "C" int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsig
     void *base = nullptr;
     if ((rc = noalloc_scratch_ptr(h->device, &base))) return rc;
     // same layout as the handle scratch of the wavefront schedule
-    char *b = (char *)base;
     ck::Queue q;
-    q.count = (unsigned int *)b;
-    b += 256;
-    double **dp[8] = {&q.x, &q.y, &q.z, &q.vx, &q.vy, &q.vz, &q.w_out, &q.t};
-    for (int i = 0; i < 8; ++i) { *dp[i] = (double *)b; b += (size_t)cap * sizeof(double); }
-    float4 *samples = (float4 *)b;
-    b += (size_t)cap * sizeof(float4);
-    int **ip[4] = {&q.id, &q.status, &q.steps, &q.face};
-    for (int i = 0; i < 4; ++i) { *ip[i] = (int *)b; b += (size_t)cap * sizeof(int); }
-    q.cap = cap;
+    float4 *samples = nullptr;
+    ck::carve_queue((char *)base, cap, q, &samples);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    // the queue counters must start at zero; everything else is written before it is read
-    cudaError_t e = cudaMemsetAsync(q.count, 0, 256, st);
+    // the queue header (counters, sort bins) must start at zero; everything else is written before it is read
+    cudaError_t e = cudaMemsetAsync(q.count, 0, ck::QUEUE_HEADER_BYTES, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     e = ck::launch_wavefront(p, polarization, spp, seed, q, samples, nullptr, h->packet, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "wavefront launch");

@@ -6,7 +6,9 @@
 //                 (x, v) accumulated as float-float (TwoSum, Knuth 1969), so rounding does not build
 //                 up over thousands of steps, and stage positions kept as float-float so r - R1 is
 //                 formed without cancellation; whole steps in FP64 where r < R1 + 0.02 (where
-//                 f -> 0); step control in FP32.
+//                 f -> 0); step control in FP32 on the part of the embedded error estimate that
+//                 exceeds its own FP32 rounding bound (the estimate is a difference of nearly equal
+//                 stage combinations, so without this the controller would chase rounding noise).
 //
 // Each lane owns one queued ray and refills from the queue when it finishes.  Every loop iteration
 // runs ONE uniform step evaluation for all lanes; the surface-crossing search (bisection prefix,
@@ -25,6 +27,7 @@ struct Stepper64 {
     typedef double real;
     double y[6], k1[6], y1[6], e6[6], k7[6];
     bool need_k1;
+    int vm;  // 2 * variant + mode when VAR = MODE = V_ANY
 
     __device__ __forceinline__ void load(const double *x, const double *yy, const double *z, const double *vx,
                                          const double *vy, const double *vz, int k) {
@@ -34,11 +37,11 @@ struct Stepper64 {
     }
     __device__ __forceinline__ void eval(const Params &p, double s) {
         if (INTEG == I_RK4) {
-            rk4_step<VAR, MODE>(p, y, s, y1);
+            rk4_step<VAR, MODE>(p, y, s, y1, vm);
         } else {
-            if (need_k1) rhs<VAR, MODE>(p, y, k1);
+            if (need_k1) rhs<VAR, MODE>(p, y, k1, vm);
             need_k1 = false;
-            dp45_step<VAR, MODE>(p, y, k1, s, y1, e6, k7);
+            dp45_step<VAR, MODE>(p, y, k1, s, y1, e6, k7, vm);
         }
     }
     // DP5(4) step control (physics.cuh: dp_control); fac is the next-step factor
@@ -92,9 +95,9 @@ __device__ __forceinline__ void ff_add(float hi, float lo, float d, float &oh, f
 // the inner radius: r^2 is formed exactly (TwoProd / TwoSum) and u = (r^2 - R1^2) / (r + R1) with
 // R1^2 as float-float (r^2 - R1^2 is then free of cancellation error).
 template <int VAR, int MODE>
-__device__ __forceinline__ void accel_f32(float R1, float R1sq_h, float R1sq_l, float K, float invK, float xh, float xl,
-                                          float yh, float yl, float vx, float vy, float vz, float &ax, float &ay,
-                                          float &az) {
+__device__ __forceinline__ void accel_f32_fixed(float R1, float R1sq_h, float R1sq_l, float K, float invK, float xh,
+                                                float xl, float yh, float yl, float vx, float vy, float vz, float &ax,
+                                                float &ay, float &az) {
     if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD)) {
         ax = 0.f; ay = 0.f; az = 0.f;
         return;
@@ -140,11 +143,27 @@ __device__ __forceinline__ void accel_f32(float R1, float R1sq_h, float R1sq_l, 
 
 // t: stage point (float), tl: low parts of its x and y
 template <int VAR, int MODE>
-__device__ __forceinline__ void rhs_f32(const Params &p, const float t[6], const float tl[2], float d[6]) {
+__device__ __forceinline__ void accel_f32(float R1, float R1sq_h, float R1sq_l, float K, float invK, float xh, float xl,
+                                          float yh, float yl, float vx, float vy, float vz, float &ax, float &ay,
+                                          float &az, int vm) {
+    if (VAR != V_ANY) {
+        accel_f32_fixed<VAR, MODE>(R1, R1sq_h, R1sq_l, K, invK, xh, xl, yh, yl, vx, vy, vz, ax, ay, az);
+        return;
+    }
+    switch (vm) {
+    case 0: accel_f32_fixed<V_RADIAL, M_ORD>(R1, R1sq_h, R1sq_l, K, invK, xh, xl, yh, yl, vx, vy, vz, ax, ay, az); break;
+    case 1: accel_f32_fixed<V_RADIAL, M_EXT>(R1, R1sq_h, R1sq_l, K, invK, xh, xl, yh, yl, vx, vy, vz, ax, ay, az); break;
+    case 2: accel_f32_fixed<V_AZIMUTHAL, M_ORD>(R1, R1sq_h, R1sq_l, K, invK, xh, xl, yh, yl, vx, vy, vz, ax, ay, az); break;
+    default: accel_f32_fixed<V_AZIMUTHAL, M_EXT>(R1, R1sq_h, R1sq_l, K, invK, xh, xl, yh, yl, vx, vy, vz, ax, ay, az); break;
+    }
+}
+
+template <int VAR, int MODE>
+__device__ __forceinline__ void rhs_f32(const Params &p, const float t[6], const float tl[2], float d[6], int vm) {
     d[0] = t[3]; d[1] = t[4]; d[2] = t[5];
     float R1sq_h = (float)p.R1sq, R1sq_l = (float)(p.R1sq - (double)R1sq_h);
     accel_f32<VAR, MODE>((float)p.R1, R1sq_h, R1sq_l, (float)p.K, (float)p.invK, t[0], tl[0], t[1], tl[1], t[3], t[4],
-                         t[5], d[3], d[4], d[5]);
+                         t[5], d[3], d[4], d[5], vm);
 }
 
 
@@ -153,7 +172,9 @@ struct StepperMixed {
     typedef float real;
     float yh[6], yl[6], k1[6];  // state (float-float) and first stage
     float y1h[6], y1l[6], e6[6], k7[6];
+    float n6[6];  // rounding bound of the FP32 error estimate (noise floor)
     bool need_k1;
+    int vm;  // 2 * variant + mode when VAR = MODE = V_ANY
 
     __device__ __forceinline__ void load(const double *x, const double *yy, const double *z, const double *vx,
                                          const double *vy, const double *vz, int k) {
@@ -166,7 +187,7 @@ struct StepperMixed {
         need_k1 = true;
     }
     __device__ __forceinline__ bool island(const Params &p) const {
-        if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD)) return false;
+        if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD) || (VAR == V_ANY && vm == 0)) return false;
         float x = yh[0] + yl[0], y = yh[1] + yl[1];
         if (!(p.mixed_band > 0.0)) return false;
         float lim = (float)(p.R1 + p.mixed_band);
@@ -185,16 +206,16 @@ struct StepperMixed {
 #pragma unroll
             for (int i = 0; i < 6; ++i) y[i] = (double)yh[i] + (double)yl[i];
             if (INTEG == I_RK4) {
-                rk4_step<VAR, MODE>(p, y, (double)s, yo);
+                rk4_step<VAR, MODE>(p, y, (double)s, yo, vm);
             } else {
-                rhs<VAR, MODE>(p, y, kk1);
-                dp45_step<VAR, MODE>(p, y, kk1, (double)s, yo, e, kk7);
+                rhs<VAR, MODE>(p, y, kk1, vm);
+                dp45_step<VAR, MODE>(p, y, kk1, (double)s, yo, e, kk7, vm);
             }
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 y1h[i] = (float)yo[i];
                 y1l[i] = (float)(yo[i] - (double)y1h[i]);
-                if (INTEG == I_DP45) { e6[i] = (float)e[i]; k7[i] = (float)kk7[i]; }
+                if (INTEG == I_DP45) { e6[i] = (float)e[i]; k7[i] = (float)kk7[i]; n6[i] = 0.f; }
             }
             need_k1 = true;
             return;
@@ -204,19 +225,19 @@ struct StepperMixed {
             float acc[6], kk[6];
             const float z6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             stage(z6, t, tl);
-            rhs_f32<VAR, MODE>(p, t, tl, kk);
+            rhs_f32<VAR, MODE>(p, t, tl, kk, vm);
 #pragma unroll
             for (int i = 0; i < 6; ++i) { acc[i] = kk[i]; d[i] = 0.5f * s * kk[i]; }
             stage(d, t, tl);
-            rhs_f32<VAR, MODE>(p, t, tl, kk);
+            rhs_f32<VAR, MODE>(p, t, tl, kk, vm);
 #pragma unroll
             for (int i = 0; i < 6; ++i) { acc[i] = fmaf(2.f, kk[i], acc[i]); d[i] = 0.5f * s * kk[i]; }
             stage(d, t, tl);
-            rhs_f32<VAR, MODE>(p, t, tl, kk);
+            rhs_f32<VAR, MODE>(p, t, tl, kk, vm);
 #pragma unroll
             for (int i = 0; i < 6; ++i) { acc[i] = fmaf(2.f, kk[i], acc[i]); d[i] = s * kk[i]; }
             stage(d, t, tl);
-            rhs_f32<VAR, MODE>(p, t, tl, kk);
+            rhs_f32<VAR, MODE>(p, t, tl, kk, vm);
 #pragma unroll
             for (int i = 0; i < 6; ++i) ff_add(yh[i], yl[i], s * (1.f / 6.f) * (acc[i] + kk[i]), y1h[i], y1l[i]);
             return;
@@ -224,7 +245,7 @@ struct StepperMixed {
         if (need_k1) {
             const float z6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             stage(z6, t, tl);
-            rhs_f32<VAR, MODE>(p, t, tl, k1);
+            rhs_f32<VAR, MODE>(p, t, tl, k1, vm);
             need_k1 = false;
         }
         const float a21 = (float)DP::a21, a31 = (float)DP::a31, a32 = (float)DP::a32, a41 = (float)DP::a41,
@@ -237,23 +258,23 @@ struct StepperMixed {
 #pragma unroll
         for (int i = 0; i < 6; ++i) d[i] = s * (a21 * k1[i]);
         stage(d, t, tl);
-        rhs_f32<VAR, MODE>(p, t, tl, k2);
+        rhs_f32<VAR, MODE>(p, t, tl, k2, vm);
 #pragma unroll
         for (int i = 0; i < 6; ++i) d[i] = s * (a31 * k1[i] + a32 * k2[i]);
         stage(d, t, tl);
-        rhs_f32<VAR, MODE>(p, t, tl, k3);
+        rhs_f32<VAR, MODE>(p, t, tl, k3, vm);
 #pragma unroll
         for (int i = 0; i < 6; ++i) d[i] = s * (a41 * k1[i] + a42 * k2[i] + a43 * k3[i]);
         stage(d, t, tl);
-        rhs_f32<VAR, MODE>(p, t, tl, k4);
+        rhs_f32<VAR, MODE>(p, t, tl, k4, vm);
 #pragma unroll
         for (int i = 0; i < 6; ++i) d[i] = s * (a51 * k1[i] + a52 * k2[i] + a53 * k3[i] + a54 * k4[i]);
         stage(d, t, tl);
-        rhs_f32<VAR, MODE>(p, t, tl, k5);
+        rhs_f32<VAR, MODE>(p, t, tl, k5, vm);
 #pragma unroll
         for (int i = 0; i < 6; ++i) d[i] = s * (a61 * k1[i] + a62 * k2[i] + a63 * k3[i] + a64 * k4[i] + a65 * k5[i]);
         stage(d, t, tl);
-        rhs_f32<VAR, MODE>(p, t, tl, k6);
+        rhs_f32<VAR, MODE>(p, t, tl, k6, vm);
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             float dd = s * (b1 * k1[i] + b3 * k3[i] + b4 * k4[i] + b5 * k5[i] + b6 * k6[i]);
@@ -264,10 +285,15 @@ struct StepperMixed {
         tl[1] = y1l[1];
 #pragma unroll
         for (int i = 2; i < 6; ++i) t[i] = y1h[i] + y1l[i];
-        rhs_f32<VAR, MODE>(p, t, tl, k7);
+        rhs_f32<VAR, MODE>(p, t, tl, k7, vm);
 #pragma unroll
-        for (int i = 0; i < 6; ++i)
+        for (int i = 0; i < 6; ++i) {
             e6[i] = s * (c1 * k1[i] + c3 * k3[i] + c4 * k4[i] + c5 * k5[i] + c6 * k6[i] + c7 * k7[i]);
+            // each k_j carries a relative rounding error of a few FP32 ulps; so does their combination
+            n6[i] = 8.f * 5.96e-8f * fabsf(s) *
+                    (fabsf(c1 * k1[i]) + fabsf(c3 * k3[i]) + fabsf(c4 * k4[i]) + fabsf(c5 * k5[i]) +
+                     fabsf(c6 * k6[i]) + fabsf(c7 * k7[i]));
+        }
     }
     __device__ __forceinline__ bool control(float tol, float &fac) const {
         bool acc = true, bad = false;
@@ -275,8 +301,8 @@ struct StepperMixed {
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             float sc = tol + tol * fmaxf(fabsf(yh[i]), fabsf(y1h[i]));
-            float ae = fabsf(e6[i]);
-            if (ae != ae) bad = true;
+            float ae = fmaxf(0.f, fabsf(e6[i]) - n6[i]);  // truncation error above the rounding noise
+            if (e6[i] != e6[i]) bad = true;
             if (!(ae <= sc)) acc = false;
             fe = fmaxf(fe, __fdividef(ae, sc));
         }

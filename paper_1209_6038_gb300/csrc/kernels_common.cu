@@ -17,6 +17,24 @@ __global__ void k_wf_resolve(int npix, int spp, const float4 *samples, float4 *o
     out[pix] = make_float4(a0 * inv, a1 * inv, a2 * inv, a3 * inv);
 }
 
+__global__ void k_wf_sort_scan(Queue q) {
+    if (threadIdx.x != 0) return;
+    unsigned int off = 0;
+    for (int b = NBINS - 1; b >= 0; --b) {  // descending cost: slowest rays first
+        unsigned int c = q.bins[b];
+        q.bins[NBINS + b] = off;
+        off += c;
+    }
+}
+
+__global__ void k_wf_sort_scatter(Queue q) {
+    const unsigned int n = q.count[0];
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        unsigned int pos = atomicAdd(q.bins + NBINS + q.key[k], 1u);
+        q.perm[pos] = (int)k;
+    }
+}
+
 cudaError_t launch_resolve(int npix, int spp, const float4 *samples, float4 *out, cudaStream_t st) {
     k_wf_resolve<<<(npix + 255) / 256, 256, 0, st>>>(npix, spp, samples, out);
     return cudaGetLastError();

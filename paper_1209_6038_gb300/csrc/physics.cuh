@@ -86,8 +86,12 @@ __device__ __forceinline__ void local_material(const Params &p, const double x[3
 
 // ------------------------------------------------------------------ equation of motion
 // dv/dt of Eq. 8 (extraordinary) or Eq. 2 (ordinary) at (x, v); cylindrical closed form.
+// VAR = MODE = -1 selects the medium at run time from vm = 2 * variant + mode (batched rendering).
+enum { V_ANY = -1 };
 template <int VAR, int MODE, typename T>
-__device__ __forceinline__ void accel(T R1, T K, T invK, T x, T y, T vx, T vy, T vz, T &ax, T &ay, T &az) {
+__device__ __forceinline__ void accel(T R1, T K, T invK, T x, T y, T vx, T vy, T vz, T &ax, T &ay, T &az, int vm = 0);
+template <int VAR, int MODE, typename T>
+__device__ __forceinline__ void accel_fixed(T R1, T K, T invK, T x, T y, T vx, T vy, T vz, T &ax, T &ay, T &az) {
     if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD)) {  // homogeneous: straight lines (Sect. 4)
         ax = T(0); ay = T(0); az = T(0);
         return;
@@ -124,27 +128,40 @@ __device__ __forceinline__ void accel(T R1, T K, T invK, T x, T y, T vx, T vy, T
     ay = ar * cy + at * cx;
     az = azz;
 }
+template <int VAR, int MODE, typename T>
+__device__ __forceinline__ void accel(T R1, T K, T invK, T x, T y, T vx, T vy, T vz, T &ax, T &ay, T &az, int vm) {
+    if (VAR != V_ANY) {
+        accel_fixed<VAR, MODE, T>(R1, K, invK, x, y, vx, vy, vz, ax, ay, az);
+        return;
+    }
+    switch (vm) {
+    case 0: accel_fixed<V_RADIAL, M_ORD, T>(R1, K, invK, x, y, vx, vy, vz, ax, ay, az); break;
+    case 1: accel_fixed<V_RADIAL, M_EXT, T>(R1, K, invK, x, y, vx, vy, vz, ax, ay, az); break;
+    case 2: accel_fixed<V_AZIMUTHAL, M_ORD, T>(R1, K, invK, x, y, vx, vy, vz, ax, ay, az); break;
+    default: accel_fixed<V_AZIMUTHAL, M_EXT, T>(R1, K, invK, x, y, vx, vy, vz, ax, ay, az); break;
+    }
+}
 
 template <int VAR, int MODE>
-__device__ __forceinline__ void rhs(const Params &p, const double y[6], double dy[6]) {
+__device__ __forceinline__ void rhs(const Params &p, const double y[6], double dy[6], int vm = 0) {
     dy[0] = y[3]; dy[1] = y[4]; dy[2] = y[5];
-    accel<VAR, MODE, double>(p.R1, p.K, p.invK, y[0], y[1], y[3], y[4], y[5], dy[3], dy[4], dy[5]);
+    accel<VAR, MODE, double>(p.R1, p.K, p.invK, y[0], y[1], y[3], y[4], y[5], dy[3], dy[4], dy[5], vm);
 }
 
 // ------------------------------------------------------------------ integrators
 template <int VAR, int MODE>
-__device__ __forceinline__ void rk4_step(const Params &p, const double y[6], double h, double out[6]) {
+__device__ __forceinline__ void rk4_step(const Params &p, const double y[6], double h, double out[6], int vm = 0) {
     double k[6], acc[6], t[6];
-    rhs<VAR, MODE>(p, y, k);
+    rhs<VAR, MODE>(p, y, k, vm);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = k[i]; t[i] = fma(0.5 * h, k[i], y[i]); }
-    rhs<VAR, MODE>(p, t, k);
+    rhs<VAR, MODE>(p, t, k, vm);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, k[i], acc[i]); t[i] = fma(0.5 * h, k[i], y[i]); }
-    rhs<VAR, MODE>(p, t, k);
+    rhs<VAR, MODE>(p, t, k, vm);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, k[i], acc[i]); t[i] = fma(h, k[i], y[i]); }
-    rhs<VAR, MODE>(p, t, k);
+    rhs<VAR, MODE>(p, t, k, vm);
 #pragma unroll
     for (int i = 0; i < 6; ++i) out[i] = fma(h * (1.0 / 6.0), acc[i] + k[i], y[i]);
 }
@@ -169,31 +186,31 @@ struct DP {
 // If err != nullptr also returns k7 = f(out) and the embedded error estimate.
 template <int VAR, int MODE>
 __device__ __forceinline__ void dp45_step(const Params &p, const double y[6], const double k1[6], double h,
-                                          double out[6], double *err, double *k7) {
+                                          double out[6], double *err, double *k7, int vm = 0) {
     double k2[6], k3[6], k4[6], k5[6], k6[6], t[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) t[i] = fma(h, DP::a21 * k1[i], y[i]);
-    rhs<VAR, MODE>(p, t, k2);
+    rhs<VAR, MODE>(p, t, k2, vm);
 #pragma unroll
     for (int i = 0; i < 6; ++i) t[i] = fma(h, DP::a31 * k1[i] + DP::a32 * k2[i], y[i]);
-    rhs<VAR, MODE>(p, t, k3);
+    rhs<VAR, MODE>(p, t, k3, vm);
 #pragma unroll
     for (int i = 0; i < 6; ++i) t[i] = fma(h, DP::a41 * k1[i] + DP::a42 * k2[i] + DP::a43 * k3[i], y[i]);
-    rhs<VAR, MODE>(p, t, k4);
+    rhs<VAR, MODE>(p, t, k4, vm);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, DP::a51 * k1[i] + DP::a52 * k2[i] + DP::a53 * k3[i] + DP::a54 * k4[i], y[i]);
-    rhs<VAR, MODE>(p, t, k5);
+    rhs<VAR, MODE>(p, t, k5, vm);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, DP::a61 * k1[i] + DP::a62 * k2[i] + DP::a63 * k3[i] + DP::a64 * k4[i] + DP::a65 * k5[i],
                    y[i]);
-    rhs<VAR, MODE>(p, t, k6);
+    rhs<VAR, MODE>(p, t, k6, vm);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         out[i] = fma(h, DP::b1 * k1[i] + DP::b3 * k3[i] + DP::b4 * k4[i] + DP::b5 * k5[i] + DP::b6 * k6[i], y[i]);
     if (err) {
-        rhs<VAR, MODE>(p, out, k7);
+        rhs<VAR, MODE>(p, out, k7, vm);
 #pragma unroll
         for (int i = 0; i < 6; ++i)
             err[i] = h * (DP::e1 * k1[i] + DP::e3 * k3[i] + DP::e4 * k4[i] + DP::e5 * k5[i] + DP::e6 * k6[i] +
@@ -251,9 +268,10 @@ __device__ __forceinline__ double event_g(const Params &p, int ev, const double 
 // One step of size s from y with the integrator's own update (RK4, or the DP
 // fifth-order solution given k1 = f(y)).
 template <int VAR, int MODE, int INTEG>
-__device__ __forceinline__ void flow(const Params &p, const double y[6], const double k1[6], double s, double out[6]) {
-    if (INTEG == I_RK4) rk4_step<VAR, MODE>(p, y, s, out);
-    else dp45_step<VAR, MODE>(p, y, k1, s, out, nullptr, nullptr);
+__device__ __forceinline__ void flow(const Params &p, const double y[6], const double k1[6], double s, double out[6],
+                                     int vm = 0) {
+    if (INTEG == I_RK4) rk4_step<VAR, MODE>(p, y, s, out, vm);
+    else dp45_step<VAR, MODE>(p, y, k1, s, out, nullptr, nullptr, vm);
 }
 
 // Root s* in (0, h] of g(flow_s(y)) for a surface crossed by the step (g(0) <= 0 < g(h)).

@@ -36,9 +36,40 @@ struct Queue {
     int *status;                       // CLOAK_RAY_* after B (EXITED / HIT_METAL_EXITED means: crossed a face)
     int *steps;
     int *face;                         // surface crossed at exit (EV_LAT / EV_TOP / EV_BOT)
+    int *key;                          // cost bucket of the ray (larger = more steps expected)
+    int *perm;                         // integration order: slots sorted by descending cost bucket
     unsigned int *count;               // [0] queued rays, [1] next ray for B, [2] error flag
+    unsigned int *bins;                // [NBINS] bucket sizes, then [NBINS] scatter cursors
     long long cap;
 };
+
+constexpr int NBINS = 64;
+constexpr size_t QUEUE_HEADER_BYTES = 1024;
+constexpr size_t QUEUE_SLOT_BYTES = 8 * sizeof(double) + 6 * sizeof(int) + sizeof(float4);
+inline size_t queue_bytes(long long cap) { return QUEUE_HEADER_BYTES + (size_t)cap * QUEUE_SLOT_BYTES; }
+
+// Lay the queue, its sort arrays and the per-sample buffer out in `base` (queue_bytes(cap) bytes,
+// 256-byte aligned).  The header (counters and bins) must be zeroed before each render.
+inline void carve_queue(char *base, long long cap, Queue &q, float4 **samples) {
+    q.count = (unsigned int *)base;
+    q.bins = (unsigned int *)(base + 64);
+    char *b = base + QUEUE_HEADER_BYTES;
+    double **dp[8] = {&q.x, &q.y, &q.z, &q.vx, &q.vy, &q.vz, &q.w_out, &q.t};
+    for (int i = 0; i < 8; ++i) { *dp[i] = (double *)b; b += (size_t)cap * sizeof(double); }
+    *samples = (float4 *)b;
+    b += (size_t)cap * sizeof(float4);
+    int **ip[6] = {&q.id, &q.status, &q.steps, &q.face, &q.key, &q.perm};
+    for (int i = 0; i < 6; ++i) { *ip[i] = (int *)b; b += (size_t)cap * sizeof(int); }
+    q.cap = cap;
+}
+
+// Cost bucket of an entering ray from its axial angular momentum L = (x cross k)_z: rays that pass
+// close to the inner radius (small |L|) are the slow ones (the ray speed grows like 1/L there).
+__device__ __forceinline__ int cost_bucket(const double x[3], const double k[3]) {
+    float L = fabsf((float)(x[0] * k[1] - x[1] * k[0]));
+    int b = (int)(-4.0f * __log2f(L + 1e-30f));
+    return min(max(b, 0), NBINS - 1);
+}
 
 __device__ __forceinline__ void store_sample(float4 *samples, cloak_record *recs, long long id,
                                              const cloak_record &rec, const float rgb[3]) {
@@ -69,18 +100,35 @@ __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned lo
     // Eq. 12 at the entry face along the physical direction: light leaves the cloak towards the camera
     double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
     double w_out = transmission_out(MODE, mat[0], mat[1], c, n_in, mk0);
-    unsigned int slot = atomicAdd(q.count, 1u);
+    // warp-aggregated append: one atomic per warp for the slot, one per distinct bucket
+    const unsigned int act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(q.count, (unsigned int)__popc(act));
+    base = __shfl_sync(act, base, leader);
+    unsigned int slot = base + __popc(act & ((1u << lane) - 1u));
     q.x[slot] = y[0]; q.y[slot] = y[1]; q.z[slot] = y[2];
     q.vx[slot] = y[3]; q.vy[slot] = y[4]; q.vz[slot] = y[5];
     q.w_out[slot] = w_out;
     q.id[slot] = (int)idx;
+    int b = cost_bucket(y, k0);
+    q.key[slot] = b;
+    unsigned int same = __match_any_sync(act, b);
+    if (lane == __ffs(same) - 1) atomicAdd(q.bins + b, (unsigned int)__popc(same));
 }
+
+// Longest-first order: a counting sort of the queue by descending cost bucket.  k_wf_sort_scan turns
+// the bucket sizes into scatter cursors, k_wf_sort_scatter writes the permutation.
+__global__ void k_wf_sort_scan(Queue q);
+__global__ void k_wf_sort_scatter(Queue q);
 
 template <int VAR, int MODE, int INTEG, int PREC>
 __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     typedef typename std::conditional<PREC == 0, Stepper64<VAR, MODE, INTEG>, StepperMixed<VAR, MODE, INTEG>>::type S;
     typedef typename S::real R;
     S st;
+    st.vm = 0;
     const unsigned int n = q.count[0];
     const int nev = p.R1 > 0.0 ? 4 : 3;
     const R tol = (R)p.h_or_tol, h0 = INTEG == I_RK4 ? (R)p.h_or_tol : (R)1e-3;
@@ -100,8 +148,8 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
         if (phase == PH_IDLE) {
             unsigned int k = atomicAdd(q.count + 1, 1u);
             if (k < n) {
-                slot = (int)k;
-                st.load(q.x, q.y, q.z, q.vx, q.vy, q.vz, (int)k);
+                slot = q.perm[k];
+                st.load(q.x, q.y, q.z, q.vx, q.vy, q.vz, slot);
                 h = h0; t = 0; steps = 0; metal = false; phase = PH_STEP;
             }
         }
@@ -194,7 +242,7 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                 h = hs * fac;
                 phase = PH_STEP;
                 if (evbest == EV_METAL) {
-                    if (VAR == V_RADIAL && MODE == M_ORD) {
+                    if ((VAR == V_RADIAL && MODE == M_ORD) || (VAR == V_ANY && st.vm == 0)) {
                         st.mirror();
                         metal = true;
                     } else {
@@ -286,6 +334,13 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
     k_wf_entry<V, M><<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(p, spp, seed, q, samples, recs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q);
+    k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
     // persistent integrator: exactly the resident grid
     static int blocks_per_sm[33] = {0};
@@ -297,9 +352,6 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
         if (e != cudaSuccess) return e;
         blocks_per_sm[slot] = nb > 0 ? nb : 1;
     }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     k_wf_integrate<V, M, I, PREC><<<blocks_per_sm[slot] * sms, pk, 0, st>>>(p, q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
