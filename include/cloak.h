@@ -142,13 +142,37 @@ int cloak_render_records(cloak_t *h, int polarization, int spp, unsigned long lo
 int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long n, void *dev_records,
                      void *cuda_stream);
 
+/* One view of a batched render: medium (CLOAK_RADIAL or CLOAK_AZIMUTHAL, with the handle's R1, R2 and
+ * height), traced polarization, pinhole camera (as cloak_camera_set) and its output, a caller-owned
+ * device buffer of float4[width*height]. */
+typedef struct cloak_view {
+    int variant;
+    int polarization;
+    double eye[3], target[3], up[3];
+    double hfov_deg;
+    int width, height;
+    void *dev_rgba;
+} cloak_view;
+
+/* Batched render (many views in one pass, Sect. 4 per ray): one camera/entry kernel over the samples
+ * of all views, one device queue of entering rays ordered by expected cost and medium, ONE persistent
+ * integration kernel for the rays of every view, one exit kernel and one resolve kernel writing every
+ * view's image.  The launch sequence is captured in a CUDA graph the first time a batch (views, spp,
+ * seed, integrator, precision, packet) is seen and replayed on later identical calls.  The handle's
+ * variant must be CLOAK_RADIAL or CLOAK_AZIMUTHAL; integrator, precision and packet come from the
+ * handle.  views: host array of nviews >= 1 entries (read during the call); total samples
+ * sum(width*height*spp) <= 2^31 - 1.  Scratch: about 104 bytes per sample, owned by the handle.
+ * Every view's output is written on cuda_stream. */
+int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
+                       void *cuda_stream);
+
 /* Allocation-free render.  The paper has no counterpart: this is a service for callers that may not
  * allocate device memory -- processes whose device memory is owned entirely by another allocator
  * (a framework's caching pool), latency-critical render loops that cannot afford the device-wide
  * synchronisation of cudaMalloc / cudaFree, or programs that must not grow their footprint after
  * start-up.  It renders exactly like cloak_render on the wavefront schedule (the handle's camera,
  * integrator and precision), but its queue and per-sample buffer live in one fixed device array
- * inside the library (104 MiB + 1 KiB, held on every GPU that loads the library until the process
+ * inside the library (104 MiB + 4 KiB, held on every GPU that loads the library until the process
  * exits) instead of handle scratch, and it calls no cudaMalloc, cudaFree or allocating routine.
  * Limit: width*height*spp <= 1048576 samples, else CLOAK_EINVAL before any launch.  The caller still
  * passes the output (dev_rgba, float4[width*height], bytes >= 16*width*height).  The first call on a

@@ -45,9 +45,17 @@ SIGNATURES = {
     "cloak_render_records": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
     "cloak_trace_rays": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
+    "cloak_render_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p]),
     "cloak_render_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
 }
+
+class View(C.Structure):
+    """cloak_view of include/cloak.h"""
+    _fields_ = [("variant", C.c_int), ("polarization", C.c_int), ("eye", C.c_double * 3), ("target", C.c_double * 3),
+                ("up", C.c_double * 3), ("hfov_deg", C.c_double), ("width", C.c_int), ("height", C.c_int),
+                ("dev_rgba", C.c_void_p)]
+
 
 _lib = None
 
@@ -155,6 +163,19 @@ def cloak_trace_rays(h, polarization, rays, n, records, stream=None):
         raise CloakError(EINVAL, "buffer too small")
     return _check(load().cloak_trace_rays(h, polarization, C.c_void_p(rays.data_ptr()), n,
                                           C.c_void_p(records.data_ptr()), _stream_ptr(stream)))
+
+
+def cloak_render_batch(h, views, spp, seed, stream=None):
+    """views: list of (variant, polarization, eye, target, up, hfov_deg, out) with out a float32 CUDA tensor
+    of shape (height, width, 4).  Renders all of them in one pass (one persistent integration kernel)."""
+    arr = (View * len(views))()
+    for a, (variant, pol, eye, target, up, hfov, out) in zip(arr, views):
+        a.variant, a.polarization = variant, pol
+        a.eye[:], a.target[:], a.up[:] = list(map(float, eye)), list(map(float, target)), list(map(float, up))
+        a.hfov_deg = hfov
+        a.height, a.width = int(out.shape[0]), int(out.shape[1])
+        a.dev_rgba = out.data_ptr()
+    return _check(load().cloak_render_batch(h, C.cast(arr, C.c_void_p), len(views), spp, seed, _stream_ptr(stream)))
 
 
 def cloak_render_noalloc(h, polarization, spp, seed, rgba, stream=None):

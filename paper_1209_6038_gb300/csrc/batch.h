@@ -1,0 +1,26 @@
+// batch.h -- device view table of a batched render (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "physics.cuh"
+
+namespace ck {
+
+struct Queue;
+
+struct ViewDev {
+    double eye[3], fw[3], rt[3], up[3], tx, ty;  // pinhole camera frame
+    long long ray_begin;                         // first global sample index of the view
+    long long pix_begin;                         // first global pixel index of the view
+    float4 *out;                                 // the view's image
+    int W, Hp, vm;                               // size; vm = 2 * variant + polarization
+    int pad;
+};
+
+// queue scratch and per-sample buffer as for the wavefront schedule; views: device copy of the table
+cudaError_t launch_batch(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
+                         long long total, long long total_pix, const Queue &q, float4 *samples, int packet,
+                         cudaStream_t st);
+
+}  // namespace ck

@@ -6,9 +6,11 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
+#include "batch.h"
 #include "internal.h"
 #include "wavefront.cuh"
 
@@ -33,6 +35,13 @@ struct cloak {
     int timed_calls;   // renders since timing was enabled
     int timed_sched;   // schedule of the last timed render
     cudaEvent_t ev[5];
+    // batched render: view table (pinned host staging + device copy) and the captured graph
+    void *batch_host, *batch_dev;
+    size_t batch_bytes;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t graph_exec;
+    cudaEvent_t graph_done;
+    unsigned long long graph_key;
 };
 
 static thread_local std::string g_err;
@@ -210,6 +219,12 @@ cloak_t *cloak_create(int variant, double R1, double R2, double height) {
     h->timing = 0;
     h->timed_calls = 0;
     h->timed_sched = 0;
+    h->batch_host = h->batch_dev = nullptr;
+    h->batch_bytes = 0;
+    h->cap_stream = nullptr;
+    h->graph_exec = nullptr;
+    h->graph_done = nullptr;
+    h->graph_key = 0;
     g_err.clear();
     return h;
 }
@@ -217,6 +232,12 @@ cloak_t *cloak_create(int variant, double R1, double R2, double height) {
 void cloak_destroy(cloak_t *h) {
     if (!h) return;
     cudaSetDevice(h->device);
+    if (h->graph_done) cudaEventSynchronize(h->graph_done);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph_done) cudaEventDestroy(h->graph_done);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->batch_host) cudaFreeHost(h->batch_host);
+    if (h->batch_dev) cudaFree(h->batch_dev);
     if (h->scratch) cudaFree(h->scratch);
     if (h->timing)
         for (int i = 0; i < 5; ++i) cudaEventDestroy(h->ev[i]);
@@ -407,6 +428,136 @@ int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Batched render
+// ---------------------------------------------------------------------------------------------
+static int view_frame(const cloak_view &v, ck::ViewDev &d) {
+    if (v.variant != CLOAK_RADIAL && v.variant != CLOAK_AZIMUTHAL) return fail(CLOAK_EINVAL, "view variant %d", v.variant);
+    if (v.polarization != CLOAK_POL_ORDINARY && v.polarization != CLOAK_POL_EXTRAORDINARY)
+        return fail(CLOAK_EINVAL, "view polarization %d", v.polarization);
+    if (!finite3(v.eye) || !finite3(v.target) || !finite3(v.up)) return fail(CLOAK_EINVAL, "view camera not finite");
+    if (!(v.hfov_deg > 0 && v.hfov_deg < 180)) return fail(CLOAK_EINVAL, "view hfov out of (0, 180)");
+    if (v.width < 1 || v.height < 1 || (long long)v.width * v.height > 2147483647LL)
+        return fail(CLOAK_EINVAL, "view size %dx%d out of range", v.width, v.height);
+    if (!v.dev_rgba) return fail(CLOAK_EINVAL, "view without output buffer");
+    double w[3], u[3], up[3];
+    for (int i = 0; i < 3; ++i) w[i] = v.target[i] - v.eye[i];
+    double l = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (!(l > 0)) return fail(CLOAK_EINVAL, "view eye and target coincide");
+    for (int i = 0; i < 3; ++i) w[i] /= l;
+    u[0] = w[1] * v.up[2] - w[2] * v.up[1];
+    u[1] = w[2] * v.up[0] - w[0] * v.up[2];
+    u[2] = w[0] * v.up[1] - w[1] * v.up[0];
+    l = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (!(l > 1e-300)) return fail(CLOAK_EINVAL, "view up vector parallel to the view direction");
+    for (int i = 0; i < 3; ++i) u[i] /= l;
+    up[0] = u[1] * w[2] - u[2] * w[1];
+    up[1] = u[2] * w[0] - u[0] * w[2];
+    up[2] = u[0] * w[1] - u[1] * w[0];
+    for (int i = 0; i < 3; ++i) { d.eye[i] = v.eye[i]; d.fw[i] = w[i]; d.rt[i] = u[i]; d.up[i] = up[i]; }
+    d.tx = std::tan(0.5 * v.hfov_deg * M_PI / 180.0);
+    d.ty = d.tx * (double)v.height / (double)v.width;
+    d.W = v.width;
+    d.Hp = v.height;
+    d.vm = 2 * v.variant + v.polarization;
+    d.pad = 0;
+    d.out = (float4 *)v.dev_rgba;
+    return CLOAK_OK;
+}
+
+static unsigned long long fnv1a(unsigned long long hsh, const void *data, size_t n) {
+    const unsigned char *b = (const unsigned char *)data;
+    for (size_t i = 0; i < n; ++i) { hsh ^= b[i]; hsh *= 1099511628211ull; }
+    return hsh;
+}
+
+extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
+                                  void *cuda_stream) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
+        return fail(CLOAK_ESTATE, "batched rendering needs a radial or azimuthal cloak handle");
+    if (!views || nviews < 1 || nviews > 65536) return fail(CLOAK_EINVAL, "need 1..65536 views");
+    if (spp < 1 || spp > 65536) return fail(CLOAK_EINVAL, "spp must be in [1, 65536]");
+    ck::Params p;
+    int rc = make_params(h, p);
+    if (rc) return rc;
+    std::vector<ck::ViewDev> table((size_t)nviews);
+    long long total = 0, total_pix = 0;
+    for (int i = 0; i < nviews; ++i) {
+        if ((rc = view_frame(views[i], table[i]))) return rc;
+        table[i].ray_begin = total;
+        table[i].pix_begin = total_pix;
+        total += (long long)views[i].width * views[i].height * spp;
+        total_pix += (long long)views[i].width * views[i].height;
+    }
+    if (total > 2147483647LL) return fail(CLOAK_EINVAL, "batch holds %lld samples, more than 2^31-1", total);
+    if ((rc = use_device(h))) return rc;
+    ck::Queue q;
+    float4 *samples = nullptr;
+    if ((rc = wavefront_scratch(h, total, q, &samples))) return rc;
+    size_t tbytes = table.size() * sizeof(ck::ViewDev);
+    unsigned long long key = 1469598103934665603ull;
+    key = fnv1a(key, table.data(), tbytes);
+    key = fnv1a(key, &p, sizeof(p));
+    int extra[3] = {spp, h->packet, nviews};
+    key = fnv1a(key, extra, sizeof(extra));
+    key = fnv1a(key, &seed, sizeof(seed));
+    key = fnv1a(key, &h->scratch, sizeof(h->scratch));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaError_t e;
+    if (!h->graph_exec || key != h->graph_key) {
+        // the previous graph may still read the staging buffer
+        if (h->graph_done && (e = cudaEventSynchronize(h->graph_done)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventSynchronize");
+        if (h->batch_bytes < tbytes) {
+            if (h->batch_host) cudaFreeHost(h->batch_host);
+            if (h->batch_dev) cudaFree(h->batch_dev);
+            h->batch_host = h->batch_dev = nullptr;
+            h->batch_bytes = 0;
+            if ((e = cudaHostAlloc(&h->batch_host, tbytes, cudaHostAllocDefault)) != cudaSuccess)
+                return fail(CLOAK_ENOMEM, "pinned view table: %s", cudaGetErrorString(e));
+            if ((e = cudaMalloc(&h->batch_dev, tbytes)) != cudaSuccess) {
+                cudaFreeHost(h->batch_host);
+                h->batch_host = nullptr;
+                return fail(CLOAK_ENOMEM, "device view table: %s", cudaGetErrorString(e));
+            }
+            h->batch_bytes = tbytes;
+        }
+        memcpy(h->batch_host, table.data(), tbytes);
+        if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate");
+        if (!h->graph_done && (e = cudaEventCreateWithFlags(&h->graph_done, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate");
+        if (h->graph_exec) {
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+        if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamBeginCapture");
+        cudaError_t e1 = cudaMemcpyAsync(h->batch_dev, h->batch_host, tbytes, cudaMemcpyHostToDevice, h->cap_stream);
+        cudaError_t e2 = e1 == cudaSuccess ? ck::launch_batch(p, (const ck::ViewDev *)h->batch_dev, nviews, spp, seed,
+                                                             total, total_pix, q, samples, h->packet, h->cap_stream)
+                                           : e1;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (e2 != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return cuda_fail(e2 != cudaSuccess ? e2 : e, "batch capture");
+        }
+        e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            h->graph_exec = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        h->graph_key = key;
+    }
+    if ((e = cudaGraphLaunch(h->graph_exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    if ((e = cudaEventRecord(h->graph_done, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    return CLOAK_OK;
+}
 
 // ---------------------------------------------------------------------------------------------
 // Allocation-free render (cloak_render_noalloc).  The wavefront queue and per-sample buffer live in

@@ -1,0 +1,138 @@
+// kernels_batch.cu -- batched rendering: many views (poses x media x polarizations x resolutions)
+// through one camera/entry kernel, one cost-ordered device queue, ONE persistent integration kernel
+// with the medium selected per ray at run time, one exit kernel and one resolve kernel.
+#include "batch.h"
+#include "wavefront.cuh"
+
+namespace ck {
+
+__device__ __forceinline__ int find_view(const ViewDev *v, int n, long long g, bool by_pixel) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        long long b = by_pixel ? v[mid].pix_begin : v[mid].ray_begin;
+        if (b <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void view_camera_ray(const ViewDev &v, int i, int j, int s, int spp, uint64_t seed,
+                                                double o[3], double d[3]) {
+    double xi1 = 0.5, xi2 = 0.5;
+    if (spp > 1) {
+        uint64_t pix = uint64_t(j) * uint64_t(v.W) + uint64_t(i);
+        xi1 = jitter(seed, pix, s, 0);
+        xi2 = jitter(seed, pix, s, 1);
+    }
+    double px = (2.0 * (i + xi1) / v.W - 1.0) * v.tx;
+    double py = (1.0 - 2.0 * (j + xi2) / v.Hp) * v.ty;
+    double l2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        d[k] = v.fw[k] + px * v.rt[k] + py * v.up[k];
+        l2 += d[k] * d[k];
+    }
+    double il = 1.0 / sqrt(l2);
+    for (int k = 0; k < 3; ++k) { d[k] *= il; o[k] = v.eye[k]; }
+}
+
+__global__ void __launch_bounds__(128) k_batch_entry(Params p, const ViewDev *views, int nviews, int spp,
+                                                     unsigned long long seed, long long total, Queue q,
+                                                     float4 *samples) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const ViewDev &vw = views[find_view(views, nviews, g, false)];
+    long long local = g - vw.ray_begin, pix = local / spp;
+    int s = (int)(local - pix * spp);
+    int i = (int)(pix % vw.W), j = (int)(pix / vw.W);
+    double o[3], d[3], y[6], k0[3], n_in[3], mat[5];
+    view_camera_ray(vw, i, j, s, spp, seed, o, d);
+    Params pv = p;
+    pv.variant = vw.vm >> 1;
+    const int mode = vw.vm & 1;
+    cloak_record rec;
+    float rgb[3];
+    bool inside = mode ? enter<M_EXT>(pv, o, d, rec, rgb, y, k0, n_in, mat)
+                       : enter<M_ORD>(pv, o, d, rec, rgb, y, k0, n_in, mat);
+    if (!inside) {
+        store_sample(samples, nullptr, g, rec, rgb);
+        return;
+    }
+    double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
+    double w_out = transmission_out(mode, mat[0], mat[1], c, n_in, mk0);
+    // queue key: cost bucket (major, slowest first after the descending sort) and medium/mode (minor)
+    queue_append(q, y, w_out, (int)g, cost_bucket(y, k0) * 4 + vw.vm);
+}
+
+__global__ void __launch_bounds__(128) k_batch_exit(Params p, const ViewDev *views, int nviews, int spp,
+                                                    unsigned long long seed, Queue q, float4 *samples) {
+    const unsigned int n = q.count[0];
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        long long g = q.id[k];
+        const ViewDev &vw = views[find_view(views, nviews, g, false)];
+        long long local = g - vw.ray_begin, pix = local / spp;
+        int s = (int)(local - pix * spp);
+        double o[3], d[3];
+        view_camera_ray(vw, (int)(pix % vw.W), (int)(pix / vw.W), s, spp, seed, o, d);
+        Params pv = p;
+        int vm = q.key[k] & 3;
+        pv.variant = vm >> 1;
+        cloak_record rec;
+        float rgb[3];
+        exit_slot(pv, vm & 1, q, k, d, rec, rgb);
+        store_sample(samples, nullptr, g, rec, rgb);
+    }
+}
+
+// per pixel of every view: mean over its samples in sample order, into the view's own image
+__global__ void k_batch_resolve(const ViewDev *views, int nviews, int spp, long long total_pix,
+                                const float4 *samples) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total_pix) return;
+    const ViewDev &vw = views[find_view(views, nviews, g, true)];
+    long long pix = g - vw.pix_begin;
+    const float4 *sp = samples + vw.ray_begin + pix * spp;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int k = 0; k < spp; ++k) {
+        float4 v = sp[k];
+        a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
+    }
+    float inv = 1.0f / spp;
+    vw.out[pix] = make_float4(a0 * inv, a1 * inv, a2 * inv, a3 * inv);
+}
+
+template <int I, int PREC>
+static cudaError_t batch_ip(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
+                            long long total, long long total_pix, const Queue &q, float4 *samples, int packet,
+                            cudaStream_t st) {
+    const int bs = 128;
+    cudaError_t e = cudaMemsetAsync(q.count, 0, QUEUE_HEADER_BYTES, st);
+    if (e != cudaSuccess) return e;
+    k_batch_entry<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(p, views, nviews, spp, seed, total, q, samples);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH, PHASE1_MIN_BIN * 4, (unsigned int)(sms * 32));
+    k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
+    int pk = packet > 0 ? packet : 128;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V_ANY, V_ANY, I, PREC>, pk, 0);
+    if (e != cudaSuccess) return e;
+    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<sms, 32, 0, st>>>(p, q, 1);
+    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(p, q, 0);
+    k_batch_exit<<<sms * 16, 128, 0, st>>>(p, views, nviews, spp, seed, q, samples);
+    k_batch_resolve<<<(unsigned)((total_pix + 255) / 256), 256, 0, st>>>(views, nviews, spp, total_pix, samples);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
+                         long long total, long long total_pix, const Queue &q, float4 *samples, int packet,
+                         cudaStream_t st) {
+    if (p.integ == I_RK4)
+        return p.precision ? batch_ip<I_RK4, 1>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st)
+                           : batch_ip<I_RK4, 0>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st);
+    return p.precision ? batch_ip<I_DP45, 1>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st)
+                       : batch_ip<I_DP45, 0>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st);
+}
+
+}  // namespace ck

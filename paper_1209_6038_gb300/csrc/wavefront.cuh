@@ -38,13 +38,16 @@ struct Queue {
     int *face;                         // surface crossed at exit (EV_LAT / EV_TOP / EV_BOT)
     int *key;                          // cost bucket of the ray (larger = more steps expected)
     int *perm;                         // integration order: slots sorted by descending cost bucket
-    unsigned int *count;               // [0] queued rays, [1] next ray for B, [2] error flag
-    unsigned int *bins;                // [NBINS] bucket sizes, then [NBINS] scatter cursors
+    unsigned int *count;               // [0] queued rays, [1] next ray (phase 1), [2] next ray (phase 2),
+                                       // [3] rays of phase 1 (the slowest, integrated first at low occupancy)
+    unsigned int *bins;                // [nbins] bucket sizes, then [nbins] scatter cursors (nbins <= 256)
     long long cap;
 };
 
-constexpr int NBINS = 64;
-constexpr size_t QUEUE_HEADER_BYTES = 1024;
+constexpr int NBINS = 64;         // cost buckets of a single image
+constexpr int PHASE1_MIN_BIN = 24;  // |L| < 2^-6: rays close enough to the inner radius to be slow
+constexpr int NBINS_BATCH = 256;  // cost bucket x medium/mode of a batch
+constexpr size_t QUEUE_HEADER_BYTES = 4096;
 constexpr size_t QUEUE_SLOT_BYTES = 8 * sizeof(double) + 6 * sizeof(int) + sizeof(float4);
 inline size_t queue_bytes(long long cap) { return QUEUE_HEADER_BYTES + (size_t)cap * QUEUE_SLOT_BYTES; }
 
@@ -80,6 +83,24 @@ __device__ __forceinline__ void store_sample(float4 *samples, cloak_record *recs
     if (recs) recs[id] = rec;
 }
 
+// Append an entering ray to the queue; one atomic per warp for the slot and one per distinct key.
+__device__ __forceinline__ void queue_append(const Queue &q, const double y[6], double w_out, int id, int key) {
+    const unsigned int act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(q.count, (unsigned int)__popc(act));
+    base = __shfl_sync(act, base, leader);
+    unsigned int slot = base + __popc(act & ((1u << lane) - 1u));
+    q.x[slot] = y[0]; q.y[slot] = y[1]; q.z[slot] = y[2];
+    q.vx[slot] = y[3]; q.vy[slot] = y[4]; q.vz[slot] = y[5];
+    q.w_out[slot] = w_out;
+    q.id[slot] = id;
+    q.key[slot] = key;
+    unsigned int same = __match_any_sync(act, key);
+    if (lane == __ffs(same) - 1) atomicAdd(q.bins + key, (unsigned int)__popc(same));
+}
+
 template <int VAR, int MODE>
 __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned long long seed, Queue q,
                                                   float4 *samples, cloak_record *recs) {
@@ -100,36 +121,26 @@ __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned lo
     // Eq. 12 at the entry face along the physical direction: light leaves the cloak towards the camera
     double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
     double w_out = transmission_out(MODE, mat[0], mat[1], c, n_in, mk0);
-    // warp-aggregated append: one atomic per warp for the slot, one per distinct bucket
-    const unsigned int act = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(act) - 1;
-    unsigned int base = 0;
-    if (lane == leader) base = atomicAdd(q.count, (unsigned int)__popc(act));
-    base = __shfl_sync(act, base, leader);
-    unsigned int slot = base + __popc(act & ((1u << lane) - 1u));
-    q.x[slot] = y[0]; q.y[slot] = y[1]; q.z[slot] = y[2];
-    q.vx[slot] = y[3]; q.vy[slot] = y[4]; q.vz[slot] = y[5];
-    q.w_out[slot] = w_out;
-    q.id[slot] = (int)idx;
-    int b = cost_bucket(y, k0);
-    q.key[slot] = b;
-    unsigned int same = __match_any_sync(act, b);
-    if (lane == __ffs(same) - 1) atomicAdd(q.bins + b, (unsigned int)__popc(same));
+    queue_append(q, y, w_out, (int)idx, cost_bucket(y, k0));
 }
 
 // Longest-first order: a counting sort of the queue by descending cost bucket.  k_wf_sort_scan turns
 // the bucket sizes into scatter cursors, k_wf_sort_scatter writes the permutation.
-__global__ void k_wf_sort_scan(Queue q);
+// min_bin: lowest bucket admitted to phase 1; cap1: most rays phase 1 may take
+__global__ void k_wf_sort_scan(Queue q, int nbins, int min_bin, unsigned int cap1);
 __global__ void k_wf_sort_scatter(Queue q);
 
+// phase 1 integrates the rays perm[0, count[3]) (launched with one warp per SM so that these slow rays
+// run at latency speed), phase 2 the rest perm[count[3], count[0]) with the full resident grid.
 template <int VAR, int MODE, int INTEG, int PREC>
-__global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
+__global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q, int phase1) {
     typedef typename std::conditional<PREC == 0, Stepper64<VAR, MODE, INTEG>, StepperMixed<VAR, MODE, INTEG>>::type S;
     typedef typename S::real R;
     S st;
     st.vm = 0;
-    const unsigned int n = q.count[0];
+    const unsigned int n1 = q.count[3];
+    const unsigned int first = phase1 ? 0u : n1, n = phase1 ? n1 : q.count[0];
+    unsigned int *next = q.count + (phase1 ? 1 : 2);
     const int nev = p.R1 > 0.0 ? 4 : 3;
     const R tol = (R)p.h_or_tol, h0 = INTEG == I_RK4 ? (R)p.h_or_tol : (R)1e-3;
     const R conv = sizeof(R) == 8 ? (R)CROSS_REL_TOL : (R)2.4e-7;  // bracket resolution of the crossing search
@@ -146,10 +157,11 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     for (;;) {
         // ---- refill: a lane without a ray takes the next queued one
         if (phase == PH_IDLE) {
-            unsigned int k = atomicAdd(q.count + 1, 1u);
+            unsigned int k = first + atomicAdd(next, 1u);
             if (k < n) {
                 slot = q.perm[k];
                 st.load(q.x, q.y, q.z, q.vx, q.vy, q.vz, slot);
+                if (VAR == V_ANY) st.vm = q.key[slot] & 3;
                 h = h0; t = 0; steps = 0; metal = false; phase = PH_STEP;
             }
         }
@@ -267,6 +279,50 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     }
 }
 
+// Exit of queue slot k: refraction into vacuum at the crossed face, the Eq. 12 factor of the exit face
+// times the stored factor of the entry face, room lookup.  d_cam: the camera ray (kept as the
+// direction of rays that do not leave).
+__device__ __forceinline__ void exit_slot(const Params &p, int mode, const Queue &q, unsigned int k, const double d_cam[3],
+                                          cloak_record &rec, float rgb[3]) {
+    double y[6] = {q.x[k], q.y[k], q.z[k], q.vx[k], q.vy[k], q.vz[k]};
+    int status = q.status[k];
+    rec.mode = mode;
+    rec.tile_id = -1;
+    rec.weight = 0.0;
+    rec.steps = q.steps[k];
+    rec.tof = q.t[k];
+    rgb[0] = rgb[1] = rgb[2] = 0.f;
+    if (status == CLOAK_RAY_EXITED || status == CLOAK_RAY_HIT_METAL_EXITED) {
+        double x[3] = {y[0], y[1], y[2]}, nrm[3], eo, ee, c[3], kk[3];
+        face_normal(q.face[k], x, nrm);
+        local_material(p, x, eo, ee, c);
+        wave_from_velocity(mode, eo, ee, c, y + 3, kk);
+        double kn = dot3(kk, nrm), kt[3];
+        for (int a = 0; a < 3; ++a) kt[a] = kk[a] - kn * nrm[a];
+        double kt2 = dot3(kt, kt);
+        set_vec(rec.exit_pos, x);
+        if (kt2 > 1.0) {
+            rec.status = CLOAK_RAY_TIR;
+            set_vec(rec.exit_dir, d_cam);
+        } else {
+            double qn = sqrt(1.0 - kt2), dout[3], mdout[3];
+            for (int a = 0; a < 3; ++a) {
+                dout[a] = fma(qn, nrm[a], kt[a]);
+                mdout[a] = -dout[a];
+            }
+            double tin = transmission_in(mode, eo, ee, c, nrm, mdout);
+            rec.weight = tin * q.w_out[k];
+            rec.status = status;
+            set_vec(rec.exit_dir, dout);
+            rec.tile_id = room_hit(p, x, dout, rgb);
+        }
+    } else {  // STEP_LIMIT or SINGULAR
+        rec.status = status;
+        rec.exit_pos[0] = y[0]; rec.exit_pos[1] = y[1]; rec.exit_pos[2] = y[2];
+        set_vec(rec.exit_dir, d_cam);
+    }
+}
+
 template <int VAR, int MODE>
 __global__ void __launch_bounds__(128) k_wf_exit(Params p, int spp, unsigned long long seed, Queue q,
                                                  float4 *samples, cloak_record *recs) {
@@ -278,44 +334,9 @@ __global__ void __launch_bounds__(128) k_wf_exit(Params p, int spp, unsigned lon
         int i = (int)(pix % p.W), j = (int)(pix / p.W);
         double o[3], d[3];
         camera_ray(p, i, j, s, spp, seed, o, d);
-        double y[6] = {q.x[k], q.y[k], q.z[k], q.vx[k], q.vy[k], q.vz[k]};
-        int status = q.status[k];
         cloak_record rec;
-        rec.mode = MODE;
-        rec.tile_id = -1;
-        rec.weight = 0.0;
-        rec.steps = q.steps[k];
-        rec.tof = q.t[k];
-        float rgb[3] = {0.f, 0.f, 0.f};
-        if (status == CLOAK_RAY_EXITED || status == CLOAK_RAY_HIT_METAL_EXITED) {
-            double x[3] = {y[0], y[1], y[2]}, nrm[3], eo, ee, c[3], kk[3];
-            face_normal(q.face[k], x, nrm);
-            local_material(p, x, eo, ee, c);
-            wave_from_velocity(MODE, eo, ee, c, y + 3, kk);
-            double kn = dot3(kk, nrm), kt[3];
-            for (int a = 0; a < 3; ++a) kt[a] = kk[a] - kn * nrm[a];
-            double kt2 = dot3(kt, kt);
-            set_vec(rec.exit_pos, x);
-            if (kt2 > 1.0) {
-                rec.status = CLOAK_RAY_TIR;
-                set_vec(rec.exit_dir, d);
-            } else {
-                double qn = sqrt(1.0 - kt2), dout[3], mdout[3];
-                for (int a = 0; a < 3; ++a) {
-                    dout[a] = fma(qn, nrm[a], kt[a]);
-                    mdout[a] = -dout[a];
-                }
-                double tin = transmission_in(MODE, eo, ee, c, nrm, mdout);
-                rec.weight = tin * q.w_out[k];
-                rec.status = status;
-                set_vec(rec.exit_dir, dout);
-                rec.tile_id = room_hit(p, x, dout, rgb);
-            }
-        } else {  // STEP_LIMIT or SINGULAR
-            rec.status = status;
-            rec.exit_pos[0] = y[0]; rec.exit_pos[1] = y[1]; rec.exit_pos[2] = y[2];
-            set_vec(rec.exit_dir, d);
-        }
+        float rgb[3];
+        exit_slot(p, MODE, q, k, d, rec, rgb);
         store_sample(samples, recs, idx, rec, rgb);
     }
 }
@@ -337,7 +358,7 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_wf_sort_scan<<<1, 32, 0, st>>>(q);
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS, PHASE1_MIN_BIN, (unsigned int)(sms * 32));
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -352,7 +373,8 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
         if (e != cudaSuccess) return e;
         blocks_per_sm[slot] = nb > 0 ? nb : 1;
     }
-    k_wf_integrate<V, M, I, PREC><<<blocks_per_sm[slot] * sms, pk, 0, st>>>(p, q);
+    k_wf_integrate<V, M, I, PREC><<<sms, 32, 0, st>>>(p, q, 1);
+    k_wf_integrate<V, M, I, PREC><<<blocks_per_sm[slot] * sms, pk, 0, st>>>(p, q, 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);

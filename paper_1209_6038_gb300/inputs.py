@@ -117,3 +117,23 @@ def ray_set(n: int, seed: int, kind: str = "mixed", R2: float = 1.0, H: float = 
     d = np.stack([tx - ox, ty - oy, zt - z0], 1)
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     return np.concatenate([np.stack([ox, oy, z0], 1), d], 1)
+
+
+BATCH_RESOLUTIONS = ((256, 256), (1024, 768), (1920, 1080), (3840, 2160))
+
+
+def batched_views(n_poses: int = 64, seed: int = 0, resolutions=BATCH_RESOLUTIONS, hfov_deg: float = 60.0):
+    """Seeded orbit of camera poses (azimuth ~ U[0, 360) deg, elevation ~ U[0, 60) deg, distance 5),
+    each at a resolution drawn uniformly from `resolutions`, rendered for both cloaks and both
+    polarizations: a list of (variant, polarization, eye, target, up, hfov_deg, width, height)."""
+    rng = np.random.default_rng(seed)
+    views = []
+    for _ in range(n_poses):
+        az = rng.uniform(0.0, 360.0)
+        el = rng.uniform(0.0, 60.0)
+        W, H = resolutions[int(rng.integers(len(resolutions)))]
+        eye, tgt, up = camera_pose(el, az)
+        for v in (RADIAL, AZIMUTHAL):
+            for p in (ORDINARY, EXTRAORDINARY):
+                views.append((v, p, eye, tgt, up, hfov_deg, W, H))
+    return views
