@@ -194,7 +194,7 @@ def main():
                     help="VARIANT,MODE,ELEV: render only this image twice (for profilers), e.g. 1,1,20")
     ap.add_argument("--width", type=int, default=None)
     ap.add_argument("--height", type=int, default=None)
-    ap.add_argument("--schedule", default="wavefront", choices=["plain", "wavefront"])
+    ap.add_argument("--schedule", default="batched", choices=["plain", "wavefront", "batched"])
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -223,7 +223,7 @@ def main():
         eye, tgt, up = inputs.camera_pose(float(e))
         c = ck.Cloak(int(v)).camera(eye, tgt, up, w.hfov_deg, W, H)
         c.integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol, ck.FP64, w.max_steps)
-        c.schedule(ck.SCHED_WAVEFRONT if args.schedule == "wavefront" else ck.SCHED_PLAIN)
+        c.schedule(ck.SCHED_PLAIN if args.schedule == "plain" else ck.SCHED_WAVEFRONT)
         img = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
         for _ in range(2):
             c.render(int(m), w.spp, w.seed, out=img)
@@ -247,24 +247,59 @@ def main():
 
     imgs = [torch.empty((w.height, w.width, 4), dtype=torch.float32, device="cuda") for _ in w.images]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stage_ms = [0.0, 0.0, 0.0, 0.0]
+    integ_kind = ck.DP45 if w.integrator == "dp45" else ck.RK4
 
-    def step(hs, timed_stages=False):
-        for i, (v, m, e) in enumerate(w.images):
-            hs[(v, e)].render(m, w.spp, w.seed, out=imgs[i])
-            if timed_stages:
-                for k, t in enumerate(hs[(v, e)].stage_times()):
+    class PerImage:
+        """one handle per (variant, elevation), one render call per image"""
+
+        def __init__(self, schedule, precision=ck.FP64):
+            self.hs = make_handles(schedule, precision)
+            for c in self.hs.values():
+                c.stage_timing(True)
+            self.launches = (4 if schedule == ck.SCHED_WAVEFRONT else 1) * len(w.images)
+
+        def step(self, stage_ms=None):
+            for i, (v, m, e) in enumerate(w.images):
+                c = self.hs[(v, e)]
+                c.render(m, w.spp, w.seed, out=imgs[i])
+                if stage_ms is not None:
+                    for k, t in enumerate(c.stage_times()):
+                        stage_ms[k] += t
+
+        def close(self):
+            for c in self.hs.values():
+                c.close()
+
+    class Batched:
+        """all images of the step in one cloak_render_batch call (one persistent integration kernel,
+        replayed CUDA graph)"""
+
+        def __init__(self, precision=ck.FP64):
+            self.h = ck.Cloak(ck.RADIAL).integrator(integ_kind, w.h_or_tol, precision, w.max_steps)
+            self.h.schedule(ck.SCHED_WAVEFRONT).stage_timing(True)
+            self.views = []
+            for i, (v, m, e) in enumerate(w.images):
+                eye, tgt, up = inputs.camera_pose(e)
+                self.views.append((v, m, eye, tgt, up, w.hfov_deg, imgs[i]))
+            self.launches = 7  # entry, sort scan, sort scatter, integrate, exit, resolve + the table copy
+
+        def step(self, stage_ms=None):
+            ck.cloak_render_batch(self.h.h, self.views, w.spp, w.seed)
+            if stage_ms is not None:
+                for k, t in enumerate(self.h.stage_times()):
                     stage_ms[k] += t
 
-    def timed(hs, warmup, steps, sampler=None):
+        def close(self):
+            self.h.close()
+
+    def timed(runner, warmup, steps, sampler=None):
         for _ in range(warmup):
-            step(hs)
+            runner.step()
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        for k in range(4):
-            stage_ms[k] = 0.0
+        stage_ms = [0.0, 0.0, 0.0, 0.0]
         ms = []
         ctx = sampler if sampler is not None else _Null()
         with ctx:
@@ -273,7 +308,7 @@ def main():
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                step(hs, timed_stages=True)
+                runner.step(stage_ms)
                 b.record(stream)
                 b.synchronize()
                 ms.append(a.elapsed_time(b))
@@ -285,34 +320,34 @@ def main():
             dist.all_reduce(tot, op=dist.ReduceOp.MAX)
         return float(tot.item()) / steps, ms, [x / steps for x in stage_ms]
 
-    main_sched = ck.SCHED_WAVEFRONT if args.schedule == "wavefront" else ck.SCHED_PLAIN
-    hs = make_handles(main_sched)
-    for c in hs.values():
-        c.stage_timing(True)
+    if args.schedule == "batched":
+        main_runner = Batched()
+    else:
+        main_runner = PerImage(ck.SCHED_WAVEFRONT if args.schedule == "wavefront" else ck.SCHED_PLAIN)
     sampler = ClockSampler(local)
-    ms_step, ms_list, stages = timed(hs, args.warmup, args.steps, sampler)
+    ms_step, ms_list, stages = timed(main_runner, args.warmup, args.steps, sampler)
     rays_step = w.rays
     value = ws * rays_step / (ms_step / 1e3)
     clocks = sampler.summary()
-    launches_per_image = 4 if main_sched == ck.SCHED_WAVEFRONT else 1
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(w),
            "schedule": args.schedule, "clocks": clocks,
-           "gpu_launches": launches_per_image * len(w.images) * args.steps,
-           "stage_ms_per_step": {"camera_entry": stages[0], "integrate": stages[1], "exit_shade": stages[2],
+           "gpu_launches": main_runner.launches * args.steps,
+           "stage_ms_per_step": {"camera_entry_sort": stages[0], "integrate": stages[1], "exit_shade": stages[2],
                                  "resolve": stages[3]}}
 
     if rank == 0:
         # ---- records pass (untimed): step counts for the roofline, sampled rays for the error
+        rec_handles = make_handles(ck.SCHED_WAVEFRONT)
         rec_buf = torch.empty(w.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
         flops = 0.0
         steps_total = 0
         status_hist = np.zeros(8, np.int64)
         gpu_samples = []
         for idx, (v, m, e) in enumerate(w.images):
-            hs[(v, e)].render_records(m, w.spp, w.seed, out=rec_buf)
+            rec_handles[(v, e)].render_records(m, w.spp, w.seed, out=rec_buf)
             i32 = rec_buf.view(torch.int32).view(-1, 20)   # cloak_record: tile_id, status, steps at 16, 17, 18
             status = i32[:, 17].long()
             steps_img = int(i32[:, 18].long().sum().item())
@@ -323,8 +358,9 @@ def main():
             sel = torch.from_numpy((pix[:, None] * w.spp + np.arange(w.spp)[None, :]).reshape(-1)).cuda()
             gpu_samples.append(ck.records_to_numpy(rec_buf.view(-1, ck.RECORD_BYTES)[sel].reshape(-1)))
         del rec_buf
-        kname = "k_wf_integrate (12 launches per step)" if main_sched == ck.SCHED_WAVEFRONT else \
-            "k_render_plain (12 launches per step)"
+        kname = {"batched": "k_wf_integrate<any medium> (1 launch per step, all 12 images)",
+                 "wavefront": "k_wf_integrate (12 launches per step)",
+                 "plain": "k_render_plain (12 launches per step)"}[args.schedule]
         achieved = flops / (stages[1] / 1e3) / 1e12
         out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
@@ -353,61 +389,64 @@ def main():
                                      "status_mismatch": int((g["status"] != o["status"]).sum()),
                                      "pixels_tile_or_status_differs_frac": float(px_diff.mean())}
 
-    # ---- the precision form: the same workload with FP32 stepping (mixed), against the oracle sample
-    if not args.no_mixed and rank == 0:
-        mh = make_handles(main_sched, precision=ck.MIXED)
-        for c in mh.values():
-            c.stage_timing(True)
-        mms, _, mstages = timed(mh, 1, 2)
-        rec_buf = torch.empty(w.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
-        msamples = []
-        for idx, (v, m, e) in enumerate(w.images):
-            mh[(v, e)].render_records(m, w.spp, w.seed, out=rec_buf)
-            pix = sample_pixels(w, idx, args.cpu_pixels)
-            sel = torch.from_numpy((pix[:, None] * w.spp + np.arange(w.spp)[None, :]).reshape(-1)).cuda()
-            msamples.append(ck.records_to_numpy(rec_buf.view(-1, ck.RECORD_BYTES)[sel].reshape(-1)))
-        del rec_buf
-        for c in mh.values():
+        # ---- the precision form: the same workload with FP32 stepping (mixed), against the oracle sample
+        if not args.no_mixed:
+            mixed_runner = Batched(ck.MIXED) if args.schedule == "batched" else PerImage(ck.SCHED_WAVEFRONT, ck.MIXED)
+            mms, _, mstages = timed(mixed_runner, 1, 2)
+            mixed_runner.close()
+            mh = make_handles(ck.SCHED_WAVEFRONT, precision=ck.MIXED)
+            rec_buf = torch.empty(w.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
+            msamples = []
+            for idx, (v, m, e) in enumerate(w.images):
+                mh[(v, e)].render_records(m, w.spp, w.seed, out=rec_buf)
+                pix = sample_pixels(w, idx, args.cpu_pixels)
+                sel = torch.from_numpy((pix[:, None] * w.spp + np.arange(w.spp)[None, :]).reshape(-1)).cuda()
+                msamples.append(ck.records_to_numpy(rec_buf.view(-1, ck.RECORD_BYTES)[sel].reshape(-1)))
+            del rec_buf
+            for c in mh.values():
+                c.close()
+            gm = np.concatenate(msamples)
+            fin = np.isin(o["status"], [0, 1, 2, 7]) & (gm["status"] == o["status"])
+            cr = np.linalg.norm(np.cross(gm["exit_dir"][fin], o["exit_dir"][fin]), axis=-1)
+            errm = np.arctan2(cr, np.sum(gm["exit_dir"][fin] * o["exit_dir"][fin], axis=-1))
+            pxm = ((gm["tile_id"] != o["tile_id"]) | (gm["status"] != o["status"])).reshape(-1, w.spp).any(1)
+            out["mixed"] = {"value": ws * rays_step / (mms / 1e3), "unit": UNIT, "ms_per_step": mms, "warmup": 1,
+                            "steps": 2, "schedule": args.schedule,
+                            "dtype": "f32 stepping, float-float state, f64 band r < R1 + 0.02",
+                            "integrate_ms_per_step": mstages[1], "speedup_vs_fp64": ms_step / mms,
+                            "accuracy_vs_oracle": {"max_exit_dir_err_rad": float(errm.max(initial=0)),
+                                                   "p999_exit_dir_err_rad": float(np.quantile(errm, 0.999)),
+                                                   "rays_over_1e-5_rad": int((errm > 1e-5).sum()),
+                                                   "rays_compared": int(fin.sum()),
+                                                   "pixels_tile_or_status_differs_frac": float(pxm.mean())}}
+        for c in rec_handles.values():
             c.close()
-        g = np.concatenate(msamples)
-        fin = np.isin(o["status"], [0, 1, 2, 7]) & (g["status"] == o["status"])
-        cr = np.linalg.norm(np.cross(g["exit_dir"][fin], o["exit_dir"][fin]), axis=-1)
-        err = np.arctan2(cr, np.sum(g["exit_dir"][fin] * o["exit_dir"][fin], axis=-1))
-        px_diff = ((g["tile_id"] != o["tile_id"]) | (g["status"] != o["status"])).reshape(-1, w.spp).any(1)
-        out["mixed"] = {"value": ws * rays_step / (mms / 1e3), "unit": UNIT, "ms_per_step": mms, "warmup": 1,
-                        "steps": 2, "dtype": "f32 stepping, float-float state, f64 band r < R1 + 0.02",
-                        "integrate_ms_per_step": mstages[1],
-                        "speedup_vs_fp64": ms_step / mms,
-                        "accuracy_vs_oracle": {"max_exit_dir_err_rad": float(err.max(initial=0)),
-                                               "p999_exit_dir_err_rad": float(np.quantile(err, 0.999)),
-                                               "rays_over_1e-5_rad": int((err > 1e-5).sum()),
-                                               "rays_compared": int(fin.sum()),
-                                               "pixels_tile_or_status_differs_frac": float(px_diff.mean())}}
 
-    # ---- the plain FP64 integrator (one thread per pixel) on the same workload, for comparison
-    if not args.no_plain and main_sched != ck.SCHED_PLAIN:
-        ph = make_handles(ck.SCHED_PLAIN)
-        for c in ph.values():
-            c.stage_timing(True)
-        pms, _, _ = timed(ph, 1, 1)
-        for c in ph.values():
-            c.close()
-        out["plain_fp64"] = {"value": ws * rays_step / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
-                             "warmup": 1, "steps": 1}
-        out["speedup_vs_plain_fp64"] = pms / ms_step
+    # ---- comparators on the same workload: per-image wavefront and the plain FP64 integrator
+    if not args.no_plain:
+        for name, sched in (("per_image_wavefront_fp64", ck.SCHED_WAVEFRONT), ("plain_fp64", ck.SCHED_PLAIN)):
+            if (args.schedule == "wavefront" and sched == ck.SCHED_WAVEFRONT) or \
+                    (args.schedule == "plain" and sched == ck.SCHED_PLAIN):
+                continue
+            r = PerImage(sched)
+            pms, _, _ = timed(r, 1, 1)
+            r.close()
+            out[name] = {"value": ws * rays_step / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "warmup": 1,
+                         "steps": 1}
+        if "plain_fp64" in out:
+            out["speedup_vs_plain_fp64"] = out["plain_fp64"]["ms_per_step"] / ms_step
 
     # ---- end to end through the public API: render and copy every image to pinned host memory
     if not args.no_e2e:
         host = [torch.empty_like(im, device="cpu").pin_memory() for im in imgs]
-        for _ in range(1):
-            step(hs)
+        main_runner.step()
         torch.cuda.synchronize()
         e2e_ms = []
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            step(hs)
+            main_runner.step()
             for hb, im in zip(host, imgs):
                 hb.copy_(im, non_blocking=True)
             torch.cuda.synchronize()
@@ -415,11 +454,10 @@ def main():
         e2e = ws * rays_step / (statistics.mean(e2e_ms) / 1e3)
         out["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0,
                       "d2h_bytes_per_step": sum(im.numel() * 4 for im in imgs),
-                      "note": "inputs are camera and integrator parameters passed by value as kernel arguments; "
+                      "note": "inputs are camera and integrator parameters (host structs passed through the C ABI); "
                               "outputs are the 12 float4 images copied to pinned host memory"}
 
-    for c in hs.values():
-        c.close()
+    main_runner.close()
     if ws > 1:
         dist.destroy_process_group()
     if rank == 0:

@@ -162,9 +162,17 @@ typedef struct cloak_view {
  * variant must be CLOAK_RADIAL or CLOAK_AZIMUTHAL; integrator, precision and packet come from the
  * handle.  views: host array of nviews >= 1 entries (read during the call); total samples
  * sum(width*height*spp) <= 2^31 - 1.  Scratch: about 104 bytes per sample, owned by the handle.
- * Every view's output is written on cuda_stream. */
+ * Every view's output is written on cuda_stream.  With stage timing on, cloak_stage_times reports the
+ * stages of the last batch (events recorded inside the graph). */
 int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
                        void *cuda_stream);
+
+/* BF16 tensor-core GEMM of the learned surrogate (tcgen05 with a TMEM accumulator, operands staged by
+ * TMA with 128-byte swizzle): C = A B^T with A[M x K] and B[N x K] row-major BF16 device arrays
+ * (16-byte aligned) and C[M x N] row-major FP32.  M % 128 == 0; N % 16 == 0 with 16 <= N <= 256;
+ * K % 64 == 0.  Synchronises cuda_stream; CLOAK_ETIMEOUT if a bounded wait inside the kernel expired.
+ * The paper has no counterpart: it serves the learned surrogate of the exit state. */
+int cloak_mlp_gemm(const void *dev_a, const void *dev_b, float *dev_c, int M, int N, int K, void *cuda_stream);
 
 /* Allocation-free render.  The paper has no counterpart: this is a service for callers that may not
  * allocate device memory -- processes whose device memory is owned entirely by another allocator

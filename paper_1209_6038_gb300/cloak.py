@@ -45,6 +45,7 @@ SIGNATURES = {
     "cloak_render_records": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
     "cloak_trace_rays": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
+    "cloak_mlp_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "cloak_render_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p]),
     "cloak_render_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
@@ -163,6 +164,14 @@ def cloak_trace_rays(h, polarization, rays, n, records, stream=None):
         raise CloakError(EINVAL, "buffer too small")
     return _check(load().cloak_trace_rays(h, polarization, C.c_void_p(rays.data_ptr()), n,
                                           C.c_void_p(records.data_ptr()), _stream_ptr(stream)))
+
+
+def cloak_mlp_gemm(a, b, c, stream=None):
+    """c[M, N] (fp32) = a[M, K] (bf16) @ b[N, K]^T (bf16) on the tensor cores."""
+    M, K = a.shape
+    N = b.shape[0]
+    return _check(load().cloak_mlp_gemm(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), C.c_void_p(c.data_ptr()),
+                                        M, N, K, _stream_ptr(stream)))
 
 
 def cloak_render_batch(h, views, spp, seed, stream=None):

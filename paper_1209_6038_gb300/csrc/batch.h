@@ -19,8 +19,10 @@ struct ViewDev {
 };
 
 // queue scratch and per-sample buffer as for the wavefront schedule; views: device copy of the table
+// ev (nullable, used while capturing): ev[0] before, ev[1] after entry + sort, ev[2] after integration,
+// ev[3] after exit, ev[4] after resolve -- recorded as external event nodes of the graph
 cudaError_t launch_batch(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
                          long long total, long long total_pix, const Queue &q, float4 *samples, int packet,
-                         cudaStream_t st);
+                         cudaStream_t st, cudaEvent_t *ev);
 
 }  // namespace ck

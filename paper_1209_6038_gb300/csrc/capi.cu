@@ -500,7 +500,7 @@ extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nview
     unsigned long long key = 1469598103934665603ull;
     key = fnv1a(key, table.data(), tbytes);
     key = fnv1a(key, &p, sizeof(p));
-    int extra[3] = {spp, h->packet, nviews};
+    int extra[4] = {spp, h->packet, nviews, h->timing};
     key = fnv1a(key, extra, sizeof(extra));
     key = fnv1a(key, &seed, sizeof(seed));
     key = fnv1a(key, &h->scratch, sizeof(h->scratch));
@@ -537,7 +537,8 @@ extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nview
             return cuda_fail(e, "cudaStreamBeginCapture");
         cudaError_t e1 = cudaMemcpyAsync(h->batch_dev, h->batch_host, tbytes, cudaMemcpyHostToDevice, h->cap_stream);
         cudaError_t e2 = e1 == cudaSuccess ? ck::launch_batch(p, (const ck::ViewDev *)h->batch_dev, nviews, spp, seed,
-                                                             total, total_pix, q, samples, h->packet, h->cap_stream)
+                                                             total, total_pix, q, samples, h->packet, h->cap_stream,
+                                                             h->timing ? h->ev : nullptr)
                                            : e1;
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(h->cap_stream, &graph);
@@ -556,6 +557,10 @@ extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nview
     }
     if ((e = cudaGraphLaunch(h->graph_exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     if ((e = cudaEventRecord(h->graph_done, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if (h->timing) {
+        h->timed_calls++;
+        h->timed_sched = CLOAK_SCHED_WAVEFRONT;
+    }
     return CLOAK_OK;
 }
 

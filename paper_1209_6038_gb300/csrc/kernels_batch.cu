@@ -101,38 +101,46 @@ __global__ void k_batch_resolve(const ViewDev *views, int nviews, int spp, long 
     vw.out[pix] = make_float4(a0 * inv, a1 * inv, a2 * inv, a3 * inv);
 }
 
+static inline void mark(cudaEvent_t *ev, int i, cudaStream_t st) {
+    if (ev) cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
+}
+
 template <int I, int PREC>
 static cudaError_t batch_ip(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
                             long long total, long long total_pix, const Queue &q, float4 *samples, int packet,
-                            cudaStream_t st) {
+                            cudaStream_t st, cudaEvent_t *ev) {
     const int bs = 128;
+    mark(ev, 0, st);
     cudaError_t e = cudaMemsetAsync(q.count, 0, QUEUE_HEADER_BYTES, st);
     if (e != cudaSuccess) return e;
     k_batch_entry<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(p, views, nviews, spp, seed, total, q, samples);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH, PHASE1_MIN_BIN * 4, (unsigned int)(sms * 32));
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH);
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
+    mark(ev, 1, st);
     int pk = packet > 0 ? packet : 128;
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V_ANY, V_ANY, I, PREC>, pk, 0);
     if (e != cudaSuccess) return e;
-    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<sms, 32, 0, st>>>(p, q, 1);
-    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(p, q, 0);
+    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(p, q);
+    mark(ev, 2, st);
     k_batch_exit<<<sms * 16, 128, 0, st>>>(p, views, nviews, spp, seed, q, samples);
+    mark(ev, 3, st);
     k_batch_resolve<<<(unsigned)((total_pix + 255) / 256), 256, 0, st>>>(views, nviews, spp, total_pix, samples);
+    mark(ev, 4, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
                          long long total, long long total_pix, const Queue &q, float4 *samples, int packet,
-                         cudaStream_t st) {
+                         cudaStream_t st, cudaEvent_t *ev) {
     if (p.integ == I_RK4)
-        return p.precision ? batch_ip<I_RK4, 1>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st)
-                           : batch_ip<I_RK4, 0>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st);
-    return p.precision ? batch_ip<I_DP45, 1>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st)
-                       : batch_ip<I_DP45, 0>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st);
+        return p.precision ? batch_ip<I_RK4, 1>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev)
+                           : batch_ip<I_RK4, 0>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev);
+    return p.precision ? batch_ip<I_DP45, 1>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev)
+                       : batch_ip<I_DP45, 0>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev);
 }
 
 }  // namespace ck

@@ -17,19 +17,14 @@ __global__ void k_wf_resolve(int npix, int spp, const float4 *samples, float4 *o
     out[pix] = make_float4(a0 * inv, a1 * inv, a2 * inv, a3 * inv);
 }
 
-__global__ void k_wf_sort_scan(Queue q, int nbins, int min_bin, unsigned int cap1) {
+__global__ void k_wf_sort_scan(Queue q, int nbins) {
     if (threadIdx.x != 0) return;
-    unsigned int off = 0, n1 = 0;
-    bool open = true;
+    unsigned int off = 0;
     for (int b = nbins - 1; b >= 0; --b) {  // descending key: slowest rays first
         unsigned int c = q.bins[b];
         q.bins[NBINS_BATCH + b] = off;
         off += c;
-        // phase 1: whole buckets, slowest first, while they fit and are slow enough
-        if (open && b >= min_bin && off <= cap1) n1 = off;
-        else if (c) open = false;
     }
-    q.count[3] = n1;
 }
 
 __global__ void k_wf_sort_scatter(Queue q) {

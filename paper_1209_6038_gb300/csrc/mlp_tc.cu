@@ -1,0 +1,218 @@
+// mlp_tc.cu -- tcgen05 / TMEM / TMA BF16 GEMM (see mlp_tc.cuh).
+#include <cudaTypedefs.h>
+
+#include "mlp_tc.cuh"
+
+namespace ck {
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
+    return d;
+}
+// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both operands K-major, M = 128
+__host__ __device__ constexpr uint32_t bf16_idesc(int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ float gelu_tanh(float x) {
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    float u = k0 * (x + k1 * x * x * x);
+    return 0.5f * x * (1.f + tanhf(u));
+}
+
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
+                                                    const __grid_constant__ CUtensorMap tb, GemmArgs g) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[GEMM_STAGES], empty_bar[GEMM_STAGES], done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int N = g.N, nk = g.K / GEMM_KCHUNK;
+    const uint32_t a_bytes = GEMM_TILE_M * 128, b_bytes = (uint32_t)N * 128;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * GEMM_TILE_M;
+    uint32_t ncols = 32;
+    while ((int)ncols < N) ncols <<= 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < GEMM_STAGES; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&done_bar), 1);
+        failed = 0;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = bf16_idesc(N);
+        bool ok = true;
+        for (int it = 0; it < nk + GEMM_STAGES - 1 && ok; ++it) {
+            if (it < nk) {  // load chunk `it`
+                const int s = it % GEMM_STAGES;
+                if (it >= GEMM_STAGES) ok = mbar_wait(smem_u32(&empty_bar[s]), ((it / GEMM_STAGES) - 1) & 1);
+                if (!ok) break;
+                unsigned char *sa = smem + s * (a_bytes + b_bytes), *sb = sa + a_bytes;
+                mbar_expect_tx(smem_u32(&full_bar[s]), a_bytes + b_bytes);
+                tma_load_2d(smem_u32(sa), &ta, it * GEMM_KCHUNK, m0, smem_u32(&full_bar[s]));
+                tma_load_2d(smem_u32(sb), &tb, it * GEMM_KCHUNK, 0, smem_u32(&full_bar[s]));
+            }
+            const int j = it - (GEMM_STAGES - 1);
+            if (j >= 0 && j < nk) {  // multiply chunk j
+                const int s = j % GEMM_STAGES;
+                ok = mbar_wait(smem_u32(&full_bar[s]), (j / GEMM_STAGES) & 1);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                unsigned char *sa = smem + s * (a_bytes + b_bytes), *sb = sa + a_bytes;
+                const uint64_t ad = sw128_desc(smem_u32(sa)), bd = sw128_desc(smem_u32(sb));
+#pragma unroll
+                for (int kk = 0; kk < GEMM_KCHUNK / 16; ++kk) {
+                    const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+                    // advance 16 K-elements (32 bytes) inside the swizzled 128-byte row
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad + (uint64_t)(2 * kk)), "l"(bd + (uint64_t)(2 * kk)), "r"(idesc), "r"(acc));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&empty_bar[s])));
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&done_bar)));
+        if (!ok) failed = 1;
+    }
+    __syncwarp();
+    const bool done = mbar_wait(smem_u32(&done_bar), 0);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (!done || failed) {
+        if (threadIdx.x == 0 && g.err) atomicExch(g.err, 1u);
+    } else {
+        const int row = m0 + warp * 32 + lane;
+        for (int c = 0; c < N; c += 16) {
+            uint32_t r[16];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+            if (row < g.M) {
+                if (g.epi == EPI_STORE) {
+                    float4 *dst = (float4 *)(g.C + (size_t)row * g.ldc + c);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += g.bias[c + i];
+                    float4 *dz = (float4 *)(g.Z + (size_t)row * g.ldz + c);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) dz[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    if (g.epi == EPI_BIAS_GELU) {
+                        __nv_bfloat162 hv[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) hv[i] = __floats2bfloat162_rn(gelu_tanh(v[2 * i]), gelu_tanh(v[2 * i + 1]));
+                        uint4 *dh = (uint4 *)(g.H + (size_t)row * g.ldh + c);
+                        dh[0] = *(uint4 *)&hv[0];
+                        dh[1] = *(uint4 *)&hv[4];
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+// ------------------------------------------------------------------ host
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+CUresult make_tmap_bf16(CUtensorMap *map, const void *base, int rows, int cols, int box_rows) {
+    auto enc = get_encode();
+    if (!enc) return CUDA_ERROR_NOT_SUPPORTED;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)GEMM_KCHUNK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+cudaError_t launch_gemm_tc(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &g, cudaStream_t st) {
+    if (g.M <= 0 || g.M % GEMM_TILE_M || g.N < 16 || g.N > 256 || g.N % 16 || g.K <= 0 || g.K % GEMM_KCHUNK)
+        return cudaErrorInvalidValue;
+    size_t smem = gemm_smem_bytes(g.N);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gemm_smem_bytes(256));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_gemm_tc<<<g.M / GEMM_TILE_M, 128, smem, st>>>(ta, tb, g);
+    return cudaGetLastError();
+}
+
+}  // namespace ck

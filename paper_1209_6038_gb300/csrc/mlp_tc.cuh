@@ -1,0 +1,51 @@
+// mlp_tc.cuh -- BF16 tensor-core GEMM for the learned surrogate (sm_103a: tcgen05 + TMEM + TMA).
+//
+//   C[M x N] = A[M x K] * B[N x K]^T      A, B row-major BF16 (K contiguous), FP32 accumulation.
+//
+// One CTA (4 warps) computes a 128 x N tile (N <= 256, multiple of 16).  K is consumed in chunks of
+// 64 elements (128 bytes, one 128B-swizzle row): warp 0 / lane 0 issues the TMA loads of A and B
+// chunks into a 3-stage shared-memory ring and the tcgen05.mma instructions (M = 128, K = 16 each,
+// accumulator in tensor memory), committing each stage back to its "empty" barrier.  After the last
+// MMA completes, every warp reads its 32 accumulator lanes with tcgen05.ld and applies the epilogue:
+//   EPI_STORE     C (FP32)
+//   EPI_BIAS_GELU Z = C + bias (FP32, kept for the backward pass) and H = GELU_tanh(Z) (BF16)
+//   EPI_BIAS      Z = C + bias (FP32)
+// Every mbarrier wait is bounded; on timeout the kernel records an error code and skips ahead.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ck {
+
+enum { EPI_STORE = 0, EPI_BIAS_GELU = 1, EPI_BIAS = 2 };
+
+struct GemmArgs {
+    int M, N, K;           // M % 128 == 0, N % 16 == 0 (16..256), K % 64 == 0
+    float *C;              // EPI_STORE: C[M x ldc]
+    int ldc;
+    const float *bias;     // [N]
+    float *Z;              // EPI_BIAS*: Z[M x ldz]
+    int ldz;
+    __nv_bfloat16 *H;      // EPI_BIAS_GELU: H[M x ldh]
+    int ldh;
+    int epi;
+    unsigned int *err;     // error flag (0 = ok)
+};
+
+constexpr int GEMM_TILE_M = 128;
+constexpr int GEMM_KCHUNK = 64;
+constexpr int GEMM_STAGES = 3;
+
+inline size_t gemm_smem_bytes(int N) {
+    return 1024 + (size_t)GEMM_STAGES * (GEMM_TILE_M * 128 + (size_t)N * 128);
+}
+
+// host: TMA descriptors for a row-major BF16 matrix [rows x cols] with box (64 cols x box_rows)
+CUresult make_tmap_bf16(CUtensorMap *map, const void *base, int rows, int cols, int box_rows);
+cudaError_t launch_gemm_tc(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &g, cudaStream_t st);
+
+}  // namespace ck

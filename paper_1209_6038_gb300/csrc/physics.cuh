@@ -246,10 +246,11 @@ __device__ __forceinline__ bool dp_control(const double y[6], const double y1[6]
 template <typename T>
 __device__ __forceinline__ T metal_chord(T x0, T y0, T x1, T y1, T R1sq) {
     T dx = x1 - x0, dy = y1 - y0, dd = dx * dx + dy * dy;
-    if (!(dd > T(0))) return T(0);
-    T sc = -(x0 * dx + y0 * dy) / dd;
-    T mx = x0 + sc * dx, my = y0 + sc * dy;
-    return (sc > T(0) && sc < T(1) && mx * mx + my * my < R1sq) ? sc : T(0);
+    T b = -(x0 * dx + y0 * dy);  // (closest-approach fraction) * dd
+    // closest approach inside the step (0 < b < dd) and inside the metal: |x0|^2 - b^2/dd < R1^2
+    if (!(b > T(0) && b < dd)) return T(0);
+    if (!((x0 * x0 + y0 * y0 - R1sq) * dd < b * b)) return T(0);
+    return b / dd;
 }
 
 // ------------------------------------------------------------------ surfaces

@@ -38,14 +38,12 @@ struct Queue {
     int *face;                         // surface crossed at exit (EV_LAT / EV_TOP / EV_BOT)
     int *key;                          // cost bucket of the ray (larger = more steps expected)
     int *perm;                         // integration order: slots sorted by descending cost bucket
-    unsigned int *count;               // [0] queued rays, [1] next ray (phase 1), [2] next ray (phase 2),
-                                       // [3] rays of phase 1 (the slowest, integrated first at low occupancy)
+    unsigned int *count;               // [0] queued rays, [1] next ray of the integration kernel
     unsigned int *bins;                // [nbins] bucket sizes, then [nbins] scatter cursors (nbins <= 256)
     long long cap;
 };
 
 constexpr int NBINS = 64;         // cost buckets of a single image
-constexpr int PHASE1_MIN_BIN = 24;  // |L| < 2^-6: rays close enough to the inner radius to be slow
 constexpr int NBINS_BATCH = 256;  // cost bucket x medium/mode of a batch
 constexpr size_t QUEUE_HEADER_BYTES = 4096;
 constexpr size_t QUEUE_SLOT_BYTES = 8 * sizeof(double) + 6 * sizeof(int) + sizeof(float4);
@@ -126,21 +124,16 @@ __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned lo
 
 // Longest-first order: a counting sort of the queue by descending cost bucket.  k_wf_sort_scan turns
 // the bucket sizes into scatter cursors, k_wf_sort_scatter writes the permutation.
-// min_bin: lowest bucket admitted to phase 1; cap1: most rays phase 1 may take
-__global__ void k_wf_sort_scan(Queue q, int nbins, int min_bin, unsigned int cap1);
+__global__ void k_wf_sort_scan(Queue q, int nbins);
 __global__ void k_wf_sort_scatter(Queue q);
 
-// phase 1 integrates the rays perm[0, count[3]) (launched with one warp per SM so that these slow rays
-// run at latency speed), phase 2 the rest perm[count[3], count[0]) with the full resident grid.
 template <int VAR, int MODE, int INTEG, int PREC>
-__global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q, int phase1) {
+__global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     typedef typename std::conditional<PREC == 0, Stepper64<VAR, MODE, INTEG>, StepperMixed<VAR, MODE, INTEG>>::type S;
     typedef typename S::real R;
     S st;
     st.vm = 0;
-    const unsigned int n1 = q.count[3];
-    const unsigned int first = phase1 ? 0u : n1, n = phase1 ? n1 : q.count[0];
-    unsigned int *next = q.count + (phase1 ? 1 : 2);
+    const unsigned int n = q.count[0];
     const int nev = p.R1 > 0.0 ? 4 : 3;
     const R tol = (R)p.h_or_tol, h0 = INTEG == I_RK4 ? (R)p.h_or_tol : (R)1e-3;
     const R conv = sizeof(R) == 8 ? (R)CROSS_REL_TOL : (R)2.4e-7;  // bracket resolution of the crossing search
@@ -157,7 +150,7 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q, int pha
     for (;;) {
         // ---- refill: a lane without a ray takes the next queued one
         if (phase == PH_IDLE) {
-            unsigned int k = first + atomicAdd(next, 1u);
+            unsigned int k = atomicAdd(q.count + 1, 1u);
             if (k < n) {
                 slot = q.perm[k];
                 st.load(q.x, q.y, q.z, q.vx, q.vy, q.vz, slot);
@@ -358,7 +351,7 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS, PHASE1_MIN_BIN, (unsigned int)(sms * 32));
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS);
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -373,8 +366,7 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
         if (e != cudaSuccess) return e;
         blocks_per_sm[slot] = nb > 0 ? nb : 1;
     }
-    k_wf_integrate<V, M, I, PREC><<<sms, 32, 0, st>>>(p, q, 1);
-    k_wf_integrate<V, M, I, PREC><<<blocks_per_sm[slot] * sms, pk, 0, st>>>(p, q, 0);
+    k_wf_integrate<V, M, I, PREC><<<blocks_per_sm[slot] * sms, pk, 0, st>>>(p, q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);
