@@ -80,6 +80,25 @@ def lib():
         L.orc_shade.argtypes = [C.POINTER(_Cloak), dp, dp, dp]
         L.orc_render.argtypes = [C.POINTER(_Cloak), C.POINTER(_Integ), C.POINTER(_Camera), C.c_int, C.c_int,
                                  C.c_uint64, C.POINTER(C.c_int64), C.c_long, dp, C.c_void_p, C.c_int]
+        # surrogate (surrogate_oracle.h)
+        ip = C.POINTER(C.c_int)
+        L.orc_gelu.restype = C.c_double
+        L.orc_gelu.argtypes = [C.c_double]
+        L.orc_gelu_grad.restype = C.c_double
+        L.orc_gelu_grad.argtypes = [C.c_double]
+        L.orc_mlp_nparams.restype = C.c_long
+        L.orc_mlp_nparams.argtypes = [C.c_int, ip]
+        L.orc_mlp_forward.argtypes = [C.c_int, ip, dp, C.c_long, dp, dp]
+        L.orc_mlp_backward.argtypes = [C.c_int, ip, dp, C.c_long, dp, dp, dp]
+        L.orc_sur_loss.restype = C.c_double
+        L.orc_sur_loss.argtypes = [C.c_int, C.c_long, dp, dp, dp, dp]
+        L.orc_adam_step.argtypes = [C.c_long, dp, dp, dp, dp, C.c_long, C.c_double, C.c_double, C.c_double,
+                                    C.c_double]
+        L.orc_sur_sample.argtypes = [C.c_uint64, C.c_uint64, C.c_double, C.c_double, dp, dp, ip, ip]
+        L.orc_sur_features.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, dp, dp, dp]
+        L.orc_sur_targets.restype = C.c_int
+        L.orc_sur_targets.argtypes = [C.c_double, C.c_double, dp, dp, C.c_void_p, dp]
+        L.orc_sur_reconstruct.argtypes = [C.c_double, C.c_double, dp, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -288,3 +307,98 @@ def render(cloak: Cloak, integ: Integrator, cam: Camera, mode, spp=1, seed=0, pi
     lib().orc_render(cloak.ref, integ.ref, cam.ref, mode, spp, seed, pix_ptr, npix, _dp(rgba),
                      recs.ctypes.data_as(C.c_void_p) if records else None, nthreads or os.cpu_count() or 1)
     return rgba, recs
+
+
+# ------------------------------------------------------------------ learned surrogate (surrogate_oracle.h)
+SUR_DIMS = (7, 256, 256, 256, 256, 5)
+
+
+def _dims(dims):
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    return len(dims) - 1, d, d.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def gelu(x: float) -> float:
+    return lib().orc_gelu(float(x))
+
+
+def gelu_grad(x: float) -> float:
+    return lib().orc_gelu_grad(float(x))
+
+
+def mlp_nparams(dims) -> int:
+    nl, d, dptr = _dims(dims)
+    return lib().orc_mlp_nparams(nl, dptr)
+
+
+def mlp_split(dims, params):
+    """[(W_l, b_l)] views of a flat parameter vector (W_l: dims[l+1] x dims[l])."""
+    out, o = [], 0
+    for l in range(len(dims) - 1):
+        nw = dims[l + 1] * dims[l]
+        out.append((params[o:o + nw].reshape(dims[l + 1], dims[l]), params[o + nw:o + nw + dims[l + 1]]))
+        o += nw + dims[l + 1]
+    return out
+
+
+def mlp_forward(dims, params, x):
+    nl, d, dptr = _dims(dims)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, dims[0])
+    y = np.zeros((x.shape[0], dims[-1]))
+    lib().orc_mlp_forward(nl, dptr, _dp(params), x.shape[0], _dp(x), _dp(y))
+    return y
+
+
+def mlp_backward(dims, params, x, dy):
+    """Gradient of sum(dy * network(x)) with respect to the flat parameters."""
+    nl, d, dptr = _dims(dims)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, dims[0])
+    dy = np.ascontiguousarray(dy, dtype=np.float64).reshape(-1, dims[-1])
+    g = np.zeros_like(params)
+    lib().orc_mlp_backward(nl, dptr, _dp(params), x.shape[0], _dp(x), _dp(dy), _dp(g))
+    return g
+
+
+def sur_loss(stage, y, t, mask):
+    y = np.ascontiguousarray(y, dtype=np.float64).reshape(-1, 5)
+    t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1, 5)
+    mask = np.ascontiguousarray(mask, dtype=np.float64).reshape(-1)
+    dy = np.zeros_like(y)
+    L = lib().orc_sur_loss(stage, y.shape[0], _dp(y), _dp(t), _dp(mask), _dp(dy))
+    return L, dy
+
+
+def adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In place on p, m, v (float64 contiguous arrays)."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    lib().orc_adam_step(p.size, _dp(p), _dp(g), _dp(m), _dp(v), step, lr, beta1, beta2, eps)
+
+
+def sur_sample(seed, i, R2=1.0, H=2.0):
+    P, d = np.zeros(3), np.zeros(3)
+    mode, variant = C.c_int(0), C.c_int(0)
+    lib().orc_sur_sample(seed, i, R2, H, _dp(P), _dp(d), C.byref(mode), C.byref(variant))
+    return P, d, mode.value, variant.value
+
+
+def sur_features(R1, R2, H, variant, mode, P, d):
+    x = np.zeros(7)
+    lib().orc_sur_features(R1, R2, H, variant, mode, _dp(_vec(P)), _dp(_vec(d)), _dp(x))
+    return x
+
+
+def sur_targets(R2, H, P, d, rec):
+    """(lateral, t[4]) of a traced record (numpy RECORD_DTYPE scalar)."""
+    r = np.array([rec], dtype=RECORD_DTYPE)
+    t = np.zeros(4)
+    ok = lib().orc_sur_targets(R2, H, _dp(_vec(P)), _dp(_vec(d)), r.ctypes.data_as(C.c_void_p), _dp(t))
+    return bool(ok), t
+
+
+def sur_reconstruct(R2, H, P, d, y):
+    y = np.ascontiguousarray(y[:4], dtype=np.float64)
+    pos, dr, tof = np.zeros(3), np.zeros(3), C.c_double(0)
+    lib().orc_sur_reconstruct(R2, H, _dp(_vec(P)), _dp(_vec(d)), _dp(y), _dp(pos), _dp(dr), C.byref(tof))
+    return pos, dr, tof.value
