@@ -186,12 +186,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--ref-pixels", type=int, default=1000, help="oracle pixels per image per step")
-    ap.add_argument("--cpu-pixels", type=int, default=15000, help="oracle pixels per image for cpu_baseline")
+    ap.add_argument("--cpu-pixels", type=int, default=100000, help="oracle pixels per image for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--profile-image", default=None,
                     help="VARIANT,MODE,ELEV: render only this image twice (for profilers), e.g. 1,1,20")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="render the step's 12 images through the batched path twice at --width x --height "
+                         "(default 480x270), for profilers")
     ap.add_argument("--width", type=int, default=None)
     ap.add_argument("--height", type=int, default=None)
     ap.add_argument("--schedule", default="batched", choices=["plain", "wavefront", "batched"])
@@ -230,6 +233,24 @@ def main():
         torch.cuda.synchronize()
         print(json.dumps({"profile_image": args.profile_image, "width": W, "height": H,
                           "mean_rgba": img.mean(dim=(0, 1)).tolist()}))
+        c.close()
+        return 0
+
+    if args.profile_batch:
+        W, H = args.width or 480, args.height or 270
+        c = ck.Cloak(ck.RADIAL).integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol, ck.FP64,
+                                           w.max_steps)
+        c.schedule(ck.SCHED_WAVEFRONT)
+        views = []
+        for v, m, e in w.images:
+            eye, tgt, up = inputs.camera_pose(e)
+            views.append((v, m, eye, tgt, up, w.hfov_deg,
+                          torch.empty((H, W, 4), dtype=torch.float32, device="cuda")))
+        for _ in range(2):
+            ck.cloak_render_batch(c.h, views, w.spp, w.seed)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_batch": True, "width": W, "height": H, "images": len(views),
+                          "mean_rgba": torch.stack([v[-1].mean(dim=(0, 1)) for v in views]).mean(0).tolist()}))
         c.close()
         return 0
 
@@ -383,7 +404,11 @@ def main():
         out["cpu_baseline"] = {"value": nr / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{args.cpu_pixels} seeded pixels x {w.spp} spp from each of the "
                                          f"{len(w.images)} images ({nr} rays), {dt:.1f} s"}
+        # axial angular momentum L = (x cross k)_z of each ray, conserved along it (read at the oracle's exit)
+        Lz = np.abs(o["exit_pos"][fin][:, 0] * o["exit_dir"][fin][:, 1] - o["exit_pos"][fin][:, 1] * o["exit_dir"][fin][:, 0])
         out["accuracy_vs_oracle"] = {"max_exit_dir_err_rad": float(err.max(initial=0)),
+                                     "max_exit_dir_err_rad_L_over_1e-3": float(err[Lz > 1e-3].max(initial=0)),
+                                     "rays_over_1e-9_rad_L_over_1e-3": int(((err > 1e-9) & (Lz > 1e-3)).sum()),
                                      "p999_exit_dir_err_rad": float(np.quantile(err, 0.999)) if len(err) else 0.0,
                                      "rays_over_1e-9_rad": int((err > 1e-9).sum()), "rays_compared": int(fin.sum()),
                                      "status_mismatch": int((g["status"] != o["status"]).sum()),

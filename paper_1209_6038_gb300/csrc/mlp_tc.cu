@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     if (threadIdx.x == 0) {
         const uint32_t idesc = bf16_idesc(N);
         bool ok = true;
+        int loaded = 0, consumed = 0;  // chunks whose TMA loads were issued / whose full barrier was seen
         for (int it = 0; it < nk + GEMM_STAGES - 1 && ok; ++it) {
             if (it < nk) {  // load chunk `it`
                 const int s = it % GEMM_STAGES;
@@ -101,12 +102,14 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
                 mbar_expect_tx(smem_u32(&full_bar[s]), a_bytes + b_bytes);
                 tma_load_2d(smem_u32(sa), &ta, it * GEMM_KCHUNK, m0, smem_u32(&full_bar[s]));
                 tma_load_2d(smem_u32(sb), &tb, it * GEMM_KCHUNK, 0, smem_u32(&full_bar[s]));
+                loaded = it + 1;
             }
             const int j = it - (GEMM_STAGES - 1);
             if (j >= 0 && j < nk) {  // multiply chunk j
                 const int s = j % GEMM_STAGES;
                 ok = mbar_wait(smem_u32(&full_bar[s]), (j / GEMM_STAGES) & 1);
                 if (!ok) break;
+                consumed = j + 1;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 unsigned char *sa = smem + s * (a_bytes + b_bytes), *sb = sa + a_bytes;
                 const uint64_t ad = sw128_desc(smem_u32(sa)), bd = sw128_desc(smem_u32(sb));
@@ -125,7 +128,12 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&done_bar)));
-        if (!ok) failed = 1;
+        if (!ok) {
+            failed = 1;
+            // let the copies still in flight land before the CTA's shared memory is released (bounded)
+            for (int c = consumed; c < loaded; ++c)
+                if (!mbar_wait(smem_u32(&full_bar[c % GEMM_STAGES]), (c / GEMM_STAGES) & 1)) break;
+        }
     }
     __syncwarp();
     const bool done = mbar_wait(smem_u32(&done_bar), 0);
