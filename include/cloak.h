@@ -51,8 +51,11 @@ enum {
     CLOAK_MIXED = 1,   /* RK stepping in FP32 (right-hand sides, stage combinations, step control) with
                           float-float state accumulation; whole steps in FP64 where r < R1 + 0.02; entry
                           and exit interface solves in FP64 (wavefront schedule only) */
-    CLOAK_MIXED_FF = 2 /* as CLOAK_MIXED without the FP64 band: stage positions in float-float keep
+    CLOAK_MIXED_FF = 2, /* as CLOAK_MIXED without the FP64 band: stage positions in float-float keep
                           r - R1 accurate down to the inner radius */
+    CLOAK_SURROGATE = 3 /* learned surrogate (see cloak_surrogate_train) for rays that enter through the
+                          lateral surface and whose predicted error passes the gate; the FP64 integrator
+                          for all others (wavefront schedule, cloak_render / cloak_render_records) */
 };
 /* kernel schedule */
 enum {
@@ -105,7 +108,8 @@ int cloak_camera_set(cloak_t *h, const double eye[3], const double target[3], co
                      int width, int height);
 /* Integrator (Sect. 4 and its adaptive form): kind CLOAK_RK4 with h_or_tol = step h > 0, or CLOAK_DP45
  * with h_or_tol = tolerance > 0 (error norm max_i |err_i| / (tol + tol max(|y_i|, |y_i'|)), safety 0.9,
- * step factor in [0.2, 5], initial step 1e-3).  precision CLOAK_FP64 or CLOAK_MIXED.
+ * step factor in [0.2, 5], initial step 1e-3).  precision CLOAK_FP64, CLOAK_MIXED, CLOAK_MIXED_FF or
+ * CLOAK_SURROGATE.
  * max_steps >= 1 bounds the step attempts of one ray. */
 int cloak_set_integrator(cloak_t *h, int kind, double h_or_tol, int precision, long max_steps);
 /* Medium of CLOAK_TEST_UNIAXIAL_CONST (Eq. 1): eps_o, eps_e > 0, optic axis c_hat (host, 3 doubles,
@@ -189,6 +193,51 @@ int cloak_mlp_gemm(const void *dev_a, const void *dev_b, float *dev_c, int M, in
  * work overlaps (other streams, other threads, other handles) race on it and must be serialised. */
 int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsigned long long seed, void *dev_rgba,
                          size_t bytes, void *cuda_stream);
+
+/* ---- learned surrogate of the exit state (the paper has none) -------------------------------------
+ * A multilayer perceptron 7 -> 256 -> 256 -> 256 -> 256 -> 5 (GELU, tanh form; BF16 weights, FP32
+ * accumulation on the tensor cores) maps a ray entering the lateral surface r = R2 -- entry height and
+ * azimuth, the two angles of its vacuum direction in the local (r, theta, z) frame, polarization bit,
+ * variant bit, R1/R2 -- to its exit through r = R2: exit height, cos and sin of the exit azimuth's
+ * departure from the straight line's, time of flight, and a confidence output (predicted log10 of its
+ * own exit error: the larger of the exit-direction angle and the exit-point distance / R2).  The exit
+ * direction follows from the exit azimuth because both media conserve k_z and L_z (rotation and
+ * translation symmetry of Eqs. 14, 15).  The model belongs to the handle; its geometry is the handle's
+ * at training time, and renders of another geometry integrate every ray (outside the support). */
+
+/* Train the handle's surrogate on n_rays rays that the handle's integrator traces (FP64 or mixed as
+ * set; both variants and polarizations, entry points uniform on the lateral surface, directions
+ * cosine-weighted about the inward normal, splitmix64 stream of `seed`).  Stage 1: `epochs` passes of
+ * Adam on the regression outputs (masked squared error; lateral exits only); stage 2: epochs / 3 passes
+ * on the confidence output alone (L1 against the stage-1 model's log10 exit error; 0 for rays that do
+ * not leave laterally).  n_rays in [19456, 2^31 - 1].  Allocates about 170 bytes per ray for the
+ * duration of the call; synchronises cuda_stream. */
+int cloak_surrogate_train(cloak_t *h, long n_rays, unsigned long long seed, int epochs, void *cuda_stream);
+/* Checkpoint: the FP32 weights, the Adam moments, the geometry, the gate and the training summary as a
+ * flat binary file with a header ("CKSURR01").  load replaces the handle's surrogate. */
+int cloak_surrogate_save(cloak_t *h, const char *path);
+int cloak_surrogate_load(cloak_t *h, const char *path);
+/* Gate of CLOAK_SURROGATE renders: a ray keeps the surrogate's exit when its predicted log10 error is
+ * <= max_log10_err (default -3) and its predicted exit height is inside the cylinder. */
+int cloak_surrogate_set_gate(cloak_t *h, double max_log10_err);
+/* Training summary (host, 8 doubles): final stage-1 loss, final stage-2 loss, lateral-exit fraction of
+ * the training rays, rays, seconds in total, seconds tracing the training rays, optimiser steps, batch
+ * size.  CLOAK_ESTATE without a trained surrogate. */
+int cloak_surrogate_info(cloak_t *h, double info[8]);
+/* Parameters as one flat FP32 host vector of n = 200709 values (per layer: W_l, out x in row-major,
+ * then b_l).  set = 0 copies them into host; set = 1 loads host into the network and clears the Adam
+ * state.  A handle without a surrogate gets one with seeded initial weights first. */
+int cloak_surrogate_params(cloak_t *h, float *host, long n, int set);
+/* Network outputs for n input rows: dev_x FP32 [n x 7] (device), dev_y FP32 [n x 5] (device).
+ * Synchronises cuda_stream. */
+int cloak_surrogate_forward(cloak_t *h, const float *dev_x, long n, float *dev_y, void *cuda_stream);
+/* One training step on a given batch: dev_x FP32 [n x 7], dev_t FP32 [n x 8] (targets of outputs 0..3,
+ * confidence target, mask, two unused), n % 128 == 0.  stage 1 or 2 selects the loss (see train).
+ * host_grad (nullable): receives the gradient of the mean loss, flat layout of cloak_surrogate_params.
+ * lr > 0 also applies one Adam step (beta 0.9 / 0.999, eps 1e-8) with that learning rate.
+ * Synchronises cuda_stream. */
+int cloak_surrogate_step(cloak_t *h, const float *dev_x, const float *dev_t, long n, int stage, double lr,
+                         float *host_grad, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libcloak.so")
 RADIAL, AZIMUTHAL, TEST_UNIAXIAL_CONST = 0, 1, 100
 POL_ORDINARY, POL_EXTRAORDINARY = 0, 1
 RK4, DP45 = 0, 1
-FP64, MIXED, MIXED_FF = 0, 1, 2
+FP64, MIXED, MIXED_FF, SURROGATE = 0, 1, 2, 3
 SCHED_PLAIN, SCHED_WAVEFRONT = 0, 1
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
 RAY_STATUS = {0: "MISSED", 1: "EXITED", 2: "HIT_METAL_EXITED", 3: "NO_TRANSMISSION", 4: "TIR",
@@ -49,6 +49,15 @@ SIGNATURES = {
     "cloak_render_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p]),
     "cloak_render_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
+    "cloak_surrogate_train": (C.c_int, [C.c_void_p, C.c_long, C.c_ulonglong, C.c_int, C.c_void_p]),
+    "cloak_surrogate_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "cloak_surrogate_load": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "cloak_surrogate_set_gate": (C.c_int, [C.c_void_p, C.c_double]),
+    "cloak_surrogate_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "cloak_surrogate_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_long, C.c_int]),
+    "cloak_surrogate_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
+    "cloak_surrogate_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_long, C.c_int, C.c_double,
+                                       C.POINTER(C.c_float), C.c_void_p]),
 }
 
 class View(C.Structure):
@@ -191,6 +200,61 @@ def cloak_render_noalloc(h, polarization, spp, seed, rgba, stream=None):
     """Allocation-free render (fixed library-owned device array; at most 1048576 samples per call)."""
     return _check(load().cloak_render_noalloc(h, polarization, spp, seed, C.c_void_p(rgba.data_ptr()),
                                               rgba.numel() * rgba.element_size(), _stream_ptr(stream)))
+
+
+# ------------------------------------------------------------------ learned surrogate
+SUR_NPARAMS = 200709
+SUR_INFO_KEYS = ("loss_stage1", "loss_stage2", "lateral_fraction", "rays", "seconds", "seconds_tracing",
+                 "optimizer_steps", "batch")
+
+
+def cloak_surrogate_train(h, n_rays, seed=0, epochs=20, stream=None):
+    return _check(load().cloak_surrogate_train(h, n_rays, seed, epochs, _stream_ptr(stream)))
+
+
+def cloak_surrogate_save(h, path):
+    return _check(load().cloak_surrogate_save(h, os.fsencode(path)))
+
+
+def cloak_surrogate_load(h, path):
+    return _check(load().cloak_surrogate_load(h, os.fsencode(path)))
+
+
+def cloak_surrogate_set_gate(h, max_log10_err):
+    return _check(load().cloak_surrogate_set_gate(h, max_log10_err))
+
+
+def cloak_surrogate_info(h) -> dict:
+    buf = (C.c_double * 8)()
+    _check(load().cloak_surrogate_info(h, buf))
+    return dict(zip(SUR_INFO_KEYS, list(buf)))
+
+
+def cloak_surrogate_params(h, values=None) -> np.ndarray:
+    """Get (values None) or set the flat FP32 parameter vector (per layer W_l then b_l)."""
+    if values is None:
+        out = np.zeros(SUR_NPARAMS, np.float32)
+        _check(load().cloak_surrogate_params(h, out.ctypes.data_as(C.POINTER(C.c_float)), SUR_NPARAMS, 0))
+        return out
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    _check(load().cloak_surrogate_params(h, v.ctypes.data_as(C.POINTER(C.c_float)), v.size, 1))
+    return v
+
+
+def cloak_surrogate_forward(h, x, y, stream=None):
+    """x: float32 CUDA tensor (n, 7); y: float32 CUDA tensor (n, 5)."""
+    return _check(load().cloak_surrogate_forward(h, C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(y.data_ptr()),
+                                                 _stream_ptr(stream)))
+
+
+def cloak_surrogate_step(h, x, t, stage=1, lr=0.0, grad=True, stream=None):
+    """One batch (x (n, 7), t (n, 8) float32 CUDA tensors, n % 128 == 0): the gradient of the mean loss
+    (flat numpy vector) and, with lr > 0, one Adam step."""
+    g = np.zeros(SUR_NPARAMS, np.float32) if grad else None
+    _check(load().cloak_surrogate_step(h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0], stage, lr,
+                                       g.ctypes.data_as(C.POINTER(C.c_float)) if grad else None,
+                                       _stream_ptr(stream)))
+    return g
 
 
 # ------------------------------------------------------------------ convenience

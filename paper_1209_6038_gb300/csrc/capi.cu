@@ -12,6 +12,7 @@
 
 #include "batch.h"
 #include "internal.h"
+#include "surrogate.h"
 #include "wavefront.cuh"
 
 struct cloak {
@@ -42,6 +43,8 @@ struct cloak {
     cudaGraphExec_t graph_exec;
     cudaEvent_t graph_done;
     unsigned long long graph_key;
+    // learned surrogate of the exit state (created by training, loading or setting parameters)
+    ck::SurNet *sur;
 };
 
 static thread_local std::string g_err;
@@ -141,11 +144,33 @@ static int run_wavefront(cloak *h, const ck::Params &p, int pol, int spp, unsign
     float4 *samples = nullptr;
     int rc = wavefront_scratch(h, cap, q, &samples);
     if (rc) return rc;
+    // learned surrogate: only for the geometry it was trained on (elsewhere every ray is integrated)
+    ck::SurRenderCtx sctx;
+    ck::WfHook hook{ck::sur_render_hook, &sctx};
+    const ck::WfHook *hk = nullptr;
+    if (h->precision == CLOAK_SURROGATE) {
+        if (!h->sur || !h->sur->trained) return fail(CLOAK_ESTATE, "CLOAK_SURROGATE needs a trained surrogate");
+        const ck::SurNet *sn = h->sur;
+        const bool same = std::fabs(sn->R1 - h->R1) <= 1e-12 * h->R2 && std::fabs(sn->R2 - h->R2) <= 1e-12 * h->R2 &&
+                          std::fabs(sn->H - h->H) <= 1e-12 * h->H &&
+                          (h->variant == CLOAK_RADIAL || h->variant == CLOAK_AZIMUTHAL);
+        if (same) {
+            sctx.s = h->sur;
+            sctx.p = p;
+            sctx.mode = pol;
+            sctx.spp = spp;
+            sctx.seed = seed;
+            sctx.samples = recs ? nullptr : samples;
+            sctx.recs = recs;
+            sctx.cap = cap;
+            hk = &hook;
+        }
+    }
     cudaEvent_t *ev = h->timing ? h->ev : nullptr;
     if (ev) cudaEventRecord(ev[0], st);
     cudaError_t e = cudaMemsetAsync(q.count, 0, ck::QUEUE_HEADER_BYTES, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    e = ck::launch_wavefront(p, pol, spp, seed, q, recs ? nullptr : samples, recs, h->packet, st, ev);
+    e = ck::launch_wavefront(p, pol, spp, seed, q, recs ? nullptr : samples, recs, h->packet, st, ev, hk);
     if (e != cudaSuccess) return cuda_fail(e, "wavefront launch");
     if (!recs) {
         e = ck::launch_resolve(p.W * p.Hp, spp, samples, out, st);
@@ -225,6 +250,7 @@ cloak_t *cloak_create(int variant, double R1, double R2, double height) {
     h->graph_exec = nullptr;
     h->graph_done = nullptr;
     h->graph_key = 0;
+    h->sur = nullptr;
     g_err.clear();
     return h;
 }
@@ -239,6 +265,7 @@ void cloak_destroy(cloak_t *h) {
     if (h->batch_host) cudaFreeHost(h->batch_host);
     if (h->batch_dev) cudaFree(h->batch_dev);
     if (h->scratch) cudaFree(h->scratch);
+    ck::sur_destroy(h->sur);
     if (h->timing)
         for (int i = 0; i < 5; ++i) cudaEventDestroy(h->ev[i]);
     delete h;
@@ -311,7 +338,8 @@ int cloak_set_integrator(cloak_t *h, int kind, double h_or_tol, int precision, l
     if (!h) return fail(CLOAK_EINVAL, "null handle");
     if (kind != CLOAK_RK4 && kind != CLOAK_DP45) return fail(CLOAK_EINVAL, "unknown integrator %d", kind);
     if (!(std::isfinite(h_or_tol) && h_or_tol > 0)) return fail(CLOAK_EINVAL, "step / tolerance must be > 0");
-    if (precision != CLOAK_FP64 && precision != CLOAK_MIXED && precision != CLOAK_MIXED_FF)
+    if (precision != CLOAK_FP64 && precision != CLOAK_MIXED && precision != CLOAK_MIXED_FF &&
+        precision != CLOAK_SURROGATE)
         return fail(CLOAK_EINVAL, "unknown precision %d", precision);
     if (max_steps < 1 || max_steps > 2000000000L) return fail(CLOAK_EINVAL, "max_steps out of range");
     h->integ = kind;
@@ -368,7 +396,7 @@ int cloak_render(cloak_t *h, int polarization, int spp, unsigned long long seed,
     if ((rc = use_device(h))) return rc;
     if (h->schedule == CLOAK_SCHED_WAVEFRONT)
         return run_wavefront(h, p, polarization, spp, seed, (float4 *)dev_rgba, nullptr, (cudaStream_t)cuda_stream);
-    if (h->precision != CLOAK_FP64) return fail(CLOAK_EINVAL, "mixed precision needs the wavefront schedule");
+    if (h->precision != CLOAK_FP64) return fail(CLOAK_EINVAL, "this precision needs the wavefront schedule");
     if (h->timing) cudaEventRecord(h->ev[0], (cudaStream_t)cuda_stream);
     cudaError_t e = ck::launch_render_plain(p, polarization, spp, seed, (float4 *)dev_rgba, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "render launch");
@@ -396,7 +424,7 @@ int cloak_render_records(cloak_t *h, int polarization, int spp, unsigned long lo
     if (h->schedule == CLOAK_SCHED_WAVEFRONT)
         return run_wavefront(h, p, polarization, spp, seed, nullptr, (cloak_record *)dev_records,
                              (cudaStream_t)cuda_stream);
-    if (h->precision != CLOAK_FP64) return fail(CLOAK_EINVAL, "mixed precision needs the wavefront schedule");
+    if (h->precision != CLOAK_FP64) return fail(CLOAK_EINVAL, "this precision needs the wavefront schedule");
     if (h->timing) cudaEventRecord(h->ev[0], (cudaStream_t)cuda_stream);
     cudaError_t e = ck::launch_records_plain(p, polarization, spp, seed, (cloak_record *)dev_records,
                                              (cudaStream_t)cuda_stream);
@@ -479,6 +507,8 @@ extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nview
         return fail(CLOAK_ESTATE, "batched rendering needs a radial or azimuthal cloak handle");
     if (!views || nviews < 1 || nviews > 65536) return fail(CLOAK_EINVAL, "need 1..65536 views");
     if (spp < 1 || spp > 65536) return fail(CLOAK_EINVAL, "spp must be in [1, 65536]");
+    if (h->precision == CLOAK_SURROGATE)
+        return fail(CLOAK_EINVAL, "the learned surrogate runs in cloak_render and cloak_render_records");
     ck::Params p;
     int rc = make_params(h, p);
     if (rc) return rc;
@@ -606,6 +636,8 @@ extern "C" int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsig
     if (cap > NOALLOC_MAX_SAMPLES)
         return fail(CLOAK_EINVAL, "width*height*spp = %lld exceeds the no-alloc limit of %lld samples", cap,
                     NOALLOC_MAX_SAMPLES);
+    if (h->precision == CLOAK_SURROGATE)
+        return fail(CLOAK_EINVAL, "the learned surrogate allocates its scratch; use cloak_render");
     ck::Params p;
     int rc = make_params(h, p);
     if (rc) return rc;
@@ -625,4 +657,105 @@ extern "C" int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsig
     e = ck::launch_resolve(p.W * p.Hp, spp, samples, (float4 *)dev_rgba, st);
     if (e != cudaSuccess) return cuda_fail(e, "resolve launch");
     return CLOAK_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Learned surrogate
+// ---------------------------------------------------------------------------------------------
+static int ensure_surrogate(cloak *h) {
+    if (h->sur) return CLOAK_OK;
+    if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
+        return fail(CLOAK_ESTATE, "the surrogate needs a radial or azimuthal cloak handle");
+    const char *why = "";
+    h->sur = ck::sur_create(h->R1, h->R2, h->H, 0x5eedull, &why);
+    if (!h->sur) return fail(CLOAK_ENOMEM, "%s", why);
+    return CLOAK_OK;
+}
+
+extern "C" int cloak_surrogate_train(cloak_t *h, long n_rays, unsigned long long seed, int epochs, void *cuda_stream) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (n_rays < 19456 || n_rays > 2147483647L) return fail(CLOAK_EINVAL, "n_rays must be in [19456, 2^31 - 1]");
+    if (epochs < 1 || epochs > 100000) return fail(CLOAK_EINVAL, "epochs must be in [1, 100000]");
+    int rc = use_device(h);
+    if (rc) return rc;
+    if ((rc = ensure_surrogate(h))) return rc;
+    ck::Params p;
+    if ((rc = make_params(h, p))) return rc;
+    h->sur->R1 = h->R1;
+    h->sur->R2 = h->R2;
+    h->sur->H = h->H;
+    std::string why;
+    rc = ck::sur_train(h->sur, p, n_rays, seed, epochs, (cudaStream_t)cuda_stream, why);
+    if (rc) return fail(rc, "surrogate training: %s", why.c_str());
+    return CLOAK_OK;
+}
+
+extern "C" int cloak_surrogate_save(cloak_t *h, const char *path) {
+    if (!h || !path) return fail(CLOAK_EINVAL, "null argument");
+    if (!h->sur) return fail(CLOAK_ESTATE, "the handle has no surrogate");
+    int rc = use_device(h);
+    if (rc) return rc;
+    std::string why;
+    rc = ck::sur_save(h->sur, path, why);
+    return rc ? fail(rc, "%s", why.c_str()) : CLOAK_OK;
+}
+
+extern "C" int cloak_surrogate_load(cloak_t *h, const char *path) {
+    if (!h || !path) return fail(CLOAK_EINVAL, "null argument");
+    int rc = use_device(h);
+    if (rc) return rc;
+    if ((rc = ensure_surrogate(h))) return rc;
+    std::string why;
+    rc = ck::sur_load(h->sur, path, why);
+    return rc ? fail(rc, "%s", why.c_str()) : CLOAK_OK;
+}
+
+extern "C" int cloak_surrogate_set_gate(cloak_t *h, double max_log10_err) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (!std::isfinite(max_log10_err)) return fail(CLOAK_EINVAL, "gate must be finite");
+    if (!h->sur) return fail(CLOAK_ESTATE, "the handle has no surrogate");
+    h->sur->gate = (float)max_log10_err;
+    return CLOAK_OK;
+}
+
+extern "C" int cloak_surrogate_info(cloak_t *h, double info[8]) {
+    if (!h || !info) return fail(CLOAK_EINVAL, "null argument");
+    if (!h->sur || !h->sur->trained) return fail(CLOAK_ESTATE, "the handle has no trained surrogate");
+    for (int i = 0; i < 8; ++i) info[i] = h->sur->info[i];
+    return CLOAK_OK;
+}
+
+extern "C" int cloak_surrogate_params(cloak_t *h, float *host, long n, int set) {
+    if (!h || !host) return fail(CLOAK_EINVAL, "null argument");
+    if (n != ck::sur_nparams()) return fail(CLOAK_EINVAL, "the network has %lld parameters", ck::sur_nparams());
+    int rc = use_device(h);
+    if (rc) return rc;
+    if ((rc = ensure_surrogate(h))) return rc;
+    cudaError_t e = set ? ck::sur_set_params(h->sur, host) : ck::sur_get_params(h->sur, host);
+    return e == cudaSuccess ? CLOAK_OK : cuda_fail(e, "surrogate parameters");
+}
+
+extern "C" int cloak_surrogate_forward(cloak_t *h, const float *dev_x, long n, float *dev_y, void *cuda_stream) {
+    if (!h || !dev_x || !dev_y) return fail(CLOAK_EINVAL, "null argument");
+    if (n < 1 || n > 2147483647L) return fail(CLOAK_EINVAL, "n out of range");
+    if (!h->sur) return fail(CLOAK_ESTATE, "the handle has no surrogate");
+    int rc = use_device(h);
+    if (rc) return rc;
+    std::string why;
+    rc = ck::sur_forward_rows(h->sur, dev_x, n, dev_y, (cudaStream_t)cuda_stream, why);
+    return rc ? fail(rc, "%s", why.c_str()) : CLOAK_OK;
+}
+
+extern "C" int cloak_surrogate_step(cloak_t *h, const float *dev_x, const float *dev_t, long n, int stage, double lr,
+                                    float *host_grad, void *cuda_stream) {
+    if (!h || !dev_x || !dev_t) return fail(CLOAK_EINVAL, "null argument");
+    if (n < 128 || n % 128 || n > (1L << 24)) return fail(CLOAK_EINVAL, "n must be a multiple of 128 in [128, 2^24]");
+    if (stage != 1 && stage != 2) return fail(CLOAK_EINVAL, "stage must be 1 or 2");
+    if (!(lr >= 0) || !std::isfinite(lr)) return fail(CLOAK_EINVAL, "lr must be >= 0");
+    if (!h->sur) return fail(CLOAK_ESTATE, "the handle has no surrogate");
+    int rc = use_device(h);
+    if (rc) return rc;
+    std::string why;
+    rc = ck::sur_batch_grad(h->sur, dev_x, dev_t, n, stage, lr, host_grad, (cudaStream_t)cuda_stream, why);
+    return rc ? fail(rc, "%s", why.c_str()) : CLOAK_OK;
 }

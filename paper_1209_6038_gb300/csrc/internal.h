@@ -47,19 +47,28 @@ inline cudaError_t launch_trace_rays(const Params &p, int mode, const double *ra
 }
 
 struct Queue;
+// A step run between the entry kernel and the sort of the wavefront schedule (the learned surrogate
+// finishes the rays it is confident about there).
+struct WfHook {
+    cudaError_t (*fn)(void *ctx, const Queue &q, cudaStream_t st);
+    void *ctx;
+};
 template <int V>
 cudaError_t launch_wavefront_v(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q,
-                               float4 *samples, cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev);
-extern template cudaError_t launch_wavefront_v<0>(const Params &, int, int, unsigned long long, const Queue &, float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *);
-extern template cudaError_t launch_wavefront_v<1>(const Params &, int, int, unsigned long long, const Queue &, float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *);
-extern template cudaError_t launch_wavefront_v<2>(const Params &, int, int, unsigned long long, const Queue &, float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *);
+                               float4 *samples, cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev,
+                               const WfHook *hook);
+extern template cudaError_t launch_wavefront_v<0>(const Params &, int, int, unsigned long long, const Queue &, float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *, const WfHook *);
+extern template cudaError_t launch_wavefront_v<1>(const Params &, int, int, unsigned long long, const Queue &, float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *, const WfHook *);
+extern template cudaError_t launch_wavefront_v<2>(const Params &, int, int, unsigned long long, const Queue &, float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *, const WfHook *);
 // ev (nullable): ev[1] after entry, ev[2] after integration, ev[3] after exit (ev[0] is recorded by the caller)
+// hook (nullable): run after the entry kernel, before the sort
 inline cudaError_t launch_wavefront(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q,
                                     float4 *samples, cloak_record *recs, int packet, cudaStream_t st,
-                                    cudaEvent_t *ev) {
-    if (p.variant == V_RADIAL) return launch_wavefront_v<0>(p, mode, spp, seed, q, samples, recs, packet, st, ev);
-    if (p.variant == V_AZIMUTHAL) return launch_wavefront_v<1>(p, mode, spp, seed, q, samples, recs, packet, st, ev);
-    return launch_wavefront_v<2>(p, mode, spp, seed, q, samples, recs, packet, st, ev);
+                                    cudaEvent_t *ev, const WfHook *hook = nullptr) {
+    if (p.variant == V_RADIAL) return launch_wavefront_v<0>(p, mode, spp, seed, q, samples, recs, packet, st, ev, hook);
+    if (p.variant == V_AZIMUTHAL)
+        return launch_wavefront_v<1>(p, mode, spp, seed, q, samples, recs, packet, st, ev, hook);
+    return launch_wavefront_v<2>(p, mode, spp, seed, q, samples, recs, packet, st, ev, hook);
 }
 cudaError_t launch_resolve(int npix, int spp, const float4 *samples, float4 *out, cudaStream_t st);
 

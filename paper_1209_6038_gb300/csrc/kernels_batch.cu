@@ -2,6 +2,8 @@
 // through one camera/entry kernel, one cost-ordered device queue, ONE persistent integration kernel
 // with the medium selected per ray at run time, one exit kernel and one resolve kernel.
 #include "batch.h"
+#include "sur_physics.cuh"
+#include "surrogate.h"
 #include "wavefront.cuh"
 
 namespace ck {
@@ -60,8 +62,9 @@ __global__ void __launch_bounds__(128) k_batch_entry(Params p, const ViewDev *vi
     }
     double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
     double w_out = transmission_out(mode, mat[0], mat[1], c, n_in, mk0);
-    // queue key: cost bucket (major, slowest first after the descending sort) and medium/mode (minor)
-    queue_append(q, y, w_out, (int)g, cost_bucket(y, k0) * 4 + vw.vm);
+    // queue key: medium/mode (major: one segment of the sorted queue per medium) and cost bucket (minor,
+    // slowest first within a segment after the descending sort)
+    queue_append(q, y, w_out, (int)g, batch_key(vw.vm, cost_bucket(y, k0)));
 }
 
 __global__ void __launch_bounds__(128) k_batch_exit(Params p, const ViewDev *views, int nviews, int spp,
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(128) k_batch_exit(Params p, const ViewDev *vie
         double o[3], d[3];
         view_camera_ray(vw, (int)(pix % vw.W), (int)(pix / vw.W), s, spp, seed, o, d);
         Params pv = p;
-        int vm = q.key[k] & 3;
+        int vm = key_vm(q.key[k]);
         pv.variant = vm >> 1;
         cloak_record rec;
         float rgb[3];
@@ -131,6 +134,87 @@ static cudaError_t batch_ip(const Params &p, const ViewDev *views, int nviews, i
     k_batch_resolve<<<(unsigned)((total_pix + 255) / 256), 256, 0, st>>>(views, nviews, spp, total_pix, samples);
     mark(ev, 4, st);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ surrogate training rays
+// Ray i of the seeded training set, started half a unit outside its entry point so that the
+// entry search finds that point; its network inputs go to X_all, its targets (after the exit
+// kernel) to T_all.
+__global__ void __launch_bounds__(128) k_sur_gen_entry(Params p, long long n, unsigned long long seed, Queue q,
+                                                       float *X_all, float *T_all) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double P[3], d[3];
+    int mode, variant;
+    sur_sample(seed, (unsigned long long)i, p.R2, p.H, P, d, mode, variant);
+    float x[SUR_IN];
+    sur_features(p.R1, p.R2, p.H, variant, mode, P, d, x);
+    float *X = X_all + i * SUR_XSTRIDE, *T = T_all + i * SUR_TSTRIDE;
+#pragma unroll
+    for (int j = 0; j < SUR_IN; ++j) X[j] = x[j];
+    X[SUR_IN] = 0.f;
+#pragma unroll
+    for (int j = 0; j < SUR_TSTRIDE; ++j) T[j] = 0.f;
+    double o[3] = {P[0] - 0.5 * d[0], P[1] - 0.5 * d[1], P[2] - 0.5 * d[2]}, y[6], k0[3], n_in[3], mat[5];
+    Params pv = p;
+    pv.variant = variant ? V_AZIMUTHAL : V_RADIAL;
+    cloak_record rec;
+    float rgb[3];
+    const bool inside = mode ? enter<M_EXT>(pv, o, d, rec, rgb, y, k0, n_in, mat)
+                             : enter<M_ORD>(pv, o, d, rec, rgb, y, k0, n_in, mat);
+    if (!inside) return;
+    queue_append(q, y, 1.0, (int)i, batch_key(2 * variant + mode, cost_bucket(y, k0)));
+}
+
+__global__ void __launch_bounds__(128) k_sur_gen_exit(Params p, unsigned long long seed, Queue q, float *T_all) {
+    const unsigned int n = q.count[0];
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const long long i = q.id[k];
+        double P[3], d[3];
+        int mode, variant;
+        sur_sample(seed, (unsigned long long)i, p.R2, p.H, P, d, mode, variant);
+        Params pv = p;
+        pv.variant = variant ? V_AZIMUTHAL : V_RADIAL;
+        cloak_record rec;
+        float rgb[3], t[4];
+        exit_slot(pv, mode, q, k, d, rec, rgb);
+        float *T = T_all + i * SUR_TSTRIDE;
+        const bool lateral = sur_targets(p.R2, p.H, P, d, rec, t);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) T[j] = lateral ? t[j] : 0.f;
+        T[4] = 0.f;
+        T[5] = lateral ? 1.f : 0.f;
+        T[6] = (float)rec.status;
+        T[7] = (float)rec.steps;
+    }
+}
+
+template <int I, int PREC>
+static cudaError_t sur_data_ip(const Params &p, long long n, unsigned long long seed, const Queue &q, float *X_all,
+                               float *T_all, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(q.count, 0, QUEUE_HEADER_BYTES, st);
+    if (e != cudaSuccess) return e;
+    k_sur_gen_entry<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(p, n, seed, q, X_all, T_all);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH);
+    k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V_ANY, V_ANY, I, PREC>, 128, 0);
+    if (e != cudaSuccess) return e;
+    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<(nb > 0 ? nb : 1) * sms, 128, 0, st>>>(p, q);
+    k_sur_gen_exit<<<sms * 16, 128, 0, st>>>(p, seed, q, T_all);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_data(const Params &p, long long n, unsigned long long seed, const Queue &q, float *X_all,
+                            float *T_all, cudaStream_t st) {
+    if (p.integ == I_RK4)
+        return p.precision ? sur_data_ip<I_RK4, 1>(p, n, seed, q, X_all, T_all, st)
+                           : sur_data_ip<I_RK4, 0>(p, n, seed, q, X_all, T_all, st);
+    return p.precision ? sur_data_ip<I_DP45, 1>(p, n, seed, q, X_all, T_all, st)
+                       : sur_data_ip<I_DP45, 0>(p, n, seed, q, X_all, T_all, st);
 }
 
 cudaError_t launch_batch(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,

@@ -20,17 +20,26 @@ __global__ void k_wf_resolve(int npix, int spp, const float4 *samples, float4 *o
 __global__ void k_wf_sort_scan(Queue q, int nbins) {
     if (threadIdx.x != 0) return;
     unsigned int off = 0;
+    for (int v = 3; v >= 0; --v) {  // empty segments for the media a single image does not use
+        q.bins[SEG_OFFSET + 2 * v] = 0;
+        q.bins[SEG_OFFSET + 2 * v + 1] = 0;
+    }
     for (int b = nbins - 1; b >= 0; --b) {  // descending key: slowest rays first
         unsigned int c = q.bins[b];
         q.bins[NBINS_BATCH + b] = off;
+        if (b % NBINS == NBINS - 1) q.bins[SEG_OFFSET + 2 * key_vm(b)] = off;
+        q.bins[SEG_OFFSET + 2 * key_vm(b) + 1] += c;
         off += c;
     }
+    q.count[2] = off;
 }
 
 __global__ void k_wf_sort_scatter(Queue q) {
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        unsigned int pos = atomicAdd(q.bins + NBINS_BATCH + q.key[k], 1u);
+        const int key = q.key[k];
+        if (key < 0) continue;  // finished before the integration (learned surrogate)
+        unsigned int pos = atomicAdd(q.bins + NBINS_BATCH + key, 1u);
         q.perm[pos] = (int)k;
     }
 }

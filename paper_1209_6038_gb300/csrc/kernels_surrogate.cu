@@ -1,0 +1,112 @@
+// kernels_surrogate.cu -- the learned surrogate inside a render: network inputs of the queued rays, and
+// the gate that finishes the rays whose prediction it trusts (exit rebuilt from k_z / L_z conservation,
+// Eq. 12 factor of the exit face, room lookup) and takes them out of the integration.
+#include "sur_physics.cuh"
+#include "wavefront.cuh"
+
+namespace ck {
+
+__global__ void __launch_bounds__(256) k_sur_features(Params p, int mode, int spp, unsigned long long seed, Queue q,
+                                                      __nv_bfloat16 *X, unsigned char *elig) {
+    const unsigned int n = q.count[0];
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double P[3] = {q.x[k], q.y[k], q.z[k]};
+        const long long idx = q.id[k], pix = idx / spp;
+        double o[3], d[3];
+        camera_ray(p, (int)(pix % p.W), (int)(pix / p.W), (int)(idx - pix * spp), spp, seed, o, d);
+        // entered through the lateral surface (not a cap)
+        const bool lateral = fabs(hypot(P[0], P[1]) - p.R2) <= 1e-9 * p.R2 && fabs(P[2]) < p.halfH;
+        float x[SUR_IN];
+        sur_features(p.R1, p.R2, p.H, p.variant == V_AZIMUTHAL ? 1 : 0, mode, P, d, x);
+        __nv_bfloat16 *row = X + (size_t)k * 64;
+#pragma unroll
+        for (int j = 0; j < SUR_IN; ++j) row[j] = __float2bfloat16_rn(x[j]);
+        elig[k] = lateral ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_sur_gate(Params p, int mode, int spp, unsigned long long seed, Queue q,
+                                                  const float *Y, const unsigned char *elig, float gate,
+                                                  float4 *samples, cloak_record *recs) {
+    const unsigned int n = q.count[0];
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (!elig[k]) continue;
+        const float *y = Y + (size_t)k * 16;
+        if (!(y[4] <= gate) || !(fabsf(y[0]) < 1.f) || !(y[1] * y[1] + y[2] * y[2] > 0.f)) continue;
+        const double P[3] = {q.x[k], q.y[k], q.z[k]};
+        const long long idx = q.id[k], pix = idx / spp;
+        double o[3], d[3];
+        camera_ray(p, (int)(pix % p.W), (int)(pix / p.W), (int)(idx - pix * spp), spp, seed, o, d);
+        double pos[3], dout[3], tof;
+        sur_reconstruct(p.R2, p.H, P, d, y, pos, dout, tof);
+        double nrm[3], eo, ee, c[3], mdout[3] = {-dout[0], -dout[1], -dout[2]};
+        face_normal(EV_LAT, pos, nrm);
+        local_material(p, pos, eo, ee, c);
+        cloak_record rec;
+        float rgb[3] = {0.f, 0.f, 0.f};
+        rec.mode = mode;
+        rec.steps = 0;
+        rec.tof = tof;
+        rec.status = CLOAK_RAY_EXITED;
+        set_vec(rec.exit_pos, pos);
+        set_vec(rec.exit_dir, dout);
+        // light from the room enters here and leaves towards the camera at the entry face
+        rec.weight = transmission_in(mode, eo, ee, c, nrm, mdout) * q.w_out[k];
+        rec.tile_id = room_hit(p, pos, dout, rgb);
+        store_sample(samples, recs, idx, rec, rgb);
+        // out of the integration: one ray fewer in its cost bucket, slot marked as finished
+        atomicSub(q.bins + q.key[k], 1u);
+        q.key[k] = -1;
+    }
+}
+
+__global__ void k_sur_conf(double R2, double H, unsigned long long seed, long long i0, long long n, const float *Y,
+                           float *T_all) {
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const long long i = i0 + b;
+    float *T = T_all + i * SUR_TSTRIDE;
+    if (T[5] == 0.f) {  // not a lateral exit: outside the surrogate's support
+        T[4] = 0.f;
+        return;
+    }
+    double P[3], d[3];
+    int mode, variant;
+    sur_sample(seed, (unsigned long long)i, R2, H, P, d, mode, variant);
+    double p1[3], d1[3], p0[3], d0[3], t1, t0;
+    sur_reconstruct(R2, H, P, d, Y + b * 16, p1, d1, t1);
+    sur_reconstruct(R2, H, P, d, T, p0, d0, t0);
+    double cx = d1[1] * d0[2] - d1[2] * d0[1], cy = d1[2] * d0[0] - d1[0] * d0[2], cz = d1[0] * d0[1] - d1[1] * d0[0];
+    double ang = atan2(sqrt(cx * cx + cy * cy + cz * cz), d1[0] * d0[0] + d1[1] * d0[1] + d1[2] * d0[2]);
+    double dp = sqrt((p1[0] - p0[0]) * (p1[0] - p0[0]) + (p1[1] - p0[1]) * (p1[1] - p0[1]) +
+                     (p1[2] - p0[2]) * (p1[2] - p0[2])) / R2;
+    T[4] = (float)log10(fmax(fmax(ang, dp), 1e-7));
+}
+
+static int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+cudaError_t launch_sur_features(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q, SurNet *s,
+                                cudaStream_t st) {
+    k_sur_features<<<sm_count() * 8, 256, 0, st>>>(p, mode, spp, seed, q, s->X, s->elig);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_gate(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q, SurNet *s,
+                            float4 *samples, cloak_record *recs, cudaStream_t st) {
+    k_sur_gate<<<sm_count() * 16, 128, 0, st>>>(p, mode, spp, seed, q, s->Y, s->elig, s->gate, samples, recs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_conf_targets(double R2, double H, unsigned long long seed, long long i0, long long n,
+                                    const float *Y, float *T_all, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_sur_conf<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(R2, H, seed, i0, n, Y, T_all);
+    return cudaGetLastError();
+}
+
+}  // namespace ck

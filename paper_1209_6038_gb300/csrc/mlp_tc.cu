@@ -49,10 +49,33 @@ __host__ __device__ constexpr uint32_t bf16_idesc(int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
+// GELU, tanh form, and its derivative (FP32)
 __device__ __forceinline__ float gelu_tanh(float x) {
     const float k0 = 0.7978845608028654f, k1 = 0.044715f;
     float u = k0 * (x + k1 * x * x * x);
     return 0.5f * x * (1.f + tanhf(u));
+}
+__device__ __forceinline__ float gelu_tanh_grad(float x) {
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    float th = tanhf(k0 * (x + k1 * x * x * x));
+    return 0.5f * (1.f + th) + 0.5f * x * (1.f - th * th) * k0 * (1.f + 3.f * k1 * x * x);
+}
+
+// 16 consecutive values of one row as BF16 into H, and into the transposed copy HT when it is set
+__device__ __forceinline__ void store_bf16_row(const GemmArgs &g, int row, int c, const float v[16]) {
+    __nv_bfloat162 hv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hv[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    uint4 *dh = (uint4 *)(g.H + (size_t)row * g.ldh + c);
+    dh[0] = *(uint4 *)&hv[0];
+    dh[1] = *(uint4 *)&hv[4];
+    if (g.HT) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            g.HT[(size_t)(c + 2 * i) * g.ldht + row] = hv[i].x;
+            g.HT[(size_t)(c + 2 * i + 1) * g.ldht + row] = hv[i].y;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
@@ -61,11 +84,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     __shared__ __align__(8) uint64_t full_bar[GEMM_STAGES], empty_bar[GEMM_STAGES], done_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
+    const int m0 = blockIdx.x * GEMM_TILE_M;
+    if (g.m_count && m0 >= (int)__ldg(g.m_count)) return;  // whole tile beyond the live rows
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int N = g.N, nk = g.K / GEMM_KCHUNK;
+    const int kslice = g.K / g.ksplit, kbase = blockIdx.y * kslice;
+    const int N = g.N, nk = kslice / GEMM_KCHUNK;
     const uint32_t a_bytes = GEMM_TILE_M * 128, b_bytes = (uint32_t)N * 128;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * GEMM_TILE_M;
     uint32_t ncols = 32;
     while ((int)ncols < N) ncols <<= 1;
 
@@ -100,8 +125,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
                 if (!ok) break;
                 unsigned char *sa = smem + s * (a_bytes + b_bytes), *sb = sa + a_bytes;
                 mbar_expect_tx(smem_u32(&full_bar[s]), a_bytes + b_bytes);
-                tma_load_2d(smem_u32(sa), &ta, it * GEMM_KCHUNK, m0, smem_u32(&full_bar[s]));
-                tma_load_2d(smem_u32(sb), &tb, it * GEMM_KCHUNK, 0, smem_u32(&full_bar[s]));
+                tma_load_2d(smem_u32(sa), &ta, kbase + it * GEMM_KCHUNK, m0, smem_u32(&full_bar[s]));
+                tma_load_2d(smem_u32(sb), &tb, kbase + it * GEMM_KCHUNK, 0, smem_u32(&full_bar[s]));
                 loaded = it + 1;
             }
             const int j = it - (GEMM_STAGES - 1);
@@ -156,23 +181,37 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
             if (row < g.M) {
-                if (g.epi == EPI_STORE) {
+                if (g.epi == EPI_STORE || g.epi == EPI_ATOMIC) {
                     float4 *dst = (float4 *)(g.C + (size_t)row * g.ldc + c);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    for (int i = 0; i < 4; ++i) {
+                        float4 q = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        if (g.epi == EPI_STORE) dst[i] = q;
+                        else atomicAdd(dst + i, q);
+                    }
+                } else if (g.epi == EPI_GELU_BWD) {
+                    const float4 *zi = (const float4 *)(g.Z + (size_t)row * g.ldz + c);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float4 z = zi[i];
+                        v[4 * i] *= gelu_tanh_grad(z.x);
+                        v[4 * i + 1] *= gelu_tanh_grad(z.y);
+                        v[4 * i + 2] *= gelu_tanh_grad(z.z);
+                        v[4 * i + 3] *= gelu_tanh_grad(z.w);
+                    }
+                    store_bf16_row(g, row, c, v);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] += g.bias[c + i];
-                    float4 *dz = (float4 *)(g.Z + (size_t)row * g.ldz + c);
+                    if (g.Z) {
+                        float4 *dz = (float4 *)(g.Z + (size_t)row * g.ldz + c);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) dz[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        for (int i = 0; i < 4; ++i) dz[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    }
                     if (g.epi == EPI_BIAS_GELU) {
-                        __nv_bfloat162 hv[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) hv[i] = __floats2bfloat162_rn(gelu_tanh(v[2 * i]), gelu_tanh(v[2 * i + 1]));
-                        uint4 *dh = (uint4 *)(g.H + (size_t)row * g.ldh + c);
-                        dh[0] = *(uint4 *)&hv[0];
-                        dh[1] = *(uint4 *)&hv[4];
+                        for (int i = 0; i < 16; ++i) v[i] = gelu_tanh(v[i]);
+                        store_bf16_row(g, row, c, v);
                     }
                 }
             }
@@ -189,7 +228,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
         void *p = nullptr;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
     }
@@ -209,7 +248,8 @@ CUresult make_tmap_bf16(CUtensorMap *map, const void *base, int rows, int cols, 
 }
 
 cudaError_t launch_gemm_tc(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &g, cudaStream_t st) {
-    if (g.M <= 0 || g.M % GEMM_TILE_M || g.N < 16 || g.N > 256 || g.N % 16 || g.K <= 0 || g.K % GEMM_KCHUNK)
+    if (g.M <= 0 || g.M % GEMM_TILE_M || g.N < 16 || g.N > 256 || g.N % 16 || g.ksplit < 1 || g.K <= 0 ||
+        g.K % (GEMM_KCHUNK * g.ksplit))
         return cudaErrorInvalidValue;
     size_t smem = gemm_smem_bytes(g.N);
     static bool attr_set = false;
@@ -219,7 +259,7 @@ cudaError_t launch_gemm_tc(const CUtensorMap &ta, const CUtensorMap &tb, const G
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_gemm_tc<<<g.M / GEMM_TILE_M, 128, smem, st>>>(ta, tb, g);
+    k_gemm_tc<<<dim3(g.M / GEMM_TILE_M, g.ksplit), 128, smem, st>>>(ta, tb, g);
     return cudaGetLastError();
 }
 

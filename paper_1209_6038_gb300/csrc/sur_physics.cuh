@@ -1,0 +1,107 @@
+// sur_physics.cuh -- ray geometry of the learned surrogate (device): training-ray sampling, network
+// inputs, regression targets and the exit rebuilt from a prediction.
+//
+// Both media are invariant under rotation about the axis and translation along it (Eqs. 14, 15), so
+// a ray keeps k_z and L_z = (x cross k)_z from the entry face to the exit face.  For a ray that enters
+// and leaves through r = R2 the vacuum exit direction is therefore fixed by the exit azimuth: in the
+// local (r, theta, z) frame it is the entry direction with its radial component reversed.
+#pragma once
+
+#include "physics.cuh"
+#include "surrogate.h"
+
+namespace ck {
+
+// local frame at azimuth phi
+__device__ __forceinline__ void sur_frame(double phi, double rh[3], double th[3]) {
+    double s, c;
+    sincos(phi, &s, &c);
+    rh[0] = c; rh[1] = s; rh[2] = 0.0;
+    th[0] = -s; th[1] = c; th[2] = 0.0;
+}
+
+// entry azimuth in [0, 2 pi) and the local components of the vacuum direction
+__device__ __forceinline__ double sur_local(const double P[3], const double d[3], double &dr, double &dt,
+                                            double &dz) {
+    double phi = atan2(P[1], P[0]);
+    if (phi < 0.0) phi += 2.0 * M_PI;
+    double rh[3], th[3];
+    sur_frame(phi, rh, th);
+    dr = d[0] * rh[0] + d[1] * rh[1];
+    dt = d[0] * th[0] + d[1] * th[1];
+    dz = d[2];
+    return phi;
+}
+
+// training ray i: entry point uniform on the lateral surface, direction cosine-weighted about the
+// inward normal (a uniform point of the unit disc lifted onto the hemisphere), mode and variant uniform
+__device__ __forceinline__ void sur_sample(unsigned long long seed, unsigned long long i, double R2, double H,
+                                           double P[3], double d[3], int &mode, int &variant) {
+    const double u0 = jitter(seed, i, SUR_STREAM, 0), u1 = jitter(seed, i, SUR_STREAM, 1);
+    const double u2 = jitter(seed, i, SUR_STREAM, 2), u3 = jitter(seed, i, SUR_STREAM, 3);
+    const double u4 = jitter(seed, i, SUR_STREAM, 4);
+    double rh[3], th[3];
+    sur_frame(2.0 * M_PI * u1, rh, th);
+    P[0] = R2 * rh[0]; P[1] = R2 * rh[1]; P[2] = (u0 - 0.5) * H;
+    double s, c;
+    sincos(2.0 * M_PI * u3, &s, &c);
+    const double rho = sqrt(u2), dr = -sqrt(1.0 - u2), dt = rho * c, dz = rho * s;
+    d[0] = dr * rh[0] + dt * th[0];
+    d[1] = dr * rh[1] + dt * th[1];
+    d[2] = dz;
+    const int bits = (int)(u4 * 4.0);
+    mode = bits & 1;
+    variant = bits >> 1;
+}
+
+// network inputs: z / (H/2), phi / pi - 1, asin(d_z) / (pi/2), atan2(d_theta, -d_r) / (pi/2),
+// 2 mode - 1, 2 variant - 1, R1 / R2
+__device__ __forceinline__ void sur_features(double R1, double R2, double H, int variant, int mode, const double P[3],
+                                             const double d[3], float x[SUR_IN]) {
+    double dr, dt, dz;
+    const double phi = sur_local(P, d, dr, dt, dz);
+    x[0] = (float)(P[2] / (0.5 * H));
+    x[1] = (float)(phi / M_PI - 1.0);
+    x[2] = (float)(asin(fmin(fmax(dz, -1.0), 1.0)) / (0.5 * M_PI));
+    x[3] = (float)(atan2(dt, -dr) / (0.5 * M_PI));
+    x[4] = (float)(2 * mode - 1);
+    x[5] = (float)(2 * variant - 1);
+    x[6] = (float)(R1 / R2);
+}
+
+// regression targets of a traced ray; false unless it left through the lateral surface
+__device__ __forceinline__ bool sur_targets(double R2, double H, const double P[3], const double d[3],
+                                            const cloak_record &rec, float t[4]) {
+    if (rec.status != CLOAK_RAY_EXITED && rec.status != CLOAK_RAY_HIT_METAL_EXITED) return false;
+    const double re = hypot(rec.exit_pos[0], rec.exit_pos[1]);
+    if (fabs(re - R2) > 1e-9 * R2 || !(fabs(rec.exit_pos[2]) < 0.5 * H)) return false;
+    double dr, dt, dz;
+    const double phi = sur_local(P, d, dr, dt, dz);
+    const double psi = atan2(rec.exit_pos[1], rec.exit_pos[0]) - (phi + M_PI - 2.0 * atan2(dt, -dr));
+    double s, c;
+    sincos(psi, &s, &c);
+    t[0] = (float)(rec.exit_pos[2] / (0.5 * H));
+    t[1] = (float)c;
+    t[2] = (float)s;
+    t[3] = (float)(rec.tof * 0.25);
+    return true;
+}
+
+// exit point on r = R2, vacuum exit direction (k_z, L_z conserved) and time of flight from y[0..3]
+__device__ __forceinline__ void sur_reconstruct(double R2, double H, const double P[3], const double d[3],
+                                                const float y[4], double pos[3], double dir[3], double &tof) {
+    double dr, dt, dz;
+    const double phi = sur_local(P, d, dr, dt, dz);
+    const double phe = phi + M_PI - 2.0 * atan2(dt, -dr) + atan2((double)y[2], (double)y[1]);
+    double rh[3], th[3];
+    sur_frame(phe, rh, th);
+    pos[0] = R2 * rh[0];
+    pos[1] = R2 * rh[1];
+    pos[2] = (double)y[0] * 0.5 * H;
+    dir[0] = -dr * rh[0] + dt * th[0];
+    dir[1] = -dr * rh[1] + dt * th[1];
+    dir[2] = dz;
+    tof = 4.0 * (double)y[3];
+}
+
+}  // namespace ck

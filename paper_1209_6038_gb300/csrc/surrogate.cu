@@ -1,14 +1,480 @@
-// surrogate.cu -- C ABI of the learned surrogate's tensor-core building blocks.
+// surrogate.cu -- the learned surrogate: parameters, BF16 tensor-core training (forward, backward, Adam)
+// and inference, and its C ABI.  See surrogate.h for the network.
+//
+// Training step on a batch of B rays (B a multiple of 128), every GEMM on the tensor cores (mlp_tc.cuh):
+//   forward  Z_l = H_{l-1} W_l^T + b_l, H_l = GELU(Z_l)          (H_{-1} = X; the last layer is affine)
+//   loss     dY = dL/dY                                           (k_sur_loss)
+//   backward dW_l = dZ_l^T H_{l-1}   (split over the batch, FP32 atomics)
+//            dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})                (fused into the GEMM epilogue)
+//            db_l = column sums of dZ_l                            (k_sur_rowsum on the transposed copy)
+//   update   Adam on the FP32 masters, then their BF16 copies W_l and W_l^T (k_sur_adam)
+#include <chrono>
+#include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <string>
+#include <vector>
 
 #include "cloak.h"
 #include "mlp_tc.cuh"
+#include "surrogate.h"
+#include "wavefront.cuh"
+
+namespace ck {
 
 namespace {
-__device__ unsigned int g_gemm_err;  // timeout flag of the last cloak_mlp_gemm call
+__device__ unsigned int g_gemm_err;  // timeout flag of the GEMM kernels launched from this file
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
 }
 
+// batch rows from the training set: random rows (sequential = 0) or rows i0 .. i0 + B - 1
+__global__ void k_sur_gather(const float *X_all, const float *T_all, long long n, unsigned long long seed,
+                             long long step, int B, int sequential, long long i0, __nv_bfloat16 *Xb,
+                             __nv_bfloat16 *XTb, float *Tb) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    long long idx = sequential ? i0 + b : (long long)(mix64(mix64(seed) ^ (uint64_t)(step * B + b)) % (uint64_t)n);
+    if (idx >= n) idx = n - 1;
+    const float *x = X_all + idx * SUR_XSTRIDE;
+#pragma unroll
+    for (int j = 0; j < SUR_IN; ++j) {
+        __nv_bfloat16 v = __float2bfloat16_rn(x[j]);
+        Xb[(size_t)b * 64 + j] = v;
+        XTb[(size_t)j * B + b] = v;
+    }
+    const float *t = T_all + idx * SUR_TSTRIDE;
+#pragma unroll
+    for (int j = 0; j < SUR_TSTRIDE; ++j) Tb[(size_t)b * SUR_TSTRIDE + j] = t[j];
+}
+
+// Loss and dL/dY (stage 1: masked weighted squared error of outputs 0..3; stage 2: L1 of the
+// confidence output 4), both as means over the batch.
+__global__ void k_sur_loss(const float *Y, const float *Tb, int B, int stage, __nv_bfloat16 *dY,
+                           __nv_bfloat16 *dYT, double *loss) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    double L = 0.0;
+    if (b < B) {
+        const float *y = Y + (size_t)b * 16, *t = Tb + (size_t)b * SUR_TSTRIDE;
+        const float w[4] = {1.f, 1.f, 1.f, 0.1f}, invB = 1.f / (float)B, mask = t[5];
+        float g[SUR_OUT] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (stage == 1) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float e = y[j] - t[j];
+                L += (double)(mask * w[j] * e * e * invB);
+                g[j] = 2.f * mask * w[j] * e * invB;
+            }
+        } else {
+            const float e = y[4] - t[4];
+            L += (double)(fabsf(e) * invB);
+            g[4] = (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) * invB;
+        }
+#pragma unroll
+        for (int j = 0; j < SUR_OUT; ++j) {
+            const __nv_bfloat16 v = __float2bfloat16_rn(g[j]);
+            dY[(size_t)b * 64 + j] = v;
+            dYT[(size_t)j * B + b] = v;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) L += __shfl_down_sync(0xffffffffu, L, o);
+    if ((threadIdx.x & 31) == 0 && L != 0.0) atomicAdd(loss, L);
+}
+
+// out[r] = sum over the columns of row r of a BF16 matrix (bias gradients from a transposed dZ)
+__global__ void k_sur_rowsum(const __nv_bfloat16 *M, int cols, float *out) {
+    const __nv_bfloat16 *row = M + (size_t)blockIdx.x * cols;
+    float s = 0.f;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) s += __bfloat162float(row[c]);
+    __shared__ float part[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) out[blockIdx.x] = s;
+    }
+}
+
+struct AdamArgs {
+    float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+};
+
+// One Adam step of layer l (weights r < out, c < in, and the bias), then the BF16 copies W (nout x kin)
+// and W^T (kin x kb).  One thread per element of the (mw + 1) x kin grid; row mw is the bias.
+__global__ void k_sur_adam(SurDims dm, float *W, float *b, float *mW, float *vW, float *mb, float *vb,
+                           const float *gW, const float *gb, __nv_bfloat16 *Wb, __nv_bfloat16 *WTb, AdamArgs a,
+                           int update) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nW = (long long)dm.mw * dm.kin;
+    if (e < nW) {
+        const int r = (int)(e / dm.kin), c = (int)(e % dm.kin);
+        if (update && r < dm.out && c < dm.in) {
+            const float g = gW[e];
+            const float m = a.b1 * mW[e] + (1.f - a.b1) * g, v = a.b2 * vW[e] + (1.f - a.b2) * g * g;
+            mW[e] = m;
+            vW[e] = v;
+            W[e] -= a.lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+        }
+        const __nv_bfloat16 wb = __float2bfloat16_rn(W[e]);
+        if (r < dm.nout) Wb[(size_t)r * dm.kin + c] = wb;
+        if (r < dm.kb) WTb[(size_t)c * dm.kb + r] = wb;
+    } else if (e < nW + dm.out && update) {
+        const int r = (int)(e - nW);
+        const float g = gb[r];
+        const float m = a.b1 * mb[r] + (1.f - a.b1) * g, v = a.b2 * vb[r] + (1.f - a.b2) * g * g;
+        mb[r] = m;
+        vb[r] = v;
+        b[r] -= a.lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+    }
+}
+
+// FP32 inputs (n x 7) into the padded BF16 input rows of the inference scratch
+__global__ void k_sur_pack(const float *x, long long n, __nv_bfloat16 *X) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int j = 0; j < SUR_IN; ++j) X[(size_t)i * 64 + j] = __float2bfloat16_rn(x[i * SUR_IN + j]);
+}
+__global__ void k_sur_unpack(const float *Y, long long n, float *y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int j = 0; j < SUR_OUT; ++j) y[i * SUR_OUT + j] = Y[(size_t)i * 16 + j];
+}
+// FP32 targets (n x 8) into the batch target buffer, and FP32 inputs into the batch input buffers
+__global__ void k_sur_pack_batch(const float *x, const float *t, int B, __nv_bfloat16 *Xb, __nv_bfloat16 *XTb,
+                                 float *Tb) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+#pragma unroll
+    for (int j = 0; j < SUR_IN; ++j) {
+        const __nv_bfloat16 v = __float2bfloat16_rn(x[(size_t)b * SUR_IN + j]);
+        Xb[(size_t)b * 64 + j] = v;
+        XTb[(size_t)j * B + b] = v;
+    }
+#pragma unroll
+    for (int j = 0; j < SUR_TSTRIDE; ++j) Tb[(size_t)b * SUR_TSTRIDE + j] = t[(size_t)b * SUR_TSTRIDE + j];
+}
+}  // namespace
+
+// ------------------------------------------------------------------ host helpers
+static uint64_t host_mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+static double host_uniform(uint64_t seed, uint64_t i) {
+    return (double)(host_mix64(host_mix64(seed) ^ i) >> 11) * 0x1.0p-53;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static cudaError_t gemm(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs g, cudaStream_t st) {
+    return launch_gemm_tc(ta, tb, g, st);
+}
+static GemmArgs gemm_args(int M, int N, int K, int epi, unsigned int *err) {
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.M = M; g.N = N; g.K = K; g.ksplit = 1; g.epi = epi; g.err = err;
+    return g;
+}
+static bool tmap(CUtensorMap *m, const void *base, long long rows, int cols, int box_rows) {
+    return make_tmap_bf16(m, base, (int)rows, cols, box_rows) == CUDA_SUCCESS;
+}
+
+SurNet *sur_create(double R1, double R2, double H, unsigned long long seed, const char **why) {
+    SurNet *s = new SurNet();
+    memset(s, 0, sizeof(*s));
+    s->R1 = R1; s->R2 = R2; s->H = H;
+    s->gate = -3.0f;
+    size_t bytes = 0;
+    for (int l = 0; l < SUR_L; ++l) {
+        SurDims d = sur_dims(l);
+        const size_t w = align256((size_t)d.mw * d.kin * 4), bb = align256((size_t)d.mw * 4);
+        bytes += 4 * w + 4 * bb;                                        // W, mW, vW, gW ; b, mb, vb, gb
+        bytes += align256((size_t)d.nout * d.kin * 2) + align256((size_t)d.kin * d.kb * 2);
+    }
+    bytes += 256;  // error flag
+    cudaError_t e = cudaMalloc(&s->arena, bytes);
+    if (e != cudaSuccess) {
+        *why = "cannot allocate the surrogate's parameters";
+        delete s;
+        return nullptr;
+    }
+    cudaMemset(s->arena, 0, bytes);
+    char *p = s->arena;
+    // gradients first, contiguous (zeroed before every step)
+    s->grad_begin = p;
+    for (int l = 0; l < SUR_L; ++l) {
+        SurDims d = sur_dims(l);
+        s->gW[l] = (float *)p; p += align256((size_t)d.mw * d.kin * 4);
+        s->gb[l] = (float *)p; p += align256((size_t)d.mw * 4);
+    }
+    s->grad_bytes = (size_t)(p - s->grad_begin);
+    for (int l = 0; l < SUR_L; ++l) {
+        SurDims d = sur_dims(l);
+        const size_t w = align256((size_t)d.mw * d.kin * 4), bb = align256((size_t)d.mw * 4);
+        s->W[l] = (float *)p; p += w;
+        s->mW[l] = (float *)p; p += w;
+        s->vW[l] = (float *)p; p += w;
+        s->b[l] = (float *)p; p += bb;
+        s->mb[l] = (float *)p; p += bb;
+        s->vb[l] = (float *)p; p += bb;
+        s->Wb[l] = (__nv_bfloat16 *)p; p += align256((size_t)d.nout * d.kin * 2);
+        s->WTb[l] = (__nv_bfloat16 *)p; p += align256((size_t)d.kin * d.kb * 2);
+        if (!tmap(&s->tWb[l], s->Wb[l], d.nout, d.kin, d.nout) || !tmap(&s->tWTb[l], s->WTb[l], d.kin, d.kb, d.kin)) {
+            *why = "cannot encode the weight tensor maps";
+            cudaFree(s->arena);
+            delete s;
+            return nullptr;
+        }
+    }
+    s->err = (unsigned int *)p;
+    // initial weights: normal with variance 1/in (Box-Muller on splitmix64 uniforms), last layer x 0.1
+    std::vector<float> host;
+    for (int l = 0; l < SUR_L; ++l) {
+        SurDims d = sur_dims(l);
+        host.assign((size_t)d.mw * d.kin, 0.f);
+        const double sd = (l == SUR_L - 1 ? 0.1 : 1.0) / std::sqrt((double)d.in);
+        for (int r = 0; r < d.out; ++r)
+            for (int c = 0; c < d.in; ++c) {
+                const uint64_t k = ((uint64_t)l << 40) ^ ((uint64_t)r << 20) ^ (uint64_t)c;
+                const double u1 = host_uniform(seed, 2 * k) + 0x1.0p-54, u2 = host_uniform(seed, 2 * k + 1);
+                host[(size_t)r * d.kin + c] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2));
+            }
+        cudaMemcpy(s->W[l], host.data(), host.size() * 4, cudaMemcpyHostToDevice);
+    }
+    if (sur_refresh_bf16(s, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        *why = "cannot initialise the surrogate's weights";
+        cudaFree(s->arena);
+        delete s;
+        return nullptr;
+    }
+    return s;
+}
+
+void sur_destroy(SurNet *s) {
+    if (!s) return;
+    if (s->inf_arena) cudaFree(s->inf_arena);
+    if (s->arena) cudaFree(s->arena);
+    delete s;
+}
+
+static cudaError_t adam_all(SurNet *s, const AdamArgs &a, int update, int first_layer, cudaStream_t st) {
+    for (int l = first_layer; l < SUR_L; ++l) {
+        SurDims d = sur_dims(l);
+        const long long n = (long long)d.mw * d.kin + d.out;
+        k_sur_adam<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, s->W[l], s->b[l], s->mW[l], s->vW[l], s->mb[l],
+                                                               s->vb[l], s->gW[l], s->gb[l], s->Wb[l], s->WTb[l], a,
+                                                               update);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t sur_refresh_bf16(SurNet *s, cudaStream_t st) {
+    AdamArgs a;
+    memset(&a, 0, sizeof(a));
+    return adam_all(s, a, 0, 0, st);
+}
+
+cudaError_t sur_ensure_inference(SurNet *s, long long rows) {
+    rows = (rows + 127) / 128 * 128;
+    if (rows <= s->inf_rows) return cudaSuccess;
+    if (s->inf_arena) {
+        cudaFree(s->inf_arena);
+        s->inf_arena = nullptr;
+        s->inf_rows = 0;
+    }
+    const size_t xb = align256((size_t)rows * 64 * 2), hb = align256((size_t)rows * SUR_W * 2),
+                 yb = align256((size_t)rows * 16 * 4), eb = align256((size_t)rows);
+    cudaError_t e = cudaMalloc(&s->inf_arena, xb + 2 * hb + yb + eb);
+    if (e != cudaSuccess) return e;
+    char *p = s->inf_arena;
+    s->X = (__nv_bfloat16 *)p; p += xb;
+    s->H0 = (__nv_bfloat16 *)p; p += hb;
+    s->H1 = (__nv_bfloat16 *)p; p += hb;
+    s->Y = (float *)p; p += yb;
+    s->elig = (unsigned char *)p;
+    if ((e = cudaMemset(s->X, 0, xb)) != cudaSuccess) return e;  // columns 7..63 stay zero
+    if (!tmap(&s->tX, s->X, rows, 64, GEMM_TILE_M) || !tmap(&s->tH0, s->H0, rows, SUR_W, GEMM_TILE_M) ||
+        !tmap(&s->tH1, s->H1, rows, SUR_W, GEMM_TILE_M))
+        return cudaErrorInvalidValue;
+    s->inf_rows = rows;
+    return cudaSuccess;
+}
+
+cudaError_t sur_forward(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st) {
+    const CUtensorMap *in = &s->tX;
+    __nv_bfloat16 *outs[2] = {s->H0, s->H1};
+    const CUtensorMap *touts[2] = {&s->tH0, &s->tH1};
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < SUR_L && e == cudaSuccess; ++l) {
+        SurDims d = sur_dims(l);
+        GemmArgs g = gemm_args((int)n, d.nout, d.kin, l < SUR_L - 1 ? EPI_BIAS_GELU : EPI_BIAS, s->err);
+        g.m_count = m_count;
+        g.bias = s->b[l];
+        if (l < SUR_L - 1) {
+            g.H = outs[l & 1];
+            g.ldh = SUR_W;
+        } else {
+            g.Z = s->Y;
+            g.ldz = 16;
+        }
+        e = gemm(*in, s->tWb[l], g, st);
+        in = touts[l & 1];
+    }
+    return e;
+}
+
+// ------------------------------------------------------------------ training workspace
+struct TrainWS {
+    int B;
+    char *arena;
+    __nv_bfloat16 *Xb, *XTb, *H[4], *HT[4], *dY, *dYT, *dZ[2], *dZT[2];
+    float *Tb, *Z[4], *Y;
+    double *loss;
+    CUtensorMap tXb, tXTb, tH[4], tHT[4], tdY, tdYT, tdZ[2], tdZT[2];
+};
+
+static cudaError_t ws_create(TrainWS &w, int B) {
+    memset(&w, 0, sizeof(w));
+    w.B = B;
+    const size_t x = align256((size_t)B * 64 * 2), z = align256((size_t)B * SUR_W * 4),
+                 h = align256((size_t)B * SUR_W * 2), t = align256((size_t)B * SUR_TSTRIDE * 4),
+                 y = align256((size_t)B * 16 * 4), dyt = align256((size_t)128 * B * 2);
+    const size_t bytes = 2 * x + t + 4 * z + 8 * h + y + x + dyt + 4 * h + 256;
+    cudaError_t e = cudaMalloc(&w.arena, bytes);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemset(w.arena, 0, bytes)) != cudaSuccess) return e;
+    char *p = w.arena;
+    w.Xb = (__nv_bfloat16 *)p; p += x;
+    w.XTb = (__nv_bfloat16 *)p; p += x;
+    w.Tb = (float *)p; p += t;
+    for (int l = 0; l < 4; ++l) { w.Z[l] = (float *)p; p += z; }
+    for (int l = 0; l < 4; ++l) { w.H[l] = (__nv_bfloat16 *)p; p += h; }
+    for (int l = 0; l < 4; ++l) { w.HT[l] = (__nv_bfloat16 *)p; p += h; }
+    w.Y = (float *)p; p += y;
+    w.dY = (__nv_bfloat16 *)p; p += x;
+    w.dYT = (__nv_bfloat16 *)p; p += dyt;
+    for (int j = 0; j < 2; ++j) { w.dZ[j] = (__nv_bfloat16 *)p; p += h; }
+    for (int j = 0; j < 2; ++j) { w.dZT[j] = (__nv_bfloat16 *)p; p += h; }
+    w.loss = (double *)p;
+    bool ok = tmap(&w.tXb, w.Xb, B, 64, GEMM_TILE_M) && tmap(&w.tXTb, w.XTb, 64, B, 64) &&
+              tmap(&w.tdY, w.dY, B, 64, GEMM_TILE_M) && tmap(&w.tdYT, w.dYT, 128, B, GEMM_TILE_M);
+    for (int l = 0; l < 4; ++l)
+        ok = ok && tmap(&w.tH[l], w.H[l], B, SUR_W, GEMM_TILE_M) && tmap(&w.tHT[l], w.HT[l], SUR_W, B, SUR_W);
+    for (int j = 0; j < 2; ++j)
+        ok = ok && tmap(&w.tdZ[j], w.dZ[j], B, SUR_W, GEMM_TILE_M) && tmap(&w.tdZT[j], w.dZT[j], SUR_W, B, GEMM_TILE_M);
+    return ok ? cudaSuccess : cudaErrorInvalidValue;
+}
+static void ws_destroy(TrainWS &w) {
+    if (w.arena) cudaFree(w.arena);
+    w.arena = nullptr;
+}
+
+// split of the batch dimension for the weight-gradient GEMMs: about one CTA per SM
+static int ksplit_for(int B, int mtiles) {
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int chunks = B / GEMM_KCHUNK;
+    int best = 1;
+    for (int k = 1; k <= chunks; ++k)
+        if (chunks % k == 0 && k * mtiles <= sms) best = k;
+    return best;
+}
+
+static cudaError_t train_forward(SurNet *s, TrainWS &w, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < SUR_L && e == cudaSuccess; ++l) {
+        SurDims d = sur_dims(l);
+        const CUtensorMap &ta = l == 0 ? w.tXb : w.tH[l - 1];
+        GemmArgs g = gemm_args(w.B, d.nout, d.kin, l < SUR_L - 1 ? EPI_BIAS_GELU : EPI_BIAS, s->err);
+        g.bias = s->b[l];
+        if (l < SUR_L - 1) {
+            g.Z = w.Z[l]; g.ldz = SUR_W;
+            g.H = w.H[l]; g.ldh = SUR_W;
+            g.HT = w.HT[l]; g.ldht = w.B;
+        } else {
+            g.Z = w.Y; g.ldz = 16;
+        }
+        e = gemm(ta, s->tWb[l], g, st);
+    }
+    return e;
+}
+
+// gradients of the loss of the batch in w (after train_forward and k_sur_loss); layers >= first only
+static cudaError_t train_backward(SurNet *s, TrainWS &w, int first, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(s->grad_begin, 0, s->grad_bytes, st);
+    const int B = w.B;
+    // output layer
+    {
+        SurDims d = sur_dims(SUR_L - 1);
+        GemmArgs g = gemm_args(d.mw, d.in, B, EPI_ATOMIC, s->err);
+        g.ksplit = ksplit_for(B, d.mw / GEMM_TILE_M);
+        g.C = s->gW[SUR_L - 1]; g.ldc = d.kin;
+        if (e == cudaSuccess) e = gemm(w.tdYT, w.tHT[SUR_L - 2], g, st);
+        k_sur_rowsum<<<d.out, 256, 0, st>>>(w.dYT, B, s->gb[SUR_L - 1]);
+    }
+    int cur = 0;
+    for (int l = SUR_L - 1; l > first && e == cudaSuccess; --l) {
+        // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
+        SurDims d = sur_dims(l), dp = sur_dims(l - 1);
+        const CUtensorMap &ta = l == SUR_L - 1 ? w.tdY : w.tdZ[cur ^ 1];
+        GemmArgs g = gemm_args(B, d.kin, d.kb, EPI_GELU_BWD, s->err);
+        g.Z = w.Z[l - 1]; g.ldz = SUR_W;
+        g.H = w.dZ[cur]; g.ldh = SUR_W;
+        g.HT = w.dZT[cur]; g.ldht = B;
+        e = gemm(ta, s->tWTb[l], g, st);
+        if (e != cudaSuccess) break;
+        // dW_{l-1} = dZ_{l-1}^T H_{l-2}, db_{l-1} = column sums of dZ_{l-1}
+        const CUtensorMap &tb = l - 1 == 0 ? w.tXTb : w.tHT[l - 2];
+        GemmArgs gw = gemm_args(dp.mw, dp.kin, B, EPI_ATOMIC, s->err);
+        gw.ksplit = ksplit_for(B, dp.mw / GEMM_TILE_M);
+        gw.C = s->gW[l - 1]; gw.ldc = dp.kin;
+        e = gemm(w.tdZT[cur], tb, gw, st);
+        k_sur_rowsum<<<dp.out, 256, 0, st>>>(w.dZT[cur], B, s->gb[l - 1]);
+        cur ^= 1;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+}
+
+static cudaError_t train_step(SurNet *s, TrainWS &w, int stage, float lr, cudaStream_t st) {
+    cudaError_t e = train_forward(s, w, st);
+    if (e != cudaSuccess) return e;
+    k_sur_loss<<<(w.B + 255) / 256, 256, 0, st>>>(w.Y, w.Tb, w.B, stage, w.dY, w.dYT, w.loss);
+    e = train_backward(s, w, stage == 1 ? 0 : SUR_L - 1, st);
+    if (e != cudaSuccess) return e;
+    s->adam_step++;
+    AdamArgs a;
+    a.lr = lr; a.b1 = 0.9f; a.b2 = 0.999f; a.eps = 1e-8f;
+    a.c1 = (float)(1.0 - std::pow(0.9, (double)s->adam_step));
+    a.c2 = (float)(1.0 - std::pow(0.999, (double)s->adam_step));
+    return adam_all(s, a, 1, stage == 1 ? 0 : SUR_L - 1, st);
+}
+
+static cudaError_t d2h(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+}
+
+static unsigned int *gemm_err_flag() {
+    unsigned int *p = nullptr;
+    cudaGetSymbolAddress((void **)&p, g_gemm_err);
+    return p;
+}
+
+}  // namespace ck
+
+// ------------------------------------------------------------------ C ABI building block
 extern "C" int cloak_mlp_gemm(const void *dev_a, const void *dev_b, float *dev_c, int M, int N, int K,
                               void *cuda_stream) {
     if (!dev_a || !dev_b || !dev_c) return CLOAK_EINVAL;
@@ -18,14 +484,324 @@ extern "C" int cloak_mlp_gemm(const void *dev_a, const void *dev_b, float *dev_c
     if (ck::make_tmap_bf16(&ta, dev_a, M, K, ck::GEMM_TILE_M) != CUDA_SUCCESS) return CLOAK_ECUDA;
     if (ck::make_tmap_bf16(&tb, dev_b, N, K, N) != CUDA_SUCCESS) return CLOAK_ECUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    unsigned int *err = nullptr;
-    if (cudaGetSymbolAddress((void **)&err, g_gemm_err) != cudaSuccess) return CLOAK_ECUDA;
+    unsigned int *err = ck::gemm_err_flag();
+    if (!err) return CLOAK_ECUDA;
     if (cudaMemsetAsync(err, 0, sizeof(unsigned int), st) != cudaSuccess) return CLOAK_ECUDA;
-    ck::GemmArgs g{};
-    g.M = M; g.N = N; g.K = K; g.C = dev_c; g.ldc = N; g.epi = ck::EPI_STORE; g.err = err;
+    ck::GemmArgs g = ck::gemm_args(M, N, K, ck::EPI_STORE, err);
+    g.C = dev_c;
+    g.ldc = N;
     if (ck::launch_gemm_tc(ta, tb, g, st) != cudaSuccess) return CLOAK_ECUDA;
     unsigned int h = 0;
     if (cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return CLOAK_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return CLOAK_ECUDA;
     return h ? CLOAK_ETIMEOUT : CLOAK_OK;
 }
+
+// ------------------------------------------------------------------ surrogate entry points (called by capi.cu)
+namespace ck {
+
+// layout of the flat FP32 parameter vector of the C ABI: per layer W_l (out x in, row-major), then b_l
+long long sur_nparams() {
+    long long n = 0;
+    for (int l = 0; l < SUR_L; ++l) {
+        SurDims d = sur_dims(l);
+        n += (long long)d.out * d.in + d.out;
+    }
+    return n;
+}
+
+cudaError_t sur_get_params(SurNet *s, float *host) {
+    cudaError_t e0 = cudaDeviceSynchronize();
+    if (e0 != cudaSuccess) return e0;
+    std::vector<float> buf;
+    long long o = 0;
+    for (int l = 0; l < SUR_L; ++l) {
+        SurDims d = sur_dims(l);
+        buf.resize((size_t)d.mw * d.kin);
+        cudaError_t e = cudaMemcpy(buf.data(), s->W[l], buf.size() * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        for (int r = 0; r < d.out; ++r)
+            for (int c = 0; c < d.in; ++c) host[o++] = buf[(size_t)r * d.kin + c];
+        e = cudaMemcpy(host + o, s->b[l], (size_t)d.out * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        o += d.out;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t sur_set_params(SurNet *s, const float *host) {
+    cudaError_t e0 = cudaDeviceSynchronize();
+    if (e0 != cudaSuccess) return e0;
+    std::vector<float> buf;
+    long long o = 0;
+    for (int l = 0; l < SUR_L; ++l) {
+        SurDims d = sur_dims(l);
+        buf.assign((size_t)d.mw * d.kin, 0.f);
+        for (int r = 0; r < d.out; ++r)
+            for (int c = 0; c < d.in; ++c) buf[(size_t)r * d.kin + c] = host[o++];
+        cudaError_t e = cudaMemcpy(s->W[l], buf.data(), buf.size() * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+        std::vector<float> bb((size_t)d.mw, 0.f);
+        for (int r = 0; r < d.out; ++r) bb[r] = host[o++];
+        if ((e = cudaMemcpy(s->b[l], bb.data(), bb.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        const size_t wb = (size_t)d.mw * d.kin * 4, bbytes = (size_t)d.mw * 4;
+        if ((e = cudaMemset(s->mW[l], 0, wb)) != cudaSuccess || (e = cudaMemset(s->vW[l], 0, wb)) != cudaSuccess ||
+            (e = cudaMemset(s->mb[l], 0, bbytes)) != cudaSuccess || (e = cudaMemset(s->vb[l], 0, bbytes)) != cudaSuccess)
+            return e;
+    }
+    s->adam_step = 0;
+    cudaError_t e = sur_refresh_bf16(s, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e;
+}
+
+// forward pass of n FP32 input rows (n x 7) into FP32 outputs (n x 5)
+int sur_forward_rows(SurNet *s, const float *dev_x, long long n, float *dev_y, cudaStream_t st, std::string &why) {
+    cudaError_t e = sur_ensure_inference(s, n);
+    if (e != cudaSuccess) { why = "cannot allocate the inference scratch"; return CLOAK_ENOMEM; }
+    const long long rows = (n + 127) / 128 * 128;
+    unsigned int *err = gemm_err_flag();
+    s->err = err;
+    cudaMemsetAsync(err, 0, 4, st);
+    k_sur_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dev_x, n, s->X);
+    if ((e = sur_forward(s, rows, nullptr, st)) != cudaSuccess) { why = cudaGetErrorString(e); return CLOAK_ECUDA; }
+    k_sur_unpack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->Y, n, dev_y);
+    unsigned int h = 0;
+    cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { why = cudaGetErrorString(e); return CLOAK_ECUDA; }
+    if (h) { why = "tensor-core GEMM timed out"; return CLOAK_ETIMEOUT; }
+    return CLOAK_OK;
+}
+
+// gradients (host, flat layout) of one batch, and optionally one Adam step with learning rate lr
+int sur_batch_grad(SurNet *s, const float *dev_x, const float *dev_t, long long n, int stage, double lr,
+                   float *host_grad, cudaStream_t st, std::string &why) {
+    TrainWS w;
+    cudaError_t e = ws_create(w, (int)n);
+    if (e != cudaSuccess) { ws_destroy(w); why = "cannot allocate the training workspace"; return CLOAK_ENOMEM; }
+    unsigned int *err = gemm_err_flag();
+    s->err = err;
+    cudaMemsetAsync(err, 0, 4, st);
+    cudaMemsetAsync(w.loss, 0, 8, st);
+    k_sur_pack_batch<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dev_x, dev_t, (int)n, w.Xb, w.XTb, w.Tb);
+    if (lr > 0) {
+        e = train_step(s, w, stage, (float)lr, st);
+    } else {
+        e = train_forward(s, w, st);
+        if (e == cudaSuccess) {
+            k_sur_loss<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.Y, w.Tb, (int)n, stage, w.dY, w.dYT, w.loss);
+            e = train_backward(s, w, 0, st);
+        }
+    }
+    unsigned int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && host_grad) {
+        std::vector<float> buf;
+        long long o = 0;
+        for (int l = 0; l < SUR_L && e == cudaSuccess; ++l) {
+            SurDims d = sur_dims(l);
+            buf.resize((size_t)d.mw * d.kin);
+            e = cudaMemcpy(buf.data(), s->gW[l], buf.size() * 4, cudaMemcpyDeviceToHost);
+            for (int r = 0; r < d.out; ++r)
+                for (int c = 0; c < d.in; ++c) host_grad[o++] = buf[(size_t)r * d.kin + c];
+            if (e == cudaSuccess) e = cudaMemcpy(host_grad + o, s->gb[l], (size_t)d.out * 4, cudaMemcpyDeviceToHost);
+            o += d.out;
+        }
+    }
+    ws_destroy(w);
+    if (e != cudaSuccess) { why = cudaGetErrorString(e); return CLOAK_ECUDA; }
+    if (h) { why = "tensor-core GEMM timed out"; return CLOAK_ETIMEOUT; }
+    return CLOAK_OK;
+}
+
+// Train on n rays traced by the integrator (parameters p: geometry, integrator, precision).
+int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, int epochs, cudaStream_t st,
+              std::string &why) {
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    const int B = 19456;  // 152 x 128: one 128-row tile per SM in the forward GEMMs
+    // 1. training set: the integrator traces n seeded rays
+    const size_t qb = queue_bytes(n), xb = (size_t)n * SUR_XSTRIDE * 4, tb = (size_t)n * SUR_TSTRIDE * 4;
+    char *data = nullptr;
+    cudaError_t e = cudaMalloc(&data, qb + xb + tb);
+    if (e != cudaSuccess) { why = "cannot allocate the training set"; return CLOAK_ENOMEM; }
+    Queue q;
+    float4 *unused = nullptr;
+    carve_queue(data, n, q, &unused);
+    float *X_all = (float *)(data + qb), *T_all = (float *)(data + qb + xb);
+    e = launch_sur_data(p, n, seed, q, X_all, T_all, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const auto t1 = clk::now();
+    // fraction of lateral exits (the surrogate's support)
+    double lateral = 0.0;
+    if (e == cudaSuccess) {
+        std::vector<float> T((size_t)std::min<long long>(n, 1 << 20) * SUR_TSTRIDE);
+        e = d2h(T.data(), T_all, T.size() * 4, st);
+        for (size_t i = 0; i < T.size() / SUR_TSTRIDE; ++i) lateral += T[i * SUR_TSTRIDE + 5];
+        lateral /= (double)(T.size() / SUR_TSTRIDE);
+    }
+    TrainWS w;
+    memset(&w, 0, sizeof(w));
+    if (e == cudaSuccess) e = ws_create(w, B);
+    unsigned int *err = gemm_err_flag();
+    s->err = err;
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, st);
+    // 2. stage 1: regression outputs, Adam with a cosine learning-rate schedule after a short warm-up
+    const long long steps_per_epoch = std::max<long long>(1, n / B);
+    const long long total1 = steps_per_epoch * std::max(epochs, 1);
+    const double lr0 = 2e-3;
+    double loss1 = 0.0, loss2 = 0.0;
+    for (long long k = 0; k < total1 && e == cudaSuccess; ++k) {
+        const double warm = std::min(1.0, (double)(k + 1) / 200.0);
+        const float lr = (float)(lr0 * warm * (0.02 + 0.98 * 0.5 * (1.0 + std::cos(M_PI * (double)k / total1))));
+        if (k == total1 - steps_per_epoch) cudaMemsetAsync(w.loss, 0, 8, st);
+        k_sur_gather<<<(B + 255) / 256, 256, 0, st>>>(X_all, T_all, n, seed ^ 0x7261696eull, k, B, 0, 0, w.Xb, w.XTb,
+                                                     w.Tb);
+        e = train_step(s, w, 1, lr, st);
+    }
+    if (e == cudaSuccess) {
+        double acc = 0;
+        e = d2h(&acc, w.loss, 8, st);
+        loss1 = acc / (double)steps_per_epoch;
+    }
+    // 3. confidence targets: the exit error of the trained regression on every training ray
+    for (long long i0 = 0; i0 < n && e == cudaSuccess; i0 += B) {
+        k_sur_gather<<<(B + 255) / 256, 256, 0, st>>>(X_all, T_all, n, 0, 0, B, 1, i0, w.Xb, w.XTb, w.Tb);
+        e = train_forward(s, w, st);
+        if (e == cudaSuccess) e = launch_sur_conf_targets(p.R2, p.H, seed, i0, std::min<long long>(B, n - i0), w.Y, T_all, st);
+    }
+    // 4. stage 2: the confidence head alone (output layer, fresh Adam moments), L1 loss
+    if (e == cudaSuccess) {
+        SurDims d = sur_dims(SUR_L - 1);
+        cudaMemsetAsync(s->mW[SUR_L - 1], 0, (size_t)d.mw * d.kin * 4, st);
+        cudaMemsetAsync(s->vW[SUR_L - 1], 0, (size_t)d.mw * d.kin * 4, st);
+        cudaMemsetAsync(s->mb[SUR_L - 1], 0, (size_t)d.mw * 4, st);
+        cudaMemsetAsync(s->vb[SUR_L - 1], 0, (size_t)d.mw * 4, st);
+        s->adam_step = 0;
+    }
+    const long long total2 = steps_per_epoch * std::max(1, epochs / 3);
+    for (long long k = 0; k < total2 && e == cudaSuccess; ++k) {
+        const float lr = (float)(1e-3 * 0.5 * (1.0 + std::cos(M_PI * (double)k / total2)));
+        if (k == total2 - steps_per_epoch) cudaMemsetAsync(w.loss, 0, 8, st);
+        k_sur_gather<<<(B + 255) / 256, 256, 0, st>>>(X_all, T_all, n, seed ^ 0x636f6e66ull, k, B, 0, 0, w.Xb, w.XTb,
+                                                     w.Tb);
+        e = train_step(s, w, 2, lr, st);
+    }
+    if (e == cudaSuccess) {
+        double acc = 0;
+        e = d2h(&acc, w.loss, 8, st);
+        loss2 = acc / (double)steps_per_epoch;
+    }
+    unsigned int h = 0;
+    if (e == cudaSuccess) e = d2h(&h, err, 4, st);
+    ws_destroy(w);
+    cudaFree(data);
+    if (e != cudaSuccess) { why = cudaGetErrorString(e); return CLOAK_ECUDA; }
+    if (h) { why = "tensor-core GEMM timed out"; return CLOAK_ETIMEOUT; }
+    const auto t2 = clk::now();
+    s->trained = 1;
+    s->info[0] = loss1;
+    s->info[1] = loss2;
+    s->info[2] = lateral;
+    s->info[3] = (double)n;
+    s->info[4] = std::chrono::duration<double>(t2 - t0).count();
+    s->info[5] = std::chrono::duration<double>(t1 - t0).count();
+    s->info[6] = (double)(total1 + total2);
+    s->info[7] = (double)B;
+    return CLOAK_OK;
+}
+
+// ------------------------------------------------------------------ checkpoint: flat binary with a header
+struct SurFileHeader {
+    char magic[8];       // "CKSURR01"
+    int version, layers;
+    int dims[SUR_L + 1];
+    double R1, R2, H;
+    float gate;
+    int trained;
+    long long adam_step;
+    double info[8];
+};
+
+int sur_save(SurNet *s, const char *path, std::string &why) {
+    SurFileHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "CKSURR01", 8);
+    hd.version = 1;
+    hd.layers = SUR_L;
+    for (int l = 0; l < SUR_L; ++l) hd.dims[l] = sur_dims(l).in;
+    hd.dims[SUR_L] = SUR_OUT;
+    hd.R1 = s->R1; hd.R2 = s->R2; hd.H = s->H;
+    hd.gate = s->gate;
+    hd.trained = s->trained;
+    hd.adam_step = s->adam_step;
+    memcpy(hd.info, s->info, sizeof(hd.info));
+    FILE *f = fopen(path, "wb");
+    if (!f) { why = std::string("cannot open ") + path; return CLOAK_EINVAL; }
+    bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1;
+    std::vector<float> buf;
+    for (int l = 0; l < SUR_L && ok; ++l) {
+        SurDims d = sur_dims(l);
+        const size_t nw = (size_t)d.mw * d.kin, nb = (size_t)d.mw;
+        float *arrs[6] = {s->W[l], s->mW[l], s->vW[l], s->b[l], s->mb[l], s->vb[l]};
+        size_t sizes[6] = {nw, nw, nw, nb, nb, nb};
+        for (int a = 0; a < 6 && ok; ++a) {
+            buf.resize(sizes[a]);
+            ok = cudaMemcpy(buf.data(), arrs[a], sizes[a] * 4, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                 fwrite(buf.data(), 4, sizes[a], f) == sizes[a];
+        }
+    }
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) { why = std::string("cannot write ") + path; return CLOAK_ECUDA; }
+    return CLOAK_OK;
+}
+
+int sur_load(SurNet *s, const char *path, std::string &why) {
+    FILE *f = fopen(path, "rb");
+    if (!f) { why = std::string("cannot open ") + path; return CLOAK_EINVAL; }
+    SurFileHeader hd;
+    bool ok = fread(&hd, sizeof(hd), 1, f) == 1 && memcmp(hd.magic, "CKSURR01", 8) == 0 && hd.version == 1 &&
+              hd.layers == SUR_L;
+    for (int l = 0; l < SUR_L && ok; ++l) ok = hd.dims[l] == sur_dims(l).in;
+    ok = ok && hd.dims[SUR_L] == SUR_OUT;
+    if (!ok) { fclose(f); why = "not a surrogate checkpoint of this network"; return CLOAK_EINVAL; }
+    std::vector<float> buf;
+    for (int l = 0; l < SUR_L && ok; ++l) {
+        SurDims d = sur_dims(l);
+        const size_t nw = (size_t)d.mw * d.kin, nb = (size_t)d.mw;
+        float *arrs[6] = {s->W[l], s->mW[l], s->vW[l], s->b[l], s->mb[l], s->vb[l]};
+        size_t sizes[6] = {nw, nw, nw, nb, nb, nb};
+        for (int a = 0; a < 6 && ok; ++a) {
+            buf.resize(sizes[a]);
+            ok = fread(buf.data(), 4, sizes[a], f) == sizes[a] &&
+                 cudaMemcpy(arrs[a], buf.data(), sizes[a] * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+    }
+    fclose(f);
+    if (!ok) { why = std::string("truncated checkpoint ") + path; return CLOAK_EINVAL; }
+    s->R1 = hd.R1; s->R2 = hd.R2; s->H = hd.H;
+    s->gate = hd.gate;
+    s->trained = hd.trained;
+    s->adam_step = hd.adam_step;
+    memcpy(s->info, hd.info, sizeof(hd.info));
+    cudaError_t e = sur_refresh_bf16(s, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { why = cudaGetErrorString(e); return CLOAK_ECUDA; }
+    return CLOAK_OK;
+}
+
+// render hook: features of the queued rays, inference, gate
+
+cudaError_t sur_render_hook(void *ctx, const Queue &q, cudaStream_t st) {
+    SurRenderCtx *c = (SurRenderCtx *)ctx;
+    SurNet *s = c->s;
+    cudaError_t e = sur_ensure_inference(s, c->cap);
+    if (e != cudaSuccess) return e;
+    s->err = gemm_err_flag();
+    if ((e = launch_sur_features(c->p, c->mode, c->spp, c->seed, q, s, st)) != cudaSuccess) return e;
+    if ((e = sur_forward(s, s->inf_rows, q.count, st)) != cudaSuccess) return e;
+    return launch_sur_gate(c->p, c->mode, c->spp, c->seed, q, s, c->samples, c->recs, st);
+}
+
+}  // namespace ck

@@ -38,13 +38,18 @@ struct Queue {
     int *face;                         // surface crossed at exit (EV_LAT / EV_TOP / EV_BOT)
     int *key;                          // cost bucket of the ray (larger = more steps expected)
     int *perm;                         // integration order: slots sorted by descending cost bucket
-    unsigned int *count;               // [0] queued rays, [1] next ray of the integration kernel
-    unsigned int *bins;                // [nbins] bucket sizes, then [nbins] scatter cursors (nbins <= 256)
+    unsigned int *count;               // [0] queued rays, [1] next ray of the integration kernel,
+                                       // [2] rays to integrate, [4 + v] next ray of medium segment v
+    unsigned int *bins;                // [nbins] bucket sizes, [nbins] scatter cursors (nbins <= 256), then
+                                       // per medium segment v: [SEG_OFFSET + 2v] first index into perm, [+1] size
     long long cap;
 };
 
 constexpr int NBINS = 64;         // cost buckets of a single image
-constexpr int NBINS_BATCH = 256;  // cost bucket x medium/mode of a batch
+constexpr int NBINS_BATCH = 256;  // medium/mode x cost bucket of a batch: key = vm * NBINS + cost
+constexpr int SEG_OFFSET = 2 * NBINS_BATCH;
+__host__ __device__ constexpr int batch_key(int vm, int cost) { return vm * NBINS + cost; }
+__host__ __device__ constexpr int key_vm(int key) { return key / NBINS; }
 constexpr size_t QUEUE_HEADER_BYTES = 4096;
 constexpr size_t QUEUE_SLOT_BYTES = 8 * sizeof(double) + 6 * sizeof(int) + sizeof(float4);
 inline size_t queue_bytes(long long cap) { return QUEUE_HEADER_BYTES + (size_t)cap * QUEUE_SLOT_BYTES; }
@@ -122,8 +127,10 @@ __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned lo
     queue_append(q, y, w_out, (int)idx, cost_bucket(y, k0));
 }
 
-// Longest-first order: a counting sort of the queue by descending cost bucket.  k_wf_sort_scan turns
-// the bucket sizes into scatter cursors, k_wf_sort_scatter writes the permutation.
+// Longest-first order: a counting sort of the queue by descending key.  k_wf_sort_scan turns the bucket
+// sizes into scatter cursors and medium segments, k_wf_sort_scatter writes the permutation.  With the
+// batch key (medium major, cost minor) every medium occupies one contiguous segment of the permutation,
+// in descending cost order.
 __global__ void k_wf_sort_scan(Queue q, int nbins);
 __global__ void k_wf_sort_scatter(Queue q);
 
@@ -133,11 +140,14 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     typedef typename S::real R;
     S st;
     st.vm = 0;
-    const unsigned int n = q.count[0];
+    const unsigned int n = q.count[2];  // rays left to integrate after the sort
     const int nev = p.R1 > 0.0 ? 4 : 3;
     const R tol = (R)p.h_or_tol, h0 = INTEG == I_RK4 ? (R)p.h_or_tol : (R)1e-3;
     const R conv = sizeof(R) == 8 ? (R)CROSS_REL_TOL : (R)2.4e-7;  // bracket resolution of the crossing search
     constexpr int prefix = bisect_prefix<INTEG>();
+    // medium segments of the permutation (batch: one per medium/mode; a lane draws rays from its
+    // warp's current segment, so that the lanes of a warp evaluate one medium's equations)
+    int seg = VAR == V_ANY ? 3 - (int)(((blockIdx.x * blockDim.x + threadIdx.x) >> 5) & 3) : 0;
     // lane state
     R h = h0, t = 0;
     int steps = 0, phase = PH_IDLE, slot = -1;
@@ -146,30 +156,56 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     R hs = 0, fac = 1, lo = 0, hi = 0, glo = 0, ghi = 0, sbest = 0, g1[4];
     int ev = 0, evbest = -1, side = 0, it = 0;
     unsigned int pending = 0;
+    bool drained = false;  // the queue had no ray left for this lane
 
+    // Every lane of a warp stays in the loop until the whole warp is drained, and the warp reconverges
+    // before the one step evaluation of each iteration, which all its live lanes then run together
+    // (stepping and crossing search alike).
     for (;;) {
         // ---- refill: a lane without a ray takes the next queued one
-        if (phase == PH_IDLE) {
-            unsigned int k = atomicAdd(q.count + 1, 1u);
-            if (k < n) {
-                slot = q.perm[k];
+        if (phase == PH_IDLE && !drained) {
+            if (VAR == V_ANY) {
+                // the current segment first, then the others in descending medium order
+                for (int tries = 0; tries < 4; ++tries) {
+                    const unsigned int len = __ldg(q.bins + SEG_OFFSET + 2 * seg + 1);
+                    const unsigned int k = len ? atomicAdd(q.count + 4 + seg, 1u) : 0xffffffffu;
+                    if (k < len) {
+                        slot = q.perm[__ldg(q.bins + SEG_OFFSET + 2 * seg) + k];
+                        st.vm = seg;
+                        phase = PH_STEP;
+                        break;
+                    }
+                    seg = (seg + 3) & 3;
+                }
+            } else {
+                unsigned int k = atomicAdd(q.count + 1, 1u);
+                if (k < n) {
+                    slot = q.perm[k];
+                    phase = PH_STEP;
+                }
+            }
+            if (phase == PH_STEP) {
                 st.load(q.x, q.y, q.z, q.vx, q.vy, q.vz, slot);
-                if (VAR == V_ANY) st.vm = q.key[slot] & 3;
-                h = h0; t = 0; steps = 0; metal = false; phase = PH_STEP;
+                h = h0; t = 0; steps = 0; metal = false;
             }
         }
-        if (phase == PH_IDLE) break;  // queue drained for this lane
+        const bool live = phase != PH_IDLE;
+        if (!live) drained = true;
+        const unsigned int lm = __ballot_sync(0xffffffffu, live);
+        if (!lm) break;     // the whole warp is drained
+        if (!live) continue;
         int status = -1;
         if (phase == PH_STEP && (steps >= p.max_steps || (INTEG == I_DP45 && h < (R)1e-14))) status = CLOAK_RAY_STEP_LIMIT;
+        R s = phase == PH_STEP ? h : sbest;
+        if (phase == PH_CROSS) {
+            // next trial point: bisection prefix, then Illinois regula falsi (see crossing())
+            if (it < prefix) s = (R)0.5 * (lo + hi);
+            else if (it - prefix < 60 && ghi > glo) s = (lo * ghi - hi * glo) / (ghi - glo);
+            else s = (R)0.5 * (lo + hi);
+            if (!(s > lo && s < hi)) s = (R)0.5 * (lo + hi);
+        }
+        __syncwarp(lm);  // a convergence point: keeps the compiler from splitting the evaluation by phase
         if (status < 0) {
-            R s = phase == PH_STEP ? h : sbest;
-            if (phase == PH_CROSS) {
-                // next trial point: bisection prefix, then Illinois regula falsi (see crossing())
-                if (it < prefix) s = (R)0.5 * (lo + hi);
-                else if (it - prefix < 60 && ghi > glo) s = (lo * ghi - hi * glo) / (ghi - glo);
-                else s = (R)0.5 * (lo + hi);
-                if (!(s > lo && s < hi)) s = (R)0.5 * (lo + hi);
-            }
             st.eval(p, s);
             if (phase == PH_STEP) {
                 ++steps;
@@ -321,6 +357,7 @@ __global__ void __launch_bounds__(128) k_wf_exit(Params p, int spp, unsigned lon
                                                  float4 *samples, cloak_record *recs) {
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (q.key[k] < 0) continue;  // finished before the integration (learned surrogate)
         long long idx = q.id[k];
         long long pix = idx / spp;
         int s = (int)(idx - pix * spp);
@@ -342,12 +379,13 @@ namespace ck {
 
 template <int V, int M, int I, int PREC>
 static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long seed, const Queue &q, float4 *samples,
-                                 cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev) {
+                                 cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev, const WfHook *hook) {
     long long n = (long long)p.W * p.Hp * spp;
     const int bs = 128;
     k_wf_entry<V, M><<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(p, spp, seed, q, samples, recs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (hook && (e = hook->fn(hook->ctx, q, st)) != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -378,27 +416,28 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
 
 template <int V, int M, int I>
 static cudaError_t wavefront_vmi(const Params &p, int spp, unsigned long long seed, const Queue &q, float4 *samples,
-                                 cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev) {
-    if (p.precision != 0) return wavefront_vmip<V, M, I, 1>(p, spp, seed, q, samples, recs, packet, st, ev);
-    return wavefront_vmip<V, M, I, 0>(p, spp, seed, q, samples, recs, packet, st, ev);
+                                 cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev, const WfHook *hook) {
+    if (p.precision != 0) return wavefront_vmip<V, M, I, 1>(p, spp, seed, q, samples, recs, packet, st, ev, hook);
+    return wavefront_vmip<V, M, I, 0>(p, spp, seed, q, samples, recs, packet, st, ev, hook);
 }
 
 template <int V>
 cudaError_t launch_wavefront_v(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q,
-                               float4 *samples, cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev) {
+                               float4 *samples, cloak_record *recs, int packet, cudaStream_t st, cudaEvent_t *ev,
+                               const WfHook *hook) {
     if (mode == M_ORD && p.integ == I_RK4)
-        return wavefront_vmi<V, M_ORD, I_RK4>(p, spp, seed, q, samples, recs, packet, st, ev);
+        return wavefront_vmi<V, M_ORD, I_RK4>(p, spp, seed, q, samples, recs, packet, st, ev, hook);
     if (mode == M_ORD && p.integ == I_DP45)
-        return wavefront_vmi<V, M_ORD, I_DP45>(p, spp, seed, q, samples, recs, packet, st, ev);
+        return wavefront_vmi<V, M_ORD, I_DP45>(p, spp, seed, q, samples, recs, packet, st, ev, hook);
     if (mode == M_EXT && p.integ == I_RK4)
-        return wavefront_vmi<V, M_EXT, I_RK4>(p, spp, seed, q, samples, recs, packet, st, ev);
+        return wavefront_vmi<V, M_EXT, I_RK4>(p, spp, seed, q, samples, recs, packet, st, ev, hook);
     if (mode == M_EXT && p.integ == I_DP45)
-        return wavefront_vmi<V, M_EXT, I_DP45>(p, spp, seed, q, samples, recs, packet, st, ev);
+        return wavefront_vmi<V, M_EXT, I_DP45>(p, spp, seed, q, samples, recs, packet, st, ev, hook);
     return cudaErrorInvalidValue;
 }
 
 #define CK_INSTANTIATE_WAVEFRONT(V)                                                                        \
     template cudaError_t launch_wavefront_v<V>(const Params &, int, int, unsigned long long, const Queue &, \
-                                               float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *);
+                                               float4 *, cloak_record *, int, cudaStream_t, cudaEvent_t *, const WfHook *);
 
 }  // namespace ck
