@@ -217,7 +217,7 @@ int orc_sur_targets(double R2, double H, const double P[3], const double d[3], c
     double phi = entry_local(P, d, &dr, &dt, &dz);
     double beta = atan2(dt, -dr);
     double psi = atan2(rec->exit_pos[1], rec->exit_pos[0]) - (phi + PI - 2.0 * beta);
-    t[0] = rec->exit_pos[2] / (0.5 * H);
+    t[0] = (rec->exit_pos[2] - P[2]) / (2.0 * R2);
     t[1] = cos(psi);
     t[2] = sin(psi);
     t[3] = rec->tof / 4.0;
@@ -234,7 +234,7 @@ void orc_sur_reconstruct(double R2, double H, const double P[3], const double d[
     frame(phe, rh, th);
     exit_pos[0] = R2 * rh[0];
     exit_pos[1] = R2 * rh[1];
-    exit_pos[2] = y[0] * 0.5 * H;
+    exit_pos[2] = P[2] + y[0] * 2.0 * R2;
     /* k_z and L_z conserved, radial component outward */
     for (int k = 0; k < 3; ++k) exit_dir[k] = -dr * rh[k] + dt * th[k];
     exit_dir[2] = dz;

@@ -70,10 +70,11 @@ void orc_sur_sample(uint64_t seed, uint64_t i, double R2, double H, double P[3],
 void orc_sur_features(double R1, double R2, double H, int variant, int mode, const double P[3], const double d[3],
                       double x[7]);
 
-/* Regression targets of a traced ray (outputs 0..3): exit z/(H/2), cos psi, sin psi, tof/4,
- * psi = exit azimuth - (entry azimuth + pi - 2 beta) (the azimuth the straight line would
- * reach).  Returns 1 if the ray left through the lateral surface (the targets are
- * defined), else 0. */
+/* Regression targets of a traced ray (outputs 0..3): (exit z - entry z) / (2 R2), cos psi,
+ * sin psi, tof/4, psi = exit azimuth - (entry azimuth + pi - 2 beta) (the azimuth the straight
+ * line would reach).  All four are functions of the direction angles, mode and variant alone:
+ * the media are invariant under translation along the axis and rotation about it.  Returns 1
+ * if the ray left through the lateral surface (the targets are defined), else 0. */
 int orc_sur_targets(double R2, double H, const double P[3], const double d[3], const orc_record *rec,
                     double t[4]);
 
