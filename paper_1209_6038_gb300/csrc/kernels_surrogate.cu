@@ -18,9 +18,14 @@ __global__ void __launch_bounds__(256) k_sur_features(Params p, int mode, int sp
         const bool lateral = fabs(hypot(P[0], P[1]) - p.R2) <= 1e-9 * p.R2 && fabs(P[2]) < p.halfH;
         float x[SUR_IN];
         sur_features(p.R1, p.R2, p.H, p.variant == V_AZIMUTHAL ? 1 : 0, mode, P, d, x);
+        // each input as a BF16 pair (hi, lo) in columns j and SUR_IN + j (the first layer weighs both alike)
         __nv_bfloat16 *row = X + (size_t)k * 64;
 #pragma unroll
-        for (int j = 0; j < SUR_IN; ++j) row[j] = __float2bfloat16_rn(x[j]);
+        for (int j = 0; j < SUR_IN; ++j) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x[j]);
+            row[j] = hi;
+            row[SUR_IN + j] = __float2bfloat16_rn(x[j] - __bfloat162float(hi));
+        }
         elig[k] = lateral ? 1 : 0;
     }
 }
@@ -32,8 +37,11 @@ __global__ void __launch_bounds__(128) k_sur_gate(Params p, int mode, int spp, u
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         if (!elig[k]) continue;
         const float *y = Y + (size_t)k * 16;
-        if (!(y[4] <= gate) || !(fabsf(y[0]) < 1.f) || !(y[1] * y[1] + y[2] * y[2] > 0.f)) continue;
+        if (!(y[4] <= gate) || !(y[1] * y[1] + y[2] * y[2] > 0.f)) continue;
         const double P[3] = {q.x[k], q.y[k], q.z[k]};
+        // the height moves monotonically along the ray: a predicted exit inside the lateral surface
+        // means no cap was crossed
+        if (!(fabs(P[2] + 2.0 * p.R2 * (double)y[0]) < p.halfH)) continue;
         const long long idx = q.id[k], pix = idx / spp;
         double o[3], d[3];
         camera_ray(p, (int)(pix % p.W), (int)(pix / p.W), (int)(idx - pix * spp), spp, seed, o, d);
@@ -78,9 +86,11 @@ __global__ void k_sur_conf(double R2, double H, unsigned long long seed, long lo
     sur_reconstruct(R2, H, P, d, T, p0, d0, t0);
     double cx = d1[1] * d0[2] - d1[2] * d0[1], cy = d1[2] * d0[0] - d1[0] * d0[2], cz = d1[0] * d0[1] - d1[1] * d0[0];
     double ang = atan2(sqrt(cx * cx + cy * cy + cz * cz), d1[0] * d0[0] + d1[1] * d0[1] + d1[2] * d0[2]);
+    // exit error as seen in the image: the room's walls are about ten cylinder radii away, so moving the
+    // exit point by dp moves the room point as much as turning the exit ray by dp / (10 R2)
     double dp = sqrt((p1[0] - p0[0]) * (p1[0] - p0[0]) + (p1[1] - p0[1]) * (p1[1] - p0[1]) +
-                     (p1[2] - p0[2]) * (p1[2] - p0[2])) / R2;
-    T[4] = (float)log10(fmax(fmax(ang, dp), 1e-7));
+                     (p1[2] - p0[2]) * (p1[2] - p0[2])) / (10.0 * R2);
+    T[4] = (float)log10(fmax(ang + dp, 1e-7));
 }
 
 static int sm_count() {

@@ -69,7 +69,10 @@ __device__ __forceinline__ void sur_features(double R1, double R2, double H, int
     x[6] = (float)(R1 / R2);
 }
 
-// regression targets of a traced ray; false unless it left through the lateral surface
+// regression targets of a traced ray: (exit z - entry z) / (2 R2), cos psi, sin psi, tof / 4 with psi the
+// exit azimuth's departure from the straight line's -- functions of the direction angles, mode and variant
+// alone (both media are invariant under rotation about the axis and translation along it); false unless
+// the ray left through the lateral surface
 __device__ __forceinline__ bool sur_targets(double R2, double H, const double P[3], const double d[3],
                                             const cloak_record &rec, float t[4]) {
     if (rec.status != CLOAK_RAY_EXITED && rec.status != CLOAK_RAY_HIT_METAL_EXITED) return false;
@@ -80,7 +83,7 @@ __device__ __forceinline__ bool sur_targets(double R2, double H, const double P[
     const double psi = atan2(rec.exit_pos[1], rec.exit_pos[0]) - (phi + M_PI - 2.0 * atan2(dt, -dr));
     double s, c;
     sincos(psi, &s, &c);
-    t[0] = (float)(rec.exit_pos[2] / (0.5 * H));
+    t[0] = (float)((rec.exit_pos[2] - P[2]) / (2.0 * R2));  // translation along the axis: a height change
     t[1] = (float)c;
     t[2] = (float)s;
     t[3] = (float)(rec.tof * 0.25);
@@ -97,7 +100,7 @@ __device__ __forceinline__ void sur_reconstruct(double R2, double H, const doubl
     sur_frame(phe, rh, th);
     pos[0] = R2 * rh[0];
     pos[1] = R2 * rh[1];
-    pos[2] = (double)y[0] * 0.5 * H;
+    pos[2] = P[2] + (double)y[0] * 2.0 * R2;
     dir[0] = -dr * rh[0] + dt * th[0];
     dir[1] = -dr * rh[1] + dt * th[1];
     dir[2] = dz;

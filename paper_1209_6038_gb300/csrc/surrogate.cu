@@ -32,20 +32,51 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-// batch rows from the training set: random rows (sequential = 0) or rows i0 .. i0 + B - 1
+// Optimiser schedule kept on the device, so that a captured training step replays unchanged: step
+// counter (batch choice and Adam bias corrections) and the learning rate of the current step.
+struct SurSched {
+    long long step;   // steps taken (this one included, after k_sur_sched_next)
+    long long total;  // length of the cosine schedule
+    float lr0, floor; // peak rate; the cosine decays to floor * lr0
+    int warm;         // linear warm-up steps
+    float lr, c1, c2; // this step: rate, 1 - beta1^step, 1 - beta2^step
+};
+
+__global__ void k_sur_sched_next(SurSched *sc) {
+    const long long k = sc->step;
+    sc->step = k + 1;
+    const float w = fminf(1.f, (float)(k + 1) / (float)sc->warm);
+    const float cs = 0.5f * (1.f + cospif(fminf((float)k / (float)sc->total, 1.f)));
+    sc->lr = sc->lr0 * w * (sc->floor + (1.f - sc->floor) * cs);
+    sc->c1 = 1.f - powf(0.9f, (float)(k + 1));
+    sc->c2 = 1.f - powf(0.999f, (float)(k + 1));
+}
+
+// An input enters the first GEMM as a BF16 pair (hi, lo), hi + lo = x to about 16 significant bits, in
+// columns j and SUR_IN + j; both columns carry the same weight, so the product is W x without the 8-bit
+// rounding of x (a quantisation of the direction angles by up to 2^-8 of pi/2 otherwise).
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// batch rows from the training set: random rows (sc: step counter) or rows i0 .. i0 + B - 1 (sc null)
 __global__ void k_sur_gather(const float *X_all, const float *T_all, long long n, unsigned long long seed,
-                             long long step, int B, int sequential, long long i0, __nv_bfloat16 *Xb,
-                             __nv_bfloat16 *XTb, float *Tb) {
+                             const SurSched *sc, int B, long long i0, __nv_bfloat16 *Xb, __nv_bfloat16 *XTb,
+                             float *Tb) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    long long idx = sequential ? i0 + b : (long long)(mix64(mix64(seed) ^ (uint64_t)(step * B + b)) % (uint64_t)n);
+    long long idx = !sc ? i0 + b : (long long)(mix64(mix64(seed) ^ (uint64_t)(sc->step * B + b)) % (uint64_t)n);
     if (idx >= n) idx = n - 1;
     const float *x = X_all + idx * SUR_XSTRIDE;
 #pragma unroll
     for (int j = 0; j < SUR_IN; ++j) {
-        __nv_bfloat16 v = __float2bfloat16_rn(x[j]);
-        Xb[(size_t)b * 64 + j] = v;
-        XTb[(size_t)j * B + b] = v;
+        __nv_bfloat16 hi, lo;
+        split_bf16(x[j], hi, lo);
+        Xb[(size_t)b * 64 + j] = hi;
+        Xb[(size_t)b * 64 + SUR_IN + j] = lo;
+        XTb[(size_t)j * B + b] = hi;
+        XTb[(size_t)(SUR_IN + j) * B + b] = lo;
     }
     const float *t = T_all + idx * SUR_TSTRIDE;
 #pragma unroll
@@ -101,36 +132,44 @@ __global__ void k_sur_rowsum(const __nv_bfloat16 *M, int cols, float *out) {
     }
 }
 
-struct AdamArgs {
-    float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
-};
-
-// One Adam step of layer l (weights r < out, c < in, and the bias), then the BF16 copies W (nout x kin)
-// and W^T (kin x kb).  One thread per element of the (mw + 1) x kin grid; row mw is the bias.
+// One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; rate and bias corrections from the schedule) of
+// layer l (weights r < out, c < in, and the bias), then the BF16 copies W (nout x kin) and W^T
+// (kin x kb).  One thread per element of the mw x kin grid plus one per bias; sc null: copies only.
+// First layer: the weight of input j also multiplies its low part (column SUR_IN + j) and its gradient is
+// the sum of both columns'; the entry height and azimuth (inputs 0, 1) keep their weights (zero after
+// initialisation: the exit does not depend on them by the symmetry of the media).
 __global__ void k_sur_adam(SurDims dm, float *W, float *b, float *mW, float *vW, float *mb, float *vb,
-                           const float *gW, const float *gb, __nv_bfloat16 *Wb, __nv_bfloat16 *WTb, AdamArgs a,
-                           int update) {
+                           const float *gW, const float *gb, __nv_bfloat16 *Wb, __nv_bfloat16 *WTb,
+                           const SurSched *sc) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nW = (long long)dm.mw * dm.kin;
+    const bool update = sc != nullptr;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float lr = update ? sc->lr : 0.f, c1 = update ? sc->c1 : 1.f, c2 = update ? sc->c2 : 1.f;
     if (e < nW) {
         const int r = (int)(e / dm.kin), c = (int)(e % dm.kin);
-        if (update && r < dm.out && c < dm.in) {
-            const float g = gW[e];
-            const float m = a.b1 * mW[e] + (1.f - a.b1) * g, v = a.b2 * vW[e] + (1.f - a.b2) * g * g;
+        const bool first = dm.in == SUR_IN;
+        if (first && c >= SUR_IN && c < 2 * SUR_IN) return;  // low-part column: written with its input's
+        if (update && r < dm.out && c < dm.in && !(first && c < 2)) {
+            const float g = first ? gW[e] + gW[e + SUR_IN] : gW[e];
+            const float m = b1 * mW[e] + (1.f - b1) * g, v = b2 * vW[e] + (1.f - b2) * g * g;
             mW[e] = m;
             vW[e] = v;
-            W[e] -= a.lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+            W[e] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
         }
         const __nv_bfloat16 wb = __float2bfloat16_rn(W[e]);
-        if (r < dm.nout) Wb[(size_t)r * dm.kin + c] = wb;
+        if (r < dm.nout) {
+            Wb[(size_t)r * dm.kin + c] = wb;
+            if (first && c < SUR_IN) Wb[(size_t)r * dm.kin + SUR_IN + c] = wb;
+        }
         if (r < dm.kb) WTb[(size_t)c * dm.kb + r] = wb;
     } else if (e < nW + dm.out && update) {
         const int r = (int)(e - nW);
         const float g = gb[r];
-        const float m = a.b1 * mb[r] + (1.f - a.b1) * g, v = a.b2 * vb[r] + (1.f - a.b2) * g * g;
+        const float m = b1 * mb[r] + (1.f - b1) * g, v = b2 * vb[r] + (1.f - b2) * g * g;
         mb[r] = m;
         vb[r] = v;
-        b[r] -= a.lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+        b[r] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
     }
 }
 
@@ -139,7 +178,7 @@ __global__ void k_sur_pack(const float *x, long long n, __nv_bfloat16 *X) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
 #pragma unroll
-    for (int j = 0; j < SUR_IN; ++j) X[(size_t)i * 64 + j] = __float2bfloat16_rn(x[i * SUR_IN + j]);
+    for (int j = 0; j < SUR_IN; ++j) split_bf16(x[i * SUR_IN + j], X[(size_t)i * 64 + j], X[(size_t)i * 64 + SUR_IN + j]);
 }
 __global__ void k_sur_unpack(const float *Y, long long n, float *y) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,9 +193,12 @@ __global__ void k_sur_pack_batch(const float *x, const float *t, int B, __nv_bfl
     if (b >= B) return;
 #pragma unroll
     for (int j = 0; j < SUR_IN; ++j) {
-        const __nv_bfloat16 v = __float2bfloat16_rn(x[(size_t)b * SUR_IN + j]);
-        Xb[(size_t)b * 64 + j] = v;
-        XTb[(size_t)j * B + b] = v;
+        __nv_bfloat16 hi, lo;
+        split_bf16(x[(size_t)b * SUR_IN + j], hi, lo);
+        Xb[(size_t)b * 64 + j] = hi;
+        Xb[(size_t)b * 64 + SUR_IN + j] = lo;
+        XTb[(size_t)j * B + b] = hi;
+        XTb[(size_t)(SUR_IN + j) * B + b] = lo;
     }
 #pragma unroll
     for (int j = 0; j < SUR_TSTRIDE; ++j) Tb[(size_t)b * SUR_TSTRIDE + j] = t[(size_t)b * SUR_TSTRIDE + j];
@@ -244,7 +286,7 @@ SurNet *sur_create(double R1, double R2, double H, unsigned long long seed, cons
         host.assign((size_t)d.mw * d.kin, 0.f);
         const double sd = (l == SUR_L - 1 ? 0.1 : 1.0) / std::sqrt((double)d.in);
         for (int r = 0; r < d.out; ++r)
-            for (int c = 0; c < d.in; ++c) {
+            for (int c = (l == 0 ? 2 : 0); c < d.in; ++c) {
                 const uint64_t k = ((uint64_t)l << 40) ^ ((uint64_t)r << 20) ^ (uint64_t)c;
                 const double u1 = host_uniform(seed, 2 * k) + 0x1.0p-54, u2 = host_uniform(seed, 2 * k + 1);
                 host[(size_t)r * d.kin + c] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2));
@@ -267,22 +309,17 @@ void sur_destroy(SurNet *s) {
     delete s;
 }
 
-static cudaError_t adam_all(SurNet *s, const AdamArgs &a, int update, int first_layer, cudaStream_t st) {
+static cudaError_t adam_all(SurNet *s, const SurSched *sc, int first_layer, cudaStream_t st) {
     for (int l = first_layer; l < SUR_L; ++l) {
         SurDims d = sur_dims(l);
         const long long n = (long long)d.mw * d.kin + d.out;
         k_sur_adam<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, s->W[l], s->b[l], s->mW[l], s->vW[l], s->mb[l],
-                                                               s->vb[l], s->gW[l], s->gb[l], s->Wb[l], s->WTb[l], a,
-                                                               update);
+                                                               s->vb[l], s->gW[l], s->gb[l], s->Wb[l], s->WTb[l], sc);
     }
     return cudaGetLastError();
 }
 
-cudaError_t sur_refresh_bf16(SurNet *s, cudaStream_t st) {
-    AdamArgs a;
-    memset(&a, 0, sizeof(a));
-    return adam_all(s, a, 0, 0, st);
-}
+cudaError_t sur_refresh_bf16(SurNet *s, cudaStream_t st) { return adam_all(s, nullptr, 0, st); }
 
 cudaError_t sur_ensure_inference(SurNet *s, long long rows) {
     rows = (rows + 127) / 128 * 128;
@@ -340,6 +377,7 @@ struct TrainWS {
     __nv_bfloat16 *Xb, *XTb, *H[4], *HT[4], *dY, *dYT, *dZ[2], *dZT[2];
     float *Tb, *Z[4], *Y;
     double *loss;
+    SurSched *sched;
     CUtensorMap tXb, tXTb, tH[4], tHT[4], tdY, tdYT, tdZ[2], tdZT[2];
 };
 
@@ -349,7 +387,7 @@ static cudaError_t ws_create(TrainWS &w, int B) {
     const size_t x = align256((size_t)B * 64 * 2), z = align256((size_t)B * SUR_W * 4),
                  h = align256((size_t)B * SUR_W * 2), t = align256((size_t)B * SUR_TSTRIDE * 4),
                  y = align256((size_t)B * 16 * 4), dyt = align256((size_t)128 * B * 2);
-    const size_t bytes = 2 * x + t + 4 * z + 8 * h + y + x + dyt + 4 * h + 256;
+    const size_t bytes = 2 * x + t + 4 * z + 8 * h + y + x + dyt + 4 * h + 512;
     cudaError_t e = cudaMalloc(&w.arena, bytes);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemset(w.arena, 0, bytes)) != cudaSuccess) return e;
@@ -366,6 +404,7 @@ static cudaError_t ws_create(TrainWS &w, int B) {
     for (int j = 0; j < 2; ++j) { w.dZ[j] = (__nv_bfloat16 *)p; p += h; }
     for (int j = 0; j < 2; ++j) { w.dZT[j] = (__nv_bfloat16 *)p; p += h; }
     w.loss = (double *)p;
+    w.sched = (SurSched *)(p + 256);
     bool ok = tmap(&w.tXb, w.Xb, B, 64, GEMM_TILE_M) && tmap(&w.tXTb, w.XTb, 64, B, 64) &&
               tmap(&w.tdY, w.dY, B, 64, GEMM_TILE_M) && tmap(&w.tdYT, w.dYT, 128, B, GEMM_TILE_M);
     for (int l = 0; l < 4; ++l)
@@ -447,18 +486,55 @@ static cudaError_t train_backward(SurNet *s, TrainWS &w, int first, cudaStream_t
     return e;
 }
 
-static cudaError_t train_step(SurNet *s, TrainWS &w, int stage, float lr, cudaStream_t st) {
+// One optimiser step on the batch already in w (schedule advanced by k_sur_sched_next first).
+static cudaError_t train_step(SurNet *s, TrainWS &w, int stage, cudaStream_t st) {
     cudaError_t e = train_forward(s, w, st);
     if (e != cudaSuccess) return e;
     k_sur_loss<<<(w.B + 255) / 256, 256, 0, st>>>(w.Y, w.Tb, w.B, stage, w.dY, w.dYT, w.loss);
     e = train_backward(s, w, stage == 1 ? 0 : SUR_L - 1, st);
     if (e != cudaSuccess) return e;
-    s->adam_step++;
-    AdamArgs a;
-    a.lr = lr; a.b1 = 0.9f; a.b2 = 0.999f; a.eps = 1e-8f;
-    a.c1 = (float)(1.0 - std::pow(0.9, (double)s->adam_step));
-    a.c2 = (float)(1.0 - std::pow(0.999, (double)s->adam_step));
-    return adam_all(s, a, 1, stage == 1 ? 0 : SUR_L - 1, st);
+    return adam_all(s, w.sched, stage == 1 ? 0 : SUR_L - 1, st);
+}
+
+static cudaError_t sched_init(TrainWS &w, long long step0, long long total, float lr0, float floor, int warm,
+                              cudaStream_t st) {
+    SurSched h;
+    memset(&h, 0, sizeof(h));
+    h.step = step0; h.total = total > 0 ? total : 1; h.lr0 = lr0; h.floor = floor; h.warm = warm > 0 ? warm : 1;
+    cudaError_t e = cudaMemcpyAsync(w.sched, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+}
+
+// `steps` optimiser steps on random batches of the training set: the first eagerly, the rest as
+// replays of a captured CUDA graph of one step (schedule, batch, forward, loss, backward, Adam).  The
+// loss accumulator is cleared before the last `tail` steps.
+static cudaError_t run_steps(SurNet *s, TrainWS &w, int stage, long long steps, long long tail, const float *X_all,
+                             const float *T_all, long long n, unsigned long long seed, cudaStream_t st) {
+    const int B = w.B;
+    auto one = [&](cudaStream_t cs) -> cudaError_t {
+        k_sur_sched_next<<<1, 1, 0, cs>>>(w.sched);
+        k_sur_gather<<<(B + 255) / 256, 256, 0, cs>>>(X_all, T_all, n, seed, w.sched, B, 0, w.Xb, w.XTb, w.Tb);
+        return train_step(s, w, stage, cs);
+    };
+    if (steps <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(w.loss, 0, 8, st);
+    if (e == cudaSuccess && steps <= tail) e = cudaMemsetAsync(w.loss, 0, 8, st);
+    if (e == cudaSuccess) e = one(st);  // eager: sets the kernels' attributes outside any capture
+    if (e != cudaSuccess || steps == 1) return e;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    cudaError_t ec = one(st);
+    e = cudaStreamEndCapture(st, &g);
+    if (ec != cudaSuccess) e = ec;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    for (long long k = 1; k < steps && e == cudaSuccess; ++k) {
+        if (steps - k == tail) e = cudaMemsetAsync(w.loss, 0, 8, st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    return e;
 }
 
 static cudaError_t d2h(void *dst, const void *src, size_t bytes, cudaStream_t st) {
@@ -585,7 +661,13 @@ int sur_batch_grad(SurNet *s, const float *dev_x, const float *dev_t, long long 
     cudaMemsetAsync(w.loss, 0, 8, st);
     k_sur_pack_batch<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dev_x, dev_t, (int)n, w.Xb, w.XTb, w.Tb);
     if (lr > 0) {
-        e = train_step(s, w, stage, (float)lr, st);
+        // a constant rate: warm-up of one step, floor 1
+        e = sched_init(w, s->adam_step, 1, (float)lr, 1.f, 1, st);
+        if (e == cudaSuccess) {
+            k_sur_sched_next<<<1, 1, 0, st>>>(w.sched);
+            e = train_step(s, w, stage, st);
+        }
+        s->adam_step++;
     } else {
         e = train_forward(s, w, st);
         if (e == cudaSuccess) {
@@ -604,7 +686,8 @@ int sur_batch_grad(SurNet *s, const float *dev_x, const float *dev_t, long long 
             buf.resize((size_t)d.mw * d.kin);
             e = cudaMemcpy(buf.data(), s->gW[l], buf.size() * 4, cudaMemcpyDeviceToHost);
             for (int r = 0; r < d.out; ++r)
-                for (int c = 0; c < d.in; ++c) host_grad[o++] = buf[(size_t)r * d.kin + c];
+                for (int c = 0; c < d.in; ++c)
+                    host_grad[o++] = buf[(size_t)r * d.kin + c] + (l == 0 ? buf[(size_t)r * d.kin + SUR_IN + c] : 0.f);
             if (e == cudaSuccess) e = cudaMemcpy(host_grad + o, s->gb[l], (size_t)d.out * 4, cudaMemcpyDeviceToHost);
             o += d.out;
         }
@@ -616,16 +699,27 @@ int sur_batch_grad(SurNet *s, const float *dev_x, const float *dev_t, long long 
 }
 
 // Train on n rays traced by the integrator (parameters p: geometry, integrator, precision).
-int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, int epochs, cudaStream_t st,
+int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, int epochs, cudaStream_t caller,
               std::string &why) {
     using clk = std::chrono::steady_clock;
     const auto t0 = clk::now();
     const int B = 19456;  // 152 x 128: one 128-row tile per SM in the forward GEMMs
+    cudaError_t e = cudaStreamSynchronize(caller);
+    if (e != cudaSuccess) { why = cudaGetErrorString(e); return CLOAK_ECUDA; }
+    cudaStream_t st = nullptr;  // private stream: graph capture is not possible on the legacy default stream
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {
+        why = cudaGetErrorString(e);
+        return CLOAK_ECUDA;
+    }
     // 1. training set: the integrator traces n seeded rays
     const size_t qb = queue_bytes(n), xb = (size_t)n * SUR_XSTRIDE * 4, tb = (size_t)n * SUR_TSTRIDE * 4;
     char *data = nullptr;
-    cudaError_t e = cudaMalloc(&data, qb + xb + tb);
-    if (e != cudaSuccess) { why = "cannot allocate the training set"; return CLOAK_ENOMEM; }
+    e = cudaMalloc(&data, qb + xb + tb);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(st);
+        why = "cannot allocate the training set";
+        return CLOAK_ENOMEM;
+    }
     Queue q;
     float4 *unused = nullptr;
     carve_queue(data, n, q, &unused);
@@ -647,27 +741,17 @@ int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, 
     unsigned int *err = gemm_err_flag();
     s->err = err;
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, st);
-    // 2. stage 1: regression outputs, Adam with a cosine learning-rate schedule after a short warm-up
+    // 2. stage 1: regression outputs, Adam, linear warm-up then cosine decay to 2 % of the peak rate
     const long long steps_per_epoch = std::max<long long>(1, n / B);
     const long long total1 = steps_per_epoch * std::max(epochs, 1);
-    const double lr0 = 2e-3;
-    double loss1 = 0.0, loss2 = 0.0;
-    for (long long k = 0; k < total1 && e == cudaSuccess; ++k) {
-        const double warm = std::min(1.0, (double)(k + 1) / 200.0);
-        const float lr = (float)(lr0 * warm * (0.02 + 0.98 * 0.5 * (1.0 + std::cos(M_PI * (double)k / total1))));
-        if (k == total1 - steps_per_epoch) cudaMemsetAsync(w.loss, 0, 8, st);
-        k_sur_gather<<<(B + 255) / 256, 256, 0, st>>>(X_all, T_all, n, seed ^ 0x7261696eull, k, B, 0, 0, w.Xb, w.XTb,
-                                                     w.Tb);
-        e = train_step(s, w, 1, lr, st);
-    }
-    if (e == cudaSuccess) {
-        double acc = 0;
-        e = d2h(&acc, w.loss, 8, st);
-        loss1 = acc / (double)steps_per_epoch;
-    }
+    double loss1 = 0.0, loss2 = 0.0, acc = 0.0;
+    if (e == cudaSuccess) e = sched_init(w, 0, total1, 2e-3f, 0.02f, 200, st);
+    if (e == cudaSuccess) e = run_steps(s, w, 1, total1, steps_per_epoch, X_all, T_all, n, seed ^ 0x7261696eull, st);
+    if (e == cudaSuccess) e = d2h(&acc, w.loss, 8, st);
+    loss1 = acc / (double)std::min(steps_per_epoch, total1);
     // 3. confidence targets: the exit error of the trained regression on every training ray
     for (long long i0 = 0; i0 < n && e == cudaSuccess; i0 += B) {
-        k_sur_gather<<<(B + 255) / 256, 256, 0, st>>>(X_all, T_all, n, 0, 0, B, 1, i0, w.Xb, w.XTb, w.Tb);
+        k_sur_gather<<<(B + 255) / 256, 256, 0, st>>>(X_all, T_all, n, 0, nullptr, B, i0, w.Xb, w.XTb, w.Tb);
         e = train_forward(s, w, st);
         if (e == cudaSuccess) e = launch_sur_conf_targets(p.R2, p.H, seed, i0, std::min<long long>(B, n - i0), w.Y, T_all, st);
     }
@@ -678,29 +762,23 @@ int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, 
         cudaMemsetAsync(s->vW[SUR_L - 1], 0, (size_t)d.mw * d.kin * 4, st);
         cudaMemsetAsync(s->mb[SUR_L - 1], 0, (size_t)d.mw * 4, st);
         cudaMemsetAsync(s->vb[SUR_L - 1], 0, (size_t)d.mw * 4, st);
-        s->adam_step = 0;
     }
     const long long total2 = steps_per_epoch * std::max(1, epochs / 3);
-    for (long long k = 0; k < total2 && e == cudaSuccess; ++k) {
-        const float lr = (float)(1e-3 * 0.5 * (1.0 + std::cos(M_PI * (double)k / total2)));
-        if (k == total2 - steps_per_epoch) cudaMemsetAsync(w.loss, 0, 8, st);
-        k_sur_gather<<<(B + 255) / 256, 256, 0, st>>>(X_all, T_all, n, seed ^ 0x636f6e66ull, k, B, 0, 0, w.Xb, w.XTb,
-                                                     w.Tb);
-        e = train_step(s, w, 2, lr, st);
-    }
-    if (e == cudaSuccess) {
-        double acc = 0;
-        e = d2h(&acc, w.loss, 8, st);
-        loss2 = acc / (double)steps_per_epoch;
-    }
+    if (e == cudaSuccess) e = sched_init(w, 0, total2, 1e-3f, 0.f, 1, st);
+    if (e == cudaSuccess) e = run_steps(s, w, 2, total2, steps_per_epoch, X_all, T_all, n, seed ^ 0x636f6e66ull, st);
+    acc = 0.0;
+    if (e == cudaSuccess) e = d2h(&acc, w.loss, 8, st);
+    loss2 = acc / (double)std::min(steps_per_epoch, total2);
     unsigned int h = 0;
     if (e == cudaSuccess) e = d2h(&h, err, 4, st);
     ws_destroy(w);
     cudaFree(data);
+    cudaStreamDestroy(st);
     if (e != cudaSuccess) { why = cudaGetErrorString(e); return CLOAK_ECUDA; }
     if (h) { why = "tensor-core GEMM timed out"; return CLOAK_ETIMEOUT; }
     const auto t2 = clk::now();
     s->trained = 1;
+    s->adam_step = total2;
     s->info[0] = loss1;
     s->info[1] = loss2;
     s->info[2] = lateral;
