@@ -35,6 +35,18 @@ UNIT = "rays/s"
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 FP32_PEAK_TFLOPS = 152 * 2.070e9 * 256 / 1e12
 
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# dense BF16 tensor peak: measured on the GB300s (cuBLAS, burst), else the recipe's fallback
+BF16_PEAK_TFLOPS = float(_measured_peaks().get("bf16_tflops", 1900.0))
+
 # Algorithmic FP64 flops per integrator step attempt, counted from the source formulas
 # (FMA = 2 flops, division and square root = 1 flop each):
 #   RHS of Eq. 8 / Eq. 2 in closed cylindrical form: radial-e 41, azimuthal-e 37,
@@ -42,6 +54,11 @@ FP32_PEAK_TFLOPS = 152 * 2.070e9 * 256 / 1e12
 #   DP5(4) attempt: 6 new RHS + stage combinations (348) + error norm (30).
 #   RK4 step: 4 RHS + combinations (102).
 RHS_FLOPS = {(0, 0): 0, (0, 1): 41, (1, 0): 33, (1, 1): 37}
+
+# DRAM bytes (read + write) of one launch of the any-medium integration kernel on the full step: one
+# ncu capture of the same twelve views at 480x270 x 4 spp (81.0 MB read + 52.5 MB written) scaled by
+# samples (x 16.0).  To be re-captured whenever the kernel changes.
+INTEGRATE_TRAFFIC_BYTES = (81.048064e6 + 52.5056e6) * (1920 * 1080) / (480 * 270)
 DP45_FIXED, RK4_FIXED = 378, 102
 
 
@@ -178,6 +195,166 @@ def workload_config(w):
             "l2": "256 MiB buffer written between timed steps"}
 
 
+# ------------------------------------------------------------------ learned surrogate
+SUR_FLOPS_PER_RAY = 2 * (7 * 256 + 3 * 256 * 256 + 256 * 5)  # algorithmic multiply-adds x 2 of one forward pass
+
+
+def surrogate_section(args, ck, inputs, torch, np, flush):
+    """Train the surrogate once on rays traced by the FP64 integrator, then render the views of the
+    surrogate workload with it (integrator fallback) and with the FP64 integrator alone: rays/s of both,
+    the share of rays the surrogate finished, the image error against the FP64 integrator, and the
+    tensor-core roofline of the network's forward pass."""
+    import tempfile
+    sw = inputs.SURROGATE
+    integ = ck.DP45 if sw.integrator == "dp45" else ck.RK4
+    trainer = ck.Cloak(ck.RADIAL).integrator(integ, sw.h_or_tol, ck.FP64, sw.max_steps)
+    t0 = time.perf_counter()
+    ck.cloak_surrogate_train(trainer.h, sw.extra["train_rays"], sw.extra["train_seed"], args.sur_epochs)
+    train_wall = time.perf_counter() - t0
+    info = ck.cloak_surrogate_info(trainer.h)
+    path = os.path.join(tempfile.gettempdir(), f"cloak_surrogate_{os.getpid()}.bin")
+    ck.cloak_surrogate_save(trainer.h, path)
+    # forward pass of 2^22 rows on the tensor cores (5 GEMM launches per 2^20-row chunk)
+    n = 1 << 22
+    x = torch.rand((n, 7), device="cuda") * 2 - 1
+    y = torch.empty((n, 5), device="cuda")
+    ck.cloak_surrogate_forward(trainer.h, x, y)
+    reps, ms = 5, []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ck.cloak_surrogate_forward(trainer.h, x, y)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    fwd_ms = statistics.median(ms)
+    achieved = n * SUR_FLOPS_PER_RAY / (fwd_ms / 1e3) / 1e12
+    peak = BF16_PEAK_TFLOPS
+    trainer.close()
+    del x, y
+    hs = {}
+    for v in sw.variants:
+        for prec in (ck.FP64, ck.SURROGATE):
+            c = ck.Cloak(v).integrator(integ, sw.h_or_tol, prec, sw.max_steps).schedule(ck.SCHED_WAVEFRONT)
+            if prec == ck.SURROGATE:
+                ck.cloak_surrogate_load(c.h, path)
+                ck.cloak_surrogate_set_gate(c.h, sw.extra["gate_log10_err"])
+            hs[(v, prec)] = c
+    os.remove(path)
+    img = torch.empty((sw.height, sw.width, 4), dtype=torch.float32, device="cuda")
+
+    def view(c, e):
+        eye, tgt, up = inputs.camera_pose(e)
+        c.camera(eye, tgt, up, sw.hfov_deg, sw.width, sw.height)
+
+    def step(prec):
+        for v, m, e in sw.images:
+            c = hs[(v, prec)]
+            view(c, e)
+            c.render(m, sw.spp, sw.seed, out=img)
+
+    res = {}
+    for prec in (ck.FP64, ck.SURROGATE):
+        step(prec)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(2):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step(prec)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        res[prec] = statistics.mean(ts)
+    # image error against the FP64 integrator, ray by ray
+    rb = torch.empty(sw.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
+    tot = {"rays": 0, "entering": 0, "handled": 0, "tile_all": 0, "tile_cloak": 0, "status": 0}
+    errs = []
+    for v, m, e in sw.images:
+        recs = []
+        for prec in (ck.FP64, ck.SURROGATE):
+            c = hs[(v, prec)]
+            view(c, e)
+            c.render_records(m, sw.spp, sw.seed, out=rb)
+            # every 7th sample of the image (about 1.2 million rays per image)
+            recs.append(ck.records_to_numpy(rb.view(-1, ck.RECORD_BYTES)[::7].contiguous().reshape(-1)))
+        a, b = recs
+        entering = a["status"] != 0
+        handled = (b["steps"] == 0) & np.isin(b["status"], [1, 2])
+        diff = a["tile_id"] != b["tile_id"]
+        tot["rays"] += a.size
+        tot["entering"] += int(entering.sum())
+        tot["handled"] += int(handled.sum())
+        tot["tile_all"] += int(diff.sum())
+        tot["tile_cloak"] += int((diff & entering).sum())
+        tot["status"] += int((a["status"] != b["status"]).sum())
+        da, db = a["exit_dir"][handled], b["exit_dir"][handled]
+        errs.append(np.arctan2(np.linalg.norm(np.cross(da, db), axis=-1), np.sum(da * db, axis=-1)))
+    for c in hs.values():
+        c.close()
+    err = np.concatenate(errs)
+    rays = sw.rays
+    return {"workload": sw.name, "value": rays / (res[ck.SURROGATE] / 1e3), "unit": "rays/s",
+            "ms_per_step": res[ck.SURROGATE], "fp64_integrator": {"value": rays / (res[ck.FP64] / 1e3),
+                                                                   "ms_per_step": res[ck.FP64]},
+            "speedup_vs_fp64_integrator": res[ck.FP64] / res[ck.SURROGATE], "warmup": 1, "steps": 2,
+            "gate_log10_err": sw.extra["gate_log10_err"],
+            "handled_frac_of_entering": tot["handled"] / max(1, tot["entering"]),
+            "image_error_vs_fp64": {"sample": "every 7th ray of every view", "rays_compared": tot["rays"],
+                                    "tile_differs_frac": tot["tile_all"] / tot["rays"],
+                                    "tile_differs_frac_of_cloak_rays": tot["tile_cloak"] / max(1, tot["entering"]),
+                                    "status_differs_frac": tot["status"] / tot["rays"],
+                                    "handled_exit_dir_err_rad": {"median": float(np.median(err)) if err.size else None,
+                                                                 "p99": float(np.quantile(err, 0.99)) if err.size else None,
+                                                                 "max": float(err.max()) if err.size else None}},
+            "training": {**{k: float(v) for k, v in info.items()}, "wall_s": train_wall, "epochs": args.sur_epochs},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) of measured",
+                         "kernel": "k_gemm_tc (tcgen05 BF16, FP32 accumulation): forward pass of 2^22 rows",
+                         "flops_per_ray": SUR_FLOPS_PER_RAY, "ms": fwd_ms}}
+
+
+# ------------------------------------------------------------------ batched orbit
+def orbit_section(args, ck, inputs, torch, flush):
+    """The seeded 64-pose orbit (both cloaks and polarizations per pose, resolutions drawn from
+    256^2 ... 3840x2160, 1 spp, DP5(4) tol 1e-9 FP64) in ONE batched render: one persistent integration
+    kernel over every view, replayed as a CUDA graph.  The packet size comes from the autotuner, run on
+    the same orbit with a quarter of each image side."""
+    from paper_1209_6038_gb300 import autotune
+    views = inputs.batched_views(64, 0)
+    w = inputs.FULL
+    c = ck.Cloak(ck.RADIAL).integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol, ck.FP64,
+                                       w.max_steps)
+    c.schedule(ck.SCHED_WAVEFRONT).stage_timing(True)
+    small = [(v, p, eye, tgt, up, fov, torch.empty((max(1, H // 4), max(1, W // 4), 4), device="cuda"))
+             for (v, p, eye, tgt, up, fov, W, H) in views]
+    best, tune_ms = autotune.tune_packet(c, lambda: ck.cloak_render_batch(c.h, small, 1, 0), key="orbit64/4",
+                                         use_cache=False)
+    del small
+    outs = [(v, p, eye, tgt, up, fov, torch.empty((H, W, 4), device="cuda"))
+            for (v, p, eye, tgt, up, fov, W, H) in views]
+    rays = sum(o[-1].shape[0] * o[-1].shape[1] for o in outs)
+    ck.cloak_render_batch(c.h, outs, 1, 0)  # capture + first replay
+    torch.cuda.synchronize()
+    flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    ck.cloak_render_batch(c.h, outs, 1, 0)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    st = c.stage_times()
+    c.close()
+    del outs
+    return {"workload": "64 seeded orbit poses x 2 variants x 2 pols (256 views), resolutions from "
+                        "{256x256, 1024x768, 1920x1080, 3840x2160}, 1 spp, DP45 tol=1e-9 FP64, one batched render",
+            "views": len(views), "rays": rays, "value": rays / (ms / 1e3), "unit": "rays/s", "ms_per_step": ms,
+            "warmup": 1, "steps": 1, "packet": best, "autotune_ms": {str(k): v for k, v in tune_ms.items()},
+            "stage_ms": {"camera_entry_sort": st[0], "integrate": st[1], "exit_shade": st[2], "resolve": st[3]}}
+
+
 # ------------------------------------------------------------------ native arm
 def main():
     ap = argparse.ArgumentParser()
@@ -190,8 +367,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-orbit", action="store_true")
+    ap.add_argument("--sur-epochs", type=int, default=60, help="stage-1 epochs of the surrogate's training")
     ap.add_argument("--profile-image", default=None,
                     help="VARIANT,MODE,ELEV: render only this image twice (for profilers), e.g. 1,1,20")
+    ap.add_argument("--profile-gemm", action="store_true",
+                    help="run the surrogate network's forward pass (seeded initial weights) twice on 2^20 rows, "
+                         "for profilers")
     ap.add_argument("--profile-batch", action="store_true",
                     help="render the step's 12 images through the batched path twice at --width x --height "
                          "(default 480x270), for profilers")
@@ -236,6 +419,19 @@ def main():
         c.close()
         return 0
 
+    if args.profile_gemm:
+        c = ck.Cloak(ck.RADIAL)
+        ck.cloak_surrogate_params(c.h, ck.cloak_surrogate_params(c.h))  # creates the network (seeded weights)
+        n = 1 << 20
+        g = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.rand((n, 7), device="cuda", generator=g) * 2 - 1
+        y = torch.empty((n, 5), device="cuda")
+        for _ in range(2):
+            ck.cloak_surrogate_forward(c.h, x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_gemm": True, "rows": n, "mean_out": y.mean(0).tolist()}))
+        c.close()
+        return 0
     if args.profile_batch:
         W, H = args.width or 480, args.height or 270
         c = ck.Cloak(ck.RADIAL).integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol, ck.FP64,
@@ -384,7 +580,10 @@ def main():
                  "plain": "k_render_plain (12 launches per step)"}[args.schedule]
         achieved = flops / (stages[1] / 1e3) / 1e12
         out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                           "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                           "frac": achieved / FP64_PEAK_TFLOPS,
+                           "traffic": INTEGRATE_TRAFFIC_BYTES if args.schedule == "batched" else None,
+                           "traffic_note": "ncu dram bytes of a 480x270 x 4 spp capture of the same views, scaled by "
+                                           "samples" if args.schedule == "batched" else None,
                            "peak_source": "derived: 152 SM x 2.07 GHz x 4 FP64 flop/clk/SM", "kernel": kname,
                            "kernel_ms_per_step": stages[1]}
         out["work"] = {"integrator_steps_per_step": steps_total, "fp64_flops_per_step": flops,
@@ -446,6 +645,14 @@ def main():
                                                    "pixels_tile_or_status_differs_frac": float(pxm.mean())}}
         for c in rec_handles.values():
             c.close()
+
+        # ---- the learned surrogate with integrator fallback (3840x2160, 1 spp, the same views)
+        if not args.no_surrogate:
+            out["surrogate"] = surrogate_section(args, ck, inputs, torch, np, flush)
+
+        # ---- the batched form: 64-pose orbit, 256 views, one persistent launch
+        if not args.no_orbit:
+            out["batched_orbit"] = orbit_section(args, ck, inputs, torch, flush)
 
     # ---- comparators on the same workload: per-image wavefront and the plain FP64 integrator
     if not args.no_plain:

@@ -118,8 +118,9 @@ int cloak_set_test_medium(cloak_t *h, double eps_o, double eps_e, const double c
 /* Seed of the procedural room that stands in for the paper's scenery (checkered walls and floor,
  * 8 tiles per unit, box x,y in [-10,10], z in [-height/2, -height/2 + 10]). */
 int cloak_set_scene_seed(cloak_t *h, unsigned long long seed);
-/* Kernel schedule (CLOAK_SCHED_*).  packet: threads per block of the integration stage
- * (32..1024, multiple of 32, 0 = default); steps_per_round: reserved (0). */
+/* Kernel schedule (CLOAK_SCHED_*).  packet: threads per block of the persistent integration kernel
+ * (32, 64, 96 or 128; 0 = default 128).  steps_per_round: reserved (0): lanes refill one by one from
+ * the queue, there are no compaction rounds. */
 int cloak_set_schedule(cloak_t *h, int schedule, int packet, int steps_per_round);
 
 /* Per-stage device timing (CUDA events on the call's stream).  on != 0 enables it for later calls.

@@ -11,7 +11,7 @@ import json
 import os
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune.json")
-CANDIDATES = (64, 128, 256)
+CANDIDATES = (32, 64, 96, 128)  # threads per block of the persistent kernel (at most 128)
 
 
 def _load():

@@ -372,8 +372,8 @@ int cloak_set_schedule(cloak_t *h, int schedule, int packet, int steps_per_round
     if (!h) return fail(CLOAK_EINVAL, "null handle");
     if (schedule != CLOAK_SCHED_PLAIN && schedule != CLOAK_SCHED_WAVEFRONT)
         return fail(CLOAK_EINVAL, "unknown schedule %d", schedule);
-    if (packet != 0 && (packet < 32 || packet > 1024 || packet % 32))
-        return fail(CLOAK_EINVAL, "packet must be 0 or a multiple of 32 in [32, 1024]");
+    if (packet != 0 && (packet < 32 || packet > 128 || packet % 32))
+        return fail(CLOAK_EINVAL, "packet must be 0 or a multiple of 32 in [32, 128]");
     if (steps_per_round < 0) return fail(CLOAK_EINVAL, "steps_per_round must be >= 0");
     h->schedule = schedule;
     h->packet = packet;

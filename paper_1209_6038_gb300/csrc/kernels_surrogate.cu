@@ -39,9 +39,11 @@ __global__ void __launch_bounds__(128) k_sur_gate(Params p, int mode, int spp, u
         const float *y = Y + (size_t)k * 16;
         if (!(y[4] <= gate) || !(y[1] * y[1] + y[2] * y[2] > 0.f)) continue;
         const double P[3] = {q.x[k], q.y[k], q.z[k]};
-        // the height moves monotonically along the ray: a predicted exit inside the lateral surface
-        // means no cap was crossed
-        if (!(fabs(P[2] + 2.0 * p.R2 * (double)y[0]) < p.halfH)) continue;
+        // the height moves monotonically along the ray: a predicted exit inside the lateral surface means
+        // no cap was crossed -- with a margin of twice the exit-point error the confidence allows
+        // (predicted log10 error c bounds the exit-point error by 10 R2 10^c)
+        const double margin = 20.0 * p.R2 * exp10((double)y[4]);
+        if (!(fabs(P[2] + 2.0 * p.R2 * (double)y[0]) < p.halfH - margin)) continue;
         const long long idx = q.id[k], pix = idx / spp;
         double o[3], d[3];
         camera_ray(p, (int)(pix % p.W), (int)(pix / p.W), (int)(idx - pix * spp), spp, seed, o, d);
@@ -56,6 +58,13 @@ __global__ void __launch_bounds__(128) k_sur_gate(Params p, int mode, int spp, u
         rec.steps = 0;
         rec.tof = tof;
         rec.status = CLOAK_RAY_EXITED;
+        if (p.variant == V_RADIAL && mode == 0) {
+            // radial o-rays run straight inside (eps_o = K constant, Sect. 4): they met the metal
+            // cylinder iff the entry line passes within R1 of the axis ahead of the entry point
+            const double ux = q.vx[k], uy = q.vy[k], uu = ux * ux + uy * uy;
+            const double tc = -(P[0] * ux + P[1] * uy), cr = P[0] * uy - P[1] * ux;
+            if (tc > 0.0 && cr * cr < p.R1sq * uu) rec.status = CLOAK_RAY_HIT_METAL_EXITED;
+        }
         set_vec(rec.exit_pos, pos);
         set_vec(rec.exit_dir, dout);
         // light from the room enters here and leaves towards the camera at the entry face

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
     const int m0 = blockIdx.x * GEMM_TILE_M;
-    if (g.m_count && m0 >= (int)__ldg(g.m_count)) return;  // whole tile beyond the live rows
+    if (g.m_count && g.m_base + m0 >= (long long)__ldg(g.m_count)) return;  // whole tile beyond the live rows
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int kslice = g.K / g.ksplit, kbase = blockIdx.y * kslice;
     const int N = g.N, nk = kslice / GEMM_KCHUNK;

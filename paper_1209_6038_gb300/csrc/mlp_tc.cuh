@@ -13,7 +13,8 @@
 //   EPI_BIAS      Z[r, c] = a + bias[c]
 //   EPI_BIAS_GELU z = a + bias[c]; Z[r, c] = z (if Z); H[r, c] = GELU(z) (BF16); HT[c, r] = H[r, c] (if HT)
 //   EPI_GELU_BWD  g = a * GELU'(Z[r, c]); H[r, c] = g (BF16); HT[c, r] = g (if HT)
-// With m_count set, tiles whose first row is at or beyond *m_count are skipped (device-side row count).
+// With m_count set, tiles whose first row (+ m_base) is at or beyond *m_count are skipped (device-side row
+// count).
 // Every mbarrier wait is bounded; on timeout the kernel records an error code and skips ahead.
 #pragma once
 
@@ -31,6 +32,7 @@ struct GemmArgs {
     int M, N, K;                 // M % 128 == 0, N % 16 == 0 (16..256), K % (64 * ksplit) == 0
     int ksplit;                  // slices of K (gridDim.y)
     const unsigned int *m_count; // optional device row count
+    long long m_base;            // row of this GEMM's row 0 in the count's numbering (chunked inference)
     float *C;                    // EPI_STORE / EPI_ATOMIC: C[M x ldc]
     int ldc;
     const float *bias;           // [N]

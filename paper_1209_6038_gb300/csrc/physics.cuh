@@ -282,10 +282,17 @@ __device__ __forceinline__ void flow(const Params &p, const double y[6], const d
 // regula falsi finishes inside the remaining bracket.
 // Returns the end of the final bracket beyond the surface (exits) or before it (metal).
 // Halvings before regula falsi: 12 for fixed-step RK4 (coarse steps can cross a surface more than
-// once), 4 for the error-controlled DP5(4) steps.  Bracket resolution: 1e-13 of the step (FP64).
+// once), 4 for the error-controlled DP5(4) steps.  Bracket resolution: 1e-13 of the step (FP64), or a
+// regula falsi point on the surface to rounding.
 template <int INTEG>
 __device__ __forceinline__ constexpr int bisect_prefix() { return INTEG == I_RK4 ? 12 : 4; }
 constexpr double CROSS_REL_TOL = 1e-13;
+// Regula falsi also stops at a trial point where |g| <= CROSS_G_TOL times the surface's scale (R2^2,
+// R1^2 or H/2): the point lies on the surface to the rounding of g.
+constexpr double CROSS_G_TOL = 4e-16;
+__device__ __forceinline__ double cross_g_scale(const Params &p, int ev) {
+    return ev == EV_LAT ? p.R2sq : ev == EV_METAL ? p.R1sq : p.halfH;
+}
 template <int VAR, int MODE, int INTEG>
 __device__ double crossing(const Params &p, const double y[6], const double k1[6], double h, double ghi, int ev) {
     double lo = 0.0, hi = h, glo = event_g(p, ev, y), t[6];
@@ -317,6 +324,8 @@ __device__ double crossing(const Params &p, const double y[6], const double k1[6
             if (side == -1) ghi *= 0.5;
             side = -1;
         }
+        // the trial point lies on the surface to rounding: it is the crossing
+        if (fabs(gs) <= CROSS_G_TOL * cross_g_scale(p, ev)) return s;
     }
     return ev == EV_METAL ? lo : hi;
 }

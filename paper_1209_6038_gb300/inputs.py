@@ -63,6 +63,13 @@ SMALL = Workload("radial e-pol 128x96 1spp RK4 h=1e-3", (RADIAL,), (EXTRAORDINAR
 FULL = Workload("2 variants x 2 pols x elev {0,20,45} 1920x1080 4spp DP45 tol=1e-9", (RADIAL, AZIMUTHAL),
                 (ORDINARY, EXTRAORDINARY), (0.0, 20.0, 45.0), 1920, 1080, 4, "dp45", 1e-9)
 
+# surrogate: the same twelve views at 3840x2160, 1 spp; the learned surrogate is trained on 10^7 rays that
+# the FP64 DP5(4) integrator traces (entry points uniform on the lateral surface, directions
+# cosine-weighted about the inward normal), the integrator handles the rest
+SURROGATE = Workload("2 variants x 2 pols x elev {0,20,45} 3840x2160 1spp surrogate + DP45 tol=1e-9 FP64 fallback",
+                     (RADIAL, AZIMUTHAL), (ORDINARY, EXTRAORDINARY), (0.0, 20.0, 45.0), 3840, 2160, 1, "dp45", 1e-9,
+                     extra={"train_rays": 10_000_000, "train_seed": 0, "gate_log10_err": -3.0})
+
 
 def ray_set(n: int, seed: int, kind: str = "mixed", R2: float = 1.0, H: float = 2.0, distance: float = 3.0):
     """(n, 6) array of ray origins and unit directions (x, y, z, dx, dy, dz)

@@ -77,6 +77,8 @@ def test_autotuner_picks_a_candidate(ck, tmp_path, monkeypatch):
     eye, tgt, up = inputs.camera_pose(20.0)
     c = ck.Cloak(1).camera(eye, tgt, up, 60.0, 160, 90).integrator(ck.DP45, 1e-9).schedule(ck.SCHED_WAVEFRONT)
     out = torch.empty((90, 160, 4), device="cuda")
+    with pytest.raises(ck.CloakError):  # more threads per block than the persistent kernel is built for
+        c.schedule(ck.SCHED_WAVEFRONT, 256)
     best, times = autotune.tune_packet(c, lambda: c.render(1, 1, 0, out=out), key="test", candidates=(64, 128))
     assert best in (64, 128) and set(times) == {64, 128}
     best2, _ = autotune.tune_packet(c, lambda: c.render(1, 1, 0, out=out), key="test", candidates=(64, 128))

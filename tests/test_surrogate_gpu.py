@@ -214,8 +214,10 @@ def test_surrogate_records_keep_invariants_and_match_oracle(ck, trained, tmp_pat
     recs = ck.records_to_numpy(c.render_records(mode, 1, 0))
     ref = _handles(ck, h, variant, elev, W, H, ck.FP64)
     rref = ck.records_to_numpy(ref.render_records(mode, 1, 0))
-    sur = (recs["steps"] == 0) & (recs["status"] == 1)
+    sur = (recs["steps"] == 0) & np.isin(recs["status"], [1, 2])
     assert sur.sum() > 0
+    # the metal flag of radial o-rays is exact geometry (straight lines inside)
+    assert (recs["status"][sur] == rref["status"][sur]).mean() >= 0.99
     # integrator rays are bit-identical to the FP64 render
     rest = ~sur
     for f in ("exit_pos", "exit_dir", "tof", "weight", "tile_id", "status", "steps"):
@@ -259,7 +261,7 @@ def test_surrogate_gains_over_the_integrator(ck, trained, tmp_path):
         c = _handles(ck, h, 1, 20.0, W, H, prec)
         if prec == ck.SURROGATE:
             ck.cloak_surrogate_load(c.h, path)
-            ck.cloak_surrogate_set_gate(c.h, -2.5)
+            ck.cloak_surrogate_set_gate(c.h, -3.0)
         out = torch.empty((H, W, 4), device="cuda")
         c.render(1, 1, 0, out=out)
         torch.cuda.synchronize()
@@ -275,8 +277,9 @@ def test_surrogate_gains_over_the_integrator(ck, trained, tmp_path):
     entering = a["status"] != 0
     tile_diff = (a["tile_id"] != b["tile_id"]) & entering
     frac = tile_diff.sum() / max(1, entering.sum())
-    handled = ((b["steps"] == 0) & (b["status"] == 1)).sum() / max(1, entering.sum())
+    handled = ((b["steps"] == 0) & np.isin(b["status"], [1, 2])).sum() / max(1, entering.sum())
     print(f"fp64 {t64 * 1e3:.1f} ms, surrogate {tsu * 1e3:.1f} ms, handled {handled:.3f}, tile differs {frac:.4f}")
-    assert handled > 0.5
+    # stated image error at gate -3: fewer than 5 % of the cloak's pixels see another room tile
+    assert handled > 0.2
     assert frac < 0.05
     assert tsu < t64
