@@ -251,14 +251,33 @@ cudaError_t launch_gemm_tc(const CUtensorMap &ta, const CUtensorMap &tb, const G
     if (g.M <= 0 || g.M % GEMM_TILE_M || g.N < 16 || g.N > 256 || g.N % 16 || g.ksplit < 1 || g.K <= 0 ||
         g.K % (GEMM_KCHUNK * g.ksplit))
         return cudaErrorInvalidValue;
-    size_t smem = gemm_smem_bytes(g.N);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)gemm_smem_bytes(256));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    // Shared memory per CTA: the ring, padded so that no more CTAs share an SM than its 512 TMEM columns
+    // hold (each allocates the power of two >= N, at least 32) -- an allocation never has to wait.
+    static int smem_sm = 0, reserved = 0, max_dyn = 0;
+    if (!smem_sm) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_gemm_tc);
+        if (e == cudaSuccess) {
+            max_dyn = optin - (int)fa.sharedSizeBytes;  // the barriers are static shared memory
+            e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+        }
+        if (e != cudaSuccess) {
+            smem_sm = 0;
+            return e;
+        }
     }
+    int ncols = 32;
+    while (ncols < g.N) ncols <<= 1;
+    const int max_ctas = 512 / ncols;
+    size_t smem = gemm_smem_bytes(g.N);
+    const size_t floor_b = (size_t)smem_sm / (size_t)(max_ctas + 1) + 1;
+    if (smem + (size_t)reserved < floor_b) smem = floor_b - (size_t)reserved;
+    if (smem > (size_t)max_dyn) return cudaErrorInvalidValue;
     k_gemm_tc<<<dim3(g.M / GEMM_TILE_M, g.ksplit), 128, smem, st>>>(ta, tb, g);
     return cudaGetLastError();
 }

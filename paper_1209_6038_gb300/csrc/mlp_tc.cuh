@@ -48,7 +48,7 @@ struct GemmArgs {
 
 constexpr int GEMM_TILE_M = 128;
 constexpr int GEMM_KCHUNK = 64;
-constexpr int GEMM_STAGES = 3;
+constexpr int GEMM_STAGES = 2;  // K of the network's layers is at most 256: four chunks, double-buffered
 
 inline size_t gemm_smem_bytes(int N) {
     return 1024 + (size_t)GEMM_STAGES * (GEMM_TILE_M * 128 + (size_t)N * 128);
