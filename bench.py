@@ -68,10 +68,8 @@ def flops_per_step(variant, mode, integ):
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1209_6038_gb300.replicas import dist_env as env
+    return env()
 
 
 class ClockSampler:
@@ -399,7 +397,7 @@ def main():
     if ws > 1:
         dist.barrier()
     from paper_1209_6038_gb300 import cloak as ck
-    from paper_1209_6038_gb300 import inputs
+    from paper_1209_6038_gb300 import inputs, replicas
     ck.load()
     w = inputs.FULL
     stream = torch.cuda.current_stream()
@@ -509,11 +507,14 @@ def main():
         def close(self):
             self.h.close()
 
-    def timed(runner, warmup, steps, sampler=None):
+    def timed(runner, warmup, steps, sampler=None, collective=True):
+        """mean ms per step (the slowest rank's when collective), per-step ms, mean stage ms; sections that
+        run on rank 0 alone pass collective=False"""
+        coll = collective and ws > 1
         for _ in range(warmup):
             runner.step()
         torch.cuda.synchronize()
-        if ws > 1:
+        if coll:
             dist.barrier()
         torch.cuda.synchronize()
         stage_ms = [0.0, 0.0, 0.0, 0.0]
@@ -530,12 +531,10 @@ def main():
                 b.synchronize()
                 ms.append(a.elapsed_time(b))
         torch.cuda.synchronize()
-        if ws > 1:
+        if coll:
             dist.barrier()
-        tot = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-        return float(tot.item()) / steps, ms, [x / steps for x in stage_ms]
+        tot = replicas.max_over_ranks(sum(ms), device="cuda") if coll else sum(ms)  # the slowest rank's time
+        return tot / steps, ms, [x / steps for x in stage_ms]
 
     if args.schedule == "batched":
         main_runner = Batched()
@@ -544,7 +543,7 @@ def main():
     sampler = ClockSampler(local)
     ms_step, ms_list, stages = timed(main_runner, args.warmup, args.steps, sampler)
     rays_step = w.rays
-    value = ws * rays_step / (ms_step / 1e3)
+    value = replicas.whole_job_rate(rays_step, ms_step / 1e3, ws)
     clocks = sampler.summary()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -616,7 +615,7 @@ def main():
         # ---- the precision form: the same workload with FP32 stepping (mixed), against the oracle sample
         if not args.no_mixed:
             mixed_runner = Batched(ck.MIXED) if args.schedule == "batched" else PerImage(ck.SCHED_WAVEFRONT, ck.MIXED)
-            mms, _, mstages = timed(mixed_runner, 1, 2)
+            mms, _, mstages = timed(mixed_runner, 1, 2, collective=False)
             mixed_runner.close()
             mh = make_handles(ck.SCHED_WAVEFRONT, precision=ck.MIXED)
             rec_buf = torch.empty(w.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
@@ -683,7 +682,8 @@ def main():
                 hb.copy_(im, non_blocking=True)
             torch.cuda.synchronize()
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        e2e = ws * rays_step / (statistics.mean(e2e_ms) / 1e3)
+        e2e_s = replicas.max_over_ranks(statistics.mean(e2e_ms) / 1e3, device="cuda")  # the slowest rank's
+        e2e = replicas.whole_job_rate(rays_step, e2e_s, ws)
         out["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0,
                       "d2h_bytes_per_step": sum(im.numel() * 4 for im in imgs),
                       "note": "inputs are camera and integrator parameters (host structs passed through the C ABI); "
