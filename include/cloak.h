@@ -195,6 +195,20 @@ int cloak_mlp_gemm(const void *dev_a, const void *dev_b, float *dev_c, int M, in
 int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsigned long long seed, void *dev_rgba,
                          size_t bytes, void *cuda_stream);
 
+/* Panels of the paper's figures (Figs. 1, 2), with the handle's camera and room, written on cuda_stream
+ * into dev_rgba (float4[width*height], bytes >= 16*width*height; RGB = mean over samples of weight x room
+ * colour, A = mean weight):
+ *   CLOAK_PANEL_ROOM         (a) the room without the cylinder
+ *   CLOAK_PANEL_METAL        (b) the bare metal cylinder of radius R1 and height H (a mirror, reflectance 1)
+ *   CLOAK_PANEL_UNPOLARIZED  (c) the cloak in unpolarised light: per sample the sum of the ordinary and the
+ *                            extraordinary contribution (each weighted by its Eq. 12 factors), a ray that
+ *                            never enters the shell counted once.  Both polarisations run in one batched
+ *                            render (radial or azimuthal handle; the handle's integrator and precision).
+ * The polarisation-analyser panels (d), (e) are not provided. */
+enum { CLOAK_PANEL_ROOM = 0, CLOAK_PANEL_METAL = 1, CLOAK_PANEL_UNPOLARIZED = 2 };
+int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long long seed, void *dev_rgba, size_t bytes,
+                       void *cuda_stream);
+
 /* ---- learned surrogate of the exit state (the paper has none) -------------------------------------
  * A multilayer perceptron 7 -> 256 -> 256 -> 256 -> 256 -> 5 (GELU, tanh form; BF16 weights, FP32
  * accumulation on the tensor cores) maps a ray entering the lateral surface r = R2 -- entry height and

@@ -49,6 +49,8 @@ SIGNATURES = {
     "cloak_render_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p]),
     "cloak_render_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
+    "cloak_render_panel": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
+                                     C.c_void_p]),
     "cloak_surrogate_train": (C.c_int, [C.c_void_p, C.c_long, C.c_ulonglong, C.c_int, C.c_void_p]),
     "cloak_surrogate_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "cloak_surrogate_load": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -202,6 +204,15 @@ def cloak_render_noalloc(h, polarization, spp, seed, rgba, stream=None):
                                               rgba.numel() * rgba.element_size(), _stream_ptr(stream)))
 
 
+# ------------------------------------------------------------------ panels of the paper's figures
+PANEL_ROOM, PANEL_METAL, PANEL_UNPOLARIZED = 0, 1, 2
+
+
+def cloak_render_panel(h, panel, spp, seed, rgba, stream=None):
+    return _check(load().cloak_render_panel(h, panel, spp, seed, C.c_void_p(rgba.data_ptr()),
+                                            rgba.numel() * rgba.element_size(), _stream_ptr(stream)))
+
+
 # ------------------------------------------------------------------ learned surrogate
 SUR_NPARAMS = 200709
 SUR_INFO_KEYS = ("loss_stage1", "loss_stage2", "lateral_fraction", "rays", "seconds", "seconds_tracing",
@@ -314,6 +325,14 @@ class Cloak:
         if out is None:
             out = torch.empty((self.height, self.width, 4), dtype=torch.float32, device="cuda")
         cloak_render(self.h, polarization, spp, seed, out, stream)
+        return out
+
+    def panel(self, panel, spp=1, seed=0, out=None, stream=None):
+        """One panel of the paper's figures (PANEL_ROOM, PANEL_METAL, PANEL_UNPOLARIZED)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.height, self.width, 4), dtype=torch.float32, device="cuda")
+        cloak_render_panel(self.h, panel, spp, seed, out, stream)
         return out
 
     def render_records(self, polarization, spp=1, seed=0, out=None, stream=None):

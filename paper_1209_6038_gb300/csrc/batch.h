@@ -25,4 +25,11 @@ cudaError_t launch_batch(const Params &p, const ViewDev *views, int nviews, int 
                          long long total, long long total_pix, const Queue &q, float4 *samples, int packet,
                          cudaStream_t st, cudaEvent_t *ev);
 
+// unpolarised image of views 0 (ordinary) and 1 (extraordinary) of the last batch: samples as carved
+// for that batch, views: its device table
+cudaError_t launch_unpol_resolve(const Params &p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
+                                 const float4 *samples, float4 *out, cudaStream_t st);
+// reference panels without the cloak: 0 the room alone, 1 the bare metal cylinder (radius R1, height H)
+cudaError_t launch_panel(const Params &p, int panel, int spp, unsigned long long seed, float4 *out, cudaStream_t st);
+
 }  // namespace ck

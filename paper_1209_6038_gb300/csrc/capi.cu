@@ -45,6 +45,9 @@ struct cloak {
     unsigned long long graph_key;
     // learned surrogate of the exit state (created by training, loading or setting parameters)
     ck::SurNet *sur;
+    // the two polarisation images behind the unpolarised panel
+    void *panel_img;
+    size_t panel_bytes;
 };
 
 static thread_local std::string g_err;
@@ -251,6 +254,8 @@ cloak_t *cloak_create(int variant, double R1, double R2, double height) {
     h->graph_done = nullptr;
     h->graph_key = 0;
     h->sur = nullptr;
+    h->panel_img = nullptr;
+    h->panel_bytes = 0;
     g_err.clear();
     return h;
 }
@@ -266,6 +271,7 @@ void cloak_destroy(cloak_t *h) {
     if (h->batch_dev) cudaFree(h->batch_dev);
     if (h->scratch) cudaFree(h->scratch);
     ck::sur_destroy(h->sur);
+    if (h->panel_img) cudaFree(h->panel_img);
     if (h->timing)
         for (int i = 0; i < 5; ++i) cudaEventDestroy(h->ev[i]);
     delete h;
@@ -500,8 +506,18 @@ static unsigned long long fnv1a(unsigned long long hsh, const void *data, size_t
     return hsh;
 }
 
+// The batched render (views validated, device table, graph capture or replay); samples_out (nullable)
+// receives the per-sample buffer of the batch.
+static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
+                      void *cuda_stream, float4 **samples_out);
+
 extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
                                   void *cuda_stream) {
+    return batch_core(h, views, nviews, spp, seed, cuda_stream, nullptr);
+}
+
+static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
+                      void *cuda_stream, float4 **samples_out) {
     if (!h) return fail(CLOAK_EINVAL, "null handle");
     if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
         return fail(CLOAK_ESTATE, "batched rendering needs a radial or azimuthal cloak handle");
@@ -591,7 +607,61 @@ extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nview
         h->timed_calls++;
         h->timed_sched = CLOAK_SCHED_WAVEFRONT;
     }
+    if (samples_out) *samples_out = samples;
     return CLOAK_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Panels of the paper's figures
+// ---------------------------------------------------------------------------------------------
+extern "C" int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long long seed, void *dev_rgba,
+                                  size_t bytes, void *cuda_stream) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (panel != CLOAK_PANEL_ROOM && panel != CLOAK_PANEL_METAL && panel != CLOAK_PANEL_UNPOLARIZED)
+        return fail(CLOAK_EINVAL, "unknown panel %d", panel);
+    if (spp < 1 || spp > 65536) return fail(CLOAK_EINVAL, "spp must be in [1, 65536]");
+    const size_t npix = (size_t)h->W * h->Hp;
+    if (!dev_rgba) return fail(CLOAK_EINVAL, "null output buffer");
+    if (bytes < npix * 16) return fail(CLOAK_EINVAL, "output buffer holds %zu bytes, needs %zu", bytes, npix * 16);
+    ck::Params p;
+    int rc = make_params(h, p);
+    if (rc) return rc;
+    if ((rc = use_device(h))) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (panel != CLOAK_PANEL_UNPOLARIZED) {
+        cudaError_t e = ck::launch_panel(p, panel, spp, seed, (float4 *)dev_rgba, st);
+        return e == cudaSuccess ? CLOAK_OK : cuda_fail(e, "panel launch");
+    }
+    if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
+        return fail(CLOAK_ESTATE, "the unpolarised panel needs a radial or azimuthal cloak handle");
+    // both polarisations in one batched render (their images go to handle scratch), then the sum
+    if (h->panel_bytes < 2 * npix * 16) {
+        if (h->panel_img) cudaFree(h->panel_img);
+        h->panel_img = nullptr;
+        h->panel_bytes = 0;
+        cudaError_t e = cudaMalloc(&h->panel_img, 2 * npix * 16);
+        if (e != cudaSuccess) {
+            h->panel_img = nullptr;
+            cudaGetLastError();
+            return fail(CLOAK_ENOMEM, "panel scratch: %s", cudaGetErrorString(e));
+        }
+        h->panel_bytes = 2 * npix * 16;
+    }
+    cloak_view v[2];
+    for (int m = 0; m < 2; ++m) {
+        v[m].variant = h->variant;
+        v[m].polarization = m;
+        for (int k = 0; k < 3; ++k) { v[m].eye[k] = h->eye[k]; v[m].target[k] = h->target[k]; v[m].up[k] = h->up[k]; }
+        v[m].hfov_deg = h->hfov;
+        v[m].width = h->W;
+        v[m].height = h->Hp;
+        v[m].dev_rgba = (char *)h->panel_img + m * npix * 16;
+    }
+    float4 *samples = nullptr;
+    if ((rc = batch_core(h, v, 2, spp, seed, cuda_stream, &samples))) return rc;
+    cudaError_t e = ck::launch_unpol_resolve(p, (const ck::ViewDev *)h->batch_dev, spp, seed, (long long)npix, samples,
+                                             (float4 *)dev_rgba, st);
+    return e == cudaSuccess ? CLOAK_OK : cuda_fail(e, "unpolarised resolve");
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -104,6 +104,39 @@ __global__ void k_batch_resolve(const ViewDev *views, int nviews, int spp, long 
     vw.out[pix] = make_float4(a0 * inv, a1 * inv, a2 * inv, a3 * inv);
 }
 
+// Unpolarised light (the paper's Fig. 1(c) / 2(c)): per pixel, the mean over its samples of the ordinary
+// plus the extraordinary sample of views 0 and 1 (the same camera); a ray that never enters the shell
+// (it misses the cylinder or mirrors off a metal end disc) is the same for both modes and counts once.
+__global__ void k_unpol_resolve(Params p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
+                                const float4 *samples, float4 *out) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npix) return;
+    const ViewDev &v0 = views[0];
+    const int i = (int)(g % v0.W), j = (int)(g / v0.W);
+    const float4 *so = samples + views[0].ray_begin + g * spp, *se = samples + views[1].ray_begin + g * spp;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int s = 0; s < spp; ++s) {
+        double o[3], d[3], pt[3], n[3];
+        view_camera_ray(v0, i, j, s, spp, seed, o, d);
+        const int face = cylinder_entry(p, o, d, pt, n);
+        const bool enters = face >= 0 && !(face != EV_LAT && p.R1 > 0.0 && hypot(pt[0], pt[1]) <= p.R1);
+        float4 v = so[s];
+        if (enters) {
+            const float4 e = se[s];
+            v.x += e.x; v.y += e.y; v.z += e.z; v.w += e.w;
+        }
+        a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
+    }
+    const float inv = 1.0f / spp;
+    out[g] = make_float4(a0 * inv, a1 * inv, a2 * inv, a3 * inv);
+}
+
+cudaError_t launch_unpol_resolve(const Params &p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
+                                 const float4 *samples, float4 *out, cudaStream_t st) {
+    k_unpol_resolve<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(p, views, spp, seed, npix, samples, out);
+    return cudaGetLastError();
+}
+
 static inline void mark(cudaEvent_t *ev, int i, cudaStream_t st) {
     if (ev) cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
 }
