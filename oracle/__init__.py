@@ -30,7 +30,7 @@ assert RECORD_DTYPE.itemsize == 80
 class _Cloak(C.Structure):
     _fields_ = [("variant", C.c_int), ("R1", C.c_double), ("R2", C.c_double), ("H", C.c_double),
                 ("eps_o_test", C.c_double), ("eps_e_test", C.c_double), ("c_test", C.c_double * 3),
-                ("scene_seed", C.c_uint64)]
+                ("scene_seed", C.c_uint64), ("analyzer", C.c_double * 3)]
 
 
 class _Integ(C.Structure):
@@ -117,8 +117,10 @@ class Cloak:
     homogeneous uniaxial test medium (Eq. 1 with a fixed optic axis)."""
 
     def __init__(self, variant=RADIAL, R1=0.5, R2=1.0, H=2.0, eps_o=1.0, eps_e=1.0, c_hat=(0, 0, 1),
-                 scene_seed=0):
-        self.s = _Cloak(variant, R1, R2, H, eps_o, eps_e, (C.c_double * 3)(*c_hat), scene_seed)
+                 scene_seed=0, analyzer=(0.0, 0.0, 0.0)):
+        """analyzer: axis of a linear polariser in front of the camera (zero: none)."""
+        self.s = _Cloak(variant, R1, R2, H, eps_o, eps_e, (C.c_double * 3)(*c_hat), scene_seed,
+                        (C.c_double * 3)(*analyzer))
 
     @property
     def ref(self):
@@ -239,6 +241,14 @@ def transmission_out(cloak: Cloak, mode, x, n, k):
     out = np.zeros(4)
     ok = lib().orc_transmission_out(cloak.ref, mode, _dp(x), _dp(n), _dp(k), _dp(out))
     return bool(ok), out[0], out[1], out[2]
+
+
+def analyzer_fraction(cloak: Cloak, mode, x, n, k):
+    """Fraction of the flux transmitted into vacuum that passes the cloak's analyser (cloak.s.analyzer)."""
+    x, n, k = _vec(x), _vec(n), _vec(k)
+    out = np.zeros(4)
+    ok = lib().orc_transmission_out(cloak.ref, mode, _dp(x), _dp(n), _dp(k), _dp(out))
+    return out[3] if ok else None
 
 
 def rk4_step(cloak: Cloak, mode, y, h):

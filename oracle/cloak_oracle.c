@@ -523,6 +523,21 @@ int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const 
     out[0] = fabs(normal_flux(n, Et, Ht)) / fi;
     out[1] = cabs(u[2]) * cabs(u[2]) * fabs(normal_flux(n, Ero, Hro)) / fi;
     out[2] = cabs(u[3]) * cabs(u[3]) * fabs(normal_flux(n, Ere, Hre)) / fi;
+    /* linear polariser in front of the camera: it passes the field component along its axis, taken
+       across the transmitted vacuum wave (Malus's law, |E . a|^2 / |E|^2) */
+    out[3] = 1.0;
+    double an = dot3(c->analyzer, c->analyzer);
+    if (an > 0.0) {
+        double a[3], ak = dot3(c->analyzer, kv);
+        for (int i = 0; i < 3; ++i) a[i] = c->analyzer[i] - ak * kv[i];
+        double al = sqrt(dot3(a, a));
+        cplx ea = 0.0, ee2 = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            ea += Et[i] * (a[i] / al);
+            ee2 += Et[i] * conj(Et[i]);
+        }
+        out[3] = al > 0.0 && creal(ee2) > 0.0 ? creal(ea * conj(ea)) / creal(ee2) : 0.0;
+    }
     return 1;
 }
 
@@ -734,9 +749,11 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
     if (path_len) *path_len = 0;
     double p[3], n[3];
     int face;
+    /* unpolarised room light through a linear polariser: half of it */
+    const double vac = dot3(c->analyzer, c->analyzer) > 0.0 ? 0.5 : 1.0;
     if (!hit_cylinder(c, o, d, p, n, &face)) {
         rec->status = ORC_MISSED;
-        rec->weight = 1.0;
+        rec->weight = vac;
         finish_vacuum(c, o, d, rec);
         return rec->status;
     }
@@ -745,7 +762,7 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
         double dr[3], dn = dot3(d, n);
         for (int i = 0; i < 3; ++i) dr[i] = d[i] - 2.0 * dn * n[i];
         rec->status = ORC_METAL_CAP;
-        rec->weight = 1.0;
+        rec->weight = vac;
         finish_vacuum(c, p, dr, rec);
         return rec->status;
     }
@@ -874,7 +891,7 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
         for (int i = 0; i < 3; ++i) { mdout[i] = -dout[i]; mk0[i] = -k0[i]; }
         double w = 0.0;
         if (orc_transmission_in(c, xo, no, mdout, Tin) && orc_transmission_out(c, mode, x_in, n_in, mk0, Tout))
-            w = (mode == ORC_ORDINARY ? Tin[6] : Tin[7]) * Tout[0];
+            w = (mode == ORC_ORDINARY ? Tin[6] : Tin[7]) * Tout[0] * Tout[3];
         rec->weight = w;
         rec->status = metal ? ORC_HIT_METAL_EXITED : ORC_EXITED;
         finish_vacuum(c, xo, dout, rec);

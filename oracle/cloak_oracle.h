@@ -47,6 +47,8 @@ typedef struct {
     double R1, R2, H;          /* inner radius a, outer radius b, height */
     double eps_o_test, eps_e_test, c_test[3];
     uint64_t scene_seed;       /* seed of the procedural room */
+    double analyzer[3];        /* axis of a linear polariser in front of the camera (the paper's
+                                  "polarization goggles"); all zero: none */
 } orc_cloak;
 
 typedef struct {
@@ -93,6 +95,8 @@ void orc_mode_fields(const orc_cloak *c, int mode, const double x[3], const doub
                      double D[3], double E[3], double H[3]);
 int orc_transmission_in(const orc_cloak *c, const double x[3], const double nhat[3],
                         const double d[3], double out[8]);
+/* out[0] transmitted flux fraction, out[1], out[2] reflected into o / e, out[3] fraction of the
+   transmitted flux that passes the analyser c->analyzer (1 without one) */
 int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const double nhat[3],
                          const double k[3], double out[4]);
 
