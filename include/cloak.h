@@ -118,6 +118,14 @@ int cloak_set_test_medium(cloak_t *h, double eps_o, double eps_e, const double c
 /* Seed of the procedural room that stands in for the paper's scenery (checkered walls and floor,
  * 8 tiles per unit, box x,y in [-10,10], z in [-height/2, -height/2 + 10]). */
 int cloak_set_scene_seed(cloak_t *h, unsigned long long seed);
+/* Linear polariser in front of the camera (the paper's "polarization goggles"): CLOAK_ANALYZER_NONE,
+ * CLOAK_ANALYZER_RIGHT (axis along the camera's right vector) or CLOAK_ANALYZER_UP (its up vector).  With
+ * one, a ray's weight is multiplied by the fraction of the vacuum wave leaving the cloak towards the
+ * camera that passes it (Malus's law, the axis taken across the wave); a ray that never enters the cloak
+ * keeps half of the unpolarised room light.  Applies to cloak_render, cloak_render_records,
+ * cloak_render_batch and cloak_render_noalloc; cloak_trace_rays has no camera and ignores it. */
+enum { CLOAK_ANALYZER_NONE = 0, CLOAK_ANALYZER_RIGHT = 1, CLOAK_ANALYZER_UP = 2 };
+int cloak_set_analyzer(cloak_t *h, int analyzer);
 /* Kernel schedule (CLOAK_SCHED_*).  packet: threads per block of the persistent integration kernel
  * (32, 64, 96 or 128; 0 = default 128).  steps_per_round: reserved (0): lanes refill one by one from
  * the queue, there are no compaction rounds. */
@@ -204,8 +212,14 @@ int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsigned long lo
  *                            extraordinary contribution (each weighted by its Eq. 12 factors), a ray that
  *                            never enters the shell counted once.  Both polarisations run in one batched
  *                            render (radial or azimuthal handle; the handle's integrator and precision).
- * The polarisation-analyser panels (d), (e) are not provided. */
-enum { CLOAK_PANEL_ROOM = 0, CLOAK_PANEL_METAL = 1, CLOAK_PANEL_UNPOLARIZED = 2 };
+ * The paper's images show the cylinder axis horizontal, here it is vertical (+z): its "vertical" goggles
+ * (d), across the cylinder axis, are CLOAK_PANEL_POLARIZER_RIGHT at elevation 0; its "horizontal" ones (e)
+ * are CLOAK_PANEL_POLARIZER_UP. */
+enum {
+    CLOAK_PANEL_ROOM = 0, CLOAK_PANEL_METAL = 1, CLOAK_PANEL_UNPOLARIZED = 2,
+    CLOAK_PANEL_POLARIZER_RIGHT = 3, /* (d): as (c) seen through a linear polariser along the camera's right vector */
+    CLOAK_PANEL_POLARIZER_UP = 4     /* (e): ... along the camera's up vector */
+};
 int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long long seed, void *dev_rgba, size_t bytes,
                        void *cuda_stream);
 

@@ -49,6 +49,7 @@ SIGNATURES = {
     "cloak_render_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p]),
     "cloak_render_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
+    "cloak_set_analyzer": (C.c_int, [C.c_void_p, C.c_int]),
     "cloak_render_panel": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                      C.c_void_p]),
     "cloak_surrogate_train": (C.c_int, [C.c_void_p, C.c_long, C.c_ulonglong, C.c_int, C.c_void_p]),
@@ -205,7 +206,12 @@ def cloak_render_noalloc(h, polarization, spp, seed, rgba, stream=None):
 
 
 # ------------------------------------------------------------------ panels of the paper's figures
-PANEL_ROOM, PANEL_METAL, PANEL_UNPOLARIZED = 0, 1, 2
+PANEL_ROOM, PANEL_METAL, PANEL_UNPOLARIZED, PANEL_POLARIZER_RIGHT, PANEL_POLARIZER_UP = 0, 1, 2, 3, 4
+ANALYZER_NONE, ANALYZER_RIGHT, ANALYZER_UP = 0, 1, 2
+
+
+def cloak_set_analyzer(h, analyzer):
+    return _check(load().cloak_set_analyzer(h, analyzer))
 
 
 def cloak_render_panel(h, panel, spp, seed, rgba, stream=None):
@@ -326,6 +332,11 @@ class Cloak:
             out = torch.empty((self.height, self.width, 4), dtype=torch.float32, device="cuda")
         cloak_render(self.h, polarization, spp, seed, out, stream)
         return out
+
+    def analyzer(self, analyzer=ANALYZER_NONE):
+        """Linear polariser in front of the camera (ANALYZER_NONE / _RIGHT / _UP)."""
+        cloak_set_analyzer(self.h, analyzer)
+        return self
 
     def panel(self, panel, spp=1, seed=0, out=None, stream=None):
         """One panel of the paper's figures (PANEL_ROOM, PANEL_METAL, PANEL_UNPOLARIZED)."""

@@ -27,6 +27,7 @@ struct cloak {
     int precision;
     long max_steps;
     int schedule, packet, steps_per_round;
+    int analyzer;  // CLOAK_ANALYZER_*
     int device;
     // library-owned scratch of the wavefront schedule (queue + per-sample buffer), grown on demand
     void *scratch;
@@ -114,6 +115,7 @@ static int make_params(const cloak *h, ck::Params &p) {
     p.ty = p.tx * (double)h->Hp / (double)h->W;
     p.W = h->W;
     p.Hp = h->Hp;
+    p.analyzer = h->analyzer;
     return CLOAK_OK;
 }
 
@@ -241,6 +243,7 @@ cloak_t *cloak_create(int variant, double R1, double R2, double height) {
     h->schedule = CLOAK_SCHED_PLAIN;
     h->packet = 0;
     h->steps_per_round = 0;
+    h->analyzer = CLOAK_ANALYZER_NONE;
     h->device = dev;
     h->scratch = nullptr;
     h->scratch_bytes = 0;
@@ -368,6 +371,14 @@ int cloak_set_test_medium(cloak_t *h, double eps_o, double eps_e, const double c
     return CLOAK_OK;
 }
 
+int cloak_set_analyzer(cloak_t *h, int analyzer) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (analyzer != CLOAK_ANALYZER_NONE && analyzer != CLOAK_ANALYZER_RIGHT && analyzer != CLOAK_ANALYZER_UP)
+        return fail(CLOAK_EINVAL, "unknown analyzer %d", analyzer);
+    h->analyzer = analyzer;
+    return CLOAK_OK;
+}
+
 int cloak_set_scene_seed(cloak_t *h, unsigned long long seed) {
     if (!h) return fail(CLOAK_EINVAL, "null handle");
     h->scene_seed = seed;
@@ -454,6 +465,7 @@ int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long 
     ck::Params p;
     int rc = make_params(h, p);
     if (rc) return rc;
+    p.analyzer = 0;  // rays without a camera: no camera polariser
     if ((rc = use_device(h))) return rc;
     cudaError_t e = ck::launch_trace_rays(p, polarization, dev_rays, n, (cloak_record *)dev_records,
                                           (cudaStream_t)cuda_stream);
@@ -509,15 +521,15 @@ static unsigned long long fnv1a(unsigned long long hsh, const void *data, size_t
 // The batched render (views validated, device table, graph capture or replay); samples_out (nullable)
 // receives the per-sample buffer of the batch.
 static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
-                      void *cuda_stream, float4 **samples_out);
+                      void *cuda_stream, float4 **samples_out, int analyzer);
 
 extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
                                   void *cuda_stream) {
-    return batch_core(h, views, nviews, spp, seed, cuda_stream, nullptr);
+    return batch_core(h, views, nviews, spp, seed, cuda_stream, nullptr, h ? h->analyzer : 0);
 }
 
 static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
-                      void *cuda_stream, float4 **samples_out) {
+                      void *cuda_stream, float4 **samples_out, int analyzer) {
     if (!h) return fail(CLOAK_EINVAL, "null handle");
     if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
         return fail(CLOAK_ESTATE, "batched rendering needs a radial or azimuthal cloak handle");
@@ -528,6 +540,7 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
     ck::Params p;
     int rc = make_params(h, p);
     if (rc) return rc;
+    p.analyzer = analyzer;
     std::vector<ck::ViewDev> table((size_t)nviews);
     long long total = 0, total_pix = 0;
     for (int i = 0; i < nviews; ++i) {
@@ -617,7 +630,8 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
 extern "C" int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long long seed, void *dev_rgba,
                                   size_t bytes, void *cuda_stream) {
     if (!h) return fail(CLOAK_EINVAL, "null handle");
-    if (panel != CLOAK_PANEL_ROOM && panel != CLOAK_PANEL_METAL && panel != CLOAK_PANEL_UNPOLARIZED)
+    if (panel != CLOAK_PANEL_ROOM && panel != CLOAK_PANEL_METAL && panel != CLOAK_PANEL_UNPOLARIZED &&
+        panel != CLOAK_PANEL_POLARIZER_RIGHT && panel != CLOAK_PANEL_POLARIZER_UP)
         return fail(CLOAK_EINVAL, "unknown panel %d", panel);
     if (spp < 1 || spp > 65536) return fail(CLOAK_EINVAL, "spp must be in [1, 65536]");
     const size_t npix = (size_t)h->W * h->Hp;
@@ -628,10 +642,14 @@ extern "C" int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long 
     if (rc) return rc;
     if ((rc = use_device(h))) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    if (panel != CLOAK_PANEL_UNPOLARIZED) {
+    if (panel == CLOAK_PANEL_ROOM || panel == CLOAK_PANEL_METAL) {
         cudaError_t e = ck::launch_panel(p, panel, spp, seed, (float4 *)dev_rgba, st);
         return e == cudaSuccess ? CLOAK_OK : cuda_fail(e, "panel launch");
     }
+    const int analyzer = panel == CLOAK_PANEL_POLARIZER_RIGHT ? CLOAK_ANALYZER_RIGHT
+                         : panel == CLOAK_PANEL_POLARIZER_UP  ? CLOAK_ANALYZER_UP
+                                                              : CLOAK_ANALYZER_NONE;
+    p.analyzer = analyzer;
     if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
         return fail(CLOAK_ESTATE, "the unpolarised panel needs a radial or azimuthal cloak handle");
     // both polarisations in one batched render (their images go to handle scratch), then the sum
@@ -658,7 +676,7 @@ extern "C" int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long 
         v[m].dev_rgba = (char *)h->panel_img + m * npix * 16;
     }
     float4 *samples = nullptr;
-    if ((rc = batch_core(h, v, 2, spp, seed, cuda_stream, &samples))) return rc;
+    if ((rc = batch_core(h, v, 2, spp, seed, cuda_stream, &samples, analyzer))) return rc;
     cudaError_t e = ck::launch_unpol_resolve(p, (const ck::ViewDev *)h->batch_dev, spp, seed, (long long)npix, samples,
                                              (float4 *)dev_rgba, st);
     return e == cudaSuccess ? CLOAK_OK : cuda_fail(e, "unpolarised resolve");

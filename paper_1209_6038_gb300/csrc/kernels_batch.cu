@@ -61,7 +61,9 @@ __global__ void __launch_bounds__(128) k_batch_entry(Params p, const ViewDev *vi
         return;
     }
     double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
-    double w_out = transmission_out(mode, mat[0], mat[1], c, n_in, mk0);
+    // the camera's polariser along this view's own right or up vector
+    const double *axis = p.analyzer == 1 ? vw.rt : p.analyzer == 2 ? vw.up : nullptr;
+    double w_out = transmission_out(mode, mat[0], mat[1], c, n_in, mk0, axis);
     // queue key: medium/mode (major: one segment of the sorted queue per medium) and cost bucket (minor,
     // slowest first within a segment after the descending sort)
     queue_append(q, y, w_out, (int)g, batch_key(vw.vm, cost_bucket(y, k0)));

@@ -42,6 +42,8 @@ struct Params {
     // camera
     double eye[3], fw[3], rt[3], up[3], tx, ty;
     int W, Hp;
+    // linear polariser in front of the camera: 0 none, 1 along the camera's right vector, 2 along its up vector
+    int analyzer;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -607,8 +609,10 @@ static __device__ __noinline__ double transmission_in(int mode, double eo, doubl
 
 // Eq. 12, medium -> vacuum (Sect. 3, last paragraph): fraction of the incident mode's normal
 // energy flux carried by the refracted vacuum wave.  0 for total internal reflection.
+// axis: a linear polariser the transmitted vacuum wave then meets (nullable): the result is multiplied by
+// the fraction of that wave's flux along the axis taken across the wave (Malus's law)
 static __device__ __noinline__ double transmission_out(int mode, double eo, double ee, const double c[3],
-                                                const double n[3], const double k[3]) {
+                                                const double n[3], const double k[3], const double *axis = nullptr) {
     double kn = dot3(k, n), kt[3];
     for (int i = 0; i < 3; ++i) kt[i] = k[i] - kn * n[i];
     double kt2 = dot3(kt, kt);
@@ -648,7 +652,25 @@ static __device__ __noinline__ double transmission_out(int mode, double eo, doub
     if (!csolve4<1>(A, B)) return 0.0;
     cx Et[3], Ht[3];
     for (int i = 0; i < 3; ++i) { Et[i] = B[0][0] * Es[i] + B[1][0] * Ep[i]; Ht[i] = B[0][0] * Hs[i] + B[1][0] * Hp[i]; }
-    return fabs(flux_n(n, Et, Ht)) / fm;
+    const double T = fabs(flux_n(n, Et, Ht)) / fm;
+    if (!axis) return T;
+    // the polariser's axis across the transmitted wave kv
+    const double ak = dot3(axis, kv);
+    double a[3];
+    for (int i = 0; i < 3; ++i) a[i] = axis[i] - ak * kv[i];
+    const double al2 = dot3(a, a);
+    double er = 0.0, ei = 0.0, e2 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        er += Et[i].re * a[i];
+        ei += Et[i].im * a[i];
+        e2 += Et[i].re * Et[i].re + Et[i].im * Et[i].im;
+    }
+    return al2 > 0.0 && e2 > 0.0 ? T * (er * er + ei * ei) / (al2 * e2) : 0.0;
+}
+
+// axis of the camera's polariser, or null
+__device__ __forceinline__ const double *analyzer_axis(const Params &p) {
+    return p.analyzer == 1 ? p.rt : p.analyzer == 2 ? p.up : nullptr;
 }
 
 // ------------------------------------------------------------------ room and camera

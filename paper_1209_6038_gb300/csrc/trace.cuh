@@ -26,9 +26,11 @@ __device__ __forceinline__ bool enter(const Params &p, const double o[3], const 
     rgb[0] = rgb[1] = rgb[2] = 0.f;
     double pt[3];
     int face = cylinder_entry(p, o, d, pt, n_in);
+    // unpolarised room light through the camera's polariser: half of it
+    const double vac = p.analyzer ? 0.5 : 1.0;
     if (face < 0) {
         rec.status = CLOAK_RAY_MISSED;
-        rec.weight = 1.0;
+        rec.weight = vac;
         set_vec(rec.exit_pos, o);
         set_vec(rec.exit_dir, d);
         rec.tile_id = room_hit(p, o, d, rgb);
@@ -38,7 +40,7 @@ __device__ __forceinline__ bool enter(const Params &p, const double o[3], const 
         double dr[3], dn = dot3(d, n_in);
         for (int i = 0; i < 3; ++i) dr[i] = d[i] - 2.0 * dn * n_in[i];
         rec.status = CLOAK_RAY_METAL_CAP;
-        rec.weight = 1.0;
+        rec.weight = vac;
         set_vec(rec.exit_pos, pt);
         set_vec(rec.exit_dir, dr);
         rec.tile_id = room_hit(p, pt, dr, rgb);
@@ -89,7 +91,7 @@ __device__ __forceinline__ void leave(const Params &p, int ev, const double y[6]
     // light enters from the room at this face and leaves towards the camera at the entry face
     double tin = transmission_in(MODE, eo, ee, c, n, mdout);
     double cin[3] = {mat_in[2], mat_in[3], mat_in[4]};
-    double tout = transmission_out(MODE, mat_in[0], mat_in[1], cin, n_in, mk0);
+    double tout = transmission_out(MODE, mat_in[0], mat_in[1], cin, n_in, mk0, analyzer_axis(p));
     rec.weight = tin * tout;
     rec.status = metal ? CLOAK_RAY_HIT_METAL_EXITED : CLOAK_RAY_EXITED;
     set_vec(rec.exit_dir, dout);

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned lo
     }
     // Eq. 12 at the entry face along the physical direction: light leaves the cloak towards the camera
     double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
-    double w_out = transmission_out(MODE, mat[0], mat[1], c, n_in, mk0);
+    double w_out = transmission_out(MODE, mat[0], mat[1], c, n_in, mk0, analyzer_axis(p));
     queue_append(q, y, w_out, (int)idx, cost_bucket(y, k0));
 }
 
