@@ -1,0 +1,218 @@
+// mlp_fused.cu -- the surrogate network's forward pass as ONE persistent tcgen05 kernel.
+//
+// Each CTA (256 threads, one per SM) takes pairs of 128-row tiles through all five layers without their
+// activations leaving the SM:
+//   * the inputs of both tiles arrive by TMA in the 128-byte-swizzled K-major layout the MMA reads;
+//   * one thread streams the layer's weights from L2 in 64-wide K chunks through a 2-slot TMA ring and
+//     issues, per chunk, the tcgen05.mma (M = 128, K = 16) of both tiles against it, accumulating in
+//     TMEM (tile t in columns 256 t .. 256 t + 255: all 512 columns);
+//   * after the layer's MMAs complete, the 8 warps read the accumulators (warp w: tile w / 4, TMEM lanes
+//     32 (w % 4) ..), add the bias, apply GELU and write the BF16 activations back into the swizzled
+//     shared-memory layout as the next layer's A operand (the last layer writes the FP32 outputs).
+// Shared memory: activations 2 x 64 KB, weight ring 2 x 32 KB.  Every mbarrier wait is bounded; on a
+// timeout the kernel sets the error flag, lets its copies in flight land, frees TMEM and returns.
+#include "surrogate.h"
+#include "tc_ptx.cuh"
+
+namespace ck {
+
+namespace {
+constexpr int F_THREADS = 256;
+constexpr uint32_t F_ACT_CHUNK = 128 * 128;                  // 128 rows x 64 BF16 = 16 KB
+constexpr uint32_t F_ACT_BYTES = 2 * 4 * F_ACT_CHUNK;         // 2 tiles x 4 K chunks
+constexpr uint32_t F_RING_SLOT = 256 * 128;                   // up to 256 weight rows x 64 BF16
+constexpr size_t F_SMEM = 1024 + F_ACT_BYTES + 2 * F_RING_SLOT;
+
+struct FusedArgs {
+    const float *bias[SUR_L];
+    float *Y;                    // outputs, 16 FP32 per row
+    long long n;                 // rows of X and Y (a multiple of 128)
+    const unsigned int *m_count; // optional live row count
+    unsigned int *err;
+};
+
+__global__ void __launch_bounds__(F_THREADS, 1)
+    k_mlp_fused(const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtensorMap tW0,
+                const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
+                const __grid_constant__ CUtensorMap tW3, const __grid_constant__ CUtensorMap tW4, FusedArgs a) {
+    extern __shared__ unsigned char fsm_raw[];
+    __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], x_bar, done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+    unsigned char *sm = (unsigned char *)(((uintptr_t)fsm_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *act = sm, *ring = sm + F_ACT_BYTES;
+    const CUtensorMap *tW[SUR_L] = {&tW0, &tW1, &tW2, &tW3, &tW4};
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long live = a.m_count ? min(a.n, (long long)__ldg(a.m_count)) : a.n;
+
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&x_bar), 1);
+        mbar_init(smem_u32(&done_bar), 1);
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+
+    uint32_t G = 0;       // weight chunks loaded so far by this CTA (ring slot G & 1, use G >> 1)
+    uint32_t layers = 0;  // layers completed (phase of done_bar)
+    uint32_t iters = 0;   // tile pairs started (phase of x_bar)
+    uint32_t pending = 0; // chunks loaded and not yet consumed (drained after a timeout)
+    for (long long base = (long long)blockIdx.x * 256; base < live; base += (long long)gridDim.x * 256) {
+        if (tid == 0 && !failed) {
+            mbar_expect_tx(smem_u32(&x_bar), 2 * F_ACT_CHUNK);
+            tma_load_2d(smem_u32(act), &tX, 0, (int)base, smem_u32(&x_bar));
+            tma_load_2d(smem_u32(act + 4 * F_ACT_CHUNK), &tX, 0, (int)(base + 128), smem_u32(&x_bar));
+        }
+        for (int l = 0; l < SUR_L; ++l) {
+            const int nk = l == 0 ? 1 : 4, N = l == SUR_L - 1 ? 16 : SUR_W;
+            if (tid == 0 && !failed) {
+                const uint32_t idesc = bf16_idesc(N), G0 = G;
+                bool ok = true;
+                for (int it = 0; it <= nk && ok; ++it) {
+                    if (it < nk) {  // load chunk it of this layer's weights
+                        const uint32_t g = G0 + it, s = g & 1;
+                        if (g >= 2) ok = mbar_wait(smem_u32(&empty_bar[s]), ((g >> 1) - 1) & 1);
+                        if (!ok) break;
+                        mbar_expect_tx(smem_u32(&full_bar[s]), (uint32_t)N * 128);
+                        tma_load_2d(smem_u32(ring + s * F_RING_SLOT), tW[l], it * 64, 0, smem_u32(&full_bar[s]));
+                        ++pending;
+                        G = g + 1;
+                    }
+                    const int j = it - 1;
+                    if (j >= 0) {  // multiply chunk j for both tiles
+                        const uint32_t g = G0 + j, s = g & 1;
+                        ok = mbar_wait(smem_u32(&full_bar[s]), (g >> 1) & 1);
+                        if (ok && l == 0 && j == 0) ok = mbar_wait(smem_u32(&x_bar), iters & 1);
+                        if (!ok) break;
+                        --pending;
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint64_t bd = sw128_desc(smem_u32(ring + s * F_RING_SLOT));
+                        for (int t = 0; t < 2; ++t) {
+                            const uint64_t ad = sw128_desc(smem_u32(act + (t * 4 + j) * F_ACT_CHUNK));
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+                                asm volatile(
+                                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * 256),
+                                    "l"(ad + (uint64_t)(2 * kk)), "l"(bd + (uint64_t)(2 * kk)), "r"(idesc), "r"(acc));
+                            }
+                        }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            smem_u32(&empty_bar[s])));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&done_bar)));
+                if (!ok) failed = 1;
+            }
+            __syncwarp();
+            const bool done = mbar_wait(smem_u32(&done_bar), layers & 1);
+            ++layers;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // epilogue: warp w reads tile w / 4, TMEM lanes 32 (w % 4) .. + 31 (one row per thread)
+            const int t = warp >> 2, q = warp & 3, r = q * 32 + lane;
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
+            if (done && !failed) {
+                const float *bias = a.bias[l];
+                for (int c = 0; c < N; c += 16) {
+                    uint32_t u[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+                        : "r"(taddr + (uint32_t)c));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    float v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(u[i]) + __ldg(bias + c + i);
+                    if (l < SUR_L - 1) {
+                        // GELU, BF16, into the 128-byte-swizzled K-major layout of chunk c / 64: 16-byte units
+                        // (c % 64) / 8 and + 1 of row r, each XOR-ed with r % 8
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            __nv_bfloat162 h = __floats2bfloat162_rn(gelu_tanh(v[2 * i]), gelu_tanh(v[2 * i + 1]));
+                            pk[i] = *(uint32_t *)&h;
+                        }
+                        unsigned char *chunk = act + (t * 4 + c / 64) * F_ACT_CHUNK + (r >> 3) * 1024 + (r & 7) * 128;
+                        const int u0 = (c & 63) >> 3;
+                        *(uint4 *)(chunk + (((u0) ^ (r & 7)) << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        *(uint4 *)(chunk + (((u0 + 1) ^ (r & 7)) << 4)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    } else {
+                        const long long row = base + t * 128 + r;
+                        if (row < live) {
+                            float4 *y = (float4 *)(a.Y + row * 16);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) y[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        }
+                    }
+                }
+                // the shared-memory writes must be visible to the tensor cores' (async) reads
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            } else if (tid == 0) {
+                failed = 1;
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (failed) break;
+        }
+        ++iters;
+        if (failed) break;
+    }
+    if (failed && tid == 0) {
+        if (a.err) atomicExch(a.err, 1u);
+        // let the weight copies still in flight land before the shared memory is released (bounded)
+        for (uint32_t k = 0; k < pending; ++k) mbar_wait(smem_u32(&full_bar[(G - pending + k) & 1]), ((G - pending + k) >> 1) & 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+}  // namespace
+
+// forward pass of rows [0, n) of s->X into s->Y (rows beyond *m_count skipped when it is set)
+cudaError_t launch_mlp_fused(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st) {
+    static int max_dyn = 0, sms = 0;
+    if (!max_dyn) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_mlp_fused);
+        if (e != cudaSuccess) return e;
+        if ((size_t)(optin - (int)fa.sharedSizeBytes) < F_SMEM) return cudaErrorInvalidValue;
+        e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM);
+        if (e != cudaSuccess) return e;
+        max_dyn = (int)F_SMEM;
+    }
+    if (n <= 0 || n % 128) return cudaErrorInvalidValue;
+    CUtensorMap tx;
+    if (make_tmap_bf16(&tx, s->X, (int)n, 64, GEMM_TILE_M) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    FusedArgs a;
+    for (int l = 0; l < SUR_L; ++l) a.bias[l] = s->b[l];
+    a.Y = s->Y;
+    a.n = n;
+    a.m_count = m_count;
+    a.err = s->err;
+    const long long pairs = (n + 255) / 256;
+    const int grid = (int)std::min<long long>(pairs, (long long)sms);
+    k_mlp_fused<<<grid, F_THREADS, F_SMEM, st>>>(tx, s->tWb[0], s->tWb[1], s->tWb[2], s->tWb[3], s->tWb[4], a);
+    return cudaGetLastError();
+}
+
+}  // namespace ck

@@ -329,51 +329,20 @@ cudaError_t sur_ensure_inference(SurNet *s, long long rows) {
         s->inf_arena = nullptr;
         s->inf_rows = 0;
     }
-    const long long crows = std::min<long long>(rows, SUR_CHUNK);
-    const size_t xb = align256((size_t)rows * 64 * 2), hb = align256((size_t)crows * SUR_W * 2),
-                 yb = align256((size_t)rows * 16 * 4), eb = align256((size_t)rows);
-    cudaError_t e = cudaMalloc(&s->inf_arena, xb + 2 * hb + yb + eb);
+    const size_t xb = align256((size_t)rows * 64 * 2), yb = align256((size_t)rows * 16 * 4), eb = align256((size_t)rows);
+    cudaError_t e = cudaMalloc(&s->inf_arena, xb + yb + eb);
     if (e != cudaSuccess) return e;
     char *p = s->inf_arena;
     s->X = (__nv_bfloat16 *)p; p += xb;
-    s->H0 = (__nv_bfloat16 *)p; p += hb;
-    s->H1 = (__nv_bfloat16 *)p; p += hb;
     s->Y = (float *)p; p += yb;
     s->elig = (unsigned char *)p;
     if ((e = cudaMemset(s->X, 0, xb)) != cudaSuccess) return e;  // columns 14..63 stay zero
-    if (!tmap(&s->tH0, s->H0, crows, SUR_W, GEMM_TILE_M) || !tmap(&s->tH1, s->H1, crows, SUR_W, GEMM_TILE_M))
-        return cudaErrorInvalidValue;
     s->inf_rows = rows;
     return cudaSuccess;
 }
 
 cudaError_t sur_forward(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st) {
-    __nv_bfloat16 *outs[2] = {s->H0, s->H1};
-    const CUtensorMap *touts[2] = {&s->tH0, &s->tH1};
-    cudaError_t e = cudaSuccess;
-    for (long long base = 0; base < n && e == cudaSuccess; base += SUR_CHUNK) {
-        const long long rows = std::min<long long>(SUR_CHUNK, n - base);
-        CUtensorMap tx;
-        if (!tmap(&tx, s->X + (size_t)base * 64, rows, 64, GEMM_TILE_M)) return cudaErrorInvalidValue;
-        const CUtensorMap *in = &tx;
-        for (int l = 0; l < SUR_L && e == cudaSuccess; ++l) {
-            SurDims d = sur_dims(l);
-            GemmArgs g = gemm_args((int)rows, d.nout, d.kin, l < SUR_L - 1 ? EPI_BIAS_GELU : EPI_BIAS, s->err);
-            g.m_count = m_count;
-            g.m_base = base;
-            g.bias = s->b[l];
-            if (l < SUR_L - 1) {
-                g.H = outs[l & 1];
-                g.ldh = SUR_W;
-            } else {
-                g.Z = s->Y + (size_t)base * 16;
-                g.ldz = 16;
-            }
-            e = gemm(*in, s->tWb[l], g, st);
-            in = touts[l & 1];
-        }
-    }
-    return e;
+    return launch_mlp_fused(s, n, m_count, st);
 }
 
 // ------------------------------------------------------------------ training workspace

@@ -69,16 +69,14 @@ struct SurNet {
     int trained;
     double info[8];       // final stage-1 loss, final stage-2 loss, lateral fraction, rays, seconds, ...
     unsigned int *err;    // device GEMM error flag
-    // inference scratch: inputs, outputs and gate flags for inf_rows rows (a multiple of 128); hidden
-    // activations for one chunk of SUR_CHUNK rows (the GEMM chain runs chunk by chunk)
+    // inference scratch: inputs, outputs and gate flags for inf_rows rows (a multiple of 128); the
+    // hidden activations never leave the SM (mlp_fused.cu)
     long long inf_rows;
     char *inf_arena;
-    __nv_bfloat16 *X, *H0, *H1;
+    __nv_bfloat16 *X;
     float *Y;
     unsigned char *elig;
-    CUtensorMap tH0, tH1;
 };
-constexpr long long SUR_CHUNK = 1 << 20;
 
 // lifetime and parameters (surrogate.cu)
 SurNet *sur_create(double R1, double R2, double H, unsigned long long seed, const char **why);
@@ -87,6 +85,8 @@ cudaError_t sur_refresh_bf16(SurNet *s, cudaStream_t st);  // Wb / WTb from the 
 // forward pass of n rows of X (BF16 input pairs, n x 64) into Y (FP32, n x 16); n % 128 == 0;
 // m_count: optional device row count (rows at or beyond it are skipped tile by tile)
 cudaError_t sur_forward(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st);
+// the same as one persistent tcgen05 kernel (mlp_fused.cu)
+cudaError_t launch_mlp_fused(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st);
 cudaError_t sur_ensure_inference(SurNet *s, long long rows);
 
 // training data (kernels_batch.cu): n seeded rays through entry, the any-medium integrator and exit;
