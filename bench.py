@@ -212,7 +212,7 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
     info = ck.cloak_surrogate_info(trainer.h)
     path = os.path.join(tempfile.gettempdir(), f"cloak_surrogate_{os.getpid()}.bin")
     ck.cloak_surrogate_save(trainer.h, path)
-    # forward pass of 2^22 rows on the tensor cores (5 GEMM launches per 2^20-row chunk)
+    # forward pass of 2^22 rows on the tensor cores (one fused persistent launch)
     n = 1 << 22
     x = torch.rand((n, 7), device="cuda") * 2 - 1
     y = torch.empty((n, 5), device="cuda")
@@ -310,7 +310,8 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
             "training": {**{k: float(v) for k, v in info.items()}, "wall_s": train_wall, "epochs": args.sur_epochs},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) of measured",
-                         "kernel": "k_gemm_tc (tcgen05 BF16, FP32 accumulation): forward pass of 2^22 rows",
+                         "kernel": "k_mlp_fused (persistent tcgen05 BF16 network, FP32 accumulation in TMEM): "
+                                   "forward pass of 2^22 rows",
                          "flops_per_ray": SUR_FLOPS_PER_RAY, "ms": fwd_ms}}
 
 

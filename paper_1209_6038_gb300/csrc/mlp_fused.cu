@@ -39,12 +39,15 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], x_bar, done_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
+    __shared__ __align__(16) float sbias[SUR_L][SUR_W];  // every layer's bias, read by the epilogue
     unsigned char *sm = (unsigned char *)(((uintptr_t)fsm_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *act = sm, *ring = sm + F_ACT_BYTES;
     const CUtensorMap *tW[SUR_L] = {&tW0, &tW1, &tW2, &tW3, &tW4};
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long live = a.m_count ? min(a.n, (long long)__ldg(a.m_count)) : a.n;
 
+    for (int l = 0; l < SUR_L; ++l)
+        for (int c = tid; c < SUR_W; c += F_THREADS) sbias[l][c] = c < (l == SUR_L - 1 ? 16 : SUR_W) ? a.bias[l][c] : 0.f;
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             const int t = warp >> 2, q = warp & 3, r = q * 32 + lane;
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
             if (done && !failed) {
-                const float *bias = a.bias[l];
+                const float *bias = sbias[l];
                 for (int c = 0; c < N; c += 16) {
                     uint32_t u[16];
                     asm volatile(
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     float v[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(u[i]) + __ldg(bias + c + i);
+                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(u[i]) + bias[c + i];
                     if (l < SUR_L - 1) {
                         // GELU, BF16, into the 128-byte-swizzled K-major layout of chunk c / 64: 16-byte units
                         // (c % 64) / 8 and + 1 of row r, each XOR-ed with r % 8
