@@ -80,6 +80,7 @@ def lib():
         L.orc_shade.argtypes = [C.POINTER(_Cloak), dp, dp, dp]
         L.orc_render.argtypes = [C.POINTER(_Cloak), C.POINTER(_Integ), C.POINTER(_Camera), C.c_int, C.c_int,
                                  C.c_uint64, C.POINTER(C.c_int64), C.c_long, dp, C.c_void_p, C.c_int]
+        L.orc_rhs_hamiltonian.argtypes = [C.POINTER(_Cloak), C.c_int, dp, dp]
         # surrogate (surrogate_oracle.h)
         ip = C.POINTER(C.c_int)
         L.orc_gelu.restype = C.c_double
@@ -205,6 +206,14 @@ def rhs(cloak: Cloak, mode, y):
     y = _vec(y, 6)
     dy = np.zeros(6)
     lib().orc_rhs(cloak.ref, mode, _dp(y), _dp(dy))
+    return dy
+
+
+def rhs_hamiltonian(cloak: Cloak, mode, y):
+    """d(x, k)/dt of the Hamiltonian form (state y = (x, k), k = M v)."""
+    y = _vec(y, 6)
+    dy = np.zeros(6)
+    lib().orc_rhs_hamiltonian(cloak.ref, mode, _dp(y), _dp(dy))
     return dy
 
 

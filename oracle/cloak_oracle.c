@@ -899,6 +899,46 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
     }
 }
 
+/* The ray equations in Hamiltonian form (the comparison system of Sect. 4's closing remark): state
+   (x, k) with k = M v (Eq. 7; M = eps_o I for the ordinary ray), H = (k^T M^-1 k - 1) / 2,
+   dx/dt = dH/dk = M^-1 k, dk/dt = -dH/dx = -(1/2) k^T (d_i M^-1) k = (1/2) v^T (d_i M) v with v = M^-1 k
+   (d M^-1 = -M^-1 (d M) M^-1, M symmetric). */
+void orc_rhs_hamiltonian(const orc_cloak *c, int mode, const double y[6], double dy[6]) {
+    const double *x = y, *k = y + 3;
+    double M[9], dM[27], Mi[9];
+    if (mode == ORC_EXTRAORDINARY) {
+        orc_aux_matrix(c, x, M, dM);
+        orc_aux_inverse(c, x, Mi);
+    } else {
+        double eo = c->eps_o_test, g[3] = {0, 0, 0};
+        if (c->variant != ORC_TEST_CONST) {
+            double r, rh[3], th[3], e[3], de[3];
+            cyl_basis(x, &r, rh, th);
+            cyl_eps(c, r, e, de);
+            eo = (c->variant == ORC_RADIAL) ? e[1] : e[0];
+            double deo = (c->variant == ORC_RADIAL) ? de[1] : de[0];
+            for (int i = 0; i < 3; ++i) g[i] = deo * rh[i];
+        }
+        memset(M, 0, sizeof(M));
+        memset(Mi, 0, sizeof(Mi));
+        memset(dM, 0, sizeof(dM));
+        for (int i = 0; i < 3; ++i) {
+            M[4 * i] = eo;
+            Mi[4 * i] = 1.0 / eo;
+            for (int d = 0; d < 3; ++d) dM[9 * d + 4 * i] = g[d];
+        }
+    }
+    double v[3];
+    matvec3(Mi, k, v);
+    for (int i = 0; i < 3; ++i) dy[i] = v[i];
+    for (int d = 0; d < 3; ++d) {
+        double s = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) s += v[i] * dM[9 * d + 3 * i + j] * v[j];
+        dy[3 + d] = 0.5 * s;
+    }
+}
+
 void orc_trace_rays(const orc_cloak *c, const orc_integrator *in, int mode, const double *rays, long n,
                     orc_record *recs, int nthreads) {
     if (nthreads < 1) nthreads = 1;

@@ -100,6 +100,10 @@ int orc_transmission_in(const orc_cloak *c, const double x[3], const double nhat
 int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const double nhat[3],
                          const double k[3], double out[4]);
 
+/* Hamiltonian form of the ray equations, state (x, k), k = M v: dx/dt = M^-1 k,
+   dk/dt = (1/2) v^T (d_i M) v (the comparison system of Sect. 4's closing remark) */
+void orc_rhs_hamiltonian(const orc_cloak *c, int mode, const double y[6], double dy[6]);
+
 /* ---- integrator steps (Sect. 4: RK4; Dormand-Prince 5(4) adaptive) ---- */
 void orc_rk4_step(const orc_cloak *c, int mode, const double y[6], double h, double out[6]);
 void orc_dp45_step(const orc_cloak *c, int mode, const double y[6], double h,
