@@ -17,6 +17,7 @@ import numpy as np
 from . import build as _build
 
 RADIAL, AZIMUTHAL, TEST_CONST = 0, 1, 100
+FERMAT, HAMILTONIAN = 0, 1
 ORDINARY, EXTRAORDINARY = 0, 1
 RK4, DP45 = 0, 1
 STATUS = {0: "MISSED", 1: "EXITED", 2: "HIT_METAL_EXITED", 3: "NO_TRANSMISSION", 4: "TIR",
@@ -30,7 +31,7 @@ assert RECORD_DTYPE.itemsize == 80
 class _Cloak(C.Structure):
     _fields_ = [("variant", C.c_int), ("R1", C.c_double), ("R2", C.c_double), ("H", C.c_double),
                 ("eps_o_test", C.c_double), ("eps_e_test", C.c_double), ("c_test", C.c_double * 3),
-                ("scene_seed", C.c_uint64), ("analyzer", C.c_double * 3)]
+                ("scene_seed", C.c_uint64), ("analyzer", C.c_double * 3), ("form", C.c_int)]
 
 
 class _Integ(C.Structure):
@@ -118,10 +119,11 @@ class Cloak:
     homogeneous uniaxial test medium (Eq. 1 with a fixed optic axis)."""
 
     def __init__(self, variant=RADIAL, R1=0.5, R2=1.0, H=2.0, eps_o=1.0, eps_e=1.0, c_hat=(0, 0, 1),
-                 scene_seed=0, analyzer=(0.0, 0.0, 0.0)):
-        """analyzer: axis of a linear polariser in front of the camera (zero: none)."""
+                 scene_seed=0, analyzer=(0.0, 0.0, 0.0), form=0):
+        """analyzer: axis of a linear polariser in front of the camera (zero: none); form: ray equations
+        (0 Fermat form, Eq. 2 / Eq. 8; 1 Hamiltonian form)."""
         self.s = _Cloak(variant, R1, R2, H, eps_o, eps_e, (C.c_double * 3)(*c_hat), scene_seed,
-                        (C.c_double * 3)(*analyzer))
+                        (C.c_double * 3)(*analyzer), form)
 
     @property
     def ref(self):

@@ -545,15 +545,21 @@ int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const 
 /* integrators                                                          */
 /* ------------------------------------------------------------------ */
 /* classical fourth-order Runge-Kutta (Sect. 4) */
+/* right-hand side of the cloak's formulation (Fermat: orc_rhs; Hamiltonian: orc_rhs_hamiltonian) */
+static void rhs_of(const orc_cloak *c, int mode, const double y[6], double dy[6]) {
+    if (c->form) orc_rhs_hamiltonian(c, mode, y, dy);
+    else orc_rhs(c, mode, y, dy);
+}
+
 void orc_rk4_step(const orc_cloak *c, int mode, const double y[6], double h, double out[6]) {
     double k1[6], k2[6], k3[6], k4[6], t[6];
-    orc_rhs(c, mode, y, k1);
+    rhs_of(c, mode, y, k1);
     for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.5 * h * k1[i];
-    orc_rhs(c, mode, t, k2);
+    rhs_of(c, mode, t, k2);
     for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.5 * h * k2[i];
-    orc_rhs(c, mode, t, k3);
+    rhs_of(c, mode, t, k3);
     for (int i = 0; i < 6; ++i) t[i] = y[i] + h * k3[i];
-    orc_rhs(c, mode, t, k4);
+    rhs_of(c, mode, t, k4);
     for (int i = 0; i < 6; ++i) out[i] = y[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
 }
 
@@ -572,14 +578,14 @@ void orc_dp45_step(const orc_cloak *c, int mode, const double y[6], double h, do
     static const double b4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200,
                                  187.0 / 2100, 1.0 / 40};
     double k[7][6], t[6];
-    orc_rhs(c, mode, y, k[0]);
+    rhs_of(c, mode, y, k[0]);
     for (int s = 1; s < 7; ++s) {
         for (int i = 0; i < 6; ++i) {
             double acc = 0.0;
             for (int j = 0; j < s; ++j) acc += a[s][j] * k[j][i];
             t[i] = y[i] + h * acc;
         }
-        orc_rhs(c, mode, t, k[s]);
+        rhs_of(c, mode, t, k[s]);
     }
     for (int i = 0; i < 6; ++i) {
         double s5 = 0.0, s4 = 0.0;
@@ -775,7 +781,10 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
         return rec->status;
     }
     double x_in[3] = {p[0], p[1], p[2]}, n_in[3] = {n[0], n[1], n[2]};
+    /* state (x, v) of the Fermat form or (x, k) of the Hamiltonian form */
     double y[6] = {p[0], p[1], p[2], v0[0], v0[1], v0[2]}, y1[6], t = 0.0;
+    if (c->form)
+        for (int i = 0; i < 3; ++i) y[3 + i] = k0[i];
     path_push(path, path_cap, &plen, t, y);
     double h = in->kind == ORC_RK4 ? in->h_or_tol : 1e-3, tol = in->h_or_tol;
     int metal = 0, steps = 0;
@@ -870,7 +879,10 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
         /* exit refraction (Sect. 3): keep k_t, vacuum k_n = +sqrt(1 - |k_t|^2) */
         double xo[3] = {y[0], y[1], y[2]}, no[3], kx[3], ktx[3];
         face_normal(ev_hit, xo, no);
-        wave_vector(c, mode, xo, y + 3, kx);
+        if (c->form)
+            for (int i = 0; i < 3; ++i) kx[i] = y[3 + i];
+        else
+            wave_vector(c, mode, xo, y + 3, kx);
         double kn = dot3(kx, no);
         for (int i = 0; i < 3; ++i) ktx[i] = kx[i] - kn * no[i];
         double kt2 = dot3(ktx, ktx);

@@ -49,6 +49,8 @@ typedef struct {
     uint64_t scene_seed;       /* seed of the procedural room */
     double analyzer[3];        /* axis of a linear polariser in front of the camera (the paper's
                                   "polarization goggles"); all zero: none */
+    int form;                  /* ray equations: 0 Fermat form (Eq. 2 / Eq. 8, state (x, v)),
+                                  1 Hamiltonian form (state (x, k), k = M v) */
 } orc_cloak;
 
 typedef struct {

@@ -74,3 +74,38 @@ def test_rk4_in_hamiltonian_form_keeps_h_zero():
             assert math.hypot(yy[0], yy[1]) > 0.5
         drift[h] = abs(H(yy))
     assert drift[2e-3] < 1e-9 and drift[4e-3] / max(drift[2e-3], 1e-300) > 8  # fourth order
+
+
+def test_hamiltonian_trace_agrees_with_the_fermat_trace():
+    """Both forms integrate the same rays: their exits agree to the integrators' accuracy."""
+    integ = O.Integrator(O.DP45, 1e-11, 2_000_000)
+    rng = np.random.default_rng(11)
+    n = 0
+    for variant in (O.RADIAL, O.AZIMUTHAL):
+        for mode in (O.ORDINARY, O.EXTRAORDINARY):
+            for _ in range(6):
+                o = np.array([4.0, rng.uniform(-0.9, 0.9), rng.uniform(-0.6, 0.6)])
+                d = np.array([-1.0, rng.uniform(-0.05, 0.05), rng.uniform(-0.1, 0.1)])
+                d /= np.linalg.norm(d)
+                rf, _ = O.trace_ray(O.Cloak(variant, form=O.FERMAT), integ, mode, o, d)
+                rh, _ = O.trace_ray(O.Cloak(variant, form=O.HAMILTONIAN), integ, mode, o, d)
+                assert rf["status"] == rh["status"]
+                if rf["status"] in (1, 2):
+                    n += 1
+                    assert np.max(np.abs(rf["exit_dir"] - rh["exit_dir"])) < 1e-8
+                    assert np.max(np.abs(rf["exit_pos"] - rh["exit_pos"])) < 1e-8
+                    assert abs(rf["weight"] - rh["weight"]) < 1e-8
+    assert n > 15
+
+
+@pytest.mark.parametrize("variant", [O.RADIAL, O.AZIMUTHAL])
+def test_hamiltonian_trace_cloaks_in_plane_rays(variant):
+    integ = O.Integrator(O.DP45, 1e-11, 2_000_000)
+    for b in (0.2, 0.55, 0.9):
+        o = np.array([-4.0, b, 0.0])
+        d = np.array([1.0, 0.0, 0.0])
+        rec, _ = O.trace_ray(O.Cloak(variant, form=O.HAMILTONIAN), integ, O.EXTRAORDINARY, o, d)
+        assert rec["status"] == 1
+        assert np.max(np.abs(rec["exit_dir"] - d)) < 1e-9
+        assert abs(rec["exit_pos"][1] - b) < 1e-9 and abs(rec["exit_pos"][0] - math.sqrt(1 - b * b)) < 1e-9
+        assert abs(rec["tof"] - 2 * math.sqrt(1 - b * b)) < 1e-9
