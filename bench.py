@@ -354,6 +354,72 @@ def orbit_section(args, ck, inputs, torch, flush):
             "stage_ms": {"camera_entry_sort": st[0], "integrate": st[1], "exit_shade": st[2], "resolve": st[3]}}
 
 
+def formulation_section(args, ck, torch):
+    """Fermat form (Eq. 2 / Eq. 8, state (x, v)) against the Hamiltonian form (state (x, k)) on rays
+    that a perfect cloak must pass undisturbed: in-plane extraordinary rays (direction across the axis,
+    impact parameter b, height z) through both cloaks, whose exact exit is the vacuum line itself (exit
+    point (sqrt(R2^2 - b^2), b, z), direction unchanged, optical time = the vacuum chord).  For each form
+    and stepper setting (RK4 step h, DP5(4) tolerance) the section measures the largest relative error
+    of exit point (/ R2), direction and time over all rays, and the time of one plain trace launch; then
+    reports, per form, the cheapest setting that reaches 1e-8 (the paper's Sect. 5 comparison)."""
+    n = 1 << 17
+    R2 = 1.0
+    g = torch.Generator(device="cpu").manual_seed(2024)
+    b = (0.05 + 0.93 * torch.rand(n, generator=g, dtype=torch.float64)) * torch.where(
+        torch.rand(n, generator=g) < 0.5, -1.0, 1.0).double()
+    z = (torch.rand(n, generator=g, dtype=torch.float64) - 0.5) * 1.6
+    rays = torch.zeros((n, 6), dtype=torch.float64)
+    rays[:, 0], rays[:, 1], rays[:, 2], rays[:, 3] = -4.0, b, z, 1.0
+    rays = rays.cuda()
+    bx = b.cuda()
+    ex = torch.stack([torch.sqrt(R2 * R2 - bx * bx), bx, z.cuda()], 1)
+    tof_exact = 2 * torch.sqrt(R2 * R2 - bx * bx)
+    out = torch.empty(n * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
+    settings = [(ck.RK4, 0.0125 / 2 ** k) for k in range(7)] + [(ck.DP45, 10.0 ** -e) for e in range(6, 14)]
+    res = {}
+    for form, fname in ((ck.FORM_FERMAT, "fermat"), (ck.FORM_HAMILTONIAN, "hamiltonian")):
+        for variant, vname in ((ck.RADIAL, "radial"), (ck.AZIMUTHAL, "azimuthal")):
+            c = ck.Cloak(variant, R2=R2)
+            for kind, hv in settings:
+                c.integrator(kind, hv, ck.FP64, 10_000_000).formulation(form)
+                c.trace_rays(ck.POL_EXTRAORDINARY, rays, out)
+                torch.cuda.synchronize()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ev[0].record()
+                c.trace_rays(ck.POL_EXTRAORDINARY, rays, out)
+                ev[1].record()
+                ev[1].synchronize()
+                f64 = out.view(torch.float64).view(n, 10)
+                i32 = out.view(torch.int32).view(n, 20)
+                ok = bool((i32[:, 17] == 1).all())
+                err_pos = float((f64[:, 0:3] - ex).abs().max()) / R2
+                err_dir = float((f64[:, 3:6] - rays[:, 3:6]).abs().max())
+                err_tof = float(((f64[:, 6] - tof_exact).abs() / tof_exact).max())
+                res[(fname, vname, kind, hv)] = {
+                    "ms": ev[0].elapsed_time(ev[1]), "mean_steps": float(i32[:, 18].double().mean()),
+                    "max_rel_err": max(err_pos, err_dir, err_tof) if ok else float("inf")}
+            c.close()
+    del out
+    summary = {}
+    for kind, kname in ((ck.RK4, "rk4"), (ck.DP45, "dp45")):
+        for vname in ("radial", "azimuthal"):
+            row = {}
+            for fname in ("fermat", "hamiltonian"):
+                hit = [(hv, r) for (f, v, k, hv), r in res.items()
+                       if f == fname and v == vname and k == kind and r["max_rel_err"] <= 1e-8]
+                if hit:
+                    hv, r = min(hit, key=lambda t: t[1]["ms"])
+                    row[fname] = {"h" if kind == ck.RK4 else "tol": hv, **r}
+            if len(row) == 2:
+                row["time_ratio_hamiltonian_over_fermat"] = row["hamiltonian"]["ms"] / row["fermat"]["ms"]
+            summary[f"{kname}_{vname}"] = row
+    return {"workload": f"{n} in-plane extraordinary rays per cloak (|b| in [0.05, 0.98] R2, |z| < 0.8), exact exit "
+                        "= the vacuum line; plain trace launch; cheapest setting with max relative error <= 1e-8",
+            "to_1e-8": summary,
+            "sweep": [{"form": f, "variant": v, "stepper": "rk4" if k == ck.RK4 else "dp45", "h_or_tol": hv, **r}
+                      for (f, v, k, hv), r in res.items()]}
+
+
 # ------------------------------------------------------------------ native arm
 def main():
     ap = argparse.ArgumentParser()
@@ -368,6 +434,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-orbit", action="store_true")
+    ap.add_argument("--no-formulation", action="store_true")
     ap.add_argument("--sur-epochs", type=int, default=60, help="stage-1 epochs of the surrogate's training")
     ap.add_argument("--profile-image", default=None,
                     help="VARIANT,MODE,ELEV: render only this image twice (for profilers), e.g. 1,1,20")
@@ -653,6 +720,10 @@ def main():
         # ---- the batched form: 64-pose orbit, 256 views, one persistent launch
         if not args.no_orbit:
             out["batched_orbit"] = orbit_section(args, ck, inputs, torch, flush)
+
+        # ---- Fermat against Hamiltonian ray equations, time to 1e-8 on perfect-cloaking rays
+        if not args.no_formulation:
+            out["formulation"] = formulation_section(args, ck, torch)
 
     # ---- comparators on the same workload: per-image wavefront and the plain FP64 integrator
     if not args.no_plain:

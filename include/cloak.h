@@ -118,6 +118,13 @@ int cloak_set_test_medium(cloak_t *h, double eps_o, double eps_e, const double c
 /* Seed of the procedural room that stands in for the paper's scenery (checkered walls and floor,
  * 8 tiles per unit, box x,y in [-10,10], z in [-height/2, -height/2 + 10]). */
 int cloak_set_scene_seed(cloak_t *h, unsigned long long seed);
+/* Ray equations: CLOAK_FORM_FERMAT (default: Eq. 2 for ordinary, Eq. 8 for extraordinary rays, state
+ * (x, v)) or CLOAK_FORM_HAMILTONIAN (the comparison system of Sect. 4's closing remark: state (x, k) with
+ * k = M v, dx/dt = M^-1 k, dk/dt = -(1/2) k^T (grad M^-1) k; the same integrator, crossings and
+ * interfaces).  The Hamiltonian form needs a radial or azimuthal handle and FP64 (precision CLOAK_FP64 or
+ * CLOAK_SURROGATE); CLOAK_ESTATE otherwise. */
+enum { CLOAK_FORM_FERMAT = 0, CLOAK_FORM_HAMILTONIAN = 1 };
+int cloak_set_formulation(cloak_t *h, int formulation);
 /* Linear polariser in front of the camera (the paper's "polarization goggles"): CLOAK_ANALYZER_NONE,
  * CLOAK_ANALYZER_RIGHT (axis along the camera's right vector) or CLOAK_ANALYZER_UP (its up vector).  With
  * one, a ray's weight is multiplied by the fraction of the vacuum wave leaving the cloak towards the

@@ -50,6 +50,7 @@ SIGNATURES = {
     "cloak_render_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
     "cloak_set_analyzer": (C.c_int, [C.c_void_p, C.c_int]),
+    "cloak_set_formulation": (C.c_int, [C.c_void_p, C.c_int]),
     "cloak_render_panel": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                      C.c_void_p]),
     "cloak_surrogate_train": (C.c_int, [C.c_void_p, C.c_long, C.c_ulonglong, C.c_int, C.c_void_p]),
@@ -208,6 +209,11 @@ def cloak_render_noalloc(h, polarization, spp, seed, rgba, stream=None):
 # ------------------------------------------------------------------ panels of the paper's figures
 PANEL_ROOM, PANEL_METAL, PANEL_UNPOLARIZED, PANEL_POLARIZER_RIGHT, PANEL_POLARIZER_UP = 0, 1, 2, 3, 4
 ANALYZER_NONE, ANALYZER_RIGHT, ANALYZER_UP = 0, 1, 2
+FORM_FERMAT, FORM_HAMILTONIAN = 0, 1
+
+
+def cloak_set_formulation(h, formulation):
+    return _check(load().cloak_set_formulation(h, formulation))
 
 
 def cloak_set_analyzer(h, analyzer):
@@ -332,6 +338,11 @@ class Cloak:
             out = torch.empty((self.height, self.width, 4), dtype=torch.float32, device="cuda")
         cloak_render(self.h, polarization, spp, seed, out, stream)
         return out
+
+    def formulation(self, formulation=FORM_FERMAT):
+        """Ray equations: FORM_FERMAT (Eq. 2 / Eq. 8) or FORM_HAMILTONIAN (state (x, k))."""
+        cloak_set_formulation(self.h, formulation)
+        return self
 
     def analyzer(self, analyzer=ANALYZER_NONE):
         """Linear polariser in front of the camera (ANALYZER_NONE / _RIGHT / _UP)."""

@@ -27,7 +27,8 @@ struct cloak {
     int precision;
     long max_steps;
     int schedule, packet, steps_per_round;
-    int analyzer;  // CLOAK_ANALYZER_*
+    int analyzer;     // CLOAK_ANALYZER_*
+    int formulation;  // CLOAK_FORM_*
     int device;
     // library-owned scratch of the wavefront schedule (queue + per-sample buffer), grown on demand
     void *scratch;
@@ -116,6 +117,7 @@ static int make_params(const cloak *h, ck::Params &p) {
     p.W = h->W;
     p.Hp = h->Hp;
     p.analyzer = h->analyzer;
+    p.formulation = h->formulation == CLOAK_FORM_HAMILTONIAN ? 1 : 0;
     return CLOAK_OK;
 }
 
@@ -244,6 +246,7 @@ cloak_t *cloak_create(int variant, double R1, double R2, double height) {
     h->packet = 0;
     h->steps_per_round = 0;
     h->analyzer = CLOAK_ANALYZER_NONE;
+    h->formulation = CLOAK_FORM_FERMAT;
     h->device = dev;
     h->scratch = nullptr;
     h->scratch_bytes = 0;
@@ -351,6 +354,8 @@ int cloak_set_integrator(cloak_t *h, int kind, double h_or_tol, int precision, l
         precision != CLOAK_SURROGATE)
         return fail(CLOAK_EINVAL, "unknown precision %d", precision);
     if (max_steps < 1 || max_steps > 2000000000L) return fail(CLOAK_EINVAL, "max_steps out of range");
+    if (h->formulation == CLOAK_FORM_HAMILTONIAN && (precision == CLOAK_MIXED || precision == CLOAK_MIXED_FF))
+        return fail(CLOAK_EINVAL, "the Hamiltonian form runs in FP64");
     h->integ = kind;
     h->h_or_tol = h_or_tol;
     h->precision = precision;
@@ -368,6 +373,20 @@ int cloak_set_test_medium(cloak_t *h, double eps_o, double eps_e, const double c
     h->eo_t = eps_o;
     h->ee_t = eps_e;
     for (int i = 0; i < 3; ++i) h->c_t[i] = c_hat[i];
+    return CLOAK_OK;
+}
+
+int cloak_set_formulation(cloak_t *h, int formulation) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (formulation != CLOAK_FORM_FERMAT && formulation != CLOAK_FORM_HAMILTONIAN)
+        return fail(CLOAK_EINVAL, "unknown formulation %d", formulation);
+    if (formulation == CLOAK_FORM_HAMILTONIAN) {
+        if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
+            return fail(CLOAK_ESTATE, "the Hamiltonian form needs a radial or azimuthal cloak handle");
+        if (h->precision == CLOAK_MIXED || h->precision == CLOAK_MIXED_FF)
+            return fail(CLOAK_ESTATE, "the Hamiltonian form runs in FP64");
+    }
+    h->formulation = formulation;
     return CLOAK_OK;
 }
 

@@ -44,6 +44,8 @@ struct Params {
     int W, Hp;
     // linear polariser in front of the camera: 0 none, 1 along the camera's right vector, 2 along its up vector
     int analyzer;
+    // ray equations: 0 Fermat form (Eq. 2 / Eq. 8, state (x, v)); 1 Hamiltonian form (state (x, k), k = M v)
+    int formulation;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -144,8 +146,70 @@ __device__ __forceinline__ void accel(T R1, T K, T invK, T x, T y, T vx, T vy, T
     }
 }
 
+// d(x, k)/dt of the Hamiltonian form, H = (k^T M^-1 k - 1) / 2: dx/dt = M^-1 k, dk/dt = -dH/dx, in closed
+// cylindrical form with k_r = k . r-hat, k_t = k . theta-hat, g = f'/f, u = r - R1:
+//   radial e    M^-1 = diag(1/K, 1/f, 1/f): dk_r = g (k_t^2 + k_z^2) / (2 f), dk_t = k_r k_t (1/f - 1/K) / r
+//   azimuthal e M^-1 = diag(1/K, 1/f, 1/K): dk_r = g k_t^2 / (2 f),           dk_t = k_r k_t (1/f - 1/K) / r
+//   azimuthal o M^-1 = I / f:              dk_r = g |k|^2 / (2 f),           dk_t = 0
+//   radial o    M^-1 = I / K:              dk = 0
+// (the terms in dk_t come from the rotation of the local frame with x at fixed Cartesian k)
+template <int VAR, int MODE>
+__device__ __forceinline__ void ham_fixed(double R1, double K, double invK, const double y[6], double dy[6]) {
+    const double kx = y[3], ky = y[4], kz = y[5];
+    if (VAR == V_RADIAL && MODE == M_ORD) {
+        dy[0] = kx * invK; dy[1] = ky * invK; dy[2] = kz * invK;
+        dy[3] = 0.0; dy[4] = 0.0; dy[5] = 0.0;
+        return;
+    }
+    const double r2 = y[0] * y[0] + y[1] * y[1];
+    const double ir = rsqrt(r2), r = r2 * ir;
+    const double cx = y[0] * ir, cy = y[1] * ir;
+    const double kr = kx * cx + ky * cy, kt = ky * cx - kx * cy;
+    const double u = r - R1, iu = 1.0 / u;
+    const double g = 2.0 * R1 * ir * iu;        // f'/f
+    const double invf = invK * r2 * iu * iu;    // 1/f = r^2 / (K u^2)
+    double vr, vt, vz, dkr, dkt;
+    if (MODE == M_EXT) {
+        vr = kr * invK;
+        vt = kt * invf;
+        dkt = kr * kt * (invf - invK) * ir;
+        if (VAR == V_RADIAL) {
+            vz = kz * invf;
+            dkr = 0.5 * g * invf * (kt * kt + kz * kz);
+        } else {
+            vz = kz * invK;
+            dkr = 0.5 * g * invf * kt * kt;
+        }
+    } else {  // azimuthal ordinary
+        vr = kr * invf;
+        vt = kt * invf;
+        vz = kz * invf;
+        dkr = 0.5 * g * invf * (kr * kr + kt * kt + kz * kz);
+        dkt = 0.0;
+    }
+    dy[0] = vr * cx - vt * cy;
+    dy[1] = vr * cy + vt * cx;
+    dy[2] = vz;
+    dy[3] = dkr * cx - dkt * cy;
+    dy[4] = dkr * cy + dkt * cx;
+    dy[5] = 0.0;
+}
+
 template <int VAR, int MODE>
 __device__ __forceinline__ void rhs(const Params &p, const double y[6], double dy[6], int vm = 0) {
+    if (p.formulation) {  // Hamiltonian form (radial and azimuthal cloaks)
+        if (VAR != V_ANY) {
+            ham_fixed<VAR, MODE>(p.R1, p.K, p.invK, y, dy);
+            return;
+        }
+        switch (vm) {
+        case 0: ham_fixed<V_RADIAL, M_ORD>(p.R1, p.K, p.invK, y, dy); break;
+        case 1: ham_fixed<V_RADIAL, M_EXT>(p.R1, p.K, p.invK, y, dy); break;
+        case 2: ham_fixed<V_AZIMUTHAL, M_ORD>(p.R1, p.K, p.invK, y, dy); break;
+        default: ham_fixed<V_AZIMUTHAL, M_EXT>(p.R1, p.K, p.invK, y, dy); break;
+        }
+        return;
+    }
     dy[0] = y[3]; dy[1] = y[4]; dy[2] = y[5];
     accel<VAR, MODE, double>(p.R1, p.K, p.invK, y[0], y[1], y[3], y[4], y[5], dy[3], dy[4], dy[5], vm);
 }

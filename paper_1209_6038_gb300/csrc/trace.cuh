@@ -58,7 +58,9 @@ __device__ __forceinline__ bool enter(const Params &p, const double o[3], const 
     }
     mat_in[0] = eo; mat_in[1] = ee; mat_in[2] = c[0]; mat_in[3] = c[1]; mat_in[4] = c[2];
     y[0] = pt[0]; y[1] = pt[1]; y[2] = pt[2];
-    y[3] = v0[0]; y[4] = v0[1]; y[5] = v0[2];
+    // the state's second half: ray velocity (Fermat form) or wave vector (Hamiltonian form)
+    const double *w = p.formulation ? k0 : v0;
+    y[3] = w[0]; y[4] = w[1]; y[5] = w[2];
     return true;
 }
 
@@ -70,7 +72,8 @@ __device__ __forceinline__ void leave(const Params &p, int ev, const double y[6]
     double x[3] = {y[0], y[1], y[2]}, n[3], eo, ee, c[3], k[3];
     face_normal(ev, x, n);
     local_material(p, x, eo, ee, c);
-    wave_from_velocity(MODE, eo, ee, c, y + 3, k);
+    if (p.formulation) set_vec(k, y + 3);
+    else wave_from_velocity(MODE, eo, ee, c, y + 3, k);
     double kn = dot3(k, n), kt[3];
     for (int i = 0; i < 3; ++i) kt[i] = k[i] - kn * n[i];
     double kt2 = dot3(kt, kt);

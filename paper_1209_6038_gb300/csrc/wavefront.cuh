@@ -333,7 +333,8 @@ __device__ __forceinline__ void exit_slot(const Params &p, int mode, const Queue
         double x[3] = {y[0], y[1], y[2]}, nrm[3], eo, ee, c[3], kk[3];
         face_normal(q.face[k], x, nrm);
         local_material(p, x, eo, ee, c);
-        wave_from_velocity(mode, eo, ee, c, y + 3, kk);
+        if (p.formulation) set_vec(kk, y + 3);  // the Hamiltonian state carries the wave vector
+        else wave_from_velocity(mode, eo, ee, c, y + 3, kk);
         double kn = dot3(kk, nrm), kt[3];
         for (int a = 0; a < 3; ++a) kt[a] = kk[a] - kn * nrm[a];
         double kt2 = dot3(kt, kt);
