@@ -161,6 +161,12 @@ int cloak_render_records(cloak_t *h, int polarization, int spp, unsigned long lo
  * xyz; origins outside the cylinder), dev_records is cloak_record[n].  Both device memory. */
 int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long n, void *dev_records,
                      void *cuda_stream);
+/* Right-hand side of the ray equations at n >= 0 states, as the integrators evaluate it.  Fermat form
+ * (default): state (x, v), result (v, dv/dt) of Eq. 8 (extraordinary) or Eq. 2 (ordinary) with the
+ * Eq. 7 matrix of Eq. 14 / 15; Hamiltonian form (cloak_set_formulation): state (x, k), result
+ * (M^-1 k, -1/2 k^T (grad M^-1) k).  dev_y and dev_dy are double[n][6] device memory; states must lie
+ * inside the shell (R1 < r).  Radial and azimuthal handles only (CLOAK_ESTATE otherwise). */
+int cloak_eval_rhs(cloak_t *h, int polarization, const double *dev_y, long n, double *dev_dy, void *cuda_stream);
 
 /* One view of a batched render: medium (CLOAK_RADIAL or CLOAK_AZIMUTHAL, with the handle's R1, R2 and
  * height), traced polarization, pinhole camera (as cloak_camera_set) and its output, a caller-owned

@@ -45,6 +45,7 @@ SIGNATURES = {
     "cloak_render_records": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
     "cloak_trace_rays": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
+    "cloak_eval_rhs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
     "cloak_mlp_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "cloak_render_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p]),
     "cloak_render_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
@@ -177,6 +178,14 @@ def cloak_trace_rays(h, polarization, rays, n, records, stream=None):
         raise CloakError(EINVAL, "buffer too small")
     return _check(load().cloak_trace_rays(h, polarization, C.c_void_p(rays.data_ptr()), n,
                                           C.c_void_p(records.data_ptr()), _stream_ptr(stream)))
+
+
+def cloak_eval_rhs(h, polarization, y, n, dy, stream=None):
+    """y, dy: float64 CUDA tensors of >= 6*n elements (states and their derivatives)."""
+    if y.numel() < 6 * n or dy.numel() < 6 * n:
+        raise CloakError(EINVAL, "buffer too small")
+    return _check(load().cloak_eval_rhs(h, polarization, C.c_void_p(y.data_ptr()), n, C.c_void_p(dy.data_ptr()),
+                                        _stream_ptr(stream)))
 
 
 def cloak_mlp_gemm(a, b, c, stream=None):
@@ -364,6 +373,14 @@ class Cloak:
             out = torch.empty(n * RECORD_BYTES, dtype=torch.uint8, device="cuda")
         cloak_render_records(self.h, polarization, spp, seed, out, stream)
         return out
+
+    def eval_rhs(self, polarization, y, stream=None):
+        """Derivative of each state (rows of y, shape (n, 6)) under the handle's ray equations."""
+        import torch
+        y = y.to(device="cuda", dtype=torch.float64).contiguous()
+        dy = torch.empty_like(y)
+        cloak_eval_rhs(self.h, polarization, y, y.shape[0], dy, stream)
+        return dy
 
     def trace_rays(self, polarization, rays, out=None, stream=None):
         import torch

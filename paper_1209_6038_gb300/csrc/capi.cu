@@ -492,6 +492,24 @@ int cloak_trace_rays(cloak_t *h, int polarization, const double *dev_rays, long 
     return CLOAK_OK;
 }
 
+int cloak_eval_rhs(cloak_t *h, int polarization, const double *dev_y, long n, double *dev_dy, void *cuda_stream) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (polarization != CLOAK_POL_ORDINARY && polarization != CLOAK_POL_EXTRAORDINARY)
+        return fail(CLOAK_EINVAL, "unknown polarization %d", polarization);
+    if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
+        return fail(CLOAK_ESTATE, "the equations of motion are evaluated for the radial and azimuthal cloaks");
+    if (n < 0) return fail(CLOAK_EINVAL, "n must be >= 0");
+    if (n == 0) return CLOAK_OK;
+    if (!dev_y || !dev_dy) return fail(CLOAK_EINVAL, "null buffer");
+    ck::Params p;
+    int rc = make_params(h, p);
+    if (rc) return rc;
+    if ((rc = use_device(h))) return rc;
+    cudaError_t e = ck::launch_eval_rhs(p, polarization, dev_y, n, dev_dy, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rhs launch");
+    return CLOAK_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------------

@@ -71,5 +71,6 @@ inline cudaError_t launch_wavefront(const Params &p, int mode, int spp, unsigned
     return launch_wavefront_v<2>(p, mode, spp, seed, q, samples, recs, packet, st, ev, hook);
 }
 cudaError_t launch_resolve(int npix, int spp, const float4 *samples, float4 *out, cudaStream_t st);
+cudaError_t launch_eval_rhs(const Params &p, int mode, const double *y, long long n, double *dy, cudaStream_t st);
 
 }  // namespace ck

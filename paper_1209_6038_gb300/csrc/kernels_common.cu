@@ -44,6 +44,21 @@ __global__ void k_wf_sort_scatter(Queue q) {
     }
 }
 
+// right-hand side of the ray equations (the handle's formulation) at n states; vm = 2 * variant + mode
+__global__ void k_eval_rhs(Params p, int vm, const double *y, long long n, double *dy) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s[6], d[6];
+    for (int a = 0; a < 6; ++a) s[a] = y[6 * i + a];
+    rhs<V_ANY, V_ANY>(p, s, d, vm);
+    for (int a = 0; a < 6; ++a) dy[6 * i + a] = d[a];
+}
+
+cudaError_t launch_eval_rhs(const Params &p, int mode, const double *y, long long n, double *dy, cudaStream_t st) {
+    k_eval_rhs<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(p, 2 * p.variant + mode, y, n, dy);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_resolve(int npix, int spp, const float4 *samples, float4 *out, cudaStream_t st) {
     k_wf_resolve<<<(npix + 255) / 256, 256, 0, st>>>(npix, spp, samples, out);
     return cudaGetLastError();

@@ -25,6 +25,30 @@
 
 namespace ck {
 
+// ------------------------------------------------------------------ FP64 reciprocal and 1/sqrt
+// The equations of motion need one 1/sqrt and one reciprocal per evaluation.  On a part with few FP64
+// units per SM these are formed from the coarse hardware approximations (PTX rcp.approx.ftz.f64 and
+// rsqrt.approx.ftz.f64, relative error near 2^-20 or better) and one third-order Newton-Raphson step each,
+// which leaves a relative error of a few 2^-53 (checked against the IEEE operations in the tests).
+//   1/a:         e = 1 - a y0,    1/a = y0 / (1 - e) ~ y0 (1 + e + e^2)
+//   1/sqrt(a):   e = 1 - a y0^2,  a^(-1/2) = y0 (1 - e)^(-1/2) ~ y0 (1 + e/2 + 3 e^2 / 8)
+// Inputs are positive normal numbers here (r^2 and r - R1 inside the shell); a zero or negative input
+// gives inf or NaN, which the step control rejects like the IEEE forms would.
+__device__ __forceinline__ double rcp_nr(double a) {
+    double y0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(a));
+    const double e = fma(-a, y0, 1.0);
+    return fma(y0, fma(e, e, e), y0);
+}
+__device__ __forceinline__ double rsqrt_nr(double a) {
+    double y0;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(a));
+    const double e = fma(-a * y0, y0, 1.0);
+    return fma(y0 * e, fma(e, 0.375, 0.5), y0);
+}
+__device__ __forceinline__ float rcp_nr(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ float rsqrt_nr(float a) { return rsqrtf(a); }
+
 enum { V_RADIAL = 0, V_AZIMUTHAL = 1, V_TEST = 2 };
 enum { M_ORD = 0, M_EXT = 1 };
 enum { I_RK4 = 0, I_DP45 = 1 };
@@ -101,13 +125,13 @@ __device__ __forceinline__ void accel_fixed(T R1, T K, T invK, T x, T y, T vx, T
         return;
     }
     T r2 = x * x + y * y;
-    T ir = rsqrt(r2);
+    T ir = rsqrt_nr(r2);
     T r = r2 * ir;
     T cx = x * ir, cy = y * ir;
     T vr = vx * cx + vy * cy;
     T vt = vy * cx - vx * cy;
     T u = r - R1;
-    T g = T(2) * R1 * ir / u;  // f'/f
+    T g = T(2) * R1 * ir * rcp_nr(u);  // f'/f
     T ar, at, azz;
     if (MODE == M_EXT) {
         T q = u * ir;
@@ -162,10 +186,10 @@ __device__ __forceinline__ void ham_fixed(double R1, double K, double invK, cons
         return;
     }
     const double r2 = y[0] * y[0] + y[1] * y[1];
-    const double ir = rsqrt(r2), r = r2 * ir;
+    const double ir = rsqrt_nr(r2), r = r2 * ir;
     const double cx = y[0] * ir, cy = y[1] * ir;
     const double kr = kx * cx + ky * cy, kt = ky * cx - kx * cy;
-    const double u = r - R1, iu = 1.0 / u;
+    const double u = r - R1, iu = rcp_nr(u);
     const double g = 2.0 * R1 * ir * iu;        // f'/f
     const double invf = invK * r2 * iu * iu;    // 1/f = r^2 / (K u^2)
     double vr, vt, vz, dkr, dkt;
