@@ -48,12 +48,12 @@ def _measured_peaks():
 BF16_PEAK_TFLOPS = float(_measured_peaks().get("bf16_tflops", 1900.0))
 
 # Algorithmic FP64 flops per integrator step attempt, counted from the source formulas
-# (FMA = 2 flops, division and square root = 1 flop each):
-#   RHS of Eq. 8 / Eq. 2 in closed cylindrical form: radial-e 41, azimuthal-e 37,
-#   azimuthal-o 33, radial-o 0 (straight lines, Sect. 4).
+# (FMA = 2 flops, reciprocal and 1/sqrt = 1 flop each):
+#   RHS of Eq. 8 / Eq. 2 in closed cylindrical form: radial-e 36, azimuthal-e 30,
+#   azimuthal-o 34, radial-o 0 (straight lines, Sect. 4).
 #   DP5(4) attempt: 6 new RHS + stage combinations (348) + error norm (30).
 #   RK4 step: 4 RHS + combinations (102).
-RHS_FLOPS = {(0, 0): 0, (0, 1): 41, (1, 0): 33, (1, 1): 37}
+RHS_FLOPS = {(0, 0): 0, (0, 1): 36, (1, 0): 34, (1, 1): 30}
 
 # DRAM bytes (read + write) of one launch of the any-medium integration kernel on the full step: one
 # ncu capture of the same twelve views at 480x270 x 4 spp (81.0 MB read + 52.5 MB written) scaled by

@@ -117,19 +117,18 @@ __device__ __forceinline__ void accel_f32_fixed(float R1, float R1sq_h, float R1
     float u = __fdividef((r2h - R1sq_h) + (r2l - R1sq_l), r + R1);
     float g = __fdividef(2.f * R1 * ir, u);  // f'/f
     float ar, at, azz;
-    if (MODE == M_EXT) {
-        float q = u * ir;
-        float f = K * q * q;
-        float fp = f * g;
-        float vt2 = vt * vt;
-        at = -g * vr * vt;
+    if (MODE == M_EXT) {  // the simplified radial terms of accel_fixed
+        const float gvr = -g * vr;
+        at = gvr * vt;
+        const float R1ir2 = R1 * ir * ir;
         if (VAR == V_RADIAL) {
-            ar = (0.5f * fp * (vt2 + vz * vz) - (K - f) * vt2 * ir) * invK;
-            azz = -g * vr * vz;
+            ar = R1ir2 * ir * (u * vz * vz - r * vt * vt);
+            azz = gvr * vz;
         } else {
-            ar = (0.5f * fp * vt2 - (K - f) * vt2 * ir) * invK;
+            ar = -R1ir2 * vt * vt;
             azz = 0.f;
         }
+        (void)K; (void)invK;
     } else {
         float hg = 0.5f * g;
         ar = hg * (vt * vt + vz * vz - vr * vr);

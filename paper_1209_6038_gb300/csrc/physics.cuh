@@ -134,18 +134,21 @@ __device__ __forceinline__ void accel_fixed(T R1, T K, T invK, T x, T y, T vx, T
     T g = T(2) * R1 * ir * rcp_nr(u);  // f'/f
     T ar, at, azz;
     if (MODE == M_EXT) {
-        T q = u * ir;
-        T f = K * q * q;
-        T fp = f * g;  // f'
-        T vt2 = vt * vt;
-        at = -g * vr * vt;
-        if (VAR == V_RADIAL) {  // M = diag(K, f, f)
-            ar = (T(0.5) * fp * (vt2 + vz * vz) - (K - f) * vt2 * ir) * invK;
-            azz = -g * vr * vz;
-        } else {  // M = diag(K, f, K)
-            ar = (T(0.5) * fp * vt2 - (K - f) * vt2 * ir) * invK;
+        // With f = K u^2 / r^2 and f' = f g the radial term [f'/2 (v_t^2 + G-part) - (K - f) v_t^2 / r] / K
+        // simplifies through 1 - u^2/r^2 = R1 (r + u) / r^2 (u = r - R1):
+        //   radial    (M = diag(K, f, f)):  a_r = R1 (u v_z^2 - r v_t^2) / r^3
+        //   azimuthal (M = diag(K, f, K)):  a_r = -R1 v_t^2 / r^2
+        const T gvr = -g * vr;
+        at = gvr * vt;
+        const T R1ir2 = R1 * ir * ir;
+        if (VAR == V_RADIAL) {
+            ar = R1ir2 * ir * (u * vz * vz - r * vt * vt);
+            azz = gvr * vz;
+        } else {
+            ar = -R1ir2 * vt * vt;
             azz = T(0);
         }
+        (void)K; (void)invK;
     } else {  // azimuthal ordinary: M = f I, Eq. 2 with n = sqrt(f)
         T hg = T(0.5) * g;
         ar = hg * (vt * vt + vz * vz - vr * vr);
