@@ -22,6 +22,7 @@ ORDINARY, EXTRAORDINARY = 0, 1
 RK4, DP45 = 0, 1
 STATUS = {0: "MISSED", 1: "EXITED", 2: "HIT_METAL_EXITED", 3: "NO_TRANSMISSION", 4: "TIR",
           5: "STEP_LIMIT", 6: "SINGULAR", 7: "METAL_CAP"}
+MISSED, EXITED, HIT_METAL_EXITED, NO_TRANSMISSION, TIR, STEP_LIMIT, SINGULAR, METAL_CAP = range(8)
 
 RECORD_DTYPE = np.dtype([("exit_pos", "<f8", 3), ("exit_dir", "<f8", 3), ("tof", "<f8"), ("weight", "<f8"),
                          ("tile_id", "<i4"), ("status", "<i4"), ("steps", "<i4"), ("mode", "<i4")])
@@ -82,6 +83,10 @@ def lib():
         L.orc_render.argtypes = [C.POINTER(_Cloak), C.POINTER(_Integ), C.POINTER(_Camera), C.c_int, C.c_int,
                                  C.c_uint64, C.POINTER(C.c_int64), C.c_long, dp, C.c_void_p, C.c_int]
         L.orc_rhs_hamiltonian.argtypes = [C.POINTER(_Cloak), C.c_int, dp, dp]
+        L.orc_room_distance.restype = C.c_double
+        L.orc_room_distance.argtypes = [C.POINTER(_Cloak), dp, dp]
+        L.orc_tof_difference.restype = C.c_double
+        L.orc_tof_difference.argtypes = [C.POINTER(_Cloak), dp, dp, C.c_void_p]
         # surrogate (surrogate_oracle.h)
         ip = C.POINTER(C.c_int)
         L.orc_gelu.restype = C.c_double
@@ -328,6 +333,45 @@ def render(cloak: Cloak, integ: Integrator, cam: Camera, mode, spp=1, seed=0, pi
     lib().orc_render(cloak.ref, integ.ref, cam.ref, mode, spp, seed, pix_ptr, npix, _dp(rgba),
                      recs.ctypes.data_as(C.c_void_p) if records else None, nthreads or os.cpu_count() or 1)
     return rgba, recs
+
+
+def room_distance(cloak: Cloak, p, d) -> float:
+    return lib().orc_room_distance(cloak.ref, _dp(_vec(p)), _dp(_vec(d)))
+
+
+def tof_difference(cloak: Cloak, o, d, rec) -> float:
+    """Time of flight of the light one camera sample receives minus the time without the cylinder."""
+    r = np.array(rec, dtype=RECORD_DTYPE).reshape(1)
+    return lib().orc_tof_difference(cloak.ref, _dp(_vec(o)), _dp(_vec(d)), r.ctypes.data_as(C.c_void_p))
+
+
+def tof_image(cloak: Cloak, integ: Integrator, cam: Camera, spp=1, seed=0, pixels=None, nthreads=None):
+    """Time-of-flight difference image (Sect. 5; the TOF images of Ref. [10]), per pixel:
+    (0) intensity-weighted mean TOF difference of the light of both polarizations, (1) of the ordinary
+    and (2) of the extraordinary light alone, (3) the summed weight (mean over samples).  A sample that
+    never enters the shell (it misses the cylinder or mirrors off a metal end disc) is the same light in
+    both polarizations and counts once in (0) and (3).  The weights include the camera polariser
+    (cloak analyzer) when one is set; a pixel without light gets 0."""
+    _, ro = render(cloak, integ, cam, ORDINARY, spp, seed, pixels, nthreads)
+    _, re = render(cloak, integ, cam, EXTRAORDINARY, spp, seed, pixels, nthreads)
+    idx = np.arange(cam.width * cam.height) if pixels is None else np.asarray(pixels)
+    out = np.zeros((len(idx), 4))
+    for n, pix in enumerate(idx):
+        i, j = int(pix) % cam.width, int(pix) // cam.width
+        A = W = Ao = Wo = Ae = We = 0.0
+        for s in range(spp):
+            o, d = camera_ray(cam, i, j, s, spp, seed)
+            a, b = ro[n * spp + s], re[n * spp + s]
+            dto, dte = tof_difference(cloak, o, d, a), tof_difference(cloak, o, d, b)
+            enters = a["status"] not in (MISSED, METAL_CAP)
+            Ao += a["weight"] * dto
+            Wo += a["weight"]
+            Ae += b["weight"] * dte
+            We += b["weight"]
+            A += a["weight"] * dto + (b["weight"] * dte if enters else 0.0)
+            W += a["weight"] + (b["weight"] if enters else 0.0)
+        out[n] = (A / W if W > 0 else 0.0, Ao / Wo if Wo > 0 else 0.0, Ae / We if We > 0 else 0.0, W / spp)
+    return out
 
 
 # ------------------------------------------------------------------ learned surrogate (surrogate_oracle.h)

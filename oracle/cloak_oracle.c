@@ -730,6 +730,44 @@ int orc_shade(const orc_cloak *c, const double p[3], const double d[3], double r
 }
 
 /* ------------------------------------------------------------------ */
+/* time-of-flight difference (Sect. 5; TOF images of Ref. [10])         */
+/* ------------------------------------------------------------------ */
+double orc_room_distance(const orc_cloak *c, const double p[3], const double d[3]) {
+    /* nearest of the six planes of the room box that the ray moves towards */
+    const double L = 10.0, z0 = -0.5 * c->H, z1 = z0 + 10.0;
+    double best = INFINITY;
+    const double lo[3] = {-L, -L, z0}, hi[3] = {L, L, z1};
+    for (int a = 0; a < 3; ++a) {
+        double s = INFINITY;
+        if (d[a] > 0.0) s = (hi[a] - p[a]) / d[a];
+        else if (d[a] < 0.0) s = (lo[a] - p[a]) / d[a];
+        if (s < best) best = s;
+    }
+    return best;
+}
+
+static double dist3(const double a[3], const double b[3]) {
+    return sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
+}
+
+double orc_tof_difference(const orc_cloak *c, const double o[3], const double d[3], const orc_record *rec) {
+    /* with c0 = 1 a time of flight is a vacuum path length, plus the time t spent inside the cloak */
+    const double t_ref = orc_room_distance(c, o, d);
+    double t;
+    if (rec->status == ORC_METAL_CAP) {
+        t = dist3(rec->exit_pos, o) + orc_room_distance(c, rec->exit_pos, rec->exit_dir);
+    } else if (rec->status == ORC_EXITED || rec->status == ORC_HIT_METAL_EXITED) {
+        double p[3], n[3];
+        int face;
+        if (!hit_cylinder(c, o, d, p, n, &face)) return 0.0;
+        t = dist3(p, o) + rec->tof + orc_room_distance(c, rec->exit_pos, rec->exit_dir);
+    } else {
+        return 0.0;
+    }
+    return t - t_ref;
+}
+
+/* ------------------------------------------------------------------ */
 /* one ray: entry split, integration, exit refraction, shading          */
 /* ------------------------------------------------------------------ */
 static void path_push(double *path, long cap, long *len, double t, const double y[6]) {
