@@ -227,11 +227,21 @@ int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsigned long lo
  *                            render (radial or azimuthal handle; the handle's integrator and precision).
  * The paper's images show the cylinder axis horizontal, here it is vertical (+z): its "vertical" goggles
  * (d), across the cylinder axis, are CLOAK_PANEL_POLARIZER_RIGHT at elevation 0; its "horizontal" ones (e)
- * are CLOAK_PANEL_POLARIZER_UP. */
+ * are CLOAK_PANEL_POLARIZER_UP.
+ *   CLOAK_PANEL_TOF          time-of-flight difference image (Sect. 5, the TOF images of its Ref. [10]):
+ *                            per sample, the time (c0 = 1: vacuum path lengths plus the time of flight
+ *                            inside the cloak) the light takes from the room point the sample sees to the
+ *                            camera, minus the time from the room point the straight camera ray sees
+ *                            without the cylinder.  Per pixel float4: x = intensity-weighted mean over
+ *                            the samples of both polarizations (a ray that never enters the shell counted
+ *                            once), y = of the ordinary and z = of the extraordinary light alone,
+ *                            w = summed weight (mean over samples); 0 where no light arrives.  The
+ *                            weights include the handle's camera polariser (cloak_set_analyzer). */
 enum {
     CLOAK_PANEL_ROOM = 0, CLOAK_PANEL_METAL = 1, CLOAK_PANEL_UNPOLARIZED = 2,
     CLOAK_PANEL_POLARIZER_RIGHT = 3, /* (d): as (c) seen through a linear polariser along the camera's right vector */
-    CLOAK_PANEL_POLARIZER_UP = 4     /* (e): ... along the camera's up vector */
+    CLOAK_PANEL_POLARIZER_UP = 4,    /* (e): ... along the camera's up vector */
+    CLOAK_PANEL_TOF = 5              /* time-of-flight difference image (see above) */
 };
 int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long long seed, void *dev_rgba, size_t bytes,
                        void *cuda_stream);

@@ -216,7 +216,7 @@ def cloak_render_noalloc(h, polarization, spp, seed, rgba, stream=None):
 
 
 # ------------------------------------------------------------------ panels of the paper's figures
-PANEL_ROOM, PANEL_METAL, PANEL_UNPOLARIZED, PANEL_POLARIZER_RIGHT, PANEL_POLARIZER_UP = 0, 1, 2, 3, 4
+PANEL_ROOM, PANEL_METAL, PANEL_UNPOLARIZED, PANEL_POLARIZER_RIGHT, PANEL_POLARIZER_UP, PANEL_TOF = 0, 1, 2, 3, 4, 5
 ANALYZER_NONE, ANALYZER_RIGHT, ANALYZER_UP = 0, 1, 2
 FORM_FERMAT, FORM_HAMILTONIAN = 0, 1
 
@@ -359,7 +359,7 @@ class Cloak:
         return self
 
     def panel(self, panel, spp=1, seed=0, out=None, stream=None):
-        """One panel of the paper's figures (PANEL_ROOM, PANEL_METAL, PANEL_UNPOLARIZED)."""
+        """One panel of the paper's figures (PANEL_*; PANEL_TOF: time-of-flight difference image)."""
         import torch
         if out is None:
             out = torch.empty((self.height, self.width, 4), dtype=torch.float32, device="cuda")

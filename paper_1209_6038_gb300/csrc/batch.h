@@ -27,6 +27,8 @@ cudaError_t launch_batch(const Params &p, const ViewDev *views, int nviews, int 
 
 // unpolarised image of views 0 (ordinary) and 1 (extraordinary) of the last batch: samples as carved
 // for that batch, views: its device table
+cudaError_t launch_tof_resolve(const Params &p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
+                               const float4 *samples, float4 *out, cudaStream_t st);
 cudaError_t launch_unpol_resolve(const Params &p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
                                  const float4 *samples, float4 *out, cudaStream_t st);
 // reference panels without the cloak: 0 the room alone, 1 the bare metal cylinder (radius R1, height H)

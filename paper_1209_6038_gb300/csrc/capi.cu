@@ -558,7 +558,7 @@ static unsigned long long fnv1a(unsigned long long hsh, const void *data, size_t
 // The batched render (views validated, device table, graph capture or replay); samples_out (nullable)
 // receives the per-sample buffer of the batch.
 static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
-                      void *cuda_stream, float4 **samples_out, int analyzer);
+                      void *cuda_stream, float4 **samples_out, int analyzer, int tof = 0);
 
 extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
                                   void *cuda_stream) {
@@ -566,7 +566,7 @@ extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nview
 }
 
 static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
-                      void *cuda_stream, float4 **samples_out, int analyzer) {
+                      void *cuda_stream, float4 **samples_out, int analyzer, int tof) {
     if (!h) return fail(CLOAK_EINVAL, "null handle");
     if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
         return fail(CLOAK_ESTATE, "batched rendering needs a radial or azimuthal cloak handle");
@@ -578,6 +578,7 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
     int rc = make_params(h, p);
     if (rc) return rc;
     p.analyzer = analyzer;
+    p.tof = tof;
     std::vector<ck::ViewDev> table((size_t)nviews);
     long long total = 0, total_pix = 0;
     for (int i = 0; i < nviews; ++i) {
@@ -668,7 +669,7 @@ extern "C" int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long 
                                   size_t bytes, void *cuda_stream) {
     if (!h) return fail(CLOAK_EINVAL, "null handle");
     if (panel != CLOAK_PANEL_ROOM && panel != CLOAK_PANEL_METAL && panel != CLOAK_PANEL_UNPOLARIZED &&
-        panel != CLOAK_PANEL_POLARIZER_RIGHT && panel != CLOAK_PANEL_POLARIZER_UP)
+        panel != CLOAK_PANEL_POLARIZER_RIGHT && panel != CLOAK_PANEL_POLARIZER_UP && panel != CLOAK_PANEL_TOF)
         return fail(CLOAK_EINVAL, "unknown panel %d", panel);
     if (spp < 1 || spp > 65536) return fail(CLOAK_EINVAL, "spp must be in [1, 65536]");
     const size_t npix = (size_t)h->W * h->Hp;
@@ -683,12 +684,18 @@ extern "C" int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long 
         cudaError_t e = ck::launch_panel(p, panel, spp, seed, (float4 *)dev_rgba, st);
         return e == cudaSuccess ? CLOAK_OK : cuda_fail(e, "panel launch");
     }
+    // the TOF image keeps the handle's own camera polariser
     const int analyzer = panel == CLOAK_PANEL_POLARIZER_RIGHT ? CLOAK_ANALYZER_RIGHT
                          : panel == CLOAK_PANEL_POLARIZER_UP  ? CLOAK_ANALYZER_UP
+                         : panel == CLOAK_PANEL_TOF           ? h->analyzer
                                                               : CLOAK_ANALYZER_NONE;
+    const int tof = panel == CLOAK_PANEL_TOF ? 1 : 0;
     p.analyzer = analyzer;
+    p.tof = tof;
     if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
-        return fail(CLOAK_ESTATE, "the unpolarised panel needs a radial or azimuthal cloak handle");
+        return fail(CLOAK_ESTATE, "the unpolarised and TOF panels need a radial or azimuthal cloak handle");
+    if (h->precision == CLOAK_SURROGATE)
+        return fail(CLOAK_EINVAL, "the panels run the integrator: set the FP64 or mixed precision");
     // both polarisations in one batched render (their images go to handle scratch), then the sum
     if (h->panel_bytes < 2 * npix * 16) {
         if (h->panel_img) cudaFree(h->panel_img);
@@ -713,10 +720,12 @@ extern "C" int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long 
         v[m].dev_rgba = (char *)h->panel_img + m * npix * 16;
     }
     float4 *samples = nullptr;
-    if ((rc = batch_core(h, v, 2, spp, seed, cuda_stream, &samples, analyzer))) return rc;
-    cudaError_t e = ck::launch_unpol_resolve(p, (const ck::ViewDev *)h->batch_dev, spp, seed, (long long)npix, samples,
-                                             (float4 *)dev_rgba, st);
-    return e == cudaSuccess ? CLOAK_OK : cuda_fail(e, "unpolarised resolve");
+    if ((rc = batch_core(h, v, 2, spp, seed, cuda_stream, &samples, analyzer, tof))) return rc;
+    cudaError_t e = tof ? ck::launch_tof_resolve(p, (const ck::ViewDev *)h->batch_dev, spp, seed, (long long)npix,
+                                                 samples, (float4 *)dev_rgba, st)
+                        : ck::launch_unpol_resolve(p, (const ck::ViewDev *)h->batch_dev, spp, seed, (long long)npix,
+                                                   samples, (float4 *)dev_rgba, st);
+    return e == cudaSuccess ? CLOAK_OK : cuda_fail(e, tof ? "TOF resolve" : "unpolarised resolve");
 }
 
 // ---------------------------------------------------------------------------------------------

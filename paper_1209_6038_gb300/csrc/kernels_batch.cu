@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(128) k_batch_entry(Params p, const ViewDev *vi
     bool inside = mode ? enter<M_EXT>(pv, o, d, rec, rgb, y, k0, n_in, mat)
                        : enter<M_ORD>(pv, o, d, rec, rgb, y, k0, n_in, mat);
     if (!inside) {
-        store_sample(samples, nullptr, g, rec, rgb);
+        if (p.tof) store_tof_sample(pv, samples, g, o, d, rec);
+        else store_sample(samples, nullptr, g, rec, rgb);
         return;
     }
     double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
@@ -85,7 +86,8 @@ __global__ void __launch_bounds__(128) k_batch_exit(Params p, const ViewDev *vie
         cloak_record rec;
         float rgb[3];
         exit_slot(pv, vm & 1, q, k, d, rec, rgb);
-        store_sample(samples, nullptr, g, rec, rgb);
+        if (p.tof) store_tof_sample(pv, samples, g, o, d, rec);
+        else store_sample(samples, nullptr, g, rec, rgb);
     }
 }
 
@@ -131,6 +133,38 @@ __global__ void k_unpol_resolve(Params p, const ViewDev *views, int spp, unsigne
     }
     const float inv = 1.0f / spp;
     out[g] = make_float4(a0 * inv, a1 * inv, a2 * inv, a3 * inv);
+}
+
+// Time-of-flight difference image (Sect. 5 after Ref. [10]) from the TOF samples (w dt, w) of views 0
+// (ordinary) and 1 (extraordinary) of one camera, per pixel: (0) intensity-weighted mean TOF difference
+// of both polarizations, a ray that never enters the shell counting once; (1) of the ordinary and (2) of
+// the extraordinary light alone; (3) the summed weight, mean over samples.  0 where no light arrives.
+__global__ void k_tof_resolve(Params p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
+                              const float4 *samples, float4 *out) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npix) return;
+    const ViewDev &v0 = views[0];
+    const int i = (int)(g % v0.W), j = (int)(g / v0.W);
+    const float4 *so = samples + views[0].ray_begin + g * spp, *se = samples + views[1].ray_begin + g * spp;
+    double A = 0, W = 0, Ao = 0, Wo = 0, Ae = 0, We = 0;
+    for (int s = 0; s < spp; ++s) {
+        double o[3], d[3], pt[3], n[3];
+        view_camera_ray(v0, i, j, s, spp, seed, o, d);
+        const int face = cylinder_entry(p, o, d, pt, n);
+        const bool enters = face >= 0 && !(face != EV_LAT && p.R1 > 0.0 && hypot(pt[0], pt[1]) <= p.R1);
+        const float4 a = so[s], b = se[s];
+        Ao += a.x; Wo += a.y; Ae += b.x; We += b.y;
+        A += a.x + (enters ? b.x : 0.f);
+        W += a.y + (enters ? b.y : 0.f);
+    }
+    out[g] = make_float4(W > 0 ? (float)(A / W) : 0.f, Wo > 0 ? (float)(Ao / Wo) : 0.f, We > 0 ? (float)(Ae / We) : 0.f,
+                         (float)(W / spp));
+}
+
+cudaError_t launch_tof_resolve(const Params &p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
+                               const float4 *samples, float4 *out, cudaStream_t st) {
+    k_tof_resolve<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(p, views, spp, seed, npix, samples, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_unpol_resolve(const Params &p, const ViewDev *views, int spp, unsigned long long seed, long long npix,

@@ -70,6 +70,9 @@ struct Params {
     int analyzer;
     // ray equations: 0 Fermat form (Eq. 2 / Eq. 8, state (x, v)); 1 Hamiltonian form (state (x, k), k = M v)
     int formulation;
+    // per-sample output of the batched render: 0 colour (w r, w g, w b, w); 1 time-of-flight difference
+    // (w dt, w, 0, 0) for the TOF difference images
+    int tof;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -767,16 +770,23 @@ __device__ __forceinline__ const double *analyzer_axis(const Params &p) {
 // ------------------------------------------------------------------ room and camera
 // Procedural room: box x, y in [-10, 10], z in [-H/2, -H/2 + 10]; checkered walls and floor with
 // 8 tiles per unit and splitmix64-hashed tints; constant ceiling.  Returns the tile id.
-__device__ __forceinline__ int room_hit(const Params &p, const double o[3], const double d[3], float rgb[3]) {
+// Distance along the unit direction d from o to the room's box and the face reached (-1: none).
+__device__ __forceinline__ double room_distance(const Params &p, const double o[3], const double d[3], int &face) {
     const double Lb = 10.0, z0 = -p.halfH, z1 = z0 + 10.0;
     double best = 1e300, s;
-    int face = -1;
+    face = -1;
     if (d[0] > 0.0) { s = (Lb - o[0]) / d[0]; if (s < best) { best = s; face = 0; } }
     else if (d[0] < 0.0) { s = (-Lb - o[0]) / d[0]; if (s < best) { best = s; face = 1; } }
     if (d[1] > 0.0) { s = (Lb - o[1]) / d[1]; if (s < best) { best = s; face = 2; } }
     else if (d[1] < 0.0) { s = (-Lb - o[1]) / d[1]; if (s < best) { best = s; face = 3; } }
     if (d[2] < 0.0) { s = (z0 - o[2]) / d[2]; if (s < best) { best = s; face = 4; } }
     else if (d[2] > 0.0) { s = (z1 - o[2]) / d[2]; if (s < best) { best = s; face = 5; } }
+    return best;
+}
+__device__ __forceinline__ int room_hit(const Params &p, const double o[3], const double d[3], float rgb[3]) {
+    const double Lb = 10.0, z0 = -p.halfH;
+    int face;
+    const double best = room_distance(p, o, d, face);
     if (face < 0) { rgb[0] = rgb[1] = rgb[2] = 0.f; return -1; }
     if (face == 5) { rgb[0] = 0.55f; rgb[1] = 0.55f; rgb[2] = 0.6f; return 5 << 20; }
     double qx = o[0] + best * d[0], qy = o[1] + best * d[1], qz = o[2] + best * d[2];

@@ -13,6 +13,30 @@ __device__ __forceinline__ void set_vec(double *dst, const double *src) {
     dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
 }
 
+// Time-of-flight difference of one camera sample (TOF images, Sect. 5 after Ref. [10]); c0 = 1, so a time
+// of flight is a vacuum path length plus the time t spent inside the cloak.  The light the sample
+// receives travels from the room point its final vacuum ray reaches, back along that ray, through the
+// cloak and to the camera; subtracted is the time from the room point the straight camera ray reaches.
+// Rays that miss the cylinder give 0, as do records that carry no light.
+__device__ __forceinline__ double tof_difference(const Params &p, const double o[3], const double d[3],
+                                                 const cloak_record &rec) {
+    int face;
+    const double t_ref = room_distance(p, o, d, face);
+    double t, pt[3], n[3];
+    if (rec.status == CLOAK_RAY_METAL_CAP) {
+        for (int i = 0; i < 3; ++i) pt[i] = rec.exit_pos[i];
+        t = 0.0;
+    } else if (rec.status == CLOAK_RAY_EXITED || rec.status == CLOAK_RAY_HIT_METAL_EXITED) {
+        if (cylinder_entry(p, o, d, pt, n) < 0) return 0.0;
+        t = rec.tof;
+    } else {
+        return 0.0;
+    }
+    const double dx = pt[0] - o[0], dy = pt[1] - o[1], dz = pt[2] - o[2];
+    t += sqrt(dx * dx + dy * dy + dz * dz) + room_distance(p, rec.exit_pos, rec.exit_dir, face);
+    return t - t_ref;
+}
+
 // Entry part: returns true when the ray continues into the medium with state y (x, v).
 // Otherwise rec and rgb are final.
 template <int MODE>

@@ -86,6 +86,13 @@ __device__ __forceinline__ void store_sample(float4 *samples, cloak_record *recs
     if (recs) recs[id] = rec;
 }
 
+// Per-sample output of a TOF difference render (Params::tof): (w dt, w, 0, 0).
+__device__ __forceinline__ void store_tof_sample(const Params &p, float4 *samples, long long id, const double o[3],
+                                                 const double d[3], const cloak_record &rec) {
+    const double w = rec.weight;
+    samples[id] = make_float4((float)(w * tof_difference(p, o, d, rec)), (float)w, 0.f, 0.f);
+}
+
 // Append an entering ray to the queue; one atomic per warp for the slot and one per distinct key.
 __device__ __forceinline__ void queue_append(const Queue &q, const double y[6], double w_out, int id, int key) {
     const unsigned int act = __activemask();
