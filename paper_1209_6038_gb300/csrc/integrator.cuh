@@ -49,6 +49,11 @@ struct Stepper64 {
     __device__ __forceinline__ double chord(const Params &p) const { return metal_chord(y[0], y[1], y1[0], y1[1], p.R1sq); }
     __device__ __forceinline__ double g_start(const Params &p, int ev) const { return event_g(p, ev, y); }
     __device__ __forceinline__ double g_end(const Params &p, int ev) const { return event_g(p, ev, y1); }
+    // d/ds of the event function at the end of the last trial step of size s, with the end point's
+    // derivative taken as the flow's, f(y1) = k7 (position part): the Newton slope of the crossing search
+    __device__ __forceinline__ double g_rate(int ev) const { return event_dg(ev, y1, k7); }
+    // the same at the start of the step, from k1 = f(y)
+    __device__ __forceinline__ double g_rate_start(int ev) const { return event_dg(ev, y, k1); }
     __device__ __forceinline__ void take_step() {
 #pragma unroll
         for (int i = 0; i < 6; ++i) y[i] = y1[i];

@@ -353,6 +353,15 @@ __device__ __forceinline__ T metal_chord(T x0, T y0, T x1, T y1, T R1sq) {
 enum { EV_LAT = 0, EV_TOP = 1, EV_BOT = 2, EV_METAL = 3 };
 // Event functions: positive once the surface has been crossed.  The radial surfaces use r^2 - R^2,
 // which has the same roots and signs as r - R and needs no square root.
+// Rate of change of the event function along a motion dx of the position x: grad g(x) . dx.
+__device__ __forceinline__ double event_dg(int ev, const double x[3], const double dx[3]) {
+    switch (ev) {
+    case EV_LAT: return 2.0 * fma(x[0], dx[0], x[1] * dx[1]);
+    case EV_TOP: return dx[2];
+    case EV_BOT: return -dx[2];
+    default: return -2.0 * fma(x[0], dx[0], x[1] * dx[1]);
+    }
+}
 __device__ __forceinline__ double event_g(const Params &p, int ev, const double y[6]) {
     switch (ev) {
     case EV_LAT: return fma(y[0], y[0], y[1] * y[1]) - p.R2sq;

@@ -152,6 +152,11 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     const R tol = (R)p.h_or_tol, h0 = INTEG == I_RK4 ? (R)p.h_or_tol : (R)1e-3;
     const R conv = sizeof(R) == 8 ? (R)CROSS_REL_TOL : (R)2.4e-7;  // bracket resolution of the crossing search
     constexpr int prefix = bisect_prefix<INTEG>();
+    // FP64 DP5(4): when the ray moves towards the surface at both ends of the crossing step (one crossing
+    // inside it), the search takes safeguarded Newton steps on the step function itself, the slope from
+    // the end point's derivative f(y1), starting from a Newton step off the coarse step's end
+    constexpr bool NEWTON = INTEG == I_DP45 && PREC == 0;
+    constexpr double NEWTON_LAST = 1e-6;
     // medium segments of the permutation (batch: one per medium/mode; a lane draws rays from its
     // warp's current segment, so that the lanes of a warp evaluate one medium's equations)
     int seg = VAR == V_ANY ? 3 - (int)(((blockIdx.x * blockDim.x + threadIdx.x) >> 5) & 3) : 0;
@@ -162,6 +167,8 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     // crossing state
     R hs = 0, fac = 1, lo = 0, hi = 0, glo = 0, ghi = 0, sbest = 0, g1[4];
     int ev = 0, evbest = -1, side = 0, it = 0;
+    bool newton = false, fin = false;
+    R snext = 0;
     unsigned int pending = 0;
     bool drained = false;  // the queue had no ray left for this lane
 
@@ -205,13 +212,16 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
         if (phase == PH_STEP && (steps >= p.max_steps || (INTEG == I_DP45 && h < (R)1e-14))) status = CLOAK_RAY_STEP_LIMIT;
         R s = phase == PH_STEP ? h : sbest;
         if (phase == PH_CROSS) {
-            // next trial point: bisection prefix, then Illinois regula falsi (see crossing())
-            if (it < prefix) s = (R)0.5 * (lo + hi);
+            // next trial point: Newton (see above), or a bisection prefix, then Illinois regula falsi
+            // (see crossing())
+            if (newton) s = snext;
+            else if (it < prefix) s = (R)0.5 * (lo + hi);
             else if (it - prefix < 60 && ghi > glo) s = (lo * ghi - hi * glo) / (ghi - glo);
             else s = (R)0.5 * (lo + hi);
             if (!(s > lo && s < hi)) s = (R)0.5 * (lo + hi);
         }
         __syncwarp(lm);  // a convergence point: keeps the compiler from splitting the evaluation by phase
+        bool land = false;
         if (status < 0) {
             st.eval(p, s);
             if (phase == PH_STEP) {
@@ -247,6 +257,18 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                         lo = 0; hi = hs; glo = st.g_start(p, ev); ghi = g1[ev];
                         if (!(glo <= (R)0)) glo = 0;
                         side = 0; it = 0;
+                        newton = false;
+                        fin = false;
+                        if constexpr (NEWTON) {
+                            const R d0 = (R)st.g_rate_start(ev), d1 = (R)st.g_rate(ev);
+                            if (d0 >= (R)0 && d1 > (R)0) {
+                                newton = true;
+                                R s0 = hs - ghi / d1;
+                                if (!(s0 > (R)0 && s0 < hs)) s0 = hs * (-glo / (ghi - glo));
+                                if (!(s0 > (R)0 && s0 < hs)) s0 = (R)0.5 * hs;
+                                snext = s0;
+                            }
+                        }
                         phase = PH_CROSS;
                     }
                 }
@@ -254,6 +276,27 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                 bool done = false;
                 if (!(s > lo && s < hi)) {
                     done = true;
+                } else if (NEWTON && newton) {
+                    // safeguarded Newton: keep the bracket, bisect when the step would leave it
+                    const R gs = st.g_end(p, ev);
+                    if (gs > (R)0) { hi = s; ghi = gs; } else { lo = s; glo = gs; }
+                    ++it;
+                    const R gtol = (R)CROSS_G_TOL * (R)cross_g_scale(p, ev);
+                    if (fin || fabs(gs) <= gtol) {
+                        // on the surface to rounding, or the trial point of a Newton correction below
+                        // NEWTON_LAST x the step: quadratic convergence put it within ~1e-12 of the step
+                        lo = s;
+                        hi = s;
+                        done = true;
+                    } else {
+                        R dg = (R)1;
+                        if constexpr (NEWTON) dg = (R)st.g_rate(ev);
+                        R sn = s - gs / dg;
+                        if (!(sn > lo && sn < hi)) sn = (R)0.5 * (lo + hi);
+                        else if (fabs(sn - s) <= (R)NEWTON_LAST * hs) fin = true;
+                        snext = sn;
+                        if (hi - lo <= conv * hi || it >= 100) done = true;
+                    }
                 } else {
                     R gs = st.g_end(p, ev);
                     if (it < prefix) {
@@ -288,11 +331,17 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                         lo = 0; hi = hs; glo = st.g_start(p, ev); ghi = g1[ev];
                         if (!(glo <= (R)0)) glo = 0;
                         side = 0; it = 0;
+                        newton = false;  // the coarse step's end point is gone: bisection for further surfaces
+                    } else if (PREC == 0 && sbest == s && evbest == ev) {
+                        land = true;  // the last trial step ended on the crossing: no re-evaluation
                     } else {
                         phase = PH_FINAL;
                     }
                 }
-            } else {  // PH_FINAL: the evaluation landed on the crossing
+            } else {
+                land = true;  // PH_FINAL: the evaluation landed on the crossing
+            }
+            if (land) {
                 st.take_crossing();
                 t += sbest;
                 h = hs * fac;
