@@ -51,7 +51,8 @@ BF16_PEAK_TFLOPS = float(_measured_peaks().get("bf16_tflops", 1900.0))
 # (FMA = 2 flops, reciprocal and 1/sqrt = 1 flop each):
 #   RHS of Eq. 8 / Eq. 2 in closed cylindrical form: radial-e 36, azimuthal-e 30,
 #   azimuthal-o 34, radial-o 0 (straight lines, Sect. 4).
-#   DP5(4) attempt: 6 new RHS + stage combinations (348) + error norm (30).
+#   DP5(4) attempt: 6 new RHS + stage combinations as FMA chains on h-scaled coefficients (332) + error
+#   norm (30).
 #   RK4 step: 4 RHS + combinations (102).
 RHS_FLOPS = {(0, 0): 0, (0, 1): 36, (1, 0): 34, (1, 1): 30}
 
@@ -59,7 +60,7 @@ RHS_FLOPS = {(0, 0): 0, (0, 1): 36, (1, 0): 34, (1, 1): 30}
 # ncu capture of the same twelve views at 480x270 x 4 spp (81.0 MB read + 52.5 MB written) scaled by
 # samples (x 16.0).  To be re-captured whenever the kernel changes.
 INTEGRATE_TRAFFIC_BYTES = (81.048064e6 + 52.5056e6) * (1920 * 1080) / (480 * 270)
-DP45_FIXED, RK4_FIXED = 378, 102
+DP45_FIXED, RK4_FIXED = 362, 102
 
 
 def flops_per_step(variant, mode, integ):

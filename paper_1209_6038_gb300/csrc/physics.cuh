@@ -283,34 +283,52 @@ struct DP {
 template <int VAR, int MODE>
 __device__ __forceinline__ void dp45_step(const Params &p, const double y[6], const double k1[6], double h,
                                           double out[6], double *err, double *k7, int vm = 0) {
+    // stage points y + sum_l (h a_jl) k_l as FMA chains on the scaled coefficients (one FMA per term)
     double k2[6], k3[6], k4[6], k5[6], k6[6], t[6];
+    {
+        const double c1 = h * DP::a21;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) t[i] = fma(h, DP::a21 * k1[i], y[i]);
+        for (int i = 0; i < 6; ++i) t[i] = fma(c1, k1[i], y[i]);
+    }
     rhs<VAR, MODE>(p, t, k2, vm);
+    {
+        const double c1 = h * DP::a31, c2 = h * DP::a32;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) t[i] = fma(h, DP::a31 * k1[i] + DP::a32 * k2[i], y[i]);
+        for (int i = 0; i < 6; ++i) t[i] = fma(c2, k2[i], fma(c1, k1[i], y[i]));
+    }
     rhs<VAR, MODE>(p, t, k3, vm);
+    {
+        const double c1 = h * DP::a41, c2 = h * DP::a42, c3 = h * DP::a43;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) t[i] = fma(h, DP::a41 * k1[i] + DP::a42 * k2[i] + DP::a43 * k3[i], y[i]);
+        for (int i = 0; i < 6; ++i) t[i] = fma(c3, k3[i], fma(c2, k2[i], fma(c1, k1[i], y[i])));
+    }
     rhs<VAR, MODE>(p, t, k4, vm);
+    {
+        const double c1 = h * DP::a51, c2 = h * DP::a52, c3 = h * DP::a53, c4 = h * DP::a54;
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
-        t[i] = fma(h, DP::a51 * k1[i] + DP::a52 * k2[i] + DP::a53 * k3[i] + DP::a54 * k4[i], y[i]);
+        for (int i = 0; i < 6; ++i) t[i] = fma(c4, k4[i], fma(c3, k3[i], fma(c2, k2[i], fma(c1, k1[i], y[i]))));
+    }
     rhs<VAR, MODE>(p, t, k5, vm);
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-        t[i] = fma(h, DP::a61 * k1[i] + DP::a62 * k2[i] + DP::a63 * k3[i] + DP::a64 * k4[i] + DP::a65 * k5[i],
-                   y[i]);
-    rhs<VAR, MODE>(p, t, k6, vm);
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-        out[i] = fma(h, DP::b1 * k1[i] + DP::b3 * k3[i] + DP::b4 * k4[i] + DP::b5 * k5[i] + DP::b6 * k6[i], y[i]);
-    if (err) {
-        rhs<VAR, MODE>(p, out, k7, vm);
+    {
+        const double c1 = h * DP::a61, c2 = h * DP::a62, c3 = h * DP::a63, c4 = h * DP::a64, c5 = h * DP::a65;
 #pragma unroll
         for (int i = 0; i < 6; ++i)
-            err[i] = h * (DP::e1 * k1[i] + DP::e3 * k3[i] + DP::e4 * k4[i] + DP::e5 * k5[i] + DP::e6 * k6[i] +
-                          DP::e7 * k7[i]);
+            t[i] = fma(c5, k5[i], fma(c4, k4[i], fma(c3, k3[i], fma(c2, k2[i], fma(c1, k1[i], y[i])))));
+    }
+    rhs<VAR, MODE>(p, t, k6, vm);
+    {
+        const double c1 = h * DP::b1, c3 = h * DP::b3, c4 = h * DP::b4, c5 = h * DP::b5, c6 = h * DP::b6;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            out[i] = fma(c6, k6[i], fma(c5, k5[i], fma(c4, k4[i], fma(c3, k3[i], fma(c1, k1[i], y[i])))));
+    }
+    if (err) {
+        rhs<VAR, MODE>(p, out, k7, vm);
+        const double c1 = h * DP::e1, c3 = h * DP::e3, c4 = h * DP::e4, c5 = h * DP::e5, c6 = h * DP::e6,
+                     c7 = h * DP::e7;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            err[i] = fma(c7, k7[i], fma(c6, k6[i], fma(c5, k5[i], fma(c4, k4[i], fma(c3, k3[i], c1 * k1[i])))));
     }
 }
 

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
             // (see crossing())
             if (newton) s = snext;
             else if (it < prefix) s = (R)0.5 * (lo + hi);
-            else if (it - prefix < 60 && ghi > glo) s = (lo * ghi - hi * glo) / (ghi - glo);
+            else if (it - prefix < 60 && ghi > glo) s = (lo * ghi - hi * glo) * rcp_nr(ghi - glo);
             else s = (R)0.5 * (lo + hi);
             if (!(s > lo && s < hi)) s = (R)0.5 * (lo + hi);
         }
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                     } else {
                         R dg = (R)1;
                         if constexpr (NEWTON) dg = (R)st.g_rate(ev);
-                        R sn = s - gs / dg;
+                        R sn = s - gs * rcp_nr(dg);
                         if (!(sn > lo && sn < hi)) sn = (R)0.5 * (lo + hi);
                         else if (fabs(sn - s) <= (R)NEWTON_LAST * hs) fin = true;
                         snext = sn;
