@@ -83,6 +83,9 @@ def lib():
         L.orc_render.argtypes = [C.POINTER(_Cloak), C.POINTER(_Integ), C.POINTER(_Camera), C.c_int, C.c_int,
                                  C.c_uint64, C.POINTER(C.c_int64), C.c_long, dp, C.c_void_p, C.c_int]
         L.orc_rhs_hamiltonian.argtypes = [C.POINTER(_Cloak), C.c_int, dp, dp]
+        L.orc_trace_reflections.restype = C.c_int
+        L.orc_trace_reflections.argtypes = [C.POINTER(_Cloak), C.POINTER(_Integ), C.c_int, dp, dp, C.c_void_p,
+                                            C.c_void_p]
         L.orc_room_distance.restype = C.c_double
         L.orc_room_distance.argtypes = [C.POINTER(_Cloak), dp, dp]
         L.orc_tof_difference.restype = C.c_double
@@ -252,7 +255,7 @@ def transmission_in(cloak: Cloak, x, n, d):
 
 
 def transmission_out(cloak: Cloak, mode, x, n, k):
-    """Eq. 12 medium -> vacuum: (ok, T, R_o, R_e); ok False on total internal reflection."""
+    """Eq. 12 medium -> vacuum: (ok, T, R_o, R_e); under total internal reflection T = 0, R_o + R_e = 1."""
     x, n, k = _vec(x), _vec(n), _vec(k)
     out = np.zeros(4)
     ok = lib().orc_transmission_out(cloak.ref, mode, _dp(x), _dp(n), _dp(k), _dp(out))
@@ -333,6 +336,42 @@ def render(cloak: Cloak, integ: Integrator, cam: Camera, mode, spp=1, seed=0, pi
     lib().orc_render(cloak.ref, integ.ref, cam.ref, mode, spp, seed, pix_ptr, npix, _dp(rgba),
                      recs.ctypes.data_as(C.c_void_p) if records else None, nthreads or os.cpu_count() or 1)
     return rgba, recs
+
+
+def trace_reflections(cloak: Cloak, integ: Integrator, mode, o, d):
+    """First-order reflections of a camera sample traced in `mode`: (vac, refl) records, vac the room light
+    the outer surface reflects into the camera, refl[m'] the light that travelled as mode m' and reflected
+    at the far face into `mode`."""
+    vac = np.zeros(1, dtype=RECORD_DTYPE)
+    refl = np.zeros(2, dtype=RECORD_DTYPE)
+    lib().orc_trace_reflections(cloak.ref, integ.ref, mode, _dp(_vec(o)), _dp(_vec(d)),
+                                vac.ctypes.data_as(C.c_void_p), refl.ctypes.data_as(C.c_void_p))
+    return vac[0], refl
+
+
+def reflections_image(cloak: Cloak, integ: Integrator, cam: Camera, spp=1, seed=0, pixels=None):
+    """Per pixel, the first-order reflections' part of the unpolarised panel (Fig. 1 (c) / 2 (c)): the mean
+    over samples of the outer-surface reflection (once) plus the far-face reflections of both traced modes
+    (each into o and e), weight x room colour; RGB and summed weight."""
+    idx = np.arange(cam.width * cam.height) if pixels is None else np.asarray(pixels)
+    out = np.zeros((len(idx), 4))
+    for n, pix in enumerate(idx):
+        i, j = int(pix) % cam.width, int(pix) // cam.width
+        acc = np.zeros(4)
+        for s in range(spp):
+            o, d = camera_ray(cam, i, j, s, spp, seed)
+            recs = []
+            for mode in (ORDINARY, EXTRAORDINARY):
+                vac, refl = trace_reflections(cloak, integ, mode, o, d)
+                recs += list(refl)
+            recs.append(vac)
+            for r in recs:
+                if r["weight"] > 0.0:
+                    _, rgb = shade(cloak, r["exit_pos"], r["exit_dir"])
+                    acc[:3] += r["weight"] * np.asarray(rgb)
+                    acc[3] += r["weight"]
+        out[n] = acc / spp
+    return out
 
 
 def room_distance(cloak: Cloak, p, d) -> float:

@@ -415,7 +415,19 @@ static void vacuum_basis(const double k[3], const double n[3], double s[3], doub
 /* Eq. 12 at a vacuum -> medium face.  Incident unit vacuum direction d
    (d . n < 0), outward normal n, face point x.  out = {T_o^s, T_o^p, T_e^s,
    T_e^p, R^s, R^p, T_o (unpolarised), T_e (unpolarised)}. */
+static int vacuum_face(const orc_cloak *c, const double x[3], const double n[3], const double d[3], const double *e3,
+                       double out[9]);
 int orc_transmission_in(const orc_cloak *c, const double x[3], const double n[3], const double d[3], double out[8]) {
+    double o9[9];
+    if (!vacuum_face(c, x, n, d, NULL, o9)) return 0;
+    for (int i = 0; i < 8; ++i) out[i] = o9[i];
+    return 1;
+}
+
+/* The solve of orc_transmission_in; with e3 (a unit incident polarisation across d) also out[8] = the
+   reflectance of that incident wave. */
+static int vacuum_face(const orc_cloak *c, const double x[3], const double n[3], const double d[3], const double *e3,
+                       double out[9]) {
     double eps[9], eo, ee, ch[3];
     orc_permittivity(c, x, eps, &eo, &ee, ch);
     double dn = dot3(d, n), kt[3], kr[3];
@@ -437,9 +449,10 @@ int orc_transmission_in(const orc_cloak *c, const double x[3], const double n[3]
     cplx Ers[3] = {s[0], s[1], s[2]}, Erp[3] = {pr[0], pr[1], pr[2]}, Hrs[3], Hrp[3];
     ccross3(ckr, Ers, Hrs);
     ccross3(ckr, Erp, Hrp);
-    for (int pol = 0; pol < 2; ++pol) {
+    out[8] = 0.0;
+    for (int pol = 0; pol < (e3 ? 3 : 2); ++pol) {
         cplx Ei[3], Hi[3];
-        for (int i = 0; i < 3; ++i) Ei[i] = pol == 0 ? s[i] : pi[i];
+        for (int i = 0; i < 3; ++i) Ei[i] = pol == 0 ? s[i] : pol == 1 ? pi[i] : e3[i];
         ccross3(cd, Ei, Hi);
         /* tangential continuity of E and H: incident + reflected = transmitted */
         const cplx *cols_E[4] = {Ers, Erp, Eo, Ee}, *cols_H[4] = {Hrs, Hrp, Ho, He};
@@ -462,6 +475,7 @@ int orc_transmission_in(const orc_cloak *c, const double x[3], const double n[3]
         cplx Er[3], Hr[3];
         for (int i = 0; i < 3; ++i) { Er[i] = u[0] * Ers[i] + u[1] * Erp[i]; Hr[i] = u[0] * Hrs[i] + u[1] * Hrp[i]; }
         double R = fabs(normal_flux(n, Er, Hr)) / fi;
+        if (pol == 2) { out[8] = R; break; }
         out[0 + pol] = To;
         out[2 + pol] = Te;
         out[4 + pol] = R;
@@ -473,8 +487,8 @@ int orc_transmission_in(const orc_cloak *c, const double x[3], const double n[3]
 
 /* Eq. 12 at a medium -> vacuum face (Sect. 3, last paragraph): incident
    wave of `mode` with real wave vector k, one refracted vacuum wave and two
-   reflected waves (o and e) in the medium.  out = {T, R_o, R_e, 0}.
-   Returns 0 for total internal reflection (|k_t| > 1). */
+   reflected waves (o and e) in the medium.  out = {T, R_o, R_e, polariser fraction of the transmitted
+   wave}.  Under total internal reflection (|k_t| > 1) T = 0 and R_o + R_e = 1. */
 int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const double n[3], const double k[3],
                          double out[4]) {
     double eps[9], eo, ee, ch[3];
@@ -483,13 +497,21 @@ int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const 
     for (int i = 0; i < 3; ++i) kt[i] = k[i] - kn * n[i];
     double kt2 = dot3(kt, kt);
     out[0] = out[1] = out[2] = out[3] = 0.0;
-    if (kt2 > 1.0) return 0;
-    double kv[3];
-    for (int i = 0; i < 3; ++i) kv[i] = kt[i] + sqrt(1.0 - kt2) * n[i];
-    double s[3], p[3];
-    vacuum_basis(kv, n, s, p);
-    cplx ckv[3] = {kv[0], kv[1], kv[2]};
-    cplx Es[3] = {s[0], s[1], s[2]}, Ep[3] = {p[0], p[1], p[2]}, Hs[3], Hp[3];
+    /* vacuum side: propagating wave, or under total internal reflection (|k_t| > 1) the evanescent wave
+       that decays away from the face (k_n = i sqrt(|k_t|^2 - 1)); it carries no flux */
+    const int tir = kt2 > 1.0;
+    cplx ckv[3];
+    for (int i = 0; i < 3; ++i) ckv[i] = kt[i] + (tir ? I * sqrt(kt2 - 1.0) : sqrt(1.0 - kt2)) * n[i];
+    double s[3];
+    cross3(kt, n, s); /* s perpendicular to the plane of incidence; p = s x k */
+    {
+        double l = norm3(s);
+        if (l < 1e-12) any_perp(n, s);
+        else for (int i = 0; i < 3; ++i) s[i] /= l;
+    }
+    double kv[3] = {creal(ckv[0]), creal(ckv[1]), creal(ckv[2])};
+    cplx Es[3] = {s[0], s[1], s[2]}, Ep[3], Hs[3], Hp[3];
+    ccross3(Es, ckv, Ep);
     ccross3(ckv, Es, Hs);
     ccross3(ckv, Ep, Hp);
     cplx kro[3], kre[3], Ero[3], Hro[3], Ere[3], Hre[3], ck[3] = {k[0], k[1], k[2]}, Em[3], Hm[3];
@@ -520,9 +542,10 @@ int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const 
     double fi = fabs(normal_flux(n, Em, Hm));
     cplx Et[3], Ht[3];
     for (int i = 0; i < 3; ++i) { Et[i] = u[0] * Es[i] + u[1] * Ep[i]; Ht[i] = u[0] * Hs[i] + u[1] * Hp[i]; }
-    out[0] = fabs(normal_flux(n, Et, Ht)) / fi;
+    out[0] = tir ? 0.0 : fabs(normal_flux(n, Et, Ht)) / fi;
     out[1] = cabs(u[2]) * cabs(u[2]) * fabs(normal_flux(n, Ero, Hro)) / fi;
     out[2] = cabs(u[3]) * cabs(u[3]) * fabs(normal_flux(n, Ere, Hre)) / fi;
+    if (tir) return 1; /* nothing reaches the camera-side polariser */
     /* linear polariser in front of the camera: it passes the field component along its axis, taken
        across the transmitted vacuum wave (Malus's law, |E . a|^2 / |E|^2) */
     out[3] = 1.0;
@@ -784,66 +807,24 @@ static void finish_vacuum(const orc_cloak *c, const double p[3], const double d[
     rec->tile_id = orc_shade(c, p, d, rgb);
 }
 
-int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const double o[3], const double d[3],
-                  orc_record *rec, double *path, long path_cap, long *path_len) {
-    memset(rec, 0, sizeof(*rec));
-    rec->mode = mode;
-    rec->tile_id = -1;
-    long plen = 0;
-    if (path_len) *path_len = 0;
-    double p[3], n[3];
-    int face;
-    /* unpolarised room light through a linear polariser: half of it */
-    const double vac = dot3(c->analyzer, c->analyzer) > 0.0 ? 0.5 : 1.0;
-    if (!hit_cylinder(c, o, d, p, n, &face)) {
-        rec->status = ORC_MISSED;
-        rec->weight = vac;
-        finish_vacuum(c, o, d, rec);
-        return rec->status;
-    }
-    if (face != EV_LATERAL && c->R1 > 0.0 && hypot(p[0], p[1]) <= c->R1) {
-        /* metal end disc seen from outside: mirror, reflectance 1 */
-        double dr[3], dn = dot3(d, n);
-        for (int i = 0; i < 3; ++i) dr[i] = d[i] - 2.0 * dn * n[i];
-        rec->status = ORC_METAL_CAP;
-        rec->weight = vac;
-        finish_vacuum(c, p, dr, rec);
-        return rec->status;
-    }
-    /* entry double refraction (Sect. 3) */
-    double dn = dot3(d, n), kt[3], k0[3], v0[3];
-    for (int i = 0; i < 3; ++i) kt[i] = d[i] - dn * n[i];
-    if (!orc_refract_into(c, mode, p, n, kt, k0, v0)) {
-        rec->status = ORC_NO_TRANSMISSION;
-        for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = p[i]; rec->exit_dir[i] = d[i]; }
-        return rec->status;
-    }
-    double x_in[3] = {p[0], p[1], p[2]}, n_in[3] = {n[0], n[1], n[2]};
-    /* state (x, v) of the Fermat form or (x, k) of the Hamiltonian form */
-    double y[6] = {p[0], p[1], p[2], v0[0], v0[1], v0[2]}, y1[6], t = 0.0;
-    if (c->form)
-        for (int i = 0; i < 3; ++i) y[3 + i] = k0[i];
-    path_push(path, path_cap, &plen, t, y);
+/* Integration inside the cloak from state y (Fermat (x, v) or Hamiltonian (x, k)) at time *t until the
+   ray crosses a face: returns ORC_EXITED with y on the crossing and *ev_hit the face, or ORC_STEP_LIMIT /
+   ORC_SINGULAR.  The metal cylinder mirrors radial ordinary rays (*metal set). */
+static int integrate_inside(const orc_cloak *c, const orc_integrator *in, int mode, double y[6], double *t,
+                            int *steps, int *metal, int *ev_hit, double *path, long path_cap, long *plen) {
+    double y1[6];
     double h = in->kind == ORC_RK4 ? in->h_or_tol : 1e-3, tol = in->h_or_tol;
-    int metal = 0, steps = 0;
     const int nev = c->R1 > 0.0 ? 4 : 3;
     for (;;) {
-        if (steps >= in->max_steps || (in->kind == ORC_DP45 && h < 1e-14)) {
-            rec->status = ORC_STEP_LIMIT;
-            rec->steps = steps;
-            for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = y[i]; rec->exit_dir[i] = d[i]; }
-            rec->tof = t;
-            if (path_len) *path_len = plen;
-            return rec->status;
-        }
+        if (*steps >= in->max_steps || (in->kind == ORC_DP45 && h < 1e-14)) return ORC_STEP_LIMIT;
         double fac = 1.0;
         if (in->kind == ORC_RK4) {
             orc_rk4_step(c, mode, y, h, y1);
-            ++steps;
+            ++*steps;
         } else {
             double e[6];
             orc_dp45_step(c, mode, y, h, y1, e);
-            ++steps;
+            ++*steps;
             /* error norm: max_i |e_i| / (tol + tol max(|y_i|, |y1_i|)) */
             double err = 0.0;
             int bad = 0;
@@ -876,77 +857,255 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
             }
         }
         /* surfaces crossed by this step; the earliest crossing wins */
-        int ev_hit = -1;
+        int hit = -1;
         double s_hit = INFINITY;
         for (int ev = 0; ev < nev; ++ev) {
             if (event_value(c, ev, y1) > 0.0) {
-                double s = crossing(c, in, mode, y, h, ev);
-                if (s < s_hit) { s_hit = s; ev_hit = ev; }
+                double sx = crossing(c, in, mode, y, h, ev);
+                if (sx < s_hit) { s_hit = sx; hit = ev; }
             }
         }
-        if (ev_hit < 0) {
+        if (hit < 0) {
             for (int i = 0; i < 6; ++i) y[i] = y1[i];
-            t += h;
+            *t += h;
             h *= fac;
-            path_push(path, path_cap, &plen, t, y);
+            path_push(path, path_cap, plen, *t, y);
             continue;
         }
         step_solution(c, in, mode, y, s_hit, y1);
         for (int i = 0; i < 6; ++i) y[i] = y1[i];
-        t += s_hit;
+        *t += s_hit;
         h *= fac;
-        path_push(path, path_cap, &plen, t, y);
-        if (ev_hit == EV_METAL) {
+        path_push(path, path_cap, plen, *t, y);
+        if (hit == EV_METAL) {
             if (c->variant == ORC_RADIAL && mode == ORC_ORDINARY) {
                 /* Sect. 4: c-hat parallel to the metal normal, single mirror ray with equal angles */
                 double nm[3], r = hypot(y[0], y[1]);
                 nm[0] = y[0] / r; nm[1] = y[1] / r; nm[2] = 0.0;
                 double vn = dot3(y + 3, nm);
                 for (int i = 0; i < 3; ++i) y[3 + i] -= 2.0 * vn * nm[i];
-                metal = 1;
-                path_push(path, path_cap, &plen, t, y);
+                *metal = 1;
+                path_push(path, path_cap, plen, *t, y);
                 continue;
             }
-            rec->status = ORC_SINGULAR;
-            rec->steps = steps;
-            rec->tof = t;
-            for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = y[i]; rec->exit_dir[i] = d[i]; }
-            if (path_len) *path_len = plen;
-            return rec->status;
+            return ORC_SINGULAR;
         }
-        /* exit refraction (Sect. 3): keep k_t, vacuum k_n = +sqrt(1 - |k_t|^2) */
-        double xo[3] = {y[0], y[1], y[2]}, no[3], kx[3], ktx[3];
-        face_normal(ev_hit, xo, no);
-        if (c->form)
-            for (int i = 0; i < 3; ++i) kx[i] = y[3 + i];
-        else
-            wave_vector(c, mode, xo, y + 3, kx);
-        double kn = dot3(kx, no);
-        for (int i = 0; i < 3; ++i) ktx[i] = kx[i] - kn * no[i];
-        double kt2 = dot3(ktx, ktx);
-        rec->steps = steps;
-        rec->tof = t;
-        if (path_len) *path_len = plen;
-        if (kt2 > 1.0) {
-            rec->status = ORC_TIR;
-            for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = xo[i]; rec->exit_dir[i] = d[i]; }
-            return rec->status;
-        }
-        double dout[3];
-        for (int i = 0; i < 3; ++i) dout[i] = ktx[i] + sqrt(1.0 - kt2) * no[i];
-        /* Eq. 12 along the physical direction of light: from the room into the
-           cloak at the exit point, and out of the cloak towards the camera at the
-           entry point.  Unpolarised source: mean over s and p. */
-        double Tin[8], Tout[4], mdout[3], mk0[3];
-        for (int i = 0; i < 3; ++i) { mdout[i] = -dout[i]; mk0[i] = -k0[i]; }
-        double w = 0.0;
-        if (orc_transmission_in(c, xo, no, mdout, Tin) && orc_transmission_out(c, mode, x_in, n_in, mk0, Tout))
-            w = (mode == ORC_ORDINARY ? Tin[6] : Tin[7]) * Tout[0] * Tout[3];
-        rec->weight = w;
-        rec->status = metal ? ORC_HIT_METAL_EXITED : ORC_EXITED;
-        finish_vacuum(c, xo, dout, rec);
+        *ev_hit = hit;
+        return ORC_EXITED;
+    }
+}
+
+/* Wave vector of the mode from the state's second half (Fermat: ray velocity, k = M v; Hamiltonian: k). */
+static void state_wave_vector(const orc_cloak *c, int mode, const double y[6], double k[3]) {
+    if (c->form)
+        for (int i = 0; i < 3; ++i) k[i] = y[3 + i];
+    else
+        wave_vector(c, mode, y, y + 3, k);
+}
+
+/* What a camera-backward ray reaches inside: entry data and the state on the far face. */
+typedef struct {
+    int status;           /* ORC_* so far; ORC_EXITED: y is on face `ev` (crossed, not yet refracted) */
+    double x_in[3], n_in[3], k0[3];
+    double y[6], t;
+    int ev, steps, metal;
+} inner_path;
+
+/* Entry split and integration of `mode` from the camera ray (o, d) to the far face. */
+static void trace_to_far_face(const orc_cloak *c, const orc_integrator *in, int mode, const double o[3],
+                              const double d[3], const double p[3], const double n[3], inner_path *ip,
+                              double *path, long path_cap, long *plen) {
+    double dn = dot3(d, n), kt[3], v0[3];
+    for (int i = 0; i < 3; ++i) kt[i] = d[i] - dn * n[i];
+    ip->t = 0.0;
+    ip->steps = 0;
+    ip->metal = 0;
+    ip->ev = -1;
+    for (int i = 0; i < 3; ++i) { ip->x_in[i] = p[i]; ip->n_in[i] = n[i]; }
+    if (!orc_refract_into(c, mode, p, n, kt, ip->k0, v0)) {
+        ip->status = ORC_NO_TRANSMISSION;
+        return;
+    }
+    /* state (x, v) of the Fermat form or (x, k) of the Hamiltonian form */
+    for (int i = 0; i < 3; ++i) { ip->y[i] = p[i]; ip->y[3 + i] = c->form ? ip->k0[i] : v0[i]; }
+    path_push(path, path_cap, plen, 0.0, ip->y);
+    ip->status = integrate_inside(c, in, mode, ip->y, &ip->t, &ip->steps, &ip->metal, &ip->ev, path, path_cap, plen);
+    (void)o;
+}
+
+int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const double o[3], const double d[3],
+                  orc_record *rec, double *path, long path_cap, long *path_len) {
+    memset(rec, 0, sizeof(*rec));
+    rec->mode = mode;
+    rec->tile_id = -1;
+    long plen = 0;
+    if (path_len) *path_len = 0;
+    double p[3], n[3];
+    int face;
+    /* unpolarised room light through a linear polariser: half of it */
+    const double vac = dot3(c->analyzer, c->analyzer) > 0.0 ? 0.5 : 1.0;
+    if (!hit_cylinder(c, o, d, p, n, &face)) {
+        rec->status = ORC_MISSED;
+        rec->weight = vac;
+        finish_vacuum(c, o, d, rec);
         return rec->status;
     }
+    if (face != EV_LATERAL && c->R1 > 0.0 && hypot(p[0], p[1]) <= c->R1) {
+        /* metal end disc seen from outside: mirror, reflectance 1 */
+        double dr[3], dn = dot3(d, n);
+        for (int i = 0; i < 3; ++i) dr[i] = d[i] - 2.0 * dn * n[i];
+        rec->status = ORC_METAL_CAP;
+        rec->weight = vac;
+        finish_vacuum(c, p, dr, rec);
+        return rec->status;
+    }
+    /* entry double refraction (Sect. 3), then the integration to the far face */
+    inner_path ip;
+    trace_to_far_face(c, in, mode, o, d, p, n, &ip, path, path_cap, &plen);
+    if (path_len) *path_len = plen;
+    rec->steps = ip.steps;
+    rec->tof = ip.t;
+    if (ip.status != ORC_EXITED) {
+        rec->status = ip.status;
+        const double *x = ip.status == ORC_NO_TRANSMISSION ? p : ip.y;
+        for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = x[i]; rec->exit_dir[i] = d[i]; }
+        if (ip.status == ORC_NO_TRANSMISSION) rec->tof = 0.0;
+        return rec->status;
+    }
+    /* exit refraction (Sect. 3): keep k_t, vacuum k_n = +sqrt(1 - |k_t|^2) */
+    double xo[3] = {ip.y[0], ip.y[1], ip.y[2]}, no[3], kx[3], ktx[3];
+    face_normal(ip.ev, xo, no);
+    state_wave_vector(c, mode, ip.y, kx);
+    double kn = dot3(kx, no);
+    for (int i = 0; i < 3; ++i) ktx[i] = kx[i] - kn * no[i];
+    double kt2 = dot3(ktx, ktx);
+    if (kt2 > 1.0) {
+        rec->status = ORC_TIR;
+        for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = xo[i]; rec->exit_dir[i] = d[i]; }
+        return rec->status;
+    }
+    double dout[3];
+    for (int i = 0; i < 3; ++i) dout[i] = ktx[i] + sqrt(1.0 - kt2) * no[i];
+    /* Eq. 12 along the physical direction of light: from the room into the
+       cloak at the exit point, and out of the cloak towards the camera at the
+       entry point.  Unpolarised source: mean over s and p. */
+    double Tin[8], Tout[4], mdout[3], mk0[3];
+    for (int i = 0; i < 3; ++i) { mdout[i] = -dout[i]; mk0[i] = -ip.k0[i]; }
+    double w = 0.0;
+    if (orc_transmission_in(c, xo, no, mdout, Tin) && orc_transmission_out(c, mode, ip.x_in, ip.n_in, mk0, Tout))
+        w = (mode == ORC_ORDINARY ? Tin[6] : Tin[7]) * Tout[0] * Tout[3];
+    rec->weight = w;
+    rec->status = ip.metal ? ORC_HIT_METAL_EXITED : ORC_EXITED;
+    finish_vacuum(c, xo, dout, rec);
+    return rec->status;
+}
+
+/* ------------------------------------------------------------------ */
+/* first-order reflections (Sect. 3 last paragraphs, Sect. 4)          */
+/* ------------------------------------------------------------------ */
+/* Fraction of unpolarised room light that the outer surface at x (normal n) reflects into the camera ray
+   d, through the camera's polariser if one is set.  Reading (reciprocity of the lossless, reciprocal
+   interface): the light arriving along d after the reflection is what, run backwards, a vacuum wave
+   incident along d reflects; so the fraction is the mean over the camera-side polarisations e (s and p,
+   or the polariser's axis across d alone) of the backward reflectance R(e), halved behind a polariser. */
+static double vacuum_reflection(const orc_cloak *c, const double x[3], const double n[3], const double d[3]) {
+    double T[8];
+    if (!orc_transmission_in(c, x, n, d, T)) return 0.0;
+    const double an = dot3(c->analyzer, c->analyzer);
+    if (!(an > 0.0)) return 0.5 * (T[4] + T[5]);
+    /* backward reflectance for the incident polarisation along the polariser's axis across d: the
+       reflected fields of the s and p solutions superposed with the axis' s and p components */
+    double a[3], ad = dot3(c->analyzer, d);
+    for (int i = 0; i < 3; ++i) a[i] = c->analyzer[i] - ad * d[i];
+    const double al = norm3(a);
+    if (!(al > 0.0)) return 0.0;
+    for (int i = 0; i < 3; ++i) a[i] /= al;
+    double o9[9];
+    if (!vacuum_face(c, x, n, d, a, o9)) return 0.0;
+    return 0.5 * o9[8];
+}
+
+int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode, const double o[3],
+                          const double d[3], orc_record *vacrec, orc_record refl[2]) {
+    memset(vacrec, 0, sizeof(*vacrec));
+    memset(refl, 0, 2 * sizeof(orc_record));
+    vacrec->tile_id = refl[0].tile_id = refl[1].tile_id = -1;
+    vacrec->status = refl[0].status = refl[1].status = ORC_MISSED;
+    refl[0].mode = ORC_ORDINARY;
+    refl[1].mode = ORC_EXTRAORDINARY;
+    vacrec->mode = -1;
+    double p[3], n[3];
+    int face;
+    if (!hit_cylinder(c, o, d, p, n, &face)) return 0;
+    if (face != EV_LATERAL && c->R1 > 0.0 && hypot(p[0], p[1]) <= c->R1) {
+        vacrec->status = refl[0].status = refl[1].status = ORC_METAL_CAP;
+        return 0;
+    }
+    /* (R0) the outer surface reflects room light into the camera (the same for both modes) */
+    {
+        double dr[3], dn = dot3(d, n);
+        for (int i = 0; i < 3; ++i) dr[i] = d[i] - 2.0 * dn * n[i];
+        vacrec->status = ORC_EXITED;
+        vacrec->weight = vacuum_reflection(c, p, n, d);
+        finish_vacuum(c, p, dr, vacrec);
+    }
+    /* (R1) the mode reaches the far face and, run backwards, reflects there into o' and e' */
+    inner_path ip;
+    trace_to_far_face(c, in, mode, o, d, p, n, &ip, NULL, 0, NULL);
+    if (ip.status != ORC_EXITED) {
+        refl[0].status = refl[1].status = ip.status;
+        return 1;
+    }
+    double x1[3] = {ip.y[0], ip.y[1], ip.y[2]}, n1[3], k1[3], kt[3];
+    face_normal(ip.ev, x1, n1);
+    state_wave_vector(c, mode, ip.y, k1);
+    const double kn = dot3(k1, n1);
+    for (int i = 0; i < 3; ++i) kt[i] = k1[i] - kn * n1[i];
+    /* camera-side factor: Eq. 12 out of the cloak at the entry point, through the polariser */
+    double Tout0[4], mk0[3], R1[4];
+    for (int i = 0; i < 3; ++i) mk0[i] = -ip.k0[i];
+    const double wcam = orc_transmission_out(c, mode, ip.x_in, ip.n_in, mk0, Tout0) ? Tout0[0] * Tout0[3] : 0.0;
+    if (!orc_transmission_out(c, mode, x1, n1, k1, R1)) R1[1] = R1[2] = 0.0;
+    for (int m2 = 0; m2 < 2; ++m2) {
+        orc_record *r = refl + m2;
+        r->mode = m2;
+        double kr[3], vr[3];
+        if (!(R1[1 + m2] > 0.0) || !orc_refract_into(c, m2, x1, n1, kt, kr, vr)) {
+            r->status = ORC_NO_TRANSMISSION; /* the reflected mode does not propagate */
+            for (int i = 0; i < 3; ++i) { r->exit_pos[i] = x1[i]; r->exit_dir[i] = d[i]; }
+            continue;
+        }
+        double y[6] = {x1[0], x1[1], x1[2], 0, 0, 0}, t = ip.t;
+        for (int i = 0; i < 3; ++i) y[3 + i] = c->form ? kr[i] : vr[i];
+        int steps = 0, metal = ip.metal, ev = -1;
+        const int st = integrate_inside(c, in, m2, y, &t, &steps, &metal, &ev, NULL, 0, NULL);
+        r->steps = steps;
+        r->tof = t;
+        if (st != ORC_EXITED) {
+            r->status = st;
+            for (int i = 0; i < 3; ++i) { r->exit_pos[i] = y[i]; r->exit_dir[i] = d[i]; }
+            continue;
+        }
+        /* refraction out at the reflected ray's own exit, no further reflection (first order) */
+        double xo[3] = {y[0], y[1], y[2]}, no[3], kx[3], ktx[3];
+        face_normal(ev, xo, no);
+        state_wave_vector(c, m2, y, kx);
+        const double kn2 = dot3(kx, no);
+        for (int i = 0; i < 3; ++i) ktx[i] = kx[i] - kn2 * no[i];
+        const double kt2 = dot3(ktx, ktx);
+        if (kt2 > 1.0) {
+            r->status = ORC_TIR;
+            for (int i = 0; i < 3; ++i) { r->exit_pos[i] = xo[i]; r->exit_dir[i] = d[i]; }
+            continue;
+        }
+        double dout[3], mdout[3], Tin[8];
+        for (int i = 0; i < 3; ++i) { dout[i] = ktx[i] + sqrt(1.0 - kt2) * no[i]; mdout[i] = -dout[i]; }
+        const double tin = orc_transmission_in(c, xo, no, mdout, Tin) ? (m2 == ORC_ORDINARY ? Tin[6] : Tin[7]) : 0.0;
+        r->weight = wcam * R1[1 + m2] * tin;
+        r->status = metal ? ORC_HIT_METAL_EXITED : ORC_EXITED;
+        finish_vacuum(c, xo, dout, r);
+    }
+    return 1;
 }
 
 /* The ray equations in Hamiltonian form (the comparison system of Sect. 4's closing remark): state

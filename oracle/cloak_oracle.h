@@ -98,9 +98,19 @@ void orc_mode_fields(const orc_cloak *c, int mode, const double x[3], const doub
 int orc_transmission_in(const orc_cloak *c, const double x[3], const double nhat[3],
                         const double d[3], double out[8]);
 /* out[0] transmitted flux fraction, out[1], out[2] reflected into o / e, out[3] fraction of the
-   transmitted flux that passes the analyser c->analyzer (1 without one) */
+   transmitted flux that passes the analyser c->analyzer (1 without one); under total internal
+   reflection out[0] = 0 and out[1] + out[2] = 1 */
 int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const double nhat[3],
                          const double k[3], double out[4]);
+
+/* First-order reflections of one camera sample traced in `mode` (the paper keeps first-order reflections,
+   Sect. 4): vac = room light the outer surface reflects into the camera at the entry point (weight =
+   reflectance, the same for both modes), refl[m'] = room light that enters the cloak, travels as mode m',
+   reflects at the far face of the camera-backward ray into `mode` and leaves towards the camera (exit
+   point and direction of the m' ray, time of flight of both legs, weight = camera-side Eq. 12 factor x
+   reflection coefficient x entry Eq. 12 factor of m').  Returns 0 for rays that never enter the shell. */
+int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode, const double o[3],
+                          const double d[3], orc_record *vac, orc_record refl[2]);
 
 /* Hamiltonian form of the ray equations, state (x, k), k = M v: dx/dt = M^-1 k,
    dk/dt = (1/2) v^T (d_i M) v (the comparison system of Sect. 4's closing remark) */
