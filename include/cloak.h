@@ -243,6 +243,17 @@ enum {
     CLOAK_PANEL_POLARIZER_UP = 4,    /* (e): ... along the camera's up vector */
     CLOAK_PANEL_TOF = 5              /* time-of-flight difference image (see above) */
 };
+/* First-order reflections (Sect. 4: the paper keeps them and omits higher orders) in the panels
+ * CLOAK_PANEL_UNPOLARIZED and CLOAK_PANEL_POLARIZER_*: on = 1 adds, per sample that enters the shell,
+ * (a) room light that the outer surface reflects into the camera (by reciprocity, the mean over the
+ * camera-side polarisations of the reflectance of a vacuum wave along the camera ray; counted once), and
+ * (b) for each traced polarization, light that travelled inside as the ordinary or the extraordinary wave
+ * and reflected at the camera-backward ray's far face into the traced wave (Sect. 3's double reflection;
+ * reflection coefficients of the 4x4 field solve, also under total internal reflection), each reflected
+ * ray traced through the cloak to its own exit and refracted out without further reflection.  The
+ * reflected rays run through a second queue and integration launch after the batched render.  on = 0
+ * (default): refraction only.  The TOF panel, cloak_render and the records ignore it. */
+int cloak_set_reflections(cloak_t *h, int on);
 int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long long seed, void *dev_rgba, size_t bytes,
                        void *cuda_stream);
 

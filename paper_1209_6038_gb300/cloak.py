@@ -51,6 +51,7 @@ SIGNATURES = {
     "cloak_render_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
     "cloak_set_analyzer": (C.c_int, [C.c_void_p, C.c_int]),
+    "cloak_set_reflections": (C.c_int, [C.c_void_p, C.c_int]),
     "cloak_set_formulation": (C.c_int, [C.c_void_p, C.c_int]),
     "cloak_render_panel": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                      C.c_void_p]),
@@ -229,6 +230,10 @@ def cloak_set_analyzer(h, analyzer):
     return _check(load().cloak_set_analyzer(h, analyzer))
 
 
+def cloak_set_reflections(h, on):
+    return _check(load().cloak_set_reflections(h, on))
+
+
 def cloak_render_panel(h, panel, spp, seed, rgba, stream=None):
     return _check(load().cloak_render_panel(h, panel, spp, seed, C.c_void_p(rgba.data_ptr()),
                                             rgba.numel() * rgba.element_size(), _stream_ptr(stream)))
@@ -356,6 +361,11 @@ class Cloak:
     def analyzer(self, analyzer=ANALYZER_NONE):
         """Linear polariser in front of the camera (ANALYZER_NONE / _RIGHT / _UP)."""
         cloak_set_analyzer(self.h, analyzer)
+        return self
+
+    def reflections(self, on=True):
+        """First-order reflections in the unpolarised and polariser panels."""
+        cloak_set_reflections(self.h, 1 if on else 0)
         return self
 
     def panel(self, panel, spp=1, seed=0, out=None, stream=None):

@@ -30,7 +30,11 @@ cudaError_t launch_batch(const Params &p, const ViewDev *views, int nviews, int 
 cudaError_t launch_tof_resolve(const Params &p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
                                const float4 *samples, float4 *out, cudaStream_t st);
 cudaError_t launch_unpol_resolve(const Params &p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
-                                 const float4 *samples, float4 *out, cudaStream_t st);
+                                 const float4 *samples, const float4 *refl, float4 *out, cudaStream_t st);
+// first-order reflections of the main rays of the last batch (queue q): reflected rays through queue q2
+// (capacity >= 2 x q's), refl[2 g + m'] (nrefl = 2 x samples of the batch) written on st
+cudaError_t launch_reflections(const Params &p, const Queue &q, const Queue &q2, float4 *refl, long long nrefl,
+                               int packet, cudaStream_t st);
 // reference panels without the cloak: 0 the room alone, 1 the bare metal cylinder (radius R1, height H)
 cudaError_t launch_panel(const Params &p, int panel, int spp, unsigned long long seed, float4 *out, cudaStream_t st);
 

@@ -50,6 +50,11 @@ struct cloak {
     // the two polarisation images behind the unpolarised panel
     void *panel_img;
     size_t panel_bytes;
+    // first-order reflections in the unpolarised and polariser panels: the reflected rays' queue and
+    // their per-sample results
+    int reflections;
+    void *refl_scratch;
+    size_t refl_bytes;
 };
 
 static thread_local std::string g_err;
@@ -278,6 +283,7 @@ void cloak_destroy(cloak_t *h) {
     if (h->scratch) cudaFree(h->scratch);
     ck::sur_destroy(h->sur);
     if (h->panel_img) cudaFree(h->panel_img);
+    if (h->refl_scratch) cudaFree(h->refl_scratch);
     if (h->timing)
         for (int i = 0; i < 5; ++i) cudaEventDestroy(h->ev[i]);
     delete h;
@@ -387,6 +393,13 @@ int cloak_set_formulation(cloak_t *h, int formulation) {
             return fail(CLOAK_ESTATE, "the Hamiltonian form runs in FP64");
     }
     h->formulation = formulation;
+    return CLOAK_OK;
+}
+
+int cloak_set_reflections(cloak_t *h, int on) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (on != 0 && on != 1) return fail(CLOAK_EINVAL, "reflections must be 0 or 1");
+    h->reflections = on;
     return CLOAK_OK;
 }
 
@@ -558,7 +571,7 @@ static unsigned long long fnv1a(unsigned long long hsh, const void *data, size_t
 // The batched render (views validated, device table, graph capture or replay); samples_out (nullable)
 // receives the per-sample buffer of the batch.
 static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
-                      void *cuda_stream, float4 **samples_out, int analyzer, int tof = 0);
+                      void *cuda_stream, float4 **samples_out, int analyzer, int tof = 0, ck::Queue *q_out = nullptr);
 
 extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
                                   void *cuda_stream) {
@@ -566,7 +579,7 @@ extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nview
 }
 
 static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
-                      void *cuda_stream, float4 **samples_out, int analyzer, int tof) {
+                      void *cuda_stream, float4 **samples_out, int analyzer, int tof, ck::Queue *q_out) {
     if (!h) return fail(CLOAK_EINVAL, "null handle");
     if (h->variant != CLOAK_RADIAL && h->variant != CLOAK_AZIMUTHAL)
         return fail(CLOAK_ESTATE, "batched rendering needs a radial or azimuthal cloak handle");
@@ -593,6 +606,7 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
     ck::Queue q;
     float4 *samples = nullptr;
     if ((rc = wavefront_scratch(h, total, q, &samples))) return rc;
+    if (q_out) *q_out = q;
     size_t tbytes = table.size() * sizeof(ck::ViewDev);
     unsigned long long key = 1469598103934665603ull;
     key = fnv1a(key, table.data(), tbytes);
@@ -720,11 +734,37 @@ extern "C" int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long 
         v[m].dev_rgba = (char *)h->panel_img + m * npix * 16;
     }
     float4 *samples = nullptr;
-    if ((rc = batch_core(h, v, 2, spp, seed, cuda_stream, &samples, analyzer, tof))) return rc;
+    const bool refl = h->reflections && !tof;
+    const long long total = 2LL * (long long)npix * spp;
+    if (refl && 2 * total > 2147483647LL)
+        return fail(CLOAK_EINVAL, "reflections: 2 x %lld samples exceed 2^31-1", total);
+    ck::Queue q;
+    if ((rc = batch_core(h, v, 2, spp, seed, cuda_stream, &samples, analyzer, tof, &q))) return rc;
+    float4 *rs = nullptr;
+    if (refl) {
+        // the reflected rays' queue; its per-sample buffer (2 x samples) holds their results
+        const size_t need = ck::queue_bytes(2 * total);
+        if (h->refl_bytes < need) {
+            if (h->refl_scratch) cudaFree(h->refl_scratch);
+            h->refl_scratch = nullptr;
+            h->refl_bytes = 0;
+            cudaError_t e = cudaMalloc(&h->refl_scratch, need);
+            if (e != cudaSuccess) {
+                h->refl_scratch = nullptr;
+                cudaGetLastError();
+                return fail(CLOAK_ENOMEM, "reflection scratch: %s", cudaGetErrorString(e));
+            }
+            h->refl_bytes = need;
+        }
+        ck::Queue q2;
+        ck::carve_queue((char *)h->refl_scratch, 2 * total, q2, &rs);
+        cudaError_t e = ck::launch_reflections(p, q, q2, rs, 2 * total, h->packet, st);
+        if (e != cudaSuccess) return cuda_fail(e, "reflections");
+    }
     cudaError_t e = tof ? ck::launch_tof_resolve(p, (const ck::ViewDev *)h->batch_dev, spp, seed, (long long)npix,
                                                  samples, (float4 *)dev_rgba, st)
                         : ck::launch_unpol_resolve(p, (const ck::ViewDev *)h->batch_dev, spp, seed, (long long)npix,
-                                                   samples, (float4 *)dev_rgba, st);
+                                                   samples, rs, (float4 *)dev_rgba, st);
     return e == cudaSuccess ? CLOAK_OK : cuda_fail(e, tof ? "TOF resolve" : "unpolarised resolve");
 }
 

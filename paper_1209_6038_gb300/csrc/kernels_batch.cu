@@ -111,13 +111,17 @@ __global__ void k_batch_resolve(const ViewDev *views, int nviews, int spp, long 
 // Unpolarised light (the paper's Fig. 1(c) / 2(c)): per pixel, the mean over its samples of the ordinary
 // plus the extraordinary sample of views 0 and 1 (the same camera); a ray that never enters the shell
 // (it misses the cylinder or mirrors off a metal end disc) is the same for both modes and counts once.
+// With first-order reflections (refl non-null: per sample index g, refl[2 g + m'] is the light that
+// reflected at the far face from mode m' into the sample's mode) a sample that enters also receives the
+// room light the outer surface reflects into the camera, once.
 __global__ void k_unpol_resolve(Params p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
-                                const float4 *samples, float4 *out) {
+                                const float4 *samples, const float4 *refl, float4 *out) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= npix) return;
     const ViewDev &v0 = views[0];
     const int i = (int)(g % v0.W), j = (int)(g / v0.W);
-    const float4 *so = samples + views[0].ray_begin + g * spp, *se = samples + views[1].ray_begin + g * spp;
+    const long long go = views[0].ray_begin + g * spp, ge = views[1].ray_begin + g * spp;
+    const float4 *so = samples + go, *se = samples + ge;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     for (int s = 0; s < spp; ++s) {
         double o[3], d[3], pt[3], n[3];
@@ -128,6 +132,20 @@ __global__ void k_unpol_resolve(Params p, const ViewDev *views, int spp, unsigne
         if (enters) {
             const float4 e = se[s];
             v.x += e.x; v.y += e.y; v.z += e.z; v.w += e.w;
+            if (refl) {
+                const float4 r[4] = {refl[2 * (go + s)], refl[2 * (go + s) + 1], refl[2 * (ge + s)], refl[2 * (ge + s) + 1]};
+                for (int q = 0; q < 4; ++q) { v.x += r[q].x; v.y += r[q].y; v.z += r[q].z; v.w += r[q].w; }
+                double eo, ee, c[3], dr[3];
+                local_material(p, pt, eo, ee, c);
+                const double dn = dot3(d, n);
+                for (int q = 0; q < 3; ++q) dr[q] = d[q] - 2.0 * dn * n[q];
+                const double axis[3] = {p.analyzer == 1 ? v0.rt[0] : v0.up[0], p.analyzer == 1 ? v0.rt[1] : v0.up[1],
+                                        p.analyzer == 1 ? v0.rt[2] : v0.up[2]};
+                const float w = (float)vacuum_reflection(eo, ee, c, n, d, p.analyzer ? axis : nullptr);
+                float rgb[3];
+                room_hit(p, pt, dr, rgb);
+                v.x += w * rgb[0]; v.y += w * rgb[1]; v.z += w * rgb[2]; v.w += w;
+            }
         }
         a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
     }
@@ -168,9 +186,92 @@ cudaError_t launch_tof_resolve(const Params &p, const ViewDev *views, int spp, u
 }
 
 cudaError_t launch_unpol_resolve(const Params &p, const ViewDev *views, int spp, unsigned long long seed, long long npix,
-                                 const float4 *samples, float4 *out, cudaStream_t st) {
-    k_unpol_resolve<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(p, views, spp, seed, npix, samples, out);
+                                 const float4 *samples, const float4 *refl, float4 *out, cudaStream_t st) {
+    k_unpol_resolve<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(p, views, spp, seed, npix, samples, refl, out);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ first-order reflections
+// Each main ray that reached a face (status EXITED or HIT_METAL_EXITED in the queue; total internal
+// reflection is decided at exit) reflects there, run backwards, into the ordinary and extraordinary
+// waves: they are appended to the second queue q2 with their camera-side weight (the main ray's
+// camera-side Eq. 12 factor x the reflection coefficient) and the slot id 2 g + m'.
+__global__ void __launch_bounds__(128) k_refl_spawn(Params p, Queue q, Queue q2) {
+    const unsigned int n = q.count[0];
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int key = q.key[k], status = q.status[k];
+        if (key < 0 || (status != CLOAK_RAY_EXITED && status != CLOAK_RAY_HIT_METAL_EXITED)) continue;
+        const int vm = key_vm(key), mode = vm & 1;
+        Params pv = p;
+        pv.variant = vm >> 1;
+        const double x[3] = {q.x[k], q.y[k], q.z[k]}, w[3] = {q.vx[k], q.vy[k], q.vz[k]};
+        double nrm[3], eo, ee, c[3], kk[3];
+        face_normal(q.face[k], x, nrm);
+        local_material(pv, x, eo, ee, c);
+        if (p.formulation) set_vec(kk, w);
+        else wave_from_velocity(mode, eo, ee, c, w, kk);
+        double R[2];
+        if (!internal_reflection(mode, eo, ee, c, nrm, kk, R)) continue;
+        const double kn = dot3(kk, nrm);
+        double kt[3];
+        for (int i = 0; i < 3; ++i) kt[i] = kk[i] - kn * nrm[i];
+        for (int m2 = 0; m2 < 2; ++m2) {
+            double k2[3], v2[3];
+            if (!(R[m2] > 0.0) || !refract_in(m2, eo, ee, c, nrm, kt, k2, v2)) continue;
+            const double y[6] = {x[0], x[1], x[2], p.formulation ? k2[0] : v2[0], p.formulation ? k2[1] : v2[1],
+                                 p.formulation ? k2[2] : v2[2]};
+            queue_append(q2, y, q.w_out[k] * R[m2], 2 * q.id[k] + m2,
+                         batch_key(2 * pv.variant + m2, cost_bucket(y, k2)));
+        }
+    }
+}
+
+// Exit of the reflected rays: refraction into the room at their own exit (no further reflection), the
+// Eq. 12 factor of room light entering there, the room colour: refl[id] = (w rgb, w).
+__global__ void __launch_bounds__(128) k_refl_exit(Params p, Queue q2, float4 *refl) {
+    const unsigned int n = q2.count[0];
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int vm = key_vm(q2.key[k]);
+        Params pv = p;
+        pv.variant = vm >> 1;
+        const double dz[3] = {0.0, 0.0, 1.0};
+        cloak_record rec;
+        float rgb[3];
+        exit_slot(pv, vm & 1, q2, k, dz, rec, rgb);
+        const float w = (float)rec.weight;
+        refl[q2.id[k]] = make_float4(w * rgb[0], w * rgb[1], w * rgb[2], w);
+    }
+}
+
+template <int I, int PREC>
+static cudaError_t refl_ip(const Params &p, const Queue &q, const Queue &q2, float4 *refl, long long nrefl, int packet,
+                           cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMemsetAsync(q2.count, 0, QUEUE_HEADER_BYTES, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(refl, 0, (size_t)nrefl * sizeof(float4), st);
+    if (e != cudaSuccess) return e;
+    k_refl_spawn<<<sms * 16, 128, 0, st>>>(p, q, q2);
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q2, NBINS_BATCH);
+    k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q2);
+    const int pk = packet > 0 ? packet : 128;
+    int nb = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V_ANY, V_ANY, I, PREC>, pk, 0)) !=
+        cudaSuccess)
+        return e;
+    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(p, q2);
+    k_refl_exit<<<sms * 16, 128, 0, st>>>(p, q2, refl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reflections(const Params &p, const Queue &q, const Queue &q2, float4 *refl, long long nrefl,
+                               int packet, cudaStream_t st) {
+    if (p.integ == I_RK4)
+        return p.precision ? refl_ip<I_RK4, 1>(p, q, q2, refl, nrefl, packet, st)
+                           : refl_ip<I_RK4, 0>(p, q, q2, refl, nrefl, packet, st);
+    return p.precision ? refl_ip<I_DP45, 1>(p, q, q2, refl, nrefl, packet, st)
+                       : refl_ip<I_DP45, 0>(p, q, q2, refl, nrefl, packet, st);
 }
 
 static inline void mark(cudaEvent_t *ev, int i, cudaStream_t st) {

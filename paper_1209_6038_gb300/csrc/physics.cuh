@@ -789,6 +789,124 @@ static __device__ __noinline__ double transmission_out(int mode, double eo, doub
     return al2 > 0.0 && e2 > 0.0 ? T * (er * er + ei * ei) / (al2 * e2) : 0.0;
 }
 
+// First-order reflections (Sect. 3 last paragraphs, Sect. 4).
+// Reflection coefficients of a wave of `mode` (real wave vector k, travelling towards the face with outward
+// normal n) into the ordinary and extraordinary waves it reflects into: R[0], R[1].  Under total internal
+// reflection (|k_t| > 1) the vacuum side carries the evanescent wave that decays away from the face and
+// R[0] + R[1] = 1.  Returns false if the 4x4 field-continuity system is singular.
+static __device__ __noinline__ bool internal_reflection(int mode, double eo, double ee, const double c[3],
+                                                        const double n[3], const double k[3], double R[2]) {
+    double kn = dot3(k, n), kt[3];
+    for (int i = 0; i < 3; ++i) kt[i] = k[i] - kn * n[i];
+    const double kt2 = dot3(kt, kt);
+    const bool tir = kt2 > 1.0;
+    const double qn = sqrt(fabs(1.0 - kt2));
+    cx kv[3];
+    for (int i = 0; i < 3; ++i) kv[i] = tir ? cx{kt[i], qn * n[i]} : cx{fma(qn, n[i], kt[i]), 0.0};
+    double s[3];
+    s_basis(kt, n, s);  // perpendicular to the plane of incidence (kt x n); p = s x k
+    cx Es[3] = {C(s[0]), C(s[1]), C(s[2])}, Ep[3], Hs[3], Hp[3];
+    ccross(Es, kv, Ep);
+    ccross(kv, Es, Hs);
+    ccross(kv, Ep, Hp);
+    cx t2c[3] = {C(n[1] * s[2] - n[2] * s[1]), C(n[2] * s[0] - n[0] * s[2]), C(n[0] * s[1] - n[1] * s[0])};
+    cx ct1[3] = {C(s[0]), C(s[1]), C(s[2])};
+    cx kro[3], kre[3], Ero[3], Hro[3], Ere[3], Hre[3], Em[3], Hm[3];
+    inward_wave_c(M_ORD, eo, ee, c, n, kt, kro);
+    inward_wave_c(M_EXT, eo, ee, c, n, kt, kre);
+    wave_fields(M_ORD, eo, ee, c, kro, Ero, Hro);
+    wave_fields(M_EXT, eo, ee, c, kre, Ere, Hre);
+    cx ck3[3] = {C(k[0]), C(k[1]), C(k[2])};
+    wave_fields(mode, eo, ee, c, ck3, Em, Hm);
+    const cx *colE[4] = {Es, Ep, Ero, Ere}, *colH[4] = {Hs, Hp, Hro, Hre};
+    cx A[4][4], B[4][1];
+    for (int j = 0; j < 4; ++j) {
+        double sg = j < 2 ? 1.0 : -1.0;
+        A[0][j] = sg * cdot(colE[j], ct1);
+        A[1][j] = sg * cdot(colE[j], t2c);
+        A[2][j] = sg * cdot(colH[j], ct1);
+        A[3][j] = sg * cdot(colH[j], t2c);
+    }
+    B[0][0] = cdot(Em, ct1);
+    B[1][0] = cdot(Em, t2c);
+    B[2][0] = cdot(Hm, ct1);
+    B[3][0] = cdot(Hm, t2c);
+    const double fm = fabs(flux_n(n, Em, Hm));
+    R[0] = R[1] = 0.0;
+    if (!csolve4<1>(A, B) || !(fm > 0.0)) return false;
+    R[0] = cabs2(B[2][0]) * fabs(flux_n(n, Ero, Hro)) / fm;
+    R[1] = cabs2(B[3][0]) * fabs(flux_n(n, Ere, Hre)) / fm;
+    return true;
+}
+
+// Fraction of unpolarised room light that the outer surface at a face point (normal n, local material)
+// reflects into the camera ray d, through the camera's polariser `axis` (nullable).  By reciprocity of the
+// lossless interface this is the mean over the camera-side polarisations of the reflectance of a vacuum
+// wave incident along d: (R_s + R_p) / 2, or behind a polariser R(e) / 2 for the incident polarisation e
+// along the polariser's axis taken across d.
+static __device__ __noinline__ double vacuum_reflection(double eo, double ee, const double c[3], const double n[3],
+                                                        const double d[3], const double *axis) {
+    double dn = dot3(d, n), kt[3], kr[3];
+    for (int i = 0; i < 3; ++i) { kt[i] = d[i] - dn * n[i]; kr[i] = d[i] - 2.0 * dn * n[i]; }
+    cx ko[3], ke[3], Eo[3], Ho[3], Ee[3], He[3];
+    inward_wave_c(M_ORD, eo, ee, c, n, kt, ko);
+    inward_wave_c(M_EXT, eo, ee, c, n, kt, ke);
+    wave_fields(M_ORD, eo, ee, c, ko, Eo, Ho);
+    wave_fields(M_EXT, eo, ee, c, ke, Ee, He);
+    double s[3], pi[3], pr[3], t2[3];
+    s_basis(d, n, s);
+    pi[0] = s[1] * d[2] - s[2] * d[1]; pi[1] = s[2] * d[0] - s[0] * d[2]; pi[2] = s[0] * d[1] - s[1] * d[0];
+    pr[0] = s[1] * kr[2] - s[2] * kr[1]; pr[1] = s[2] * kr[0] - s[0] * kr[2]; pr[2] = s[0] * kr[1] - s[1] * kr[0];
+    t2[0] = n[1] * s[2] - n[2] * s[1]; t2[1] = n[2] * s[0] - n[0] * s[2]; t2[2] = n[0] * s[1] - n[1] * s[0];
+    cx Ers[3] = {C(s[0]), C(s[1]), C(s[2])}, Erp[3] = {C(pr[0]), C(pr[1]), C(pr[2])}, Hrs[3], Hrp[3];
+    cx ckr[3] = {C(kr[0]), C(kr[1]), C(kr[2])};
+    ccross(ckr, Ers, Hrs);
+    ccross(ckr, Erp, Hrp);
+    cx ct1[3] = {C(s[0]), C(s[1]), C(s[2])}, ct2[3] = {C(t2[0]), C(t2[1]), C(t2[2])};
+    const cx *colE[4] = {Ers, Erp, Eo, Ee}, *colH[4] = {Hrs, Hrp, Ho, He};
+    cx A[4][4], B[4][2];
+    for (int j = 0; j < 4; ++j) {
+        double sg = j < 2 ? 1.0 : -1.0;
+        A[0][j] = sg * cdot(colE[j], ct1);
+        A[1][j] = sg * cdot(colE[j], ct2);
+        A[2][j] = sg * cdot(colH[j], ct1);
+        A[3][j] = sg * cdot(colH[j], ct2);
+    }
+    // incident polarisations: s and p, or the polariser's axis across d (second column unused)
+    double e[2][3];
+    for (int i = 0; i < 3; ++i) { e[0][i] = s[i]; e[1][i] = pi[i]; }
+    if (axis) {
+        const double ad = dot3(axis, d);
+        double a[3];
+        for (int i = 0; i < 3; ++i) a[i] = axis[i] - ad * d[i];
+        const double al = sqrt(dot3(a, a));
+        if (!(al > 0.0)) return 0.0;
+        for (int i = 0; i < 3; ++i) e[0][i] = a[i] / al;
+    }
+    cx cd[3] = {C(d[0]), C(d[1]), C(d[2])};
+    double fin[2];
+    for (int pol = 0; pol < 2; ++pol) {
+        cx Ei[3] = {C(e[pol][0]), C(e[pol][1]), C(e[pol][2])}, Hi[3];
+        ccross(cd, Ei, Hi);
+        B[0][pol] = -1.0 * cdot(Ei, ct1);
+        B[1][pol] = -1.0 * cdot(Ei, ct2);
+        B[2][pol] = -1.0 * cdot(Hi, ct1);
+        B[3][pol] = -1.0 * cdot(Hi, ct2);
+        fin[pol] = fabs(flux_n(n, Ei, Hi));
+    }
+    if (!csolve4<2>(A, B)) return 0.0;
+    double Rv[2];
+    for (int pol = 0; pol < 2; ++pol) {
+        cx Er[3], Hr[3];
+        for (int i = 0; i < 3; ++i) {
+            Er[i] = B[0][pol] * Ers[i] + B[1][pol] * Erp[i];
+            Hr[i] = B[0][pol] * Hrs[i] + B[1][pol] * Hrp[i];
+        }
+        Rv[pol] = fabs(flux_n(n, Er, Hr)) / fin[pol];
+    }
+    return axis ? 0.5 * Rv[0] : 0.5 * (Rv[0] + Rv[1]);
+}
+
 // axis of the camera's polariser, or null
 __device__ __forceinline__ const double *analyzer_axis(const Params &p) {
     return p.analyzer == 1 ? p.rt : p.analyzer == 2 ? p.up : nullptr;

@@ -176,3 +176,17 @@ def test_rays_that_never_enter_have_no_reflections():
     assert vac["weight"] == 0.0 and refl["weight"].sum() == 0.0 and vac["status"] == O.MISSED
     vac, refl = O.trace_reflections(cl, INTEG, O.ORDINARY, (0.2, 0.0, 5.0), (0.0, 0.0, -1.0))
     assert vac["status"] == O.METAL_CAP and vac["weight"] == 0.0
+
+
+@pytest.mark.parametrize("variant", [O.RADIAL, O.AZIMUTHAL])
+def test_first_order_light_never_exceeds_the_room_light(variant):
+    """Per pixel, refracted plus first-order reflected light of the unpolarised image is at most the
+    room light a bare pixel sees (weight 1): the camera-backward splits at each face conserve flux."""
+    cam = O.Camera((4, 1, 0.8), (0, 0, 0), (0, 0, 1), 60.0, 16, 12)
+    c, integ = O.Cloak(variant), O.Integrator(O.DP45, 1e-9, 1_000_000)
+    _, ro = O.render(c, integ, cam, O.ORDINARY, 1, 0)
+    _, re = O.render(c, integ, cam, O.EXTRAORDINARY, 1, 0)
+    enters = ~np.isin(ro["status"], [O.MISSED, O.METAL_CAP])
+    total = ro["weight"] + np.where(enters, re["weight"], 0.0) + O.reflections_image(c, integ, cam, 1, 0)[:, 3]
+    assert np.all(total <= 1.0 + 1e-12)
+    assert np.all(total[enters] > 0.3) and enters.sum() > 20
