@@ -159,7 +159,11 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     constexpr double NEWTON_LAST = 1e-6;
     // medium segments of the permutation (batch: one per medium/mode; a lane draws rays from its
     // warp's current segment, so that the lanes of a warp evaluate one medium's equations)
-    int seg = VAR == V_ANY ? 3 - (int)(((blockIdx.x * blockDim.x + threadIdx.x) >> 5) & 3) : 0;
+    // the first segment is chosen per SM, so that the warps resident on one SM run one medium's code
+    // (a quarter of the kernel's instructions for the instruction caches)
+    unsigned int smid = 0;
+    if (VAR == V_ANY) asm("mov.u32 %0, %%smid;" : "=r"(smid));
+    int seg = VAR == V_ANY ? 3 - (int)(smid & 3u) : 0;
     // lane state
     R h = h0, t = 0;
     int steps = 0, phase = PH_IDLE, slot = -1;
