@@ -1,14 +1,15 @@
 // mlp_fused.cu -- the surrogate network's forward pass as ONE persistent tcgen05 kernel.
 //
-// Each CTA (256 threads, one per SM) takes pairs of 128-row tiles through all five layers without their
+// Each CTA (512 threads, one per SM) takes pairs of 128-row tiles through all five layers without their
 // activations leaving the SM:
 //   * the inputs of both tiles arrive by TMA in the 128-byte-swizzled K-major layout the MMA reads;
 //   * one thread streams the layer's weights from L2 in 64-wide K chunks through a 2-slot TMA ring and
 //     issues, per chunk, the tcgen05.mma (M = 128, K = 16) of both tiles against it, accumulating in
 //     TMEM (tile t in columns 256 t .. 256 t + 255: all 512 columns);
-//   * after the layer's MMAs complete, the 8 warps read the accumulators (warp w: tile w / 4, TMEM lanes
-//     32 (w % 4) ..), add the bias, apply GELU and write the BF16 activations back into the swizzled
-//     shared-memory layout as the next layer's A operand (the last layer writes the FP32 outputs).
+//   * after the layer's MMAs complete, the 16 warps read the accumulators (warp w: tile (w / 4) % 2, TMEM
+//     lanes 32 (w % 4) .., column half w / 8), add the bias, apply GELU and write the BF16 activations back
+//     into the swizzled shared-memory layout as the next layer's A operand (the last layer writes the FP32
+//     outputs).  Two warps per row quarter and tile keep twice as many epilogue instructions in flight.
 // Shared memory: activations 2 x 64 KB, weight ring 2 x 32 KB.  Every mbarrier wait is bounded; on a
 // timeout the kernel sets the error flag, lets its copies in flight land, frees TMEM and returns.
 #include "surrogate.h"
@@ -17,7 +18,8 @@
 namespace ck {
 
 namespace {
-constexpr int F_THREADS = 256;
+constexpr int F_THREADS = 512;
+constexpr int F_PARTS = F_THREADS / 256;  // warps sharing a row quarter of a tile (column parts)
 constexpr uint32_t F_ACT_CHUNK = 128 * 128;                  // 128 rows x 64 BF16 = 16 KB
 constexpr uint32_t F_ACT_BYTES = 2 * 4 * F_ACT_CHUNK;         // 2 tiles x 4 K chunks
 constexpr uint32_t F_RING_SLOT = 256 * 128;                   // up to 256 weight rows x 64 BF16
@@ -125,12 +127,14 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             const bool done = mbar_wait(smem_u32(&done_bar), layers & 1);
             ++layers;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // epilogue: warp w reads tile w / 4, TMEM lanes 32 (w % 4) .. + 31 (one row per thread)
-            const int t = warp >> 2, q = warp & 3, r = q * 32 + lane;
+            // epilogue: warp w reads tile (w / 4) % 2, TMEM lanes 32 (w % 4) .. + 31 (one row per thread),
+            // columns of part w / 8
+            const int t = (warp >> 2) & 1, q = warp & 3, r = q * 32 + lane, part = warp >> 3;
+            const int cw = max(16, N / F_PARTS), c0 = part * cw, c1 = min(N, c0 + cw);
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
             if (done && !failed) {
                 const float *bias = sbias[l];
-                for (int c = 0; c < N; c += 16) {
+                for (int c = c0; c < c1; c += 16) {
                     uint32_t u[16];
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
