@@ -1,25 +1,31 @@
 // mlp_fused.cu -- the surrogate network's forward pass as ONE persistent tcgen05 kernel.
 //
-// Each CTA (512 threads, one per SM) takes pairs of 128-row tiles through all five layers without their
-// activations leaving the SM:
-//   * the inputs of both tiles arrive by TMA in the 128-byte-swizzled K-major layout the MMA reads;
-//   * one thread streams the layer's weights from L2 in 64-wide K chunks through a 2-slot TMA ring and
-//     issues, per chunk, the tcgen05.mma (M = 128, K = 16) of both tiles against it, accumulating in
-//     TMEM (tile t in columns 256 t .. 256 t + 255: all 512 columns);
-//   * after the layer's MMAs complete, the 16 warps read the accumulators (warp w: tile (w / 4) % 2, TMEM
-//     lanes 32 (w % 4) .., column half w / 8), add the bias, apply GELU and write the BF16 activations back
-//     into the swizzled shared-memory layout as the next layer's A operand (the last layer writes the FP32
-//     outputs).  Two warps per row quarter and tile keep twice as many epilogue instructions in flight.
-// Shared memory: activations 2 x 64 KB, weight ring 2 x 32 KB.  Every mbarrier wait is bounded; on a
-// timeout the kernel sets the error flag, lets its copies in flight land, frees TMEM and returns.
+// Each CTA (one per SM) takes pairs of 128-row tiles through all five layers without their activations
+// leaving the SM.  Warp-specialised:
+//   * the producer warp (one thread) loads the inputs of both tiles by TMA in the 128-byte-swizzled K-major
+//     layout the MMA reads, streams the layers' weights from L2 in 64-wide K chunks through a 2-slot TMA
+//     ring and issues, per chunk, the tcgen05.mma (M = 128, K = 16) of both tiles against it, accumulating
+//     in TMEM (tile t in columns 256 t .. 256 t + 255: all 512 columns).  It requests the next layer's
+//     weights as soon as ring slots free up, while the epilogue of the current layer still runs, and only
+//     waits for that epilogue before the next layer's first MMA;
+//   * 16 epilogue warps (warp w: tile (w / 4) % 2, TMEM lanes 32 (w % 4) .., column half w / 8) read the
+//     accumulators once the layer's MMAs completed, add the bias, apply GELU and write the BF16
+//     activations back into the swizzled shared-memory layout as the next layer's A operand (the last
+//     layer writes the FP32 outputs), then arrive on the barrier the producer waits for.
+// Barriers: full/empty per ring slot, the inputs' barrier, layer done (MMAs complete; committed by the
+// producer) and activations ready (16 arrivals).  Shared memory: activations 2 x 64 KB, weight ring
+// 2 x 32 KB.  Every mbarrier wait is bounded; on a timeout the kernel sets the error flag, lets its copies
+// in flight land, frees TMEM and returns.
 #include "surrogate.h"
 #include "tc_ptx.cuh"
 
 namespace ck {
 
 namespace {
-constexpr int F_THREADS = 512;
-constexpr int F_PARTS = F_THREADS / 256;  // warps sharing a row quarter of a tile (column parts)
+constexpr int F_EPI_WARPS = 16;
+constexpr int F_PRODUCER = F_EPI_WARPS;                        // warp index of the producer
+constexpr int F_THREADS = 32 * (F_EPI_WARPS + 1);
+constexpr int F_PARTS = F_EPI_WARPS / 8;                       // epilogue warps per row quarter and tile
 constexpr uint32_t F_ACT_CHUNK = 128 * 128;                  // 128 rows x 64 BF16 = 16 KB
 constexpr uint32_t F_ACT_BYTES = 2 * 4 * F_ACT_CHUNK;         // 2 tiles x 4 K chunks
 constexpr uint32_t F_RING_SLOT = 256 * 128;                   // up to 256 weight rows x 64 BF16
@@ -38,7 +44,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                 const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
                 const __grid_constant__ CUtensorMap tW3, const __grid_constant__ CUtensorMap tW4, FusedArgs a) {
     extern __shared__ unsigned char fsm_raw[];
-    __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], x_bar, done_bar;
+    __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], x_bar, done_bar, act_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
     __shared__ __align__(16) float sbias[SUR_L][SUR_W];  // every layer's bias, read by the epilogue
@@ -47,6 +53,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     const CUtensorMap *tW[SUR_L] = {&tW0, &tW1, &tW2, &tW3, &tW4};
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long live = a.m_count ? min(a.n, (long long)__ldg(a.m_count)) : a.n;
+    volatile int *vfailed = &failed;
 
     for (int l = 0; l < SUR_L; ++l)
         for (int c = tid; c < SUR_W; c += F_THREADS) sbias[l][c] = c < (l == SUR_L - 1 ? 16 : SUR_W) ? a.bias[l][c] : 0.f;
@@ -57,6 +64,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         }
         mbar_init(smem_u32(&x_bar), 1);
         mbar_init(smem_u32(&done_bar), 1);
+        mbar_init(smem_u32(&act_bar), F_EPI_WARPS);
         failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -69,70 +77,99 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
+    const long long stride = (long long)gridDim.x * 256;
 
-    uint32_t G = 0;       // weight chunks loaded so far by this CTA (ring slot G & 1, use G >> 1)
-    uint32_t layers = 0;  // layers completed (phase of done_bar)
-    uint32_t iters = 0;   // tile pairs started (phase of x_bar)
-    uint32_t pending = 0; // chunks loaded and not yet consumed (drained after a timeout)
-    for (long long base = (long long)blockIdx.x * 256; base < live; base += (long long)gridDim.x * 256) {
-        if (tid == 0 && !failed) {
-            mbar_expect_tx(smem_u32(&x_bar), 2 * F_ACT_CHUNK);
-            tma_load_2d(smem_u32(act), &tX, 0, (int)base, smem_u32(&x_bar));
-            tma_load_2d(smem_u32(act + 4 * F_ACT_CHUNK), &tX, 0, (int)(base + 128), smem_u32(&x_bar));
-        }
-        for (int l = 0; l < SUR_L; ++l) {
-            const int nk = l == 0 ? 1 : 4, N = l == SUR_L - 1 ? 16 : SUR_W;
-            if (tid == 0 && !failed) {
-                const uint32_t idesc = bf16_idesc(N), G0 = G;
-                bool ok = true;
-                for (int it = 0; it <= nk && ok; ++it) {
-                    if (it < nk) {  // load chunk it of this layer's weights
-                        const uint32_t g = G0 + it, s = g & 1;
-                        if (g >= 2) ok = mbar_wait(smem_u32(&empty_bar[s]), ((g >> 1) - 1) & 1);
-                        if (!ok) break;
-                        mbar_expect_tx(smem_u32(&full_bar[s]), (uint32_t)N * 128);
-                        tma_load_2d(smem_u32(ring + s * F_RING_SLOT), tW[l], it * 64, 0, smem_u32(&full_bar[s]));
-                        ++pending;
-                        G = g + 1;
-                    }
-                    const int j = it - 1;
-                    if (j >= 0) {  // multiply chunk j for both tiles
-                        const uint32_t g = G0 + j, s = g & 1;
-                        ok = mbar_wait(smem_u32(&full_bar[s]), (g >> 1) & 1);
-                        if (ok && l == 0 && j == 0) ok = mbar_wait(smem_u32(&x_bar), iters & 1);
-                        if (!ok) break;
-                        --pending;
-                        asm volatile("tcgen05.fence::after_thread_sync;");
-                        const uint64_t bd = sw128_desc(smem_u32(ring + s * F_RING_SLOT));
-                        for (int t = 0; t < 2; ++t) {
-                            const uint64_t ad = sw128_desc(smem_u32(act + (t * 4 + j) * F_ACT_CHUNK));
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
-                                asm volatile(
-                                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * 256),
-                                    "l"(ad + (uint64_t)(2 * kk)), "l"(bd + (uint64_t)(2 * kk)), "r"(idesc), "r"(acc));
-                            }
+    if (warp == F_PRODUCER) {
+        if (lane == 0) {
+            uint32_t G = 0;        // weight chunks loaded so far (ring slot G & 1, use G >> 1)
+            uint32_t L = 0;        // layers whose MMAs were issued and committed (phase of done_bar / act_bar)
+            uint32_t iters = 0;    // tile pairs started (phase of x_bar)
+            uint32_t pending = 0;  // weight chunks loaded and not yet consumed (drained after a timeout)
+            bool x_pending = false;
+            bool ok = true;
+            for (long long base = (long long)blockIdx.x * 256; base < live && ok; base += stride) {
+                // the inputs overwrite the activations, which the previous pair's last layer's MMAs read
+                if (L > 0) ok = mbar_wait(smem_u32(&done_bar), (L - 1) & 1);
+                if (!ok || *vfailed) { ok = false; break; }
+                mbar_expect_tx(smem_u32(&x_bar), 2 * F_ACT_CHUNK);
+                tma_load_2d(smem_u32(act), &tX, 0, (int)base, smem_u32(&x_bar));
+                tma_load_2d(smem_u32(act + 4 * F_ACT_CHUNK), &tX, 0, (int)(base + 128), smem_u32(&x_bar));
+                x_pending = true;
+                for (int l = 0; l < SUR_L && ok; ++l) {
+                    const int nk = l == 0 ? 1 : 4, N = l == SUR_L - 1 ? 16 : SUR_W;
+                    const uint32_t idesc = bf16_idesc(N), G0 = G;
+                    for (int it = 0; it <= nk && ok; ++it) {
+                        if (it < nk) {  // load chunk it of this layer's weights into a free ring slot
+                            const uint32_t g = G0 + it, s = g & 1;
+                            if (g >= 2) ok = mbar_wait(smem_u32(&empty_bar[s]), ((g >> 1) - 1) & 1);
+                            if (!ok) break;
+                            mbar_expect_tx(smem_u32(&full_bar[s]), (uint32_t)N * 128);
+                            tma_load_2d(smem_u32(ring + s * F_RING_SLOT), tW[l], it * 64, 0, smem_u32(&full_bar[s]));
+                            ++pending;
+                            G = g + 1;
                         }
-                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                            smem_u32(&empty_bar[s])));
+                        const int j = it - 1;
+                        if (j >= 0) {  // multiply chunk j for both tiles
+                            const uint32_t g = G0 + j, s = g & 1;
+                            ok = mbar_wait(smem_u32(&full_bar[s]), (g >> 1) & 1);
+                            if (ok && j == 0) {
+                                // the previous layer's epilogue has read its accumulators and written this
+                                // layer's inputs
+                                if (L > 0) ok = mbar_wait(smem_u32(&act_bar), (L - 1) & 1);
+                                if (ok && l == 0) {
+                                    ok = mbar_wait(smem_u32(&x_bar), iters & 1);
+                                    if (ok) x_pending = false;
+                                }
+                            }
+                            if (!ok) break;
+                            --pending;
+                            asm volatile("tcgen05.fence::after_thread_sync;");
+                            const uint64_t bd = sw128_desc(smem_u32(ring + s * F_RING_SLOT));
+                            for (int t = 0; t < 2; ++t) {
+                                const uint64_t ad = sw128_desc(smem_u32(act + (t * 4 + j) * F_ACT_CHUNK));
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+                                    asm volatile(
+                                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * 256),
+                                        "l"(ad + (uint64_t)(2 * kk)), "l"(bd + (uint64_t)(2 * kk)), "r"(idesc), "r"(acc));
+                                }
+                            }
+                            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                smem_u32(&empty_bar[s])));
+                        }
                     }
+                    if (!ok) break;
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&done_bar)));
+                    ++L;
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&done_bar)));
-                if (!ok) failed = 1;
+                ++iters;
             }
-            __syncwarp();
-            const bool done = mbar_wait(smem_u32(&done_bar), layers & 1);
-            ++layers;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            // epilogue: warp w reads tile (w / 4) % 2, TMEM lanes 32 (w % 4) .. + 31 (one row per thread),
-            // columns of part w / 8
-            const int t = (warp >> 2) & 1, q = warp & 3, r = q * 32 + lane, part = warp >> 3;
-            const int cw = max(16, N / F_PARTS), c0 = part * cw, c1 = min(N, c0 + cw);
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
-            if (done && !failed) {
+            if (!ok) {
+                *vfailed = 1;
+                if (a.err) atomicExch(a.err, 1u);
+                // let the copies still in flight land before the shared memory is released (bounded)
+                for (uint32_t k = 0; k < pending; ++k)
+                    mbar_wait(smem_u32(&full_bar[(G - pending + k) & 1]), ((G - pending + k) >> 1) & 1);
+                if (x_pending) mbar_wait(smem_u32(&x_bar), iters & 1);
+            }
+        }
+    } else {
+        // epilogue: warp w reads tile (w / 4) % 2, TMEM lanes 32 (w % 4) .. + 31 (one row per thread), columns
+        // of part w / 8
+        const int t = (warp >> 2) & 1, q = warp & 3, r = q * 32 + lane, part = warp >> 3;
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
+        uint32_t L = 0;
+        bool ok = true;
+        for (long long base = (long long)blockIdx.x * 256; base < live && ok; base += stride) {
+            for (int l = 0; l < SUR_L; ++l) {
+                const int N = l == SUR_L - 1 ? 16 : SUR_W;
+                ok = mbar_wait(smem_u32(&done_bar), L & 1) && !*vfailed;
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int cw = max(16, N / F_PARTS), c0 = part * cw, c1 = min(N, c0 + cw);
                 const float *bias = sbias[l];
                 for (int c = c0; c < c1; c += 16) {
                     uint32_t u[16];
@@ -167,23 +204,16 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                         }
                     }
                 }
-                // the shared-memory writes must be visible to the tensor cores' (async) reads
+                // the shared-memory writes must be visible to the tensor cores' (async) reads, and the TMEM
+                // reads complete, before the producer's next MMAs
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            } else if (tid == 0) {
-                failed = 1;
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&act_bar));
+                ++L;
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            if (failed) break;
         }
-        ++iters;
-        if (failed) break;
-    }
-    if (failed && tid == 0) {
-        if (a.err) atomicExch(a.err, 1u);
-        // let the weight copies still in flight land before the shared memory is released (bounded)
-        for (uint32_t k = 0; k < pending; ++k) mbar_wait(smem_u32(&full_bar[(G - pending + k) & 1]), ((G - pending + k) >> 1) & 1);
+        if (!ok) *vfailed = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
