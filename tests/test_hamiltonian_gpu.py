@@ -77,3 +77,22 @@ def test_formulation_needs_fp64_and_a_cloak(ck):
     with pytest.raises(ck.CloakError):
         t.formulation(ck.FORM_HAMILTONIAN)
     t.close()
+
+
+def test_hamiltonian_batch_matches_single_renders(ck):
+    """The batched persistent form integrates the Hamiltonian form too: each view equals its own render."""
+    import torch
+    views, refs = [], []
+    for variant, pol, elev, W, H in ((0, 1, 20.0, 64, 40), (1, 0, 0.0, 48, 48), (1, 1, 45.0, 56, 30)):
+        eye, tgt, up = inputs.camera_pose(elev, 5.0)
+        c = ck.Cloak(variant).camera(eye, tgt, up, 60.0, W, H).integrator(ck.DP45, 1e-9, ck.FP64)
+        c.schedule(ck.SCHED_WAVEFRONT).formulation(ck.FORM_HAMILTONIAN)
+        refs.append(c.render(pol, 2, 9).cpu().numpy())
+        c.close()
+        views.append((variant, pol, eye, tgt, up, 60.0, torch.empty((H, W, 4), device="cuda")))
+    b = ck.Cloak(0).integrator(ck.DP45, 1e-9, ck.FP64).schedule(ck.SCHED_WAVEFRONT).formulation(ck.FORM_HAMILTONIAN)
+    ck.cloak_render_batch(b.h, views, 2, 9)
+    torch.cuda.synchronize()
+    b.close()
+    for (_, _, _, _, _, _, out), ref in zip(views, refs):
+        assert np.max(np.abs(out.cpu().numpy() - ref)) < 1e-6
