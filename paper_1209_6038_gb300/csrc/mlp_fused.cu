@@ -187,10 +187,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                         // (c % 64) / 8 and + 1 of row r, each XOR-ed with r % 8
                         uint32_t pk[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            __nv_bfloat162 h = __floats2bfloat162_rn(gelu_tanh(v[2 * i]), gelu_tanh(v[2 * i + 1]));
-                            pk[i] = *(uint32_t *)&h;
-                        }
+                        for (int i = 0; i < 8; ++i) pk[i] = gelu2_bf16(v[2 * i], v[2 * i + 1]);
                         unsigned char *chunk = act + (t * 4 + c / 64) * F_ACT_CHUNK + (r >> 3) * 1024 + (r & 7) * 128;
                         const int u0 = (c & 63) >> 3;
                         *(uint4 *)(chunk + (((u0) ^ (r & 7)) << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);

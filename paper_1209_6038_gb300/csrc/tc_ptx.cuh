@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -66,6 +68,21 @@ __device__ __forceinline__ float gelu_tanh(float x) {
     const float k0 = 0.7978845608028654f, k1 = 0.044715f;
     float u = k0 * (x + k1 * x * x * x);
     return 0.5f * x * (1.f + tanh_fast(u));
+}
+// GELU of two values in half-precision pair arithmetic (tanh.approx.f16x2: one hardware tanh for two values),
+// packed as BF16x2.  Half precision carries 11 significant bits against the 8 of the BF16 result it feeds;
+// inputs must stay below the half-precision range (|x| < 65504), where x^2 overflowing only saturates tanh.
+__device__ __forceinline__ uint32_t gelu2_bf16(float a, float b) {
+    const __half2 x = __floats2half2_rn(a, b);
+    const __half2 one = __float2half2_rn(1.f), k0 = __float2half2_rn(0.7978845608028654f),
+                  k1 = __float2half2_rn(0.044715f), half = __float2half2_rn(0.5f);
+    const __half2 u = __hmul2(__hmul2(k0, x), __hfma2(k1, __hmul2(x, x), one));  // k0 x (1 + k1 x^2)
+    __half2 th;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(*(uint32_t *)&th) : "r"(*(const uint32_t *)&u));
+    const __half2 hx = __hmul2(half, x);
+    const float2 g = __half22float2(__hfma2(hx, th, hx));  // x (1 + tanh) / 2
+    const __nv_bfloat162 o = __floats2bfloat162_rn(g.x, g.y);
+    return *(const uint32_t *)&o;
 }
 __device__ __forceinline__ float gelu_tanh_grad(float x) {
     const float k0 = 0.7978845608028654f, k1 = 0.044715f;
