@@ -913,9 +913,7 @@ __device__ __forceinline__ const double *analyzer_axis(const Params &p) {
 }
 
 // ------------------------------------------------------------------ room and camera
-// Procedural room: box x, y in [-10, 10], z in [-H/2, -H/2 + 10]; checkered walls and floor with
-// 8 tiles per unit and splitmix64-hashed tints; constant ceiling.  Returns the tile id.
-// Distance along the unit direction d from o to the room's box and the face reached (-1: none).
+// Distance along the unit direction d from o to the room's box (below) and the face reached (-1: none).
 __device__ __forceinline__ double room_distance(const Params &p, const double o[3], const double d[3], int &face) {
     const double Lb = 10.0, z0 = -p.halfH, z1 = z0 + 10.0;
     double best = 1e300, s;
@@ -928,6 +926,8 @@ __device__ __forceinline__ double room_distance(const Params &p, const double o[
     else if (d[2] > 0.0) { s = (z1 - o[2]) / d[2]; if (s < best) { best = s; face = 5; } }
     return best;
 }
+// Procedural room: box x, y in [-10, 10], z in [-H/2, -H/2 + 10]; checkered walls and floor with
+// 8 tiles per unit and splitmix64-hashed tints; constant ceiling.  Returns the tile id.
 __device__ __forceinline__ int room_hit(const Params &p, const double o[3], const double d[3], float rgb[3]) {
     const double Lb = 10.0, z0 = -p.halfH;
     int face;
