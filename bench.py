@@ -362,7 +362,7 @@ def formulation_section(args, ck, torch):
     point (sqrt(R2^2 - b^2), b, z), direction unchanged, optical time = the vacuum chord).  For each form
     and stepper setting (RK4 step h, DP5(4) tolerance) the section measures the largest relative error
     of exit point (/ R2), direction and time over all rays, and the time of one plain trace launch; then
-    reports, per form, the cheapest setting that reaches 1e-8 (the paper's Sect. 5 comparison)."""
+    reports, per form, the cheapest setting that reaches 1e-8 (the paper's Sect. 4 comparison)."""
     n = 1 << 17
     R2 = 1.0
     g = torch.Generator(device="cpu").manual_seed(2024)

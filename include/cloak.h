@@ -228,7 +228,7 @@ int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsigned long lo
  * The paper's images show the cylinder axis horizontal, here it is vertical (+z): its "vertical" goggles
  * (d), across the cylinder axis, are CLOAK_PANEL_POLARIZER_RIGHT at elevation 0; its "horizontal" ones (e)
  * are CLOAK_PANEL_POLARIZER_UP.
- *   CLOAK_PANEL_TOF          time-of-flight difference image (Sect. 5, the TOF images of its Ref. [10]):
+ *   CLOAK_PANEL_TOF          time-of-flight difference image (Sect. 4, the TOF images of its Ref. [10]):
  *                            per sample, the time (c0 = 1: vacuum path lengths plus the time of flight
  *                            inside the cloak) the light takes from the room point the sample sees to the
  *                            camera, minus the time from the room point the straight camera ray sees

@@ -385,7 +385,7 @@ def tof_difference(cloak: Cloak, o, d, rec) -> float:
 
 
 def tof_image(cloak: Cloak, integ: Integrator, cam: Camera, spp=1, seed=0, pixels=None, nthreads=None):
-    """Time-of-flight difference image (Sect. 5; the TOF images of Ref. [10]), per pixel:
+    """Time-of-flight difference image (Sect. 4; the TOF images of Ref. [10]), per pixel:
     (0) intensity-weighted mean TOF difference of the light of both polarizations, (1) of the ordinary
     and (2) of the extraordinary light alone, (3) the summed weight (mean over samples).  A sample that
     never enters the shell (it misses the cylinder or mirrors off a metal end disc) is the same light in

@@ -753,7 +753,7 @@ int orc_shade(const orc_cloak *c, const double p[3], const double d[3], double r
 }
 
 /* ------------------------------------------------------------------ */
-/* time-of-flight difference (Sect. 5; TOF images of Ref. [10])         */
+/* time-of-flight difference (Sect. 4; TOF images of Ref. [10])         */
 /* ------------------------------------------------------------------ */
 double orc_room_distance(const orc_cloak *c, const double p[3], const double d[3]) {
     /* nearest of the six planes of the room box that the ray moves towards */

@@ -136,7 +136,7 @@ void orc_render(const orc_cloak *c, const orc_integrator *in, const orc_camera *
                 int mode, int spp, uint64_t seed, const int64_t *pixels, long npix,
                 double *rgba, orc_record *recs, int nthreads);
 
-/* ---- time-of-flight difference images (Sect. 5, after Ref. [10]) ---- */
+/* ---- time-of-flight difference images (Sect. 4, after Ref. [10]) ---- */
 /* distance from p along the unit direction d to the room of orc_shade (INFINITY if none) */
 double orc_room_distance(const orc_cloak *c, const double p[3], const double d[3]);
 /* time of flight (c0 = 1) of the light a camera sample (o, d, its record) receives from the room, minus

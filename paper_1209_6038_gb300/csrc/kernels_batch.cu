@@ -153,7 +153,7 @@ __global__ void k_unpol_resolve(Params p, const ViewDev *views, int spp, unsigne
     out[g] = make_float4(a0 * inv, a1 * inv, a2 * inv, a3 * inv);
 }
 
-// Time-of-flight difference image (Sect. 5 after Ref. [10]) from the TOF samples (w dt, w) of views 0
+// Time-of-flight difference image (Sect. 4 after Ref. [10]) from the TOF samples (w dt, w) of views 0
 // (ordinary) and 1 (extraordinary) of one camera, per pixel: (0) intensity-weighted mean TOF difference
 // of both polarizations, a ray that never enters the shell counting once; (1) of the ordinary and (2) of
 // the extraordinary light alone; (3) the summed weight, mean over samples.  0 where no light arrives.

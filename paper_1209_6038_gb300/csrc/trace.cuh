@@ -13,7 +13,7 @@ __device__ __forceinline__ void set_vec(double *dst, const double *src) {
     dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
 }
 
-// Time-of-flight difference of one camera sample (TOF images, Sect. 5 after Ref. [10]); c0 = 1, so a time
+// Time-of-flight difference of one camera sample (TOF images, Sect. 4 after Ref. [10]); c0 = 1, so a time
 // of flight is a vacuum path length plus the time t spent inside the cloak.  The light the sample
 // receives travels from the room point its final vacuum ray reaches, back along that ray, through the
 // cloak and to the camera; subtracted is the time from the room point the straight camera ray reaches.

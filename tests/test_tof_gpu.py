@@ -1,4 +1,4 @@
-"""Time-of-flight difference images (Sect. 5 after Ref. [10]) on the GPU: the TOF panel against the
+"""Time-of-flight difference images (Sect. 4 after Ref. [10]) on the GPU: the TOF panel against the
 oracle's TOF images pixel by pixel, and the paper's expectation on the centre row of a level camera
 (extraordinary light arrives exactly when it would without the cylinder; through the polariser across
 the cylinder axis the whole pixel does)."""

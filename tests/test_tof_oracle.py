@@ -1,4 +1,4 @@
-"""Pins of the oracle's time-of-flight difference images (Sect. 5; the TOF images of Ref. [10]): room
+"""Pins of the oracle's time-of-flight difference images (Sect. 4; the TOF images of Ref. [10]): room
 distances by geometry, rays that miss, the metal end disc, the radial cloak's ordinary rays (straight
 lines in the index-2 medium, mirrored at the metal cylinder: a closed form), and the paper's expectation
 that in-plane extraordinary light arrives exactly when it would without the cylinder."""
