@@ -16,6 +16,7 @@
 // producer) and activations ready (16 arrivals).  Shared memory: activations 2 x 64 KB, weight ring
 // 2 x 32 KB.  Every mbarrier wait is bounded; on a timeout the kernel sets the error flag, lets its copies
 // in flight land, frees TMEM and returns.
+#include "device_once.h"
 #include "surrogate.h"
 #include "tc_ptx.cuh"
 
@@ -220,20 +221,22 @@ __global__ void __launch_bounds__(F_THREADS, 1)
 
 // forward pass of rows [0, n) of s->X into s->Y (rows beyond *m_count skipped when it is set)
 cudaError_t launch_mlp_fused(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st) {
-    static int max_dyn = 0, sms = 0;
-    if (!max_dyn) {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
+    static DeviceOnce once;
+    static int sms_of[MAX_DEVICES];
+    cudaError_t e0 = once.run([](int dev) {
+        int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&sms_of[dev], cudaDevAttrMultiProcessorCount, dev);
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, k_mlp_fused);
         if (e != cudaSuccess) return e;
         if ((size_t)(optin - (int)fa.sharedSizeBytes) < F_SMEM) return cudaErrorInvalidValue;
-        e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM);
-        if (e != cudaSuccess) return e;
-        max_dyn = (int)F_SMEM;
-    }
+        return cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM);
+    });
+    if (e0 != cudaSuccess) return e0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int sms = sms_of[dev];
     if (n <= 0 || n % 128) return cudaErrorInvalidValue;
     CUtensorMap tx;
     if (make_tmap_bf16(&tx, s->X, (int)n, 64, GEMM_TILE_M) != CUDA_SUCCESS) return cudaErrorInvalidValue;

@@ -1,6 +1,7 @@
 // mlp_tc.cu -- tcgen05 / TMEM / TMA BF16 GEMM (see mlp_tc.cuh).
 #include <cudaTypedefs.h>
 
+#include "device_once.h"
 #include "mlp_tc.cuh"
 #include "tc_ptx.cuh"
 
@@ -198,24 +199,23 @@ cudaError_t launch_gemm_tc(const CUtensorMap &ta, const CUtensorMap &tb, const G
         return cudaErrorInvalidValue;
     // Shared memory per CTA: the ring, padded so that no more CTAs share an SM than its 512 TMEM columns
     // hold (each allocates the power of two >= N, at least 32) -- an allocation never has to wait.
-    static int smem_sm = 0, reserved = 0, max_dyn = 0;
-    if (!smem_sm) {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    static DeviceOnce once;
+    static int smem_sm_of[MAX_DEVICES], reserved_of[MAX_DEVICES], max_dyn_of[MAX_DEVICES];
+    cudaError_t e0 = once.run([](int dev) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&smem_sm_of[dev], cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved_of[dev], cudaDevAttrReservedSharedMemoryPerBlock, dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, k_gemm_tc);
-        if (e == cudaSuccess) {
-            max_dyn = optin - (int)fa.sharedSizeBytes;  // the barriers are static shared memory
-            e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
-        }
-        if (e != cudaSuccess) {
-            smem_sm = 0;
-            return e;
-        }
-    }
+        if (e != cudaSuccess) return e;
+        max_dyn_of[dev] = optin - (int)fa.sharedSizeBytes;  // the barriers are static shared memory
+        return cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_of[dev]);
+    });
+    if (e0 != cudaSuccess) return e0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int smem_sm = smem_sm_of[dev], reserved = reserved_of[dev], max_dyn = max_dyn_of[dev];
     int ncols = 32;
     while (ncols < g.N) ncols <<= 1;
     const int max_ctas = 512 / ncols;

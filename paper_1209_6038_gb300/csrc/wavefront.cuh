@@ -464,16 +464,11 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
     // persistent integrator: exactly the resident grid
-    static int blocks_per_sm[33] = {0};
-    int pk = packet > 0 ? packet : 128;
-    int slot = pk / 32;
-    if (blocks_per_sm[slot] == 0) {
-        int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V, M, I, PREC>, pk, 0);
-        if (e != cudaSuccess) return e;
-        blocks_per_sm[slot] = nb > 0 ? nb : 1;
-    }
-    k_wf_integrate<V, M, I, PREC><<<blocks_per_sm[slot] * sms, pk, 0, st>>>(p, q);
+    const int pk = packet > 0 ? packet : 128;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V, M, I, PREC>, pk, 0);
+    if (e != cudaSuccess) return e;
+    k_wf_integrate<V, M, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(p, q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);
