@@ -1,19 +1,20 @@
 // mlp_fused.cu -- the surrogate network's forward pass as ONE persistent tcgen05 kernel.
 //
 // Each CTA (one per SM) takes pairs of 128-row tiles through all five layers without their activations
-// leaving the SM.  Warp-specialised:
-//   * the producer warp (one thread) loads the inputs of both tiles by TMA in the 128-byte-swizzled K-major
-//     layout the MMA reads, streams the layers' weights from L2 in 64-wide K chunks through a 2-slot TMA
-//     ring and issues, per chunk, the tcgen05.mma (M = 128, K = 16) of both tiles against it, accumulating
-//     in TMEM (tile t in columns 256 t .. 256 t + 255: all 512 columns).  It requests the next layer's
-//     weights as soon as ring slots free up, while the epilogue of the current layer still runs, and only
-//     waits for that epilogue before the next layer's first MMA;
-//   * 16 epilogue warps (warp w: tile (w / 4) % 2, TMEM lanes 32 (w % 4) .., column half w / 8) read the
-//     accumulators once the layer's MMAs completed, add the bias, apply GELU and write the BF16
-//     activations back into the swizzled shared-memory layout as the next layer's A operand (the last
-//     layer writes the FP32 outputs), then arrive on the barrier the producer waits for.
-// Barriers: full/empty per ring slot, the inputs' barrier, layer done (MMAs complete; committed by the
-// producer) and activations ready (16 arrivals).  Shared memory: activations 2 x 64 KB, weight ring
+// leaving the SM.  Warp-specialised, the two tiles of a pair in ping-pong:
+//   * the producer warp (one thread) works through the jobs (tile 0, layer 0), (tile 1, layer 0),
+//     (tile 0, layer 1), ...: for each it streams the layer's weights from L2 in 64-wide K chunks through a
+//     2-slot TMA ring and issues, per chunk, the tcgen05.mma (M = 128, K = 16) of that tile, accumulating
+//     in its TMEM columns (tile t: 256 t .. 256 t + 255).  Before a job's first MMA it waits only for the
+//     epilogue of the same tile's previous layer, so the MMAs of one tile run while the epilogue of the
+//     other tile runs.  It also loads the inputs of both tiles by TMA in the 128-byte-swizzled K-major
+//     layout the MMA reads;
+//   * 16 epilogue warps take the jobs in the same order (warp w: TMEM lanes 32 (w % 4) .., column quarter
+//     w / 4): they read the tile's accumulators once its MMAs completed, add the bias, apply GELU and write
+//     the BF16 activations back into the swizzled shared-memory layout as the tile's next A operand (the
+//     last layer writes the FP32 outputs), then arrive on the tile's barrier the producer waits for.
+// Barriers: full/empty per ring slot; per tile the inputs' barrier, "MMAs done" (committed by the
+// producer) and "activations ready" (16 arrivals).  Shared memory: activations 2 x 64 KB, weight ring
 // 2 x 32 KB.  Every mbarrier wait is bounded; on a timeout the kernel sets the error flag, lets its copies
 // in flight land, frees TMEM and returns.
 #include "device_once.h"
@@ -26,7 +27,7 @@ namespace {
 constexpr int F_EPI_WARPS = 16;
 constexpr int F_PRODUCER = F_EPI_WARPS;                        // warp index of the producer
 constexpr int F_THREADS = 32 * (F_EPI_WARPS + 1);
-constexpr int F_PARTS = F_EPI_WARPS / 8;                       // epilogue warps per row quarter and tile
+constexpr int F_PARTS = F_EPI_WARPS / 4;                       // epilogue warps per row quarter (column parts)
 constexpr uint32_t F_ACT_CHUNK = 128 * 128;                  // 128 rows x 64 BF16 = 16 KB
 constexpr uint32_t F_ACT_BYTES = 2 * 4 * F_ACT_CHUNK;         // 2 tiles x 4 K chunks
 constexpr uint32_t F_RING_SLOT = 256 * 128;                   // up to 256 weight rows x 64 BF16
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                 const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
                 const __grid_constant__ CUtensorMap tW3, const __grid_constant__ CUtensorMap tW4, FusedArgs a) {
     extern __shared__ unsigned char fsm_raw[];
-    __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], x_bar, done_bar, act_bar;
+    __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], x_bar[2], done_bar[2], act_bar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
     __shared__ __align__(16) float sbias[SUR_L][SUR_W];  // every layer's bias, read by the epilogue
@@ -62,10 +63,10 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
+            mbar_init(smem_u32(&x_bar[s]), 1);
+            mbar_init(smem_u32(&done_bar[s]), 1);
+            mbar_init(smem_u32(&act_bar[s]), F_EPI_WARPS);
         }
-        mbar_init(smem_u32(&x_bar), 1);
-        mbar_init(smem_u32(&done_bar), 1);
-        mbar_init(smem_u32(&act_bar), F_EPI_WARPS);
         failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -82,21 +83,23 @@ __global__ void __launch_bounds__(F_THREADS, 1)
 
     if (warp == F_PRODUCER) {
         if (lane == 0) {
-            uint32_t G = 0;        // weight chunks loaded so far (ring slot G & 1, use G >> 1)
-            uint32_t L = 0;        // layers whose MMAs were issued and committed (phase of done_bar / act_bar)
-            uint32_t iters = 0;    // tile pairs started (phase of x_bar)
-            uint32_t pending = 0;  // weight chunks loaded and not yet consumed (drained after a timeout)
-            bool x_pending = false;
+            uint32_t G = 0;          // weight chunks loaded so far (ring slot G & 1, use G >> 1)
+            uint32_t Lt[2] = {0, 0}; // jobs committed per tile (phases of done_bar[t] / act_bar[t])
+            uint32_t iters = 0;      // tile pairs started (phase of x_bar[t])
+            uint32_t pending = 0;    // weight chunks loaded and not yet consumed (drained after a timeout)
+            bool x_pending[2] = {false, false};
             bool ok = true;
             for (long long base = (long long)blockIdx.x * 256; base < live && ok; base += stride) {
-                // the inputs overwrite the activations, which the previous pair's last layer's MMAs read
-                if (L > 0) ok = mbar_wait(smem_u32(&done_bar), (L - 1) & 1);
-                if (!ok || *vfailed) { ok = false; break; }
-                mbar_expect_tx(smem_u32(&x_bar), 2 * F_ACT_CHUNK);
-                tma_load_2d(smem_u32(act), &tX, 0, (int)base, smem_u32(&x_bar));
-                tma_load_2d(smem_u32(act + 4 * F_ACT_CHUNK), &tX, 0, (int)(base + 128), smem_u32(&x_bar));
-                x_pending = true;
-                for (int l = 0; l < SUR_L && ok; ++l) {
+                // a tile's inputs overwrite its activations, which its previous last-layer MMAs read
+                for (int t = 0; t < 2 && ok; ++t) {
+                    if (Lt[t] > 0) ok = mbar_wait(smem_u32(&done_bar[t]), (Lt[t] - 1) & 1);
+                    if (!ok || *vfailed) { ok = false; break; }
+                    mbar_expect_tx(smem_u32(&x_bar[t]), F_ACT_CHUNK);
+                    tma_load_2d(smem_u32(act + t * 4 * F_ACT_CHUNK), &tX, 0, (int)(base + 128 * t), smem_u32(&x_bar[t]));
+                    x_pending[t] = true;
+                }
+                for (int job = 0; job < 2 * SUR_L && ok; ++job) {
+                    const int l = job >> 1, t = job & 1;
                     const int nk = l == 0 ? 1 : 4, N = l == SUR_L - 1 ? 16 : SUR_W;
                     const uint32_t idesc = bf16_idesc(N), G0 = G;
                     for (int it = 0; it <= nk && ok; ++it) {
@@ -110,32 +113,29 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                             G = g + 1;
                         }
                         const int j = it - 1;
-                        if (j >= 0) {  // multiply chunk j for both tiles
+                        if (j >= 0) {  // multiply chunk j for tile t
                             const uint32_t g = G0 + j, s = g & 1;
                             ok = mbar_wait(smem_u32(&full_bar[s]), (g >> 1) & 1);
                             if (ok && j == 0) {
-                                // the previous layer's epilogue has read its accumulators and written this
-                                // layer's inputs
-                                if (L > 0) ok = mbar_wait(smem_u32(&act_bar), (L - 1) & 1);
+                                // the tile's previous epilogue has read its accumulators and written these inputs
+                                if (Lt[t] > 0) ok = mbar_wait(smem_u32(&act_bar[t]), (Lt[t] - 1) & 1);
                                 if (ok && l == 0) {
-                                    ok = mbar_wait(smem_u32(&x_bar), iters & 1);
-                                    if (ok) x_pending = false;
+                                    ok = mbar_wait(smem_u32(&x_bar[t]), iters & 1);
+                                    if (ok) x_pending[t] = false;
                                 }
                             }
                             if (!ok) break;
                             --pending;
                             asm volatile("tcgen05.fence::after_thread_sync;");
                             const uint64_t bd = sw128_desc(smem_u32(ring + s * F_RING_SLOT));
-                            for (int t = 0; t < 2; ++t) {
-                                const uint64_t ad = sw128_desc(smem_u32(act + (t * 4 + j) * F_ACT_CHUNK));
+                            const uint64_t ad = sw128_desc(smem_u32(act + (t * 4 + j) * F_ACT_CHUNK));
 #pragma unroll
-                                for (int kk = 0; kk < 4; ++kk) {
-                                    const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
-                                    asm volatile(
-                                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * 256),
-                                        "l"(ad + (uint64_t)(2 * kk)), "l"(bd + (uint64_t)(2 * kk)), "r"(idesc), "r"(acc));
-                                }
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+                                asm volatile(
+                                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * 256),
+                                    "l"(ad + (uint64_t)(2 * kk)), "l"(bd + (uint64_t)(2 * kk)), "r"(idesc), "r"(acc));
                             }
                             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                 smem_u32(&empty_bar[s])));
@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                     }
                     if (!ok) break;
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        smem_u32(&done_bar)));
-                    ++L;
+                        smem_u32(&done_bar[t])));
+                    ++Lt[t];
                 }
                 ++iters;
             }
@@ -154,22 +154,23 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                 // let the copies still in flight land before the shared memory is released (bounded)
                 for (uint32_t k = 0; k < pending; ++k)
                     mbar_wait(smem_u32(&full_bar[(G - pending + k) & 1]), ((G - pending + k) >> 1) & 1);
-                if (x_pending) mbar_wait(smem_u32(&x_bar), iters & 1);
+                for (int t = 0; t < 2; ++t)
+                    if (x_pending[t]) mbar_wait(smem_u32(&x_bar[t]), iters & 1);
             }
         }
     } else {
-        // epilogue: warp w reads tile (w / 4) % 2, TMEM lanes 32 (w % 4) .. + 31 (one row per thread), columns
-        // of part w / 8
-        const int t = (warp >> 2) & 1, q = warp & 3, r = q * 32 + lane, part = warp >> 3;
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
-        uint32_t L = 0;
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one row per thread), column quarter w / 4
+        const int q = warp & 3, r = q * 32 + lane, part = warp >> 2;
+        uint32_t Lt[2] = {0, 0};
         bool ok = true;
         for (long long base = (long long)blockIdx.x * 256; base < live && ok; base += stride) {
-            for (int l = 0; l < SUR_L; ++l) {
+            for (int job = 0; job < 2 * SUR_L; ++job) {
+                const int l = job >> 1, t = job & 1;
                 const int N = l == SUR_L - 1 ? 16 : SUR_W;
-                ok = mbar_wait(smem_u32(&done_bar), L & 1) && !*vfailed;
+                ok = mbar_wait(smem_u32(&done_bar[t]), Lt[t] & 1) && !*vfailed;
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
                 const int cw = max(16, N / F_PARTS), c0 = part * cw, c1 = min(N, c0 + cw);
                 const float *bias = sbias[l];
                 for (int c = c0; c < c1; c += 16) {
@@ -203,12 +204,12 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                     }
                 }
                 // the shared-memory writes must be visible to the tensor cores' (async) reads, and the TMEM
-                // reads complete, before the producer's next MMAs
+                // reads complete, before the producer's next MMAs of this tile
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&act_bar));
-                ++L;
+                if (lane == 0) mbar_arrive(smem_u32(&act_bar[t]));
+                ++Lt[t];
             }
         }
         if (!ok) *vfailed = 1;
