@@ -173,34 +173,49 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
                 const int cw = max(16, N / F_PARTS), c0 = part * cw, c1 = min(N, c0 + cw);
                 const float *bias = sbias[l];
-                for (int c = c0; c < c1; c += 16) {
+                if (l < SUR_L - 1) {
+                    for (int c = c0; c < c1; c += 32) {  // 32 columns per TMEM load (parts are 64 wide)
+                        uint32_t u[32];
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                            : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                              "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+                              "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]),
+                              "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]),
+                              "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+                            : "r"(taddr + (uint32_t)c));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        // GELU, BF16, into the 128-byte-swizzled K-major layout of chunk c / 64: 16-byte units
+                        // (c % 64) / 8 .. + 3 of row r, each XOR-ed with r % 8
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            pk[i] = gelu2_bf16(__uint_as_float(u[2 * i]) + bias[c + 2 * i],
+                                               __uint_as_float(u[2 * i + 1]) + bias[c + 2 * i + 1]);
+                        unsigned char *chunk = act + (t * 4 + c / 64) * F_ACT_CHUNK + (r >> 3) * 1024 + (r & 7) * 128;
+                        const int u0 = (c & 63) >> 3;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            *(uint4 *)(chunk + (((u0 + k) ^ (r & 7)) << 4)) =
+                                make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+                    }
+                } else if (c0 < c1) {  // the 16 outputs in FP32
                     uint32_t u[16];
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                         : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
                           "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
-                        : "r"(taddr + (uint32_t)c));
+                        : "r"(taddr));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    float v[16];
+                    const long long row = base + t * 128 + r;
+                    if (row < live) {
+                        float4 *y = (float4 *)(a.Y + row * 16);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(u[i]) + bias[c + i];
-                    if (l < SUR_L - 1) {
-                        // GELU, BF16, into the 128-byte-swizzled K-major layout of chunk c / 64: 16-byte units
-                        // (c % 64) / 8 and + 1 of row r, each XOR-ed with r % 8
-                        uint32_t pk[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) pk[i] = gelu2_bf16(v[2 * i], v[2 * i + 1]);
-                        unsigned char *chunk = act + (t * 4 + c / 64) * F_ACT_CHUNK + (r >> 3) * 1024 + (r & 7) * 128;
-                        const int u0 = (c & 63) >> 3;
-                        *(uint4 *)(chunk + (((u0) ^ (r & 7)) << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        *(uint4 *)(chunk + (((u0 + 1) ^ (r & 7)) << 4)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                    } else {
-                        const long long row = base + t * 128 + r;
-                        if (row < live) {
-                            float4 *y = (float4 *)(a.Y + row * 16);
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) y[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                        }
+                        for (int i = 0; i < 4; ++i)
+                            y[i] = make_float4(__uint_as_float(u[4 * i]) + bias[4 * i], __uint_as_float(u[4 * i + 1]) + bias[4 * i + 1],
+                                               __uint_as_float(u[4 * i + 2]) + bias[4 * i + 2],
+                                               __uint_as_float(u[4 * i + 3]) + bias[4 * i + 3]);
                     }
                 }
                 // the shared-memory writes must be visible to the tensor cores' (async) reads, and the TMEM
