@@ -187,7 +187,7 @@ typedef struct cloak_view {
  * seed, integrator, precision, packet) is seen and replayed on later identical calls.  The handle's
  * variant must be CLOAK_RADIAL or CLOAK_AZIMUTHAL; integrator, precision and packet come from the
  * handle.  views: host array of nviews >= 1 entries (read during the call); total samples
- * sum(width*height*spp) <= 2^31 - 1.  Scratch: about 104 bytes per sample, owned by the handle.
+ * sum(width*height*spp) <= 2^31 - 1.  Scratch: about 128 bytes per sample, owned by the handle.
  * Every view's output is written on cuda_stream.  With stage timing on, cloak_stage_times reports the
  * stages of the last batch (events recorded inside the graph). */
 int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
@@ -206,7 +206,7 @@ int cloak_mlp_gemm(const void *dev_a, const void *dev_b, float *dev_c, int M, in
  * synchronisation of cudaMalloc / cudaFree, or programs that must not grow their footprint after
  * start-up.  It renders exactly like cloak_render on the wavefront schedule (the handle's camera,
  * integrator and precision), but its queue and per-sample buffer live in one fixed device array
- * inside the library (104 MiB + 4 KiB, held on every GPU that loads the library until the process
+ * inside the library (128 MiB + 4 KiB, held on every GPU that loads the library until the process
  * exits) instead of handle scratch, and it calls no cudaMalloc, cudaFree or allocating routine.
  * Limit: width*height*spp <= 1048576 samples, else CLOAK_EINVAL before any launch.  The caller still
  * passes the output (dev_rgba, float4[width*height], bytes >= 16*width*height).  The first call on a

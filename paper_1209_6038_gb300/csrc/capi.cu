@@ -776,7 +776,7 @@ extern "C" int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long 
 // resolved once per device with cudaGetSymbolAddress and passed to the kernels.
 // ---------------------------------------------------------------------------------------------
 static constexpr long long NOALLOC_MAX_SAMPLES = 1LL << 20;  // width * height * spp
-static constexpr size_t NOALLOC_BYTES = ck::QUEUE_HEADER_BYTES + (size_t)NOALLOC_MAX_SAMPLES * ck::QUEUE_SLOT_BYTES;
+static constexpr size_t NOALLOC_BYTES = ck::queue_bytes(NOALLOC_MAX_SAMPLES);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 static constexpr int NOALLOC_MAX_DEVICES = 64;

@@ -29,11 +29,17 @@ struct Stepper64 {
     bool need_k1;
     int vm;  // 2 * variant + mode when VAR = MODE = V_ANY
 
-    __device__ __forceinline__ void load(const double *x, const double *yy, const double *z, const double *vx,
-                                         const double *vy, const double *vz, int k) {
-        y[0] = x[k]; y[1] = yy[k]; y[2] = z[k];
-        y[3] = vx[k]; y[4] = vy[k]; y[5] = vz[k];
-        need_k1 = true;
+    // state of queue slot k; the first stage comes with it when the entry kernel computed it (Fermat form)
+    template <typename Q>
+    __device__ __forceinline__ void load(const Q &q, int k) {
+        y[0] = q.x[k]; y[1] = q.y[k]; y[2] = q.z[k];
+        y[3] = q.vx[k]; y[4] = q.vy[k]; y[5] = q.vz[k];
+        const double a0 = q.ax[k];
+        need_k1 = a0 != a0;
+        if (!need_k1) {
+            k1[0] = y[3]; k1[1] = y[4]; k1[2] = y[5];
+            k1[3] = a0; k1[4] = q.ay[k]; k1[5] = q.az[k];
+        }
     }
     __device__ __forceinline__ void eval(const Params &p, double s) {
         if (INTEG == I_RK4) {
@@ -180,9 +186,9 @@ struct StepperMixed {
     bool need_k1;
     int vm;  // 2 * variant + mode when VAR = MODE = V_ANY
 
-    __device__ __forceinline__ void load(const double *x, const double *yy, const double *z, const double *vx,
-                                         const double *vy, const double *vz, int k) {
-        double v[6] = {x[k], yy[k], z[k], vx[k], vy[k], vz[k]};
+    template <typename Q>
+    __device__ __forceinline__ void load(const Q &q, int k) {
+        double v[6] = {q.x[k], q.y[k], q.z[k], q.vx[k], q.vy[k], q.vz[k]};
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             yh[i] = (float)v[i];

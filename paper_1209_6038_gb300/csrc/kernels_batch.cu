@@ -67,7 +67,10 @@ __global__ void __launch_bounds__(128) k_batch_entry(Params p, const ViewDev *vi
     double w_out = transmission_out(mode, mat[0], mat[1], c, n_in, mk0, axis);
     // queue key: medium/mode (major: one segment of the sorted queue per medium) and cost bucket (minor,
     // slowest first within a segment after the descending sort)
-    queue_append(q, y, w_out, (int)g, batch_key(vw.vm, cost_bucket(y, k0)));
+    double dy[6];
+    const bool first = p.precision == 0 && p.formulation == 0;  // the FP64 Fermat stepper's first stage
+    if (first) rhs<V_ANY, V_ANY>(pv, y, dy, vw.vm);
+    queue_append(q, y, w_out, (int)g, batch_key(vw.vm, cost_bucket(y, k0)), first ? dy + 3 : nullptr);
 }
 
 __global__ void __launch_bounds__(128) k_batch_exit(Params p, const ViewDev *views, int nviews, int spp,

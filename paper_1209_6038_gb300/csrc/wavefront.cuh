@@ -30,6 +30,7 @@ namespace ck {
 // queue slot layout (structure of arrays; capacity = rays per image)
 struct Queue {
     double *x, *y, *z, *vx, *vy, *vz;  // state on entry; final state after B
+    double *ax, *ay, *az;              // dv/dt at the entry state (Fermat form, FP64), NaN where not computed
     double *w_out;                     // Eq. 12 factor of the entry face (physical exit towards the camera)
     double *t;                         // time of flight after B
     int *id;                           // sample index (pixel * spp + sample)
@@ -51,8 +52,12 @@ constexpr int SEG_OFFSET = 2 * NBINS_BATCH;
 __host__ __device__ constexpr int batch_key(int vm, int cost) { return vm * NBINS + cost; }
 __host__ __device__ constexpr int key_vm(int key) { return key / NBINS; }
 constexpr size_t QUEUE_HEADER_BYTES = 4096;
-constexpr size_t QUEUE_SLOT_BYTES = 8 * sizeof(double) + 6 * sizeof(int) + sizeof(float4);
-inline size_t queue_bytes(long long cap) { return QUEUE_HEADER_BYTES + (size_t)cap * QUEUE_SLOT_BYTES; }
+// every array of the queue starts on a 256-byte boundary (the float4 per-sample buffer needs 16 bytes)
+constexpr size_t queue_array_bytes(long long cap, size_t elem) { return ((size_t)cap * elem + 255) & ~(size_t)255; }
+constexpr size_t queue_bytes(long long cap) {
+    return QUEUE_HEADER_BYTES + 11 * queue_array_bytes(cap, sizeof(double)) + queue_array_bytes(cap, sizeof(float4)) +
+           6 * queue_array_bytes(cap, sizeof(int));
+}
 
 // Lay the queue, its sort arrays and the per-sample buffer out in `base` (queue_bytes(cap) bytes,
 // 256-byte aligned).  The header (counters and bins) must be zeroed before each render.
@@ -60,12 +65,12 @@ inline void carve_queue(char *base, long long cap, Queue &q, float4 **samples) {
     q.count = (unsigned int *)base;
     q.bins = (unsigned int *)(base + 64);
     char *b = base + QUEUE_HEADER_BYTES;
-    double **dp[8] = {&q.x, &q.y, &q.z, &q.vx, &q.vy, &q.vz, &q.w_out, &q.t};
-    for (int i = 0; i < 8; ++i) { *dp[i] = (double *)b; b += (size_t)cap * sizeof(double); }
+    double **dp[11] = {&q.x, &q.y, &q.z, &q.vx, &q.vy, &q.vz, &q.ax, &q.ay, &q.az, &q.w_out, &q.t};
+    for (int i = 0; i < 11; ++i) { *dp[i] = (double *)b; b += queue_array_bytes(cap, sizeof(double)); }
     *samples = (float4 *)b;
-    b += (size_t)cap * sizeof(float4);
+    b += queue_array_bytes(cap, sizeof(float4));
     int **ip[6] = {&q.id, &q.status, &q.steps, &q.face, &q.key, &q.perm};
-    for (int i = 0; i < 6; ++i) { *ip[i] = (int *)b; b += (size_t)cap * sizeof(int); }
+    for (int i = 0; i < 6; ++i) { *ip[i] = (int *)b; b += queue_array_bytes(cap, sizeof(int)); }
     q.cap = cap;
 }
 
@@ -94,7 +99,10 @@ __device__ __forceinline__ void store_tof_sample(const Params &p, float4 *sample
 }
 
 // Append an entering ray to the queue; one atomic per warp for the slot and one per distinct key.
-__device__ __forceinline__ void queue_append(const Queue &q, const double y[6], double w_out, int id, int key) {
+// a: dv/dt at y (the integrator's first stage, computed here where every lane of the warp has one), or
+// null.
+__device__ __forceinline__ void queue_append(const Queue &q, const double y[6], double w_out, int id, int key,
+                                             const double *a = nullptr) {
     const unsigned int act = __activemask();
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(act) - 1;
@@ -104,6 +112,9 @@ __device__ __forceinline__ void queue_append(const Queue &q, const double y[6], 
     unsigned int slot = base + __popc(act & ((1u << lane) - 1u));
     q.x[slot] = y[0]; q.y[slot] = y[1]; q.z[slot] = y[2];
     q.vx[slot] = y[3]; q.vy[slot] = y[4]; q.vz[slot] = y[5];
+    q.ax[slot] = a ? a[0] : __longlong_as_double(0x7ff8000000000000ll);
+    q.ay[slot] = a ? a[1] : 0.0;
+    q.az[slot] = a ? a[2] : 0.0;
     q.w_out[slot] = w_out;
     q.id[slot] = id;
     q.key[slot] = key;
@@ -131,7 +142,10 @@ __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned lo
     // Eq. 12 at the entry face along the physical direction: light leaves the cloak towards the camera
     double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
     double w_out = transmission_out(MODE, mat[0], mat[1], c, n_in, mk0, analyzer_axis(p));
-    queue_append(q, y, w_out, (int)idx, cost_bucket(y, k0));
+    double dy[6];
+    const bool first = p.precision == 0 && p.formulation == 0;  // the FP64 Fermat stepper's first stage
+    if (first) rhs<VAR, MODE>(p, y, dy);
+    queue_append(q, y, w_out, (int)idx, cost_bucket(y, k0), first ? dy + 3 : nullptr);
 }
 
 // Longest-first order: a counting sort of the queue by descending key.  k_wf_sort_scan turns the bucket
@@ -203,7 +217,7 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                 }
             }
             if (phase == PH_STEP) {
-                st.load(q.x, q.y, q.z, q.vx, q.vy, q.vz, slot);
+                st.load(q, slot);
                 h = h0; t = 0; steps = 0; metal = false;
             }
         }
