@@ -585,13 +585,18 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
         return fail(CLOAK_ESTATE, "batched rendering needs a radial or azimuthal cloak handle");
     if (!views || nviews < 1 || nviews > 65536) return fail(CLOAK_EINVAL, "need 1..65536 views");
     if (spp < 1 || spp > 65536) return fail(CLOAK_EINVAL, "spp must be in [1, 65536]");
-    if (h->precision == CLOAK_SURROGATE)
-        return fail(CLOAK_EINVAL, "the learned surrogate runs in cloak_render and cloak_render_records");
     ck::Params p;
     int rc = make_params(h, p);
     if (rc) return rc;
     p.analyzer = analyzer;
     p.tof = tof;
+    // learned surrogate: rays it is confident about leave the queue before the integration (the
+    // integrator handles the rest, and everything when the network was trained on another geometry)
+    const bool sur = h->precision == CLOAK_SURROGATE && tof == 0 && h->sur && h->sur->trained &&
+                     std::fabs(h->sur->R1 - h->R1) <= 1e-12 * h->R2 && std::fabs(h->sur->R2 - h->R2) <= 1e-12 * h->R2 &&
+                     std::fabs(h->sur->H - h->H) <= 1e-12 * h->H;
+    if (h->precision == CLOAK_SURROGATE && !(h->sur && h->sur->trained))
+        return fail(CLOAK_ESTATE, "CLOAK_SURROGATE needs a trained surrogate");
     std::vector<ck::ViewDev> table((size_t)nviews);
     long long total = 0, total_pix = 0;
     for (int i = 0; i < nviews; ++i) {
@@ -607,14 +612,24 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
     float4 *samples = nullptr;
     if ((rc = wavefront_scratch(h, total, q, &samples))) return rc;
     if (q_out) *q_out = q;
+    if (sur) {  // the network's buffers for every queued ray and its kernel set up, before any capture
+        cudaError_t e = ck::sur_ensure_inference(h->sur, total);
+        if (e == cudaSuccess) e = ck::mlp_fused_prepare();
+        if (e != cudaSuccess) return cuda_fail(e, "surrogate buffers");
+    }
     size_t tbytes = table.size() * sizeof(ck::ViewDev);
     unsigned long long key = 1469598103934665603ull;
     key = fnv1a(key, table.data(), tbytes);
     key = fnv1a(key, &p, sizeof(p));
-    int extra[4] = {spp, h->packet, nviews, h->timing};
+    int extra[5] = {spp, h->packet, nviews, h->timing, sur ? 1 : 0};
     key = fnv1a(key, extra, sizeof(extra));
     key = fnv1a(key, &seed, sizeof(seed));
     key = fnv1a(key, &h->scratch, sizeof(h->scratch));
+    if (sur) {  // the captured launches hold the network's buffers and the gate
+        const void *bufs[3] = {h->sur->X, h->sur->Y, h->sur->elig};
+        key = fnv1a(key, bufs, sizeof(bufs));
+        key = fnv1a(key, &h->sur->gate, sizeof(h->sur->gate));
+    }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     cudaError_t e;
     if (!h->graph_exec || key != h->graph_key) {
@@ -647,9 +662,23 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
         if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return cuda_fail(e, "cudaStreamBeginCapture");
         cudaError_t e1 = cudaMemcpyAsync(h->batch_dev, h->batch_host, tbytes, cudaMemcpyHostToDevice, h->cap_stream);
+        ck::SurRenderCtx sctx;
+        ck::WfHook hook{ck::sur_render_hook, &sctx};
+        if (sur) {
+            sctx.s = h->sur;
+            sctx.p = p;
+            sctx.mode = 0;
+            sctx.spp = spp;
+            sctx.seed = seed;
+            sctx.samples = samples;
+            sctx.recs = nullptr;
+            sctx.cap = total;
+            sctx.views = (const ck::ViewDev *)h->batch_dev;
+            sctx.nviews = nviews;
+        }
         cudaError_t e2 = e1 == cudaSuccess ? ck::launch_batch(p, (const ck::ViewDev *)h->batch_dev, nviews, spp, seed,
                                                              total, total_pix, q, samples, h->packet, h->cap_stream,
-                                                             h->timing ? h->ev : nullptr)
+                                                             h->timing ? h->ev : nullptr, sur ? &hook : nullptr)
                                            : e1;
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(h->cap_stream, &graph);

@@ -8,36 +8,6 @@
 
 namespace ck {
 
-__device__ __forceinline__ int find_view(const ViewDev *v, int n, long long g, bool by_pixel) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        long long b = by_pixel ? v[mid].pix_begin : v[mid].ray_begin;
-        if (b <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ void view_camera_ray(const ViewDev &v, int i, int j, int s, int spp, uint64_t seed,
-                                                double o[3], double d[3]) {
-    double xi1 = 0.5, xi2 = 0.5;
-    if (spp > 1) {
-        uint64_t pix = uint64_t(j) * uint64_t(v.W) + uint64_t(i);
-        xi1 = jitter(seed, pix, s, 0);
-        xi2 = jitter(seed, pix, s, 1);
-    }
-    double px = (2.0 * (i + xi1) / v.W - 1.0) * v.tx;
-    double py = (1.0 - 2.0 * (j + xi2) / v.Hp) * v.ty;
-    double l2 = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        d[k] = v.fw[k] + px * v.rt[k] + py * v.up[k];
-        l2 += d[k] * d[k];
-    }
-    double il = 1.0 / sqrt(l2);
-    for (int k = 0; k < 3; ++k) { d[k] *= il; o[k] = v.eye[k]; }
-}
-
 __global__ void __launch_bounds__(128) k_batch_entry(Params p, const ViewDev *views, int nviews, int spp,
                                                      unsigned long long seed, long long total, Queue q,
                                                      float4 *samples) {
@@ -77,6 +47,7 @@ __global__ void __launch_bounds__(128) k_batch_exit(Params p, const ViewDev *vie
                                                     unsigned long long seed, Queue q, float4 *samples) {
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (q.key[k] < 0) continue;  // finished before the integration (learned surrogate)
         long long g = q.id[k];
         const ViewDev &vw = views[find_view(views, nviews, g, false)];
         long long local = g - vw.ray_begin, pix = local / spp;
@@ -284,12 +255,13 @@ static inline void mark(cudaEvent_t *ev, int i, cudaStream_t st) {
 template <int I, int PREC>
 static cudaError_t batch_ip(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
                             long long total, long long total_pix, const Queue &q, float4 *samples, int packet,
-                            cudaStream_t st, cudaEvent_t *ev) {
+                            cudaStream_t st, cudaEvent_t *ev, const WfHook *hook) {
     const int bs = 128;
     mark(ev, 0, st);
     cudaError_t e = cudaMemsetAsync(q.count, 0, QUEUE_HEADER_BYTES, st);
     if (e != cudaSuccess) return e;
     k_batch_entry<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(p, views, nviews, spp, seed, total, q, samples);
+    if (hook && (e = hook->fn(hook->ctx, q, st)) != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -392,12 +364,14 @@ cudaError_t launch_sur_data(const Params &p, long long n, unsigned long long see
 
 cudaError_t launch_batch(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
                          long long total, long long total_pix, const Queue &q, float4 *samples, int packet,
-                         cudaStream_t st, cudaEvent_t *ev) {
+                         cudaStream_t st, cudaEvent_t *ev, const WfHook *hook) {
     if (p.integ == I_RK4)
-        return p.precision ? batch_ip<I_RK4, 1>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev)
-                           : batch_ip<I_RK4, 0>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev);
-    return p.precision ? batch_ip<I_DP45, 1>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev)
-                       : batch_ip<I_DP45, 0>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev);
+        return p.precision
+                   ? batch_ip<I_RK4, 1>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev, hook)
+                   : batch_ip<I_RK4, 0>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev, hook);
+    return p.precision
+               ? batch_ip<I_DP45, 1>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev, hook)
+               : batch_ip<I_DP45, 0>(p, views, nviews, spp, seed, total, total_pix, q, samples, packet, st, ev, hook);
 }
 
 }  // namespace ck

@@ -1,33 +1,98 @@
 // kernels_surrogate.cu -- the learned surrogate inside a render: network inputs of the queued rays, and
 // the gate that finishes the rays whose prediction it trusts (exit rebuilt from k_z / L_z conservation,
 // Eq. 12 factor of the exit face, room lookup) and takes them out of the integration.
+#include "batch.h"
 #include "sur_physics.cuh"
+#include "surrogate.h"
 #include "wavefront.cuh"
 
 namespace ck {
+
+// one queued ray's network inputs (each as a BF16 pair hi, lo in columns j and SUR_IN + j: the first layer
+// weighs both alike) and whether it entered through the lateral surface (the surrogate's support)
+__device__ __forceinline__ void sur_feature_row(const Params &p, int mode, const Queue &q, unsigned int k,
+                                                const double d[3], __nv_bfloat16 *X, unsigned char *elig) {
+    const double P[3] = {q.x[k], q.y[k], q.z[k]};
+    const bool lateral = fabs(hypot(P[0], P[1]) - p.R2) <= 1e-9 * p.R2 && fabs(P[2]) < p.halfH;
+    float x[SUR_IN];
+    sur_features(p.R1, p.R2, p.H, p.variant == V_AZIMUTHAL ? 1 : 0, mode, P, d, x);
+    __nv_bfloat16 *row = X + (size_t)k * 64;
+#pragma unroll
+    for (int j = 0; j < SUR_IN; ++j) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x[j]);
+        row[j] = hi;
+        row[SUR_IN + j] = __float2bfloat16_rn(x[j] - __bfloat162float(hi));
+    }
+    elig[k] = lateral ? 1 : 0;
+}
 
 __global__ void __launch_bounds__(256) k_sur_features(Params p, int mode, int spp, unsigned long long seed, Queue q,
                                                       __nv_bfloat16 *X, unsigned char *elig) {
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const double P[3] = {q.x[k], q.y[k], q.z[k]};
         const long long idx = q.id[k], pix = idx / spp;
         double o[3], d[3];
         camera_ray(p, (int)(pix % p.W), (int)(pix / p.W), (int)(idx - pix * spp), spp, seed, o, d);
-        // entered through the lateral surface (not a cap)
-        const bool lateral = fabs(hypot(P[0], P[1]) - p.R2) <= 1e-9 * p.R2 && fabs(P[2]) < p.halfH;
-        float x[SUR_IN];
-        sur_features(p.R1, p.R2, p.H, p.variant == V_AZIMUTHAL ? 1 : 0, mode, P, d, x);
-        // each input as a BF16 pair (hi, lo) in columns j and SUR_IN + j (the first layer weighs both alike)
-        __nv_bfloat16 *row = X + (size_t)k * 64;
-#pragma unroll
-        for (int j = 0; j < SUR_IN; ++j) {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(x[j]);
-            row[j] = hi;
-            row[SUR_IN + j] = __float2bfloat16_rn(x[j] - __bfloat162float(hi));
-        }
-        elig[k] = lateral ? 1 : 0;
+        sur_feature_row(p, mode, q, k, d, X, elig);
     }
+}
+
+__global__ void __launch_bounds__(256) k_sur_features_batch(Params p, const ViewDev *views, int nviews, int spp,
+                                                            unsigned long long seed, Queue q, __nv_bfloat16 *X,
+                                                            unsigned char *elig) {
+    const unsigned int n = q.count[0];
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double o[3], d[3];
+        batch_camera_ray(views, nviews, spp, seed, q.id[k], o, d);
+        const int vm = key_vm(q.key[k]);
+        Params pv = p;
+        pv.variant = vm >> 1;
+        sur_feature_row(pv, vm & 1, q, k, d, X, elig);
+    }
+}
+
+// The gate for one queued ray: if the network is confident (predicted log10 exit error <= gate) and the
+// predicted exit lies on the lateral surface, the ray is finished here (exit rebuilt from k_z / L_z
+// conservation, Eq. 12 factor of the exit face, room lookup) and leaves the integration.
+__device__ __forceinline__ void sur_gate_one(const Params &p, int mode, const Queue &q, unsigned int k,
+                                             const double d[3], const float *Y, const unsigned char *elig, float gate,
+                                             float4 *samples, cloak_record *recs) {
+    if (!elig[k]) return;
+    const float *y = Y + (size_t)k * 16;
+    if (!(y[4] <= gate) || !(y[1] * y[1] + y[2] * y[2] > 0.f)) return;
+    const double P[3] = {q.x[k], q.y[k], q.z[k]};
+    // the height moves monotonically along the ray: a predicted exit inside the lateral surface means
+    // no cap was crossed -- with a margin of twice the exit-point error the confidence allows
+    // (predicted log10 error c bounds the exit-point error by 10 R2 10^c)
+    const double margin = 20.0 * p.R2 * exp10((double)y[4]);
+    if (!(fabs(P[2] + 2.0 * p.R2 * (double)y[0]) < p.halfH - margin)) return;
+    double pos[3], dout[3], tof;
+    sur_reconstruct(p.R2, p.H, P, d, y, pos, dout, tof);
+    double nrm[3], eo, ee, c[3], mdout[3] = {-dout[0], -dout[1], -dout[2]};
+    face_normal(EV_LAT, pos, nrm);
+    local_material(p, pos, eo, ee, c);
+    cloak_record rec;
+    float rgb[3] = {0.f, 0.f, 0.f};
+    rec.mode = mode;
+    rec.steps = 0;
+    rec.tof = tof;
+    rec.status = CLOAK_RAY_EXITED;
+    if (p.variant == V_RADIAL && mode == 0) {
+        // radial o-rays run straight inside (eps_o = K constant, Sect. 4): they met the metal
+        // cylinder iff the entry line passes within R1 of the axis ahead of the entry point
+        const double ux = q.vx[k], uy = q.vy[k], uu = ux * ux + uy * uy;
+        const double tc = -(P[0] * ux + P[1] * uy), cr = P[0] * uy - P[1] * ux;
+        if (tc > 0.0 && cr * cr < p.R1sq * uu) rec.status = CLOAK_RAY_HIT_METAL_EXITED;
+    }
+    set_vec(rec.exit_pos, pos);
+    set_vec(rec.exit_dir, dout);
+    // light from the room enters here and leaves towards the camera at the entry face
+    rec.weight = transmission_in(mode, eo, ee, c, nrm, mdout) * q.w_out[k];
+    rec.tile_id = room_hit(p, pos, dout, rgb);
+    store_sample(samples, recs, q.id[k], rec, rgb);
+    // out of the integration: one ray fewer in its cost bucket, slot marked as finished
+    atomicSub(q.bins + q.key[k], 1u);
+    q.key[k] = -1;
 }
 
 __global__ void __launch_bounds__(128) k_sur_gate(Params p, int mode, int spp, unsigned long long seed, Queue q,
@@ -35,45 +100,24 @@ __global__ void __launch_bounds__(128) k_sur_gate(Params p, int mode, int spp, u
                                                   float4 *samples, cloak_record *recs) {
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        if (!elig[k]) continue;
-        const float *y = Y + (size_t)k * 16;
-        if (!(y[4] <= gate) || !(y[1] * y[1] + y[2] * y[2] > 0.f)) continue;
-        const double P[3] = {q.x[k], q.y[k], q.z[k]};
-        // the height moves monotonically along the ray: a predicted exit inside the lateral surface means
-        // no cap was crossed -- with a margin of twice the exit-point error the confidence allows
-        // (predicted log10 error c bounds the exit-point error by 10 R2 10^c)
-        const double margin = 20.0 * p.R2 * exp10((double)y[4]);
-        if (!(fabs(P[2] + 2.0 * p.R2 * (double)y[0]) < p.halfH - margin)) continue;
         const long long idx = q.id[k], pix = idx / spp;
         double o[3], d[3];
         camera_ray(p, (int)(pix % p.W), (int)(pix / p.W), (int)(idx - pix * spp), spp, seed, o, d);
-        double pos[3], dout[3], tof;
-        sur_reconstruct(p.R2, p.H, P, d, y, pos, dout, tof);
-        double nrm[3], eo, ee, c[3], mdout[3] = {-dout[0], -dout[1], -dout[2]};
-        face_normal(EV_LAT, pos, nrm);
-        local_material(p, pos, eo, ee, c);
-        cloak_record rec;
-        float rgb[3] = {0.f, 0.f, 0.f};
-        rec.mode = mode;
-        rec.steps = 0;
-        rec.tof = tof;
-        rec.status = CLOAK_RAY_EXITED;
-        if (p.variant == V_RADIAL && mode == 0) {
-            // radial o-rays run straight inside (eps_o = K constant, Sect. 4): they met the metal
-            // cylinder iff the entry line passes within R1 of the axis ahead of the entry point
-            const double ux = q.vx[k], uy = q.vy[k], uu = ux * ux + uy * uy;
-            const double tc = -(P[0] * ux + P[1] * uy), cr = P[0] * uy - P[1] * ux;
-            if (tc > 0.0 && cr * cr < p.R1sq * uu) rec.status = CLOAK_RAY_HIT_METAL_EXITED;
-        }
-        set_vec(rec.exit_pos, pos);
-        set_vec(rec.exit_dir, dout);
-        // light from the room enters here and leaves towards the camera at the entry face
-        rec.weight = transmission_in(mode, eo, ee, c, nrm, mdout) * q.w_out[k];
-        rec.tile_id = room_hit(p, pos, dout, rgb);
-        store_sample(samples, recs, idx, rec, rgb);
-        // out of the integration: one ray fewer in its cost bucket, slot marked as finished
-        atomicSub(q.bins + q.key[k], 1u);
-        q.key[k] = -1;
+        sur_gate_one(p, mode, q, k, d, Y, elig, gate, samples, recs);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_sur_gate_batch(Params p, const ViewDev *views, int nviews, int spp,
+                                                        unsigned long long seed, Queue q, const float *Y,
+                                                        const unsigned char *elig, float gate, float4 *samples) {
+    const unsigned int n = q.count[0];
+    for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double o[3], d[3];
+        batch_camera_ray(views, nviews, spp, seed, q.id[k], o, d);
+        const int vm = key_vm(q.key[k]);
+        Params pv = p;
+        pv.variant = vm >> 1;
+        sur_gate_one(pv, vm & 1, q, k, d, Y, elig, gate, samples, nullptr);
     }
 }
 
@@ -112,6 +156,18 @@ static int sm_count() {
 cudaError_t launch_sur_features(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q, SurNet *s,
                                 cudaStream_t st) {
     k_sur_features<<<sm_count() * 8, 256, 0, st>>>(p, mode, spp, seed, q, s->X, s->elig);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_features_batch(const Params &p, const ViewDev *views, int nviews, int spp,
+                                      unsigned long long seed, const Queue &q, SurNet *s, cudaStream_t st) {
+    k_sur_features_batch<<<sm_count() * 8, 256, 0, st>>>(p, views, nviews, spp, seed, q, s->X, s->elig);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_gate_batch(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
+                                  const Queue &q, SurNet *s, float4 *samples, cudaStream_t st) {
+    k_sur_gate_batch<<<sm_count() * 16, 128, 0, st>>>(p, views, nviews, spp, seed, q, s->Y, s->elig, s->gate, samples);
     return cudaGetLastError();
 }
 

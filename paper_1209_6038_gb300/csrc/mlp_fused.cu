@@ -235,24 +235,30 @@ __global__ void __launch_bounds__(F_THREADS, 1)
 }
 }  // namespace
 
-// forward pass of rows [0, n) of s->X into s->Y (rows beyond *m_count skipped when it is set)
-cudaError_t launch_mlp_fused(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st) {
-    static DeviceOnce once;
-    static int sms_of[MAX_DEVICES];
-    cudaError_t e0 = once.run([](int dev) {
+static DeviceOnce g_fused_once;
+static int g_fused_sms[MAX_DEVICES];
+
+// one-time setup of the kernel on the current device (also before a stream capture)
+cudaError_t mlp_fused_prepare() {
+    return g_fused_once.run([](int dev) {
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaDeviceGetAttribute(&sms_of[dev], cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&g_fused_sms[dev], cudaDevAttrMultiProcessorCount, dev);
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, k_mlp_fused);
         if (e != cudaSuccess) return e;
         if ((size_t)(optin - (int)fa.sharedSizeBytes) < F_SMEM) return cudaErrorInvalidValue;
         return cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM);
     });
+}
+
+// forward pass of rows [0, n) of s->X into s->Y (rows beyond *m_count skipped when it is set)
+cudaError_t launch_mlp_fused(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st) {
+    cudaError_t e0 = mlp_fused_prepare();
     if (e0 != cudaSuccess) return e0;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int sms = sms_of[dev];
+    const int sms = g_fused_sms[dev];
     if (n <= 0 || n % 128) return cudaErrorInvalidValue;
     CUtensorMap tx;
     if (make_tmap_bf16(&tx, s->X, (int)n, 64, GEMM_TILE_M) != CUDA_SUCCESS) return cudaErrorInvalidValue;

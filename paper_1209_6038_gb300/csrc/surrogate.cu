@@ -851,6 +851,13 @@ cudaError_t sur_render_hook(void *ctx, const Queue &q, cudaStream_t st) {
     SurNet *s = c->s;
     cudaError_t e = sur_ensure_inference(s, c->cap);
     if (e != cudaSuccess) return e;
+    if (c->views) {  // batched render (captured in a graph): per-ray view, mode and variant; the timeout
+                     // flag stays the network's own
+        if ((e = launch_sur_features_batch(c->p, c->views, c->nviews, c->spp, c->seed, q, s, st)) != cudaSuccess)
+            return e;
+        if ((e = sur_forward(s, s->inf_rows, q.count, st)) != cudaSuccess) return e;
+        return launch_sur_gate_batch(c->p, c->views, c->nviews, c->spp, c->seed, q, s, c->samples, st);
+    }
     s->err = gemm_err_flag();
     if ((e = launch_sur_features(c->p, c->mode, c->spp, c->seed, q, s, st)) != cudaSuccess) return e;
     if ((e = sur_forward(s, s->inf_rows, q.count, st)) != cudaSuccess) return e;

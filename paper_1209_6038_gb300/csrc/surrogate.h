@@ -87,6 +87,7 @@ cudaError_t sur_refresh_bf16(SurNet *s, cudaStream_t st);  // Wb / WTb from the 
 cudaError_t sur_forward(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st);
 // the same as one persistent tcgen05 kernel (mlp_fused.cu)
 cudaError_t launch_mlp_fused(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st);
+cudaError_t mlp_fused_prepare();  // one-time setup on the current device (call before capturing a forward pass)
 cudaError_t sur_ensure_inference(SurNet *s, long long rows);
 
 // training data (kernels_batch.cu): n seeded rays through entry, the any-medium integrator and exit;
@@ -116,6 +117,7 @@ int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, 
 int sur_save(SurNet *s, const char *path, std::string &why);
 int sur_load(SurNet *s, const char *path, std::string &why);
 
+struct ViewDev;
 struct SurRenderCtx {
     SurNet *s;
     Params p;
@@ -124,7 +126,14 @@ struct SurRenderCtx {
     float4 *samples;
     cloak_record *recs;
     long long cap;
+    // batched render: the device view table (mode, variant and camera ray per queued ray); null for one image
+    const ViewDev *views = nullptr;
+    int nviews = 0;
 };
 cudaError_t sur_render_hook(void *ctx, const Queue &q, cudaStream_t st);  // a WfHook function
+cudaError_t launch_sur_features_batch(const Params &p, const ViewDev *views, int nviews, int spp,
+                                      unsigned long long seed, const Queue &q, SurNet *s, cudaStream_t st);
+cudaError_t launch_sur_gate_batch(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
+                                  const Queue &q, SurNet *s, float4 *samples, cudaStream_t st);
 
 }  // namespace ck
