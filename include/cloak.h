@@ -55,7 +55,8 @@ enum {
                           r - R1 accurate down to the inner radius */
     CLOAK_SURROGATE = 3 /* learned surrogate (see cloak_surrogate_train) for rays that enter through the
                           lateral surface and whose predicted error passes the gate; the FP64 integrator
-                          for all others (wavefront schedule, cloak_render / cloak_render_records) */
+                          for all others (wavefront schedule: cloak_render, cloak_render_records,
+                          cloak_render_batch) */
 };
 /* kernel schedule */
 enum {
@@ -186,8 +187,11 @@ typedef struct cloak_view {
  * view's image.  The launch sequence is captured in a CUDA graph the first time a batch (views, spp,
  * seed, integrator, precision, packet) is seen and replayed on later identical calls.  The handle's
  * variant must be CLOAK_RADIAL or CLOAK_AZIMUTHAL; integrator, precision and packet come from the
- * handle.  views: host array of nviews >= 1 entries (read during the call); total samples
- * sum(width*height*spp) <= 2^31 - 1.  Scratch: about 128 bytes per sample, owned by the handle.
+ * handle.  With CLOAK_SURROGATE (a trained network of the handle's geometry) the network and its gate
+ * run on the whole queue before the sort and the integrator takes the rays the gate leaves; with a
+ * network of another geometry every ray is integrated.  views: host array of nviews >= 1 entries (read
+ * during the call); total samples sum(width*height*spp) <= 2^31 - 1.  Scratch: about 128 bytes per
+ * sample, owned by the handle (plus the network's inference buffers, 208 bytes per sample).
  * Every view's output is written on cuda_stream.  With stage timing on, cloak_stage_times reports the
  * stages of the last batch (events recorded inside the graph). */
 int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
