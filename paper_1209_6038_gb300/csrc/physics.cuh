@@ -553,9 +553,9 @@ __device__ __forceinline__ cx operator*(cx a, cx b) {
     return cx{fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
 }
 __device__ __forceinline__ cx operator*(double s, cx a) { return cx{s * a.re, s * a.im}; }
-__device__ __forceinline__ cx cdiv(cx a, cx b) {
-    double d = b.re * b.re + b.im * b.im;
-    return cx{(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+__device__ __forceinline__ cx cdiv(cx a, cx b) {  // a / b = a conj(b) / |b|^2, one reciprocal
+    const double id = rcp_nr(b.re * b.re + b.im * b.im);
+    return cx{(a.re * b.re + a.im * b.im) * id, (a.im * b.re - a.re * b.im) * id};
 }
 __device__ __forceinline__ double cabs2(cx a) { return a.re * a.re + a.im * a.im; }
 __device__ __forceinline__ cx cdot(const cx a[3], const cx b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
