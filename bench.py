@@ -441,7 +441,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--ref-pixels", type=int, default=1000, help="oracle pixels per image per step")
+    ap.add_argument("--ref-pixels", type=int, default=20000,
+                    help="oracle pixels per image per step (enough rays per image to keep all host cores busy)")
     ap.add_argument("--cpu-pixels", type=int, default=100000, help="oracle pixels per image for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
