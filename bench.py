@@ -20,6 +20,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -82,7 +83,7 @@ class ClockSampler:
 
     def __init__(self, gpu_index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"cloak_bench_clocks_{os.getpid()}.csv")
         self.gpu = gpu_index
 
     def __enter__(self):
@@ -204,7 +205,6 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
     batched render of all views: rays/s of both, the share of rays the surrogate finished, the image error
     against the FP64 integrator (per-view records), and the tensor-core roofline of the network's forward
     pass."""
-    import tempfile
     sw = inputs.SURROGATE
     integ = ck.DP45 if sw.integrator == "dp45" else ck.RK4
     trainer = ck.Cloak(ck.RADIAL).integrator(integ, sw.h_or_tol, ck.FP64, sw.max_steps)
