@@ -85,3 +85,19 @@ def test_mixed_needs_wavefront(ck):
     with pytest.raises(ck.CloakError):
         c.render(1, 1, 0)
     c.close()
+
+
+@pytest.mark.parametrize("geom", [(0.9, 1.0, 2.0), (1.2, 3.0, 0.7)])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_mixed_other_geometries(ck, geom, variant):
+    """The mixed path on a thin shell (K = 100) and on a squat cloak of radius 3, extraordinary light."""
+    W, H, spp = 64, 48, 2
+    rgba, orec, sp = oracle_render(variant, 1, 1, 1e-9, W, H, spp, 20.0, 4, geom=geom)
+    img, rec = small_render(ck, variant, 1, 1, 1e-9, W, H, spp, 20.0, seed=4, schedule="wavefront", precision=1,
+                            geom=geom)
+    err, lim, same = mixed_errors(rec, orec, sp)
+    over = np.nonzero(err > lim)[0]
+    assert len(over) == 0, f"{geom} v{variant}: exit-direction errors {err[over[:5]]}"
+    assert (~same).mean() < 0.005, f"{geom} v{variant}: {(~same).sum()} status changes"
+    assert np.all(np.isfinite(img))
+    print(f"{geom} v{variant}: max exit-direction error {err.max(initial=0):.2e} rad")

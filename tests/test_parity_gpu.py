@@ -91,7 +91,7 @@ def tile_edge_gap(pos, d, H=2.0):
     return np.minimum(gap + 0.0, np.where(np.isfinite(face_gap), face_gap, np.inf))
 
 
-def compare_records(g, o, sp, what, steps_exact=True, max_unstable=0.02):
+def compare_records(g, o, sp, what, steps_exact=True, max_unstable=0.02, H=2.0):
     """Element-by-element comparison of GPU and oracle records (see module docstring)."""
     assert g.shape == o.shape
     n = len(o)
@@ -119,7 +119,7 @@ def compare_records(g, o, sp, what, steps_exact=True, max_unstable=0.02):
     tb = np.nonzero(st & (g["tile_id"] != o["tile_id"]))[0]
     if len(tb):
         seen = np.stack(sp["tiles"], 1)[tb]
-        tie = (tile_edge_gap(o["exit_pos"][tb], o["exit_dir"][tb]) < 1e-9) | (seen == g["tile_id"][tb, None]).any(1)
+        tie = (tile_edge_gap(o["exit_pos"][tb], o["exit_dir"][tb], H) < 1e-9) | (seen == g["tile_id"][tb, None]).any(1)
         assert tie.all(), f"{what}: {(~tie).sum()} tile mismatches away from a tile edge"
     if steps_exact:
         sb = np.nonzero(st & (g["steps"] != o["steps"]) & (sp["dir"] < 1e-12))[0]
@@ -129,9 +129,10 @@ def compare_records(g, o, sp, what, steps_exact=True, max_unstable=0.02):
                 illcond_frac=float(1 - wc.mean()) if len(wc) else 0.0, unstable=int(uns.sum()))
 
 
-def gpu_trace(ck, variant, mode, rays, integ, h_or_tol, max_steps=1_000_000, test_medium=None, R1=0.5):
+def gpu_trace(ck, variant, mode, rays, integ, h_or_tol, max_steps=1_000_000, test_medium=None, R1=0.5, R2=1.0,
+              height=2.0):
     import torch
-    c = ck.Cloak(variant, R1=R1, R2=1.0, height=2.0)
+    c = ck.Cloak(variant, R1=R1, R2=R2, height=height)
     if test_medium:
         c.test_medium(*test_medium)
     c.integrator(integ, h_or_tol, ck.FP64, max_steps)
@@ -172,10 +173,11 @@ SCHEDULES = ("plain", "wavefront")
 
 
 def small_render(ck, variant, mode, integ, h_or_tol, W, H, spp, elev, seed=0, records=True, schedule="plain",
-                 precision=0):
+                 precision=0, geom=(0.5, 1.0, 2.0)):
+    """geom: (R1, R2, height) of the cloak."""
     import torch
     eye, tgt, up = inputs.camera_pose(elev)
-    c = ck.Cloak(variant).camera(eye, tgt, up, 60.0, W, H).integrator(integ, h_or_tol, precision)
+    c = ck.Cloak(variant, *geom).camera(eye, tgt, up, 60.0, W, H).integrator(integ, h_or_tol, precision)
     c.schedule(ck.SCHED_WAVEFRONT if schedule == "wavefront" else ck.SCHED_PLAIN)
     img = c.render(mode, spp, seed)
     rec = c.render_records(mode, spp, seed) if records else None
@@ -186,17 +188,18 @@ def small_render(ck, variant, mode, integ, h_or_tol, W, H, spp, elev, seed=0, re
     return img, rec
 
 
-def oracle_render(variant, mode, integ, h_or_tol, W, H, spp, elev, seed, pixels=None):
+def oracle_render(variant, mode, integ, h_or_tol, W, H, spp, elev, seed, pixels=None, geom=(0.5, 1.0, 2.0)):
     """Oracle image and records, plus the spread under 1e-13 perturbations of the camera."""
     eye, tgt, up = inputs.camera_pose(elev)
     integ_o = O.Integrator(integ, h_or_tol)
-    rgba, rec = O.render(O.Cloak(variant), integ_o, O.Camera(eye, tgt, up, 60, W, H), mode, spp, seed, pixels=pixels)
+    cl = O.Cloak(variant, R1=geom[0], R2=geom[1], H=geom[2])
+    rgba, rec = O.render(cl, integ_o, O.Camera(eye, tgt, up, 60, W, H), mode, spp, seed, pixels=pixels)
     others = []
     for k in range(3):
         rng = np.random.default_rng(2000 + k)
         e2 = np.array(eye) + PERTURB * rng.normal(size=3)
         t2 = np.array(tgt) + PERTURB * rng.normal(size=3)
-        others.append(O.render(O.Cloak(variant), integ_o, O.Camera(e2, t2, up, 60, W, H), mode, spp, seed,
+        others.append(O.render(cl, integ_o, O.Camera(e2, t2, up, 60, W, H), mode, spp, seed,
                                pixels=pixels)[1])
     return rgba, rec, spread_of(rec, others)
 
@@ -313,3 +316,38 @@ def test_wavefront_matches_plain(ck, variant, mode):
         assert angles(a_rec["exit_dir"], b_rec["exit_dir"]).max() < TOL_DIR
         assert np.abs(a_rec["tof"] - b_rec["tof"]).max() < TOL_ABS
         assert np.abs(a_img - b_img).max() < 1e-6
+
+
+# Cloak shapes away from R1 = 0.5, R2 = 1, height 2: a thin core (K = 1.11, nearly vacuum), a thin shell
+# (K = 100: strong anisotropy, rays that crawl around the metal) and a squat cloak of another scale
+# (nothing in the kernels may assume R2 = 1 or a fixed height).
+GEOMETRIES = ((0.05, 1.0, 2.0), (0.9, 1.0, 2.0), (1.2, 3.0, 0.7))
+
+
+@pytest.mark.parametrize("geom", GEOMETRIES)
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_geometry_trace_rays_parity(ck, geom, variant, mode):
+    """Ray sets scaled to each cloak shape, DP5(4) tol 1e-9, FP64 bar; rays longer than 2e5 step
+    attempts end as step-limited on both sides."""
+    R1, R2, H = geom
+    rays = inputs.ray_set(240, seed=31 + 2 * variant + mode, kind="mixed", R2=R2, H=H, distance=3.0 * R2)
+    g = gpu_trace(ck, variant, mode, rays, 1, 1e-9, max_steps=200_000, R1=R1, R2=R2, height=H)
+    o, sp = oracle_trace(O.Cloak(variant, R1=R1, R2=R2, H=H), O.Integrator(1, 1e-9, 200_000), mode, rays)
+    stats = compare_records(g, o, sp, f"R1={R1} R2={R2} H={H} v{variant} m{mode}", steps_exact=False,
+                            max_unstable=0.05, H=H)
+    print(stats)
+    assert np.isin(o["status"], [1, 2]).sum() > 100
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_geometry_render_wavefront(ck, variant, mode):
+    """Camera renders of the squat cloak of radius 3 through the wavefront schedule, FP64 DP5(4)."""
+    geom = (1.2, 3.0, 0.7)
+    W, H, spp = 64, 48, 2
+    rgba, orec, sp = oracle_render(variant, mode, 1, 1e-9, W, H, spp, 20.0, 3, geom=geom)
+    img, rec = small_render(ck, variant, mode, 1, 1e-9, W, H, spp, 20.0, seed=3, schedule="wavefront", geom=geom)
+    compare_records(rec, orec, sp, f"squat cloak v{variant} m{mode}", steps_exact=False, H=geom[2])
+    compare_images(img, rgba, rec, orec, sp, spp, f"squat cloak v{variant} m{mode}")
+    assert np.isin(orec["status"], [1, 2]).mean() > 0.3
