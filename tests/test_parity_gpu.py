@@ -328,12 +328,14 @@ GEOMETRIES = ((0.05, 1.0, 2.0), (0.9, 1.0, 2.0), (1.2, 3.0, 0.7))
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_geometry_trace_rays_parity(ck, geom, variant, mode):
-    """Ray sets scaled to each cloak shape, DP5(4) tol 1e-9, FP64 bar; rays longer than 2e5 step
-    attempts end as step-limited on both sides."""
+    """Ray sets scaled to each cloak shape, DP5(4) tol 1e-9, FP64 bar.  In the thin shell, near-axis
+    extraordinary rays of the azimuthal cloak come within 1.5e-5 of R1, where the oracle's literal Eq. 8
+    (1/f ~ 4e7 there) rejects a third of its steps: up to ~1e6 step attempts, so the limit is 2e6."""
     R1, R2, H = geom
     rays = inputs.ray_set(240, seed=31 + 2 * variant + mode, kind="mixed", R2=R2, H=H, distance=3.0 * R2)
-    g = gpu_trace(ck, variant, mode, rays, 1, 1e-9, max_steps=200_000, R1=R1, R2=R2, height=H)
-    o, sp = oracle_trace(O.Cloak(variant, R1=R1, R2=R2, H=H), O.Integrator(1, 1e-9, 200_000), mode, rays)
+    g = gpu_trace(ck, variant, mode, rays, 1, 1e-9, max_steps=2_000_000, R1=R1, R2=R2, height=H)
+    o, sp = oracle_trace(O.Cloak(variant, R1=R1, R2=R2, H=H), O.Integrator(1, 1e-9, 2_000_000), mode, rays)
+    assert (o["status"] != 5).all()
     stats = compare_records(g, o, sp, f"R1={R1} R2={R2} H={H} v{variant} m{mode}", steps_exact=False,
                             max_unstable=0.05, H=H)
     print(stats)
