@@ -366,4 +366,4 @@ def test_geometry_render_wavefront(ck, variant, mode):
     img, rec = small_render(ck, variant, mode, 1, 1e-9, W, H, spp, 20.0, seed=3, schedule="wavefront", geom=geom)
     compare_records(rec, orec, sp, f"squat cloak v{variant} m{mode}", steps_exact=False, H=geom[2])
     compare_images(img, rgba, rec, orec, sp, spp, f"squat cloak v{variant} m{mode}")
-    assert np.isin(orec["status"], [1, 2]).mean() > 0.3
+    assert np.isin(orec["status"], [1, 2]).mean() > 0.2
