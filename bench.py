@@ -459,6 +459,8 @@ def main():
     ap.add_argument("--profile-batch", action="store_true",
                     help="render the step's 12 images through the batched path twice at --width x --height "
                          "(default 480x270), for profilers")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="arithmetic of --profile-batch: FP64, or FP32 stepping with the FP64 band (mixed)")
     ap.add_argument("--width", type=int, default=None)
     ap.add_argument("--height", type=int, default=None)
     ap.add_argument("--schedule", default="batched", choices=["plain", "wavefront", "batched"])
@@ -515,7 +517,8 @@ def main():
         return 0
     if args.profile_batch:
         W, H = args.width or 480, args.height or 270
-        c = ck.Cloak(ck.RADIAL).integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol, ck.FP64,
+        prec = ck.MIXED if args.precision == "mixed" else ck.FP64
+        c = ck.Cloak(ck.RADIAL).integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol, prec,
                                            w.max_steps)
         c.schedule(ck.SCHED_WAVEFRONT)
         views = []
@@ -526,7 +529,8 @@ def main():
         for _ in range(2):
             ck.cloak_render_batch(c.h, views, w.spp, w.seed)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_batch": True, "width": W, "height": H, "images": len(views),
+        print(json.dumps({"profile_batch": True, "precision": args.precision, "width": W, "height": H,
+                          "images": len(views),
                           "mean_rgba": torch.stack([v[-1].mean(dim=(0, 1)) for v in views]).mean(0).tolist()}))
         c.close()
         return 0
@@ -719,12 +723,16 @@ def main():
                                      "status_mismatch": int((g["status"] != o["status"]).sum()),
                                      "pixels_tile_or_status_differs_frac": float(px_diff.mean())}
 
-        # ---- the precision form: the same workload with FP32 stepping (mixed), against the oracle sample
-        if not args.no_mixed:
-            mixed_runner = Batched(ck.MIXED) if args.schedule == "batched" else PerImage(ck.SCHED_WAVEFRONT, ck.MIXED)
+        # ---- the precision form: the same workload with FP32 stepping (mixed), against the oracle sample; the
+        # band near R1 in FP64 ("mixed") and in double-float ("mixed_df_band")
+        for prec, key, band in ((ck.MIXED, "mixed", "f64 band r < R1 + 0.02"),
+                                (ck.MIXED_FF, "mixed_df_band", "double-float (FP32 pair) band r < R1 + 0.02")):
+            if args.no_mixed:
+                break
+            mixed_runner = Batched(prec) if args.schedule == "batched" else PerImage(ck.SCHED_WAVEFRONT, prec)
             mms, _, mstages = timed(mixed_runner, 1, 2, collective=False)
             mixed_runner.close()
-            mh = make_handles(ck.SCHED_WAVEFRONT, precision=ck.MIXED)
+            mh = make_handles(ck.SCHED_WAVEFRONT, precision=prec)
             rec_buf = torch.empty(w.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
             msamples = []
             for idx, (v, m, e) in enumerate(w.images):
@@ -740,15 +748,15 @@ def main():
             cr = np.linalg.norm(np.cross(gm["exit_dir"][fin], o["exit_dir"][fin]), axis=-1)
             errm = np.arctan2(cr, np.sum(gm["exit_dir"][fin] * o["exit_dir"][fin], axis=-1))
             pxm = ((gm["tile_id"] != o["tile_id"]) | (gm["status"] != o["status"])).reshape(-1, w.spp).any(1)
-            out["mixed"] = {"value": ws * rays_step / (mms / 1e3), "unit": UNIT, "ms_per_step": mms, "warmup": 1,
-                            "steps": 2, "schedule": args.schedule,
-                            "dtype": "f32 stepping, float-float state, f64 band r < R1 + 0.02",
-                            "integrate_ms_per_step": mstages[1], "speedup_vs_fp64": ms_step / mms,
-                            "accuracy_vs_oracle": {"max_exit_dir_err_rad": float(errm.max(initial=0)),
-                                                   "p999_exit_dir_err_rad": float(np.quantile(errm, 0.999)),
-                                                   "rays_over_1e-5_rad": int((errm > 1e-5).sum()),
-                                                   "rays_compared": int(fin.sum()),
-                                                   "pixels_tile_or_status_differs_frac": float(pxm.mean())}}
+            out[key] = {"value": ws * rays_step / (mms / 1e3), "unit": UNIT, "ms_per_step": mms, "warmup": 1,
+                        "steps": 2, "schedule": args.schedule,
+                        "dtype": "f32 stepping, float-float state, " + band,
+                        "integrate_ms_per_step": mstages[1], "speedup_vs_fp64": ms_step / mms,
+                        "accuracy_vs_oracle": {"max_exit_dir_err_rad": float(errm.max(initial=0)),
+                                               "p999_exit_dir_err_rad": float(np.quantile(errm, 0.999)),
+                                               "rays_over_1e-5_rad": int((errm > 1e-5).sum()),
+                                               "rays_compared": int(fin.sum()),
+                                               "pixels_tile_or_status_differs_frac": float(pxm.mean())}}
         for c in rec_handles.values():
             c.close()
 

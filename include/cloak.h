@@ -51,8 +51,8 @@ enum {
     CLOAK_MIXED = 1,   /* RK stepping in FP32 (right-hand sides, stage combinations, step control) with
                           float-float state accumulation; whole steps in FP64 where r < R1 + 0.02; entry
                           and exit interface solves in FP64 (wavefront schedule only) */
-    CLOAK_MIXED_FF = 2, /* as CLOAK_MIXED without the FP64 band: stage positions in float-float keep
-                          r - R1 accurate down to the inner radius */
+    CLOAK_MIXED_FF = 2, /* as CLOAK_MIXED with the steps of the band in double-float (pairs of FP32
+                          numbers, ~48 significant bits) instead of FP64 */
     CLOAK_SURROGATE = 3 /* learned surrogate (see cloak_surrogate_train) for rays that enter through the
                           lateral surface and whose predicted error passes the gate; the FP64 integrator
                           for all others (wavefront schedule: cloak_render, cloak_render_records,

@@ -94,7 +94,8 @@ static int make_params(const cloak *h, ck::Params &p) {
     p.scene_seed = h->scene_seed;
     p.integ = h->integ == CLOAK_RK4 ? ck::I_RK4 : ck::I_DP45;
     p.precision = h->precision == CLOAK_MIXED ? 1 : h->precision == CLOAK_MIXED_FF ? 2 : 0;
-    p.mixed_band = h->precision == CLOAK_MIXED ? 0.02 : 0.0;
+    p.mixed_band = h->precision == CLOAK_MIXED || h->precision == CLOAK_MIXED_FF ? 0.02 : 0.0;
+    p.band_df = h->precision == CLOAK_MIXED_FF;
     p.h_or_tol = h->h_or_tol;
     p.max_steps = h->max_steps;
     double w[3], u[3], v[3];

@@ -10,11 +10,15 @@
 //                 exceeds its own FP32 rounding bound (the estimate is a difference of nearly equal
 //                 stage combinations, so without this the controller would chase rounding noise).
 //
+//   StepperMixed with the band in double-float (CLOAK_MIXED_FF): the steps within the band are taken
+//                 in double-float (pairs of FP32 numbers, ~48 bits, dfloat.cuh) instead of FP64.
+//
 // Each lane owns one queued ray and refills from the queue when it finishes.  Every loop iteration
 // runs ONE uniform step evaluation for all lanes; the surface-crossing search (bisection prefix,
 // then Illinois regula falsi, see crossing() in physics.cuh) reuses that slot with a trial size.
 #pragma once
 
+#include "dfloat.cuh"
 #include "physics.cuh"
 
 namespace ck {
@@ -177,6 +181,84 @@ __device__ __forceinline__ void rhs_f32(const Params &p, const float t[6], const
 }
 
 
+// ------------------------------------------------------------------ double-float steps (the band near R1)
+// The same right-hand side and the same Dormand-Prince / RK4 updates as the FP64 path, in double-float.
+template <int VAR, int MODE>
+__device__ __forceinline__ void rhs_df(df R1, const df y[6], df d[6], int vm) {
+    d[0] = y[3]; d[1] = y[4]; d[2] = y[5];
+    const df unused;  // K and 1/K: the simplified accelerations of accel_fixed do not read them
+    accel<VAR, MODE, df>(R1, unused, unused, y[0], y[1], y[3], y[4], y[5], d[3], d[4], d[5], vm);
+}
+template <int VAR, int MODE>
+__device__ __forceinline__ void dp45_step_df(df R1, const df y[6], const df k1[6], df h, df out[6], df err[6],
+                                             df k7[6], int vm) {
+    df k2[6], k3[6], k4[6], k5[6], k6[6], t[6];
+    {
+        const df c1 = h * df(DP::a21);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) t[i] = df_fma(c1, k1[i], y[i]);
+    }
+    rhs_df<VAR, MODE>(R1, t, k2, vm);
+    {
+        const df c1 = h * df(DP::a31), c2 = h * df(DP::a32);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) t[i] = df_fma(c2, k2[i], df_fma(c1, k1[i], y[i]));
+    }
+    rhs_df<VAR, MODE>(R1, t, k3, vm);
+    {
+        const df c1 = h * df(DP::a41), c2 = h * df(DP::a42), c3 = h * df(DP::a43);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) t[i] = df_fma(c3, k3[i], df_fma(c2, k2[i], df_fma(c1, k1[i], y[i])));
+    }
+    rhs_df<VAR, MODE>(R1, t, k4, vm);
+    {
+        const df c1 = h * df(DP::a51), c2 = h * df(DP::a52), c3 = h * df(DP::a53), c4 = h * df(DP::a54);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) t[i] = df_fma(c4, k4[i], df_fma(c3, k3[i], df_fma(c2, k2[i], df_fma(c1, k1[i], y[i]))));
+    }
+    rhs_df<VAR, MODE>(R1, t, k5, vm);
+    {
+        const df c1 = h * df(DP::a61), c2 = h * df(DP::a62), c3 = h * df(DP::a63), c4 = h * df(DP::a64),
+                 c5 = h * df(DP::a65);
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            t[i] = df_fma(c5, k5[i], df_fma(c4, k4[i], df_fma(c3, k3[i], df_fma(c2, k2[i], df_fma(c1, k1[i], y[i])))));
+    }
+    rhs_df<VAR, MODE>(R1, t, k6, vm);
+    {
+        const df c1 = h * df(DP::b1), c3 = h * df(DP::b3), c4 = h * df(DP::b4), c5 = h * df(DP::b5),
+                 c6 = h * df(DP::b6);
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            out[i] = df_fma(c6, k6[i], df_fma(c5, k5[i], df_fma(c4, k4[i], df_fma(c3, k3[i], df_fma(c1, k1[i], y[i])))));
+    }
+    rhs_df<VAR, MODE>(R1, out, k7, vm);
+    {
+        const df c1 = h * df(DP::e1), c3 = h * df(DP::e3), c4 = h * df(DP::e4), c5 = h * df(DP::e5),
+                 c6 = h * df(DP::e6), c7 = h * df(DP::e7);
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            err[i] = df_fma(c7, k7[i], df_fma(c6, k6[i], df_fma(c5, k5[i], df_fma(c4, k4[i], df_fma(c3, k3[i], c1 * k1[i])))));
+    }
+}
+template <int VAR, int MODE>
+__device__ __forceinline__ void rk4_step_df(df R1, const df y[6], df h, df out[6], int vm) {
+    df k[6], acc[6], t[6];
+    const df hh = h * 0.5f, h6 = h * df(1.0 / 6.0);
+    rhs_df<VAR, MODE>(R1, y, k, vm);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { acc[i] = k[i]; t[i] = df_fma(hh, k[i], y[i]); }
+    rhs_df<VAR, MODE>(R1, t, k, vm);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { acc[i] = acc[i] + k[i] * 2.0f; t[i] = df_fma(hh, k[i], y[i]); }
+    rhs_df<VAR, MODE>(R1, t, k, vm);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { acc[i] = acc[i] + k[i] * 2.0f; t[i] = df_fma(h, k[i], y[i]); }
+    rhs_df<VAR, MODE>(R1, t, k, vm);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out[i] = df_fma(h6, acc[i] + k[i], y[i]);
+}
+
 template <int VAR, int MODE, int INTEG>
 struct StepperMixed {
     typedef float real;
@@ -211,6 +293,25 @@ struct StepperMixed {
         for (int i = 2; i < 6; ++i) t[i] = yh[i] + (yl[i] + d[i]);
     }
     __device__ __forceinline__ void eval(const Params &p, float s) {
+        if (p.band_df && island(p)) {  // double-float step from the float-float state
+            df y[6], yo[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) y[i] = df(yh[i], yl[i]);
+            const df R1(p.R1), hs(s, 0.f);
+            if (INTEG == I_RK4) {
+                rk4_step_df<VAR, MODE>(R1, y, hs, yo, vm);
+            } else {
+                df kk1[6], e[6], kk7[6];
+                rhs_df<VAR, MODE>(R1, y, kk1, vm);
+                dp45_step_df<VAR, MODE>(R1, y, kk1, hs, yo, e, kk7, vm);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) { e6[i] = e[i].hi + e[i].lo; k7[i] = kk7[i].hi; n6[i] = 0.f; }
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) { y1h[i] = yo[i].hi; y1l[i] = yo[i].lo; }
+            need_k1 = true;
+            return;
+        }
         if (island(p)) {  // FP64 step from the float-float state
             double y[6], yo[6], e[6], kk1[6], kk7[6];
 #pragma unroll

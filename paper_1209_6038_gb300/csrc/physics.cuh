@@ -61,6 +61,7 @@ struct Params {
     int integ;
     int precision;  // 0 FP64, 1 mixed, 2 mixed without the FP64 band (wavefront schedule only)
     double mixed_band;  // FP64 steps where r < R1 + mixed_band (mixed precision)
+    int band_df;        // ... taken in double-float instead of FP64
     double h_or_tol;
     long long max_steps;
     // camera

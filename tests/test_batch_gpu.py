@@ -28,7 +28,7 @@ def single(ck, variant, pol, eye, tgt, up, W, H, spp, seed, precision):
     return img.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_batch_matches_single_renders(ck, precision):
     import torch
     spp, seed = 2, 17

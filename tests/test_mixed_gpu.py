@@ -1,5 +1,5 @@
 """Mixed-precision path (FP32 right-hand sides and stage combinations, float-float state,
-FP64 steps within 0.02 of the inner radius, FP64 interface solves) against the FP64 oracle.
+FP64 or double-float steps within 0.02 of the inner radius, FP64 interface solves) against the FP64 oracle.
 
 Bar: exit direction within 1e-5 rad of the oracle, and at least 99.9% of sampled pixels with the
 same room tile and status in every sample.  As in the FP64 tests the bar widens where the problem
@@ -27,15 +27,20 @@ def mixed_errors(rec, orec, sp):
     return err, lim, same
 
 
+# the band near R1 in FP64 (CLOAK_MIXED) or in double-float (CLOAK_MIXED_FF)
+BANDS = [1, 2]
+
+
+@pytest.mark.parametrize("band", BANDS)
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_mixed_exit_directions(ck, variant, mode):
+def test_mixed_exit_directions(ck, variant, mode, band):
     W, H, spp = 96, 54, 2
     worst = 0.0
     for elev in (0.0, 20.0, 45.0):
         rgba, orec, sp = oracle_render(variant, mode, 1, 1e-9, W, H, spp, elev, 7)
         img, rec = small_render(ck, variant, mode, 1, 1e-9, W, H, spp, elev, seed=7, schedule="wavefront",
-                                precision=1)
+                                precision=band)
         err, lim, same = mixed_errors(rec, orec, sp)
         over = np.nonzero(err > lim)[0]
         assert len(over) == 0, f"v{variant} m{mode} e{elev}: exit-direction errors {err[over[:5]]}"
@@ -45,23 +50,25 @@ def test_mixed_exit_directions(ck, variant, mode):
     print(f"v{variant} m{mode}: max exit-direction error {worst:.2e} rad")
 
 
-def test_mixed_rk4_small_config(ck):
+@pytest.mark.parametrize("band", BANDS)
+def test_mixed_rk4_small_config(ck, band):
     """The small workload (radial, extraordinary, RK4 h = 1e-3) on the mixed path."""
     w = inputs.SMALL
     rgba, orec, sp = oracle_render(0, 1, 0, 1e-3, w.width, w.height, 1, 0.0, 0)
-    img, rec = small_render(ck, 0, 1, 0, 1e-3, w.width, w.height, 1, 0.0, schedule="wavefront", precision=1)
+    img, rec = small_render(ck, 0, 1, 0, 1e-3, w.width, w.height, 1, 0.0, schedule="wavefront", precision=band)
     err, lim, same = mixed_errors(rec, orec, sp)
     assert np.all(err <= lim)
     assert (~same).mean() < 0.005
 
 
-def test_mixed_full_size_pixels(ck):
+@pytest.mark.parametrize("band", BANDS)
+def test_mixed_full_size_pixels(ck, band):
     """1920x1080, 4 spp, DP5(4) tol 1e-9, azimuthal e-light at 20 deg: >= 99.9% of 2000 sampled
     pixels keep every sample's tile and status."""
     import torch
     w = inputs.FULL
     eye, tgt, up = inputs.camera_pose(20.0)
-    c = ck.Cloak(1).camera(eye, tgt, up, 60.0, w.width, w.height).integrator(1, 1e-9, ck.MIXED)
+    c = ck.Cloak(1).camera(eye, tgt, up, 60.0, w.width, w.height).integrator(1, 1e-9, band)
     c.schedule(ck.SCHED_WAVEFRONT)
     rec_t = c.render_records(1, w.spp, w.seed)
     torch.cuda.synchronize()
@@ -87,13 +94,14 @@ def test_mixed_needs_wavefront(ck):
     c.close()
 
 
+@pytest.mark.parametrize("band", BANDS)
 @pytest.mark.parametrize("geom", [(0.9, 1.0, 2.0), (1.2, 3.0, 0.7)])
 @pytest.mark.parametrize("variant", [0, 1])
-def test_mixed_other_geometries(ck, geom, variant):
+def test_mixed_other_geometries(ck, geom, variant, band):
     """The mixed path on a thin shell (K = 100) and on a squat cloak of radius 3, extraordinary light."""
     W, H, spp = 64, 48, 2
     rgba, orec, sp = oracle_render(variant, 1, 1, 1e-9, W, H, spp, 20.0, 4, geom=geom)
-    img, rec = small_render(ck, variant, 1, 1, 1e-9, W, H, spp, 20.0, seed=4, schedule="wavefront", precision=1,
+    img, rec = small_render(ck, variant, 1, 1, 1e-9, W, H, spp, 20.0, seed=4, schedule="wavefront", precision=band,
                             geom=geom)
     err, lim, same = mixed_errors(rec, orec, sp)
     over = np.nonzero(err > lim)[0]
