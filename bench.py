@@ -459,8 +459,9 @@ def main():
     ap.add_argument("--profile-batch", action="store_true",
                     help="render the step's 12 images through the batched path twice at --width x --height "
                          "(default 480x270), for profilers")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="arithmetic of --profile-batch: FP64, or FP32 stepping with the FP64 band (mixed)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_df"],
+                    help="arithmetic of --profile-batch: FP64, or FP32 stepping with the band near R1 in FP64 "
+                         "(mixed) or in double-float (mixed_df)")
     ap.add_argument("--width", type=int, default=None)
     ap.add_argument("--height", type=int, default=None)
     ap.add_argument("--schedule", default="batched", choices=["plain", "wavefront", "batched"])
@@ -517,7 +518,7 @@ def main():
         return 0
     if args.profile_batch:
         W, H = args.width or 480, args.height or 270
-        prec = ck.MIXED if args.precision == "mixed" else ck.FP64
+        prec = {"fp64": ck.FP64, "mixed": ck.MIXED, "mixed_df": ck.MIXED_FF}[args.precision]
         c = ck.Cloak(ck.RADIAL).integrator(ck.DP45 if w.integrator == "dp45" else ck.RK4, w.h_or_tol, prec,
                                            w.max_steps)
         c.schedule(ck.SCHED_WAVEFRONT)
