@@ -96,6 +96,14 @@ static int make_params(const cloak *h, ck::Params &p) {
     p.precision = h->precision == CLOAK_MIXED ? 1 : h->precision == CLOAK_MIXED_FF ? 2 : 0;
     p.mixed_band = h->precision == CLOAK_MIXED || h->precision == CLOAK_MIXED_FF ? 0.02 : 0.0;
     p.band_df = h->precision == CLOAK_MIXED_FF;
+    p.R1f = (float)p.R1;
+    p.R2f = (float)p.R2;
+    p.halfHf = (float)p.halfH;
+    p.Kf = (float)p.K;
+    p.invKf = (float)p.invK;
+    p.R1sq_hf = (float)p.R1sq;
+    p.R1sq_lf = (float)(p.R1sq - (double)p.R1sq_hf);
+    p.band_limf = (float)(p.R1 + p.mixed_band);
     p.h_or_tol = h->h_or_tol;
     p.max_steps = h->max_steps;
     double w[3], u[3], v[3];

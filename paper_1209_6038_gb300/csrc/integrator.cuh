@@ -175,8 +175,7 @@ __device__ __forceinline__ void accel_f32(float R1, float R1sq_h, float R1sq_l, 
 template <int VAR, int MODE>
 __device__ __forceinline__ void rhs_f32(const Params &p, const float t[6], const float tl[2], float d[6], int vm) {
     d[0] = t[3]; d[1] = t[4]; d[2] = t[5];
-    float R1sq_h = (float)p.R1sq, R1sq_l = (float)(p.R1sq - (double)R1sq_h);
-    accel_f32<VAR, MODE>((float)p.R1, R1sq_h, R1sq_l, (float)p.K, (float)p.invK, t[0], tl[0], t[1], tl[1], t[3], t[4],
+    accel_f32<VAR, MODE>(p.R1f, p.R1sq_hf, p.R1sq_lf, p.Kf, p.invKf, t[0], tl[0], t[1], tl[1], t[3], t[4],
                          t[5], d[3], d[4], d[5], vm);
 }
 
@@ -282,7 +281,7 @@ struct StepperMixed {
         if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD) || (VAR == V_ANY && vm == 0)) return false;
         float x = yh[0] + yl[0], y = yh[1] + yl[1];
         if (!(p.mixed_band > 0.0)) return false;
-        float lim = (float)(p.R1 + p.mixed_band);
+        const float lim = p.band_limf;
         return x * x + y * y < lim * lim;
     }
     // stage point y + d: x, y as float-float (t, tl), the rest in FP32
@@ -425,14 +424,14 @@ struct StepperMixed {
     static __device__ __forceinline__ float gval(const Params &p, int ev, const float h[6], const float l[6]) {
         float x = h[0] + l[0], y = h[1] + l[1], z = h[2] + l[2];
         switch (ev) {
-        case EV_LAT: return sqrtf(x * x + y * y) - (float)p.R2;
-        case EV_TOP: return z - (float)p.halfH;
-        case EV_BOT: return -z - (float)p.halfH;
-        default: return (float)p.R1 - sqrtf(x * x + y * y);
+        case EV_LAT: return sqrtf(x * x + y * y) - p.R2f;
+        case EV_TOP: return z - p.halfHf;
+        case EV_BOT: return -z - p.halfHf;
+        default: return p.R1f - sqrtf(x * x + y * y);
         }
     }
     __device__ __forceinline__ float chord(const Params &p) const {
-        return metal_chord(yh[0] + yl[0], yh[1] + yl[1], y1h[0] + y1l[0], y1h[1] + y1l[1], (float)p.R1sq);
+        return metal_chord(yh[0] + yl[0], yh[1] + yl[1], y1h[0] + y1l[0], y1h[1] + y1l[1], p.R1sq_hf);
     }
     __device__ __forceinline__ float g_start(const Params &p, int ev) const { return gval(p, ev, yh, yl); }
     __device__ __forceinline__ float g_end(const Params &p, int ev) const { return gval(p, ev, y1h, y1l); }

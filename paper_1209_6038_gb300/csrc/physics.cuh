@@ -62,6 +62,9 @@ struct Params {
     int precision;  // 0 FP64, 1 mixed, 2 mixed without the FP64 band (wavefront schedule only)
     double mixed_band;  // FP64 steps where r < R1 + mixed_band (mixed precision)
     int band_df;        // ... taken in double-float instead of FP64
+    // FP32 copies for the mixed-precision stepper, rounded once on the host (not converted per step):
+    // R1, R2, H/2, K, 1/K, R1^2 as float-float (hi, lo), and the band's outer radius R1 + mixed_band
+    float R1f, R2f, halfHf, Kf, invKf, R1sq_hf, R1sq_lf, band_limf;
     double h_or_tol;
     long long max_steps;
     // camera
