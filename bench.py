@@ -736,8 +736,11 @@ def main():
             mh = make_handles(ck.SCHED_WAVEFRONT, precision=prec)
             rec_buf = torch.empty(w.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
             msamples = []
+            mflops = 0.0
             for idx, (v, m, e) in enumerate(w.images):
                 mh[(v, e)].render_records(m, w.spp, w.seed, out=rec_buf)
+                msteps = int(rec_buf.view(torch.int32).view(-1, 20)[:, 18].long().sum().item())
+                mflops += msteps * flops_per_step(v, m, 1 if w.integrator == "dp45" else 0)
                 pix = sample_pixels(w, idx, args.cpu_pixels)
                 sel = torch.from_numpy((pix[:, None] * w.spp + np.arange(w.spp)[None, :]).reshape(-1)).cuda()
                 msamples.append(ck.records_to_numpy(rec_buf.view(-1, ck.RECORD_BYTES)[sel].reshape(-1)))
@@ -753,6 +756,14 @@ def main():
                         "steps": 2, "schedule": args.schedule,
                         "dtype": "f32 stepping, float-float state, " + band,
                         "integrate_ms_per_step": mstages[1], "speedup_vs_fp64": ms_step / mms,
+                        "roofline": {"bound": "alu", "achieved": mflops / (mstages[1] / 1e3) / 1e12,
+                                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                     "frac": mflops / (mstages[1] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                                     "peak_source": "derived: 152 SM x 2.07 GHz x 128 FP32 FMA/clk/SM",
+                                     "note": "algorithmic flops of the step attempts (the FP64 path's per-attempt "
+                                             "count, band steps included) over the integration kernel's time; the "
+                                             "kernel is bound by latency and lane divergence, not an FP32 pipe "
+                                             "(profiles/k_wf_integrate_batched_mixed_480x270x4.md)"},
                         "accuracy_vs_oracle": {"max_exit_dir_err_rad": float(errm.max(initial=0)),
                                                "p999_exit_dir_err_rad": float(np.quantile(errm, 0.999)),
                                                "rays_over_1e-5_rad": int((errm > 1e-5).sum()),
