@@ -227,7 +227,7 @@ static cudaError_t refl_ip(const Params &p, const Queue &q, const Queue &q2, flo
     if (e == cudaSuccess) e = cudaMemsetAsync(refl, 0, (size_t)nrefl * sizeof(float4), st);
     if (e != cudaSuccess) return e;
     k_refl_spawn<<<sms * 16, 128, 0, st>>>(p, q, q2);
-    k_wf_sort_scan<<<1, 32, 0, st>>>(q2, NBINS_BATCH);
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q2, NBINS_BATCH, 0u);
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q2);
     const int pk = packet > 0 ? packet : 128;
     int nb = 0;
@@ -265,14 +265,18 @@ static cudaError_t batch_ip(const Params &p, const ViewDev *views, int nviews, i
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH);
+    int pk = packet > 0 ? packet : 128;
+    // the slowest rays of the batch go to the warps of LONG_RAY_BLOCKS blocks that have their SMs to
+    // themselves (k_wf_integrate)
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH, (unsigned int)(LONG_RAY_BLOCKS * pk));
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
     mark(ev, 1, st);
-    int pk = packet > 0 ? packet : 128;
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V_ANY, V_ANY, I, PREC>, pk, 0);
     if (e != cudaSuccess) return e;
-    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(p, q);
+    Params pl = p;
+    pl.dedicated_blocks = LONG_RAY_BLOCKS;
+    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(pl, q);
     mark(ev, 2, st);
     k_batch_exit<<<sms * 16, 128, 0, st>>>(p, views, nviews, spp, seed, q, samples);
     mark(ev, 3, st);
@@ -343,7 +347,7 @@ static cudaError_t sur_data_ip(const Params &p, long long n, unsigned long long 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH);
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH, 0u);
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V_ANY, V_ANY, I, PREC>, 128, 0);

@@ -17,21 +17,34 @@ __global__ void k_wf_resolve(int npix, int spp, const float4 *samples, float4 *o
     out[pix] = make_float4(a0 * inv, a1 * inv, a2 * inv, a3 * inv);
 }
 
-__global__ void k_wf_sort_scan(Queue q, int nbins) {
+// reserve > 0: set aside the first min(reserve, segment size) rays of the medium segment whose highest
+// nonempty cost bucket is highest (its slowest rays are the slowest of the batch) for the long-ray
+// blocks of the integration kernel: count[8] = that segment, count[9] = the number reserved.
+__global__ void k_wf_sort_scan(Queue q, int nbins, unsigned int reserve) {
     if (threadIdx.x != 0) return;
     unsigned int off = 0;
     for (int v = 3; v >= 0; --v) {  // empty segments for the media a single image does not use
         q.bins[SEG_OFFSET + 2 * v] = 0;
         q.bins[SEG_OFFSET + 2 * v + 1] = 0;
     }
+    int top_v = -1, top_cost = -1;
     for (int b = nbins - 1; b >= 0; --b) {  // descending key: slowest rays first
         unsigned int c = q.bins[b];
         q.bins[NBINS_BATCH + b] = off;
         if (b % NBINS == NBINS - 1) q.bins[SEG_OFFSET + 2 * key_vm(b)] = off;
         q.bins[SEG_OFFSET + 2 * key_vm(b) + 1] += c;
         off += c;
+        if (c && b % NBINS > top_cost) {
+            top_cost = b % NBINS;
+            top_v = key_vm(b);
+        }
     }
     q.count[2] = off;
+    if (reserve && top_v >= 0) {
+        const unsigned int len = q.bins[SEG_OFFSET + 2 * top_v + 1];
+        q.count[8] = (unsigned int)top_v;
+        q.count[9] = len < reserve ? len : reserve;
+    }
 }
 
 __global__ void k_wf_sort_scatter(Queue q) {

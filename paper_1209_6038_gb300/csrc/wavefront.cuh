@@ -52,6 +52,12 @@ constexpr int SEG_OFFSET = 2 * NBINS_BATCH;
 __host__ __device__ constexpr int batch_key(int vm, int cost) { return vm * NBINS + cost; }
 __host__ __device__ constexpr int key_vm(int key) { return key / NBINS; }
 constexpr size_t QUEUE_HEADER_BYTES = 4096;
+// count[8]: medium segment of the reserved long rays, count[9]: their number, count[10]: their cursor;
+// from count[DEDICATED_FLAGS]: one flag per SM id (mod 256) that hosts a long-ray block
+constexpr int DEDICATED_FLAGS = 576;
+constexpr int LONG_RAY_BLOCKS = 4;  // blocks (SMs) for the long rays of a batch
+static_assert((DEDICATED_FLAGS + 256) * 4 <= (int)QUEUE_HEADER_BYTES, "queue header too small");
+static_assert(DEDICATED_FLAGS * 4 >= 64 + 4 * (SEG_OFFSET + 8), "long-ray flags overlap the bins");
 // every array of the queue starts on a 256-byte boundary (the float4 per-sample buffer needs 16 bytes)
 constexpr size_t queue_array_bytes(long long cap, size_t elem) { return ((size_t)cap * elem + 255) & ~(size_t)255; }
 constexpr size_t queue_bytes(long long cap) {
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned lo
 // sizes into scatter cursors and medium segments, k_wf_sort_scatter writes the permutation.  With the
 // batch key (medium major, cost minor) every medium occupies one contiguous segment of the permutation,
 // in descending cost order.
-__global__ void k_wf_sort_scan(Queue q, int nbins);
+__global__ void k_wf_sort_scan(Queue q, int nbins, unsigned int reserve);
 __global__ void k_wf_sort_scatter(Queue q);
 
 template <int VAR, int MODE, int INTEG, int PREC>
@@ -178,6 +184,31 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     unsigned int smid = 0;
     if (VAR == V_ANY) asm("mov.u32 %0, %%smid;" : "=r"(smid));
     int seg = VAR == V_ANY ? 3 - (int)(smid & 3u) : 0;
+    // Long-ray blocks (batch): the sort reserved the first rl rays of segment rv -- those that pass
+    // closest to the inner radius, up to ~3e4 steps each -- for the warps of the first
+    // p.dedicated_blocks blocks.  The other blocks resident on those SMs leave at once, so these warps
+    // share their SM's FP64 unit with no others and advance their long rays at close to one warp's
+    // latency; on a full SM they would get a twelfth of it and finish last, after the rest of the queue.
+    // (A block that misses the flag only costs speed: every ray is still integrated once.)
+    unsigned int rv = 0, rl = 0;
+    bool reserve = false;
+    if (VAR == V_ANY) {
+        rl = q.count[9];
+        if (rl) {
+            rv = q.count[8];
+            volatile unsigned int *sm_taken = q.count + DEDICATED_FLAGS;
+            if ((int)blockIdx.x < p.dedicated_blocks) {
+                reserve = true;
+                seg = (int)rv;
+                if (threadIdx.x == 0) sm_taken[smid & 255u] = 1u;
+            } else {
+                __nanosleep(2000);
+                unsigned int f = 0;
+                if ((threadIdx.x & 31u) == 0) f = sm_taken[smid & 255u];
+                if (__shfl_sync(0xffffffffu, f, 0)) return;  // the whole warp leaves
+            }
+        }
+    }
     // lane state
     R h = h0, t = 0;
     int steps = 0, phase = PH_IDLE, slot = -1;
@@ -197,12 +228,25 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
         // ---- refill: a lane without a ray takes the next queued one
         if (phase == PH_IDLE && !drained) {
             if (VAR == V_ANY) {
-                // the current segment first, then the others in descending medium order
-                for (int tries = 0; tries < 4; ++tries) {
-                    const unsigned int len = __ldg(q.bins + SEG_OFFSET + 2 * seg + 1);
+                if (reserve) {  // a long-ray lane: the reserved rays first
+                    const unsigned int k = atomicAdd(q.count + 10, 1u);
+                    if (k < rl) {
+                        slot = q.perm[__ldg(q.bins + SEG_OFFSET + 2 * rv) + k];
+                        seg = (int)rv;
+                        st.vm = seg;
+                        phase = PH_STEP;
+                    } else {
+                        reserve = false;
+                    }
+                }
+                // the current segment first, then the others in descending medium order (segment rv
+                // without its reserved head)
+                for (int tries = 0; tries < 4 && phase != PH_STEP; ++tries) {
+                    const unsigned int skip = (unsigned int)seg == rv ? rl : 0u;
+                    const unsigned int len = __ldg(q.bins + SEG_OFFSET + 2 * seg + 1) - skip;
                     const unsigned int k = len ? atomicAdd(q.count + 4 + seg, 1u) : 0xffffffffu;
                     if (k < len) {
-                        slot = q.perm[__ldg(q.bins + SEG_OFFSET + 2 * seg) + k];
+                        slot = q.perm[__ldg(q.bins + SEG_OFFSET + 2 * seg) + skip + k];
                         st.vm = seg;
                         phase = PH_STEP;
                         break;
@@ -472,7 +516,7 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS);
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS, 0u);
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
