@@ -58,9 +58,9 @@ BF16_PEAK_TFLOPS = float(_measured_peaks().get("bf16_tflops", 1900.0))
 RHS_FLOPS = {(0, 0): 0, (0, 1): 36, (1, 0): 34, (1, 1): 30}
 
 # DRAM bytes (read + write) of one launch of the any-medium integration kernel on the full step: one
-# ncu capture of the same twelve views at 480x270 x 4 spp (120.5 MB read + 53.9 MB written) scaled by
+# ncu capture of the same twelve views at 480x270 x 4 spp (122.5 MB read + 54.1 MB written) scaled by
 # samples (x 16.0).  To be re-captured whenever the kernel changes.
-INTEGRATE_TRAFFIC_BYTES = (120.548352e6 + 53.887488e6) * (1920 * 1080) / (480 * 270)
+INTEGRATE_TRAFFIC_BYTES = (122.539008e6 + 54.080512e6) * (1920 * 1080) / (480 * 270)
 DP45_FIXED, RK4_FIXED = 362, 102
 
 
