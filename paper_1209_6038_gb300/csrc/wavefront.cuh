@@ -192,10 +192,11 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     // (A block that misses the flag only costs speed: every ray is still integrated once.)
     unsigned int rv = 0, rl = 0;
     bool reserve = false;
-    if (VAR == V_ANY) {
+    {
         rl = q.count[9];
         if (rl) {
             rv = q.count[8];
+            if (VAR != V_ANY) asm("mov.u32 %0, %%smid;" : "=r"(smid));
             volatile unsigned int *sm_taken = q.count + DEDICATED_FLAGS;
             if ((int)blockIdx.x < p.dedicated_blocks) {
                 reserve = true;
@@ -254,10 +255,21 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                     seg = (seg + 3) & 3;
                 }
             } else {
-                unsigned int k = atomicAdd(q.count + 1, 1u);
-                if (k < n) {
-                    slot = q.perm[k];
-                    phase = PH_STEP;
+                if (reserve) {  // a long-ray lane: the reserved head of the order first
+                    const unsigned int k = atomicAdd(q.count + 10, 1u);
+                    if (k < rl) {
+                        slot = q.perm[k];
+                        phase = PH_STEP;
+                    } else {
+                        reserve = false;
+                    }
+                }
+                if (phase != PH_STEP) {
+                    const unsigned int k = atomicAdd(q.count + 1, 1u) + rl;
+                    if (k < n) {
+                        slot = q.perm[k];
+                        phase = PH_STEP;
+                    }
                 }
             }
             if (phase == PH_STEP) {
@@ -516,17 +528,20 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS, 0u);
+    const int pk = packet > 0 ? packet : 128;
+    // the slowest rays go to the warps of LONG_RAY_BLOCKS blocks that have their SMs to themselves
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS, (unsigned int)(LONG_RAY_BLOCKS * pk));
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
     // persistent integrator: exactly the resident grid
-    const int pk = packet > 0 ? packet : 128;
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V, M, I, PREC>, pk, 0);
     if (e != cudaSuccess) return e;
-    k_wf_integrate<V, M, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(p, q);
+    Params pl = p;
+    pl.dedicated_blocks = LONG_RAY_BLOCKS;
+    k_wf_integrate<V, M, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(pl, q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);
