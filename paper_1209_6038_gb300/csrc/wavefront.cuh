@@ -184,30 +184,27 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     unsigned int smid = 0;
     if (VAR == V_ANY) asm("mov.u32 %0, %%smid;" : "=r"(smid));
     int seg = VAR == V_ANY ? 3 - (int)(smid & 3u) : 0;
-    // Long-ray blocks (batch): the sort reserved the first rl rays of segment rv -- those that pass
-    // closest to the inner radius, up to ~3e4 steps each -- for the warps of the first
-    // p.dedicated_blocks blocks.  The other blocks resident on those SMs leave at once, so these warps
-    // share their SM's FP64 unit with no others and advance their long rays at close to one warp's
-    // latency; on a full SM they would get a twelfth of it and finish last, after the rest of the queue.
-    // (A block that misses the flag only costs speed: every ray is still integrated once.)
-    unsigned int rv = 0, rl = 0;
+    // Long-ray blocks: the sort reserved the first rl rays of the order (of medium segment rv in a
+    // batch) -- those that pass closest to the inner radius, up to ~3e4 steps each -- for the warps of
+    // the first p.dedicated_blocks blocks.  The other blocks resident on those SMs leave at once, so
+    // these warps share their SM's FP64 unit with no others and advance their long rays at close to
+    // one warp's latency; on a full SM they would get a twelfth of it and finish last, after the rest
+    // of the queue.  (A block that misses the flag only costs speed: every ray is still integrated once.)
+    const unsigned int rl = q.count[9];
+    const unsigned int rv = rl ? q.count[8] : 0u;
     bool reserve = false;
-    {
-        rl = q.count[9];
-        if (rl) {
-            rv = q.count[8];
-            if (VAR != V_ANY) asm("mov.u32 %0, %%smid;" : "=r"(smid));
-            volatile unsigned int *sm_taken = q.count + DEDICATED_FLAGS;
-            if ((int)blockIdx.x < p.dedicated_blocks) {
-                reserve = true;
-                seg = (int)rv;
-                if (threadIdx.x == 0) sm_taken[smid & 255u] = 1u;
-            } else {
-                __nanosleep(2000);
-                unsigned int f = 0;
-                if ((threadIdx.x & 31u) == 0) f = sm_taken[smid & 255u];
-                if (__shfl_sync(0xffffffffu, f, 0)) return;  // the whole warp leaves
-            }
+    if (rl) {
+        if (VAR != V_ANY) asm("mov.u32 %0, %%smid;" : "=r"(smid));
+        volatile unsigned int *sm_taken = q.count + DEDICATED_FLAGS;
+        if ((int)blockIdx.x < p.dedicated_blocks) {
+            reserve = true;
+            seg = (int)rv;
+            if (threadIdx.x == 0) sm_taken[smid & 255u] = 1u;
+        } else {
+            __nanosleep(2000);
+            unsigned int f = 0;
+            if ((threadIdx.x & 31u) == 0) f = sm_taken[smid & 255u];
+            if (__shfl_sync(0xffffffffu, f, 0)) return;  // the whole warp leaves
         }
     }
     // lane state
