@@ -103,7 +103,7 @@ static int make_params(const cloak *h, ck::Params &p) {
     p.invKf = (float)p.invK;
     p.R1sq_hf = (float)p.R1sq;
     p.R1sq_lf = (float)(p.R1sq - (double)p.R1sq_hf);
-    p.band_limf = (float)(p.R1 + p.mixed_band);
+    p.band_limf = p.mixed_band > 0.0 ? (float)(p.R1 + p.mixed_band) : 0.f;
     p.h_or_tol = h->h_or_tol;
     p.max_steps = h->max_steps;
     double w[3], u[3], v[3];

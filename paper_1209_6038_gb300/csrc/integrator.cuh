@@ -280,8 +280,8 @@ struct StepperMixed {
     __device__ __forceinline__ bool island(const Params &p) const {
         if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD) || (VAR == V_ANY && vm == 0)) return false;
         float x = yh[0] + yl[0], y = yh[1] + yl[1];
-        if (!(p.mixed_band > 0.0)) return false;
-        const float lim = p.band_limf;
+        const float lim = p.band_limf;  // 0 without a band
+        if (!(lim > 0.f)) return false;
         return x * x + y * y < lim * lim;
     }
     // stage point y + d: x, y as float-float (t, tl), the rest in FP32
