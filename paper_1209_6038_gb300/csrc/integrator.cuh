@@ -23,8 +23,6 @@
 
 namespace ck {
 
-struct Queue;
-
 // ------------------------------------------------------------------ FP64 stepper
 template <int VAR, int MODE, int INTEG>
 struct Stepper64 {
@@ -468,10 +466,8 @@ struct StepperMixed {
     }
 };
 
-// ------------------------------------------------------------------ the persistent loop
+// ------------------------------------------------------------------ lane phases of the persistent loop
+// (k_wf_integrate in wavefront.cuh)
 enum { PH_STEP = 0, PH_CROSS = 1, PH_FINAL = 2, PH_IDLE = 3 };
-
-template <int VAR, int MODE, int INTEG, class S>
-__device__ __forceinline__ void integrate_loop(const Params &p, const Queue &q);
 
 }  // namespace ck
