@@ -63,6 +63,10 @@ RHS_FLOPS = {(0, 0): 0, (0, 1): 36, (1, 0): 34, (1, 1): 30}
 INTEGRATE_TRAFFIC_BYTES = (122.539008e6 + 54.080512e6) * (1920 * 1080) / (480 * 270)
 DP45_FIXED, RK4_FIXED = 362, 102
 
+# bytes per view of the table a batched render copies host to device at every step (the camera frame,
+# sample offsets, output pointer and size of each view; csrc/batch.h: ViewDev)
+VIEW_TABLE_BYTES = 152
+
 
 def flops_per_step(variant, mode, integ):
     r = RHS_FLOPS[(variant, mode)]
@@ -660,10 +664,12 @@ def main():
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
         e2e_s = replicas.max_over_ranks(statistics.mean(e2e_ms) / 1e3, device="cuda")  # the slowest rank's
         e2e = replicas.whole_job_rate(rays_step, e2e_s, ws)
-        out["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0,
+        out["e2e"] = {"value": e2e, "unit": UNIT,
+                      "h2d_bytes_per_step": VIEW_TABLE_BYTES * len(w.images) if args.schedule == "batched" else 0,
                       "d2h_bytes_per_step": sum(im.numel() * 4 for im in imgs),
-                      "note": "inputs are camera and integrator parameters (host structs passed through the C ABI); "
-                              "outputs are the 12 float4 images copied to pinned host memory"}
+                      "note": "inputs are camera and integrator parameters (host structs passed through the C ABI; the "
+                              "batched render copies its view table to the device each step); outputs are the 12 "
+                              "float4 images copied to pinned host memory"}
 
 
     if rank == 0:

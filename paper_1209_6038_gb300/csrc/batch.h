@@ -17,6 +17,8 @@ struct ViewDev {
     int W, Hp, vm;                               // size; vm = 2 * variant + polarization
     int pad;
 };
+// one entry per view is copied host to device at every batched render (bench.py counts these bytes)
+static_assert(sizeof(ViewDev) == 152, "view table entry size changed: update bench.py's VIEW_TABLE_BYTES");
 
 // view of global sample (by_pixel false) or pixel (by_pixel true) g: binary search on the prefix sums
 __device__ __forceinline__ int find_view(const ViewDev *v, int n, long long g, bool by_pixel) {
