@@ -563,7 +563,8 @@ def main():
             self.hs = make_handles(schedule, precision)
             for c in self.hs.values():
                 c.stage_timing(True)
-            self.launches = (4 if schedule == ck.SCHED_WAVEFRONT else 1) * len(w.images)
+            # kernels per image: entry, sort scan, sort scatter, integrate, exit, resolve (wavefront); one (plain)
+            self.launches = (6 if schedule == ck.SCHED_WAVEFRONT else 1) * len(w.images)
 
         def step(self, stage_ms=None):
             for i, (v, m, e) in enumerate(w.images):
@@ -588,7 +589,9 @@ def main():
             for i, (v, m, e) in enumerate(w.images):
                 eye, tgt, up = inputs.camera_pose(e)
                 self.views.append((v, m, eye, tgt, up, w.hfov_deg, imgs[i]))
-            self.launches = 7  # entry, sort scan, sort scatter, integrate, exit, resolve + the table copy
+            # kernels per step: entry, sort scan, sort scatter, integrate, exit, resolve (the view-table copy
+            # and the queue-header memset of the same graph are not kernels)
+            self.launches = 6
 
         def step(self, stage_ms=None):
             ck.cloak_render_batch(self.h.h, self.views, w.spp, w.seed)
