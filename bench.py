@@ -9,7 +9,10 @@ second (whole job).  Also reported: the plain FP64 path (one thread per pixel),
 the roofline of the dominant kernel against the FP64 ALU peak, the CPU FP64
 oracle on a bounded sample of the same workload (and the exit-direction error
 against it), an end-to-end number through the public API with the images copied
-to pinned host memory, and the SM clocks seen during the timed region.
+to pinned host memory, the SM clocks seen during the timed region, the mixed-
+precision forms (the band near R1 in FP64 and in double-float) with their error
+against the oracle, the learned surrogate with its FP64 fallback, a 256-view
+batched orbit and the Fermat/Hamiltonian comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 """
