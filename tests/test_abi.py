@@ -52,3 +52,27 @@ def test_record_layout():
     import oracle
     assert cloak.RECORD_DTYPE.itemsize == 80
     assert cloak.RECORD_DTYPE == oracle.RECORD_DTYPE
+
+
+def declared_enums():
+    """CLOAK_<NAME> = value pairs of every enum in include/*.h."""
+    vals = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+            for name, v in re.findall(r"\bCLOAK_(\w+)\s*=\s*(-?\d+)", body):
+                vals[name] = int(v)
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's constants carry the header's enum values (precision, schedule, panels, ray
+    status, error codes, ...): a value passed through the ABI means the same on both sides."""
+    from paper_1209_6038_gb300 import cloak
+    vals = declared_enums()
+    assert len(vals) >= 35
+    for name, v in vals.items():
+        if name.startswith("RAY_"):
+            assert cloak.RAY_STATUS[v] == name[4:], name
+        else:
+            assert getattr(cloak, name) == v, name
