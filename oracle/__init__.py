@@ -113,6 +113,28 @@ def lib():
     return _lib
 
 
+_ext_libs = {}
+
+
+def ext_lib(kind: str = "ld"):
+    """The same oracle source built in extended precision (kind "ld": long double, "q": _Float128), for the
+    rays FP64 cannot determine.  Only orc_render and orc_trace_rays are bound: their arguments are FP64 in
+    every build (inputs exact, outputs rounded once at the end)."""
+    if kind not in _ext_libs:
+        L = C.CDLL(_build.build_ext(kind))
+        L.orc_trace_rays.argtypes = [C.POINTER(_Cloak), C.POINTER(_Integ), C.c_int, C.POINTER(C.c_double),
+                                     C.c_long, C.c_void_p, C.c_int]
+        L.orc_render.argtypes = [C.POINTER(_Cloak), C.POINTER(_Integ), C.POINTER(_Camera), C.c_int, C.c_int,
+                                 C.c_uint64, C.POINTER(C.c_int64), C.c_long, C.POINTER(C.c_double), C.c_void_p,
+                                 C.c_int]
+        _ext_libs[kind] = L
+    return _ext_libs[kind]
+
+
+def _select(precision):
+    return lib() if precision == "f64" else ext_lib(precision)
+
+
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -297,11 +319,12 @@ def trace_ray(cloak: Cloak, integ: Integrator, mode, o, d, path_cap=0):
     return rec[0], path[: min(plen.value, path_cap)]
 
 
-def trace_rays(cloak: Cloak, integ: Integrator, mode, rays, nthreads=None):
+def trace_rays(cloak: Cloak, integ: Integrator, mode, rays, nthreads=None, precision="f64"):
+    """precision: "f64" (the oracle), or "ld" / "q" (the same source in extended precision)."""
     rays = np.ascontiguousarray(rays, dtype=np.float64).reshape(-1, 6)
     n = rays.shape[0]
     recs = np.zeros(n, dtype=RECORD_DTYPE)
-    lib().orc_trace_rays(cloak.ref, integ.ref, mode, _dp(rays), n, recs.ctypes.data_as(C.c_void_p),
+    _select(precision).orc_trace_rays(cloak.ref, integ.ref, mode, _dp(rays), n, recs.ctypes.data_as(C.c_void_p),
                          nthreads or os.cpu_count() or 1)
     return recs
 
@@ -321,9 +344,10 @@ def shade(cloak: Cloak, p, d):
 
 
 def render(cloak: Cloak, integ: Integrator, cam: Camera, mode, spp=1, seed=0, pixels=None, nthreads=None,
-           records=True):
+           records=True, precision="f64"):
     """Whole image (or a pixel subset, flat indices j*W+i): RGBA = mean over samples of
-    weight * colour (alpha = mean weight) and per-sample records."""
+    weight * colour (alpha = mean weight) and per-sample records.  precision: "f64" (the oracle), or
+    "ld" / "q" (the same source in extended precision)."""
     if pixels is None:
         npix = cam.width * cam.height
         pix_ptr = None
@@ -333,7 +357,7 @@ def render(cloak: Cloak, integ: Integrator, cam: Camera, mode, spp=1, seed=0, pi
         pix_ptr = pixels.ctypes.data_as(C.POINTER(C.c_int64))
     rgba = np.zeros((npix, 4))
     recs = np.zeros(npix * spp, dtype=RECORD_DTYPE) if records else None
-    lib().orc_render(cloak.ref, integ.ref, cam.ref, mode, spp, seed, pix_ptr, npix, _dp(rgba),
+    _select(precision).orc_render(cloak.ref, integ.ref, cam.ref, mode, spp, seed, pix_ptr, npix, _dp(rgba),
                      recs.ctypes.data_as(C.c_void_p) if records else None, nthreads or os.cpu_count() or 1)
     return rgba, recs
 

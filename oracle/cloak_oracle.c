@@ -13,37 +13,57 @@
  *
  * Readings where the paper is silent are marked "Reading:".
  */
+#define __STDC_WANT_IEC_60559_TYPES_EXT__ 1 /* _Float128 in <tgmath.h> (extended-precision build) */
 #include "cloak_oracle.h"
 
 #include <complex.h>
-#include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
 
-typedef double complex cplx;
+/* Arithmetic type.  The oracle is FP64 (orc_real = double).  The same source also builds in extended
+   precision (cloak_oracle.h: ORC_REAL_KIND 1 = long double, 2 = _Float128) to settle what FP64 cannot determine:
+   <tgmath.h> makes sqrt, sin, fabs, ... follow the argument type, complex arguments included. */
+typedef orc_real real;
+#if ORC_REAL_KIND == 0
+typedef _Complex double cplx;
+#define R_PI 3.141592653589793
+#elif ORC_REAL_KIND == 1
+typedef _Complex long double cplx;
+#define R_PI 3.14159265358979323846264338327950288L
+#else
+typedef _Complex _Float128 cplx;
+#define R_PI 3.14159265358979323846264338327950288f128
+#endif
+/* exact ratios of the Dormand-Prince tableau evaluated in the arithmetic type */
+#define R(x) ((real)(x))
+static cplx csqrt_r(cplx z) { return sqrt(z); }
+static real cabs_r(cplx z) { return fabs(z); }
 
 /* ------------------------------------------------------------------ */
 /* small linear algebra                                                */
 /* ------------------------------------------------------------------ */
-static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
-static void cross3(const double a[3], const double b[3], double o[3]) {
+static real dot3(const real a[3], const real b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const real a[3], const real b[3], real o[3]) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
-static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
-static void matvec3(const double A[9], const double x[3], double y[3]) {
+static real norm3(const real a[3]) { return sqrt(dot3(a, a)); }
+/* a vector of the (FP64) input structures in the arithmetic type */
+static void vec_in(const double a[3], real o[3]) { o[0] = a[0]; o[1] = a[1]; o[2] = a[2]; }
+static void matvec3(const real A[9], const real x[3], real y[3]) {
     for (int i = 0; i < 3; ++i) y[i] = A[3 * i] * x[0] + A[3 * i + 1] * x[1] + A[3 * i + 2] * x[2];
 }
 /* some unit vector perpendicular to n */
-static void any_perp(const double n[3], double t[3]) {
-    double ax[3] = {1.0, 0.0, 0.0};
+static void any_perp(const real n[3], real t[3]) {
+    real ax[3] = {1.0, 0.0, 0.0};
     if (fabs(n[0]) > 0.9) { ax[0] = 0.0; ax[1] = 1.0; }
     cross3(n, ax, t);
-    double l = norm3(t);
+    real l = norm3(t);
     for (int i = 0; i < 3; ++i) t[i] /= l;
 }
 
@@ -53,11 +73,11 @@ static void ccross3(const cplx a[3], const cplx b[3], cplx o[3]) {
     o[1] = a[2] * b[0] - a[0] * b[2];
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
-static double cnorm2(const cplx a[3]) {
+static real cnorm2(const cplx a[3]) {
     return creal(a[0] * conj(a[0]) + a[1] * conj(a[1]) + a[2] * conj(a[2]));
 }
 /* normal component of the time-averaged Poynting vector, n . Re(E x H*) (factor 1/2 dropped) */
-static double normal_flux(const double n[3], const cplx E[3], const cplx H[3]) {
+static real normal_flux(const real n[3], const cplx E[3], const cplx H[3]) {
     cplx Hc[3] = {conj(H[0]), conj(H[1]), conj(H[2])}, S[3];
     ccross3(E, Hc, S);
     return n[0] * creal(S[0]) + n[1] * creal(S[1]) + n[2] * creal(S[2]);
@@ -67,8 +87,8 @@ static int solve4(cplx A[4][4], cplx b[4], cplx x[4]) {
     for (int col = 0; col < 4; ++col) {
         int piv = col;
         for (int r = col + 1; r < 4; ++r)
-            if (cabs(A[r][col]) > cabs(A[piv][col])) piv = r;
-        if (cabs(A[piv][col]) == 0.0) return 0;
+            if (cabs_r(A[r][col]) > cabs_r(A[piv][col])) piv = r;
+        if (cabs_r(A[piv][col]) == 0.0) return 0;
         if (piv != col) {
             for (int k = 0; k < 4; ++k) { cplx t = A[col][k]; A[col][k] = A[piv][k]; A[piv][k] = t; }
             cplx t = b[col]; b[col] = b[piv]; b[piv] = t;
@@ -110,12 +130,12 @@ double orc_uniform(uint64_t seed, uint64_t pixel, uint32_t sample, uint32_t dim)
 /* ------------------------------------------------------------------ */
 /* Cylindrical components (eps'_r, eps'_theta, eps'_z) at radius r and their
    r-derivatives.  a = R1, b = R2. */
-static void cyl_eps(const orc_cloak *c, double r, double e[3], double de[3]) {
-    double a = c->R1, b = c->R2;
-    double K = (b / (b - a)) * (b / (b - a));
-    double q = (r - a) / r;
-    double er = q * q * K;                      /* ((r-a)/r)^2 (b/(b-a))^2 */
-    double der = 2.0 * q * (a / (r * r)) * K;   /* d/dr of the above */
+static void cyl_eps(const orc_cloak *c, real r, real e[3], real de[3]) {
+    real a = c->R1, b = c->R2;
+    real K = (b / (b - a)) * (b / (b - a));
+    real q = (r - a) / r;
+    real er = q * q * K;                      /* ((r-a)/r)^2 (b/(b-a))^2 */
+    real der = 2.0 * q * (a / (r * r)) * K;   /* d/dr of the above */
     e[0] = er;
     de[0] = der;
     e[1] = K; /* eps'_theta = (b/(b-a))^2 in both Eq. 14 and Eq. 15 */
@@ -123,7 +143,7 @@ static void cyl_eps(const orc_cloak *c, double r, double e[3], double de[3]) {
     if (c->variant == ORC_RADIAL) { e[2] = K; de[2] = 0.0; }   /* Eq. 14 */
     else { e[2] = er; de[2] = der; }                            /* Eq. 15 */
 }
-static void cyl_basis(const double x[3], double *r, double rh[3], double th[3]) {
+static void cyl_basis(const real x[3], real *r, real rh[3], real th[3]) {
     *r = hypot(x[0], x[1]);
     rh[0] = x[0] / *r; rh[1] = x[1] / *r; rh[2] = 0.0;
     th[0] = -x[1] / *r; th[1] = x[0] / *r; th[2] = 0.0;
@@ -131,11 +151,13 @@ static void cyl_basis(const double x[3], double *r, double rh[3], double th[3]) 
 
 /* Cartesian permittivity tensor (Eq. 1 rotated to the lab frame), with the
    ordinary/extraordinary values and the optic axis c-hat. */
-void orc_permittivity(const orc_cloak *c, const double x[3], double eps[9], double *eps_o, double *eps_e,
-                      double chat[3]) {
+void orc_permittivity(const orc_cloak *c, const real x[3], real eps[9], real *eps_o, real *eps_e,
+                      real chat[3]) {
     if (c->variant == ORC_TEST_CONST) {
-        double l = norm3(c->c_test);
-        for (int i = 0; i < 3; ++i) chat[i] = c->c_test[i] / l;
+        real ct[3];
+        vec_in(c->c_test, ct);
+        real l = norm3(ct);
+        for (int i = 0; i < 3; ++i) chat[i] = ct[i] / l;
         *eps_o = c->eps_o_test;
         *eps_e = c->eps_e_test;
         for (int i = 0; i < 3; ++i)
@@ -143,7 +165,7 @@ void orc_permittivity(const orc_cloak *c, const double x[3], double eps[9], doub
                 eps[3 * i + j] = (i == j ? *eps_o : 0.0) + (*eps_e - *eps_o) * chat[i] * chat[j];
         return;
     }
-    double r, rh[3], th[3], zh[3] = {0, 0, 1}, e[3], de[3];
+    real r, rh[3], th[3], zh[3] = {0, 0, 1}, e[3], de[3];
     cyl_basis(x, &r, rh, th);
     cyl_eps(c, r, e, de);
     for (int i = 0; i < 3; ++i)
@@ -163,17 +185,19 @@ void orc_permittivity(const orc_cloak *c, const double x[3], double eps[9], doub
    the reciprocal principal values times the projectors -- no numerical
    inversion (which would lose ~eps_max/eps_min of relative precision near
    r = R1, where one principal value tends to zero). */
-static void inv_permittivity(const orc_cloak *c, const double x[3], double ie[9]) {
+static void inv_permittivity(const orc_cloak *c, const real x[3], real ie[9]) {
     if (c->variant == ORC_TEST_CONST) {
-        double l = norm3(c->c_test), ch[3];
-        for (int i = 0; i < 3; ++i) ch[i] = c->c_test[i] / l;
+        real ct[3], ch[3];
+        vec_in(c->c_test, ct);
+        real l = norm3(ct);
+        for (int i = 0; i < 3; ++i) ch[i] = ct[i] / l;
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j)
                 ie[3 * i + j] = (i == j ? 1.0 / c->eps_o_test : 0.0) +
                                 (1.0 / c->eps_e_test - 1.0 / c->eps_o_test) * ch[i] * ch[j];
         return;
     }
-    double r, rh[3], th[3], zh[3] = {0, 0, 1}, e[3], de[3];
+    real r, rh[3], th[3], zh[3] = {0, 0, 1}, e[3], de[3];
     cyl_basis(x, &r, rh, th);
     cyl_eps(c, r, e, de);
     for (int i = 0; i < 3; ++i)
@@ -183,27 +207,27 @@ static void inv_permittivity(const orc_cloak *c, const double x[3], double ie[9]
 
 /* Eq. 7: M = n_o^2 n_e^2 eps^{-1} and its Cartesian gradient.
    dM[9*k + 3*i + j] = d M_ij / d x_k. */
-void orc_aux_matrix(const orc_cloak *c, const double x[3], double M[9], double dM[27]) {
-    double eps[9], eo, ee, ch[3], ie[9];
+void orc_aux_matrix(const orc_cloak *c, const real x[3], real M[9], real dM[27]) {
+    real eps[9], eo, ee, ch[3], ie[9];
     orc_permittivity(c, x, eps, &eo, &ee, ch);
     inv_permittivity(c, x, ie);
-    double P = eo * ee; /* n_o^2 n_e^2 */
+    real P = eo * ee; /* n_o^2 n_e^2 */
     for (int i = 0; i < 9; ++i) M[i] = P * ie[i];
     if (c->variant == ORC_TEST_CONST) {
-        memset(dM, 0, 27 * sizeof(double));
+        memset(dM, 0, 27 * sizeof(real));
         return;
     }
-    double r, rh[3], th[3], zh[3] = {0, 0, 1}, e[3], de[3];
+    real r, rh[3], th[3], zh[3] = {0, 0, 1}, e[3], de[3];
     cyl_basis(x, &r, rh, th);
     cyl_eps(c, r, e, de);
-    double deo, dee; /* d eps_o / dr, d eps_e / dr */
+    real deo, dee; /* d eps_o / dr, d eps_e / dr */
     if (c->variant == ORC_RADIAL) { dee = de[0]; deo = de[1]; }
     else { dee = de[1]; deo = de[0]; }
     for (int k = 0; k < 3; ++k) {
         /* derivatives of the basis along x_k: d rh = th_k th / r, d th = -th_k rh / r, d zh = 0 */
-        double drh[3], dth[3];
+        real drh[3], dth[3];
         for (int i = 0; i < 3; ++i) { drh[i] = th[k] * th[i] / r; dth[i] = -th[k] * rh[i] / r; }
-        double die[9]; /* d(eps^{-1}) / dx_k */
+        real die[9]; /* d(eps^{-1}) / dx_k */
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j)
                 die[3 * i + j] = -de[0] / (e[0] * e[0]) * rh[k] * rh[i] * rh[j] +
@@ -211,14 +235,14 @@ void orc_aux_matrix(const orc_cloak *c, const double x[3], double M[9], double d
                                  de[1] / (e[1] * e[1]) * rh[k] * th[i] * th[j] +
                                  (dth[i] * th[j] + th[i] * dth[j]) / e[1] -
                                  de[2] / (e[2] * e[2]) * rh[k] * zh[i] * zh[j];
-        double dP = (deo * ee + eo * dee) * rh[k];
+        real dP = (deo * ee + eo * dee) * rh[k];
         for (int i = 0; i < 9; ++i) dM[9 * k + i] = dP * ie[i] + P * die[i];
     }
 }
 
 /* Eq. 7 inverted: M^{-1} = eps / (n_o^2 n_e^2). */
-void orc_aux_inverse(const orc_cloak *c, const double x[3], double Mi[9]) {
-    double eps[9], eo, ee, ch[3];
+void orc_aux_inverse(const orc_cloak *c, const real x[3], real Mi[9]) {
+    real eps[9], eo, ee, ch[3];
     orc_permittivity(c, x, eps, &eo, &ee, ch);
     for (int i = 0; i < 9; ++i) Mi[i] = eps[i] / (eo * ee);
 }
@@ -226,16 +250,16 @@ void orc_aux_inverse(const orc_cloak *c, const double x[3], double Mi[9]) {
 /* Eq. 8: dv/dt = (1/2) M^{-1} [ v (grad M) v - 2 ((grad M) . v) v ].
    Reading: component i of "v (grad M) v" is v^T (d_i M) v; "((grad M) . v) v"
    is sum_l v_l (d_l M) v. */
-void orc_eq8_accel(const double Mi[9], const double dM[27], const double v[3], double a[3]) {
-    double g[3], h[3], w[3];
+void orc_eq8_accel(const real Mi[9], const real dM[27], const real v[3], real a[3]) {
+    real g[3], h[3], w[3];
     for (int i = 0; i < 3; ++i) {
-        double s = 0.0;
+        real s = 0.0;
         for (int j = 0; j < 3; ++j)
             for (int k = 0; k < 3; ++k) s += v[j] * dM[9 * i + 3 * j + k] * v[k];
         g[i] = s;
     }
     for (int j = 0; j < 3; ++j) {
-        double s = 0.0;
+        real s = 0.0;
         for (int l = 0; l < 3; ++l)
             for (int k = 0; k < 3; ++k) s += v[l] * dM[9 * l + 3 * j + k] * v[k];
         h[j] = s;
@@ -246,30 +270,30 @@ void orc_eq8_accel(const double Mi[9], const double dM[27], const double v[3], d
 }
 
 /* Eq. 2: dv/dt = ( |v|^2 grad n - 2 (grad n . v) v ) / n. */
-void orc_eq2_accel(double n, const double gn[3], const double v[3], double a[3]) {
-    double vv = dot3(v, v), gv = dot3(gn, v);
+void orc_eq2_accel(real n, const real gn[3], const real v[3], real a[3]) {
+    real vv = dot3(v, v), gv = dot3(gn, v);
     for (int i = 0; i < 3; ++i) a[i] = (vv * gn[i] - 2.0 * gv * v[i]) / n;
 }
 
 /* right-hand side of the first-order system y = (x, v): dx/dt = v, dv/dt = Eq. 2 (o) or Eq. 8 (e) */
-void orc_rhs(const orc_cloak *c, int mode, const double y[6], double dy[6]) {
-    const double *x = y, *v = y + 3;
+void orc_rhs(const orc_cloak *c, int mode, const real y[6], real dy[6]) {
+    const real *x = y, *v = y + 3;
     dy[0] = v[0]; dy[1] = v[1]; dy[2] = v[2];
     if (mode == ORC_EXTRAORDINARY) {
-        double M[9], dM[27], Mi[9];
+        real M[9], dM[27], Mi[9];
         orc_aux_matrix(c, x, M, dM);
         orc_aux_inverse(c, x, Mi);
         orc_eq8_accel(Mi, dM, v, dy + 3);
     } else {
-        double gn[3] = {0, 0, 0}, n;
+        real gn[3] = {0, 0, 0}, n;
         if (c->variant == ORC_TEST_CONST) {
             n = sqrt(c->eps_o_test);
         } else {
-            double r, rh[3], th[3], e[3], de[3];
+            real r, rh[3], th[3], e[3], de[3];
             cyl_basis(x, &r, rh, th);
             cyl_eps(c, r, e, de);
-            double eo = (c->variant == ORC_RADIAL) ? e[1] : e[0];
-            double deo = (c->variant == ORC_RADIAL) ? de[1] : de[0];
+            real eo = (c->variant == ORC_RADIAL) ? e[1] : e[0];
+            real deo = (c->variant == ORC_RADIAL) ? de[1] : de[0];
             n = sqrt(eo);                       /* n_o = sqrt(eps_o) */
             for (int i = 0; i < 3; ++i) gn[i] = deo / (2.0 * n) * rh[i];
         }
@@ -284,9 +308,9 @@ void orc_rhs(const orc_cloak *c, int mode, const double y[6], double dy[6]) {
    makes angle phi with -n-hat inside the plane of incidence (unit tangent t).
    Eq. 10 gives the angle of D_e with c-hat through its sine; only its sine and
    cosine squared enter Eq. 9, so the arcsin is not taken. */
-static double eq9_index(double no, double ne, const double ch[3], const double t[3], const double n[3], double phi) {
-    double s = dot3(ch, t) * sin(phi) - dot3(ch, n) * cos(phi);
-    double s2 = s * s, c2 = 1.0 - s2;
+static real eq9_index(real no, real ne, const real ch[3], const real t[3], const real n[3], real phi) {
+    real s = dot3(ch, t) * sin(phi) - dot3(ch, n) * cos(phi);
+    real s2 = s * s, c2 = 1.0 - s2;
     return no * ne / sqrt(no * no * c2 + ne * ne * s2);
 }
 
@@ -294,41 +318,41 @@ static double eq9_index(double no, double ne, const double ch[3], const double t
    normal n) whose tangential wave vector is kt, travelling inward.
    Returns 1 with k and v = M^{-1} k (Eq. 6), or 0 if the mode has no real
    angle of refraction in [0, pi/2] (evanescent). */
-int orc_refract_into(const orc_cloak *c, int mode, const double x[3], const double n[3], const double kt[3],
-                     double k[3], double v[3]) {
-    double eps[9], eo, ee, ch[3];
+int orc_refract_into(const orc_cloak *c, int mode, const real x[3], const real n[3], const real kt[3],
+                     real k[3], real v[3]) {
+    real eps[9], eo, ee, ch[3];
     orc_permittivity(c, x, eps, &eo, &ee, ch);
-    double no = sqrt(eo), ne = sqrt(ee);
-    double st = norm3(kt); /* n_i sin(phi_i), left side of Eq. 11 */
-    double t[3];
+    real no = sqrt(eo), ne = sqrt(ee);
+    real st = norm3(kt); /* n_i sin(phi_i), left side of Eq. 11 */
+    real t[3];
     if (st > 0.0) for (int i = 0; i < 3; ++i) t[i] = kt[i] / st;
     else any_perp(n, t);
     if (mode == ORC_ORDINARY) {
-        double s = st / no; /* Eq. 11: n_o sin(phi_o) = n_i sin(phi_i) */
+        real s = st / no; /* Eq. 11: n_o sin(phi_o) = n_i sin(phi_i) */
         if (s > 1.0) return 0;
-        double phi = asin(s);
+        real phi = asin(s);
         for (int i = 0; i < 3; ++i) k[i] = no * (t[i] * sin(phi) - n[i] * cos(phi)); /* |k_o| = n_o */
         for (int i = 0; i < 3; ++i) v[i] = k[i] / eo; /* Eq. 6 with M = n_o^2 I */
         return 1;
     }
     /* Eq. 11 for the extraordinary wave: n(phi) sin(phi) = st, root in [0, pi/2] by bisection */
-    double phi;
+    real phi;
     if (st == 0.0) {
         phi = 0.0;
     } else {
-        double hi = 0.5 * M_PI, lo = 0.0;
+        real hi = 0.5 * R_PI, lo = 0.0;
         if (eq9_index(no, ne, ch, t, n, hi) * sin(hi) - st < 0.0) return 0;
         for (int it = 0; it < 400; ++it) {
-            double mid = 0.5 * (lo + hi);
+            real mid = 0.5 * (lo + hi);
             if (mid <= lo || mid >= hi) break;
             if (eq9_index(no, ne, ch, t, n, mid) * sin(mid) - st < 0.0) lo = mid;
             else hi = mid;
         }
         phi = 0.5 * (lo + hi);
     }
-    double nn = eq9_index(no, ne, ch, t, n, phi); /* |k_e| = n(phi_e) */
+    real nn = eq9_index(no, ne, ch, t, n, phi); /* |k_e| = n(phi_e) */
     for (int i = 0; i < 3; ++i) k[i] = nn * (t[i] * sin(phi) - n[i] * cos(phi));
-    double Mi[9];
+    real Mi[9];
     orc_aux_inverse(c, x, Mi);
     matvec3(Mi, k, v); /* Eq. 6 */
     return 1;
@@ -338,25 +362,25 @@ int orc_refract_into(const orc_cloak *c, int mode, const double x[3], const doub
    Propagating: Eqs. 9-11 (above).  Evanescent -- Reading: the paper is silent;
    the normal component q solves the dispersion relation |k|^2 = eps_o (o) or
    k^T M^{-1} k = 1 (e) with the branch that decays into the medium. */
-static void inward_wave(const orc_cloak *c, int mode, const double x[3], const double n[3], const double kt[3],
+static void inward_wave(const orc_cloak *c, int mode, const real x[3], const real n[3], const real kt[3],
                         cplx k[3]) {
-    double kr[3], vr[3];
+    real kr[3], vr[3];
     if (orc_refract_into(c, mode, x, n, kt, kr, vr)) {
         for (int i = 0; i < 3; ++i) k[i] = kr[i];
         return;
     }
-    double eps[9], eo, ee, ch[3];
+    real eps[9], eo, ee, ch[3];
     orc_permittivity(c, x, eps, &eo, &ee, ch);
     cplx q;
     if (mode == ORC_ORDINARY) {
-        q = -csqrt(eo - dot3(kt, kt));
+        q = -csqrt_r((cplx)(eo - dot3(kt, kt)));
     } else {
-        double Mi[9], Mn[3], Mk[3];
+        real Mi[9], Mn[3], Mk[3];
         orc_aux_inverse(c, x, Mi);
         matvec3(Mi, n, Mn);
         matvec3(Mi, kt, Mk);
-        double A = dot3(n, Mn), B = dot3(n, Mk), C = dot3(kt, Mk) - 1.0;
-        q = (-B - csqrt(B * B - A * C)) / A;
+        real A = dot3(n, Mn), B = dot3(n, Mk), C = dot3(kt, Mk) - 1.0;
+        q = (-B - csqrt_r((cplx)(B * B - A * C))) / A;
     }
     for (int i = 0; i < 3; ++i) k[i] = kt[i] + q * n[i];
 }
@@ -367,7 +391,7 @@ static void inward_wave(const orc_cloak *c, int mode, const double x[3], const d
    H = k x E (mu = 1, omega = c0 = 1).
    Reading: when k is parallel to c-hat the two modes are degenerate and
    D_o is taken along z-hat x k (x-hat x k if that vanishes too). */
-static void mode_fields(int mode, const cplx k[3], const double ie[9], const double ch[3], cplx E[3], cplx H[3]) {
+static void mode_fields(int mode, const cplx k[3], const real ie[9], const real ch[3], cplx E[3], cplx H[3]) {
     cplx c3[3] = {ch[0], ch[1], ch[2]}, Do[3], D[3];
     ccross3(c3, k, Do);
     if (cnorm2(Do) < 1e-20 * cnorm2(k)) {
@@ -391,12 +415,12 @@ static void mode_fields(int mode, const cplx k[3], const double ie[9], const dou
 
 /* Field directions (D, E, H) of a propagating wave of `mode` with real wave
    vector k at point x (for tests of the Sect. 3 / Sect. 5 field rules). */
-void orc_mode_fields(const orc_cloak *c, int mode, const double x[3], const double k[3], double D[3], double E[3],
-                     double H[3]) {
-    double eps[9], eo, ee, ch[3];
+void orc_mode_fields(const orc_cloak *c, int mode, const real x[3], const real k[3], real D[3], real E[3],
+                     real H[3]) {
+    real eps[9], eo, ee, ch[3];
     orc_permittivity(c, x, eps, &eo, &ee, ch);
     cplx ck[3] = {k[0], k[1], k[2]}, cE[3], cH[3];
-    double ie[9];
+    real ie[9];
     inv_permittivity(c, x, ie);
     mode_fields(mode, ck, ie, ch, cE, cH);
     for (int i = 0; i < 3; ++i) { E[i] = creal(cE[i]); H[i] = creal(cH[i]); }
@@ -404,9 +428,9 @@ void orc_mode_fields(const orc_cloak *c, int mode, const double x[3], const doub
 }
 
 /* s and p unit polarisations of a real vacuum wave k at a face with normal n */
-static void vacuum_basis(const double k[3], const double n[3], double s[3], double p[3]) {
+static void vacuum_basis(const real k[3], const real n[3], real s[3], real p[3]) {
     cross3(k, n, s);
-    double l = norm3(s);
+    real l = norm3(s);
     if (l < 1e-12) any_perp(n, s);
     else for (int i = 0; i < 3; ++i) s[i] /= l;
     cross3(s, k, p);
@@ -415,10 +439,10 @@ static void vacuum_basis(const double k[3], const double n[3], double s[3], doub
 /* Eq. 12 at a vacuum -> medium face.  Incident unit vacuum direction d
    (d . n < 0), outward normal n, face point x.  out = {T_o^s, T_o^p, T_e^s,
    T_e^p, R^s, R^p, T_o (unpolarised), T_e (unpolarised)}. */
-static int vacuum_face(const orc_cloak *c, const double x[3], const double n[3], const double d[3], const double *e3,
-                       double out[9]);
-int orc_transmission_in(const orc_cloak *c, const double x[3], const double n[3], const double d[3], double out[8]) {
-    double o9[9];
+static int vacuum_face(const orc_cloak *c, const real x[3], const real n[3], const real d[3], const real *e3,
+                       real out[9]);
+int orc_transmission_in(const orc_cloak *c, const real x[3], const real n[3], const real d[3], real out[8]) {
+    real o9[9];
     if (!vacuum_face(c, x, n, d, NULL, o9)) return 0;
     for (int i = 0; i < 8; ++i) out[i] = o9[i];
     return 1;
@@ -426,23 +450,23 @@ int orc_transmission_in(const orc_cloak *c, const double x[3], const double n[3]
 
 /* The solve of orc_transmission_in; with e3 (a unit incident polarisation across d) also out[8] = the
    reflectance of that incident wave. */
-static int vacuum_face(const orc_cloak *c, const double x[3], const double n[3], const double d[3], const double *e3,
-                       double out[9]) {
-    double eps[9], eo, ee, ch[3];
+static int vacuum_face(const orc_cloak *c, const real x[3], const real n[3], const real d[3], const real *e3,
+                       real out[9]) {
+    real eps[9], eo, ee, ch[3];
     orc_permittivity(c, x, eps, &eo, &ee, ch);
-    double dn = dot3(d, n), kt[3], kr[3];
+    real dn = dot3(d, n), kt[3], kr[3];
     for (int i = 0; i < 3; ++i) { kt[i] = d[i] - dn * n[i]; kr[i] = d[i] - 2.0 * dn * n[i]; }
     cplx ko[3], ke[3], Eo[3], Ho[3], Ee[3], He[3];
     inward_wave(c, ORC_ORDINARY, x, n, kt, ko);
     inward_wave(c, ORC_EXTRAORDINARY, x, n, kt, ke);
-    double ie[9];
+    real ie[9];
     inv_permittivity(c, x, ie);
     mode_fields(ORC_ORDINARY, ko, ie, ch, Eo, Ho);
     mode_fields(ORC_EXTRAORDINARY, ke, ie, ch, Ee, He);
-    double s[3], pi[3], pr[3];
+    real s[3], pi[3], pr[3];
     vacuum_basis(d, n, s, pi);
     cross3(s, kr, pr); /* reflected wave: same s, p = s x k_r */
-    double t1[3], t2[3];
+    real t1[3], t2[3];
     for (int i = 0; i < 3; ++i) t1[i] = s[i];
     cross3(n, s, t2);
     cplx ckr[3] = {kr[0], kr[1], kr[2]}, cd[3] = {d[0], d[1], d[2]};
@@ -456,7 +480,7 @@ static int vacuum_face(const orc_cloak *c, const double x[3], const double n[3],
         ccross3(cd, Ei, Hi);
         /* tangential continuity of E and H: incident + reflected = transmitted */
         const cplx *cols_E[4] = {Ers, Erp, Eo, Ee}, *cols_H[4] = {Hrs, Hrp, Ho, He};
-        double sign[4] = {1, 1, -1, -1};
+        real sign[4] = {1, 1, -1, -1};
         cplx A[4][4], b[4], u[4];
         for (int col = 0; col < 4; ++col) {
             cplx t1c[3] = {t1[0], t1[1], t1[2]}, t2c[3] = {t2[0], t2[1], t2[2]};
@@ -469,12 +493,12 @@ static int vacuum_face(const orc_cloak *c, const double x[3], const double n[3],
         b[0] = -cdot3(Ei, t1c); b[1] = -cdot3(Ei, t2c);
         b[2] = -cdot3(Hi, t1c); b[3] = -cdot3(Hi, t2c);
         if (!solve4(A, b, u)) return 0;
-        double fi = fabs(normal_flux(n, Ei, Hi));
-        double To = cabs(u[2]) * cabs(u[2]) * fabs(normal_flux(n, Eo, Ho)) / fi;
-        double Te = cabs(u[3]) * cabs(u[3]) * fabs(normal_flux(n, Ee, He)) / fi;
+        real fi = fabs(normal_flux(n, Ei, Hi));
+        real To = cabs_r(u[2]) * cabs_r(u[2]) * fabs(normal_flux(n, Eo, Ho)) / fi;
+        real Te = cabs_r(u[3]) * cabs_r(u[3]) * fabs(normal_flux(n, Ee, He)) / fi;
         cplx Er[3], Hr[3];
         for (int i = 0; i < 3; ++i) { Er[i] = u[0] * Ers[i] + u[1] * Erp[i]; Hr[i] = u[0] * Hrs[i] + u[1] * Hrp[i]; }
-        double R = fabs(normal_flux(n, Er, Hr)) / fi;
+        real R = fabs(normal_flux(n, Er, Hr)) / fi;
         if (pol == 2) { out[8] = R; break; }
         out[0 + pol] = To;
         out[2 + pol] = Te;
@@ -489,27 +513,27 @@ static int vacuum_face(const orc_cloak *c, const double x[3], const double n[3],
    wave of `mode` with real wave vector k, one refracted vacuum wave and two
    reflected waves (o and e) in the medium.  out = {T, R_o, R_e, polariser fraction of the transmitted
    wave}.  Under total internal reflection (|k_t| > 1) T = 0 and R_o + R_e = 1. */
-int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const double n[3], const double k[3],
-                         double out[4]) {
-    double eps[9], eo, ee, ch[3];
+int orc_transmission_out(const orc_cloak *c, int mode, const real x[3], const real n[3], const real k[3],
+                         real out[4]) {
+    real eps[9], eo, ee, ch[3];
     orc_permittivity(c, x, eps, &eo, &ee, ch);
-    double kn = dot3(k, n), kt[3];
+    real kn = dot3(k, n), kt[3];
     for (int i = 0; i < 3; ++i) kt[i] = k[i] - kn * n[i];
-    double kt2 = dot3(kt, kt);
+    real kt2 = dot3(kt, kt);
     out[0] = out[1] = out[2] = out[3] = 0.0;
     /* vacuum side: propagating wave, or under total internal reflection (|k_t| > 1) the evanescent wave
        that decays away from the face (k_n = i sqrt(|k_t|^2 - 1)); it carries no flux */
     const int tir = kt2 > 1.0;
     cplx ckv[3];
     for (int i = 0; i < 3; ++i) ckv[i] = kt[i] + (tir ? I * sqrt(kt2 - 1.0) : sqrt(1.0 - kt2)) * n[i];
-    double s[3];
+    real s[3];
     cross3(kt, n, s); /* s perpendicular to the plane of incidence; p = s x k */
     {
-        double l = norm3(s);
+        real l = norm3(s);
         if (l < 1e-12) any_perp(n, s);
         else for (int i = 0; i < 3; ++i) s[i] /= l;
     }
-    double kv[3] = {creal(ckv[0]), creal(ckv[1]), creal(ckv[2])};
+    real kv[3] = {creal(ckv[0]), creal(ckv[1]), creal(ckv[2])};
     cplx Es[3] = {s[0], s[1], s[2]}, Ep[3], Hs[3], Hp[3];
     ccross3(Es, ckv, Ep);
     ccross3(ckv, Es, Hs);
@@ -517,18 +541,18 @@ int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const 
     cplx kro[3], kre[3], Ero[3], Hro[3], Ere[3], Hre[3], ck[3] = {k[0], k[1], k[2]}, Em[3], Hm[3];
     inward_wave(c, ORC_ORDINARY, x, n, kt, kro);
     inward_wave(c, ORC_EXTRAORDINARY, x, n, kt, kre);
-    double ie[9];
+    real ie[9];
     inv_permittivity(c, x, ie);
     mode_fields(ORC_ORDINARY, kro, ie, ch, Ero, Hro);
     mode_fields(ORC_EXTRAORDINARY, kre, ie, ch, Ere, Hre);
     mode_fields(mode, ck, ie, ch, Em, Hm);
-    double t1[3], t2[3];
+    real t1[3], t2[3];
     for (int i = 0; i < 3; ++i) t1[i] = s[i];
     cross3(n, s, t2);
     cplx t1c[3] = {t1[0], t1[1], t1[2]}, t2c[3] = {t2[0], t2[1], t2[2]};
     /* tangential continuity: incident + reflected (medium side) = transmitted (vacuum side) */
     const cplx *cols_E[4] = {Es, Ep, Ero, Ere}, *cols_H[4] = {Hs, Hp, Hro, Hre};
-    double sign[4] = {1, 1, -1, -1};
+    real sign[4] = {1, 1, -1, -1};
     cplx A[4][4], b[4], u[4];
     for (int col = 0; col < 4; ++col) {
         A[0][col] = sign[col] * cdot3(cols_E[col], t1c);
@@ -539,21 +563,23 @@ int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const 
     b[0] = cdot3(Em, t1c); b[1] = cdot3(Em, t2c);
     b[2] = cdot3(Hm, t1c); b[3] = cdot3(Hm, t2c);
     if (!solve4(A, b, u)) return 0;
-    double fi = fabs(normal_flux(n, Em, Hm));
+    real fi = fabs(normal_flux(n, Em, Hm));
     cplx Et[3], Ht[3];
     for (int i = 0; i < 3; ++i) { Et[i] = u[0] * Es[i] + u[1] * Ep[i]; Ht[i] = u[0] * Hs[i] + u[1] * Hp[i]; }
     out[0] = tir ? 0.0 : fabs(normal_flux(n, Et, Ht)) / fi;
-    out[1] = cabs(u[2]) * cabs(u[2]) * fabs(normal_flux(n, Ero, Hro)) / fi;
-    out[2] = cabs(u[3]) * cabs(u[3]) * fabs(normal_flux(n, Ere, Hre)) / fi;
+    out[1] = cabs_r(u[2]) * cabs_r(u[2]) * fabs(normal_flux(n, Ero, Hro)) / fi;
+    out[2] = cabs_r(u[3]) * cabs_r(u[3]) * fabs(normal_flux(n, Ere, Hre)) / fi;
     if (tir) return 1; /* nothing reaches the camera-side polariser */
     /* linear polariser in front of the camera: it passes the field component along its axis, taken
        across the transmitted vacuum wave (Malus's law, |E . a|^2 / |E|^2) */
     out[3] = 1.0;
-    double an = dot3(c->analyzer, c->analyzer);
+    real av[3];
+    vec_in(c->analyzer, av);
+    real an = dot3(av, av);
     if (an > 0.0) {
-        double a[3], ak = dot3(c->analyzer, kv);
-        for (int i = 0; i < 3; ++i) a[i] = c->analyzer[i] - ak * kv[i];
-        double al = sqrt(dot3(a, a));
+        real a[3], ak = dot3(av, kv);
+        for (int i = 0; i < 3; ++i) a[i] = av[i] - ak * kv[i];
+        real al = sqrt(dot3(a, a));
         cplx ea = 0.0, ee2 = 0.0;
         for (int i = 0; i < 3; ++i) {
             ea += Et[i] * (a[i] / al);
@@ -569,13 +595,13 @@ int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const 
 /* ------------------------------------------------------------------ */
 /* classical fourth-order Runge-Kutta (Sect. 4) */
 /* right-hand side of the cloak's formulation (Fermat: orc_rhs; Hamiltonian: orc_rhs_hamiltonian) */
-static void rhs_of(const orc_cloak *c, int mode, const double y[6], double dy[6]) {
+static void rhs_of(const orc_cloak *c, int mode, const real y[6], real dy[6]) {
     if (c->form) orc_rhs_hamiltonian(c, mode, y, dy);
     else orc_rhs(c, mode, y, dy);
 }
 
-void orc_rk4_step(const orc_cloak *c, int mode, const double y[6], double h, double out[6]) {
-    double k1[6], k2[6], k3[6], k4[6], t[6];
+void orc_rk4_step(const orc_cloak *c, int mode, const real y[6], real h, real out[6]) {
+    real k1[6], k2[6], k3[6], k4[6], t[6];
     rhs_of(c, mode, y, k1);
     for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.5 * h * k1[i];
     rhs_of(c, mode, t, k2);
@@ -588,40 +614,40 @@ void orc_rk4_step(const orc_cloak *c, int mode, const double y[6], double h, dou
 
 /* Dormand & Prince (1980) 5(4) pair: out = fifth-order solution, err = its
    difference from the embedded fourth-order solution. */
-void orc_dp45_step(const orc_cloak *c, int mode, const double y[6], double h, double out[6], double err[6]) {
-    static const double a[7][6] = {
+void orc_dp45_step(const orc_cloak *c, int mode, const real y[6], real h, real out[6], real err[6]) {
+    static const real a[7][6] = {
         {0, 0, 0, 0, 0, 0},
-        {1.0 / 5, 0, 0, 0, 0, 0},
-        {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
-        {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
-        {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
-        {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
-        {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
-    static const double b5[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0};
-    static const double b4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200,
-                                 187.0 / 2100, 1.0 / 40};
-    double k[7][6], t[6];
+        {R(1) / 5, 0, 0, 0, 0, 0},
+        {R(3) / 40, R(9) / 40, 0, 0, 0, 0},
+        {R(44) / 45, -R(56) / 15, R(32) / 9, 0, 0, 0},
+        {R(19372) / 6561, -R(25360) / 2187, R(64448) / 6561, -R(212) / 729, 0, 0},
+        {R(9017) / 3168, -R(355) / 33, R(46732) / 5247, R(49) / 176, -R(5103) / 18656, 0},
+        {R(35) / 384, 0, R(500) / 1113, R(125) / 192, -R(2187) / 6784, R(11) / 84}};
+    static const real b5[7] = {R(35) / 384, 0, R(500) / 1113, R(125) / 192, -R(2187) / 6784, R(11) / 84, 0};
+    static const real b4[7] = {R(5179) / 57600, 0, R(7571) / 16695, R(393) / 640, -R(92097) / 339200,
+                                 R(187) / 2100, R(1) / 40};
+    real k[7][6], t[6];
     rhs_of(c, mode, y, k[0]);
     for (int s = 1; s < 7; ++s) {
         for (int i = 0; i < 6; ++i) {
-            double acc = 0.0;
+            real acc = 0.0;
             for (int j = 0; j < s; ++j) acc += a[s][j] * k[j][i];
             t[i] = y[i] + h * acc;
         }
         rhs_of(c, mode, t, k[s]);
     }
     for (int i = 0; i < 6; ++i) {
-        double s5 = 0.0, s4 = 0.0;
+        real s5 = 0.0, s4 = 0.0;
         for (int j = 0; j < 7; ++j) { s5 += b5[j] * k[j][i]; s4 += b4[j] * k[j][i]; }
         out[i] = y[i] + h * s5;
         err[i] = h * (s5 - s4);
     }
 }
 
-static void step_solution(const orc_cloak *c, const orc_integrator *in, int mode, const double y[6], double h,
-                          double out[6]) {
+static void step_solution(const orc_cloak *c, const orc_integrator *in, int mode, const real y[6], real h,
+                          real out[6]) {
     if (in->kind == ORC_RK4) orc_rk4_step(c, mode, y, h, out);
-    else { double e[6]; orc_dp45_step(c, mode, y, h, out, e); }
+    else { real e[6]; orc_dp45_step(c, mode, y, h, out, e); }
 }
 
 /* ------------------------------------------------------------------ */
@@ -629,7 +655,7 @@ static void step_solution(const orc_cloak *c, const orc_integrator *in, int mode
 /* ------------------------------------------------------------------ */
 /* event functions: positive once the surface has been crossed */
 enum { EV_LATERAL = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_METAL = 3 };
-static double event_value(const orc_cloak *c, int ev, const double y[6]) {
+static real event_value(const orc_cloak *c, int ev, const real y[6]) {
     switch (ev) {
     case EV_LATERAL: return hypot(y[0], y[1]) - c->R2;
     case EV_TOP: return y[2] - 0.5 * c->H;
@@ -644,10 +670,10 @@ static double event_value(const orc_cloak *c, int ev, const double y[6]) {
    converges to (this selects one root when a coarse step crosses the
    surface more than once).  The returned s is on the far side (exits) or the
    near side (metal). */
-static double crossing(const orc_cloak *c, const orc_integrator *in, int mode, const double y[6], double h, int ev) {
-    double lo = 0.0, hi = h, t[6];
+static real crossing(const orc_cloak *c, const orc_integrator *in, int mode, const real y[6], real h, int ev) {
+    real lo = 0.0, hi = h, t[6];
     for (int it = 0; it < 400; ++it) {
-        double mid = 0.5 * (lo + hi);
+        real mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
         step_solution(c, in, mode, y, mid, t);
         if (event_value(c, ev, t) > 0.0) hi = mid;
@@ -657,31 +683,31 @@ static double crossing(const orc_cloak *c, const orc_integrator *in, int mode, c
 }
 
 /* first entry of the ray o + s d into the finite cylinder r <= R2, |z| <= H/2 */
-static int hit_cylinder(const orc_cloak *c, const double o[3], const double d[3], double p[3], double n[3],
+static int hit_cylinder(const orc_cloak *c, const real o[3], const real d[3], real p[3], real n[3],
                         int *face) {
-    double best = INFINITY;
+    real best = INFINITY;
     *face = -1;
-    double A = d[0] * d[0] + d[1] * d[1], B = o[0] * d[0] + o[1] * d[1],
+    real A = d[0] * d[0] + d[1] * d[1], B = o[0] * d[0] + o[1] * d[1],
            C = o[0] * o[0] + o[1] * o[1] - c->R2 * c->R2;
     if (A > 0.0) {
-        double disc = B * B - A * C;
+        real disc = B * B - A * C;
         if (disc >= 0.0) {
-            double s = (-B - sqrt(disc)) / A; /* nearer root: where the ray enters the infinite cylinder */
+            real s = (-B - sqrt(disc)) / A; /* nearer root: where the ray enters the infinite cylinder */
             if (s > 0.0 && fabs(o[2] + s * d[2]) <= 0.5 * c->H) { best = s; *face = EV_LATERAL; }
         }
     }
     for (int cap = 0; cap < 2; ++cap) {
-        double zc = cap == 0 ? 0.5 * c->H : -0.5 * c->H;
+        real zc = cap == 0 ? 0.5 * c->H : -0.5 * c->H;
         if (d[2] == 0.0) continue;
         if ((cap == 0 && d[2] >= 0.0) || (cap == 1 && d[2] <= 0.0)) continue; /* must approach from outside */
-        double s = (zc - o[2]) / d[2];
-        double px = o[0] + s * d[0], py = o[1] + s * d[1];
+        real s = (zc - o[2]) / d[2];
+        real px = o[0] + s * d[0], py = o[1] + s * d[1];
         if (s > 0.0 && px * px + py * py <= c->R2 * c->R2 && s < best) { best = s; *face = cap == 0 ? EV_TOP : EV_BOTTOM; }
     }
     if (*face < 0) return 0;
     for (int i = 0; i < 3; ++i) p[i] = o[i] + best * d[i];
     if (*face == EV_LATERAL) {
-        double r = hypot(p[0], p[1]);
+        real r = hypot(p[0], p[1]);
         n[0] = p[0] / r; n[1] = p[1] / r; n[2] = 0.0;
     } else {
         n[0] = n[1] = 0.0;
@@ -690,9 +716,9 @@ static int hit_cylinder(const orc_cloak *c, const double o[3], const double d[3]
     return 1;
 }
 
-static void face_normal(int ev, const double x[3], double n[3]) {
+static void face_normal(int ev, const real x[3], real n[3]) {
     if (ev == EV_LATERAL) {
-        double r = hypot(x[0], x[1]);
+        real r = hypot(x[0], x[1]);
         n[0] = x[0] / r; n[1] = x[1] / r; n[2] = 0.0;
     } else {
         n[0] = n[1] = 0.0;
@@ -701,13 +727,13 @@ static void face_normal(int ev, const double x[3], double n[3]) {
 }
 
 /* wave vector of the mode from the ray velocity: k = M v (Eq. 6) */
-static void wave_vector(const orc_cloak *c, int mode, const double x[3], const double v[3], double k[3]) {
+static void wave_vector(const orc_cloak *c, int mode, const real x[3], const real v[3], real k[3]) {
     if (mode == ORC_EXTRAORDINARY) {
-        double M[9], dM[27];
+        real M[9], dM[27];
         orc_aux_matrix(c, x, M, dM);
         matvec3(M, v, k);
     } else {
-        double eps[9], eo, ee, ch[3];
+        real eps[9], eo, ee, ch[3];
         orc_permittivity(c, x, eps, &eo, &ee, ch);
         for (int i = 0; i < 3; ++i) k[i] = eo * v[i];
     }
@@ -719,9 +745,9 @@ static void wave_vector(const orc_cloak *c, int mode, const double x[3], const d
 /* Reading: axis-aligned box x, y in [-10, 10], z in [-H/2, -H/2 + 10];
    walls and floor checkered with 8 tiles per unit, per-tile tint from
    splitmix64(scene seed, face, i, j); constant ceiling. */
-int orc_shade(const orc_cloak *c, const double p[3], const double d[3], double rgb[3]) {
-    const double L = 10.0, z0 = -0.5 * c->H, z1 = z0 + 10.0;
-    double best = INFINITY, s;
+int orc_shade(const orc_cloak *c, const real p[3], const real d[3], real rgb[3]) {
+    const real L = 10.0, z0 = -0.5 * c->H, z1 = z0 + 10.0;
+    real best = INFINITY, s;
     int face = -1;
     if (d[0] > 0.0) { s = (L - p[0]) / d[0]; if (s < best) { best = s; face = 0; } }
     else if (d[0] < 0.0) { s = (-L - p[0]) / d[0]; if (s < best) { best = s; face = 1; } }
@@ -731,9 +757,9 @@ int orc_shade(const orc_cloak *c, const double p[3], const double d[3], double r
     else if (d[2] > 0.0) { s = (z1 - p[2]) / d[2]; if (s < best) { best = s; face = 5; } }
     if (face < 0) { rgb[0] = rgb[1] = rgb[2] = 0.0; return -1; }
     if (face == 5) { rgb[0] = 0.55; rgb[1] = 0.55; rgb[2] = 0.6; return 5 << 20; }
-    double q[3];
+    real q[3];
     for (int i = 0; i < 3; ++i) q[i] = p[i] + best * d[i];
-    double u, v;
+    real u, v;
     int nu = 160, nv;
     if (face <= 1) { u = q[1] + L; v = q[2] - z0; nv = 80; }
     else if (face <= 3) { u = q[0] + L; v = q[2] - z0; nv = 80; }
@@ -747,21 +773,21 @@ int orc_shade(const orc_cloak *c, const double p[3], const double d[3], double r
     h = orc_splitmix64(h ^ (uint64_t)face);
     h = orc_splitmix64(h ^ (uint64_t)i);
     h = orc_splitmix64(h ^ (uint64_t)j);
-    double base = ((i + j) & 1) ? 0.25 : 0.85;
-    for (int ch = 0; ch < 3; ++ch) rgb[ch] = base * (0.6 + 0.4 * (double)((h >> (8 * ch)) & 255u) / 255.0);
+    real base = ((i + j) & 1) ? 0.25 : 0.85;
+    for (int ch = 0; ch < 3; ++ch) rgb[ch] = base * (0.6 + 0.4 * (real)((h >> (8 * ch)) & 255u) / 255.0);
     return (face << 20) | (i << 10) | j;
 }
 
 /* ------------------------------------------------------------------ */
 /* time-of-flight difference (Sect. 4; TOF images of Ref. [10])         */
 /* ------------------------------------------------------------------ */
-double orc_room_distance(const orc_cloak *c, const double p[3], const double d[3]) {
+real orc_room_distance(const orc_cloak *c, const real p[3], const real d[3]) {
     /* nearest of the six planes of the room box that the ray moves towards */
-    const double L = 10.0, z0 = -0.5 * c->H, z1 = z0 + 10.0;
-    double best = INFINITY;
-    const double lo[3] = {-L, -L, z0}, hi[3] = {L, L, z1};
+    const real L = 10.0, z0 = -0.5 * c->H, z1 = z0 + 10.0;
+    real best = INFINITY;
+    const real lo[3] = {-L, -L, z0}, hi[3] = {L, L, z1};
     for (int a = 0; a < 3; ++a) {
-        double s = INFINITY;
+        real s = INFINITY;
         if (d[a] > 0.0) s = (hi[a] - p[a]) / d[a];
         else if (d[a] < 0.0) s = (lo[a] - p[a]) / d[a];
         if (s < best) best = s;
@@ -769,21 +795,23 @@ double orc_room_distance(const orc_cloak *c, const double p[3], const double d[3
     return best;
 }
 
-static double dist3(const double a[3], const double b[3]) {
+static real dist3(const real a[3], const real b[3]) {
     return sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
 }
 
-double orc_tof_difference(const orc_cloak *c, const double o[3], const double d[3], const orc_record *rec) {
+real orc_tof_difference(const orc_cloak *c, const real o[3], const real d[3], const orc_record *rec) {
     /* with c0 = 1 a time of flight is a vacuum path length, plus the time t spent inside the cloak */
-    const double t_ref = orc_room_distance(c, o, d);
-    double t;
+    const real t_ref = orc_room_distance(c, o, d);
+    const real xp[3] = {rec->exit_pos[0], rec->exit_pos[1], rec->exit_pos[2]};
+    const real xd[3] = {rec->exit_dir[0], rec->exit_dir[1], rec->exit_dir[2]};
+    real t;
     if (rec->status == ORC_METAL_CAP) {
-        t = dist3(rec->exit_pos, o) + orc_room_distance(c, rec->exit_pos, rec->exit_dir);
+        t = dist3(xp, o) + orc_room_distance(c, xp, xd);
     } else if (rec->status == ORC_EXITED || rec->status == ORC_HIT_METAL_EXITED) {
-        double p[3], n[3];
+        real p[3], n[3];
         int face;
         if (!hit_cylinder(c, o, d, p, n, &face)) return 0.0;
-        t = dist3(p, o) + rec->tof + orc_room_distance(c, rec->exit_pos, rec->exit_dir);
+        t = dist3(p, o) + rec->tof + orc_room_distance(c, xp, xd);
     } else {
         return 0.0;
     }
@@ -793,16 +821,16 @@ double orc_tof_difference(const orc_cloak *c, const double o[3], const double d[
 /* ------------------------------------------------------------------ */
 /* one ray: entry split, integration, exit refraction, shading          */
 /* ------------------------------------------------------------------ */
-static void path_push(double *path, long cap, long *len, double t, const double y[6]) {
+static void path_push(real *path, long cap, long *len, real t, const real y[6]) {
     if (!path || *len >= cap) { if (len) ++*len; return; }
-    double *p = path + 7 * (*len);
+    real *p = path + 7 * (*len);
     p[0] = t;
     for (int i = 0; i < 6; ++i) p[1 + i] = y[i];
     ++*len;
 }
 
-static void finish_vacuum(const orc_cloak *c, const double p[3], const double d[3], orc_record *rec) {
-    double rgb[3];
+static void finish_vacuum(const orc_cloak *c, const real p[3], const real d[3], orc_record *rec) {
+    real rgb[3];
     for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = p[i]; rec->exit_dir[i] = d[i]; }
     rec->tile_id = orc_shade(c, p, d, rgb);
 }
@@ -810,27 +838,27 @@ static void finish_vacuum(const orc_cloak *c, const double p[3], const double d[
 /* Integration inside the cloak from state y (Fermat (x, v) or Hamiltonian (x, k)) at time *t until the
    ray crosses a face: returns ORC_EXITED with y on the crossing and *ev_hit the face, or ORC_STEP_LIMIT /
    ORC_SINGULAR.  The metal cylinder mirrors radial ordinary rays (*metal set). */
-static int integrate_inside(const orc_cloak *c, const orc_integrator *in, int mode, double y[6], double *t,
-                            int *steps, int *metal, int *ev_hit, double *path, long path_cap, long *plen) {
-    double y1[6];
-    double h = in->kind == ORC_RK4 ? in->h_or_tol : 1e-3, tol = in->h_or_tol;
+static int integrate_inside(const orc_cloak *c, const orc_integrator *in, int mode, real y[6], real *t,
+                            int *steps, int *metal, int *ev_hit, real *path, long path_cap, long *plen) {
+    real y1[6];
+    real h = in->kind == ORC_RK4 ? in->h_or_tol : 1e-3, tol = in->h_or_tol;
     const int nev = c->R1 > 0.0 ? 4 : 3;
     for (;;) {
         if (*steps >= in->max_steps || (in->kind == ORC_DP45 && h < 1e-14)) return ORC_STEP_LIMIT;
-        double fac = 1.0;
+        real fac = 1.0;
         if (in->kind == ORC_RK4) {
             orc_rk4_step(c, mode, y, h, y1);
             ++*steps;
         } else {
-            double e[6];
+            real e[6];
             orc_dp45_step(c, mode, y, h, y1, e);
             ++*steps;
             /* error norm: max_i |e_i| / (tol + tol max(|y_i|, |y1_i|)) */
-            double err = 0.0;
+            real err = 0.0;
             int bad = 0;
             for (int i = 0; i < 6; ++i) {
-                double sc = tol + tol * fmax(fabs(y[i]), fabs(y1[i]));
-                double q = fabs(e[i]) / sc;
+                real sc = tol + tol * fmax(fabs(y[i]), fabs(y1[i]));
+                real q = fabs(e[i]) / sc;
                 if (q != q) bad = 1;
                 else if (q > err) err = q;
             }
@@ -846,10 +874,10 @@ static int integrate_inside(const orc_cloak *c, const orc_integrator *in, int mo
            approach.  (Sect. 4: all radial ordinary rays reach the metal; they travel on straight
            lines, along which the error estimate vanishes and the step grows without bound.) */
         if (in->kind == ORC_DP45 && c->R1 > 0.0 && event_value(c, EV_METAL, y1) <= 0.0) {
-            double dx = y1[0] - y[0], dy = y1[1] - y[1], dd = dx * dx + dy * dy;
+            real dx = y1[0] - y[0], dy = y1[1] - y[1], dd = dx * dx + dy * dy;
             if (dd > 0.0) {
-                double sc = -(y[0] * dx + y[1] * dy) / dd;
-                double mx = y[0] + sc * dx, my = y[1] + sc * dy;
+                real sc = -(y[0] * dx + y[1] * dy) / dd;
+                real mx = y[0] + sc * dx, my = y[1] + sc * dy;
                 if (sc > 0.0 && sc < 1.0 && mx * mx + my * my < c->R1 * c->R1) {
                     h *= sc;
                     continue;
@@ -858,10 +886,10 @@ static int integrate_inside(const orc_cloak *c, const orc_integrator *in, int mo
         }
         /* surfaces crossed by this step; the earliest crossing wins */
         int hit = -1;
-        double s_hit = INFINITY;
+        real s_hit = INFINITY;
         for (int ev = 0; ev < nev; ++ev) {
             if (event_value(c, ev, y1) > 0.0) {
-                double sx = crossing(c, in, mode, y, h, ev);
+                real sx = crossing(c, in, mode, y, h, ev);
                 if (sx < s_hit) { s_hit = sx; hit = ev; }
             }
         }
@@ -880,9 +908,9 @@ static int integrate_inside(const orc_cloak *c, const orc_integrator *in, int mo
         if (hit == EV_METAL) {
             if (c->variant == ORC_RADIAL && mode == ORC_ORDINARY) {
                 /* Sect. 4: c-hat parallel to the metal normal, single mirror ray with equal angles */
-                double nm[3], r = hypot(y[0], y[1]);
+                real nm[3], r = hypot(y[0], y[1]);
                 nm[0] = y[0] / r; nm[1] = y[1] / r; nm[2] = 0.0;
-                double vn = dot3(y + 3, nm);
+                real vn = dot3(y + 3, nm);
                 for (int i = 0; i < 3; ++i) y[3 + i] -= 2.0 * vn * nm[i];
                 *metal = 1;
                 path_push(path, path_cap, plen, *t, y);
@@ -896,7 +924,7 @@ static int integrate_inside(const orc_cloak *c, const orc_integrator *in, int mo
 }
 
 /* Wave vector of the mode from the state's second half (Fermat: ray velocity, k = M v; Hamiltonian: k). */
-static void state_wave_vector(const orc_cloak *c, int mode, const double y[6], double k[3]) {
+static void state_wave_vector(const orc_cloak *c, int mode, const real y[6], real k[3]) {
     if (c->form)
         for (int i = 0; i < 3; ++i) k[i] = y[3 + i];
     else
@@ -906,16 +934,16 @@ static void state_wave_vector(const orc_cloak *c, int mode, const double y[6], d
 /* What a camera-backward ray reaches inside: entry data and the state on the far face. */
 typedef struct {
     int status;           /* ORC_* so far; ORC_EXITED: y is on face `ev` (crossed, not yet refracted) */
-    double x_in[3], n_in[3], k0[3];
-    double y[6], t;
+    real x_in[3], n_in[3], k0[3];
+    real y[6], t;
     int ev, steps, metal;
 } inner_path;
 
 /* Entry split and integration of `mode` from the camera ray (o, d) to the far face. */
-static void trace_to_far_face(const orc_cloak *c, const orc_integrator *in, int mode, const double o[3],
-                              const double d[3], const double p[3], const double n[3], inner_path *ip,
-                              double *path, long path_cap, long *plen) {
-    double dn = dot3(d, n), kt[3], v0[3];
+static void trace_to_far_face(const orc_cloak *c, const orc_integrator *in, int mode, const real o[3],
+                              const real d[3], const real p[3], const real n[3], inner_path *ip,
+                              real *path, long path_cap, long *plen) {
+    real dn = dot3(d, n), kt[3], v0[3];
     for (int i = 0; i < 3; ++i) kt[i] = d[i] - dn * n[i];
     ip->t = 0.0;
     ip->steps = 0;
@@ -933,17 +961,19 @@ static void trace_to_far_face(const orc_cloak *c, const orc_integrator *in, int 
     (void)o;
 }
 
-int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const double o[3], const double d[3],
-                  orc_record *rec, double *path, long path_cap, long *path_len) {
+int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const real o[3], const real d[3],
+                  orc_record *rec, real *path, long path_cap, long *path_len) {
     memset(rec, 0, sizeof(*rec));
     rec->mode = mode;
     rec->tile_id = -1;
     long plen = 0;
     if (path_len) *path_len = 0;
-    double p[3], n[3];
+    real p[3], n[3];
     int face;
     /* unpolarised room light through a linear polariser: half of it */
-    const double vac = dot3(c->analyzer, c->analyzer) > 0.0 ? 0.5 : 1.0;
+    real av[3];
+    vec_in(c->analyzer, av);
+    const real vac = dot3(av, av) > 0.0 ? 0.5 : 1.0;
     if (!hit_cylinder(c, o, d, p, n, &face)) {
         rec->status = ORC_MISSED;
         rec->weight = vac;
@@ -952,14 +982,14 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
     }
     if (face != EV_LATERAL && c->R1 > 0.0 && hypot(p[0], p[1]) <= c->R1) {
         /* metal end disc seen from outside: mirror, reflectance 1 */
-        double dr[3], dn = dot3(d, n);
+        real dr[3], dn = dot3(d, n);
         for (int i = 0; i < 3; ++i) dr[i] = d[i] - 2.0 * dn * n[i];
         rec->status = ORC_METAL_CAP;
         rec->weight = vac;
         finish_vacuum(c, p, dr, rec);
         return rec->status;
     }
-    /* entry double refraction (Sect. 3), then the integration to the far face */
+    /* entry real refraction (Sect. 3), then the integration to the far face */
     inner_path ip;
     trace_to_far_face(c, in, mode, o, d, p, n, &ip, path, path_cap, &plen);
     if (path_len) *path_len = plen;
@@ -967,31 +997,31 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
     rec->tof = ip.t;
     if (ip.status != ORC_EXITED) {
         rec->status = ip.status;
-        const double *x = ip.status == ORC_NO_TRANSMISSION ? p : ip.y;
+        const real *x = ip.status == ORC_NO_TRANSMISSION ? p : ip.y;
         for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = x[i]; rec->exit_dir[i] = d[i]; }
         if (ip.status == ORC_NO_TRANSMISSION) rec->tof = 0.0;
         return rec->status;
     }
     /* exit refraction (Sect. 3): keep k_t, vacuum k_n = +sqrt(1 - |k_t|^2) */
-    double xo[3] = {ip.y[0], ip.y[1], ip.y[2]}, no[3], kx[3], ktx[3];
+    real xo[3] = {ip.y[0], ip.y[1], ip.y[2]}, no[3], kx[3], ktx[3];
     face_normal(ip.ev, xo, no);
     state_wave_vector(c, mode, ip.y, kx);
-    double kn = dot3(kx, no);
+    real kn = dot3(kx, no);
     for (int i = 0; i < 3; ++i) ktx[i] = kx[i] - kn * no[i];
-    double kt2 = dot3(ktx, ktx);
+    real kt2 = dot3(ktx, ktx);
     if (kt2 > 1.0) {
         rec->status = ORC_TIR;
         for (int i = 0; i < 3; ++i) { rec->exit_pos[i] = xo[i]; rec->exit_dir[i] = d[i]; }
         return rec->status;
     }
-    double dout[3];
+    real dout[3];
     for (int i = 0; i < 3; ++i) dout[i] = ktx[i] + sqrt(1.0 - kt2) * no[i];
     /* Eq. 12 along the physical direction of light: from the room into the
        cloak at the exit point, and out of the cloak towards the camera at the
        entry point.  Unpolarised source: mean over s and p. */
-    double Tin[8], Tout[4], mdout[3], mk0[3];
+    real Tin[8], Tout[4], mdout[3], mk0[3];
     for (int i = 0; i < 3; ++i) { mdout[i] = -dout[i]; mk0[i] = -ip.k0[i]; }
-    double w = 0.0;
+    real w = 0.0;
     if (orc_transmission_in(c, xo, no, mdout, Tin) && orc_transmission_out(c, mode, ip.x_in, ip.n_in, mk0, Tout))
         w = (mode == ORC_ORDINARY ? Tin[6] : Tin[7]) * Tout[0] * Tout[3];
     rec->weight = w;
@@ -1008,25 +1038,27 @@ int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode, const 
    interface): the light arriving along d after the reflection is what, run backwards, a vacuum wave
    incident along d reflects; so the fraction is the mean over the camera-side polarisations e (s and p,
    or the polariser's axis across d alone) of the backward reflectance R(e), halved behind a polariser. */
-static double vacuum_reflection(const orc_cloak *c, const double x[3], const double n[3], const double d[3]) {
-    double T[8];
+static real vacuum_reflection(const orc_cloak *c, const real x[3], const real n[3], const real d[3]) {
+    real T[8];
     if (!orc_transmission_in(c, x, n, d, T)) return 0.0;
-    const double an = dot3(c->analyzer, c->analyzer);
+    real av[3];
+    vec_in(c->analyzer, av);
+    const real an = dot3(av, av);
     if (!(an > 0.0)) return 0.5 * (T[4] + T[5]);
     /* backward reflectance for the incident polarisation along the polariser's axis across d: the
        reflected fields of the s and p solutions superposed with the axis' s and p components */
-    double a[3], ad = dot3(c->analyzer, d);
-    for (int i = 0; i < 3; ++i) a[i] = c->analyzer[i] - ad * d[i];
-    const double al = norm3(a);
+    real a[3], ad = dot3(av, d);
+    for (int i = 0; i < 3; ++i) a[i] = av[i] - ad * d[i];
+    const real al = norm3(a);
     if (!(al > 0.0)) return 0.0;
     for (int i = 0; i < 3; ++i) a[i] /= al;
-    double o9[9];
+    real o9[9];
     if (!vacuum_face(c, x, n, d, a, o9)) return 0.0;
     return 0.5 * o9[8];
 }
 
-int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode, const double o[3],
-                          const double d[3], orc_record *vacrec, orc_record refl[2]) {
+int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode, const real o[3],
+                          const real d[3], orc_record *vacrec, orc_record refl[2]) {
     memset(vacrec, 0, sizeof(*vacrec));
     memset(refl, 0, 2 * sizeof(orc_record));
     vacrec->tile_id = refl[0].tile_id = refl[1].tile_id = -1;
@@ -1034,7 +1066,7 @@ int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode
     refl[0].mode = ORC_ORDINARY;
     refl[1].mode = ORC_EXTRAORDINARY;
     vacrec->mode = -1;
-    double p[3], n[3];
+    real p[3], n[3];
     int face;
     if (!hit_cylinder(c, o, d, p, n, &face)) return 0;
     if (face != EV_LATERAL && c->R1 > 0.0 && hypot(p[0], p[1]) <= c->R1) {
@@ -1043,7 +1075,7 @@ int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode
     }
     /* (R0) the outer surface reflects room light into the camera (the same for both modes) */
     {
-        double dr[3], dn = dot3(d, n);
+        real dr[3], dn = dot3(d, n);
         for (int i = 0; i < 3; ++i) dr[i] = d[i] - 2.0 * dn * n[i];
         vacrec->status = ORC_EXITED;
         vacrec->weight = vacuum_reflection(c, p, n, d);
@@ -1056,26 +1088,26 @@ int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode
         refl[0].status = refl[1].status = ip.status;
         return 1;
     }
-    double x1[3] = {ip.y[0], ip.y[1], ip.y[2]}, n1[3], k1[3], kt[3];
+    real x1[3] = {ip.y[0], ip.y[1], ip.y[2]}, n1[3], k1[3], kt[3];
     face_normal(ip.ev, x1, n1);
     state_wave_vector(c, mode, ip.y, k1);
-    const double kn = dot3(k1, n1);
+    const real kn = dot3(k1, n1);
     for (int i = 0; i < 3; ++i) kt[i] = k1[i] - kn * n1[i];
     /* camera-side factor: Eq. 12 out of the cloak at the entry point, through the polariser */
-    double Tout0[4], mk0[3], R1[4];
+    real Tout0[4], mk0[3], R1[4];
     for (int i = 0; i < 3; ++i) mk0[i] = -ip.k0[i];
-    const double wcam = orc_transmission_out(c, mode, ip.x_in, ip.n_in, mk0, Tout0) ? Tout0[0] * Tout0[3] : 0.0;
+    const real wcam = orc_transmission_out(c, mode, ip.x_in, ip.n_in, mk0, Tout0) ? Tout0[0] * Tout0[3] : 0.0;
     if (!orc_transmission_out(c, mode, x1, n1, k1, R1)) R1[1] = R1[2] = 0.0;
     for (int m2 = 0; m2 < 2; ++m2) {
         orc_record *r = refl + m2;
         r->mode = m2;
-        double kr[3], vr[3];
+        real kr[3], vr[3];
         if (!(R1[1 + m2] > 0.0) || !orc_refract_into(c, m2, x1, n1, kt, kr, vr)) {
             r->status = ORC_NO_TRANSMISSION; /* the reflected mode does not propagate */
             for (int i = 0; i < 3; ++i) { r->exit_pos[i] = x1[i]; r->exit_dir[i] = d[i]; }
             continue;
         }
-        double y[6] = {x1[0], x1[1], x1[2], 0, 0, 0}, t = ip.t;
+        real y[6] = {x1[0], x1[1], x1[2], 0, 0, 0}, t = ip.t;
         for (int i = 0; i < 3; ++i) y[3 + i] = c->form ? kr[i] : vr[i];
         int steps = 0, metal = ip.metal, ev = -1;
         const int st = integrate_inside(c, in, m2, y, &t, &steps, &metal, &ev, NULL, 0, NULL);
@@ -1087,20 +1119,20 @@ int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode
             continue;
         }
         /* refraction out at the reflected ray's own exit, no further reflection (first order) */
-        double xo[3] = {y[0], y[1], y[2]}, no[3], kx[3], ktx[3];
+        real xo[3] = {y[0], y[1], y[2]}, no[3], kx[3], ktx[3];
         face_normal(ev, xo, no);
         state_wave_vector(c, m2, y, kx);
-        const double kn2 = dot3(kx, no);
+        const real kn2 = dot3(kx, no);
         for (int i = 0; i < 3; ++i) ktx[i] = kx[i] - kn2 * no[i];
-        const double kt2 = dot3(ktx, ktx);
+        const real kt2 = dot3(ktx, ktx);
         if (kt2 > 1.0) {
             r->status = ORC_TIR;
             for (int i = 0; i < 3; ++i) { r->exit_pos[i] = xo[i]; r->exit_dir[i] = d[i]; }
             continue;
         }
-        double dout[3], mdout[3], Tin[8];
+        real dout[3], mdout[3], Tin[8];
         for (int i = 0; i < 3; ++i) { dout[i] = ktx[i] + sqrt(1.0 - kt2) * no[i]; mdout[i] = -dout[i]; }
-        const double tin = orc_transmission_in(c, xo, no, mdout, Tin) ? (m2 == ORC_ORDINARY ? Tin[6] : Tin[7]) : 0.0;
+        const real tin = orc_transmission_in(c, xo, no, mdout, Tin) ? (m2 == ORC_ORDINARY ? Tin[6] : Tin[7]) : 0.0;
         r->weight = wcam * R1[1 + m2] * tin;
         r->status = metal ? ORC_HIT_METAL_EXITED : ORC_EXITED;
         finish_vacuum(c, xo, dout, r);
@@ -1112,20 +1144,20 @@ int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode
    (x, k) with k = M v (Eq. 7; M = eps_o I for the ordinary ray), H = (k^T M^-1 k - 1) / 2,
    dx/dt = dH/dk = M^-1 k, dk/dt = -dH/dx = -(1/2) k^T (d_i M^-1) k = (1/2) v^T (d_i M) v with v = M^-1 k
    (d M^-1 = -M^-1 (d M) M^-1, M symmetric). */
-void orc_rhs_hamiltonian(const orc_cloak *c, int mode, const double y[6], double dy[6]) {
-    const double *x = y, *k = y + 3;
-    double M[9], dM[27], Mi[9];
+void orc_rhs_hamiltonian(const orc_cloak *c, int mode, const real y[6], real dy[6]) {
+    const real *x = y, *k = y + 3;
+    real M[9], dM[27], Mi[9];
     if (mode == ORC_EXTRAORDINARY) {
         orc_aux_matrix(c, x, M, dM);
         orc_aux_inverse(c, x, Mi);
     } else {
-        double eo = c->eps_o_test, g[3] = {0, 0, 0};
+        real eo = c->eps_o_test, g[3] = {0, 0, 0};
         if (c->variant != ORC_TEST_CONST) {
-            double r, rh[3], th[3], e[3], de[3];
+            real r, rh[3], th[3], e[3], de[3];
             cyl_basis(x, &r, rh, th);
             cyl_eps(c, r, e, de);
             eo = (c->variant == ORC_RADIAL) ? e[1] : e[0];
-            double deo = (c->variant == ORC_RADIAL) ? de[1] : de[0];
+            real deo = (c->variant == ORC_RADIAL) ? de[1] : de[0];
             for (int i = 0; i < 3; ++i) g[i] = deo * rh[i];
         }
         memset(M, 0, sizeof(M));
@@ -1137,11 +1169,11 @@ void orc_rhs_hamiltonian(const orc_cloak *c, int mode, const double y[6], double
             for (int d = 0; d < 3; ++d) dM[9 * d + 4 * i] = g[d];
         }
     }
-    double v[3];
+    real v[3];
     matvec3(Mi, k, v);
     for (int i = 0; i < 3; ++i) dy[i] = v[i];
     for (int d = 0; d < 3; ++d) {
-        double s = 0.0;
+        real s = 0.0;
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) s += v[i] * dM[9 * d + 3 * i + j] * v[j];
         dy[3 + d] = 0.5 * s;
@@ -1153,7 +1185,8 @@ void orc_trace_rays(const orc_cloak *c, const orc_integrator *in, int mode, cons
     if (nthreads < 1) nthreads = 1;
 #pragma omp parallel for schedule(dynamic, 8) num_threads(nthreads)
     for (long i = 0; i < n; ++i) {
-        const double *r = rays + 6 * i;
+        real r[6];
+        for (int k = 0; k < 6; ++k) r[k] = rays[6 * i + k];
         orc_trace_ray(c, in, mode, r, r + 3, recs + i, NULL, 0, NULL);
     }
 }
@@ -1164,25 +1197,27 @@ void orc_trace_rays(const orc_cloak *c, const orc_integrator *in, int mode, cons
 /* Pinhole camera; horizontal field of view; row 0 at the top.  One sample per
    pixel goes through the pixel centre; more samples are jittered with
    orc_uniform(seed, pixel, sample, 0 / 1). */
-void orc_camera_ray(const orc_camera *cam, int i, int j, int s, int spp, uint64_t seed, double o[3], double d[3]) {
-    double w[3], u[3], v[3];
+void orc_camera_ray(const orc_camera *cam, int i, int j, int s, int spp, uint64_t seed, real o[3], real d[3]) {
+    real w[3], u[3], v[3];
     for (int k = 0; k < 3; ++k) w[k] = cam->target[k] - cam->eye[k];
-    double l = norm3(w);
+    real l = norm3(w);
     for (int k = 0; k < 3; ++k) w[k] /= l;
-    cross3(w, cam->up, u);
+    real up[3];
+    vec_in(cam->up, up);
+    cross3(w, up, u);
     l = norm3(u);
     for (int k = 0; k < 3; ++k) u[k] /= l;
     cross3(u, w, v);
-    double tx = tan(0.5 * cam->hfov_deg * M_PI / 180.0);
-    double ty = tx * (double)cam->height / (double)cam->width;
-    double xi1 = 0.5, xi2 = 0.5;
+    real tx = tan(0.5 * cam->hfov_deg * R_PI / 180.0);
+    real ty = tx * (real)cam->height / (real)cam->width;
+    real xi1 = 0.5, xi2 = 0.5;
     if (spp > 1) {
         uint64_t pix = (uint64_t)j * (uint64_t)cam->width + (uint64_t)i;
         xi1 = orc_uniform(seed, pix, (uint32_t)s, 0);
         xi2 = orc_uniform(seed, pix, (uint32_t)s, 1);
     }
-    double px = (2.0 * (i + xi1) / cam->width - 1.0) * tx;
-    double py = (1.0 - 2.0 * (j + xi2) / cam->height) * ty;
+    real px = (2.0 * (i + xi1) / cam->width - 1.0) * tx;
+    real py = (1.0 - 2.0 * (j + xi2) / cam->height) * ty;
     for (int k = 0; k < 3; ++k) d[k] = w[k] + px * u[k] + py * v[k];
     l = norm3(d);
     for (int k = 0; k < 3; ++k) { d[k] /= l; o[k] = cam->eye[k]; }
@@ -1196,13 +1231,17 @@ void orc_render(const orc_cloak *c, const orc_integrator *in, const orc_camera *
     for (long idx = 0; idx < total; ++idx) {
         long pix = pixels ? (long)pixels[idx] : idx;
         int i = (int)(pix % cam->width), j = (int)(pix / cam->width);
-        double acc[4] = {0, 0, 0, 0};
+        real acc[4] = {0, 0, 0, 0};
         for (int s = 0; s < spp; ++s) {
-            double o[3], d[3], rgb[3];
+            real o[3], d[3], rgb[3];
             orc_record rec;
             orc_camera_ray(cam, i, j, s, spp, seed, o, d);
             orc_trace_ray(c, in, mode, o, d, &rec, NULL, 0, NULL);
-            if (rec.tile_id >= 0) orc_shade(c, rec.exit_pos, rec.exit_dir, rgb);
+            if (rec.tile_id >= 0) {
+                real xp[3] = {rec.exit_pos[0], rec.exit_pos[1], rec.exit_pos[2]};
+                real xd[3] = {rec.exit_dir[0], rec.exit_dir[1], rec.exit_dir[2]};
+                orc_shade(c, xp, xd, rgb);
+            }
             else rgb[0] = rgb[1] = rgb[2] = 0.0;
             for (int k = 0; k < 3; ++k) acc[k] += rec.weight * rgb[k];
             acc[3] += rec.weight;

@@ -19,6 +19,21 @@
 
 #include <stdint.h>
 
+/* Arithmetic type of the oracle: FP64.  Built with -DORC_REAL_KIND=1 (long double) or 2 (_Float128) the
+   same source runs in extended precision (test infrastructure for rays FP64 cannot determine); the
+   structures, the records, orc_uniform, the rays of orc_trace_rays and the image of orc_render stay FP64
+   in every build. */
+#ifndef ORC_REAL_KIND
+#define ORC_REAL_KIND 0
+#endif
+#if ORC_REAL_KIND == 0
+typedef double orc_real;
+#elif ORC_REAL_KIND == 1
+typedef long double orc_real;
+#else
+typedef _Float128 orc_real;
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -82,26 +97,26 @@ uint64_t orc_splitmix64(uint64_t z);
 double orc_uniform(uint64_t seed, uint64_t pixel, uint32_t sample, uint32_t dim);
 
 /* ---- material (Eq. 1, 7, 14, 15) ---- */
-void orc_permittivity(const orc_cloak *c, const double x[3], double eps[9],
-                      double *eps_o, double *eps_e, double chat[3]);
-void orc_aux_matrix(const orc_cloak *c, const double x[3], double M[9], double dM[27]);
-void orc_aux_inverse(const orc_cloak *c, const double x[3], double Minv[9]);
-void orc_eq8_accel(const double Minv[9], const double dM[27], const double v[3], double a[3]);
-void orc_eq2_accel(double n, const double gradn[3], const double v[3], double a[3]);
-void orc_rhs(const orc_cloak *c, int mode, const double y[6], double dy[6]);
+void orc_permittivity(const orc_cloak *c, const orc_real x[3], orc_real eps[9],
+                      orc_real *eps_o, orc_real *eps_e, orc_real chat[3]);
+void orc_aux_matrix(const orc_cloak *c, const orc_real x[3], orc_real M[9], orc_real dM[27]);
+void orc_aux_inverse(const orc_cloak *c, const orc_real x[3], orc_real Minv[9]);
+void orc_eq8_accel(const orc_real Minv[9], const orc_real dM[27], const orc_real v[3], orc_real a[3]);
+void orc_eq2_accel(orc_real n, const orc_real gradn[3], const orc_real v[3], orc_real a[3]);
+void orc_rhs(const orc_cloak *c, int mode, const orc_real y[6], orc_real dy[6]);
 
 /* ---- interface (Sect. 3, Eqs. 9-12) ---- */
-int orc_refract_into(const orc_cloak *c, int mode, const double x[3], const double nhat[3],
-                     const double kt[3], double k[3], double v[3]);
-void orc_mode_fields(const orc_cloak *c, int mode, const double x[3], const double k[3],
-                     double D[3], double E[3], double H[3]);
-int orc_transmission_in(const orc_cloak *c, const double x[3], const double nhat[3],
-                        const double d[3], double out[8]);
+int orc_refract_into(const orc_cloak *c, int mode, const orc_real x[3], const orc_real nhat[3],
+                     const orc_real kt[3], orc_real k[3], orc_real v[3]);
+void orc_mode_fields(const orc_cloak *c, int mode, const orc_real x[3], const orc_real k[3],
+                     orc_real D[3], orc_real E[3], orc_real H[3]);
+int orc_transmission_in(const orc_cloak *c, const orc_real x[3], const orc_real nhat[3],
+                        const orc_real d[3], orc_real out[8]);
 /* out[0] transmitted flux fraction, out[1], out[2] reflected into o / e, out[3] fraction of the
    transmitted flux that passes the analyser c->analyzer (1 without one); under total internal
    reflection out[0] = 0 and out[1] + out[2] = 1 */
-int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const double nhat[3],
-                         const double k[3], double out[4]);
+int orc_transmission_out(const orc_cloak *c, int mode, const orc_real x[3], const orc_real nhat[3],
+                         const orc_real k[3], orc_real out[4]);
 
 /* First-order reflections of one camera sample traced in `mode` (the paper keeps first-order reflections,
    Sect. 4): vac = room light the outer surface reflects into the camera at the entry point (weight =
@@ -109,40 +124,40 @@ int orc_transmission_out(const orc_cloak *c, int mode, const double x[3], const 
    reflects at the far face of the camera-backward ray into `mode` and leaves towards the camera (exit
    point and direction of the m' ray, time of flight of both legs, weight = camera-side Eq. 12 factor x
    reflection coefficient x entry Eq. 12 factor of m').  Returns 0 for rays that never enter the shell. */
-int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode, const double o[3],
-                          const double d[3], orc_record *vac, orc_record refl[2]);
+int orc_trace_reflections(const orc_cloak *c, const orc_integrator *in, int mode, const orc_real o[3],
+                          const orc_real d[3], orc_record *vac, orc_record refl[2]);
 
 /* Hamiltonian form of the ray equations, state (x, k), k = M v: dx/dt = M^-1 k,
    dk/dt = (1/2) v^T (d_i M) v (the comparison system of Sect. 4's closing remark) */
-void orc_rhs_hamiltonian(const orc_cloak *c, int mode, const double y[6], double dy[6]);
+void orc_rhs_hamiltonian(const orc_cloak *c, int mode, const orc_real y[6], orc_real dy[6]);
 
 /* ---- integrator steps (Sect. 4: RK4; Dormand-Prince 5(4) adaptive) ---- */
-void orc_rk4_step(const orc_cloak *c, int mode, const double y[6], double h, double out[6]);
-void orc_dp45_step(const orc_cloak *c, int mode, const double y[6], double h,
-                   double out[6], double err[6]);
+void orc_rk4_step(const orc_cloak *c, int mode, const orc_real y[6], orc_real h, orc_real out[6]);
+void orc_dp45_step(const orc_cloak *c, int mode, const orc_real y[6], orc_real h,
+                   orc_real out[6], orc_real err[6]);
 
 /* ---- whole-ray tracing ---- */
 int orc_trace_ray(const orc_cloak *c, const orc_integrator *in, int mode,
-                  const double o[3], const double d[3], orc_record *rec,
-                  double *path, long path_cap, long *path_len);
+                  const orc_real o[3], const orc_real d[3], orc_record *rec,
+                  orc_real *path, long path_cap, long *path_len);
 void orc_trace_rays(const orc_cloak *c, const orc_integrator *in, int mode,
                     const double *rays, long n, orc_record *recs, int nthreads);
 
 /* ---- camera, room, render ---- */
 void orc_camera_ray(const orc_camera *cam, int i, int j, int s, int spp, uint64_t seed,
-                    double o[3], double d[3]);
-int orc_shade(const orc_cloak *c, const double p[3], const double d[3], double rgb[3]);
+                    orc_real o[3], orc_real d[3]);
+int orc_shade(const orc_cloak *c, const orc_real p[3], const orc_real d[3], orc_real rgb[3]);
 void orc_render(const orc_cloak *c, const orc_integrator *in, const orc_camera *cam,
                 int mode, int spp, uint64_t seed, const int64_t *pixels, long npix,
                 double *rgba, orc_record *recs, int nthreads);
 
 /* ---- time-of-flight difference images (Sect. 4, after Ref. [10]) ---- */
 /* distance from p along the unit direction d to the room of orc_shade (INFINITY if none) */
-double orc_room_distance(const orc_cloak *c, const double p[3], const double d[3]);
+orc_real orc_room_distance(const orc_cloak *c, const orc_real p[3], const orc_real d[3]);
 /* time of flight (c0 = 1) of the light a camera sample (o, d, its record) receives from the room, minus
    the time from the room point the same camera ray sees without the cylinder; 0 for rays that miss the
    cylinder and for records that carry no light */
-double orc_tof_difference(const orc_cloak *c, const double o[3], const double d[3], const orc_record *rec);
+orc_real orc_tof_difference(const orc_cloak *c, const orc_real o[3], const orc_real d[3], const orc_record *rec);
 
 #ifdef __cplusplus
 }
