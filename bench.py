@@ -22,7 +22,6 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import tempfile
 import sys
 import time
@@ -34,10 +33,25 @@ if ROOT not in sys.path:
 METRIC = "traced rays/s at 1920x1080 vs plain FP64 GPU integrator; max exit-dir err"
 UNIT = "rays/s"
 
-# FP64 ALU peak derived from the GB300 unit counts and clock: 152 SMs x 2070 MHz x
-# 4 FP64 flop per clock per SM (two DFMA) = 1.26 TFLOP/s (nominal FP64 figure 1.25 TFLOP/s).
-FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
-FP32_PEAK_TFLOPS = 152 * 2.070e9 * 256 / 1e12
+# FP64 and FP32 ALU peaks: FMA throughput measured on this GPU model by the library's microbenchmark
+# (paper_1209_6038_gb300/alu_peaks.py: independent FMA chains, CUDA events, clocks sampled), committed in
+# profiles/alu_peaks.json; the bench re-measures them for a second each and reports both.  Without the file
+# the unit-count derivation stands in (152 SMs x 2070 MHz x 4 FP64 / 256 FP32 flop per clock per SM).
+ALU_PEAKS_PATH = os.path.join(ROOT, "profiles", "alu_peaks.json")
+
+
+def _alu_peaks():
+    try:
+        with open(ALU_PEAKS_PATH) as f:
+            d = json.load(f)
+        return (float(d["fp64"]["tflops"]), float(d["fp32"]["tflops"]),
+                f"measured: FMA microbenchmark, profiles/alu_peaks.json ({d.get('gpu', 'GPU')}, "
+                f"SM {d.get('clocks', {}).get('sm_mhz')} MHz)")
+    except (OSError, ValueError, KeyError):
+        return 152 * 2.070e9 * 4 / 1e12, 152 * 2.070e9 * 256 / 1e12, "derived: 152 SM x 2.07 GHz x 4 / 256 flop/clk/SM"
+
+
+FP64_PEAK_TFLOPS, FP32_PEAK_TFLOPS, ALU_PEAK_SOURCE = _alu_peaks()
 
 
 def _measured_peaks():
@@ -76,65 +90,12 @@ def flops_per_step(variant, mode, integ):
     return 6 * r + DP45_FIXED if integ == 1 else 4 * r + RK4_FIXED
 
 
+from paper_1209_6038_gb300.clocks import ClockSampler  # noqa: E402
+
+
 def dist_env():
     from paper_1209_6038_gb300.replicas import dist_env as env
     return env()
-
-
-class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
-
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index):
-        self.proc = None
-        self.path = os.path.join(tempfile.gettempdir(), f"cloak_bench_clocks_{os.getpid()}.csv")
-        self.gpu = gpu_index
-
-    def __enter__(self):
-        try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
-                                         stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
-            self.proc = None
-        return self
-
-    def __exit__(self, *a):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-            self.fh.close()
-
-    def summary(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5], f[6], f[7], f[8]))
-            except ValueError:
-                continue
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            for nm, v in zip(names, r[3:]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
 
 
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
@@ -644,11 +605,15 @@ def main():
     value = replicas.whole_job_rate(rays_step, ms_step / 1e3, ws)
     clocks = sampler.summary()
 
+    from paper_1209_6038_gb300 import alu_peaks
+    live = alu_peaks.measure(seconds=1.0, repeats=1)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(w),
            "schedule": args.schedule, "clocks": clocks,
            "gpu_launches": main_runner.launches * args.steps,
+           "alu_peaks_tflops": {"fp64": FP64_PEAK_TFLOPS, "fp32": FP32_PEAK_TFLOPS, "source": ALU_PEAK_SOURCE,
+                                "fp64_this_run": live["fp64"]["tflops"], "fp32_this_run": live["fp32"]["tflops"]},
            "stage_ms_per_step": {"camera_entry_sort": stages[0], "integrate": stages[1], "exit_shade": stages[2],
                                  "resolve": stages[3]}}
 
@@ -707,7 +672,7 @@ def main():
                            "traffic": INTEGRATE_TRAFFIC_BYTES if args.schedule == "batched" else None,
                            "traffic_note": "ncu dram bytes of a 480x270 x 4 spp capture of the same views, scaled by "
                                            "samples" if args.schedule == "batched" else None,
-                           "peak_source": "derived: 152 SM x 2.07 GHz x 4 FP64 flop/clk/SM", "kernel": kname,
+                           "peak_source": ALU_PEAK_SOURCE + " (FP64)", "kernel": kname,
                            "kernel_ms_per_step": stages[1]}
         out["work"] = {"integrator_steps_per_step": steps_total, "fp64_flops_per_step": flops,
                        "status_hist": {ck.RAY_STATUS[i]: int(status_hist[i]) for i in range(8)}}
@@ -771,11 +736,11 @@ def main():
                         "roofline": {"bound": "alu", "achieved": mflops / (mstages[1] / 1e3) / 1e12,
                                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                                      "frac": mflops / (mstages[1] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
-                                     "peak_source": "derived: 152 SM x 2.07 GHz x 128 FP32 FMA/clk/SM",
+                                     "peak_source": ALU_PEAK_SOURCE + " (FP32)",
                                      "note": "algorithmic flops of the step attempts (the FP64 path's per-attempt "
                                              "count, band steps included) over the integration kernel's time; the "
                                              "kernel is bound by latency and lane divergence, not an FP32 pipe "
-                                             "(profiles/k_wf_integrate_batched_mixed_480x270x4.md)"},
+                                             "(ncu summary of k_wf_integrate, mixed, 480x270 x 4 spp)"},
                         "accuracy_vs_oracle": {"max_exit_dir_err_rad": float(errm.max(initial=0)),
                                                "p999_exit_dir_err_rad": float(np.quantile(errm, 0.999)),
                                                "rays_over_1e-5_rad": int((errm > 1e-5).sum()),

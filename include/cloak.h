@@ -204,6 +204,16 @@ int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp,
  * The paper has no counterpart: it serves the learned surrogate of the exit state. */
 int cloak_mlp_gemm(const void *dev_a, const void *dev_b, float *dev_c, int M, int N, int K, void *cuda_stream);
 
+/* FMA throughput microbenchmark (the measured denominators of the ALU rooflines; the paper has no
+ * counterpart).  Launches `blocks` x `threads` threads (threads a multiple of 32 in [32, 256]), each
+ * running 8 independent fused multiply-add chains for 8 x iters steps, in FP64 (precision CLOAK_FP64)
+ * or FP32 (CLOAK_MIXED) on cuda_stream, and returns at once; *flops (host) receives the floating-point
+ * operations the launch performs (2 per FMA).  The caller times the launch (CUDA events on the same
+ * stream).  dev_sink: device memory of blocks x threads elements of the chosen type (never written in
+ * practice; it keeps the chains live).  CLOAK_EINVAL on bad arguments, CLOAK_ECUDA if the launch fails. */
+int cloak_fma_peak(int precision, int blocks, int threads, long long iters, void *dev_sink, double *flops,
+                   void *cuda_stream);
+
 /* Allocation-free render.  The paper has no counterpart: this is a service for callers that may not
  * allocate device memory -- processes whose device memory is owned entirely by another allocator
  * (a framework's caching pool), latency-critical render loops that cannot afford the device-wide

@@ -47,6 +47,8 @@ SIGNATURES = {
     "cloak_trace_rays": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
     "cloak_eval_rhs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
     "cloak_mlp_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "cloak_fma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_void_p, C.POINTER(C.c_double),
+                                 C.c_void_p]),
     "cloak_render_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p]),
     "cloak_render_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
                                        C.c_void_p]),
@@ -195,6 +197,15 @@ def cloak_mlp_gemm(a, b, c, stream=None):
     N = b.shape[0]
     return _check(load().cloak_mlp_gemm(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), C.c_void_p(c.data_ptr()),
                                         M, N, K, _stream_ptr(stream)))
+
+
+def cloak_fma_peak(precision, blocks, threads, iters, sink, stream=None):
+    """Launch the FMA throughput microbenchmark (FP64 or, with precision MIXED, FP32) on the stream; returns
+    the floating-point operations of the launch.  sink: CUDA tensor of blocks*threads elements of the type."""
+    flops = C.c_double(0.0)
+    _check(load().cloak_fma_peak(precision, blocks, threads, iters, C.c_void_p(sink.data_ptr()), C.byref(flops),
+                                 _stream_ptr(stream)))
+    return flops.value
 
 
 def cloak_render_batch(h, views, spp, seed, stream=None):

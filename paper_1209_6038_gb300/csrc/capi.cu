@@ -582,6 +582,19 @@ static unsigned long long fnv1a(unsigned long long hsh, const void *data, size_t
 static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
                       void *cuda_stream, float4 **samples_out, int analyzer, int tof = 0, ck::Queue *q_out = nullptr);
 
+extern "C" int cloak_fma_peak(int precision, int blocks, int threads, long long iters, void *dev_sink,
+                              double *flops, void *cuda_stream) {
+    g_err.clear();
+    if (precision != CLOAK_FP64 && precision != CLOAK_MIXED)
+        return fail(CLOAK_EINVAL, "cloak_fma_peak: precision must be CLOAK_FP64 or CLOAK_MIXED");
+    if (blocks < 1 || threads < 32 || threads > 256 || threads % 32 != 0 || iters < 1)
+        return fail(CLOAK_EINVAL, "cloak_fma_peak: need blocks >= 1, threads a multiple of 32 in [32, 256], iters >= 1");
+    if (!dev_sink || !flops) return fail(CLOAK_EINVAL, "cloak_fma_peak: null sink or flops");
+    cudaError_t e = ck::launch_fma_peak(precision == CLOAK_FP64, blocks, threads, iters, dev_sink, flops,
+                                        (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? CLOAK_OK : cuda_fail(e, "cloak_fma_peak");
+}
+
 extern "C" int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
                                   void *cuda_stream) {
     return batch_core(h, views, nviews, spp, seed, cuda_stream, nullptr, h ? h->analyzer : 0);

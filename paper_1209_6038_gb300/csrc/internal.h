@@ -72,5 +72,8 @@ inline cudaError_t launch_wavefront(const Params &p, int mode, int spp, unsigned
 }
 cudaError_t launch_resolve(int npix, int spp, const float4 *samples, float4 *out, cudaStream_t st);
 cudaError_t launch_eval_rhs(const Params &p, int mode, const double *y, long long n, double *dy, cudaStream_t st);
+// FMA throughput microbenchmark (alu_peak.cu): fp64 != 0 selects FP64 chains, else FP32
+cudaError_t launch_fma_peak(int fp64, int blocks, int threads, long long iters, void *sink, double *flops,
+                            cudaStream_t st);
 
 }  // namespace ck

@@ -76,3 +76,15 @@ def test_binding_constants_match_the_header():
             assert cloak.RAY_STATUS[v] == name[4:], name
         else:
             assert getattr(cloak, name) == v, name
+
+
+def test_fma_peak_rejects_bad_arguments_on_host(lib):
+    flops = C.c_double(0.0)
+    sink = C.c_void_p(16)  # never dereferenced: every call below fails its argument check before a launch
+    assert lib.cloak_fma_peak(7, 1, 32, 1, sink, C.byref(flops), None) == 1   # not FP64 / FP32
+    assert lib.cloak_fma_peak(0, 0, 32, 1, sink, C.byref(flops), None) == 1   # no blocks
+    assert lib.cloak_fma_peak(0, 1, 48, 1, sink, C.byref(flops), None) == 1   # not a multiple of 32
+    assert lib.cloak_fma_peak(0, 1, 512, 1, sink, C.byref(flops), None) == 1  # above 256 threads
+    assert lib.cloak_fma_peak(0, 1, 32, 0, sink, C.byref(flops), None) == 1   # no iterations
+    assert lib.cloak_fma_peak(0, 1, 32, 1, None, C.byref(flops), None) == 1   # no sink
+    assert b"cloak_fma_peak" in lib.cloak_last_error()
