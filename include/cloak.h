@@ -204,6 +204,17 @@ int cloak_render_batch(cloak_t *h, const cloak_view *views, int nviews, int spp,
  * The paper has no counterpart: it serves the learned surrogate of the exit state. */
 int cloak_mlp_gemm(const void *dev_a, const void *dev_b, float *dev_c, int M, int N, int K, void *cuda_stream);
 
+/* Bounded waits of the tensor-core kernels (the surrogate's GEMMs and fused forward pass; the paper has no
+ * counterpart).  Every mbarrier wait of those kernels polls at most a bounded number of times; when a wait
+ * that the kernel's progress depends on runs out, the kernel sets its error flag, lets the MMAs and copies
+ * it has in flight complete (those waits keep the default bound), frees its TMEM and returns:
+ * cloak_mlp_gemm, cloak_surrogate_forward, _step and _train then return CLOAK_ETIMEOUT, and a
+ * CLOAK_SURROGATE render leaves every ray to the FP64 integrator (the image is the integrator's).
+ * polls: the bound for all later launches in this process (default 2^22 polls, 0 restores it).  A small
+ * bound makes the waits run out on purpose -- this is how the timeout path is tested.  CLOAK_EINVAL
+ * outside [0, 2^32 - 1]. */
+int cloak_set_wait_limit(long long polls);
+
 /* FMA throughput microbenchmark (the measured denominators of the ALU rooflines; the paper has no
  * counterpart).  Launches `blocks` x `threads` threads (threads a multiple of 32 in [32, 256]), each
  * running 8 independent fused multiply-add chains for 8 x iters steps, in FP64 (precision CLOAK_FP64)
@@ -224,9 +235,12 @@ int cloak_fma_peak(int precision, int blocks, int threads, long long iters, void
  * exits) instead of handle scratch, and it calls no cudaMalloc, cudaFree or allocating routine.
  * Limit: width*height*spp <= 1048576 samples, else CLOAK_EINVAL before any launch.  The caller still
  * passes the output (dev_rgba, float4[width*height], bytes >= 16*width*height).  The first call on a
- * device resolves the array's device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the array, which keeps the last call's contents: calls whose GPU
- * work overlaps (other streams, other threads, other handles) race on it and must be serialised. */
+ * device resolves the array's device address (cudaGetSymbolAddress) and caches it for the life of the
+ * process; make that first call before any stream capture, and do not use this entry point again on a
+ * device after cudaDeviceReset (the cached address belongs to the old context).  Stage timing
+ * (cloak_set_stage_timing) does not cover this call.  All calls share the array, which keeps the last
+ * call's contents: calls whose GPU work overlaps (other streams, other threads, other handles) race on it
+ * and must be serialised. */
 int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsigned long long seed, void *dev_rgba,
                          size_t bytes, void *cuda_stream);
 

@@ -398,6 +398,55 @@ def reflections_image(cloak: Cloak, integ: Integrator, cam: Camera, spp=1, seed=
     return out
 
 
+def camera_axes(cam: Camera):
+    """The pinhole camera's right and up unit vectors (the frame orc_camera_ray builds: w towards the target,
+    right = w x up normalised, up' = right x w)."""
+    e = np.array(cam.s.eye[:])
+    w = np.array(cam.s.target[:]) - e
+    w /= np.linalg.norm(w)
+    u = np.cross(w, np.array(cam.s.up[:]))
+    u /= np.linalg.norm(u)
+    return u, np.cross(u, w)
+
+
+PANELS = ("unpolarized", "polarizer_right", "polarizer_up")
+
+
+def panel_image(variant, integ: Integrator, cam: Camera, kind="unpolarized", spp=1, seed=0, pixels=None,
+                reflections=False, R1=0.5, R2=1.0, H=2.0, nthreads=None):
+    """Panels (c)-(e) of Figs. 1 and 2 (Sect. 4; Sect. 5 for the polariser): the cloak seen in unpolarised room
+    light ("unpolarized"), or through a linear polariser in front of the camera whose axis is the camera's
+    right ("polarizer_right") or up ("polarizer_up") vector.  Per sample, the light arriving as the ordinary
+    and as the extraordinary wave add incoherently, each with its own Eq. 12 factors (and the polariser's
+    Malus factor); a sample that never enters the shell -- it misses the cylinder or mirrors off a metal end
+    disc -- is the same room light for both and counts once.  reflections: add the first-order reflections
+    (the outer surface's, once, and the far-face reflections of both waves: reflections_image).
+    Per pixel: RGB = mean over samples of weight x room colour, A = mean summed weight."""
+    if kind not in PANELS:
+        raise ValueError(kind)
+    axis = (0.0, 0.0, 0.0)
+    if kind != "unpolarized":
+        right, up = camera_axes(cam)
+        axis = tuple(right if kind == "polarizer_right" else up)
+    cl = Cloak(variant, R1=R1, R2=R2, H=H, analyzer=axis)
+    _, ro = render(cl, integ, cam, ORDINARY, spp, seed, pixels, nthreads)
+    _, re = render(cl, integ, cam, EXTRAORDINARY, spp, seed, pixels, nthreads)
+    n = len(ro) // spp
+    out = np.zeros((n, 4))
+    for k in range(n * spp):
+        a, b = ro[k], re[k]
+        enters = a["status"] not in (MISSED, METAL_CAP)
+        for r in ((a, b) if enters else (a,)):
+            if r["weight"] > 0.0 and r["tile_id"] >= 0:
+                _, rgb = shade(cl, r["exit_pos"], r["exit_dir"])
+                out[k // spp, :3] += r["weight"] * np.asarray(rgb)
+            out[k // spp, 3] += r["weight"]
+    out /= spp
+    if reflections:
+        out += reflections_image(cl, integ, cam, spp, seed, pixels)
+    return out
+
+
 def room_distance(cloak: Cloak, p, d) -> float:
     return lib().orc_room_distance(cloak.ref, _dp(_vec(p)), _dp(_vec(d)))
 

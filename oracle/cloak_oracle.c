@@ -38,6 +38,15 @@ typedef _Complex long double cplx;
 typedef _Complex _Float128 cplx;
 #define R_PI 3.14159265358979323846264338327950288f128
 #endif
+/* ORC_STATE_F64 (extended-precision builds only): the integrated state and every stage point are rounded
+   to FP64 -- the right-hand sides and all other arithmetic stay exact -- to measure how far FP64 states
+   alone move a ray, i.e. what an FP64 integrator can determine at best. */
+#ifndef ORC_STATE_F64
+#define ORC_STATE_F64 0
+#endif
+static void store_state(real y[6], const real y1[6]) {
+    for (int i = 0; i < 6; ++i) y[i] = ORC_STATE_F64 ? (real)(double)y1[i] : y1[i];
+}
 /* exact ratios of the Dormand-Prince tableau evaluated in the arithmetic type */
 #define R(x) ((real)(x))
 static cplx csqrt_r(cplx z) { return sqrt(z); }
@@ -595,9 +604,28 @@ int orc_transmission_out(const orc_cloak *c, int mode, const real x[3], const re
 /* ------------------------------------------------------------------ */
 /* classical fourth-order Runge-Kutta (Sect. 4) */
 /* right-hand side of the cloak's formulation (Fermat: orc_rhs; Hamiltonian: orc_rhs_hamiltonian) */
+/* ORC_MIXED_F32 (extended-precision builds only): a model of where FP32 enters a mixed-precision
+   integrator.  Outside the band r < R1 + ORC_F32_BAND the stage point's z and velocity are FP32 numbers (x
+   and y stay exact) and the right-hand side is rounded to FP32; inside the band the stage point is an FP64
+   state.  Everything else stays exact, so the distance of the result from the exact run measures how far
+   FP32 right-hand sides alone move a ray -- what such an integrator can determine at best. */
+#ifndef ORC_MIXED_F32
+#define ORC_MIXED_F32 0
+#endif
+#define ORC_F32_BAND 0.02
 static void rhs_of(const orc_cloak *c, int mode, const real y[6], real dy[6]) {
-    if (c->form) orc_rhs_hamiltonian(c, mode, y, dy);
-    else orc_rhs(c, mode, y, dy);
+    real ys[6];
+    store_state(ys, y);  /* ORC_STATE_F64: every stage point the right-hand side is evaluated at is an FP64 state */
+    int f32 = 0;
+    if (ORC_MIXED_F32) {
+        f32 = !(hypot(y[0], y[1]) < c->R1 + ORC_F32_BAND);
+        for (int i = 0; i < 6; ++i)
+            ys[i] = f32 ? (i < 2 ? y[i] : (real)(float)y[i]) : (real)(double)y[i];
+    }
+    if (c->form) orc_rhs_hamiltonian(c, mode, ys, dy);
+    else orc_rhs(c, mode, ys, dy);
+    if (f32)
+        for (int i = 3; i < 6; ++i) dy[i] = (real)(float)dy[i];
 }
 
 void orc_rk4_step(const orc_cloak *c, int mode, const real y[6], real h, real out[6]) {
@@ -894,14 +922,14 @@ static int integrate_inside(const orc_cloak *c, const orc_integrator *in, int mo
             }
         }
         if (hit < 0) {
-            for (int i = 0; i < 6; ++i) y[i] = y1[i];
+            store_state(y, y1);
             *t += h;
             h *= fac;
             path_push(path, path_cap, plen, *t, y);
             continue;
         }
         step_solution(c, in, mode, y, s_hit, y1);
-        for (int i = 0; i < 6; ++i) y[i] = y1[i];
+        store_state(y, y1);
         *t += s_hit;
         h *= fac;
         path_push(path, path_cap, plen, *t, y);

@@ -47,6 +47,7 @@ SIGNATURES = {
     "cloak_trace_rays": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
     "cloak_eval_rhs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
     "cloak_mlp_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "cloak_set_wait_limit": (C.c_int, [C.c_longlong]),
     "cloak_fma_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_void_p, C.POINTER(C.c_double),
                                  C.c_void_p]),
     "cloak_render_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p]),
@@ -197,6 +198,11 @@ def cloak_mlp_gemm(a, b, c, stream=None):
     N = b.shape[0]
     return _check(load().cloak_mlp_gemm(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), C.c_void_p(c.data_ptr()),
                                         M, N, K, _stream_ptr(stream)))
+
+
+def cloak_set_wait_limit(polls=0):
+    """Polls of the tensor-core kernels' bounded waits (0: the default 2^22)."""
+    return _check(load().cloak_set_wait_limit(int(polls)))
 
 
 def cloak_fma_peak(precision, blocks, threads, iters, sink, stream=None):

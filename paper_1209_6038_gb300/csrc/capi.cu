@@ -103,6 +103,10 @@ static int make_params(const cloak *h, ck::Params &p) {
     p.invKf = (float)p.invK;
     p.R1sq_hf = (float)p.R1sq;
     p.R1sq_lf = (float)(p.R1sq - (double)p.R1sq_hf);
+    p.R2sq_hf = (float)p.R2sq;
+    p.R2sq_lf = (float)(p.R2sq - (double)p.R2sq_hf);
+    p.halfH_hf = (float)p.halfH;
+    p.halfH_lf = (float)(p.halfH - (double)p.halfH_hf);
     p.band_limf = p.mixed_band > 0.0 ? (float)(p.R1 + p.mixed_band) : 0.f;
     p.h_or_tol = h->h_or_tol;
     p.max_steps = h->max_steps;
@@ -582,6 +586,13 @@ static unsigned long long fnv1a(unsigned long long hsh, const void *data, size_t
 static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, unsigned long long seed,
                       void *cuda_stream, float4 **samples_out, int analyzer, int tof = 0, ck::Queue *q_out = nullptr);
 
+extern "C" int cloak_set_wait_limit(long long polls) {
+    g_err.clear();
+    if (polls < 0 || polls > 0xffffffffll) return fail(CLOAK_EINVAL, "cloak_set_wait_limit: polls must be in [0, 2^32 - 1]");
+    ck::set_wait_limit((unsigned int)polls);
+    return CLOAK_OK;
+}
+
 extern "C" int cloak_fma_peak(int precision, int blocks, int threads, long long iters, void *dev_sink,
                               double *flops, void *cuda_stream) {
     g_err.clear();
@@ -651,6 +662,8 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
         const void *bufs[3] = {h->sur->X, h->sur->Y, h->sur->elig};
         key = fnv1a(key, bufs, sizeof(bufs));
         key = fnv1a(key, &h->sur->gate, sizeof(h->sur->gate));
+        const unsigned int lim = ck::wait_limit();  // baked into the captured network launch
+        key = fnv1a(key, &lim, sizeof(lim));
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     cudaError_t e;
@@ -841,7 +854,8 @@ static int noalloc_scratch_ptr(int dev, void **out) {
     if (!g_noalloc_ptr[dev]) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        if (!ptr) return fail(CLOAK_ECUDA, "cudaGetSymbolAddress returned a null address for the no-alloc scratch");
         g_noalloc_ptr[dev] = ptr;
     }
     *out = g_noalloc_ptr[dev];

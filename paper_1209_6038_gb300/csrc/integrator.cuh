@@ -419,14 +419,21 @@ struct StepperMixed {
         if (!(fe < 3.0e38f)) fac = 0.2f;
         return acc;
     }
+    // Event functions with the roots and signs of event_g (r^2 - R2^2, z - H/2, -z - H/2, R1^2 - r^2) from
+    // the float-float position: r^2 is formed exactly (products by FMA, sums by TwoSum) and the surface
+    // constants are float-float, so g keeps its precision where it is small -- next to the root, where the
+    // crossing search reads it.  (In plain FP32, g carries an absolute error ~1e-7; on the short chords of
+    // grazing rays, where g changes by little more than that, the crossing moved by up to 1e-4.)
     static __device__ __forceinline__ float gval(const Params &p, int ev, const float h[6], const float l[6]) {
-        float x = h[0] + l[0], y = h[1] + l[1], z = h[2] + l[2];
-        switch (ev) {
-        case EV_LAT: return sqrtf(x * x + y * y) - p.R2f;
-        case EV_TOP: return z - p.halfHf;
-        case EV_BOT: return -z - p.halfHf;
-        default: return p.R1f - sqrtf(x * x + y * y);
-        }
+        if (ev == EV_TOP) return (h[2] - p.halfH_hf) + (l[2] - p.halfH_lf);
+        if (ev == EV_BOT) return (-h[2] - p.halfH_hf) + (-l[2] - p.halfH_lf);
+        const float px = h[0] * h[0], ex = fmaf(h[0], h[0], -px);
+        const float py = h[1] * h[1], ey = fmaf(h[1], h[1], -py);
+        float r2h, r2l;
+        two_sum(px, py, r2h, r2l);
+        r2l += ex + ey + 2.f * (h[0] * l[0] + h[1] * l[1]);
+        if (ev == EV_LAT) return (r2h - p.R2sq_hf) + (r2l - p.R2sq_lf);
+        return (p.R1sq_hf - r2h) + (p.R1sq_lf - r2l);
     }
     __device__ __forceinline__ float chord(const Params &p) const {
         return metal_chord(yh[0] + yl[0], yh[1] + yl[1], y1h[0] + y1l[0], y1h[1] + y1l[1], p.R1sq_hf);

@@ -97,7 +97,8 @@ __device__ __forceinline__ void sur_gate_one(const Params &p, int mode, const Qu
 
 __global__ void __launch_bounds__(128) k_sur_gate(Params p, int mode, int spp, unsigned long long seed, Queue q,
                                                   const float *Y, const unsigned char *elig, float gate,
-                                                  float4 *samples, cloak_record *recs) {
+                                                  float4 *samples, cloak_record *recs, const unsigned int *err) {
+    if (*err) return;  // the network's forward pass timed out: every ray stays with the integrator
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const long long idx = q.id[k], pix = idx / spp;
@@ -109,7 +110,9 @@ __global__ void __launch_bounds__(128) k_sur_gate(Params p, int mode, int spp, u
 
 __global__ void __launch_bounds__(128) k_sur_gate_batch(Params p, const ViewDev *views, int nviews, int spp,
                                                         unsigned long long seed, Queue q, const float *Y,
-                                                        const unsigned char *elig, float gate, float4 *samples) {
+                                                        const unsigned char *elig, float gate, float4 *samples,
+                                                        const unsigned int *err) {
+    if (*err) return;  // the network's forward pass timed out: every ray stays with the integrator
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         double o[3], d[3];
@@ -167,13 +170,15 @@ cudaError_t launch_sur_features_batch(const Params &p, const ViewDev *views, int
 
 cudaError_t launch_sur_gate_batch(const Params &p, const ViewDev *views, int nviews, int spp, unsigned long long seed,
                                   const Queue &q, SurNet *s, float4 *samples, cudaStream_t st) {
-    k_sur_gate_batch<<<sm_count() * 16, 128, 0, st>>>(p, views, nviews, spp, seed, q, s->Y, s->elig, s->gate, samples);
+    k_sur_gate_batch<<<sm_count() * 16, 128, 0, st>>>(p, views, nviews, spp, seed, q, s->Y, s->elig, s->gate, samples,
+                                                              s->err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sur_gate(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q, SurNet *s,
                             float4 *samples, cloak_record *recs, cudaStream_t st) {
-    k_sur_gate<<<sm_count() * 16, 128, 0, st>>>(p, mode, spp, seed, q, s->Y, s->elig, s->gate, samples, recs);
+    k_sur_gate<<<sm_count() * 16, 128, 0, st>>>(p, mode, spp, seed, q, s->Y, s->elig, s->gate, samples, recs,
+                                                        s->err);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ struct FusedArgs {
     long long n;                 // rows of X and Y (a multiple of 128)
     const unsigned int *m_count; // optional live row count
     unsigned int *err;
+    unsigned int wait_limit;     // polls of the waits that decide a timeout
 };
 
 __global__ void __launch_bounds__(F_THREADS, 1)
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                 const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
                 const __grid_constant__ CUtensorMap tW3, const __grid_constant__ CUtensorMap tW4, FusedArgs a) {
     extern __shared__ unsigned char fsm_raw[];
-    __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], x_bar[2], done_bar[2], act_bar[2];
+    __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], x_bar[2], done_bar[2], act_bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
     __shared__ __align__(16) float sbias[SUR_L][SUR_W];  // every layer's bias, read by the epilogue
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long live = a.m_count ? min(a.n, (long long)__ldg(a.m_count)) : a.n;
     volatile int *vfailed = &failed;
+    const uint32_t lim = a.wait_limit;
 
     for (int l = 0; l < SUR_L; ++l)
         for (int c = tid; c < SUR_W; c += F_THREADS) sbias[l][c] = c < (l == SUR_L - 1 ? 16 : SUR_W) ? a.bias[l][c] : 0.f;
@@ -67,6 +69,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             mbar_init(smem_u32(&done_bar[s]), 1);
             mbar_init(smem_u32(&act_bar[s]), F_EPI_WARPS);
         }
+        mbar_init(smem_u32(&drain_bar), 1);
         failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             for (long long base = (long long)blockIdx.x * 256; base < live && ok; base += stride) {
                 // a tile's inputs overwrite its activations, which its previous last-layer MMAs read
                 for (int t = 0; t < 2 && ok; ++t) {
-                    if (Lt[t] > 0) ok = mbar_wait(smem_u32(&done_bar[t]), (Lt[t] - 1) & 1);
+                    if (Lt[t] > 0) ok = mbar_wait(smem_u32(&done_bar[t]), (Lt[t] - 1) & 1, lim);
                     if (!ok || *vfailed) { ok = false; break; }
                     mbar_expect_tx(smem_u32(&x_bar[t]), F_ACT_CHUNK);
                     tma_load_2d(smem_u32(act + t * 4 * F_ACT_CHUNK), &tX, 0, (int)(base + 128 * t), smem_u32(&x_bar[t]));
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                     for (int it = 0; it <= nk && ok; ++it) {
                         if (it < nk) {  // load chunk it of this layer's weights into a free ring slot
                             const uint32_t g = G0 + it, s = g & 1;
-                            if (g >= 2) ok = mbar_wait(smem_u32(&empty_bar[s]), ((g >> 1) - 1) & 1);
+                            if (g >= 2) ok = mbar_wait(smem_u32(&empty_bar[s]), ((g >> 1) - 1) & 1, lim);
                             if (!ok) break;
                             mbar_expect_tx(smem_u32(&full_bar[s]), (uint32_t)N * 128);
                             tma_load_2d(smem_u32(ring + s * F_RING_SLOT), tW[l], it * 64, 0, smem_u32(&full_bar[s]));
@@ -115,12 +118,12 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                         const int j = it - 1;
                         if (j >= 0) {  // multiply chunk j for tile t
                             const uint32_t g = G0 + j, s = g & 1;
-                            ok = mbar_wait(smem_u32(&full_bar[s]), (g >> 1) & 1);
+                            ok = mbar_wait(smem_u32(&full_bar[s]), (g >> 1) & 1, lim);
                             if (ok && j == 0) {
                                 // the tile's previous epilogue has read its accumulators and written these inputs
-                                if (Lt[t] > 0) ok = mbar_wait(smem_u32(&act_bar[t]), (Lt[t] - 1) & 1);
+                                if (Lt[t] > 0) ok = mbar_wait(smem_u32(&act_bar[t]), (Lt[t] - 1) & 1, lim);
                                 if (ok && l == 0) {
-                                    ok = mbar_wait(smem_u32(&x_bar[t]), iters & 1);
+                                    ok = mbar_wait(smem_u32(&x_bar[t]), iters & 1, lim);
                                     if (ok) x_pending[t] = false;
                                 }
                             }
@@ -151,7 +154,12 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             if (!ok) {
                 *vfailed = 1;
                 if (a.err) atomicExch(a.err, 1u);
-                // let the copies still in flight land before the shared memory is released (bounded)
+                // let the MMAs already issued complete before the accumulators are freed (a commit arrives once
+                // every earlier MMA of this thread is done), then the copies still in flight land before the
+                // shared memory is released; both bounded by the default limit
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&drain_bar)));
+                mbar_wait(smem_u32(&drain_bar), 0);
                 for (uint32_t k = 0; k < pending; ++k)
                     mbar_wait(smem_u32(&full_bar[(G - pending + k) & 1]), ((G - pending + k) >> 1) & 1);
                 for (int t = 0; t < 2; ++t)
@@ -167,7 +175,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             for (int job = 0; job < 2 * SUR_L; ++job) {
                 const int l = job >> 1, t = job & 1;
                 const int N = l == SUR_L - 1 ? 16 : SUR_W;
-                ok = mbar_wait(smem_u32(&done_bar[t]), Lt[t] & 1) && !*vfailed;
+                ok = mbar_wait(smem_u32(&done_bar[t]), Lt[t] & 1, lim) && !*vfailed;
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
@@ -227,7 +235,10 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                 ++Lt[t];
             }
         }
-        if (!ok) *vfailed = 1;
+        if (!ok) {
+            *vfailed = 1;
+            if (lane == 0 && a.err) atomicExch(a.err, 1u);  // this warp's rows were not written
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -268,6 +279,7 @@ cudaError_t launch_mlp_fused(SurNet *s, long long n, const unsigned int *m_count
     a.n = n;
     a.m_count = m_count;
     a.err = s->err;
+    a.wait_limit = wait_limit();
     const long long pairs = (n + 255) / 256;
     const int grid = (int)std::min<long long>(pairs, (long long)sms);
     k_mlp_fused<<<grid, F_THREADS, F_SMEM, st>>>(tx, s->tWb[0], s->tWb[1], s->tWb[2], s->tWb[3], s->tWb[4], a);

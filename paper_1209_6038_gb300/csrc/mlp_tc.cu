@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
         for (int it = 0; it < nk + GEMM_STAGES - 1 && ok; ++it) {
             if (it < nk) {  // load chunk `it`
                 const int s = it % GEMM_STAGES;
-                if (it >= GEMM_STAGES) ok = mbar_wait(smem_u32(&empty_bar[s]), ((it / GEMM_STAGES) - 1) & 1);
+                if (it >= GEMM_STAGES) ok = mbar_wait(smem_u32(&empty_bar[s]), ((it / GEMM_STAGES) - 1) & 1, g.wait_limit);
                 if (!ok) break;
                 unsigned char *sa = smem + s * (a_bytes + b_bytes), *sb = sa + a_bytes;
                 mbar_expect_tx(smem_u32(&full_bar[s]), a_bytes + b_bytes);
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
             const int j = it - (GEMM_STAGES - 1);
             if (j >= 0 && j < nk) {  // multiply chunk j
                 const int s = j % GEMM_STAGES;
-                ok = mbar_wait(smem_u32(&full_bar[s]), (j / GEMM_STAGES) & 1);
+                ok = mbar_wait(smem_u32(&full_bar[s]), (j / GEMM_STAGES) & 1, g.wait_limit);
                 if (!ok) break;
                 consumed = j + 1;
                 asm volatile("tcgen05.fence::after_thread_sync;");

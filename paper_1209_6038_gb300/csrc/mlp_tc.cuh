@@ -44,6 +44,7 @@ struct GemmArgs {
     int ldht;
     int epi;
     unsigned int *err;           // error flag (0 = ok)
+    unsigned int wait_limit;     // polls of the waits that decide a timeout (MBAR_DEFAULT_LIMIT)
 };
 
 constexpr int GEMM_TILE_M = 128;

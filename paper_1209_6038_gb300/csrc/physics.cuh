@@ -64,8 +64,9 @@ struct Params {
     int band_df;        // ... taken in double-float instead of FP64
     // FP32 copies for the mixed-precision stepper, rounded once on the host (not converted per step):
     // R1, R2, H/2, K, 1/K, R1^2 as float-float (hi, lo), and the band's outer radius R1 + mixed_band
-    // (0 without a band)
+    // (0 without a band); R2^2 and H/2 as float-float for the event functions of the crossing search
     float R1f, R2f, halfHf, Kf, invKf, R1sq_hf, R1sq_lf, band_limf;
+    float R2sq_hf, R2sq_lf, halfH_hf, halfH_lf;
     int dedicated_blocks;  // batched integration: blocks whose warps take the reserved long rays
     double h_or_tol;
     long long max_steps;

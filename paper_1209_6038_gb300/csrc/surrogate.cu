@@ -8,6 +8,7 @@
 //            dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})                (fused into the GEMM epilogue)
 //            db_l = column sums of dZ_l                            (k_sur_rowsum on the transposed copy)
 //   update   Adam on the FP32 masters, then their BF16 copies W_l and W_l^T (k_sur_adam)
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -18,6 +19,7 @@
 #include "cloak.h"
 #include "mlp_tc.cuh"
 #include "surrogate.h"
+#include "tc_ptx.cuh"
 #include "wavefront.cuh"
 
 namespace ck {
@@ -221,10 +223,16 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static cudaError_t gemm(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs g, cudaStream_t st) {
     return launch_gemm_tc(ta, tb, g, st);
 }
+// Polls of the tensor-core kernels' waits that decide a timeout (process-wide; cloak_set_wait_limit).
+static std::atomic<unsigned int> g_wait_limit{MBAR_DEFAULT_LIMIT};
+unsigned int wait_limit() { return g_wait_limit.load(); }
+void set_wait_limit(unsigned int polls) { g_wait_limit.store(polls ? polls : MBAR_DEFAULT_LIMIT); }
+
 static GemmArgs gemm_args(int M, int N, int K, int epi, unsigned int *err) {
     GemmArgs g;
     memset(&g, 0, sizeof(g));
     g.M = M; g.N = N; g.K = K; g.ksplit = 1; g.epi = epi; g.err = err;
+    g.wait_limit = wait_limit();
     return g;
 }
 static bool tmap(CUtensorMap *m, const void *base, long long rows, int cols, int box_rows) {
@@ -611,8 +619,7 @@ int sur_forward_rows(SurNet *s, const float *dev_x, long long n, float *dev_y, c
     cudaError_t e = sur_ensure_inference(s, n);
     if (e != cudaSuccess) { why = "cannot allocate the inference scratch"; return CLOAK_ENOMEM; }
     const long long rows = (n + 127) / 128 * 128;
-    unsigned int *err = gemm_err_flag();
-    s->err = err;
+    unsigned int *err = s->err;  // this network's own timeout flag
     cudaMemsetAsync(err, 0, 4, st);
     k_sur_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dev_x, n, s->X);
     if ((e = sur_forward(s, rows, nullptr, st)) != cudaSuccess) { why = cudaGetErrorString(e); return CLOAK_ECUDA; }
@@ -630,8 +637,7 @@ int sur_batch_grad(SurNet *s, const float *dev_x, const float *dev_t, long long 
     TrainWS w;
     cudaError_t e = ws_create(w, (int)n);
     if (e != cudaSuccess) { ws_destroy(w); why = "cannot allocate the training workspace"; return CLOAK_ENOMEM; }
-    unsigned int *err = gemm_err_flag();
-    s->err = err;
+    unsigned int *err = s->err;  // this network's own timeout flag
     cudaMemsetAsync(err, 0, 4, st);
     cudaMemsetAsync(w.loss, 0, 8, st);
     k_sur_pack_batch<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dev_x, dev_t, (int)n, w.Xb, w.XTb, w.Tb);
@@ -713,8 +719,7 @@ int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, 
     TrainWS w;
     memset(&w, 0, sizeof(w));
     if (e == cudaSuccess) e = ws_create(w, B);
-    unsigned int *err = gemm_err_flag();
-    s->err = err;
+    unsigned int *err = s->err;  // this network's own timeout flag
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, st);
     // 2. stage 1: regression outputs, Adam, linear warm-up then cosine decay to 2 % of the peak rate
     const long long steps_per_epoch = std::max<long long>(1, n / B);
@@ -851,14 +856,16 @@ cudaError_t sur_render_hook(void *ctx, const Queue &q, cudaStream_t st) {
     SurNet *s = c->s;
     cudaError_t e = sur_ensure_inference(s, c->cap);
     if (e != cudaSuccess) return e;
-    if (c->views) {  // batched render (captured in a graph): per-ray view, mode and variant; the timeout
-                     // flag stays the network's own
+    // The network's timeout flag is cleared before its forward pass and read by the gate: if a bounded wait
+    // of the tensor-core kernel ran out, its outputs are incomplete and the gate leaves every ray to the
+    // integrator (the render stays exact, at the integrator's cost).
+    if ((e = cudaMemsetAsync(s->err, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+    if (c->views) {  // batched render (captured in a graph): per-ray view, mode and variant
         if ((e = launch_sur_features_batch(c->p, c->views, c->nviews, c->spp, c->seed, q, s, st)) != cudaSuccess)
             return e;
         if ((e = sur_forward(s, s->inf_rows, q.count, st)) != cudaSuccess) return e;
         return launch_sur_gate_batch(c->p, c->views, c->nviews, c->spp, c->seed, q, s, c->samples, st);
     }
-    s->err = gemm_err_flag();
     if ((e = launch_sur_features(c->p, c->mode, c->spp, c->seed, q, s, st)) != cudaSuccess) return e;
     if ((e = sur_forward(s, s->inf_rows, q.count, st)) != cudaSuccess) return e;
     return launch_sur_gate(c->p, c->mode, c->spp, c->seed, q, s, c->samples, c->recs, st);

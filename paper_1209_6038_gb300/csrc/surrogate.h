@@ -106,6 +106,9 @@ cudaError_t launch_sur_conf_targets(double R2, double H, unsigned long long seed
                                     const float *Y, float *T_all, cudaStream_t st);
 
 // C ABI back ends (surrogate.cu); CLOAK_* return codes, `why` receives the error text
+// polls of the tensor-core kernels' bounded waits that decide a timeout (0 restores the default)
+unsigned int wait_limit();
+void set_wait_limit(unsigned int polls);
 long long sur_nparams();  // flat FP32 parameter vector: per layer W_l (out x in, row-major), then b_l
 cudaError_t sur_get_params(SurNet *s, float *host);
 cudaError_t sur_set_params(SurNet *s, const float *host);  // also clears the Adam state

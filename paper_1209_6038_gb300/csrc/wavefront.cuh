@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                     if (it >= prefix && hi - lo <= conv * hi) done = true;
                     // or a regula falsi trial point lies on the surface to rounding (Illinois approaches
                     // the root from one side, so the far end of the bracket may lag for many iterations)
-                    const R gtol = (sizeof(R) == 8 ? (R)CROSS_G_TOL : (R)2.4e-7) * (R)cross_g_scale(p, ev);
+                    const R gtol = (R)CROSS_G_TOL * (R)cross_g_scale(p, ev);
                     if (!done && it > prefix && fabs(gs) <= gtol) {
                         lo = s;
                         hi = s;

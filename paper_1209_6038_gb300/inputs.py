@@ -126,6 +126,13 @@ def ray_set(n: int, seed: int, kind: str = "mixed", R2: float = 1.0, H: float = 
     return np.concatenate([np.stack([ox, oy, z0], 1), d], 1)
 
 
+def sample_pixels(w: Workload, img_index: int, n: int, seed: int = 12345):
+    """Seeded sample of n distinct pixels (flat indices j * width + i, sorted) of image img_index of w: the
+    pixels whose rays are checked against the oracle."""
+    rng = np.random.default_rng(seed + img_index)
+    return np.sort(rng.choice(w.width * w.height, n, replace=False))
+
+
 BATCH_RESOLUTIONS = ((256, 256), (1024, 768), (1920, 1080), (3840, 2160))
 
 
