@@ -86,6 +86,12 @@ struct Stepper64 {
 #pragma unroll
         for (int i = 0; i < 6; ++i) out[i] = y[i];
     }
+    // final state into queue slot k (FP64 format)
+    template <typename Q>
+    __device__ __forceinline__ void store(const Q &q, int k) const {
+        q.x[k] = y[0]; q.y[k] = y[1]; q.z[k] = y[2];
+        q.vx[k] = y[3]; q.vy[k] = y[4]; q.vz[k] = y[5];
+    }
 };
 
 // ------------------------------------------------------------------ mixed stepper
@@ -265,15 +271,23 @@ struct StepperMixed {
     bool need_k1;
     int vm;  // 2 * variant + mode when VAR = MODE = V_ANY
 
+    // the queue holds the mixed path's states as float-float pairs: no conversion
     template <typename Q>
     __device__ __forceinline__ void load(const Q &q, int k) {
-        double v[6] = {q.x[k], q.y[k], q.z[k], q.vx[k], q.vy[k], q.vz[k]};
+        const double *a[6] = {q.x, q.y, q.z, q.vx, q.vy, q.vz};
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            yh[i] = (float)v[i];
-            yl[i] = (float)(v[i] - (double)yh[i]);
+            const float2 v = reinterpret_cast<const float2 *>(a[i])[k];
+            yh[i] = v.x;
+            yl[i] = v.y;
         }
         need_k1 = true;
+    }
+    template <typename Q>
+    __device__ __forceinline__ void store(const Q &q, int k) const {
+        double *a[6] = {q.x, q.y, q.z, q.vx, q.vy, q.vz};
+#pragma unroll
+        for (int i = 0; i < 6; ++i) reinterpret_cast<float2 *>(a[i])[k] = make_float2(yh[i], yl[i]);
     }
     __device__ __forceinline__ bool island(const Params &p) const {
         if (VAR == V_TEST || (VAR == V_RADIAL && MODE == M_ORD) || (VAR == V_ANY && vm == 0)) return false;

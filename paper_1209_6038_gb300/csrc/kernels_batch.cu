@@ -34,13 +34,14 @@ __global__ void __launch_bounds__(128) k_batch_entry(Params p, const ViewDev *vi
     double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
     // the camera's polariser along this view's own right or up vector
     const double *axis = p.analyzer == 1 ? vw.rt : p.analyzer == 2 ? vw.up : nullptr;
-    double w_out = transmission_out(mode, mat[0], mat[1], c, n_in, mk0, axis);
+    double w_out = entry_factor(p, mode, mat[0], mat[1], c, n_in, mk0, axis);
     // queue key: medium/mode (major: one segment of the sorted queue per medium) and cost bucket (minor,
     // slowest first within a segment after the descending sort)
     double dy[6];
     const bool first = p.precision == 0 && p.formulation == 0;  // the FP64 Fermat stepper's first stage
     if (first) rhs<V_ANY, V_ANY>(pv, y, dy, vw.vm);
-    queue_append(q, y, w_out, (int)g, batch_key(vw.vm, cost_bucket(y, k0)), first ? dy + 3 : nullptr);
+    queue_append(q, y, w_out, (int)g, batch_key(vw.vm, cost_bucket(y, k0)), first ? dy + 3 : nullptr,
+                 p.precision != 0);
 }
 
 __global__ void __launch_bounds__(128) k_batch_exit(Params p, const ViewDev *views, int nviews, int spp,
@@ -178,7 +179,9 @@ __global__ void __launch_bounds__(128) k_refl_spawn(Params p, Queue q, Queue q2)
         const int vm = key_vm(key), mode = vm & 1;
         Params pv = p;
         pv.variant = vm >> 1;
-        const double x[3] = {q.x[k], q.y[k], q.z[k]}, w[3] = {q.vx[k], q.vy[k], q.vz[k]};
+        double ys[6];
+        get_state(p.precision != 0, q, k, ys);
+        const double x[3] = {ys[0], ys[1], ys[2]}, w[3] = {ys[3], ys[4], ys[5]};
         double nrm[3], eo, ee, c[3], kk[3];
         face_normal(q.face[k], x, nrm);
         local_material(pv, x, eo, ee, c);
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(128) k_refl_spawn(Params p, Queue q, Queue q2)
             const double y[6] = {x[0], x[1], x[2], p.formulation ? k2[0] : v2[0], p.formulation ? k2[1] : v2[1],
                                  p.formulation ? k2[2] : v2[2]};
             queue_append(q2, y, q.w_out[k] * R[m2], 2 * q.id[k] + m2,
-                         batch_key(2 * pv.variant + m2, cost_bucket(y, k2)));
+                         batch_key(2 * pv.variant + m2, cost_bucket(y, k2)), nullptr, p.precision != 0);
         }
     }
 }
@@ -231,10 +234,10 @@ static cudaError_t refl_ip(const Params &p, const Queue &q, const Queue &q2, flo
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q2);
     const int pk = packet > 0 ? packet : 128;
     int nb = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V_ANY, V_ANY, I, PREC>, pk, 0)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wf_integrate_kernel<V_ANY, V_ANY, I, PREC>(), pk, 0)) !=
         cudaSuccess)
         return e;
-    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(p, q2);
+    wf_integrate_kernel<V_ANY, V_ANY, I, PREC>()<<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(p, q2);
     k_refl_exit<<<sms * 16, 128, 0, st>>>(p, q2, refl);
     return cudaGetLastError();
 }
@@ -272,11 +275,11 @@ static cudaError_t batch_ip(const Params &p, const ViewDev *views, int nviews, i
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
     mark(ev, 1, st);
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V_ANY, V_ANY, I, PREC>, pk, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wf_integrate_kernel<V_ANY, V_ANY, I, PREC>(), pk, 0);
     if (e != cudaSuccess) return e;
     Params pl = p;
     pl.dedicated_blocks = LONG_RAY_BLOCKS;
-    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(pl, q);
+    wf_integrate_kernel<V_ANY, V_ANY, I, PREC>()<<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(pl, q);
     mark(ev, 2, st);
     k_batch_exit<<<sms * 16, 128, 0, st>>>(p, views, nviews, spp, seed, q, samples);
     mark(ev, 3, st);
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(128) k_sur_gen_entry(Params p, long long n, un
     const bool inside = mode ? enter<M_EXT>(pv, o, d, rec, rgb, y, k0, n_in, mat)
                              : enter<M_ORD>(pv, o, d, rec, rgb, y, k0, n_in, mat);
     if (!inside) return;
-    queue_append(q, y, 1.0, (int)i, batch_key(2 * variant + mode, cost_bucket(y, k0)));
+    queue_append(q, y, 1.0, (int)i, batch_key(2 * variant + mode, cost_bucket(y, k0)), nullptr, p.precision != 0);
 }
 
 __global__ void __launch_bounds__(128) k_sur_gen_exit(Params p, unsigned long long seed, Queue q, float *T_all) {
@@ -350,9 +353,9 @@ static cudaError_t sur_data_ip(const Params &p, long long n, unsigned long long 
     k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH, 0u);
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V_ANY, V_ANY, I, PREC>, 128, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wf_integrate_kernel<V_ANY, V_ANY, I, PREC>(), 128, 0);
     if (e != cudaSuccess) return e;
-    k_wf_integrate<V_ANY, V_ANY, I, PREC><<<(nb > 0 ? nb : 1) * sms, 128, 0, st>>>(p, q);
+    wf_integrate_kernel<V_ANY, V_ANY, I, PREC>()<<<(nb > 0 ? nb : 1) * sms, 128, 0, st>>>(p, q);
     k_sur_gen_exit<<<sms * 16, 128, 0, st>>>(p, seed, q, T_all);
     return cudaGetLastError();
 }

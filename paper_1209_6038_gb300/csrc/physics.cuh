@@ -83,7 +83,8 @@ struct Params {
 };
 
 // ------------------------------------------------------------------ helpers
-__device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
+template <typename T>
+__device__ __forceinline__ T dot3(const T a[3], const T b[3]) {
     return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
 }
 
@@ -510,96 +511,112 @@ __device__ __forceinline__ void face_normal(int ev, const double x[3], double n[
 // ------------------------------------------------------------------ interface (Sect. 3)
 // Inward wave of the mode with tangential wave vector kt at a face with outward normal n.
 // Returns false if the mode is evanescent; else wave vector k and ray velocity v = M^-1 k (Eq. 6).
-__device__ __forceinline__ bool refract_in(int mode, double eo, double ee, const double c[3], const double n[3],
-                                           const double kt[3], double k[3], double v[3]) {
-    double kt2 = dot3(kt, kt);
+template <typename T>
+__device__ __forceinline__ bool refract_in(int mode, T eo, T ee, const T c[3], const T n[3],
+                                           const T kt[3], T k[3], T v[3]) {
+    T kt2 = dot3(kt, kt);
     if (mode == M_ORD) {
-        double a = eo - kt2;
-        if (a < 0.0) return false;
-        double q = -sqrt(a);
-        double ie = 1.0 / eo;
+        T a = eo - kt2;
+        if (a < T(0)) return false;
+        T q = -sqrt(a);
+        T ie = T(1) / eo;
         for (int i = 0; i < 3; ++i) { k[i] = fma(q, n[i], kt[i]); v[i] = k[i] * ie; }
         return true;
     }
-    double iee = 1.0 / ee, dl = 1.0 / eo - iee;
-    double cn = dot3(c, n), ckt = dot3(c, kt);
-    double A = fma(dl * cn, cn, iee);
-    double B = dl * cn * ckt;
-    double C = fma(iee, kt2, fma(dl * ckt, ckt, -1.0));
-    double disc = B * B - A * C;
-    if (disc < 0.0) return false;
-    double sq = sqrt(disc);
-    double q;
-    if (B > 0.0) q = (-B - sq) / A;
-    else q = (-B + sq) > 0.0 ? C / (-B + sq) : 0.0;
+    T iee = T(1) / ee, dl = T(1) / eo - iee;
+    T cn = dot3(c, n), ckt = dot3(c, kt);
+    T A = fma(dl * cn, cn, iee);
+    T B = dl * cn * ckt;
+    T C = fma(iee, kt2, fma(dl * ckt, ckt, -T(1)));
+    T disc = B * B - A * C;
+    if (disc < T(0)) return false;
+    T sq = sqrt(disc);
+    T q;
+    if (B > T(0)) q = (-B - sq) / A;
+    else q = (-B + sq) > T(0) ? C / (-B + sq) : T(0);
     for (int i = 0; i < 3; ++i) k[i] = fma(q, n[i], kt[i]);
-    double ck_ = dot3(c, k);
+    T ck_ = dot3(c, k);
     for (int i = 0; i < 3; ++i) v[i] = fma(iee, k[i], dl * ck_ * c[i]);
     return true;
 }
 
 // k = M v for the mode (Eq. 6 inverted)
-__device__ __forceinline__ void wave_from_velocity(int mode, double eo, double ee, const double c[3],
-                                                   const double v[3], double k[3]) {
+template <typename T>
+__device__ __forceinline__ void wave_from_velocity(int mode, T eo, T ee, const T c[3],
+                                                   const T v[3], T k[3]) {
     if (mode == M_ORD) {
         for (int i = 0; i < 3; ++i) k[i] = eo * v[i];
     } else {
-        double cv = dot3(c, v);
+        T cv = dot3(c, v);
         for (int i = 0; i < 3; ++i) k[i] = fma(ee, v[i], (eo - ee) * cv * c[i]);
     }
 }
 
 // ---- complex helpers for Eq. 12
-struct cx {
-    double re, im;
+template <typename T>
+struct cxt {
+    T re, im;
 };
-__device__ __forceinline__ cx C(double a, double b = 0.0) { return cx{a, b}; }
-__device__ __forceinline__ cx operator+(cx a, cx b) { return cx{a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ cx operator-(cx a, cx b) { return cx{a.re - b.re, a.im - b.im}; }
-__device__ __forceinline__ cx operator*(cx a, cx b) {
-    return cx{fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+typedef cxt<double> cx;
+template <typename T>
+__device__ __forceinline__ cxt<T> C(T a, T b = T(0)) { return cxt<T>{a, b}; }
+template <typename T>
+__device__ __forceinline__ cxt<T> operator+(cxt<T> a, cxt<T> b) { return cxt<T>{a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ cxt<T> operator-(cxt<T> a, cxt<T> b) { return cxt<T>{a.re - b.re, a.im - b.im}; }
+template <typename T>
+__device__ __forceinline__ cxt<T> operator*(cxt<T> a, cxt<T> b) {
+    return cxt<T>{fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
 }
-__device__ __forceinline__ cx operator*(double s, cx a) { return cx{s * a.re, s * a.im}; }
-__device__ __forceinline__ cx cdiv(cx a, cx b) {  // a / b = a conj(b) / |b|^2, one reciprocal
-    const double id = rcp_nr(b.re * b.re + b.im * b.im);
-    return cx{(a.re * b.re + a.im * b.im) * id, (a.im * b.re - a.re * b.im) * id};
+template <typename T>
+__device__ __forceinline__ cxt<T> operator*(T s, cxt<T> a) { return cxt<T>{s * a.re, s * a.im}; }
+template <typename T>
+__device__ __forceinline__ cxt<T> cdiv(cxt<T> a, cxt<T> b) {  // a / b = a conj(b) / |b|^2, one reciprocal
+    const T id = rcp_nr(b.re * b.re + b.im * b.im);
+    return cxt<T>{(a.re * b.re + a.im * b.im) * id, (a.im * b.re - a.re * b.im) * id};
 }
-__device__ __forceinline__ double cabs2(cx a) { return a.re * a.re + a.im * a.im; }
-__device__ __forceinline__ cx cdot(const cx a[3], const cx b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
-__device__ __forceinline__ void ccross(const cx a[3], const cx b[3], cx o[3]) {
+template <typename T>
+__device__ __forceinline__ T cabs2(cxt<T> a) { return a.re * a.re + a.im * a.im; }
+template <typename T>
+__device__ __forceinline__ cxt<T> cdot(const cxt<T> a[3], const cxt<T> b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+template <typename T>
+__device__ __forceinline__ void ccross(const cxt<T> a[3], const cxt<T> b[3], cxt<T> o[3]) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
-__device__ __forceinline__ double vnorm2(const cx a[3]) { return cabs2(a[0]) + cabs2(a[1]) + cabs2(a[2]); }
+template <typename T>
+__device__ __forceinline__ T vnorm2(const cxt<T> a[3]) { return cabs2(a[0]) + cabs2(a[1]) + cabs2(a[2]); }
 // n . Re(E x conj(H))
-__device__ __forceinline__ double flux_n(const double n[3], const cx E[3], const cx H[3]) {
-    double s = 0.0;
+template <typename T>
+__device__ __forceinline__ T flux_n(const T n[3], const cxt<T> E[3], const cxt<T> H[3]) {
+    T s = T(0);
     const int i1[3] = {1, 2, 0}, i2[3] = {2, 0, 1};
     for (int i = 0; i < 3; ++i) {
         // Re(E_a conj(H_b) - E_b conj(H_a))
         int a = i1[i], b = i2[i];
-        double re = (E[a].re * H[b].re + E[a].im * H[b].im) - (E[b].re * H[a].re + E[b].im * H[a].im);
+        T re = (E[a].re * H[b].re + E[a].im * H[b].im) - (E[b].re * H[a].re + E[b].im * H[a].im);
         s += n[i] * re;
     }
     return s;
 }
 
 // Inward wave (possibly evanescent: decaying into the medium) of the mode with tangential kt.
-__device__ __forceinline__ void inward_wave_c(int mode, double eo, double ee, const double c[3], const double n[3],
-                                              const double kt[3], cx k[3]) {
-    double kr[3], vr[3];
+template <typename T>
+__device__ __forceinline__ void inward_wave_c(int mode, T eo, T ee, const T c[3], const T n[3],
+                                              const T kt[3], cxt<T> k[3]) {
+    T kr[3], vr[3];
     if (refract_in(mode, eo, ee, c, n, kt, kr, vr)) {
         for (int i = 0; i < 3; ++i) k[i] = C(kr[i]);
         return;
     }
-    cx q;
+    cxt<T> q;
     if (mode == M_ORD) {
-        q = C(0.0, -sqrt(dot3(kt, kt) - eo));
+        q = C(T(0), -sqrt(dot3(kt, kt) - eo));
     } else {
-        double iee = 1.0 / ee, dl = 1.0 / eo - iee;
-        double cn = dot3(c, n), ckt = dot3(c, kt);
-        double A = fma(dl * cn, cn, iee), B = dl * cn * ckt, Cc = iee * dot3(kt, kt) + dl * ckt * ckt - 1.0;
+        T iee = T(1) / ee, dl = T(1) / eo - iee;
+        T cn = dot3(c, n), ckt = dot3(c, kt);
+        T A = fma(dl * cn, cn, iee), B = dl * cn * ckt, Cc = iee * dot3(kt, kt) + dl * ckt * ckt - T(1);
         q = C(-B / A, -sqrt(A * Cc - B * B) / A);
     }
     for (int i = 0; i < 3; ++i) k[i] = C(kt[i]) + q * C(n[i]);
@@ -608,16 +625,17 @@ __device__ __forceinline__ void inward_wave_c(int mode, double eo, double ee, co
 // Field directions of a plane wave of the mode (Sect. 3): D_o perpendicular to the ordinary
 // main section, D_e in the extraordinary main section and perpendicular to k; E = eps^-1 D,
 // H = k x E.  Degenerate k parallel to c: D_o along z x k (x x k if that vanishes too).
-__device__ __forceinline__ void wave_fields(int mode, double eo, double ee, const double c[3], const cx k[3],
-                                            cx E[3], cx H[3]) {
-    cx cc[3] = {C(c[0]), C(c[1]), C(c[2])}, Do[3], D[3];
+template <typename T>
+__device__ __forceinline__ void wave_fields(int mode, T eo, T ee, const T c[3], const cxt<T> k[3],
+                                            cxt<T> E[3], cxt<T> H[3]) {
+    cxt<T> cc[3] = {C(c[0]), C(c[1]), C(c[2])}, Do[3], D[3];
     ccross(cc, k, Do);
-    double kk2 = vnorm2(k);
-    if (vnorm2(Do) < 1e-20 * kk2) {
-        cx z3[3] = {C(0), C(0), C(1)};
+    T kk2 = vnorm2(k);
+    if (vnorm2(Do) < T(1e-20) * kk2) {
+        cxt<T> z3[3] = {C(T(0)), C(T(0)), C(T(1))};
         ccross(z3, k, Do);
-        if (vnorm2(Do) < 1e-20 * kk2) {
-            cx x3[3] = {C(1), C(0), C(0)};
+        if (vnorm2(Do) < T(1e-20) * kk2) {
+            cxt<T> x3[3] = {C(T(1)), C(T(0)), C(T(0))};
             ccross(x3, k, Do);
         }
         if (mode == M_EXT) ccross(k, Do, D);
@@ -625,61 +643,63 @@ __device__ __forceinline__ void wave_fields(int mode, double eo, double ee, cons
     } else if (mode == M_ORD) {
         for (int i = 0; i < 3; ++i) D[i] = Do[i];
     } else {
-        cx kk = cdot(k, k), ckk = cdot(cc, k);
+        cxt<T> kk = cdot(k, k), ckk = cdot(cc, k);
         for (int i = 0; i < 3; ++i) D[i] = kk * cc[i] - ckk * k[i];
     }
     // eps^-1 = I/eo + (1/ee - 1/eo) c c^T
-    double ieo = 1.0 / eo, dl = 1.0 / ee - ieo;
-    cx cD = cdot(cc, D);
+    T ieo = T(1) / eo, dl = T(1) / ee - ieo;
+    cxt<T> cD = cdot(cc, D);
     for (int i = 0; i < 3; ++i) E[i] = ieo * D[i] + (dl * c[i]) * cD;
     ccross(k, E, H);
 }
 
-__device__ __forceinline__ void unit_perp(const double n[3], double t[3]) {
+template <typename T>
+__device__ __forceinline__ void unit_perp(const T n[3], T t[3]) {
     // any unit vector perpendicular to n
-    double a[3] = {0.0, 0.0, 0.0};
+    T a[3] = {T(0), T(0), T(0)};
     int m = fabs(n[0]) < fabs(n[1]) ? (fabs(n[0]) < fabs(n[2]) ? 0 : 2) : (fabs(n[1]) < fabs(n[2]) ? 1 : 2);
-    a[m] = 1.0;
+    a[m] = T(1);
     t[0] = n[1] * a[2] - n[2] * a[1];
     t[1] = n[2] * a[0] - n[0] * a[2];
     t[2] = n[0] * a[1] - n[1] * a[0];
-    double l = sqrt(dot3(t, t));
+    T l = sqrt(dot3(t, t));
     for (int i = 0; i < 3; ++i) t[i] /= l;
 }
 
-__device__ __forceinline__ void s_basis(const double k[3], const double n[3], double s[3]) {
+template <typename T>
+__device__ __forceinline__ void s_basis(const T k[3], const T n[3], T s[3]) {
     s[0] = k[1] * n[2] - k[2] * n[1];
     s[1] = k[2] * n[0] - k[0] * n[2];
     s[2] = k[0] * n[1] - k[1] * n[0];
-    double l = sqrt(dot3(s, s));
-    if (l < 1e-12) unit_perp(n, s);
+    T l = sqrt(dot3(s, s));
+    if (l < T(1e-12)) unit_perp(n, s);
     else for (int i = 0; i < 3; ++i) s[i] /= l;
 }
 
 // Solve the complex 4x4 system A X = B for NR right-hand sides (Gaussian elimination, partial pivoting).
-template <int NR>
-__device__ bool csolve4(cx A[4][4], cx B[4][NR]) {
+template <int NR, typename T>
+__device__ bool csolve4(cxt<T> A[4][4], cxt<T> B[4][NR]) {
     for (int col = 0; col < 4; ++col) {
         int piv = col;
-        double best = cabs2(A[col][col]);
+        T best = cabs2(A[col][col]);
         for (int r = col + 1; r < 4; ++r) {
-            double v = cabs2(A[r][col]);
+            T v = cabs2(A[r][col]);
             if (v > best) { best = v; piv = r; }
         }
-        if (best == 0.0) return false;
+        if (best == T(0)) return false;
         if (piv != col) {
-            for (int k = 0; k < 4; ++k) { cx t = A[col][k]; A[col][k] = A[piv][k]; A[piv][k] = t; }
-            for (int k = 0; k < NR; ++k) { cx t = B[col][k]; B[col][k] = B[piv][k]; B[piv][k] = t; }
+            for (int k = 0; k < 4; ++k) { cxt<T> t = A[col][k]; A[col][k] = A[piv][k]; A[piv][k] = t; }
+            for (int k = 0; k < NR; ++k) { cxt<T> t = B[col][k]; B[col][k] = B[piv][k]; B[piv][k] = t; }
         }
         for (int r = col + 1; r < 4; ++r) {
-            cx f = cdiv(A[r][col], A[col][col]);
+            cxt<T> f = cdiv(A[r][col], A[col][col]);
             for (int k = col; k < 4; ++k) A[r][k] = A[r][k] - f * A[col][k];
             for (int k = 0; k < NR; ++k) B[r][k] = B[r][k] - f * B[col][k];
         }
     }
     for (int r = 3; r >= 0; --r)
         for (int k = 0; k < NR; ++k) {
-            cx s = B[r][k];
+            cxt<T> s = B[r][k];
             for (int j = r + 1; j < 4; ++j) s = s - A[r][j] * B[j][k];
             B[r][k] = cdiv(s, A[r][r]);
         }
@@ -687,86 +707,88 @@ __device__ bool csolve4(cx A[4][4], cx B[4][NR]) {
 }
 
 // Eq. 12, vacuum -> medium, unpolarised light (mean over s and p): transmission into `mode`.
-static __device__ __noinline__ double transmission_in(int mode, double eo, double ee, const double c[3], const double n[3],
-                                               const double d[3]) {
-    double dn = dot3(d, n), kt[3], kr[3];
-    for (int i = 0; i < 3; ++i) { kt[i] = d[i] - dn * n[i]; kr[i] = d[i] - 2.0 * dn * n[i]; }
-    cx ko[3], ke[3], Eo[3], Ho[3], Ee[3], He[3];
+template <typename T>
+static __device__ __noinline__ T transmission_in(int mode, T eo, T ee, const T c[3], const T n[3],
+                                               const T d[3]) {
+    T dn = dot3(d, n), kt[3], kr[3];
+    for (int i = 0; i < 3; ++i) { kt[i] = d[i] - dn * n[i]; kr[i] = d[i] - T(2) * dn * n[i]; }
+    cxt<T> ko[3], ke[3], Eo[3], Ho[3], Ee[3], He[3];
     inward_wave_c(M_ORD, eo, ee, c, n, kt, ko);
     inward_wave_c(M_EXT, eo, ee, c, n, kt, ke);
     wave_fields(M_ORD, eo, ee, c, ko, Eo, Ho);
     wave_fields(M_EXT, eo, ee, c, ke, Ee, He);
-    double s[3], pi[3], pr[3], t2[3];
+    T s[3], pi[3], pr[3], t2[3];
     s_basis(d, n, s);
     pi[0] = s[1] * d[2] - s[2] * d[1]; pi[1] = s[2] * d[0] - s[0] * d[2]; pi[2] = s[0] * d[1] - s[1] * d[0];
     pr[0] = s[1] * kr[2] - s[2] * kr[1]; pr[1] = s[2] * kr[0] - s[0] * kr[2]; pr[2] = s[0] * kr[1] - s[1] * kr[0];
     t2[0] = n[1] * s[2] - n[2] * s[1]; t2[1] = n[2] * s[0] - n[0] * s[2]; t2[2] = n[0] * s[1] - n[1] * s[0];
     // columns: reflected s, reflected p, -o, -e ; rows: E.t1, E.t2, H.t1, H.t2 with t1 = s
-    cx Ers[3] = {C(s[0]), C(s[1]), C(s[2])}, Erp[3] = {C(pr[0]), C(pr[1]), C(pr[2])}, Hrs[3], Hrp[3];
-    cx ckr[3] = {C(kr[0]), C(kr[1]), C(kr[2])};
+    cxt<T> Ers[3] = {C(s[0]), C(s[1]), C(s[2])}, Erp[3] = {C(pr[0]), C(pr[1]), C(pr[2])}, Hrs[3], Hrp[3];
+    cxt<T> ckr[3] = {C(kr[0]), C(kr[1]), C(kr[2])};
     ccross(ckr, Ers, Hrs);
     ccross(ckr, Erp, Hrp);
-    cx ct1[3] = {C(s[0]), C(s[1]), C(s[2])}, ct2[3] = {C(t2[0]), C(t2[1]), C(t2[2])};
-    const cx *colE[4] = {Ers, Erp, Eo, Ee}, *colH[4] = {Hrs, Hrp, Ho, He};
-    cx A[4][4], B[4][2];
+    cxt<T> ct1[3] = {C(s[0]), C(s[1]), C(s[2])}, ct2[3] = {C(t2[0]), C(t2[1]), C(t2[2])};
+    const cxt<T> *colE[4] = {Ers, Erp, Eo, Ee}, *colH[4] = {Hrs, Hrp, Ho, He};
+    cxt<T> A[4][4], B[4][2];
     for (int j = 0; j < 4; ++j) {
-        double sg = j < 2 ? 1.0 : -1.0;
+        T sg = j < 2 ? T(1) : -T(1);
         A[0][j] = sg * cdot(colE[j], ct1);
         A[1][j] = sg * cdot(colE[j], ct2);
         A[2][j] = sg * cdot(colH[j], ct1);
         A[3][j] = sg * cdot(colH[j], ct2);
     }
-    cx cd[3] = {C(d[0]), C(d[1]), C(d[2])};
-    double fin[2];
+    cxt<T> cd[3] = {C(d[0]), C(d[1]), C(d[2])};
+    T fin[2];
     for (int pol = 0; pol < 2; ++pol) {
-        const double *e = pol == 0 ? s : pi;
-        cx Ei[3] = {C(e[0]), C(e[1]), C(e[2])}, Hi[3];
+        const T *e = pol == 0 ? s : pi;
+        cxt<T> Ei[3] = {C(e[0]), C(e[1]), C(e[2])}, Hi[3];
         ccross(cd, Ei, Hi);
-        B[0][pol] = -1.0 * cdot(Ei, ct1);
-        B[1][pol] = -1.0 * cdot(Ei, ct2);
-        B[2][pol] = -1.0 * cdot(Hi, ct1);
-        B[3][pol] = -1.0 * cdot(Hi, ct2);
+        B[0][pol] = -T(1) * cdot(Ei, ct1);
+        B[1][pol] = -T(1) * cdot(Ei, ct2);
+        B[2][pol] = -T(1) * cdot(Hi, ct1);
+        B[3][pol] = -T(1) * cdot(Hi, ct2);
         fin[pol] = fabs(flux_n(n, Ei, Hi));
     }
-    if (!csolve4<2>(A, B)) return 0.0;
-    const cx *Em = mode == M_ORD ? Eo : Ee, *Hm = mode == M_ORD ? Ho : He;
+    if (!csolve4<2>(A, B)) return T(0);
+    const cxt<T> *Em = mode == M_ORD ? Eo : Ee, *Hm = mode == M_ORD ? Ho : He;
     int row = mode == M_ORD ? 2 : 3;
-    double fm = fabs(flux_n(n, Em, Hm));
-    return 0.5 * (cabs2(B[row][0]) * fm / fin[0] + cabs2(B[row][1]) * fm / fin[1]);
+    T fm = fabs(flux_n(n, Em, Hm));
+    return T(0.5) * (cabs2(B[row][0]) * fm / fin[0] + cabs2(B[row][1]) * fm / fin[1]);
 }
 
 // Eq. 12, medium -> vacuum (Sect. 3, last paragraph): fraction of the incident mode's normal
 // energy flux carried by the refracted vacuum wave.  0 for total internal reflection.
 // axis: a linear polariser the transmitted vacuum wave then meets (nullable): the result is multiplied by
 // the fraction of that wave's flux along the axis taken across the wave (Malus's law)
-static __device__ __noinline__ double transmission_out(int mode, double eo, double ee, const double c[3],
-                                                const double n[3], const double k[3], const double *axis = nullptr) {
-    double kn = dot3(k, n), kt[3];
+template <typename T>
+static __device__ __noinline__ T transmission_out(int mode, T eo, T ee, const T c[3],
+                                                const T n[3], const T k[3], const T *axis = nullptr) {
+    T kn = dot3(k, n), kt[3];
     for (int i = 0; i < 3; ++i) kt[i] = k[i] - kn * n[i];
-    double kt2 = dot3(kt, kt);
-    if (kt2 > 1.0) return 0.0;
-    double kv[3], s[3], pv[3], t2[3];
-    double qn = sqrt(1.0 - kt2);
+    T kt2 = dot3(kt, kt);
+    if (kt2 > T(1)) return T(0);
+    T kv[3], s[3], pv[3], t2[3];
+    T qn = sqrt(T(1) - kt2);
     for (int i = 0; i < 3; ++i) kv[i] = fma(qn, n[i], kt[i]);
     s_basis(kv, n, s);
     pv[0] = s[1] * kv[2] - s[2] * kv[1]; pv[1] = s[2] * kv[0] - s[0] * kv[2]; pv[2] = s[0] * kv[1] - s[1] * kv[0];
     t2[0] = n[1] * s[2] - n[2] * s[1]; t2[1] = n[2] * s[0] - n[0] * s[2]; t2[2] = n[0] * s[1] - n[1] * s[0];
-    cx ckv[3] = {C(kv[0]), C(kv[1]), C(kv[2])};
-    cx Es[3] = {C(s[0]), C(s[1]), C(s[2])}, Ep[3] = {C(pv[0]), C(pv[1]), C(pv[2])}, Hs[3], Hp[3];
+    cxt<T> ckv[3] = {C(kv[0]), C(kv[1]), C(kv[2])};
+    cxt<T> Es[3] = {C(s[0]), C(s[1]), C(s[2])}, Ep[3] = {C(pv[0]), C(pv[1]), C(pv[2])}, Hs[3], Hp[3];
     ccross(ckv, Es, Hs);
     ccross(ckv, Ep, Hp);
-    cx kro[3], kre[3], Ero[3], Hro[3], Ere[3], Hre[3], Em[3], Hm[3];
+    cxt<T> kro[3], kre[3], Ero[3], Hro[3], Ere[3], Hre[3], Em[3], Hm[3];
     inward_wave_c(M_ORD, eo, ee, c, n, kt, kro);
     inward_wave_c(M_EXT, eo, ee, c, n, kt, kre);
     wave_fields(M_ORD, eo, ee, c, kro, Ero, Hro);
     wave_fields(M_EXT, eo, ee, c, kre, Ere, Hre);
-    cx ck3[3] = {C(k[0]), C(k[1]), C(k[2])};
+    cxt<T> ck3[3] = {C(k[0]), C(k[1]), C(k[2])};
     wave_fields(mode, eo, ee, c, ck3, Em, Hm);
-    cx ct1[3] = {C(s[0]), C(s[1]), C(s[2])}, ct2[3] = {C(t2[0]), C(t2[1]), C(t2[2])};
-    const cx *colE[4] = {Es, Ep, Ero, Ere}, *colH[4] = {Hs, Hp, Hro, Hre};
-    cx A[4][4], B[4][1];
+    cxt<T> ct1[3] = {C(s[0]), C(s[1]), C(s[2])}, ct2[3] = {C(t2[0]), C(t2[1]), C(t2[2])};
+    const cxt<T> *colE[4] = {Es, Ep, Ero, Ere}, *colH[4] = {Hs, Hp, Hro, Hre};
+    cxt<T> A[4][4], B[4][1];
     for (int j = 0; j < 4; ++j) {
-        double sg = j < 2 ? 1.0 : -1.0;
+        T sg = j < 2 ? T(1) : -T(1);
         A[0][j] = sg * cdot(colE[j], ct1);
         A[1][j] = sg * cdot(colE[j], ct2);
         A[2][j] = sg * cdot(colH[j], ct1);
@@ -776,24 +798,24 @@ static __device__ __noinline__ double transmission_out(int mode, double eo, doub
     B[1][0] = cdot(Em, ct2);
     B[2][0] = cdot(Hm, ct1);
     B[3][0] = cdot(Hm, ct2);
-    double fm = fabs(flux_n(n, Em, Hm));
-    if (!csolve4<1>(A, B)) return 0.0;
-    cx Et[3], Ht[3];
+    T fm = fabs(flux_n(n, Em, Hm));
+    if (!csolve4<1>(A, B)) return T(0);
+    cxt<T> Et[3], Ht[3];
     for (int i = 0; i < 3; ++i) { Et[i] = B[0][0] * Es[i] + B[1][0] * Ep[i]; Ht[i] = B[0][0] * Hs[i] + B[1][0] * Hp[i]; }
-    const double T = fabs(flux_n(n, Et, Ht)) / fm;
-    if (!axis) return T;
+    const T Tr = fabs(flux_n(n, Et, Ht)) / fm;
+    if (!axis) return Tr;
     // the polariser's axis across the transmitted wave kv
-    const double ak = dot3(axis, kv);
-    double a[3];
+    const T ak = dot3(axis, kv);
+    T a[3];
     for (int i = 0; i < 3; ++i) a[i] = axis[i] - ak * kv[i];
-    const double al2 = dot3(a, a);
-    double er = 0.0, ei = 0.0, e2 = 0.0;
+    const T al2 = dot3(a, a);
+    T er = T(0), ei = T(0), e2 = T(0);
     for (int i = 0; i < 3; ++i) {
         er += Et[i].re * a[i];
         ei += Et[i].im * a[i];
         e2 += Et[i].re * Et[i].re + Et[i].im * Et[i].im;
     }
-    return al2 > 0.0 && e2 > 0.0 ? T * (er * er + ei * ei) / (al2 * e2) : 0.0;
+    return al2 > T(0) && e2 > T(0) ? Tr * (er * er + ei * ei) / (al2 * e2) : T(0);
 }
 
 // First-order reflections (Sect. 3 last paragraphs, Sect. 4).

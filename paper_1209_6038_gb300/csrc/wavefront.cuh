@@ -104,11 +104,71 @@ __device__ __forceinline__ void store_tof_sample(const Params &p, float4 *sample
     samples[id] = make_float4((float)(w * tof_difference(p, o, d, rec)), (float)w, 0.f, 0.f);
 }
 
+// State format of the queue.  FP64 renders keep (x, v) as doubles; the mixed-precision path keeps each
+// component as a float-float pair (hi, lo) in the same 8-byte slot, so that its FP32 stepper loads and
+// stores rays with no FP64 arithmetic (a lone refilling lane converting doubles held the SM's FP64 unit
+// 16 cycles per instruction for its whole warp).
+__device__ __forceinline__ void put_state(bool ff, const Queue &q, unsigned int k, const double y[6]) {
+    double *a[6] = {q.x, q.y, q.z, q.vx, q.vy, q.vz};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (ff) {
+            const float hi = (float)y[i];
+            reinterpret_cast<float2 *>(a[i])[k] = make_float2(hi, (float)(y[i] - (double)hi));
+        } else {
+            a[i][k] = y[i];
+        }
+    }
+}
+__device__ __forceinline__ void get_state(bool ff, const Queue &q, unsigned int k, double y[6]) {
+    const double *a[6] = {q.x, q.y, q.z, q.vx, q.vy, q.vz};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (ff) {
+            const float2 v = reinterpret_cast<const float2 *>(a[i])[k];
+            y[i] = (double)v.x + (double)v.y;
+        } else {
+            y[i] = a[i][k];
+        }
+    }
+}
+
+// Eq. 12 factors of the mixed-precision path: the field-continuity solve in FP32 where the vacuum wave meets
+// the face at more than ~11.5 degrees from grazing (cos > 0.2), in FP64 otherwise (the 4x4 system loses its
+// conditioning towards grazing).  The face geometry, the double refraction and the exit refraction stay
+// in FP64 on every path.
+constexpr double F32_EQ12_MIN_COS = 0.2;
+// axis: the camera's polariser (nullable)
+__device__ __forceinline__ double entry_factor(const Params &p, int mode, double eo, double ee, const double c[3],
+                                               const double n[3], const double k[3], const double *axis) {
+    if (p.precision != 0) {
+        const double kn = dot3(k, n), kt2 = dot3(k, k) - kn * kn;  // the vacuum wave's normal part: 1 - kt2
+        if (1.0 - kt2 > F32_EQ12_MIN_COS * F32_EQ12_MIN_COS) {
+            const float cf[3] = {(float)c[0], (float)c[1], (float)c[2]}, nf[3] = {(float)n[0], (float)n[1], (float)n[2]},
+                        kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
+            float af[3];
+            if (axis) { af[0] = (float)axis[0]; af[1] = (float)axis[1]; af[2] = (float)axis[2]; }
+            return (double)transmission_out(mode, (float)eo, (float)ee, cf, nf, kf, axis ? af : (const float *)nullptr);
+        }
+    }
+    return transmission_out(mode, eo, ee, c, n, k, axis);
+}
+// cos_vac: |d . n| of the vacuum wave d at the exit face
+__device__ __forceinline__ double exit_factor(const Params &p, int mode, double eo, double ee, const double c[3],
+                                              const double n[3], const double d[3], double cos_vac) {
+    if (p.precision != 0 && cos_vac > F32_EQ12_MIN_COS) {
+        const float cf[3] = {(float)c[0], (float)c[1], (float)c[2]}, nf[3] = {(float)n[0], (float)n[1], (float)n[2]},
+                    df[3] = {(float)d[0], (float)d[1], (float)d[2]};
+        return (double)transmission_in(mode, (float)eo, (float)ee, cf, nf, df);
+    }
+    return transmission_in(mode, eo, ee, c, n, d);
+}
+
 // Append an entering ray to the queue; one atomic per warp for the slot and one per distinct key.
 // a: dv/dt at y (the integrator's first stage, computed here where every lane of the warp has one), or
-// null.
+// null.  ff: store the state as float-float pairs (mixed precision).
 __device__ __forceinline__ void queue_append(const Queue &q, const double y[6], double w_out, int id, int key,
-                                             const double *a = nullptr) {
+                                             const double *a = nullptr, bool ff = false) {
     const unsigned int act = __activemask();
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(act) - 1;
@@ -116,8 +176,7 @@ __device__ __forceinline__ void queue_append(const Queue &q, const double y[6], 
     if (lane == leader) base = atomicAdd(q.count, (unsigned int)__popc(act));
     base = __shfl_sync(act, base, leader);
     unsigned int slot = base + __popc(act & ((1u << lane) - 1u));
-    q.x[slot] = y[0]; q.y[slot] = y[1]; q.z[slot] = y[2];
-    q.vx[slot] = y[3]; q.vy[slot] = y[4]; q.vz[slot] = y[5];
+    put_state(ff, q, slot, y);
     q.ax[slot] = a ? a[0] : __longlong_as_double(0x7ff8000000000000ll);
     q.ay[slot] = a ? a[1] : 0.0;
     q.az[slot] = a ? a[2] : 0.0;
@@ -147,11 +206,11 @@ __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned lo
     }
     // Eq. 12 at the entry face along the physical direction: light leaves the cloak towards the camera
     double mk0[3] = {-k0[0], -k0[1], -k0[2]}, c[3] = {mat[2], mat[3], mat[4]};
-    double w_out = transmission_out(MODE, mat[0], mat[1], c, n_in, mk0, analyzer_axis(p));
+    double w_out = entry_factor(p, MODE, mat[0], mat[1], c, n_in, mk0, analyzer_axis(p));
     double dy[6];
     const bool first = p.precision == 0 && p.formulation == 0;  // the FP64 Fermat stepper's first stage
     if (first) rhs<VAR, MODE>(p, y, dy);
-    queue_append(q, y, w_out, (int)idx, cost_bucket(y, k0), first ? dy + 3 : nullptr);
+    queue_append(q, y, w_out, (int)idx, cost_bucket(y, k0), first ? dy + 3 : nullptr, p.precision != 0);
 }
 
 // Longest-first order: a counting sort of the queue by descending key.  k_wf_sort_scan turns the bucket
@@ -162,7 +221,7 @@ __global__ void k_wf_sort_scan(Queue q, int nbins, unsigned int reserve);
 __global__ void k_wf_sort_scatter(Queue q);
 
 template <int VAR, int MODE, int INTEG, int PREC>
-__global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
+__device__ __forceinline__ void wf_integrate_body(const Params &p, const Queue &q) {
     typedef typename std::conditional<PREC == 0, Stepper64<VAR, MODE, INTEG>, StepperMixed<VAR, MODE, INTEG>>::type S;
     typedef typename S::real R;
     S st;
@@ -429,11 +488,8 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
                 }
             }
         }
-        if (status >= 0) {  // ray finished: write back, lane becomes idle
-            double y[6];
-            st.state(y);
-            q.x[slot] = y[0]; q.y[slot] = y[1]; q.z[slot] = y[2];
-            q.vx[slot] = y[3]; q.vy[slot] = y[4]; q.vz[slot] = y[5];
+        if (status >= 0) {  // ray finished: write back (in the queue's state format), lane becomes idle
+            st.store(q, slot);
             q.t[slot] = (double)t;
             q.status[slot] = status;
             q.steps[slot] = steps;
@@ -443,12 +499,30 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     }
 }
 
+// The FP64 integrator keeps the compiler's register choice (148-151 registers, three blocks of 128
+// threads per SM); the mixed one is held to 128 registers for four blocks per SM -- its FP32 steps are
+// latency-bound and gain from the extra warps, while the rare band steps near R1 may spill.
+template <int VAR, int MODE, int INTEG, int PREC>
+__global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
+    wf_integrate_body<VAR, MODE, INTEG, PREC>(p, q);
+}
+template <int VAR, int MODE, int INTEG, int PREC>
+__global__ void __launch_bounds__(128, 4) k_wf_integrate_mixed(Params p, Queue q) {
+    wf_integrate_body<VAR, MODE, INTEG, PREC>(p, q);
+}
+template <int VAR, int MODE, int INTEG, int PREC>
+constexpr auto wf_integrate_kernel() {
+    if constexpr (PREC == 0) return k_wf_integrate<VAR, MODE, INTEG, PREC>;
+    else return k_wf_integrate_mixed<VAR, MODE, INTEG, PREC>;
+}
+
 // Exit of queue slot k: refraction into vacuum at the crossed face, the Eq. 12 factor of the exit face
 // times the stored factor of the entry face, room lookup.  d_cam: the camera ray (kept as the
 // direction of rays that do not leave).
 __device__ __forceinline__ void exit_slot(const Params &p, int mode, const Queue &q, unsigned int k, const double d_cam[3],
                                           cloak_record &rec, float rgb[3]) {
-    double y[6] = {q.x[k], q.y[k], q.z[k], q.vx[k], q.vy[k], q.vz[k]};
+    double y[6];
+    get_state(p.precision != 0, q, k, y);
     int status = q.status[k];
     rec.mode = mode;
     rec.tile_id = -1;
@@ -475,7 +549,7 @@ __device__ __forceinline__ void exit_slot(const Params &p, int mode, const Queue
                 dout[a] = fma(qn, nrm[a], kt[a]);
                 mdout[a] = -dout[a];
             }
-            double tin = transmission_in(mode, eo, ee, c, nrm, mdout);
+            double tin = exit_factor(p, mode, eo, ee, c, nrm, mdout, qn);
             rec.weight = tin * q.w_out[k];
             rec.status = status;
             set_vec(rec.exit_dir, dout);
@@ -534,11 +608,12 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
     if (ev) cudaEventRecord(ev[1], st);
     // persistent integrator: exactly the resident grid
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wf_integrate<V, M, I, PREC>, pk, 0);
+    constexpr auto kern = wf_integrate_kernel<V, M, I, PREC>();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, pk, 0);
     if (e != cudaSuccess) return e;
     Params pl = p;
     pl.dedicated_blocks = LONG_RAY_BLOCKS;
-    k_wf_integrate<V, M, I, PREC><<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(pl, q);
+    kern<<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(pl, q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);

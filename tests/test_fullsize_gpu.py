@@ -13,10 +13,10 @@ every ray; on the undetermined rays the bar widens by 8 x D64, D64 being how far
 when its states are FP64 numbers.  The batched launch (all twelve views in one persistent kernel, the
 benchmark's timed call) renders the same images as the per-image launches whose records are compared.
 
-Mixed path (FP32 stepping, FP64 band): exit directions within 1e-5 on every ray whose D32 (the distance a
-model of FP32 right-hand sides moves it, tests/golden/fp32_sensitive_rays.txt) is at most 1e-7; the listed
-rays within max(1e-5, 40 D32) capped at 1e-4; >= 99.9 % of the sampled pixels with the reference's tile and
-status in every sample.
+Mixed path (FP32 stepping, FP64 or double-float band): exit direction within min(1e-4, max(1e-5, 40 D32))
+of the reference, D32 the distance a model of FP32 right-hand sides moves the ray (1e-5 unless
+tests/golden/fp32_sensitive_rays.txt lists the ray); >= 99.9 % of the sampled pixels with the reference's
+tile and status in every sample.
 """
 import os
 
@@ -31,7 +31,7 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 NPIX = 100000
 SEED = 12345
 TOL_DIR, TOL_ABS, D64_FACTOR = 1e-9, 1e-9, 8.0
-TOL_MIXED, D32_DETERMINED, D32_FACTOR, CAP = 1e-5, 1e-7, 40.0, 1e-4
+TOL_MIXED, D32_DETERMINED, D32_FACTOR, CAP = 1e-5, 2.5e-7, 40.0, 1e-4
 
 
 def angles(a, b):
@@ -166,7 +166,7 @@ def test_mixed_full_workload_against_the_oracle(ck, reference, band):
             got = d32.get((idx, int(s)))
             if got:
                 if got[0] > D32_DETERMINED:
-                    lim[k] = min(CAP, max(TOL_MIXED, D32_FACTOR * got[0]))
+                    lim[k] = min(CAP, D32_FACTOR * got[0])
                 flip[k] = got[1]
         same = g["status"] == ref["status"]
         bad = np.nonzero(~same & ~flip)[0]
