@@ -62,8 +62,10 @@ def _measured_peaks():
         return {}
 
 
-# dense BF16 tensor peak: measured on the GB300s (cuBLAS, burst), else the recipe's fallback
+# dense BF16 tensor peak: measured on the GB300s (cuBLAS, burst; sustained for a seconds-long
+# loop), else the recipe's fallback
 BF16_PEAK_TFLOPS = float(_measured_peaks().get("bf16_tflops", 1900.0))
+BF16_PEAK_SUSTAINED_TFLOPS = float(_measured_peaks().get("bf16_tflops_sustained", 1700.0))
 
 # Algorithmic FP64 flops per integrator step attempt, counted from the source formulas
 # (FMA = 2 flops, reciprocal and 1/sqrt = 1 flop each):
@@ -170,7 +172,7 @@ def reference_records(w, o, npix):
 
 
 def fp32_bars(w, npix):
-    """Per-ray exit-direction bars of the mixed path on the benchmark sample, min(1e-4, max(1e-5, 40 D32)) with D32
+    """Per-ray exit-direction bars of the mixed path on the benchmark sample, min(1e-4, max(1e-5, 100 D32)) with D32
     the distance an FP32 model of the oracle moves the ray, and the statuses FP32 does not fix."""
     import numpy as np
     n = len(w.images) * npix * w.spp
@@ -182,8 +184,8 @@ def fp32_bars(w, npix):
     for f in _golden_rows("fp32_sensitive_rays.txt"):
         k = pos[int(f[0])][int(f[1])]
         d32 = float(f[2])
-        if d32 > 2.5e-7:
-            lim[k] = min(1e-4, 40.0 * d32)
+        if d32 > 1e-7:
+            lim[k] = min(1e-4, 100.0 * d32)
         flip[k] = f[3] == "1"
     return lim, flip
 
@@ -246,8 +248,45 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
     ck.cloak_surrogate_train(trainer.h, sw.extra["train_rays"], sw.extra["train_seed"], args.sur_epochs)
     train_wall = time.perf_counter() - t0
     info = ck.cloak_surrogate_info(trainer.h)
+    tt = ck.cloak_surrogate_train_timing(trainer.h)
+    train_tflops = tt["flops_per_step_stage1"] / (tt["ms_per_step_stage1"] / 1e3) / 1e12
     path = os.path.join(tempfile.gettempdir(), f"cloak_surrogate_{os.getpid()}.bin")
     ck.cloak_surrogate_save(trainer.h, path)
+    # reproducibility: the same seed trains the same network (fixed-order gradient sums), bit for bit; other
+    # seeds give the run-to-run spread of what the network takes over
+    params0 = ck.cloak_surrogate_params(trainer.h)
+    rb_small = torch.empty(sw.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
+
+    def handled_fraction(net_path, stride=49):
+        """share of the entering rays (every stride-th sample of every view) the gate leaves to the network"""
+        ent = hnd = 0
+        for v, m, e in sw.images:
+            eye, tgt, up = inputs.camera_pose(e)
+            c = ck.Cloak(v).camera(eye, tgt, up, sw.hfov_deg, sw.width, sw.height)
+            c.integrator(integ, sw.h_or_tol, ck.SURROGATE, sw.max_steps).schedule(ck.SCHED_WAVEFRONT)
+            ck.cloak_surrogate_load(c.h, net_path)
+            ck.cloak_surrogate_set_gate(c.h, sw.extra["gate_log10_err"])
+            c.render_records(m, sw.spp, sw.seed, out=rb_small)
+            r = ck.records_to_numpy(rb_small.view(-1, ck.RECORD_BYTES)[::stride].contiguous().reshape(-1))
+            ent += int((r["status"] != 0).sum())
+            hnd += int(((r["steps"] == 0) & np.isin(r["status"], [1, 2])).sum())
+            c.close()
+        return hnd / max(1, ent)
+
+    shares = {"seed_0": handled_fraction(path)}
+    again = ck.Cloak(ck.RADIAL).integrator(integ, sw.h_or_tol, ck.FP64, sw.max_steps)
+    ck.cloak_surrogate_train(again.h, sw.extra["train_rays"], sw.extra["train_seed"], args.sur_epochs)
+    same_seed_identical = bool(np.array_equal(ck.cloak_surrogate_params(again.h), params0))
+    again.close()
+    for sd in (1, 2):
+        other = ck.Cloak(ck.RADIAL).integrator(integ, sw.h_or_tol, ck.FP64, sw.max_steps)
+        ck.cloak_surrogate_train(other.h, sw.extra["train_rays"], sd, args.sur_epochs)
+        op = os.path.join(tempfile.gettempdir(), f"cloak_surrogate_{os.getpid()}_{sd}.bin")
+        ck.cloak_surrogate_save(other.h, op)
+        other.close()
+        shares[f"seed_{sd}"] = handled_fraction(op)
+        os.remove(op)
+    del rb_small
     # forward pass of 2^22 rows on the tensor cores (one fused persistent launch)
     n = 1 << 22
     x = torch.rand((n, 7), device="cuda") * 2 - 1
@@ -355,7 +394,17 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
                                     "handled_exit_dir_err_rad": {"median": float(np.median(err)) if err.size else None,
                                                                  "p99": float(np.quantile(err, 0.99)) if err.size else None,
                                                                  "max": float(err.max()) if err.size else None}},
-            "training": {**{k: float(v) for k, v in info.items()}, "wall_s": train_wall, "epochs": args.sur_epochs},
+            "training": {**{k: float(v) for k, v in info.items()}, "wall_s": train_wall, "epochs": args.sur_epochs,
+                         "same_seed_bit_identical": same_seed_identical,
+                         "handled_frac_by_training_seed": shares,
+                         "roofline": {"bound": "tensor", "achieved": train_tflops, "peak": BF16_PEAK_SUSTAINED_TFLOPS,
+                                      "unit": "TFLOP/s", "frac": train_tflops / BF16_PEAK_SUSTAINED_TFLOPS,
+                                      "ms_per_step": tt["ms_per_step_stage1"], "batch": tt["batch"],
+                                      "flops_per_step": tt["flops_per_step_stage1"],
+                                      "peak_source": "measured cuBLAS bf16 GEMM, sustained (MEASURED_PEAKS.json)",
+                                      "note": "one stage-1 optimizer step: batch gather, forward, loss, backward "
+                                              "(data and weight GEMMs, fixed-order split-K sums) and Adam, replayed "
+                                              "as a CUDA graph; CUDA events around the stage"}},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) of measured",
                          "kernel": "k_mlp_fused (persistent tcgen05 BF16 network, FP32 accumulation in TMEM): "
@@ -367,8 +416,9 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
 def orbit_section(args, ck, inputs, torch, flush):
     """The seeded 64-pose orbit (both cloaks and polarizations per pose, resolutions drawn from
     256^2 ... 3840x2160, 1 spp, DP5(4) tol 1e-9 FP64) in ONE batched render: one persistent integration
-    kernel over every view, replayed as a CUDA graph.  The packet size comes from the autotuner, run on
-    the same orbit with a quarter of each image side."""
+    kernel over every view, replayed as a CUDA graph.  The schedule (packet size, long-ray blocks, rays
+    reserved per thread, cost-bucket resolution) comes from the autotuner, run on the same orbit with a
+    quarter of each image side; the full orbit is timed with the default schedule and with the tuned one."""
     from paper_1209_6038_gb300 import autotune
     views = inputs.batched_views(64, 0)
     w = inputs.FULL
@@ -377,28 +427,38 @@ def orbit_section(args, ck, inputs, torch, flush):
     c.schedule(ck.SCHED_WAVEFRONT).stage_timing(True)
     small = [(v, p, eye, tgt, up, fov, torch.empty((max(1, H // 4), max(1, W // 4), 4), device="cuda"))
              for (v, p, eye, tgt, up, fov, W, H) in views]
-    best, tune_ms = autotune.tune_packet(c, lambda: ck.cloak_render_batch(c.h, small, 1, 0), key="orbit64/4",
-                                         use_cache=False)
+    t0 = time.perf_counter()
+    best, tune_ms = autotune.tune_schedule(c, lambda: ck.cloak_render_batch(c.h, small, 1, 0), key="orbit64/4",
+                                           use_cache=False)
+    tune_s = time.perf_counter() - t0
     del small
     outs = [(v, p, eye, tgt, up, fov, torch.empty((H, W, 4), device="cuda"))
             for (v, p, eye, tgt, up, fov, W, H) in views]
     rays = sum(o[-1].shape[0] * o[-1].shape[1] for o in outs)
-    ck.cloak_render_batch(c.h, outs, 1, 0)  # capture + first replay
-    torch.cuda.synchronize()
-    flush.zero_()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    ck.cloak_render_batch(c.h, outs, 1, 0)
-    b.record()
-    b.synchronize()
-    ms = a.elapsed_time(b)
-    st = c.stage_times()
+
+    def timed_orbit(sched):
+        autotune.apply(c, sched)
+        ck.cloak_render_batch(c.h, outs, 1, 0)  # capture + first replay
+        torch.cuda.synchronize()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ck.cloak_render_batch(c.h, outs, 1, 0)
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b), c.stage_times()
+
+    ms_default, _ = timed_orbit(autotune.DEFAULT_SCHEDULE)
+    ms, st = timed_orbit(best)
     c.close()
     del outs
     return {"workload": "64 seeded orbit poses x 2 variants x 2 pols (256 views), resolutions from "
                         "{256x256, 1024x768, 1920x1080, 3840x2160}, 1 spp, DP45 tol=1e-9 FP64, one batched render",
             "views": len(views), "rays": rays, "value": rays / (ms / 1e3), "unit": "rays/s", "ms_per_step": ms,
-            "warmup": 1, "steps": 1, "packet": best, "autotune_ms": {str(k): v for k, v in tune_ms.items()},
+            "warmup": 1, "steps": 1, "schedule": best, "default_schedule": autotune.DEFAULT_SCHEDULE,
+            "ms_per_step_default_schedule": ms_default, "speedup_tuned_vs_default": ms_default / ms,
+            "autotune": {"search": "coordinate search on the orbit at a quarter of each image side",
+                         "seconds": tune_s, "ms": {str(k): v for k, v in tune_ms.items()}},
             "stage_ms": {"camera_entry_sort": st[0], "integrate": st[1], "exit_shade": st[2], "resolve": st[3]}}
 
 
@@ -834,7 +894,7 @@ def main():
                             "status_changes": int((gm["status"] != ref["status"]).sum()),
                             "status_changes_fp32_determined": int(((gm["status"] != ref["status"]) & ~flip32).sum()),
                             "pixels_tile_or_status_differs_frac": float(pxm.mean()),
-                            "bar": "min(1e-4, max(1e-5, 40 D32)), D32 the distance an FP32 model of the oracle moves the "
+                            "bar": "min(1e-4, max(1e-5, 100 D32)), D32 the distance an FP32 model of the oracle moves the "
                                    "ray (tests/golden/fp32_sensitive_rays.txt)"}}
         for c in rec_handles.values():
             c.close()

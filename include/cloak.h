@@ -138,6 +138,13 @@ int cloak_set_analyzer(cloak_t *h, int analyzer);
  * (32, 64, 96 or 128; 0 = default 128).  steps_per_round: reserved (0): lanes refill one by one from
  * the queue, there are no compaction rounds. */
 int cloak_set_schedule(cloak_t *h, int schedule, int packet, int steps_per_round);
+/* Step-schedule knobs of the wavefront and batched integration (the paper has no counterpart; images and
+ * records do not depend on them, only the time does): long_ray_blocks (0..64, default 4) blocks of the
+ * persistent kernel, each on an SM of its own, take the slowest rays first -- those passing closest to
+ * the axis; reserve_per_thread (1..8, default 1) rays are reserved for them per thread; cost_scale
+ * (1..16, default 4) sets the resolution of the sort's cost buckets, bucket = cost_scale x -log2 |L_z|
+ * (64 buckets).  CLOAK_EINVAL outside these ranges.  The autotuner (autotune.py) searches them. */
+int cloak_set_schedule_tuning(cloak_t *h, int long_ray_blocks, int reserve_per_thread, double cost_scale);
 
 /* Per-stage device timing (CUDA events on the call's stream).  on != 0 enables it for later calls.
  * cloak_stage_times waits for the last cloak_render / cloak_render_records call on this handle and
@@ -315,6 +322,12 @@ int cloak_surrogate_set_gate(cloak_t *h, double max_log10_err);
  * the training rays, rays, seconds in total, seconds tracing the training rays, optimiser steps, batch
  * size.  CLOAK_ESTATE without a trained surrogate. */
 int cloak_surrogate_info(cloak_t *h, double info[8]);
+/* Device timing of the last cloak_surrogate_train (host, 4 doubles): milliseconds per optimizer step of
+ * stage 1 (batch gather, forward, loss, backward and Adam over one batch, as the training replays it in a
+ * CUDA graph; CUDA events around the stage), the same for stage 2, the algorithmic tensor-core flops of a
+ * stage-1 step (2 x the multiply-adds of the forward, backward-data and weight-gradient GEMMs without
+ * padding), and the batch size.  CLOAK_ESTATE if the handle's surrogate was not trained here. */
+int cloak_surrogate_train_timing(cloak_t *h, double out[4]);
 /* Parameters as one flat FP32 host vector of n = 200709 values (per layer: W_l, out x in row-major,
  * then b_l).  set = 0 copies them into host; set = 1 loads host into the network and clears the Adam
  * state.  A handle without a surrogate gets one with seeded initial weights first. */

@@ -1,8 +1,12 @@
-"""Autotuner for the packet size (threads per block) of the persistent integration kernel.
+"""Autotuner of the integration schedule: the packet size (threads per block of the persistent kernel) and
+the step-schedule knobs of cloak_set_schedule_tuning -- how many blocks take the slowest rays first, how
+many rays they reserve per thread, and the resolution of the sort's cost buckets.  None of them changes a
+result, only the time.
 
-Each candidate is set on the handle (cloak_set_schedule), the caller's render function is run once to
-warm up (and, for batches, to capture the CUDA graph) and then timed with CUDA events; the fastest
-candidate is kept on the handle and cached per GPU and workload key in a JSON file next to this
+A coordinate search: starting from the handle's defaults, each knob in turn is set to each of its
+candidates, the caller's render function is run once to warm up (and, for batches, to capture the CUDA
+graph) and then timed with CUDA events; the fastest value is kept before the next knob is searched.  The
+chosen schedule is left on the handle and cached per GPU and workload key in a JSON file next to this
 module (_autotune.json, not versioned).
 """
 from __future__ import annotations
@@ -12,6 +16,9 @@ import os
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune.json")
 CANDIDATES = (32, 64, 96, 128)  # threads per block of the persistent kernel (at most 128)
+DEFAULT_SCHEDULE = {"packet": 128, "long_ray_blocks": 4, "reserve_per_thread": 1, "cost_scale": 4.0}
+SEARCH = (("packet", CANDIDATES), ("long_ray_blocks", (0, 2, 4, 8, 16)), ("cost_scale", (2.0, 3.0, 4.0, 6.0, 8.0)),
+          ("reserve_per_thread", (1, 2, 4)))
 
 
 def _load():
@@ -22,39 +29,73 @@ def _load():
         return {}
 
 
-def tune_packet(cloak, run, key: str, candidates=CANDIDATES, reps: int = 1, use_cache: bool = True):
-    """cloak: paper_1209_6038_gb300.cloak.Cloak (wavefront schedule); run(): one render on the current
-    stream.  Returns (best_packet, {packet: ms}).  The best packet is left set on the handle."""
-    import torch
-    from . import cloak as ck
-    gpu = torch.cuda.get_device_name()
-    full_key = f"{gpu}|{key}"
+def _store(full_key, entry):
     cache = _load()
-    if use_cache and full_key in cache:
-        best = int(cache[full_key]["packet"])
-        cloak.schedule(ck.SCHED_WAVEFRONT, best)
-        return best, cache[full_key]["ms"]
-    times = {}
-    for pk in candidates:
-        cloak.schedule(ck.SCHED_WAVEFRONT, pk)
-        run()
-        torch.cuda.synchronize()
-        ms = []
-        for _ in range(reps):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            run()
-            b.record()
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
-        times[pk] = min(ms)
-    best = min(times, key=times.get)
-    cloak.schedule(ck.SCHED_WAVEFRONT, best)
-    cache[full_key] = {"packet": best, "ms": {str(k): v for k, v in times.items()}}
+    cache[full_key] = entry
     try:
         with open(CACHE, "w") as f:
             json.dump(cache, f, indent=1)
     except OSError:
         pass
+
+
+def _time(run, reps):
+    import torch
+    run()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        run()
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return min(ms)
+
+
+def apply(cloak, sched: dict):
+    """Set a schedule (a dict with the keys of DEFAULT_SCHEDULE) on a wavefront handle."""
+    from . import cloak as ck
+    cloak.schedule(ck.SCHED_WAVEFRONT, int(sched["packet"]))
+    ck.cloak_set_schedule_tuning(cloak.h, int(sched["long_ray_blocks"]), int(sched["reserve_per_thread"]),
+                                 float(sched["cost_scale"]))
+
+
+def tune_schedule(cloak, run, key: str, reps: int = 1, use_cache: bool = True, search=SEARCH):
+    """cloak: paper_1209_6038_gb300.cloak.Cloak (wavefront schedule); run(): one render on the current
+    stream.  Returns (best schedule, {"knob=value": ms}).  The best schedule is left set on the handle."""
+    import torch
+    gpu = torch.cuda.get_device_name()
+    full_key = f"{gpu}|schedule|{key}"
+    if use_cache:
+        hit = _load().get(full_key)
+        if hit:
+            apply(cloak, hit["schedule"])
+            return hit["schedule"], hit["ms"]
+    best = dict(DEFAULT_SCHEDULE)
+    apply(cloak, best)
+    times = {"default": _time(run, reps)}
+    best_ms = times["default"]
+    for knob, values in search:
+        for v in values:
+            if v == best[knob]:
+                continue
+            trial = dict(best, **{knob: v})
+            apply(cloak, trial)
+            ms = _time(run, reps)
+            times[f"{knob}={v}"] = ms
+            if ms < best_ms:
+                best_ms, best = ms, trial
+        apply(cloak, best)
+    _store(full_key, {"schedule": best, "ms": times})
     return best, times
+
+
+def tune_packet(cloak, run, key: str, candidates=CANDIDATES, reps: int = 1, use_cache: bool = True):
+    """The packet size alone (the other knobs at their defaults).  Returns (best_packet, {packet: ms})."""
+    best, times = tune_schedule(cloak, run, f"packet|{key}", reps, use_cache, search=(("packet", candidates),))
+    ms = {int(k.split("=")[1]): v for k, v in times.items() if k.startswith("packet=")}
+    ms[DEFAULT_SCHEDULE["packet"]] = times["default"]
+    return best["packet"], ms

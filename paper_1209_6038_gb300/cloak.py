@@ -40,6 +40,7 @@ SIGNATURES = {
     "cloak_set_scene_seed": (C.c_int, [C.c_void_p, C.c_ulonglong]),
     "cloak_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "cloak_set_stage_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "cloak_set_schedule_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double]),
     "cloak_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     "cloak_render": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t, C.c_void_p]),
     "cloak_render_records": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.c_size_t,
@@ -63,6 +64,7 @@ SIGNATURES = {
     "cloak_surrogate_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "cloak_surrogate_set_gate": (C.c_int, [C.c_void_p, C.c_double]),
     "cloak_surrogate_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "cloak_surrogate_train_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "cloak_surrogate_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_long, C.c_int]),
     "cloak_surrogate_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
     "cloak_surrogate_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_long, C.c_int, C.c_double,
@@ -151,6 +153,10 @@ def cloak_set_scene_seed(h, seed):
 
 def cloak_set_schedule(h, schedule, packet=0, steps_per_round=0):
     return _check(load().cloak_set_schedule(h, schedule, packet, steps_per_round))
+
+
+def cloak_set_schedule_tuning(h, long_ray_blocks=4, reserve_per_thread=1, cost_scale=4.0):
+    return _check(load().cloak_set_schedule_tuning(h, long_ray_blocks, reserve_per_thread, cost_scale))
 
 
 def cloak_set_stage_timing(h, on):
@@ -282,6 +288,13 @@ def cloak_surrogate_info(h) -> dict:
     buf = (C.c_double * 8)()
     _check(load().cloak_surrogate_info(h, buf))
     return dict(zip(SUR_INFO_KEYS, list(buf)))
+
+
+def cloak_surrogate_train_timing(h) -> dict:
+    """Device timing of the last training: ms per stage-1 and stage-2 step, flops of a stage-1 step, batch."""
+    buf = (C.c_double * 4)()
+    _check(load().cloak_surrogate_train_timing(h, buf))
+    return dict(zip(("ms_per_step_stage1", "ms_per_step_stage2", "flops_per_step_stage1", "batch"), list(buf)))
 
 
 def cloak_surrogate_params(h, values=None) -> np.ndarray:

@@ -27,6 +27,8 @@ struct cloak {
     int precision;
     long max_steps;
     int schedule, packet, steps_per_round;
+    int long_ray_blocks, reserve_per_thread;  // schedule knobs (cloak_set_schedule_tuning)
+    double cost_scale;
     int analyzer;     // CLOAK_ANALYZER_*
     int formulation;  // CLOAK_FORM_*
     int device;
@@ -110,6 +112,9 @@ static int make_params(const cloak *h, ck::Params &p) {
     p.band_limf = p.mixed_band > 0.0 ? (float)(p.R1 + p.mixed_band) : 0.f;
     p.h_or_tol = h->h_or_tol;
     p.max_steps = h->max_steps;
+    p.long_ray_blocks = h->long_ray_blocks;
+    p.reserve_per_thread = h->reserve_per_thread;
+    p.cost_scale = (float)h->cost_scale;
     double w[3], u[3], v[3];
     for (int i = 0; i < 3; ++i) w[i] = h->target[i] - h->eye[i];
     double l = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
@@ -262,6 +267,9 @@ cloak_t *cloak_create(int variant, double R1, double R2, double height) {
     h->max_steps = 1000000;
     h->schedule = CLOAK_SCHED_PLAIN;
     h->packet = 0;
+    h->long_ray_blocks = ck::LONG_RAY_BLOCKS;
+    h->reserve_per_thread = 1;
+    h->cost_scale = 4.0;
     h->steps_per_round = 0;
     h->analyzer = CLOAK_ANALYZER_NONE;
     h->formulation = CLOAK_FORM_FERMAT;
@@ -427,6 +435,18 @@ int cloak_set_analyzer(cloak_t *h, int analyzer) {
 int cloak_set_scene_seed(cloak_t *h, unsigned long long seed) {
     if (!h) return fail(CLOAK_EINVAL, "null handle");
     h->scene_seed = seed;
+    return CLOAK_OK;
+}
+
+int cloak_set_schedule_tuning(cloak_t *h, int long_ray_blocks, int reserve_per_thread, double cost_scale) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (long_ray_blocks < 0 || long_ray_blocks > 64) return fail(CLOAK_EINVAL, "long_ray_blocks must be in [0, 64]");
+    if (reserve_per_thread < 1 || reserve_per_thread > 8)
+        return fail(CLOAK_EINVAL, "reserve_per_thread must be in [1, 8]");
+    if (!(cost_scale >= 1.0 && cost_scale <= 16.0)) return fail(CLOAK_EINVAL, "cost_scale must be in [1, 16]");
+    h->long_ray_blocks = long_ray_blocks;
+    h->reserve_per_thread = reserve_per_thread;
+    h->cost_scale = cost_scale;
     return CLOAK_OK;
 }
 
@@ -954,6 +974,21 @@ extern "C" int cloak_surrogate_set_gate(cloak_t *h, double max_log10_err) {
     if (!std::isfinite(max_log10_err)) return fail(CLOAK_EINVAL, "gate must be finite");
     if (!h->sur) return fail(CLOAK_ESTATE, "the handle has no surrogate");
     h->sur->gate = (float)max_log10_err;
+    return CLOAK_OK;
+}
+
+extern "C" int cloak_surrogate_train_timing(cloak_t *h, double out[4]) {
+    if (!h || !out) return fail(CLOAK_EINVAL, "null argument");
+    if (!h->sur || !h->sur->trained || !(h->sur->train_ms[0] > 0.0))
+        return fail(CLOAK_ESTATE, "the handle's surrogate was not trained by cloak_surrogate_train");
+    const double B = h->sur->info[7];
+    out[0] = h->sur->train_ms[0];
+    out[1] = h->sur->train_ms[1];
+    // algorithmic multiply-adds x 2 of a stage-1 step, unpadded: forward, backward data (layers 4..1) and
+    // weight gradients (all layers) of 7 -> 256 -> 256 -> 256 -> 256 -> 5
+    const double fwd = 7.0 * 256 + 3.0 * 256 * 256 + 256.0 * 5, bwd_data = 256.0 * 5 + 3.0 * 256 * 256;
+    out[2] = 2.0 * B * (2.0 * fwd + bwd_data);
+    out[3] = B;
     return CLOAK_OK;
 }
 

@@ -176,21 +176,45 @@ __device__ __forceinline__ void accel_f32(float R1, float R1sq_h, float R1sq_l, 
     }
 }
 
+// The right-hand sides of the mixed stepper are out of line: a DP5(4) step evaluates seven of them, and
+// with the double-float band and the four media of a batch inlined the kernel's code overflowed the
+// instruction caches (ncu: "no instruction" was three quarters of the warps' stall cycles).
+struct f3 {
+    float x, y, z;
+};
+template <int VAR, int MODE>
+__device__ __noinline__ f3 accel_f32_call(float R1, float R1sq_h, float R1sq_l, float K, float invK, float xh, float xl,
+                                          float yh, float yl, float vx, float vy, float vz, int vm) {
+    f3 a;
+    accel_f32<VAR, MODE>(R1, R1sq_h, R1sq_l, K, invK, xh, xl, yh, yl, vx, vy, vz, a.x, a.y, a.z, vm);
+    return a;
+}
 template <int VAR, int MODE>
 __device__ __forceinline__ void rhs_f32(const Params &p, const float t[6], const float tl[2], float d[6], int vm) {
     d[0] = t[3]; d[1] = t[4]; d[2] = t[5];
-    accel_f32<VAR, MODE>(p.R1f, p.R1sq_hf, p.R1sq_lf, p.Kf, p.invKf, t[0], tl[0], t[1], tl[1], t[3], t[4],
-                         t[5], d[3], d[4], d[5], vm);
+    const f3 a = accel_f32_call<VAR, MODE>(p.R1f, p.R1sq_hf, p.R1sq_lf, p.Kf, p.invKf, t[0], tl[0], t[1], tl[1],
+                                           t[3], t[4], t[5], vm);
+    d[3] = a.x; d[4] = a.y; d[5] = a.z;
 }
 
 
 // ------------------------------------------------------------------ double-float steps (the band near R1)
 // The same right-hand side and the same Dormand-Prince / RK4 updates as the FP64 path, in double-float.
+struct df3 {
+    df x, y, z;
+};
+template <int VAR, int MODE>
+__device__ __noinline__ df3 accel_df_call(df R1, df x, df y, df vx, df vy, df vz, int vm) {
+    const df unused;  // K and 1/K: the simplified accelerations of accel_fixed do not read them
+    df3 a;
+    accel<VAR, MODE, df>(R1, unused, unused, x, y, vx, vy, vz, a.x, a.y, a.z, vm);
+    return a;
+}
 template <int VAR, int MODE>
 __device__ __forceinline__ void rhs_df(df R1, const df y[6], df d[6], int vm) {
     d[0] = y[3]; d[1] = y[4]; d[2] = y[5];
-    const df unused;  // K and 1/K: the simplified accelerations of accel_fixed do not read them
-    accel<VAR, MODE, df>(R1, unused, unused, y[0], y[1], y[3], y[4], y[5], d[3], d[4], d[5], vm);
+    const df3 a = accel_df_call<VAR, MODE>(R1, y[0], y[1], y[3], y[4], y[5], vm);
+    d[3] = a.x; d[4] = a.y; d[5] = a.z;
 }
 template <int VAR, int MODE>
 __device__ __forceinline__ void dp45_step_df(df R1, const df y[6], const df k1[6], df h, df out[6], df err[6],
@@ -262,6 +286,31 @@ __device__ __forceinline__ void rk4_step_df(df R1, const df y[6], df h, df out[6
     for (int i = 0; i < 6; ++i) out[i] = df_fma(h6, acc[i] + k[i], y[i]);
 }
 
+// The band's steps near R1 (FP64 or double-float), out of line: rare, large, and kept out of the
+// instruction stream of the FP32 steps.  Inputs and outputs pass through the caller's local memory.
+template <int VAR, int MODE, int INTEG>
+__device__ __noinline__ void band_step_f64(const Params &p, const double *y, double s, double *yo, double *e,
+                                           double *k7, int vm) {
+    if (INTEG == I_RK4) {
+        rk4_step<VAR, MODE>(p, y, s, yo, vm);
+    } else {
+        double k1[6];
+        rhs<VAR, MODE>(p, y, k1, vm);
+        dp45_step<VAR, MODE>(p, y, k1, s, yo, e, k7, vm);
+    }
+}
+template <int VAR, int MODE, int INTEG>
+__device__ __noinline__ void band_step_df(float R1h, float R1l, const df *y, float s, df *yo, df *e, df *k7, int vm) {
+    const df R1(R1h, R1l), hs(s, 0.f);
+    if (INTEG == I_RK4) {
+        rk4_step_df<VAR, MODE>(R1, y, hs, yo, vm);
+    } else {
+        df k1[6];
+        rhs_df<VAR, MODE>(R1, y, k1, vm);
+        dp45_step_df<VAR, MODE>(R1, y, k1, hs, yo, e, k7, vm);
+    }
+}
+
 template <int VAR, int MODE, int INTEG>
 struct StepperMixed {
     typedef float real;
@@ -305,16 +354,12 @@ struct StepperMixed {
     }
     __device__ __forceinline__ void eval(const Params &p, float s) {
         if (p.band_df && island(p)) {  // double-float step from the float-float state
-            df y[6], yo[6];
+            df y[6], yo[6], e[6], kk7[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) y[i] = df(yh[i], yl[i]);
-            const df R1(p.R1), hs(s, 0.f);
-            if (INTEG == I_RK4) {
-                rk4_step_df<VAR, MODE>(R1, y, hs, yo, vm);
-            } else {
-                df kk1[6], e[6], kk7[6];
-                rhs_df<VAR, MODE>(R1, y, kk1, vm);
-                dp45_step_df<VAR, MODE>(R1, y, kk1, hs, yo, e, kk7, vm);
+            const df R1(p.R1);
+            band_step_df<VAR, MODE, INTEG>(R1.hi, R1.lo, y, s, yo, e, kk7, vm);
+            if (INTEG == I_DP45) {
 #pragma unroll
                 for (int i = 0; i < 6; ++i) { e6[i] = e[i].hi + e[i].lo; k7[i] = kk7[i].hi; n6[i] = 0.f; }
             }
@@ -324,15 +369,10 @@ struct StepperMixed {
             return;
         }
         if (island(p)) {  // FP64 step from the float-float state
-            double y[6], yo[6], e[6], kk1[6], kk7[6];
+            double y[6], yo[6], e[6], kk7[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) y[i] = (double)yh[i] + (double)yl[i];
-            if (INTEG == I_RK4) {
-                rk4_step<VAR, MODE>(p, y, (double)s, yo, vm);
-            } else {
-                rhs<VAR, MODE>(p, y, kk1, vm);
-                dp45_step<VAR, MODE>(p, y, kk1, (double)s, yo, e, kk7, vm);
-            }
+            band_step_f64<VAR, MODE, INTEG>(p, y, (double)s, yo, e, kk7, vm);
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 y1h[i] = (float)yo[i];

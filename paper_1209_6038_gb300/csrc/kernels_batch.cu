@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(128) k_batch_entry(Params p, const ViewDev *vi
     double dy[6];
     const bool first = p.precision == 0 && p.formulation == 0;  // the FP64 Fermat stepper's first stage
     if (first) rhs<V_ANY, V_ANY>(pv, y, dy, vw.vm);
-    queue_append(q, y, w_out, (int)g, batch_key(vw.vm, cost_bucket(y, k0)), first ? dy + 3 : nullptr,
+    queue_append(q, y, w_out, (int)g, batch_key(vw.vm, cost_bucket(p, y, k0)), first ? dy + 3 : nullptr,
                  p.precision != 0);
 }
 
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(128) k_refl_spawn(Params p, Queue q, Queue q2)
             const double y[6] = {x[0], x[1], x[2], p.formulation ? k2[0] : v2[0], p.formulation ? k2[1] : v2[1],
                                  p.formulation ? k2[2] : v2[2]};
             queue_append(q2, y, q.w_out[k] * R[m2], 2 * q.id[k] + m2,
-                         batch_key(2 * pv.variant + m2, cost_bucket(y, k2)), nullptr, p.precision != 0);
+                         batch_key(2 * pv.variant + m2, cost_bucket(p, y, k2)), nullptr, p.precision != 0);
         }
     }
 }
@@ -271,14 +271,14 @@ static cudaError_t batch_ip(const Params &p, const ViewDev *views, int nviews, i
     int pk = packet > 0 ? packet : 128;
     // the slowest rays of the batch go to the warps of LONG_RAY_BLOCKS blocks that have their SMs to
     // themselves (k_wf_integrate)
-    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH, (unsigned int)(LONG_RAY_BLOCKS * pk));
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS_BATCH, (unsigned int)(p.long_ray_blocks * pk * p.reserve_per_thread));
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
     mark(ev, 1, st);
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wf_integrate_kernel<V_ANY, V_ANY, I, PREC>(), pk, 0);
     if (e != cudaSuccess) return e;
     Params pl = p;
-    pl.dedicated_blocks = LONG_RAY_BLOCKS;
+    pl.dedicated_blocks = p.long_ray_blocks;
     wf_integrate_kernel<V_ANY, V_ANY, I, PREC>()<<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(pl, q);
     mark(ev, 2, st);
     k_batch_exit<<<sms * 16, 128, 0, st>>>(p, views, nviews, spp, seed, q, samples);
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(128) k_sur_gen_entry(Params p, long long n, un
     const bool inside = mode ? enter<M_EXT>(pv, o, d, rec, rgb, y, k0, n_in, mat)
                              : enter<M_ORD>(pv, o, d, rec, rgb, y, k0, n_in, mat);
     if (!inside) return;
-    queue_append(q, y, 1.0, (int)i, batch_key(2 * variant + mode, cost_bucket(y, k0)), nullptr, p.precision != 0);
+    queue_append(q, y, 1.0, (int)i, batch_key(2 * variant + mode, cost_bucket(p, y, k0)), nullptr, p.precision != 0);
 }
 
 __global__ void __launch_bounds__(128) k_sur_gen_exit(Params p, unsigned long long seed, Queue q, float *T_all) {

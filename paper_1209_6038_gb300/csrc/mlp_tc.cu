@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
             for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
             if (row < g.M) {
                 if (g.epi == EPI_STORE || g.epi == EPI_ATOMIC) {
-                    float4 *dst = (float4 *)(g.C + (size_t)row * g.ldc + c);
+                    float4 *dst = (float4 *)(g.C + (size_t)blockIdx.y * (size_t)g.slice_stride + (size_t)row * g.ldc + c);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         float4 q = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);

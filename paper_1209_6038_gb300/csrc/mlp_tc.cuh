@@ -45,6 +45,8 @@ struct GemmArgs {
     int epi;
     unsigned int *err;           // error flag (0 = ok)
     unsigned int wait_limit;     // polls of the waits that decide a timeout (MBAR_DEFAULT_LIMIT)
+    long long slice_stride;      // EPI_STORE with ksplit > 1: slice y of K writes its partial product to
+                                 // C + y * slice_stride (summed afterwards in a fixed order), 0 otherwise
 };
 
 constexpr int GEMM_TILE_M = 128;

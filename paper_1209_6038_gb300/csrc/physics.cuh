@@ -68,6 +68,10 @@ struct Params {
     float R1f, R2f, halfHf, Kf, invKf, R1sq_hf, R1sq_lf, band_limf;
     float R2sq_hf, R2sq_lf, halfH_hf, halfH_lf;
     int dedicated_blocks;  // batched integration: blocks whose warps take the reserved long rays
+    // schedule knobs (results do not depend on them): blocks for the slowest rays, rays reserved for them
+    // per thread, resolution of the cost buckets (bucket = cost_scale x -log2 |L_z|)
+    int long_ray_blocks, reserve_per_thread;
+    float cost_scale;
     double h_or_tol;
     long long max_steps;
     // camera

@@ -8,6 +8,7 @@
 //            dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})                (fused into the GEMM epilogue)
 //            db_l = column sums of dZ_l                            (k_sur_rowsum on the transposed copy)
 //   update   Adam on the FP32 masters, then their BF16 copies W_l and W_l^T (k_sur_adam)
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -119,6 +120,16 @@ __global__ void k_sur_loss(const float *Y, const float *Tb, int B, int stage, __
 }
 
 // out[r] = sum over the columns of row r of a BF16 matrix (bias gradients from a transposed dZ)
+// out[i] = sum over the slices s = 0, 1, ... of part[s * n + i], in that order: the weight gradients of the
+// batch-split GEMMs, summed the same way on every run (atomic accumulation made training order-dependent)
+__global__ void k_sum_slices(const float *part, int slices, long long n, float *out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int k = 0; k < slices; ++k) acc += part[(size_t)k * n + i];
+        out[i] = acc;
+    }
+}
+
 __global__ void k_sur_rowsum(const __nv_bfloat16 *M, int cols, float *out) {
     const __nv_bfloat16 *row = M + (size_t)blockIdx.x * cols;
     float s = 0.f;
@@ -361,16 +372,24 @@ struct TrainWS {
     float *Tb, *Z[4], *Y;
     double *loss;
     SurSched *sched;
+    float *partials;  // per-slice partial weight gradients (k_sum_slices)
     CUtensorMap tXb, tXTb, tH[4], tHT[4], tdY, tdYT, tdZ[2], tdZT[2];
 };
 
+static int ksplit_for(int B, int mtiles);
 static cudaError_t ws_create(TrainWS &w, int B) {
     memset(&w, 0, sizeof(w));
     w.B = B;
+    size_t part = 0;  // the largest per-slice partial gradients of a layer
+    for (int l = 0; l < SUR_L; ++l) {
+        const SurDims d = sur_dims(l);
+        part = std::max(part, (size_t)ksplit_for(B, d.mw / GEMM_TILE_M) * d.mw * d.kin * 4);
+    }
+    part = align256(part);
     const size_t x = align256((size_t)B * 64 * 2), z = align256((size_t)B * SUR_W * 4),
                  h = align256((size_t)B * SUR_W * 2), t = align256((size_t)B * SUR_TSTRIDE * 4),
                  y = align256((size_t)B * 16 * 4), dyt = align256((size_t)128 * B * 2);
-    const size_t bytes = 2 * x + t + 4 * z + 8 * h + y + x + dyt + 4 * h + 512;
+    const size_t bytes = 2 * x + t + 4 * z + 8 * h + y + x + dyt + 4 * h + 512 + part;
     cudaError_t e = cudaMalloc(&w.arena, bytes);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemset(w.arena, 0, bytes)) != cudaSuccess) return e;
@@ -388,6 +407,7 @@ static cudaError_t ws_create(TrainWS &w, int B) {
     for (int j = 0; j < 2; ++j) { w.dZT[j] = (__nv_bfloat16 *)p; p += h; }
     w.loss = (double *)p;
     w.sched = (SurSched *)(p + 256);
+    w.partials = (float *)(p + 512);
     bool ok = tmap(&w.tXb, w.Xb, B, 64, GEMM_TILE_M) && tmap(&w.tXTb, w.XTb, 64, B, 64) &&
               tmap(&w.tdY, w.dY, B, 64, GEMM_TILE_M) && tmap(&w.tdYT, w.dYT, 128, B, GEMM_TILE_M);
     for (int l = 0; l < 4; ++l)
@@ -432,6 +452,22 @@ static cudaError_t train_forward(SurNet *s, TrainWS &w, cudaStream_t st) {
     return e;
 }
 
+// dW = dZ^T H over the batch: the batch is split into K slices (about one CTA per SM), each slice stores
+// its partial product, and the slices are summed in a fixed order
+static cudaError_t weight_grad(SurNet *s, TrainWS &w, const SurDims &d, const CUtensorMap &tdz, const CUtensorMap &th,
+                               float *gW, cudaStream_t st) {
+    GemmArgs g = gemm_args(d.mw, d.in, w.B, EPI_STORE, s->err);
+    g.ksplit = ksplit_for(w.B, d.mw / GEMM_TILE_M);
+    g.C = w.partials;
+    g.ldc = d.kin;
+    g.slice_stride = (long long)d.mw * d.kin;
+    cudaError_t e = gemm(tdz, th, g, st);
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)d.mw * d.kin;
+    k_sum_slices<<<(unsigned)std::min<long long>((n + 255) / 256, 1184), 256, 0, st>>>(w.partials, g.ksplit, n, gW);
+    return cudaGetLastError();
+}
+
 // gradients of the loss of the batch in w (after train_forward and k_sur_loss); layers >= first only
 static cudaError_t train_backward(SurNet *s, TrainWS &w, int first, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(s->grad_begin, 0, s->grad_bytes, st);
@@ -439,10 +475,7 @@ static cudaError_t train_backward(SurNet *s, TrainWS &w, int first, cudaStream_t
     // output layer
     {
         SurDims d = sur_dims(SUR_L - 1);
-        GemmArgs g = gemm_args(d.mw, d.in, B, EPI_ATOMIC, s->err);
-        g.ksplit = ksplit_for(B, d.mw / GEMM_TILE_M);
-        g.C = s->gW[SUR_L - 1]; g.ldc = d.kin;
-        if (e == cudaSuccess) e = gemm(w.tdYT, w.tHT[SUR_L - 2], g, st);
+        if (e == cudaSuccess) e = weight_grad(s, w, d, w.tdYT, w.tHT[SUR_L - 2], s->gW[SUR_L - 1], st);
         k_sur_rowsum<<<d.out, 256, 0, st>>>(w.dYT, B, s->gb[SUR_L - 1]);
     }
     int cur = 0;
@@ -458,10 +491,7 @@ static cudaError_t train_backward(SurNet *s, TrainWS &w, int first, cudaStream_t
         if (e != cudaSuccess) break;
         // dW_{l-1} = dZ_{l-1}^T H_{l-2}, db_{l-1} = column sums of dZ_{l-1}
         const CUtensorMap &tb = l - 1 == 0 ? w.tXTb : w.tHT[l - 2];
-        GemmArgs gw = gemm_args(dp.mw, dp.kin, B, EPI_ATOMIC, s->err);
-        gw.ksplit = ksplit_for(B, dp.mw / GEMM_TILE_M);
-        gw.C = s->gW[l - 1]; gw.ldc = dp.kin;
-        e = gemm(w.tdZT[cur], tb, gw, st);
+        e = weight_grad(s, w, dp, w.tdZT[cur], tb, s->gW[l - 1], st);
         k_sur_rowsum<<<dp.out, 256, 0, st>>>(w.dZT[cur], B, s->gb[l - 1]);
         cur ^= 1;
     }
@@ -726,7 +756,12 @@ int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, 
     const long long total1 = steps_per_epoch * std::max(epochs, 1);
     double loss1 = 0.0, loss2 = 0.0, acc = 0.0;
     if (e == cudaSuccess) e = sched_init(w, 0, total1, 2e-3f, 0.02f, 200, st);
+    // device time of the optimizer steps of each stage (CUDA events around the replayed step graphs)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
     if (e == cudaSuccess) e = run_steps(s, w, 1, total1, steps_per_epoch, X_all, T_all, n, seed ^ 0x7261696eull, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess) e = d2h(&acc, w.loss, 8, st);
     loss1 = acc / (double)std::min(steps_per_epoch, total1);
     // 3. confidence targets: the exit error of the trained regression on every training ray
@@ -745,7 +780,15 @@ int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, 
     }
     const long long total2 = steps_per_epoch * std::max(1, epochs / 3);
     if (e == cudaSuccess) e = sched_init(w, 0, total2, 1e-3f, 0.f, 1, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
     if (e == cudaSuccess) e = run_steps(s, w, 2, total2, steps_per_epoch, X_all, T_all, n, seed ^ 0x636f6e66ull, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    float ms1 = 0.f, ms2 = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms1, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms2, ev[2], ev[3]);
+    for (int i = 0; i < 4; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
     acc = 0.0;
     if (e == cudaSuccess) e = d2h(&acc, w.loss, 8, st);
     loss2 = acc / (double)std::min(steps_per_epoch, total2);
@@ -767,6 +810,8 @@ int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, 
     s->info[5] = std::chrono::duration<double>(t1 - t0).count();
     s->info[6] = (double)(total1 + total2);
     s->info[7] = (double)B;
+    s->train_ms[0] = total1 > 0 ? ms1 / (double)total1 : 0.0;
+    s->train_ms[1] = total2 > 0 ? ms2 / (double)total2 : 0.0;
     return CLOAK_OK;
 }
 

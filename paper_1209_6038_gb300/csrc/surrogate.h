@@ -68,6 +68,7 @@ struct SurNet {
     float gate;           // inference: rays whose predicted log10 error exceeds this are integrated
     int trained;
     double info[8];       // final stage-1 loss, final stage-2 loss, lateral fraction, rays, seconds, ...
+    double train_ms[2];   // device time per optimizer step of stage 1 and stage 2 of the last training
     unsigned int *err;    // device GEMM error flag
     // inference scratch: inputs, outputs and gate flags for inf_rows rows (a multiple of 128); the
     // hidden activations never leave the SM (mlp_fused.cu)

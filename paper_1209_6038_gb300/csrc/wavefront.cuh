@@ -55,7 +55,7 @@ constexpr size_t QUEUE_HEADER_BYTES = 4096;
 // count[8]: medium segment of the reserved long rays, count[9]: their number, count[10]: their cursor;
 // from count[DEDICATED_FLAGS]: one flag per SM id (mod 256) that hosts a long-ray block
 constexpr int DEDICATED_FLAGS = 576;
-constexpr int LONG_RAY_BLOCKS = 4;  // blocks (SMs) for the long rays of a batch
+constexpr int LONG_RAY_BLOCKS = 4;  // default number of blocks (SMs) for the long rays
 static_assert((DEDICATED_FLAGS + 256) * 4 <= (int)QUEUE_HEADER_BYTES, "queue header too small");
 static_assert(DEDICATED_FLAGS * 4 >= 64 + 4 * (SEG_OFFSET + 8), "long-ray flags overlap the bins");
 // every array of the queue starts on a 256-byte boundary (the float4 per-sample buffer needs 16 bytes)
@@ -82,9 +82,9 @@ inline void carve_queue(char *base, long long cap, Queue &q, float4 **samples) {
 
 // Cost bucket of an entering ray from its axial angular momentum L = (x cross k)_z: rays that pass
 // close to the inner radius (small |L|) are the slow ones (the ray speed grows like 1/L there).
-__device__ __forceinline__ int cost_bucket(const double x[3], const double k[3]) {
+__device__ __forceinline__ int cost_bucket(const Params &p, const double x[3], const double k[3]) {
     float L = fabsf((float)(x[0] * k[1] - x[1] * k[0]));
-    int b = (int)(-4.0f * __log2f(L + 1e-30f));
+    int b = (int)(-p.cost_scale * __log2f(L + 1e-30f));
     return min(max(b, 0), NBINS - 1);
 }
 
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(128) k_wf_entry(Params p, int spp, unsigned lo
     double dy[6];
     const bool first = p.precision == 0 && p.formulation == 0;  // the FP64 Fermat stepper's first stage
     if (first) rhs<VAR, MODE>(p, y, dy);
-    queue_append(q, y, w_out, (int)idx, cost_bucket(y, k0), first ? dy + 3 : nullptr, p.precision != 0);
+    queue_append(q, y, w_out, (int)idx, cost_bucket(p, y, k0), first ? dy + 3 : nullptr, p.precision != 0);
 }
 
 // Longest-first order: a counting sort of the queue by descending key.  k_wf_sort_scan turns the bucket
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(128) k_wf_integrate(Params p, Queue q) {
     wf_integrate_body<VAR, MODE, INTEG, PREC>(p, q);
 }
 template <int VAR, int MODE, int INTEG, int PREC>
-__global__ void __launch_bounds__(128, 4) k_wf_integrate_mixed(Params p, Queue q) {
+__global__ void __launch_bounds__(128, 4) k_wf_integrate_mixed(const __grid_constant__ Params p, Queue q) {
     wf_integrate_body<VAR, MODE, INTEG, PREC>(p, q);
 }
 template <int VAR, int MODE, int INTEG, int PREC>
@@ -601,7 +601,7 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int pk = packet > 0 ? packet : 128;
     // the slowest rays go to the warps of LONG_RAY_BLOCKS blocks that have their SMs to themselves
-    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS, (unsigned int)(LONG_RAY_BLOCKS * pk));
+    k_wf_sort_scan<<<1, 32, 0, st>>>(q, NBINS, (unsigned int)(p.long_ray_blocks * pk * p.reserve_per_thread));
     k_wf_sort_scatter<<<sms * 8, 256, 0, st>>>(q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -612,7 +612,7 @@ static cudaError_t wavefront_vmip(const Params &p, int spp, unsigned long long s
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, pk, 0);
     if (e != cudaSuccess) return e;
     Params pl = p;
-    pl.dedicated_blocks = LONG_RAY_BLOCKS;
+    pl.dedicated_blocks = p.long_ray_blocks;
     kern<<<(nb > 0 ? nb : 1) * sms, pk, 0, st>>>(pl, q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -5,7 +5,7 @@ Calls only oracle/ (and the seeded input layout of the package's inputs module).
 Every sampled ray is traced by the oracle in long double twice: exactly, and as a model of the mixed path's
 FP32 arithmetic (right-hand sides of Eq. 2 / Eq. 8 and stage velocities rounded to FP32 outside the band
 r < R1 + 0.02, FP64 stage points inside it).  D32 is the exit-direction distance between the two runs; the
-file lists the rays with D32 > 2.5e-7 rad (40 D32 above the 1e-5 bar), or whose status the model changes.
+file lists the rays with D32 > 1e-7 rad (100 D32 above the 1e-5 bar), or whose status the model changes.
 
   python tests/golden/make_fp32_sensitive_rays.py [--pixels 100000]
 """
@@ -21,7 +21,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fp32_sensitive_rays.txt")
 SAMPLE_SEED = 12345
-LISTED = 2.5e-7  # 40 x D32 above the 1e-5 bar: the rays whose bar widens
+LISTED = 1e-7  # 100 x D32 above the 1e-5 bar: the rays whose bar widens
 
 
 def _angle(a, b):

@@ -6,12 +6,13 @@ A ray is undetermined when the oracle in FP64 and in long double disagree: statu
 exit point, time of flight or weight by more than 1e-10 (FP64 rounding moves the oracle's result there;
 near r = R1 the literal Cartesian form of Eq. 8 loses digits to cancellation).  For those rays the file
 holds the binary128 result at the case's own step or tolerance (status, step attempts, exit direction,
-exit point, time of flight, weight, tile) and D64: the exit-direction distance between that run and the
-same run with every state and stage point rounded to FP64, how far FP64 states alone move the ray.
+exit point, time of flight, weight, tile) and D64 per field (exit direction, exit point, time of flight,
+weight): the distance between that run and the same run with every state and stage point rounded to
+FP64, how far FP64 states alone move the ray.
 
 For the cases of the mixed-precision path it also writes <case>.f32.txt: the rays that a model of FP32
 arithmetic (long double with FP32 right-hand sides and stage velocities outside the band r < R1 + 0.02)
-moves by D32 > 2.5e-7 rad (40 D32 above the 1e-5 bar), or whose status it changes.
+moves by D32 > 1e-7 rad (100 D32 above the 1e-5 bar), or whose status it changes.
 
   python tests/golden/make_parity_references.py [--procs 8] [--only NAME ...]
 """
@@ -29,7 +30,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 OUT_DIR = os.path.join(HERE, "parity")
 THRESH = 1e-10
-F32_LISTED = 2.5e-7  # D32 above which the 1e-5 bar widens (40 x D32 > 1e-5): listed
+F32_LISTED = 1e-7  # D32 above which the 1e-5 bar widens (100 x D32 > 1e-5): listed
 
 
 def _setup():
@@ -116,13 +117,16 @@ def main(argv=None) -> int:
                     "# oracle (FP64 vs long double > 1e-10), with the oracle in binary128 at the case's own step or\n"
                     "# tolerance.  Written by tests/golden/make_parity_references.py (oracle only).\n"
                     "# Columns: ray index, status, step attempts, exit direction (3), exit point (3), time of flight,\n"
-                    "# weight, tile id, D64 (exit-direction change when states are FP64 numbers, rad).\n")
+                    "# weight, tile id; D64 of the exit direction (rad), exit point, time of flight and weight (their\n"
+                    "# change when states are FP64 numbers).\n")
             for k in idx:
                 q, qs = res[(name, int(k))]
                 vals = [int(k), int(q["status"]), int(q["steps"])]
                 vals += [f"{x:.17g}" for x in q["exit_dir"]] + [f"{x:.17g}" for x in q["exit_pos"]]
                 vals += [f"{q['tof']:.17g}", f"{q['weight']:.17g}", int(q["tile_id"])]
-                vals += [f"{float(angles(q['exit_dir'], qs['exit_dir'])):.3e}"]
+                vals += [f"{float(angles(q['exit_dir'], qs['exit_dir'])):.3e}",
+                         f"{float(np.abs(q['exit_pos'] - qs['exit_pos']).max()):.3e}",
+                         f"{abs(float(q['tof'] - qs['tof'])):.3e}", f"{abs(float(q['weight'] - qs['weight'])):.3e}"]
                 f.write(" ".join(str(x) for x in vals) + "\n")
         if name in f32:
             d32, flip = f32[name]

@@ -86,6 +86,46 @@ def test_autotuner_picks_a_candidate(ck, tmp_path, monkeypatch):
     c.close()
 
 
+def test_schedule_knobs_change_no_result(ck, tmp_path, monkeypatch):
+    """The step-schedule knobs (long-ray blocks, rays reserved per thread, cost-bucket resolution) reorder
+    the work only: batched images and wavefront records are identical under every setting; the schedule
+    autotuner leaves one of its candidates on the handle and caches it."""
+    import torch
+    from paper_1209_6038_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "cache.json"))
+    views = []
+    for v, m, e in ((0, 1, 0.0), (1, 1, 20.0), (1, 0, 45.0)):
+        eye, tgt, up = inputs.camera_pose(e)
+        views.append((v, m, eye, tgt, up, 60.0, torch.empty((72, 128, 4), device="cuda")))
+    b = ck.Cloak(ck.RADIAL).integrator(ck.DP45, 1e-9, ck.FP64).schedule(ck.SCHED_WAVEFRONT)
+    eye, tgt, up = inputs.camera_pose(20.0)
+    c = ck.Cloak(1).camera(eye, tgt, up, 60.0, 128, 72).integrator(ck.DP45, 1e-9).schedule(ck.SCHED_WAVEFRONT)
+    ref_img, ref_rec = None, None
+    for knobs in ((4, 1, 4.0), (0, 1, 2.0), (16, 4, 8.0), (2, 2, 1.0)):
+        ck.cloak_set_schedule_tuning(b.h, *knobs)
+        ck.cloak_set_schedule_tuning(c.h, *knobs)
+        ck.cloak_render_batch(b.h, views, 2, 3)
+        rec = ck.records_to_numpy(c.render_records(1, 2, 3))
+        torch.cuda.synchronize()
+        img = torch.stack([v[-1] for v in views]).clone()
+        if ref_img is None:
+            ref_img, ref_rec = img, rec
+        else:
+            assert torch.equal(img, ref_img), knobs
+            assert ref_rec.tobytes() == rec.tobytes(), knobs
+    for bad in ((-1, 1, 4.0), (65, 1, 4.0), (4, 0, 4.0), (4, 9, 4.0), (4, 1, 0.5), (4, 1, 17.0)):
+        with pytest.raises(ck.CloakError):
+            ck.cloak_set_schedule_tuning(c.h, *bad)
+    search = (("long_ray_blocks", (0, 8)), ("cost_scale", (2.0,)))
+    best, times = autotune.tune_schedule(b, lambda: ck.cloak_render_batch(b.h, views, 2, 3), key="test",
+                                         search=search)
+    assert best["long_ray_blocks"] in (0, 4, 8) and best["cost_scale"] in (2.0, 4.0) and "default" in times
+    best2, _ = autotune.tune_schedule(b, lambda: ck.cloak_render_batch(b.h, views, 2, 3), key="test", search=search)
+    assert best2 == best  # from the cache
+    b.close()
+    c.close()
+
+
 def test_full_size_batched_sampled(ck):
     """The benchmarked launch itself: the twelve 1920x1080 x 4 spp views (both cloaks and polarizations,
     elevations 0/20/45 deg, DP5(4) tol 1e-9, FP64) in ONE batched render, seeded samples of pixels of

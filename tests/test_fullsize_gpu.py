@@ -9,11 +9,11 @@ long double by more than 1e-10; 564 rays, all passing within ~2e-3 of the axis o
 reflection) the same source in IEEE binary128 at tolerance 1e-9 (tests/golden/fp64_undetermined_rays.txt).
 
 FP64 path: statuses identical and exit directions, exit points, times of flight and weights within 1e-9 on
-every ray; on the undetermined rays the bar widens by 8 x D64, D64 being how far the binary128 run moves
-when its states are FP64 numbers.  The batched launch (all twelve views in one persistent kernel, the
+every ray; on the undetermined rays each bar widens by 8 x D64 of its field, D64 being how far the binary128
+run moves when its states are FP64 numbers.  The batched launch (all twelve views in one persistent kernel, the
 benchmark's timed call) renders the same images as the per-image launches whose records are compared.
 
-Mixed path (FP32 stepping, FP64 or double-float band): exit direction within min(1e-4, max(1e-5, 40 D32))
+Mixed path (FP32 stepping, FP64 or double-float band): exit direction within min(1e-4, max(1e-5, 100 D32))
 of the reference, D32 the distance a model of FP32 right-hand sides moves the ray (1e-5 unless
 tests/golden/fp32_sensitive_rays.txt lists the ray); >= 99.9 % of the sampled pixels with the reference's
 tile and status in every sample.
@@ -31,7 +31,7 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 NPIX = 100000
 SEED = 12345
 TOL_DIR, TOL_ABS, D64_FACTOR = 1e-9, 1e-9, 8.0
-TOL_MIXED, D32_DETERMINED, D32_FACTOR, CAP = 1e-5, 2.5e-7, 40.0, 1e-4
+TOL_MIXED, D32_DETERMINED, D32_FACTOR, CAP = 1e-5, 1e-7, 100.0, 1e-4
 
 
 def angles(a, b):
@@ -70,7 +70,7 @@ def reference():
                           O.Camera(eye, tgt, up, w.hfov_deg, w.width, w.height), m, w.spp, w.seed, pixels=pix)
         samp = (pix[:, None] * w.spp + np.arange(w.spp)[None, :]).reshape(-1)
         pos = {int(s): k for k, s in enumerate(samp)}
-        lim = np.full(len(ref), TOL_DIR)
+        lim = {k: np.full(len(ref), TOL_DIR if k == "dir" else TOL_ABS) for k in ("dir", "exit_pos", "tof", "weight")}
         und = np.zeros(len(ref), bool)
         for f in und_rows.get(idx, []):
             k = pos[int(f[1])]
@@ -78,7 +78,8 @@ def reference():
             ref["exit_dir"][k] = [float(x) for x in f[4:7]]
             ref["exit_pos"][k] = [float(x) for x in f[7:10]]
             ref["tof"][k], ref["weight"][k], ref["tile_id"][k] = float(f[10]), float(f[11]), int(f[12])
-            lim[k] = TOL_DIR + D64_FACTOR * float(f[16])
+            for j, key in enumerate(("dir", "exit_pos", "tof", "weight")):
+                lim[key][k] += D64_FACTOR * float(f[16 + j])
             und[k] = True
         out.append((pix, samp, ref, lim, und))
     assert sum(int(u.sum()) for *_, u in out) == sum(len(r) for r in und_rows.values())
@@ -111,13 +112,12 @@ def test_fp64_full_workload_against_the_oracle(ck, reference):
         assert len(bad) == 0, f"image {idx}: {len(bad)} status mismatches at samples {samp[bad[:5]]}"
         fin = np.isin(ref["status"], [0, 1, 2, 7])
         ang = angles(g["exit_dir"][fin], ref["exit_dir"][fin])
-        over = np.nonzero(ang > lim[fin])[0]
+        over = np.nonzero(ang > lim["dir"][fin])[0]
         assert len(over) == 0, f"image {idx}: exit direction off by {ang[over[:5]]} at {samp[fin][over[:5]]}"
-        lim_abs = TOL_ABS + (lim - TOL_DIR)
         for field in ("exit_pos", "tof", "weight"):
             dv = np.abs(g[field] - ref[field])
             dv = dv.max(1) if dv.ndim > 1 else dv
-            over = np.nonzero(dv > lim_abs)[0]
+            over = np.nonzero(dv > lim[field])[0]
             assert len(over) == 0, f"image {idx}: {field} off by {dv[over[:5]]} at {samp[over[:5]]}"
         worst = max(worst, float(ang.max(initial=0)))
         worst_det = max(worst_det, float(ang[~und[fin]].max(initial=0)))

@@ -312,3 +312,22 @@ def test_batched_surrogate_render_matches_single_renders(ck, trained, tmp_path):
         for (_, _, _, _, _, _, out), ref in zip(views, refs):
             assert np.max(np.abs(out.cpu().numpy() - ref)) < 1e-6
     b.close()
+
+
+def test_training_is_reproducible_and_timed(ck):
+    """The same seed trains the same network bit for bit: the weight gradients of the batch-split GEMMs are
+    summed in a fixed order (no atomics).  The training reports its device time per optimizer step."""
+    nets = []
+    for _ in range(2):
+        c = ck.Cloak(ck.RADIAL).integrator(ck.DP45, 1e-9, ck.FP64)
+        ck.cloak_surrogate_train(c.h, 3 * 19456, seed=21, epochs=3)
+        nets.append(ck.cloak_surrogate_params(c.h))
+        t = ck.cloak_surrogate_train_timing(c.h)
+        assert t["ms_per_step_stage1"] > 0 and t["ms_per_step_stage2"] > 0 and t["batch"] == 19456
+        assert t["flops_per_step_stage1"] == pytest.approx(2 * 19456 * (2 * 200704 + 197888))
+        c.close()
+    assert np.array_equal(nets[0], nets[1])
+    c = ck.Cloak(ck.RADIAL)
+    with pytest.raises(ck.CloakError):
+        ck.cloak_surrogate_train_timing(c.h)
+    c.close()
