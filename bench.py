@@ -848,6 +848,15 @@ def main():
             if args.no_mixed:
                 break
             mixed_runner = Batched(prec) if args.schedule == "batched" else PerImage(ck.SCHED_WAVEFRONT, prec)
+            sched, tune_ms, tune_s = None, None, 0.0
+            if args.schedule == "batched":
+                # the step schedule from the autotuner, on this step itself (coordinate search, one timed
+                # render per candidate)
+                from paper_1209_6038_gb300 import autotune
+                t0 = time.perf_counter()
+                sched, tune_ms = autotune.tune_schedule(mixed_runner.h, mixed_runner.step, key=f"full12|{key}",
+                                                        use_cache=False)
+                tune_s = time.perf_counter() - t0
             mms, _, mstages = timed(mixed_runner, 1, 2, collective=False)
             mixed_runner.close()
             mh = make_handles(ck.SCHED_WAVEFRONT, precision=prec)
@@ -874,6 +883,12 @@ def main():
                         "steps": 2, "schedule": args.schedule,
                         "dtype": "f32 stepping, float-float state, " + band,
                         "integrate_ms_per_step": mstages[1], "speedup_vs_fp64": ms_step / mms,
+                        "schedule": sched,
+                        "autotune": None if sched is None else {
+                            "seconds": tune_s, "default_ms": tune_ms["default"],
+                            "ms": {k: v for k, v in tune_ms.items()},
+                            "search": "coordinate search over packet, long-ray blocks, cost scale and rays "
+                                      "reserved per thread, one timed batched step per candidate"},
                         "roofline": {"bound": "alu", "achieved": mflops / (mstages[1] / 1e3) / 1e12,
                                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                                      "frac": mflops / (mstages[1] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
