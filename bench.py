@@ -166,7 +166,7 @@ def reference_records(w, o, npix):
         ref["exit_dir"][k] = [float(x) for x in f[4:7]]
         ref["exit_pos"][k] = [float(x) for x in f[7:10]]
         ref["tof"][k], ref["weight"][k], ref["tile_id"][k] = float(f[10]), float(f[11]), int(f[12])
-        lim[k] = 1e-9 + 8.0 * float(f[16])
+        lim[k] = 1e-9 + 8.0 * max(float(x) for x in f[16:19])
         und[k] = True
     return ref, lim, und
 

@@ -269,7 +269,14 @@ SurNet *sur_create(double R1, double R2, double H, unsigned long long seed, cons
         delete s;
         return nullptr;
     }
-    cudaMemset(s->arena, 0, bytes);
+    // zeroed before any stream uses it: cudaMemset runs on the legacy default stream, which the library's
+    // non-blocking streams do not wait for
+    if (cudaMemset(s->arena, 0, bytes) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        *why = "cannot clear the surrogate's parameters";
+        cudaFree(s->arena);
+        delete s;
+        return nullptr;
+    }
     char *p = s->arena;
     // gradients first, contiguous (zeroed before every step)
     s->grad_begin = p;
@@ -355,7 +362,9 @@ cudaError_t sur_ensure_inference(SurNet *s, long long rows) {
     s->X = (__nv_bfloat16 *)p; p += xb;
     s->Y = (float *)p; p += yb;
     s->elig = (unsigned char *)p;
-    if ((e = cudaMemset(s->X, 0, xb)) != cudaSuccess) return e;  // columns 14..63 stay zero
+    // columns 14..63 stay zero; cleared before any stream uses the buffer (cudaMemset runs on the legacy default
+    // stream, which the library's non-blocking streams do not wait for)
+    if ((e = cudaMemset(s->X, 0, xb)) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) return e;
     s->inf_rows = rows;
     return cudaSuccess;
 }
@@ -377,7 +386,7 @@ struct TrainWS {
 };
 
 static int ksplit_for(int B, int mtiles);
-static cudaError_t ws_create(TrainWS &w, int B) {
+static cudaError_t ws_create(TrainWS &w, int B, cudaStream_t st) {
     memset(&w, 0, sizeof(w));
     w.B = B;
     size_t part = 0;  // the largest per-slice partial gradients of a layer
@@ -392,7 +401,9 @@ static cudaError_t ws_create(TrainWS &w, int B) {
     const size_t bytes = 2 * x + t + 4 * z + 8 * h + y + x + dyt + 4 * h + 512 + part;
     cudaError_t e = cudaMalloc(&w.arena, bytes);
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemset(w.arena, 0, bytes)) != cudaSuccess) return e;
+    // cleared on the stream that uses it (a cudaMemset on the legacy default stream can still be running
+    // when the first kernels of a non-blocking stream start)
+    if ((e = cudaMemsetAsync(w.arena, 0, bytes, st)) != cudaSuccess) return e;
     char *p = w.arena;
     w.Xb = (__nv_bfloat16 *)p; p += x;
     w.XTb = (__nv_bfloat16 *)p; p += x;
@@ -456,7 +467,7 @@ static cudaError_t train_forward(SurNet *s, TrainWS &w, cudaStream_t st) {
 // its partial product, and the slices are summed in a fixed order
 static cudaError_t weight_grad(SurNet *s, TrainWS &w, const SurDims &d, const CUtensorMap &tdz, const CUtensorMap &th,
                                float *gW, cudaStream_t st) {
-    GemmArgs g = gemm_args(d.mw, d.in, w.B, EPI_STORE, s->err);
+    GemmArgs g = gemm_args(d.mw, d.kin, w.B, EPI_STORE, s->err);
     g.ksplit = ksplit_for(w.B, d.mw / GEMM_TILE_M);
     g.C = w.partials;
     g.ldc = d.kin;
@@ -665,7 +676,7 @@ int sur_forward_rows(SurNet *s, const float *dev_x, long long n, float *dev_y, c
 int sur_batch_grad(SurNet *s, const float *dev_x, const float *dev_t, long long n, int stage, double lr,
                    float *host_grad, cudaStream_t st, std::string &why) {
     TrainWS w;
-    cudaError_t e = ws_create(w, (int)n);
+    cudaError_t e = ws_create(w, (int)n, st);
     if (e != cudaSuccess) { ws_destroy(w); why = "cannot allocate the training workspace"; return CLOAK_ENOMEM; }
     unsigned int *err = s->err;  // this network's own timeout flag
     cudaMemsetAsync(err, 0, 4, st);
@@ -748,7 +759,7 @@ int sur_train(SurNet *s, const Params &p, long long n, unsigned long long seed, 
     }
     TrainWS w;
     memset(&w, 0, sizeof(w));
-    if (e == cudaSuccess) e = ws_create(w, B);
+    if (e == cudaSuccess) e = ws_create(w, B, st);
     unsigned int *err = s->err;  // this network's own timeout flag
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, st);
     // 2. stage 1: regression outputs, Adam, linear warm-up then cosine decay to 2 % of the peak rate

@@ -9,9 +9,12 @@ The reference is the oracle.  Where the FP64 oracle does not determine a ray -- 
 source in long double by more than 1e-10 (status, exit direction, point, time of flight or weight): near
 r = R1 the literal Cartesian form of Eq. 8 loses digits to cancellation -- the reference is that oracle
 source in IEEE binary128 at the same step or tolerance (tests/golden/parity/, written by
-make_parity_references.py).  Those rays keep the 1e-9 bars, each widened only by 8 x D64 of its field, where
-D64 is how far the binary128 run moves when its states and stage points are rounded to FP64 (what FP64 can
-determine at best; the GPU's own rounding lands within 2-6 D64 on the rays measured).
+make_parity_references.py).  Those rays keep the 1e-9 bars, widened only by 8 x D64, where D64 is how far
+the binary128 run moves when its states and stage points are rounded to FP64 (what FP64 can determine at
+best).  The exit direction, exit point and time of flight share the largest of their three D64: one
+displacement of the path shows in all three, and a single perturbed run can leave one of them small by
+chance (on a near-axis ray of the full workload the GPU's time of flight moved 40 times its own D64, 5 times
+the shared one).  The weight keeps its own D64.
 """
 import os
 
@@ -62,8 +65,10 @@ def reference(name, spec=None):
         ref["exit_dir"][k] = [float(x) for x in f[3:6]]
         ref["exit_pos"][k] = [float(x) for x in f[6:9]]
         ref["tof"][k], ref["weight"][k], ref["tile_id"][k] = float(f[9]), float(f[10]), int(f[11])
-        for j, key in enumerate(("dir", "exit_pos", "tof", "weight")):
-            lim[key][k] += D64_FACTOR * float(f[12 + j])
+        d64 = [float(x) for x in f[12:16]]
+        for key in ("dir", "exit_pos", "tof"):
+            lim[key][k] += D64_FACTOR * max(d64[:3])
+        lim["weight"][k] += D64_FACTOR * d64[3]
         und[k] = True
     return ref, lim, und
 
