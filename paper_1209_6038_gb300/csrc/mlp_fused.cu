@@ -1,22 +1,26 @@
 // mlp_fused.cu -- the surrogate network's forward pass as ONE persistent tcgen05 kernel.
 //
 // Each CTA (one per SM) takes pairs of 128-row tiles through all five layers without their activations
-// leaving the SM.  Warp-specialised, the two tiles of a pair in ping-pong:
-//   * the producer warp (one thread) works through the jobs (tile 0, layer 0), (tile 1, layer 0),
-//     (tile 0, layer 1), ...: for each it streams the layer's weights from L2 in 64-wide K chunks through a
-//     2-slot TMA ring and issues, per chunk, the tcgen05.mma (M = 128, K = 16) of that tile, accumulating
-//     in its TMEM columns (tile t: 256 t .. 256 t + 255).  Before a job's first MMA it waits only for the
-//     epilogue of the same tile's previous layer, so the MMAs of one tile run while the epilogue of the
-//     other tile runs.  It also loads the inputs of both tiles by TMA in the 128-byte-swizzled K-major
-//     layout the MMA reads;
+// leaving the SM.  Warp-specialised, the two tiles of a pair in ping-pong; the jobs are (tile 0, layer 0),
+// (tile 1, layer 0), (tile 0, layer 1), ...:
+//   * the copy warp (one thread) streams the jobs' weights from L2 by TMA in 64-wide K chunks (32 KB,
+//     128-byte swizzle) through a 3-slot ring, refilling a slot as soon as the MMAs that read it are done,
+//     and loads each tile's inputs (the K-major layout the MMA reads) once the tile's previous last-layer
+//     MMAs are done -- after the weight chunk of the tile's first job, so that chunk is already on its way;
+//   * the MMA warp (one thread) issues, per chunk, the four tcgen05.mma (M = 128, K = 16) of the job's tile
+//     into its TMEM columns (tile t: 256 t .. 256 t + 255) and frees the slot by a commit.  Before a job's
+//     first MMA it waits only for the epilogue of the same tile's previous layer, so the MMAs of one tile
+//     run while the epilogue of the other tile runs.  The two roles are separate threads because one
+//     thread doing both spent longer per chunk on its barrier waits and bookkeeping than the tensor core
+//     spent on the chunk's four MMAs;
 //   * 16 epilogue warps take the jobs in the same order (warp w: TMEM lanes 32 (w % 4) .., column quarter
-//     w / 4): they read the tile's accumulators once its MMAs completed, add the bias, apply GELU and write
-//     the BF16 activations back into the swizzled shared-memory layout as the tile's next A operand (the
-//     last layer writes the FP32 outputs), then arrive on the tile's barrier the producer waits for.
-// Barriers: full/empty per ring slot; per tile the inputs' barrier, "MMAs done" (committed by the
-// producer) and "activations ready" (16 arrivals).  Shared memory: activations 2 x 64 KB, weight ring
-// 2 x 32 KB.  Every mbarrier wait is bounded; on a timeout the kernel sets the error flag, lets its copies
-// in flight land, frees TMEM and returns.
+//     w / 4): they read the tile's accumulators once its MMAs completed, add the bias (read through L1),
+//     apply GELU and write the BF16 activations back into the swizzled shared-memory layout as the tile's
+//     next A operand (the last layer writes the FP32 outputs), then arrive on the tile's barrier.
+// Barriers: full/empty per ring slot; per tile the inputs' barrier, "MMAs done" (committed by the MMA
+// warp) and "activations ready" (16 arrivals).  Shared memory: activations 2 x 64 KB, weight ring
+// 3 x 32 KB.  Every mbarrier wait is bounded; on a timeout the kernel sets the error flag, lets its MMAs and
+// copies in flight complete, frees TMEM and returns.
 #include "device_once.h"
 #include "surrogate.h"
 #include "tc_ptx.cuh"
@@ -25,13 +29,15 @@ namespace ck {
 
 namespace {
 constexpr int F_EPI_WARPS = 16;
-constexpr int F_PRODUCER = F_EPI_WARPS;                        // warp index of the producer
-constexpr int F_THREADS = 32 * (F_EPI_WARPS + 1);
+constexpr int F_COPY_WARP = F_EPI_WARPS;                       // warp index of the TMA copy thread
+constexpr int F_MMA_WARP = F_EPI_WARPS + 1;                    // warp index of the MMA thread
+constexpr int F_THREADS = 32 * (F_EPI_WARPS + 2);
 constexpr int F_PARTS = F_EPI_WARPS / 4;                       // epilogue warps per row quarter (column parts)
 constexpr uint32_t F_ACT_CHUNK = 128 * 128;                  // 128 rows x 64 BF16 = 16 KB
 constexpr uint32_t F_ACT_BYTES = 2 * 4 * F_ACT_CHUNK;         // 2 tiles x 4 K chunks
 constexpr uint32_t F_RING_SLOT = 256 * 128;                   // up to 256 weight rows x 64 BF16
-constexpr size_t F_SMEM = 1024 + F_ACT_BYTES + 2 * F_RING_SLOT;
+constexpr int F_SLOTS = 3;                                     // weight ring depth
+constexpr size_t F_SMEM = 1024 + F_ACT_BYTES + F_SLOTS * F_RING_SLOT;
 
 struct FusedArgs {
     const float *bias[SUR_L];
@@ -47,27 +53,25 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                 const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
                 const __grid_constant__ CUtensorMap tW3, const __grid_constant__ CUtensorMap tW4, FusedArgs a) {
     extern __shared__ unsigned char fsm_raw[];
-    __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], x_bar[2], done_bar[2], act_bar[2], drain_bar;
+    __shared__ __align__(8) uint64_t full_bar[F_SLOTS], empty_bar[F_SLOTS], x_bar[2], done_bar[2], act_bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
-    __shared__ __align__(16) float sbias[SUR_L][SUR_W];  // every layer's bias, read by the epilogue
     unsigned char *sm = (unsigned char *)(((uintptr_t)fsm_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *act = sm, *ring = sm + F_ACT_BYTES;
-    const CUtensorMap *tW[SUR_L] = {&tW0, &tW1, &tW2, &tW3, &tW4};
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long live = a.m_count ? min(a.n, (long long)__ldg(a.m_count)) : a.n;
     volatile int *vfailed = &failed;
     const uint32_t lim = a.wait_limit;
 
-    for (int l = 0; l < SUR_L; ++l)
-        for (int c = tid; c < SUR_W; c += F_THREADS) sbias[l][c] = c < (l == SUR_L - 1 ? 16 : SUR_W) ? a.bias[l][c] : 0.f;
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < F_SLOTS; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
-            mbar_init(smem_u32(&x_bar[s]), 1);
-            mbar_init(smem_u32(&done_bar[s]), 1);
-            mbar_init(smem_u32(&act_bar[s]), F_EPI_WARPS);
+        }
+        for (int t = 0; t < 2; ++t) {
+            mbar_init(smem_u32(&x_bar[t]), 1);
+            mbar_init(smem_u32(&done_bar[t]), 1);
+            mbar_init(smem_u32(&act_bar[t]), F_EPI_WARPS);
         }
         mbar_init(smem_u32(&drain_bar), 1);
         failed = 0;
@@ -84,65 +88,92 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     const uint32_t tmem = tmem_slot;
     const long long stride = (long long)gridDim.x * 256;
 
-    if (warp == F_PRODUCER) {
+    if (warp == F_COPY_WARP) {
         if (lane == 0) {
-            uint32_t G = 0;          // weight chunks loaded so far (ring slot G & 1, use G >> 1)
-            uint32_t Lt[2] = {0, 0}; // jobs committed per tile (phases of done_bar[t] / act_bar[t])
-            uint32_t iters = 0;      // tile pairs started (phase of x_bar[t])
-            uint32_t pending = 0;    // weight chunks loaded and not yet consumed (drained after a timeout)
+            uint32_t s = 0, ph = 0;  // ring slot of the next load and its use count's parity
+            uint32_t loads = 0;      // weight chunks loaded
+            uint32_t Lx = 0;         // tile pairs whose inputs were loaded (x_bar phase)
             bool x_pending[2] = {false, false};
+            uint32_t x_phase[2] = {0, 0};
             bool ok = true;
             for (long long base = (long long)blockIdx.x * 256; base < live && ok; base += stride) {
-                // a tile's inputs overwrite its activations, which its previous last-layer MMAs read
-                for (int t = 0; t < 2 && ok; ++t) {
-                    if (Lt[t] > 0) ok = mbar_wait(smem_u32(&done_bar[t]), (Lt[t] - 1) & 1, lim);
-                    if (!ok || *vfailed) { ok = false; break; }
-                    mbar_expect_tx(smem_u32(&x_bar[t]), F_ACT_CHUNK);
-                    tma_load_2d(smem_u32(act + t * 4 * F_ACT_CHUNK), &tX, 0, (int)(base + 128 * t), smem_u32(&x_bar[t]));
-                    x_pending[t] = true;
-                }
                 for (int job = 0; job < 2 * SUR_L && ok; ++job) {
                     const int l = job >> 1, t = job & 1;
-                    const int nk = l == 0 ? 1 : 4, N = l == SUR_L - 1 ? 16 : SUR_W;
-                    const uint32_t idesc = bf16_idesc(N), G0 = G;
-                    for (int it = 0; it <= nk && ok; ++it) {
-                        if (it < nk) {  // load chunk it of this layer's weights into a free ring slot
-                            const uint32_t g = G0 + it, s = g & 1;
-                            if (g >= 2) ok = mbar_wait(smem_u32(&empty_bar[s]), ((g >> 1) - 1) & 1, lim);
-                            if (!ok) break;
-                            mbar_expect_tx(smem_u32(&full_bar[s]), (uint32_t)N * 128);
-                            tma_load_2d(smem_u32(ring + s * F_RING_SLOT), tW[l], it * 64, 0, smem_u32(&full_bar[s]));
-                            ++pending;
-                            G = g + 1;
+                    const int nk = l == 0 ? 1 : 4;
+                    const uint32_t bytes = l == SUR_L - 1 ? 16u * 128u : 256u * 128u;
+                    const CUtensorMap *map = l == 0 ? &tW0 : l == 1 ? &tW1 : l == 2 ? &tW2 : l == 3 ? &tW3 : &tW4;
+                    for (int j = 0; j < nk; ++j) {
+                        // the slot is free once the MMAs of the chunk loaded F_SLOTS chunks ago are done
+                        if (loads >= F_SLOTS) ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, lim);
+                        if (!ok) break;
+                        mbar_expect_tx(smem_u32(&full_bar[s]), bytes);
+                        tma_load_2d(smem_u32(ring + s * F_RING_SLOT), map, j * 64, 0, smem_u32(&full_bar[s]));
+                        ++loads;
+                        if (++s == F_SLOTS) { s = 0; ph ^= 1u; }
+                    }
+                    if (!ok) break;
+                    if (l == 0) {
+                        // the tile's inputs overwrite its activations, which its previous last-layer MMAs read
+                        // ("MMAs done" completes SUR_L times per tile and pair)
+                        if (Lx > 0) ok = mbar_wait(smem_u32(&done_bar[t]), (SUR_L * Lx - 1) & 1, lim);
+                        if (!ok || *vfailed) { ok = false; break; }
+                        mbar_expect_tx(smem_u32(&x_bar[t]), F_ACT_CHUNK);
+                        tma_load_2d(smem_u32(act + t * 4 * F_ACT_CHUNK), &tX, 0, (int)(base + 128 * t), smem_u32(&x_bar[t]));
+                        x_pending[t] = true;
+                        x_phase[t] = Lx & 1;
+                    }
+                }
+                ++Lx;
+            }
+            if (!ok) {
+                *vfailed = 1;
+                if (a.err) atomicExch(a.err, 1u);
+            }
+            // every copy has landed before the shared memory is released: the last load into each slot and
+            // the last inputs of each tile (at once on a normal exit, where the MMAs consumed them; bounded by
+            // the default limit after a timeout)
+            for (uint32_t k = 0; k < F_SLOTS && k < loads; ++k) {
+                const uint32_t g = loads - 1 - k;  // one of the last F_SLOTS loads, each in its own slot
+                mbar_wait(smem_u32(&full_bar[g % F_SLOTS]), (g / F_SLOTS) & 1);
+            }
+            for (int t = 0; t < 2; ++t)
+                if (x_pending[t]) mbar_wait(smem_u32(&x_bar[t]), x_phase[t]);
+        }
+    } else if (warp == F_MMA_WARP) {
+        if (lane == 0) {
+            uint32_t s = 0, ph = 0;  // ring slot of the next chunk and its fill parity
+            uint32_t Lt[2] = {0, 0}; // jobs committed per tile (phases of done_bar[t] / act_bar[t])
+            uint32_t iters = 0;      // tile pairs started (phase of x_bar[t])
+            bool ok = true;
+            const uint32_t ring0 = smem_u32(ring), act0 = smem_u32(act);
+            for (long long base = (long long)blockIdx.x * 256; base < live && ok; base += stride) {
+                for (int job = 0; job < 2 * SUR_L && ok; ++job) {
+                    const int l = job >> 1, t = job & 1;
+                    const int nk = l == 0 ? 1 : 4;
+                    const uint32_t idesc = bf16_idesc(l == SUR_L - 1 ? 16 : SUR_W), d_tmem = tmem + t * 256;
+                    for (int j = 0; j < nk; ++j) {
+                        ok = mbar_wait(smem_u32(&full_bar[s]), ph, lim);
+                        if (ok && j == 0) {
+                            // the tile's previous epilogue has read its accumulators and written these inputs
+                            if (Lt[t] > 0) ok = mbar_wait(smem_u32(&act_bar[t]), (Lt[t] - 1) & 1, lim);
+                            if (ok && l == 0) ok = mbar_wait(smem_u32(&x_bar[t]), iters & 1, lim);
+                            if (ok && *vfailed) ok = false;
                         }
-                        const int j = it - 1;
-                        if (j >= 0) {  // multiply chunk j for tile t
-                            const uint32_t g = G0 + j, s = g & 1;
-                            ok = mbar_wait(smem_u32(&full_bar[s]), (g >> 1) & 1, lim);
-                            if (ok && j == 0) {
-                                // the tile's previous epilogue has read its accumulators and written these inputs
-                                if (Lt[t] > 0) ok = mbar_wait(smem_u32(&act_bar[t]), (Lt[t] - 1) & 1, lim);
-                                if (ok && l == 0) {
-                                    ok = mbar_wait(smem_u32(&x_bar[t]), iters & 1, lim);
-                                    if (ok) x_pending[t] = false;
-                                }
-                            }
-                            if (!ok) break;
-                            --pending;
-                            asm volatile("tcgen05.fence::after_thread_sync;");
-                            const uint64_t bd = sw128_desc(smem_u32(ring + s * F_RING_SLOT));
-                            const uint64_t ad = sw128_desc(smem_u32(act + (t * 4 + j) * F_ACT_CHUNK));
+                        if (!ok) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint64_t bd = sw128_desc(ring0 + s * F_RING_SLOT);
+                        const uint64_t ad = sw128_desc(act0 + (uint32_t)(t * 4 + j) * F_ACT_CHUNK);
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
-                                asm volatile(
-                                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * 256),
-                                    "l"(ad + (uint64_t)(2 * kk)), "l"(bd + (uint64_t)(2 * kk)), "r"(idesc), "r"(acc));
-                            }
-                            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                smem_u32(&empty_bar[s])));
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+                            asm volatile(
+                                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+                                "l"(ad + (uint64_t)(2 * kk)), "l"(bd + (uint64_t)(2 * kk)), "r"(idesc), "r"(acc));
                         }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            smem_u32(&empty_bar[s])));
+                        if (++s == F_SLOTS) { s = 0; ph ^= 1u; }
                     }
                     if (!ok) break;
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -154,16 +185,11 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             if (!ok) {
                 *vfailed = 1;
                 if (a.err) atomicExch(a.err, 1u);
-                // let the MMAs already issued complete before the accumulators are freed (a commit arrives once
-                // every earlier MMA of this thread is done), then the copies still in flight land before the
-                // shared memory is released; both bounded by the default limit
+                // the MMAs already issued complete before the accumulators are freed (a commit arrives once every
+                // earlier MMA of this thread is done); bounded by the default limit
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_u32(&drain_bar)));
                 mbar_wait(smem_u32(&drain_bar), 0);
-                for (uint32_t k = 0; k < pending; ++k)
-                    mbar_wait(smem_u32(&full_bar[(G - pending + k) & 1]), ((G - pending + k) >> 1) & 1);
-                for (int t = 0; t < 2; ++t)
-                    if (x_pending[t]) mbar_wait(smem_u32(&x_bar[t]), iters & 1);
             }
         }
     } else {
@@ -180,7 +206,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
                 const int cw = max(16, N / F_PARTS), c0 = part * cw, c1 = min(N, c0 + cw);
-                const float *bias = sbias[l];
+                const float *__restrict__ bias = a.bias[l];  // through L1 (read-only)
                 if (l < SUR_L - 1) {
                     for (int c = c0; c < c1; c += 32) {  // 32 columns per TMEM load (parts are 64 wide)
                         uint32_t u[32];
