@@ -223,10 +223,13 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                         // GELU, BF16, into the 128-byte-swizzled K-major layout of chunk c / 64: 16-byte units
                         // (c % 64) / 8 .. + 3 of row r, each XOR-ed with r % 8
                         uint32_t pk[16];
+                        const float4 *b4 = reinterpret_cast<const float4 *>(bias + c);  // 16-byte aligned
 #pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            pk[i] = gelu2_bf16(__uint_as_float(u[2 * i]) + bias[c + 2 * i],
-                                               __uint_as_float(u[2 * i + 1]) + bias[c + 2 * i + 1]);
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 bv = __ldg(b4 + i);
+                            pk[2 * i] = gelu2_bf16(__uint_as_float(u[4 * i]) + bv.x, __uint_as_float(u[4 * i + 1]) + bv.y);
+                            pk[2 * i + 1] = gelu2_bf16(__uint_as_float(u[4 * i + 2]) + bv.z, __uint_as_float(u[4 * i + 3]) + bv.w);
+                        }
                         unsigned char *chunk = act + (t * 4 + c / 64) * F_ACT_CHUNK + (r >> 3) * 1024 + (r & 7) * 128;
                         const int u0 = (c & 63) >> 3;
 #pragma unroll
