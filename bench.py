@@ -79,7 +79,7 @@ RHS_FLOPS = {(0, 0): 0, (0, 1): 36, (1, 0): 34, (1, 1): 30}
 # DRAM bytes (read + write) of one launch of the any-medium integration kernel on the full step: one
 # ncu capture of the same twelve views at 480x270 x 4 spp (122.5 MB read + 54.1 MB written) scaled by
 # samples (x 16.0).  To be re-captured whenever the kernel changes.
-INTEGRATE_TRAFFIC_BYTES = (122.539008e6 + 54.080512e6) * (1920 * 1080) / (480 * 270)
+INTEGRATE_TRAFFIC_BYTES = (122.350336e6 + 54.126080e6) * (1920 * 1080) / (480 * 270)
 DP45_FIXED, RK4_FIXED = 362, 102
 
 # bytes per view of the table a batched render copies host to device at every step (the camera frame,
@@ -319,6 +319,7 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
     bh = {}
     for prec in (ck.FP64, ck.SURROGATE):
         b = ck.Cloak(ck.RADIAL).integrator(integ, sw.h_or_tol, prec, sw.max_steps).schedule(ck.SCHED_WAVEFRONT)
+        b.stage_timing(True)
         if prec == ck.SURROGATE:
             ck.cloak_surrogate_load(b.h, path)
             ck.cloak_surrogate_set_gate(b.h, sw.extra["gate_log10_err"])
@@ -337,10 +338,11 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
     def step(prec):
         ck.cloak_render_batch(bh[prec].h, bviews, sw.spp, sw.seed)
 
-    res = {}
+    res, stages = {}, {}
     for prec in (ck.FP64, ck.SURROGATE):
         step(prec)
         torch.cuda.synchronize()
+        stages[prec] = list(bh[prec].stage_times())
         ts = []
         for _ in range(2):
             flush.zero_()
@@ -385,6 +387,10 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
             "ms_per_step": res[ck.SURROGATE], "fp64_integrator": {"value": rays / (res[ck.FP64] / 1e3),
                                                                    "ms_per_step": res[ck.FP64]},
             "speedup_vs_fp64_integrator": res[ck.FP64] / res[ck.SURROGATE], "warmup": 1, "steps": 2,
+            "stage_ms": {name: {"surrogate": stages[ck.SURROGATE][k], "fp64_integrator": stages[ck.FP64][k]}
+                         for k, name in enumerate(("camera_entry_network_gate_sort", "integrate", "exit_shade",
+                                                   "resolve"))},
+            "network_features_gate_ms": stages[ck.SURROGATE][0] - stages[ck.FP64][0],
             "gate_log10_err": sw.extra["gate_log10_err"],
             "handled_frac_of_entering": tot["handled"] / max(1, tot["entering"]),
             "image_error_vs_fp64": {"sample": "every 7th ray of every view", "rays_compared": tot["rays"],
