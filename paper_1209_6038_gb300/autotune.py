@@ -63,32 +63,39 @@ def apply(cloak, sched: dict):
                                  float(sched["cost_scale"]))
 
 
-def tune_schedule(cloak, run, key: str, reps: int = 1, use_cache: bool = True, search=SEARCH):
+def tune_schedule(cloak, run, key: str, reps: int = 1, use_cache: bool = True, search=SEARCH, timer=None,
+                  setter=None, device_name=None):
     """cloak: paper_1209_6038_gb300.cloak.Cloak (wavefront schedule); run(): one render on the current
-    stream.  Returns (best schedule, {"knob=value": ms}).  The best schedule is left set on the handle."""
-    import torch
-    gpu = torch.cuda.get_device_name()
-    full_key = f"{gpu}|schedule|{key}"
+    stream.  Returns (best schedule, {"knob=value": ms}).  The best schedule is left set on the handle.
+    timer(run, reps) -> ms, setter(cloak, schedule) and device_name replace the CUDA-event timing, the
+    handle call and the GPU's name (the search itself is host logic, tested without a GPU)."""
+    timer = timer or _time
+    setter = setter or apply
+    if device_name is None:
+        import torch
+        device_name = torch.cuda.get_device_name()
+    full_key = f"{device_name}|schedule|{key}"
     if use_cache:
         hit = _load().get(full_key)
         if hit:
-            apply(cloak, hit["schedule"])
+            setter(cloak, hit["schedule"])
             return hit["schedule"], hit["ms"]
     best = dict(DEFAULT_SCHEDULE)
-    apply(cloak, best)
-    times = {"default": _time(run, reps)}
+    setter(cloak, best)
+    times = {"default": timer(run, reps)}
     best_ms = times["default"]
     for knob, values in search:
+        incumbent = best[knob]  # already timed
         for v in values:
-            if v == best[knob]:
+            if v == incumbent:
                 continue
             trial = dict(best, **{knob: v})
-            apply(cloak, trial)
-            ms = _time(run, reps)
+            setter(cloak, trial)
+            ms = timer(run, reps)
             times[f"{knob}={v}"] = ms
             if ms < best_ms:
                 best_ms, best = ms, trial
-        apply(cloak, best)
+        setter(cloak, best)
     _store(full_key, {"schedule": best, "ms": times})
     return best, times
 
