@@ -293,8 +293,9 @@ int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long long seed, 
                        void *cuda_stream);
 
 /* ---- learned surrogate of the exit state (the paper has none) -------------------------------------
- * A multilayer perceptron 7 -> 256 -> 256 -> 256 -> 256 -> 5 (GELU, tanh form; BF16 weights, FP32
- * accumulation on the tensor cores) maps a ray entering the lateral surface r = R2 -- entry height and
+ * A multilayer perceptron 7 -> 256 -> 256 -> 256 -> 256 -> 5 (GELU, tanh form; FP32 accumulation on the
+ * tensor cores; trained with BF16 operands, evaluated in renders and by cloak_surrogate_forward with FP16
+ * operands and activations) maps a ray entering the lateral surface r = R2 -- entry height and
  * azimuth, the two angles of its vacuum direction in the local (r, theta, z) frame, polarization bit,
  * variant bit, R1/R2 -- to its exit through r = R2: exit height, cos and sin of the exit azimuth's
  * departure from the straight line's, time of flight, and a confidence output (predicted log10 of its

@@ -8,26 +8,26 @@
 
 namespace ck {
 
-// one queued ray's network inputs (each as a BF16 pair hi, lo in columns j and SUR_IN + j: the first layer
-// weighs both alike) and whether it entered through the lateral surface (the surrogate's support)
+// one queued ray's network inputs (each as a half-precision pair hi, lo in columns j and SUR_IN + j: the
+// first layer weighs both alike) and whether it entered through the lateral surface (the surrogate's support)
 __device__ __forceinline__ void sur_feature_row(const Params &p, int mode, const Queue &q, unsigned int k,
-                                                const double d[3], __nv_bfloat16 *X, unsigned char *elig) {
+                                                const double d[3], __half *X, unsigned char *elig) {
     const double P[3] = {q.x[k], q.y[k], q.z[k]};
     const bool lateral = fabs(hypot(P[0], P[1]) - p.R2) <= 1e-9 * p.R2 && fabs(P[2]) < p.halfH;
     float x[SUR_IN];
     sur_features(p.R1, p.R2, p.H, p.variant == V_AZIMUTHAL ? 1 : 0, mode, P, d, x);
-    __nv_bfloat16 *row = X + (size_t)k * 64;
+    __half *row = X + (size_t)k * 64;
 #pragma unroll
     for (int j = 0; j < SUR_IN; ++j) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x[j]);
+        const __half hi = __float2half_rn(x[j]);
         row[j] = hi;
-        row[SUR_IN + j] = __float2bfloat16_rn(x[j] - __bfloat162float(hi));
+        row[SUR_IN + j] = __float2half_rn(x[j] - __half2float(hi));
     }
     elig[k] = lateral ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(256) k_sur_features(Params p, int mode, int spp, unsigned long long seed, Queue q,
-                                                      __nv_bfloat16 *X, unsigned char *elig) {
+                                                      __half *X, unsigned char *elig) {
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const long long idx = q.id[k], pix = idx / spp;
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256) k_sur_features(Params p, int mode, int sp
 }
 
 __global__ void __launch_bounds__(256) k_sur_features_batch(Params p, const ViewDev *views, int nviews, int spp,
-                                                            unsigned long long seed, Queue q, __nv_bfloat16 *X,
+                                                            unsigned long long seed, Queue q, __half *X,
                                                             unsigned char *elig) {
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {

@@ -181,16 +181,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-CUresult make_tmap_bf16(CUtensorMap *map, const void *base, int rows, int cols, int box_rows) {
+static CUresult make_tmap_16bit(CUtensorMap *map, CUtensorMapDataType type, const void *base, int rows, int cols,
+                                int box_rows) {
     auto enc = get_encode();
     if (!enc) return CUDA_ERROR_NOT_SUPPORTED;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
     cuuint32_t box[2] = {(cuuint32_t)GEMM_KCHUNK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return enc(map, type, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+CUresult make_tmap_bf16(CUtensorMap *map, const void *base, int rows, int cols, int box_rows) {
+    return make_tmap_16bit(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, rows, cols, box_rows);
+}
+CUresult make_tmap_f16(CUtensorMap *map, const void *base, int rows, int cols, int box_rows) {
+    return make_tmap_16bit(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, base, rows, cols, box_rows);
 }
 
 cudaError_t launch_gemm_tc(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &g, cudaStream_t st) {

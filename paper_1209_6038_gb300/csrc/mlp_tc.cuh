@@ -59,6 +59,8 @@ inline size_t gemm_smem_bytes(int N) {
 
 // host: TMA descriptors for a row-major BF16 matrix [rows x cols] with box (64 cols x box_rows)
 CUresult make_tmap_bf16(CUtensorMap *map, const void *base, int rows, int cols, int box_rows);
+// the same for a half-precision (FP16) matrix
+CUresult make_tmap_f16(CUtensorMap *map, const void *base, int rows, int cols, int box_rows);
 cudaError_t launch_gemm_tc(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &g, cudaStream_t st);
 
 }  // namespace ck

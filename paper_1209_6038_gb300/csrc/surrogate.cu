@@ -152,8 +152,8 @@ __global__ void k_sur_rowsum(const __nv_bfloat16 *M, int cols, float *out) {
 // the sum of both columns'; the entry height and azimuth (inputs 0, 1) keep their weights (zero after
 // initialisation: the exit does not depend on them by the symmetry of the media).
 __global__ void k_sur_adam(SurDims dm, float *W, float *b, float *mW, float *vW, float *mb, float *vb,
-                           const float *gW, const float *gb, __nv_bfloat16 *Wb, __nv_bfloat16 *WTb,
-                           const SurSched *sc) {
+                           const float *gW, const float *gb, __nv_bfloat16 *Wb, __nv_bfloat16 *WTb, __half *Wh,
+                           __half *bh, const SurSched *sc) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nW = (long long)dm.mw * dm.kin;
     const bool update = sc != nullptr;
@@ -171,27 +171,40 @@ __global__ void k_sur_adam(SurDims dm, float *W, float *b, float *mW, float *vW,
             W[e] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
         }
         const __nv_bfloat16 wb = __float2bfloat16_rn(W[e]);
+        const __half wh = __float2half_rn(W[e]);
         if (r < dm.nout) {
             Wb[(size_t)r * dm.kin + c] = wb;
-            if (first && c < SUR_IN) Wb[(size_t)r * dm.kin + SUR_IN + c] = wb;
+            Wh[(size_t)r * dm.kin + c] = wh;
+            if (first && c < SUR_IN) {
+                Wb[(size_t)r * dm.kin + SUR_IN + c] = wb;
+                Wh[(size_t)r * dm.kin + SUR_IN + c] = wh;
+            }
         }
         if (r < dm.kb) WTb[(size_t)c * dm.kb + r] = wb;
-    } else if (e < nW + dm.out && update) {
+    } else if (e < nW + dm.mw) {
         const int r = (int)(e - nW);
-        const float g = gb[r];
-        const float m = b1 * mb[r] + (1.f - b1) * g, v = b2 * vb[r] + (1.f - b2) * g * g;
-        mb[r] = m;
-        vb[r] = v;
-        b[r] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+        if (update && r < dm.out) {
+            const float g = gb[r];
+            const float m = b1 * mb[r] + (1.f - b1) * g, v = b2 * vb[r] + (1.f - b2) * g * g;
+            mb[r] = m;
+            vb[r] = v;
+            b[r] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+        }
+        bh[r] = __float2half_rn(b[r]);
     }
 }
 
-// FP32 inputs (n x 7) into the padded BF16 input rows of the inference scratch
-__global__ void k_sur_pack(const float *x, long long n, __nv_bfloat16 *X) {
+// FP32 inputs (n x 7) into the padded half-precision input rows of the inference scratch (hi, lo pairs)
+__global__ void k_sur_pack(const float *x, long long n, __half *X) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
 #pragma unroll
-    for (int j = 0; j < SUR_IN; ++j) split_bf16(x[i * SUR_IN + j], X[(size_t)i * 64 + j], X[(size_t)i * 64 + SUR_IN + j]);
+    for (int j = 0; j < SUR_IN; ++j) {
+        const float v = x[i * SUR_IN + j];
+        const __half hi = __float2half_rn(v);
+        X[(size_t)i * 64 + j] = hi;
+        X[(size_t)i * 64 + SUR_IN + j] = __float2half_rn(v - __half2float(hi));
+    }
 }
 __global__ void k_sur_unpack(const float *Y, long long n, float *y) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,6 +274,7 @@ SurNet *sur_create(double R1, double R2, double H, unsigned long long seed, cons
         const size_t w = align256((size_t)d.mw * d.kin * 4), bb = align256((size_t)d.mw * 4);
         bytes += 4 * w + 4 * bb;                                        // W, mW, vW, gW ; b, mb, vb, gb
         bytes += align256((size_t)d.nout * d.kin * 2) + align256((size_t)d.kin * d.kb * 2);
+        bytes += align256((size_t)d.nout * d.kin * 2) + align256((size_t)d.mw * 2);  // Wh, bh
     }
     bytes += 256;  // error flag
     cudaError_t e = cudaMalloc(&s->arena, bytes);
@@ -297,7 +311,10 @@ SurNet *sur_create(double R1, double R2, double H, unsigned long long seed, cons
         s->vb[l] = (float *)p; p += bb;
         s->Wb[l] = (__nv_bfloat16 *)p; p += align256((size_t)d.nout * d.kin * 2);
         s->WTb[l] = (__nv_bfloat16 *)p; p += align256((size_t)d.kin * d.kb * 2);
-        if (!tmap(&s->tWb[l], s->Wb[l], d.nout, d.kin, d.nout) || !tmap(&s->tWTb[l], s->WTb[l], d.kin, d.kb, d.kin)) {
+        s->Wh[l] = (__half *)p; p += align256((size_t)d.nout * d.kin * 2);
+        s->bh[l] = (__half *)p; p += align256((size_t)d.mw * 2);
+        if (!tmap(&s->tWb[l], s->Wb[l], d.nout, d.kin, d.nout) || !tmap(&s->tWTb[l], s->WTb[l], d.kin, d.kb, d.kin) ||
+            make_tmap_f16(&s->tWh[l], s->Wh[l], d.nout, d.kin, d.nout) != CUDA_SUCCESS) {
             *why = "cannot encode the weight tensor maps";
             cudaFree(s->arena);
             delete s;
@@ -338,9 +355,10 @@ void sur_destroy(SurNet *s) {
 static cudaError_t adam_all(SurNet *s, const SurSched *sc, int first_layer, cudaStream_t st) {
     for (int l = first_layer; l < SUR_L; ++l) {
         SurDims d = sur_dims(l);
-        const long long n = (long long)d.mw * d.kin + d.out;
+        const long long n = (long long)d.mw * d.kin + d.mw;
         k_sur_adam<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, s->W[l], s->b[l], s->mW[l], s->vW[l], s->mb[l],
-                                                               s->vb[l], s->gW[l], s->gb[l], s->Wb[l], s->WTb[l], sc);
+                                                               s->vb[l], s->gW[l], s->gb[l], s->Wb[l], s->WTb[l],
+                                                               s->Wh[l], s->bh[l], sc);
     }
     return cudaGetLastError();
 }
@@ -359,7 +377,7 @@ cudaError_t sur_ensure_inference(SurNet *s, long long rows) {
     cudaError_t e = cudaMalloc(&s->inf_arena, xb + yb + eb);
     if (e != cudaSuccess) return e;
     char *p = s->inf_arena;
-    s->X = (__nv_bfloat16 *)p; p += xb;
+    s->X = (__half *)p; p += xb;
     s->Y = (float *)p; p += yb;
     s->elig = (unsigned char *)p;
     // columns 14..63 stay zero; cleared before any stream uses the buffer (cudaMemset runs on the legacy default

@@ -59,7 +59,9 @@ struct SurNet {
     float *gW[SUR_L], *gb[SUR_L];                          // gradients
     __nv_bfloat16 *Wb[SUR_L];   // nout x kin, B operand of the forward GEMM
     __nv_bfloat16 *WTb[SUR_L];  // kin x kb, B operand of the input-gradient GEMM
-    CUtensorMap tWb[SUR_L], tWTb[SUR_L];
+    __half *Wh[SUR_L];          // nout x kin in half precision: B operand of the fused inference kernel
+    __half *bh[SUR_L];          // the biases in half precision (the fused kernel's hidden layers)
+    CUtensorMap tWb[SUR_L], tWTb[SUR_L], tWh[SUR_L];
     char *arena;          // one allocation for all of the above
     size_t grad_bytes;    // the gradients are contiguous from gW[0]
     char *grad_begin;
@@ -74,7 +76,7 @@ struct SurNet {
     // hidden activations never leave the SM (mlp_fused.cu)
     long long inf_rows;
     char *inf_arena;
-    __nv_bfloat16 *X;
+    __half *X;  // half-precision input pairs (hi, lo), n x 64
     float *Y;
     unsigned char *elig;
 };
@@ -82,8 +84,8 @@ struct SurNet {
 // lifetime and parameters (surrogate.cu)
 SurNet *sur_create(double R1, double R2, double H, unsigned long long seed, const char **why);
 void sur_destroy(SurNet *s);
-cudaError_t sur_refresh_bf16(SurNet *s, cudaStream_t st);  // Wb / WTb from the FP32 masters
-// forward pass of n rows of X (BF16 input pairs, n x 64) into Y (FP32, n x 16); n % 128 == 0;
+cudaError_t sur_refresh_bf16(SurNet *s, cudaStream_t st);  // Wb / WTb / Wh / bh from the FP32 masters
+// forward pass of n rows of X (half-precision input pairs, n x 64) into Y (FP32, n x 16); n % 128 == 0;
 // m_count: optional device row count (rows at or beyond it are skipped tile by tile)
 cudaError_t sur_forward(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st);
 // the same as one persistent tcgen05 kernel (mlp_fused.cu)

@@ -68,6 +68,10 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t bf16_idesc(int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
+// the same for FP16 x FP16 -> FP32 (operand formats 0)
+__host__ __device__ constexpr uint32_t f16_idesc(int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
 
 // GELU, tanh form, with the hardware tanh approximation (tanh.approx.f32, relative error about 2^-11: below
 // the BF16 rounding of the activations it feeds), and its derivative (FP32)
@@ -94,6 +98,19 @@ __device__ __forceinline__ uint32_t gelu2_bf16(float a, float b) {
     const __half2 hx = __hmul2(half, x);
     const float2 g = __half22float2(__hfma2(hx, th, hx));  // x (1 + tanh) / 2
     const __nv_bfloat162 o = __floats2bfloat162_rn(g.x, g.y);
+    return *(const uint32_t *)&o;
+}
+// GELU of x + b for a pair in half precision (x: FP32 accumulators, b: half-precision biases), the
+// result as a half-precision pair -- the fused inference kernel's activations
+__device__ __forceinline__ uint32_t gelu2_f16(float a, float b, __half2 bias) {
+    const __half2 x = __hadd2(__floats2half2_rn(a, b), bias);
+    const __half2 one = __float2half2_rn(1.f), k0 = __float2half2_rn(0.7978845608028654f),
+                  k1 = __float2half2_rn(0.044715f), half = __float2half2_rn(0.5f);
+    const __half2 u = __hmul2(__hmul2(k0, x), __hfma2(k1, __hmul2(x, x), one));  // k0 x (1 + k1 x^2)
+    __half2 th;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(*(uint32_t *)&th) : "r"(*(const uint32_t *)&u));
+    const __half2 hx = __hmul2(half, x);
+    const __half2 o = __hfma2(hx, th, hx);  // x (1 + tanh) / 2
     return *(const uint32_t *)&o;
 }
 __device__ __forceinline__ float gelu_tanh_grad(float x) {
