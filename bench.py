@@ -412,8 +412,10 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
                                               "(data and weight GEMMs, fixed-order split-K sums) and Adam, replayed "
                                               "as a CUDA graph; CUDA events around the stage"}},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) of measured",
-                         "kernel": "k_mlp_fused (persistent tcgen05 BF16 network, FP32 accumulation in TMEM): "
+                         "frac": achieved / peak,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) of measured; FP16 operands: "
+                                        "the same nominal dense rate as BF16 (ratio 1)",
+                         "kernel": "k_mlp_fused (persistent tcgen05 network, FP16 operands, FP32 accumulation in TMEM): "
                                    "forward pass of 2^22 rows",
                          "flops_per_ray": SUR_FLOPS_PER_RAY, "ms": fwd_ms}}
 
