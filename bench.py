@@ -808,8 +808,14 @@ def main():
                                            "samples" if args.schedule == "batched" else None,
                            "peak_source": ALU_PEAK_SOURCE + " (FP64)", "kernel": kname,
                            "kernel_ms_per_step": stages[1]}
+        # camera rays integrated through the cloak: exited, exited after the metal mirror, TIR at the exit,
+        # step limit, singular (not: missed, no transmitted mode at entry, metal cap disc hit from outside)
+        in_cloak = int(status_hist[[1, 2, 4, 5, 6]].sum())
         out["work"] = {"integrator_steps_per_step": steps_total, "fp64_flops_per_step": flops,
-                       "status_hist": {ck.RAY_STATUS[i]: int(status_hist[i]) for i in range(8)}}
+                       "status_hist": {ck.RAY_STATUS[i]: int(status_hist[i]) for i in range(8)},
+                       "in_cloak_rays_per_step": in_cloak,
+                       "in_cloak_rays_per_s": in_cloak / (ms_step / 1e3),
+                       "rk_step_attempts_per_s": steps_total / (ms_step / 1e3)}
 
         # ---- CPU oracle on a bounded sample, and the exit-direction error against it
         cores = os.cpu_count() or 1
