@@ -291,17 +291,22 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
     n = 1 << 22
     x = torch.rand((n, 7), device="cuda") * 2 - 1
     y = torch.empty((n, 5), device="cuda")
-    ck.cloak_surrogate_forward(trainer.h, x, y)
-    reps, ms = 5, []
-    for _ in range(reps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
+    def fwd_time(fp16):
+        ck.cloak_surrogate_set_precision(trainer.h, fp16)
         ck.cloak_surrogate_forward(trainer.h, x, y)
-        b.record()
-        b.synchronize()
-        ms.append(a.elapsed_time(b))
-    fwd_ms = statistics.median(ms)
+        ms = []
+        for _ in range(5):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ck.cloak_surrogate_forward(trainer.h, x, y)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    fwd_ms16 = fwd_time(True)   # FP16 operands (optional inference precision)
+    fwd_ms = fwd_time(False)    # BF16 operands, the training precision (default)
     achieved = n * SUR_FLOPS_PER_RAY / (fwd_ms / 1e3) / 1e12
     peak = BF16_PEAK_TFLOPS
     trainer.close()
@@ -338,11 +343,10 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
     def step(prec):
         ck.cloak_render_batch(bh[prec].h, bviews, sw.spp, sw.seed)
 
-    res, stages = {}, {}
-    for prec in (ck.FP64, ck.SURROGATE):
+    def timed_render(prec):
         step(prec)
         torch.cuda.synchronize()
-        stages[prec] = list(bh[prec].stage_times())
+        st = list(bh[prec].stage_times())
         ts = []
         for _ in range(2):
             flush.zero_()
@@ -352,7 +356,15 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
             b.record()
             b.synchronize()
             ts.append(a.elapsed_time(b))
-        res[prec] = statistics.mean(ts)
+        return statistics.mean(ts), st
+
+    res, stages = {}, {}
+    for prec in (ck.FP64, ck.SURROGATE):
+        res[prec], stages[prec] = timed_render(prec)
+    # the same surrogate render with FP16 inference
+    ck.cloak_surrogate_set_precision(bh[ck.SURROGATE].h, True)
+    res16, stages16 = timed_render(ck.SURROGATE)
+    ck.cloak_surrogate_set_precision(bh[ck.SURROGATE].h, False)
     # image error against the FP64 integrator, ray by ray
     rb = torch.empty(sw.rays_per_image * ck.RECORD_BYTES, dtype=torch.uint8, device="cuda")
     tot = {"rays": 0, "entering": 0, "handled": 0, "tile_all": 0, "tile_cloak": 0, "status": 0}
@@ -391,6 +403,13 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
                          for k, name in enumerate(("camera_entry_network_gate_sort", "integrate", "exit_shade",
                                                    "resolve"))},
             "network_features_gate_ms": stages[ck.SURROGATE][0] - stages[ck.FP64][0],
+            "fp16_inference": {"value": rays / (res16 / 1e3), "ms_per_step": res16,
+                               "speedup_vs_fp64_integrator": res[ck.FP64] / res16,
+                               "network_features_gate_ms": stages16[0] - stages[ck.FP64][0],
+                               "forward_tflops": n * SUR_FLOPS_PER_RAY / (fwd_ms16 / 1e3) / 1e12,
+                               "forward_frac_of_peak": n * SUR_FLOPS_PER_RAY / (fwd_ms16 / 1e3) / 1e12 / peak,
+                               "note": "cloak_surrogate_set_precision(h, 1): FP16 weights, hidden biases, input "
+                                       "pairs and activations, FP32 accumulation; same peak as BF16"},
             "gate_log10_err": sw.extra["gate_log10_err"],
             "handled_frac_of_entering": tot["handled"] / max(1, tot["entering"]),
             "image_error_vs_fp64": {"sample": "every 7th ray of every view", "rays_compared": tot["rays"],
@@ -413,9 +432,8 @@ def surrogate_section(args, ck, inputs, torch, np, flush):
                                               "as a CUDA graph; CUDA events around the stage"}},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) of measured; FP16 operands: "
-                                        "the same nominal dense rate as BF16 (ratio 1)",
-                         "kernel": "k_mlp_fused (persistent tcgen05 network, FP16 operands, FP32 accumulation in TMEM): "
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) of measured",
+                         "kernel": "k_mlp_fused (persistent tcgen05 network, BF16 operands, FP32 accumulation in TMEM): "
                                    "forward pass of 2^22 rows",
                          "flops_per_ray": SUR_FLOPS_PER_RAY, "ms": fwd_ms}}
 
@@ -555,6 +573,8 @@ def main():
     ap.add_argument("--sur-epochs", type=int, default=60, help="stage-1 epochs of the surrogate's training")
     ap.add_argument("--profile-image", default=None,
                     help="VARIANT,MODE,ELEV: render only this image twice (for profilers), e.g. 1,1,20")
+    ap.add_argument("--sur-fp16", action="store_true",
+                    help="with --profile-gemm: the network's FP16 inference (cloak_surrogate_set_precision)")
     ap.add_argument("--profile-gemm", action="store_true",
                     help="run the surrogate network's forward pass (seeded initial weights) twice on 2^20 rows, "
                          "for profilers")
@@ -608,6 +628,7 @@ def main():
     if args.profile_gemm:
         c = ck.Cloak(ck.RADIAL)
         ck.cloak_surrogate_params(c.h, ck.cloak_surrogate_params(c.h))  # creates the network (seeded weights)
+        ck.cloak_surrogate_set_precision(c.h, args.sur_fp16)
         n = 1 << 20
         g = torch.Generator(device="cuda").manual_seed(0)
         x = torch.rand((n, 7), device="cuda", generator=g) * 2 - 1
@@ -615,7 +636,7 @@ def main():
         for _ in range(2):
             ck.cloak_surrogate_forward(c.h, x, y)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_gemm": True, "rows": n, "mean_out": y.mean(0).tolist()}))
+        print(json.dumps({"profile_gemm": True, "fp16": args.sur_fp16, "rows": n, "mean_out": y.mean(0).tolist()}))
         c.close()
         return 0
     if args.profile_batch:

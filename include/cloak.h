@@ -293,9 +293,9 @@ int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long long seed, 
                        void *cuda_stream);
 
 /* ---- learned surrogate of the exit state (the paper has none) -------------------------------------
- * A multilayer perceptron 7 -> 256 -> 256 -> 256 -> 256 -> 5 (GELU, tanh form; FP32 accumulation on the
- * tensor cores; trained with BF16 operands, evaluated in renders and by cloak_surrogate_forward with FP16
- * operands and activations) maps a ray entering the lateral surface r = R2 -- entry height and
+ * A multilayer perceptron 7 -> 256 -> 256 -> 256 -> 256 -> 5 (GELU, tanh form; BF16 operands, FP32
+ * accumulation on the tensor cores; FP16 inference on request, cloak_surrogate_set_precision) maps a
+ * ray entering the lateral surface r = R2 -- entry height and
  * azimuth, the two angles of its vacuum direction in the local (r, theta, z) frame, polarization bit,
  * variant bit, R1/R2 -- to its exit through r = R2: exit height, cos and sin of the exit azimuth's
  * departure from the straight line's, time of flight, and a confidence output (predicted log10 of its
@@ -323,6 +323,13 @@ int cloak_surrogate_set_gate(cloak_t *h, double max_log10_err);
  * the training rays, rays, seconds in total, seconds tracing the training rays, optimiser steps, batch
  * size.  CLOAK_ESTATE without a trained surrogate. */
 int cloak_surrogate_info(cloak_t *h, double info[8]);
+/* Operand precision of the surrogate's inference (renders with CLOAK_SURROGATE and
+ * cloak_surrogate_forward): fp16 = 0, the default, evaluates the network in BF16 like its training;
+ * fp16 = 1 in FP16 (weights, hidden biases, input pairs and activations; FP32 accumulation in both):
+ * 11 significant bits instead of 8 and a faster epilogue.  The setting belongs to the handle's network
+ * (kept across cloak_surrogate_load); a handle without a surrogate gets one with seeded weights first.
+ * The paper has no counterpart. */
+int cloak_surrogate_set_precision(cloak_t *h, int fp16);
 /* Device timing of the last cloak_surrogate_train (host, 4 doubles): milliseconds per optimizer step of
  * stage 1 (batch gather, forward, loss, backward and Adam over one batch, as the training replays it in a
  * CUDA graph; CUDA events around the stage), the same for stage 2, the algorithmic tensor-core flops of a

@@ -64,6 +64,7 @@ SIGNATURES = {
     "cloak_surrogate_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "cloak_surrogate_set_gate": (C.c_int, [C.c_void_p, C.c_double]),
     "cloak_surrogate_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "cloak_surrogate_set_precision": (C.c_int, [C.c_void_p, C.c_int]),
     "cloak_surrogate_train_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "cloak_surrogate_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_long, C.c_int]),
     "cloak_surrogate_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
@@ -288,6 +289,11 @@ def cloak_surrogate_info(h) -> dict:
     buf = (C.c_double * 8)()
     _check(load().cloak_surrogate_info(h, buf))
     return dict(zip(SUR_INFO_KEYS, list(buf)))
+
+
+def cloak_surrogate_set_precision(h, fp16):
+    """Inference operands of the handle's surrogate: False = BF16 (default), True = FP16."""
+    return _check(load().cloak_surrogate_set_precision(h, 1 if fp16 else 0))
 
 
 def cloak_surrogate_train_timing(h) -> dict:

@@ -682,6 +682,7 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
         const void *bufs[3] = {h->sur->X, h->sur->Y, h->sur->elig};
         key = fnv1a(key, bufs, sizeof(bufs));
         key = fnv1a(key, &h->sur->gate, sizeof(h->sur->gate));
+        key = fnv1a(key, &h->sur->inf_f16, sizeof(h->sur->inf_f16));
         const unsigned int lim = ck::wait_limit();  // baked into the captured network launch
         key = fnv1a(key, &lim, sizeof(lim));
     }
@@ -974,6 +975,16 @@ extern "C" int cloak_surrogate_set_gate(cloak_t *h, double max_log10_err) {
     if (!std::isfinite(max_log10_err)) return fail(CLOAK_EINVAL, "gate must be finite");
     if (!h->sur) return fail(CLOAK_ESTATE, "the handle has no surrogate");
     h->sur->gate = (float)max_log10_err;
+    return CLOAK_OK;
+}
+
+extern "C" int cloak_surrogate_set_precision(cloak_t *h, int fp16) {
+    if (!h) return fail(CLOAK_EINVAL, "null handle");
+    if (fp16 != 0 && fp16 != 1) return fail(CLOAK_EINVAL, "fp16 must be 0 (BF16) or 1 (FP16)");
+    int rc = use_device(h);
+    if (rc) return rc;
+    if ((rc = ensure_surrogate(h))) return rc;
+    h->sur->inf_f16 = fp16;
     return CLOAK_OK;
 }
 

@@ -8,37 +8,34 @@
 
 namespace ck {
 
-// one queued ray's network inputs (each as a half-precision pair hi, lo in columns j and SUR_IN + j: the
-// first layer weighs both alike) and whether it entered through the lateral surface (the surrogate's support)
+// one queued ray's network inputs (each as a pair hi, lo in columns j and SUR_IN + j, BF16 or FP16 as f16
+// says: the first layer weighs both alike) and whether it entered through the lateral surface (the
+// surrogate's support)
 __device__ __forceinline__ void sur_feature_row(const Params &p, int mode, const Queue &q, unsigned int k,
-                                                const double d[3], __half *X, unsigned char *elig) {
+                                                const double d[3], uint16_t *X, int f16, unsigned char *elig) {
     const double P[3] = {q.x[k], q.y[k], q.z[k]};
     const bool lateral = fabs(hypot(P[0], P[1]) - p.R2) <= 1e-9 * p.R2 && fabs(P[2]) < p.halfH;
     float x[SUR_IN];
     sur_features(p.R1, p.R2, p.H, p.variant == V_AZIMUTHAL ? 1 : 0, mode, P, d, x);
-    __half *row = X + (size_t)k * 64;
+    uint16_t *row = X + (size_t)k * 64;
 #pragma unroll
-    for (int j = 0; j < SUR_IN; ++j) {
-        const __half hi = __float2half_rn(x[j]);
-        row[j] = hi;
-        row[SUR_IN + j] = __float2half_rn(x[j] - __half2float(hi));
-    }
+    for (int j = 0; j < SUR_IN; ++j) sur_split_pair(x[j], f16, row + j, row + SUR_IN + j);
     elig[k] = lateral ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(256) k_sur_features(Params p, int mode, int spp, unsigned long long seed, Queue q,
-                                                      __half *X, unsigned char *elig) {
+                                                      uint16_t *X, int f16, unsigned char *elig) {
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const long long idx = q.id[k], pix = idx / spp;
         double o[3], d[3];
         camera_ray(p, (int)(pix % p.W), (int)(pix / p.W), (int)(idx - pix * spp), spp, seed, o, d);
-        sur_feature_row(p, mode, q, k, d, X, elig);
+        sur_feature_row(p, mode, q, k, d, X, f16, elig);
     }
 }
 
 __global__ void __launch_bounds__(256) k_sur_features_batch(Params p, const ViewDev *views, int nviews, int spp,
-                                                            unsigned long long seed, Queue q, __half *X,
+                                                            unsigned long long seed, Queue q, uint16_t *X, int f16,
                                                             unsigned char *elig) {
     const unsigned int n = q.count[0];
     for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
@@ -47,7 +44,7 @@ __global__ void __launch_bounds__(256) k_sur_features_batch(Params p, const View
         const int vm = key_vm(q.key[k]);
         Params pv = p;
         pv.variant = vm >> 1;
-        sur_feature_row(pv, vm & 1, q, k, d, X, elig);
+        sur_feature_row(pv, vm & 1, q, k, d, X, f16, elig);
     }
 }
 
@@ -158,13 +155,13 @@ static int sm_count() {
 
 cudaError_t launch_sur_features(const Params &p, int mode, int spp, unsigned long long seed, const Queue &q, SurNet *s,
                                 cudaStream_t st) {
-    k_sur_features<<<sm_count() * 8, 256, 0, st>>>(p, mode, spp, seed, q, s->X, s->elig);
+    k_sur_features<<<sm_count() * 8, 256, 0, st>>>(p, mode, spp, seed, q, s->X, s->inf_f16, s->elig);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sur_features_batch(const Params &p, const ViewDev *views, int nviews, int spp,
                                       unsigned long long seed, const Queue &q, SurNet *s, cudaStream_t st) {
-    k_sur_features_batch<<<sm_count() * 8, 256, 0, st>>>(p, views, nviews, spp, seed, q, s->X, s->elig);
+    k_sur_features_batch<<<sm_count() * 8, 256, 0, st>>>(p, views, nviews, spp, seed, q, s->X, s->inf_f16, s->elig);
     return cudaGetLastError();
 }
 

@@ -14,14 +14,14 @@
 //     thread doing both spent longer per chunk on its barrier waits and bookkeeping than the tensor core
 //     spent on the chunk's four MMAs;
 //   * 16 epilogue warps take the jobs in the same order (warp w: TMEM lanes 32 (w % 4) .., column quarter
-//     w / 4): they read the tile's accumulators once its MMAs completed, add the bias (half precision, read
-//     through L1), apply GELU in half-precision pairs and write the activations back into the swizzled
-//     shared-memory layout as the tile's next A operand (the last layer writes the FP32 outputs), then
-//     arrive on the tile's barrier.
-// Operands are FP16 (weights, inputs as (hi, lo) pairs, activations; FP32 accumulation): the GELU is
-// evaluated in half-precision pairs anyway, so its result is stored as it is -- no conversion back through
-// FP32 to BF16, and 11 significant bits instead of 8.  (Training keeps BF16, whose range the gradients
-// need; the inference copies are refreshed from the FP32 masters with the BF16 ones.)
+//     w / 4): they read the tile's accumulators once its MMAs completed, add the bias (read through L1),
+//     apply GELU in half-precision pairs and write the activations back into the swizzled shared-memory
+//     layout as the tile's next A operand (the last layer writes the FP32 outputs), then arrive on the
+//     tile's barrier.
+// Operands (weights, inputs as (hi, lo) pairs, activations) are BF16, the precision the network is trained
+// in, or -- selected per network -- FP16: the GELU is evaluated in half-precision pairs in both forms, and
+// in FP16 its result is stored as it is (no conversion back through FP32 to BF16: faster, and 11
+// significant bits instead of 8).  Accumulation is FP32 in both.
 // Barriers: full/empty per ring slot; per tile the inputs' barrier, "MMAs done" (committed by the MMA
 // warp) and "activations ready" (16 arrivals).  Shared memory: activations 2 x 64 KB, weight ring
 // 3 x 32 KB.  Every mbarrier wait is bounded; on a timeout the kernel sets the error flag, lets its MMAs and
@@ -45,8 +45,8 @@ constexpr int F_SLOTS = 3;                                     // weight ring de
 constexpr size_t F_SMEM = 1024 + F_ACT_BYTES + F_SLOTS * F_RING_SLOT;
 
 struct FusedArgs {
-    const __half *bias_h[SUR_L - 1]; // hidden layers' biases in half precision
-    const float *bias_out;       // the output layer's biases (FP32)
+    const float *bias[SUR_L];    // FP32 biases (the BF16 form, and the output layer of both)
+    const __half *bias_h[SUR_L - 1]; // hidden layers' biases in half precision (the FP16 form)
     float *Y;                    // outputs, 16 FP32 per row
     long long n;                 // rows of X and Y (a multiple of 128)
     const unsigned int *m_count; // optional live row count
@@ -54,6 +54,7 @@ struct FusedArgs {
     unsigned int wait_limit;     // polls of the waits that decide a timeout
 };
 
+template <bool F16>
 __global__ void __launch_bounds__(F_THREADS, 1)
     k_mlp_fused(const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtensorMap tW0,
                 const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
@@ -156,7 +157,8 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                 for (int job = 0; job < 2 * SUR_L && ok; ++job) {
                     const int l = job >> 1, t = job & 1;
                     const int nk = l == 0 ? 1 : 4;
-                    const uint32_t idesc = f16_idesc(l == SUR_L - 1 ? 16 : SUR_W), d_tmem = tmem + t * 256;
+                    const uint32_t idesc = F16 ? f16_idesc(l == SUR_L - 1 ? 16 : SUR_W) : bf16_idesc(l == SUR_L - 1 ? 16 : SUR_W);
+                    const uint32_t d_tmem = tmem + t * 256;
                     for (int j = 0; j < nk; ++j) {
                         ok = mbar_wait(smem_u32(&full_bar[s]), ph, lim);
                         if (ok && j == 0) {
@@ -225,19 +227,32 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                               "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
                             : "r"(taddr + (uint32_t)c));
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        // GELU in half precision into the 128-byte-swizzled K-major layout of chunk c / 64: 16-byte units
+                        // GELU, into the 128-byte-swizzled K-major layout of chunk c / 64: 16-byte units
                         // (c % 64) / 8 .. + 3 of row r, each XOR-ed with r % 8
                         uint32_t pk[16];
-                        // the biases of these 32 columns as half pairs, 16 bytes (8 halves) per load through L1
-                        const uint4 *b8 = reinterpret_cast<const uint4 *>(a.bias_h[l] + c);  // 16-byte aligned
+                        if constexpr (F16) {
+                            // the biases of these 32 columns as half pairs, 8 halves per 16-byte load through L1
+                            const uint4 *b8 = reinterpret_cast<const uint4 *>(a.bias_h[l] + c);  // 16-byte aligned
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const uint4 bv = __ldg(b8 + i);
-                            const uint32_t bw[4] = {bv.x, bv.y, bv.z, bv.w};
+                            for (int i = 0; i < 4; ++i) {
+                                const uint4 bv = __ldg(b8 + i);
+                                const uint32_t bw[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-                            for (int k2 = 0; k2 < 4; ++k2)
-                                pk[4 * i + k2] = gelu2_f16(__uint_as_float(u[8 * i + 2 * k2]), __uint_as_float(u[8 * i + 2 * k2 + 1]),
-                                                           *reinterpret_cast<const __half2 *>(&bw[k2]));
+                                for (int k2 = 0; k2 < 4; ++k2)
+                                    pk[4 * i + k2] = gelu2_f16(__uint_as_float(u[8 * i + 2 * k2]),
+                                                               __uint_as_float(u[8 * i + 2 * k2 + 1]),
+                                                               *reinterpret_cast<const __half2 *>(&bw[k2]));
+                            }
+                        } else {
+                            // FP32 biases, 4 per 16-byte load through L1
+                            const float4 *b4 = reinterpret_cast<const float4 *>(a.bias[l] + c);  // 16-byte aligned
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const float4 bv = __ldg(b4 + i);
+                                pk[2 * i] = gelu2_bf16(__uint_as_float(u[4 * i]) + bv.x, __uint_as_float(u[4 * i + 1]) + bv.y);
+                                pk[2 * i + 1] =
+                                    gelu2_bf16(__uint_as_float(u[4 * i + 2]) + bv.z, __uint_as_float(u[4 * i + 3]) + bv.w);
+                            }
                         }
                         unsigned char *chunk = act + (t * 4 + c / 64) * F_ACT_CHUNK + (r >> 3) * 1024 + (r & 7) * 128;
                         const int u0 = (c & 63) >> 3;
@@ -259,10 +274,10 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                         float4 *y = (float4 *)(a.Y + row * 16);
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            y[i] = make_float4(__uint_as_float(u[4 * i]) + __ldg(a.bias_out + 4 * i),
-                                               __uint_as_float(u[4 * i + 1]) + __ldg(a.bias_out + 4 * i + 1),
-                                               __uint_as_float(u[4 * i + 2]) + __ldg(a.bias_out + 4 * i + 2),
-                                               __uint_as_float(u[4 * i + 3]) + __ldg(a.bias_out + 4 * i + 3));
+                            y[i] = make_float4(__uint_as_float(u[4 * i]) + __ldg(a.bias[SUR_L - 1] + 4 * i),
+                                               __uint_as_float(u[4 * i + 1]) + __ldg(a.bias[SUR_L - 1] + 4 * i + 1),
+                                               __uint_as_float(u[4 * i + 2]) + __ldg(a.bias[SUR_L - 1] + 4 * i + 2),
+                                               __uint_as_float(u[4 * i + 3]) + __ldg(a.bias[SUR_L - 1] + 4 * i + 3));
                     }
                 }
                 // the shared-memory writes must be visible to the tensor cores' (async) reads, and the TMEM
@@ -294,11 +309,15 @@ cudaError_t mlp_fused_prepare() {
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaDeviceGetAttribute(&g_fused_sms[dev], cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, k_mlp_fused);
-        if (e != cudaSuccess) return e;
-        if ((size_t)(optin - (int)fa.sharedSizeBytes) < F_SMEM) return cudaErrorInvalidValue;
-        return cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM);
+        for (auto kern : {k_mlp_fused<false>, k_mlp_fused<true>}) {
+            cudaFuncAttributes fa;
+            cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+            if (e != cudaSuccess) return e;
+            if ((size_t)(optin - (int)fa.sharedSizeBytes) < F_SMEM) return cudaErrorInvalidValue;
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM)) != cudaSuccess)
+                return e;
+        }
+        return cudaSuccess;
     });
 }
 
@@ -311,10 +330,13 @@ cudaError_t launch_mlp_fused(SurNet *s, long long n, const unsigned int *m_count
     const int sms = g_fused_sms[dev];
     if (n <= 0 || n % 128) return cudaErrorInvalidValue;
     CUtensorMap tx;
-    if (make_tmap_f16(&tx, s->X, (int)n, 64, GEMM_TILE_M) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const bool f16 = s->inf_f16 != 0;
+    if ((f16 ? make_tmap_f16(&tx, s->X, (int)n, 64, GEMM_TILE_M) : make_tmap_bf16(&tx, s->X, (int)n, 64, GEMM_TILE_M)) !=
+        CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     FusedArgs a;
+    for (int l = 0; l < SUR_L; ++l) a.bias[l] = s->b[l];
     for (int l = 0; l < SUR_L - 1; ++l) a.bias_h[l] = s->bh[l];
-    a.bias_out = s->b[SUR_L - 1];
     a.Y = s->Y;
     a.n = n;
     a.m_count = m_count;
@@ -322,7 +344,10 @@ cudaError_t launch_mlp_fused(SurNet *s, long long n, const unsigned int *m_count
     a.wait_limit = wait_limit();
     const long long pairs = (n + 255) / 256;
     const int grid = (int)std::min<long long>(pairs, (long long)sms);
-    k_mlp_fused<<<grid, F_THREADS, F_SMEM, st>>>(tx, s->tWh[0], s->tWh[1], s->tWh[2], s->tWh[3], s->tWh[4], a);
+    if (f16)
+        k_mlp_fused<true><<<grid, F_THREADS, F_SMEM, st>>>(tx, s->tWh[0], s->tWh[1], s->tWh[2], s->tWh[3], s->tWh[4], a);
+    else
+        k_mlp_fused<false><<<grid, F_THREADS, F_SMEM, st>>>(tx, s->tWb[0], s->tWb[1], s->tWb[2], s->tWb[3], s->tWb[4], a);
     return cudaGetLastError();
 }
 

@@ -12,6 +12,20 @@
 
 namespace ck {
 
+// x as an unevaluated pair hi + lo of BF16 (f16 = 0) or FP16 (f16 = 1) numbers (bit patterns), the network's
+// input representation: the first layer weighs both parts alike
+__device__ __forceinline__ void sur_split_pair(float x, int f16, uint16_t *hi, uint16_t *lo) {
+    if (f16) {
+        const __half h = __float2half_rn(x), l = __float2half_rn(x - __half2float(h));
+        *hi = __half_as_ushort(h);
+        *lo = __half_as_ushort(l);
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x), l = __float2bfloat16_rn(x - __bfloat162float(h));
+        *hi = __bfloat16_as_ushort(h);
+        *lo = __bfloat16_as_ushort(l);
+    }
+}
+
 // local frame at azimuth phi
 __device__ __forceinline__ void sur_frame(double phi, double rh[3], double th[3]) {
     double s, c;

@@ -19,6 +19,7 @@
 
 #include "cloak.h"
 #include "mlp_tc.cuh"
+#include "sur_physics.cuh"
 #include "surrogate.h"
 #include "tc_ptx.cuh"
 #include "wavefront.cuh"
@@ -194,17 +195,12 @@ __global__ void k_sur_adam(SurDims dm, float *W, float *b, float *mW, float *vW,
     }
 }
 
-// FP32 inputs (n x 7) into the padded half-precision input rows of the inference scratch (hi, lo pairs)
-__global__ void k_sur_pack(const float *x, long long n, __half *X) {
+// FP32 inputs (n x 7) into the padded input rows of the inference scratch as (hi, lo) pairs, BF16 or FP16
+__global__ void k_sur_pack(const float *x, long long n, uint16_t *X, int f16) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
 #pragma unroll
-    for (int j = 0; j < SUR_IN; ++j) {
-        const float v = x[i * SUR_IN + j];
-        const __half hi = __float2half_rn(v);
-        X[(size_t)i * 64 + j] = hi;
-        X[(size_t)i * 64 + SUR_IN + j] = __float2half_rn(v - __half2float(hi));
-    }
+    for (int j = 0; j < SUR_IN; ++j) sur_split_pair(x[i * SUR_IN + j], f16, X + (size_t)i * 64 + j, X + (size_t)i * 64 + SUR_IN + j);
 }
 __global__ void k_sur_unpack(const float *Y, long long n, float *y) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -377,7 +373,7 @@ cudaError_t sur_ensure_inference(SurNet *s, long long rows) {
     cudaError_t e = cudaMalloc(&s->inf_arena, xb + yb + eb);
     if (e != cudaSuccess) return e;
     char *p = s->inf_arena;
-    s->X = (__half *)p; p += xb;
+    s->X = (uint16_t *)p; p += xb;
     s->Y = (float *)p; p += yb;
     s->elig = (unsigned char *)p;
     // columns 14..63 stay zero; cleared before any stream uses the buffer (cudaMemset runs on the legacy default
@@ -680,7 +676,7 @@ int sur_forward_rows(SurNet *s, const float *dev_x, long long n, float *dev_y, c
     const long long rows = (n + 127) / 128 * 128;
     unsigned int *err = s->err;  // this network's own timeout flag
     cudaMemsetAsync(err, 0, 4, st);
-    k_sur_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dev_x, n, s->X);
+    k_sur_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dev_x, n, s->X, s->inf_f16);
     if ((e = sur_forward(s, rows, nullptr, st)) != cudaSuccess) { why = cudaGetErrorString(e); return CLOAK_ECUDA; }
     k_sur_unpack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->Y, n, dev_y);
     unsigned int h = 0;

@@ -76,7 +76,8 @@ struct SurNet {
     // hidden activations never leave the SM (mlp_fused.cu)
     long long inf_rows;
     char *inf_arena;
-    __half *X;  // half-precision input pairs (hi, lo), n x 64
+    uint16_t *X;  // input pairs (hi, lo), n x 64, BF16 or FP16 as the inference precision is
+    int inf_f16;  // inference operands: 0 = BF16 (the training precision, default), 1 = FP16
     float *Y;
     unsigned char *elig;
 };
@@ -85,7 +86,7 @@ struct SurNet {
 SurNet *sur_create(double R1, double R2, double H, unsigned long long seed, const char **why);
 void sur_destroy(SurNet *s);
 cudaError_t sur_refresh_bf16(SurNet *s, cudaStream_t st);  // Wb / WTb / Wh / bh from the FP32 masters
-// forward pass of n rows of X (half-precision input pairs, n x 64) into Y (FP32, n x 16); n % 128 == 0;
+// forward pass of n rows of X (input pairs, n x 64) into Y (FP32, n x 16); n % 128 == 0;
 // m_count: optional device row count (rows at or beyond it are skipped tile by tile)
 cudaError_t sur_forward(SurNet *s, long long n, const unsigned int *m_count, cudaStream_t st);
 // the same as one persistent tcgen05 kernel (mlp_fused.cu)

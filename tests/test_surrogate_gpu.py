@@ -82,26 +82,30 @@ def make_handle(ck, params):
     return h
 
 
-def test_forward_matches_oracle(ck):
+@pytest.mark.parametrize("fp16", [False, True])
+def test_forward_matches_oracle(ck, fp16):
     import torch
     params = init_params(1, out_scale=1.0)
     h = make_handle(ck, params)
+    ck.cloak_surrogate_set_precision(h.h, fp16)
     rng = np.random.default_rng(2)
     n = 1000
     x = rng.uniform(-1, 1, (n, 7)).astype(np.float32)
     y = torch.zeros((n, 5), dtype=torch.float32, device="cuda")
     ck.cloak_surrogate_forward(h.h, torch.from_numpy(x).cuda(), y)
     got = y.cpu().numpy().astype(np.float64)
-    ref = O.mlp_forward(DIMS, f16_inference_params(params), x.astype(np.float64))
-    # the fused inference kernel takes FP16 weights and hidden biases (the reference uses the same rounded
-    # values), the inputs as FP16 (hi, lo) pairs (about 22 bits), and rounds each of the 4 hidden
-    # activations to FP16 (the GELU itself in half-precision pairs, hardware tanh with relative error
-    # ~2^-11), accumulating in FP32; with unit-gain layers the output error stays within a few units of
-    # 2^-11 times the output scale
+    scale_u = F16_U if fp16 else BF16_U
+    ref = O.mlp_forward(DIMS, f16_inference_params(params) if fp16 else bf16_weights(params), x.astype(np.float64))
+    # BF16 (default): weights rounded to BF16 as the reference has them, inputs as BF16 (hi, lo) pairs
+    # (about 16 bits), each of the 4 hidden activations rounded to BF16 (relative error <= 2^-9), FP32
+    # accumulation.  FP16: weights and hidden biases rounded to FP16 (the reference uses the same values),
+    # inputs as FP16 pairs (about 22 bits), activations rounded to FP16 (2^-11).  The GELU runs in
+    # half-precision pairs in both (hardware tanh, relative error ~2^-11).  With unit-gain layers the output
+    # error stays within a few units of the activations' unit roundoff times the output scale.
     scale = np.abs(ref).max()
     err = np.abs(got - ref).max()
-    print(f"forward error {err / scale / F16_U:.2f} units of 2^-11 of the output scale")
-    assert err <= 8 * F16_U * scale, (err, scale)
+    print(f"forward error ({'FP16' if fp16 else 'BF16'}) {err / scale / scale_u:.2f} units roundoff of the output scale")
+    assert err <= 8 * scale_u * scale, (err, scale)
     assert np.isfinite(got).all()
     h.close()
 
@@ -217,10 +221,12 @@ def _handles(ck, trained_h, variant, elev, W, H, precision):
     return c
 
 
-@pytest.mark.parametrize("variant,mode,elev", [(0, 1, 20.0), (1, 1, 0.0), (1, 0, 45.0), (0, 0, 20.0)])
-def test_surrogate_records_keep_invariants_and_match_oracle(ck, trained, tmp_path, variant, mode, elev):
+@pytest.mark.parametrize("variant,mode,elev,fp16", [(0, 1, 20.0, False), (1, 1, 0.0, False), (1, 0, 45.0, False),
+                                                    (0, 0, 20.0, False), (0, 1, 20.0, True), (1, 1, 0.0, True)])
+def test_surrogate_records_keep_invariants_and_match_oracle(ck, trained, tmp_path, variant, mode, elev, fp16):
     """Rays finished by the surrogate leave through r = R2 with k_z and L_z of the camera ray (exact), and
-    their exit direction agrees with the FP64 oracle within the gate; all other rays are the integrator's."""
+    their exit direction agrees with the FP64 oracle within the gate; all other rays are the integrator's.
+    Inference in BF16 (the default) and in FP16."""
     import torch
     from paper_1209_6038_gb300 import inputs
     h, _ = trained
@@ -229,6 +235,7 @@ def test_surrogate_records_keep_invariants_and_match_oracle(ck, trained, tmp_pat
     W, H = 96, 54
     c = _handles(ck, h, variant, elev, W, H, ck.SURROGATE)
     ck.cloak_surrogate_load(c.h, path)
+    ck.cloak_surrogate_set_precision(c.h, fp16)
     ck.cloak_surrogate_set_gate(c.h, -2.5)
     recs = ck.records_to_numpy(c.render_records(mode, 1, 0))
     ref = _handles(ck, h, variant, elev, W, H, ck.FP64)
