@@ -790,7 +790,7 @@ def main():
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
         e2e_s = replicas.max_over_ranks(statistics.mean(e2e_ms) / 1e3, device="cuda")  # the slowest rank's
         e2e = replicas.whole_job_rate(rays_step, e2e_s, ws)
-        out["e2e"] = {"value": e2e, "unit": UNIT,
+        out["e2e"] = {"value": e2e, "unit": UNIT, "ms_per_step": [round(x, 2) for x in e2e_ms],
                       "h2d_bytes_per_step": VIEW_TABLE_BYTES * len(w.images) if args.schedule == "batched" else 0,
                       "d2h_bytes_per_step": sum(im.numel() * 4 for im in imgs),
                       "note": "inputs are camera and integrator parameters (host structs passed through the C ABI; the "
