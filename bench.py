@@ -867,6 +867,9 @@ def main():
         nr, dt, orecs = run_oracle_sample(w, args.cpu_pixels, cores)
         # one core on a sample a twelfth the size (seeded the same way): the per-core rate
         nr1, dt1, _ = run_oracle_sample(w, max(1, args.cpu_pixels // 12), 1)
+        # the small workload (radial e, 128x96 x 1 spp, RK4 h = 1e-3) in full, all cores
+        ws_small = inputs.SMALL
+        nrs, dts, _ = run_oracle_sample(ws_small, ws_small.width * ws_small.height, cores)
         g = np.concatenate(gpu_samples)
         o = np.concatenate(orecs)
         ref, lim64, und = reference_records(w, o, args.cpu_pixels)
@@ -879,7 +882,10 @@ def main():
                                          f"{len(w.images)} images ({nr} rays), {dt:.1f} s",
                                "single_core": {"value": nr1 / dt1, "unit": UNIT, "cores": 1,
                                                "sample": f"{max(1, args.cpu_pixels // 12)} seeded pixels x {w.spp} spp "
-                                                         f"per image ({nr1} rays), {dt1:.1f} s"}}
+                                                         f"per image ({nr1} rays), {dt1:.1f} s"},
+                               "small_workload_full": {"value": nrs / dts, "unit": UNIT, "cores": cores,
+                                                       "sample": f"{ws_small.name}, every pixel ({nrs} rays), "
+                                                                 f"{dts:.2f} s"}}
         e_det = err[~und[fin]]
         e_und = err[und[fin]]
         out["accuracy_vs_oracle"] = {
