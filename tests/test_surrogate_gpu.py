@@ -312,9 +312,11 @@ def test_surrogate_gains_over_the_integrator(ck, trained, tmp_path):
     assert tsu < t64
 
 
-def test_batched_surrogate_render_matches_single_renders(ck, trained, tmp_path):
+@pytest.mark.parametrize("fp16", [False, True])
+def test_batched_surrogate_render_matches_single_renders(ck, trained, tmp_path, fp16):
     """The learned surrogate inside the batched persistent render (one queue for all views, the network and
-    gate on every queued ray, the integrator on the rest): each view equals its own surrogate render."""
+    gate on every queued ray, the integrator on the rest): each view equals its own surrogate render, with
+    the network in BF16 (default) and in FP16."""
     import torch
     h, _ = trained
     path = str(tmp_path / "s.bin")
@@ -323,6 +325,7 @@ def test_batched_surrogate_render_matches_single_renders(ck, trained, tmp_path):
     for variant, pol, elev, W, H in ((1, 1, 20.0, 96, 64), (0, 0, 0.0, 80, 48), (1, 0, 45.0, 64, 64), (0, 1, 10.0, 72, 40)):
         c = _handles(ck, h, variant, elev, W, H, ck.SURROGATE)
         ck.cloak_surrogate_load(c.h, path)
+        ck.cloak_surrogate_set_precision(c.h, fp16)
         ck.cloak_surrogate_set_gate(c.h, -3.0)
         refs.append(c.render(pol, 2, 4).cpu().numpy())
         from paper_1209_6038_gb300 import inputs
@@ -331,6 +334,7 @@ def test_batched_surrogate_render_matches_single_renders(ck, trained, tmp_path):
         c.close()
     b = ck.Cloak(ck.RADIAL).integrator(ck.DP45, 1e-9, ck.SURROGATE, 1_000_000).schedule(ck.SCHED_WAVEFRONT)
     ck.cloak_surrogate_load(b.h, path)
+    ck.cloak_surrogate_set_precision(b.h, fp16)
     ck.cloak_surrogate_set_gate(b.h, -3.0)
     for _ in range(2):  # capture, then replay of the graph
         ck.cloak_render_batch(b.h, views, 2, 4)
