@@ -922,7 +922,7 @@ def main():
                 # two timed renders per candidate (the faster counts): one-render timings differ by ~3 % from
                 # call to call, as much as the knobs' effects near the optimum
                 sched, tune_ms = autotune.tune_schedule(mixed_runner.h, mixed_runner.step, key=f"full12|{key}",
-                                                        reps=2, use_cache=False)
+                                                        reps=2, use_cache=False, start=autotune.MIXED_SCHEDULE)
                 tune_s = time.perf_counter() - t0
             mms, _, mstages = timed(mixed_runner, 1, 2, collective=False)
             mixed_runner.close()

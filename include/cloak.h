@@ -135,7 +135,8 @@ int cloak_set_formulation(cloak_t *h, int formulation);
 enum { CLOAK_ANALYZER_NONE = 0, CLOAK_ANALYZER_RIGHT = 1, CLOAK_ANALYZER_UP = 2 };
 int cloak_set_analyzer(cloak_t *h, int analyzer);
 /* Kernel schedule (CLOAK_SCHED_*).  packet: threads per block of the persistent integration kernel
- * (32, 64, 96 or 128; 0 = default 128).  steps_per_round: reserved (0): lanes refill one by one from
+ * (32, 64, 96 or 128; 0 = the precision's default: 128 for CLOAK_FP64, 64 for CLOAK_MIXED and
+ * CLOAK_MIXED_FF).  steps_per_round: reserved (0): lanes refill one by one from
  * the queue, there are no compaction rounds. */
 int cloak_set_schedule(cloak_t *h, int schedule, int packet, int steps_per_round);
 /* Step-schedule knobs of the wavefront and batched integration (the paper has no counterpart; images and
@@ -143,7 +144,9 @@ int cloak_set_schedule(cloak_t *h, int schedule, int packet, int steps_per_round
  * persistent kernel, each on an SM of its own, take the slowest rays first -- those passing closest to
  * the axis; reserve_per_thread (1..8, default 1) rays are reserved for them per thread; cost_scale
  * (1..16, default 4) sets the resolution of the sort's cost buckets, bucket = cost_scale x -log2 |L_z|
- * (64 buckets).  CLOAK_EINVAL outside these ranges.  The autotuner (autotune.py) searches them. */
+ * (64 buckets).  CLOAK_EINVAL outside these ranges.  Until this call is made on a handle, CLOAK_MIXED and
+ * CLOAK_MIXED_FF use their own defaults (16, 4, 3): the slow near-axis rays weigh more in their shorter
+ * steps.  The autotuner (autotune.py) searches them. */
 int cloak_set_schedule_tuning(cloak_t *h, int long_ray_blocks, int reserve_per_thread, double cost_scale);
 
 /* Per-stage device timing (CUDA events on the call's stream).  on != 0 enables it for later calls.

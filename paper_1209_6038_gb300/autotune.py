@@ -17,6 +17,8 @@ import os
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune.json")
 CANDIDATES = (32, 64, 96, 128)  # threads per block of the persistent kernel (at most 128)
 DEFAULT_SCHEDULE = {"packet": 128, "long_ray_blocks": 4, "reserve_per_thread": 1, "cost_scale": 4.0}
+# the library's defaults for the mixed precisions (CLOAK_MIXED, CLOAK_MIXED_FF) while no schedule is set
+MIXED_SCHEDULE = {"packet": 64, "long_ray_blocks": 16, "reserve_per_thread": 4, "cost_scale": 3.0}
 SEARCH = (("packet", CANDIDATES), ("long_ray_blocks", (0, 2, 4, 8, 16)), ("cost_scale", (2.0, 3.0, 4.0, 6.0, 8.0)),
           ("reserve_per_thread", (1, 2, 4)))
 
@@ -64,11 +66,12 @@ def apply(cloak, sched: dict):
 
 
 def tune_schedule(cloak, run, key: str, reps: int = 1, use_cache: bool = True, search=SEARCH, timer=None,
-                  setter=None, device_name=None):
+                  setter=None, device_name=None, start=None):
     """cloak: paper_1209_6038_gb300.cloak.Cloak (wavefront schedule); run(): one render on the current
     stream.  Returns (best schedule, {"knob=value": ms}).  The best schedule is left set on the handle.
-    timer(run, reps) -> ms, setter(cloak, schedule) and device_name replace the CUDA-event timing, the
-    handle call and the GPU's name (the search itself is host logic, tested without a GPU)."""
+    start: the schedule the search begins from (DEFAULT_SCHEDULE if None; MIXED_SCHEDULE suits the mixed
+    precisions).  timer(run, reps) -> ms, setter(cloak, schedule) and device_name replace the CUDA-event
+    timing, the handle call and the GPU's name (the search itself is host logic, tested without a GPU)."""
     timer = timer or _time
     setter = setter or apply
     if device_name is None:
@@ -80,7 +83,7 @@ def tune_schedule(cloak, run, key: str, reps: int = 1, use_cache: bool = True, s
         if hit:
             setter(cloak, hit["schedule"])
             return hit["schedule"], hit["ms"]
-    best = dict(DEFAULT_SCHEDULE)
+    best = dict(start or DEFAULT_SCHEDULE)
     setter(cloak, best)
     times = {"default": timer(run, reps)}
     best_ms = times["default"]

@@ -29,6 +29,7 @@ struct cloak {
     int schedule, packet, steps_per_round;
     int long_ray_blocks, reserve_per_thread;  // schedule knobs (cloak_set_schedule_tuning)
     double cost_scale;
+    int tuned;  // the knobs were set explicitly; until then the mixed precisions use their own defaults
     int analyzer;     // CLOAK_ANALYZER_*
     int formulation;  // CLOAK_FORM_*
     int device;
@@ -75,6 +76,13 @@ static int cuda_fail(cudaError_t e, const char *where) {
 }
 static bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
+// Threads per block of the persistent integration kernel: the handle's setting, or the precision's default
+// (128 for FP64, 64 for the mixed precisions)
+static int eff_packet(const cloak *h) {
+    if (h->packet > 0) return h->packet;
+    return h->precision == CLOAK_MIXED || h->precision == CLOAK_MIXED_FF ? 64 : 0;
+}
+
 // Camera frame and material constants for the kernels.
 static int make_params(const cloak *h, ck::Params &p) {
     memset(&p, 0, sizeof(p));
@@ -112,9 +120,15 @@ static int make_params(const cloak *h, ck::Params &p) {
     p.band_limf = p.mixed_band > 0.0 ? (float)(p.R1 + p.mixed_band) : 0.f;
     p.h_or_tol = h->h_or_tol;
     p.max_steps = h->max_steps;
-    p.long_ray_blocks = h->long_ray_blocks;
-    p.reserve_per_thread = h->reserve_per_thread;
-    p.cost_scale = (float)h->cost_scale;
+    if (h->tuned || !(h->precision == CLOAK_MIXED || h->precision == CLOAK_MIXED_FF)) {
+        p.long_ray_blocks = h->long_ray_blocks;
+        p.reserve_per_thread = h->reserve_per_thread;
+        p.cost_scale = (float)h->cost_scale;
+    } else {  // the mixed precisions' defaults: the best settings the tuner found on the twelve-view step
+        p.long_ray_blocks = 16;
+        p.reserve_per_thread = 4;
+        p.cost_scale = 3.0f;
+    }
     double w[3], u[3], v[3];
     for (int i = 0; i < 3; ++i) w[i] = h->target[i] - h->eye[i];
     double l = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
@@ -200,7 +214,7 @@ static int run_wavefront(cloak *h, const ck::Params &p, int pol, int spp, unsign
     if (ev) cudaEventRecord(ev[0], st);
     cudaError_t e = cudaMemsetAsync(q.count, 0, ck::QUEUE_HEADER_BYTES, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    e = ck::launch_wavefront(p, pol, spp, seed, q, recs ? nullptr : samples, recs, h->packet, st, ev, hk);
+    e = ck::launch_wavefront(p, pol, spp, seed, q, recs ? nullptr : samples, recs, eff_packet(h), st, ev, hk);
     if (e != cudaSuccess) return cuda_fail(e, "wavefront launch");
     if (!recs) {
         e = ck::launch_resolve(p.W * p.Hp, spp, samples, out, st);
@@ -447,6 +461,7 @@ int cloak_set_schedule_tuning(cloak_t *h, int long_ray_blocks, int reserve_per_t
     h->long_ray_blocks = long_ray_blocks;
     h->reserve_per_thread = reserve_per_thread;
     h->cost_scale = cost_scale;
+    h->tuned = 1;
     return CLOAK_OK;
 }
 
@@ -674,7 +689,7 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
     unsigned long long key = 1469598103934665603ull;
     key = fnv1a(key, table.data(), tbytes);
     key = fnv1a(key, &p, sizeof(p));
-    int extra[5] = {spp, h->packet, nviews, h->timing, sur ? 1 : 0};
+    int extra[5] = {spp, eff_packet(h), nviews, h->timing, sur ? 1 : 0};
     key = fnv1a(key, extra, sizeof(extra));
     key = fnv1a(key, &seed, sizeof(seed));
     key = fnv1a(key, &h->scratch, sizeof(h->scratch));
@@ -733,7 +748,7 @@ static int batch_core(cloak_t *h, const cloak_view *views, int nviews, int spp, 
             sctx.nviews = nviews;
         }
         cudaError_t e2 = e1 == cudaSuccess ? ck::launch_batch(p, (const ck::ViewDev *)h->batch_dev, nviews, spp, seed,
-                                                             total, total_pix, q, samples, h->packet, h->cap_stream,
+                                                             total, total_pix, q, samples, eff_packet(h), h->cap_stream,
                                                              h->timing ? h->ev : nullptr, sur ? &hook : nullptr)
                                            : e1;
         cudaGraph_t graph = nullptr;
@@ -843,7 +858,7 @@ extern "C" int cloak_render_panel(cloak_t *h, int panel, int spp, unsigned long 
         }
         ck::Queue q2;
         ck::carve_queue((char *)h->refl_scratch, 2 * total, q2, &rs);
-        cudaError_t e = ck::launch_reflections(p, q, q2, rs, 2 * total, h->packet, st);
+        cudaError_t e = ck::launch_reflections(p, q, q2, rs, 2 * total, eff_packet(h), st);
         if (e != cudaSuccess) return cuda_fail(e, "reflections");
     }
     cudaError_t e = tof ? ck::launch_tof_resolve(p, (const ck::ViewDev *)h->batch_dev, spp, seed, (long long)npix,
@@ -912,7 +927,7 @@ extern "C" int cloak_render_noalloc(cloak_t *h, int polarization, int spp, unsig
     // the queue header (counters, sort bins) must start at zero; everything else is written before it is read
     cudaError_t e = cudaMemsetAsync(q.count, 0, ck::QUEUE_HEADER_BYTES, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    e = ck::launch_wavefront(p, polarization, spp, seed, q, samples, nullptr, h->packet, st, nullptr);
+    e = ck::launch_wavefront(p, polarization, spp, seed, q, samples, nullptr, eff_packet(h), st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "wavefront launch");
     e = ck::launch_resolve(p.W * p.Hp, spp, samples, (float4 *)dev_rgba, st);
     if (e != cudaSuccess) return cuda_fail(e, "resolve launch");

@@ -79,3 +79,17 @@ def test_cache_hit_skips_the_search_and_is_per_device(cache):
     autotune.tune_schedule(h2, lambda: None, "k", timer=timer2, setter=setter, device_name="gpu A",
                            use_cache=False)
     assert len(calls2) == n  # use_cache=False searches again
+
+
+def test_search_starts_from_the_given_schedule(cache):
+    h = FakeHandle()
+    timer, calls = make_timer(h, lambda s: 1.0)
+    best, times = autotune.tune_schedule(h, lambda: None, "mixed", timer=timer, setter=setter, device_name="fake",
+                                         start=autotune.MIXED_SCHEDULE)
+    assert h.history[0] == autotune.MIXED_SCHEDULE and calls[0] == autotune.MIXED_SCHEDULE
+    assert best == autotune.MIXED_SCHEDULE  # a flat cost keeps the start
+    n_cand = sum(len([v for v in vals if v != autotune.MIXED_SCHEDULE[k]]) for k, vals in autotune.SEARCH)
+    assert len(times) == 1 + n_cand
+    # every start value is one of the search's candidates, so the search can come back to it
+    for k, vals in autotune.SEARCH:
+        assert autotune.MIXED_SCHEDULE[k] in vals and autotune.DEFAULT_SCHEDULE[k] in vals

@@ -137,3 +137,32 @@ def test_mixed_other_geometries(ck, geom, variant, band):
     stats = check_mixed(rec, name, spp)
     assert stats["pixels_differing"] <= 5e-3, stats
     print(name, band, stats)
+
+
+@pytest.mark.parametrize("band", BANDS)
+def test_mixed_default_schedule_reorders_only(ck, band):
+    """The mixed precisions' own schedule defaults (64 threads per block, knobs 16 / 4 / 3) and the FP64
+    defaults set explicitly (128; 4 / 1 / 4) give the same records bit for bit, on single renders and in
+    a batch."""
+    import torch
+    eye, tgt, up = inputs.camera_pose(20.0)
+    views = []
+    for v, m, e in ((0, 1, 0.0), (1, 1, 20.0), (1, 0, 45.0)):
+        ve, vt, vu = inputs.camera_pose(e)
+        views.append((v, m, ve, vt, vu, 60.0, torch.empty((54, 96, 4), device="cuda")))
+    out = []
+    for explicit in (False, True):
+        c = ck.Cloak(1).camera(eye, tgt, up, 60.0, 96, 54).integrator(1, 1e-9, band).schedule(ck.SCHED_WAVEFRONT)
+        b = ck.Cloak(0).integrator(1, 1e-9, band).schedule(ck.SCHED_WAVEFRONT)
+        if explicit:
+            for h in (c, b):
+                h.schedule(ck.SCHED_WAVEFRONT, 128)
+                ck.cloak_set_schedule_tuning(h.h, 4, 1, 4.0)
+        rec = ck.records_to_numpy(c.render_records(1, 2, 5))
+        ck.cloak_render_batch(b.h, views, 2, 5)
+        torch.cuda.synchronize()
+        out.append((rec.tobytes(), torch.stack([v[-1] for v in views]).clone()))
+        c.close()
+        b.close()
+    assert out[0][0] == out[1][0]
+    assert torch.equal(out[0][1], out[1][1])
