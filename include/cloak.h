@@ -327,9 +327,10 @@ int cloak_surrogate_set_gate(cloak_t *h, double max_log10_err);
  * size.  CLOAK_ESTATE without a trained surrogate. */
 int cloak_surrogate_info(cloak_t *h, double info[8]);
 /* Operand precision of the surrogate's inference (renders with CLOAK_SURROGATE and
- * cloak_surrogate_forward): fp16 = 0, the default, evaluates the network in BF16 like its training;
- * fp16 = 1 in FP16 (weights, hidden biases, input pairs and activations; FP32 accumulation in both):
- * 11 significant bits instead of 8 and a faster epilogue.  The setting belongs to the handle's network
+ * cloak_surrogate_forward): fp16 = 0, the default, evaluates the network with BF16 weights, input pairs
+ * and activations like its training; fp16 = 1 in FP16 (weights, input pairs and activations: 11
+ * significant bits instead of 8, slightly faster).  In both the accumulation is FP32 and the hidden
+ * layers' bias and GELU are computed in half-precision pairs.  The setting belongs to the handle's network
  * (kept across cloak_surrogate_load); a handle without a surrogate gets one with seeded weights first.
  * The paper has no counterpart. */
 int cloak_surrogate_set_precision(cloak_t *h, int fp16);

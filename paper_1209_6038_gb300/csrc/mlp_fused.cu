@@ -8,15 +8,17 @@
 //     and loads each tile's inputs (the K-major layout the MMA reads) once the tile's previous last-layer
 //     MMAs are done -- after the weight chunk of the tile's first job, so that chunk is already on its way;
 //   * the MMA warp (one thread) issues, per chunk, the four tcgen05.mma (M = 128, K = 16) of the job's tile
-//     into its TMEM columns (tile t: 256 t .. 256 t + 255) and frees the slot by a commit.  Before a job's
+//     (one for the first layer, whose 14 input columns fit one K step) into its TMEM columns (tile t:
+//     256 t .. 256 t + 255) and frees the slot by a commit.  Before a job's
 //     first MMA it waits only for the epilogue of the same tile's previous layer, so the MMAs of one tile
 //     run while the epilogue of the other tile runs.  The two roles are separate threads because one
 //     thread doing both spent longer per chunk on its barrier waits and bookkeeping than the tensor core
 //     spent on the chunk's four MMAs;
 //   * 16 epilogue warps take the jobs in the same order (warp w: TMEM lanes 32 (w % 4) .., column quarter
-//     w / 4): they read the tile's accumulators once its MMAs completed, add the bias (read through L1),
-//     apply GELU in half-precision pairs and write the activations back into the swizzled shared-memory
-//     layout as the tile's next A operand (the last layer writes the FP32 outputs), then arrive on the
+//     w / 4): they read the tile's accumulators once its MMAs completed (16 columns per TMEM load), round
+//     them to half-precision pairs, add the half-precision bias (read through L1), apply GELU in the
+//     same pairs and write the activations back into the swizzled shared-memory layout as the tile's
+//     next A operand (the last layer writes the FP32 outputs, its bias added in FP32), then arrive on the
 //     tile's barrier.
 // Operands (weights, inputs as (hi, lo) pairs, activations) are BF16, the precision the network is trained
 // in, or -- selected per network -- FP16: the GELU is evaluated in half-precision pairs in both forms, and
@@ -45,14 +47,34 @@ constexpr int F_SLOTS = 3;                                     // weight ring de
 constexpr size_t F_SMEM = 1024 + F_ACT_BYTES + F_SLOTS * F_RING_SLOT;
 
 struct FusedArgs {
-    const float *bias[SUR_L];    // FP32 biases (the BF16 form, and the output layer of both)
-    const __half *bias_h[SUR_L - 1]; // hidden layers' biases in half precision (the FP16 form)
+    const float *bias[SUR_L];    // FP32 biases (the output layer's are used)
+    const __half *bias_h[SUR_L - 1]; // hidden layers' biases in half precision (both forms)
     float *Y;                    // outputs, 16 FP32 per row
     long long n;                 // rows of X and Y (a multiple of 128)
     const unsigned int *m_count; // optional live row count
     unsigned int *err;
     unsigned int wait_limit;     // polls of the waits that decide a timeout
 };
+
+// bias, GELU and the store of 16 columns from c (a multiple of 16) of row r: u the FP32 accumulators,
+// b0, b1 the 16 half-precision biases; the result goes into the 128-byte-swizzled K-major layout of chunk
+// c / 64 of the tile's activations (16-byte units (c % 64) / 8 and + 1 of the row, each XOR-ed with r % 8)
+template <bool F16>
+__device__ __forceinline__ void epi_piece(const uint32_t (&u)[16], uint4 b0, uint4 b1, unsigned char *act_t, int c,
+                                          int r) {
+    const uint32_t bw[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    uint32_t pk[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const __half2 bias = *reinterpret_cast<const __half2 *>(&bw[k]);
+        pk[k] = F16 ? gelu2_f16(__uint_as_float(u[2 * k]), __uint_as_float(u[2 * k + 1]), bias)
+                    : gelu2_bf16(__uint_as_float(u[2 * k]), __uint_as_float(u[2 * k + 1]), bias);
+    }
+    unsigned char *chunk = act_t + (c / 64) * F_ACT_CHUNK + (r >> 3) * 1024 + (r & 7) * 128;
+    const int u0 = (c & 63) >> 3;
+    *(uint4 *)(chunk + ((u0 ^ (r & 7)) << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *(uint4 *)(chunk + (((u0 + 1) ^ (r & 7)) << 4)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
 
 template <bool F16>
 __global__ void __launch_bounds__(F_THREADS, 1)
@@ -171,8 +193,12 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                         asm volatile("tcgen05.fence::after_thread_sync;");
                         const uint64_t bd = sw128_desc(ring0 + s * F_RING_SLOT);
                         const uint64_t ad = sw128_desc(act0 + (uint32_t)(t * 4 + j) * F_ACT_CHUNK);
+                        // the first layer's inputs (7 values as hi/lo pairs) and weights fill K columns 0..13 of
+                        // the chunk and are zero beyond: one MMA covers them
+                        const int nmma = l == 0 ? 1 : 4;
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
+                            if (kk >= nmma) break;
                             const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
                             asm volatile(
                                 "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -209,66 +235,38 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             for (int job = 0; job < 2 * SUR_L; ++job) {
                 const int l = job >> 1, t = job & 1;
                 const int N = l == SUR_L - 1 ? 16 : SUR_W;
+                const int cw = max(16, N / F_PARTS), c0 = part * cw, c1 = min(N, c0 + cw);
+                // the half-precision biases of the warp's columns, 16 per piece (two 16-byte loads through L1);
+                // the first piece's are read while the MMAs run
+                const uint4 *bias8 = reinterpret_cast<const uint4 *>(a.bias_h[l < SUR_L - 1 ? l : 0] + c0);
+                uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0;
+                if (l < SUR_L - 1) {
+                    b0 = __ldg(bias8);
+                    b1 = __ldg(bias8 + 1);
+                }
                 ok = mbar_wait(smem_u32(&done_bar[t]), Lt[t] & 1, lim) && !*vfailed;
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256);
-                const int cw = max(16, N / F_PARTS), c0 = part * cw, c1 = min(N, c0 + cw);
                 if (l < SUR_L - 1) {
-                    for (int c = c0; c < c1; c += 32) {  // 32 columns per TMEM load (parts are 64 wide)
-                        uint32_t u[32];
-                        asm volatile(
-                            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                            : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-                              "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
-                              "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]),
-                              "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]),
-                              "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
-                            : "r"(taddr + (uint32_t)c));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        // GELU, into the 128-byte-swizzled K-major layout of chunk c / 64: 16-byte units
-                        // (c % 64) / 8 .. + 3 of row r, each XOR-ed with r % 8
-                        uint32_t pk[16];
-                        if constexpr (F16) {
-                            // the biases of these 32 columns as half pairs, 8 halves per 16-byte load through L1
-                            const uint4 *b8 = reinterpret_cast<const uint4 *>(a.bias_h[l] + c);  // 16-byte aligned
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const uint4 bv = __ldg(b8 + i);
-                                const uint32_t bw[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-                                for (int k2 = 0; k2 < 4; ++k2)
-                                    pk[4 * i + k2] = gelu2_f16(__uint_as_float(u[8 * i + 2 * k2]),
-                                                               __uint_as_float(u[8 * i + 2 * k2 + 1]),
-                                                               *reinterpret_cast<const __half2 *>(&bw[k2]));
-                            }
-                        } else {
-                            // FP32 biases, 4 per 16-byte load through L1
-                            const float4 *b4 = reinterpret_cast<const float4 *>(a.bias[l] + c);  // 16-byte aligned
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const float4 bv = __ldg(b4 + i);
-                                pk[2 * i] = gelu2_bf16(__uint_as_float(u[4 * i]) + bv.x, __uint_as_float(u[4 * i + 1]) + bv.y);
-                                pk[2 * i + 1] =
-                                    gelu2_bf16(__uint_as_float(u[4 * i + 2]) + bv.z, __uint_as_float(u[4 * i + 3]) + bv.w);
-                            }
+                    // four 16-column pieces, one TMEM load each (loads kept in flight across the GELU of the
+                    // previous piece measured slower: 32 more live registers per thread)
+                    unsigned char *act_t = act + t * 4 * F_ACT_CHUNK;
+#pragma unroll 1
+                    for (int pc = 0; pc < 4; ++pc) {
+                        if (pc) {
+                            b0 = __ldg(bias8 + 2 * pc);
+                            b1 = __ldg(bias8 + 2 * pc + 1);
                         }
-                        unsigned char *chunk = act + (t * 4 + c / 64) * F_ACT_CHUNK + (r >> 3) * 1024 + (r & 7) * 128;
-                        const int u0 = (c & 63) >> 3;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            *(uint4 *)(chunk + (((u0 + k) ^ (r & 7)) << 4)) =
-                                make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+                        uint32_t u[16];
+                        tmem_ld16(taddr + (uint32_t)(c0 + 16 * pc), u);
+                        tmem_wait16(u);
+                        epi_piece<F16>(u, b0, b1, act_t, c0 + 16 * pc, r);
                     }
                 } else if (c0 < c1) {  // the 16 outputs in FP32
                     uint32_t u[16];
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-                          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
-                        : "r"(taddr));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    tmem_ld16(taddr, u);
+                    tmem_wait16(u);
                     const long long row = base + t * 128 + r;
                     if (row < live) {
                         float4 *y = (float4 *)(a.Y + row * 16);

@@ -85,32 +85,45 @@ __device__ __forceinline__ float gelu_tanh(float x) {
     float u = k0 * (x + k1 * x * x * x);
     return 0.5f * x * (1.f + tanh_fast(u));
 }
-// GELU of two values in half-precision pair arithmetic (tanh.approx.f16x2: one hardware tanh for two values),
-// packed as BF16x2.  Half precision carries 11 significant bits against the 8 of the BF16 result it feeds;
-// inputs must stay below the half-precision range (|x| < 65504), where x^2 overflowing only saturates tanh.
-__device__ __forceinline__ uint32_t gelu2_bf16(float a, float b) {
-    const __half2 x = __floats2half2_rn(a, b);
-    const __half2 one = __float2half2_rn(1.f), k0 = __float2half2_rn(0.7978845608028654f),
-                  k1 = __float2half2_rn(0.044715f), half = __float2half2_rn(0.5f);
-    const __half2 u = __hmul2(__hmul2(k0, x), __hfma2(k1, __hmul2(x, x), one));  // k0 x (1 + k1 x^2)
+// 16 consecutive TMEM columns of the warp's 32 lanes (one lane per thread) into u; the load is
+// asynchronous: read u only after tmem_wait16(u)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&u)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                   "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+                 : "r"(taddr));
+}
+// waits for every TMEM load of the thread; u as operands, so that no use of u moves above the wait
+__device__ __forceinline__ void tmem_wait16(uint32_t (&u)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(u[0]), "+r"(u[1]), "+r"(u[2]), "+r"(u[3]), "+r"(u[4]), "+r"(u[5]), "+r"(u[6]), "+r"(u[7]),
+                   "+r"(u[8]), "+r"(u[9]), "+r"(u[10]), "+r"(u[11]), "+r"(u[12]), "+r"(u[13]), "+r"(u[14]), "+r"(u[15])
+                 :
+                 : "memory");
+}
+// GELU (tanh form) of x = (a, b) + bias in half-precision pair arithmetic: x rounded to a half pair, the
+// bias added, then x (1 + tanh(u)) / 2 with u = x (k0 + k0 k1 x^2), k0 = sqrt(2/pi), k1 = 0.044715 (one
+// hardware tanh, tanh.approx.f16x2, for two values).  Half precision carries 11 significant bits;
+// inputs must stay below its range (|x| < 65504), where x^2 overflowing only saturates tanh.
+__device__ __forceinline__ __half2 gelu2_h2(float a, float b, __half2 bias) {
+    const __half2 x = __hadd2(__floats2half2_rn(a, b), bias);
+    const __half2 c1 = __float2half2_rn(0.7978845608028654f * 0.044715f), c0 = __float2half2_rn(0.7978845608028654f),
+                  half = __float2half2_rn(0.5f);
+    const __half2 u = __hmul2(x, __hfma2(c1, __hmul2(x, x), c0));
     __half2 th;
     asm("tanh.approx.f16x2 %0, %1;" : "=r"(*(uint32_t *)&th) : "r"(*(const uint32_t *)&u));
     const __half2 hx = __hmul2(half, x);
-    const float2 g = __half22float2(__hfma2(hx, th, hx));  // x (1 + tanh) / 2
+    return __hfma2(hx, th, hx);
+}
+// the same packed as BF16x2 (8 significant bits): the BF16 activations of the fused inference kernel
+__device__ __forceinline__ uint32_t gelu2_bf16(float a, float b, __half2 bias) {
+    const float2 g = __half22float2(gelu2_h2(a, b, bias));
     const __nv_bfloat162 o = __floats2bfloat162_rn(g.x, g.y);
     return *(const uint32_t *)&o;
 }
-// GELU of x + b for a pair in half precision (x: FP32 accumulators, b: half-precision biases), the
-// result as a half-precision pair -- the fused inference kernel's activations
+// the same as a half-precision pair: the FP16 activations
 __device__ __forceinline__ uint32_t gelu2_f16(float a, float b, __half2 bias) {
-    const __half2 x = __hadd2(__floats2half2_rn(a, b), bias);
-    const __half2 one = __float2half2_rn(1.f), k0 = __float2half2_rn(0.7978845608028654f),
-                  k1 = __float2half2_rn(0.044715f), half = __float2half2_rn(0.5f);
-    const __half2 u = __hmul2(__hmul2(k0, x), __hfma2(k1, __hmul2(x, x), one));  // k0 x (1 + k1 x^2)
-    __half2 th;
-    asm("tanh.approx.f16x2 %0, %1;" : "=r"(*(uint32_t *)&th) : "r"(*(const uint32_t *)&u));
-    const __half2 hx = __hmul2(half, x);
-    const __half2 o = __hfma2(hx, th, hx);  // x (1 + tanh) / 2
+    const __half2 o = gelu2_h2(a, b, bias);
     return *(const uint32_t *)&o;
 }
 __device__ __forceinline__ float gelu_tanh_grad(float x) {
