@@ -605,6 +605,45 @@ __device__ __forceinline__ T flux_n(const T n[3], const cxt<T> E[3], const cxt<T
     return s;
 }
 
+// The same operations on real field components: while every wave at a face propagates (its wave vector
+// real), the Eq. 12 system is real and is solved in real arithmetic (a quarter of the multiplications);
+// the complex form serves faces with an evanescent wave.  fld<F>(a) is a as a field component of type F.
+template <typename T>
+__device__ __forceinline__ T cdiv(T a, T b) { return a * rcp_nr(b); }
+template <typename T>
+__device__ __forceinline__ T cabs2(T a) { return a * a; }
+template <typename T>
+__device__ __forceinline__ T cdot(const T a[3], const T b[3]) { return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2])); }
+template <typename T>
+__device__ __forceinline__ void ccross(const T a[3], const T b[3], T o[3]) {
+    o[0] = fma(a[1], b[2], -a[2] * b[1]);
+    o[1] = fma(a[2], b[0], -a[0] * b[2]);
+    o[2] = fma(a[0], b[1], -a[1] * b[0]);
+}
+template <typename T>
+__device__ __forceinline__ T vnorm2(const T a[3]) { return cdot(a, a); }
+// n . (E x H)
+template <typename T>
+__device__ __forceinline__ T flux_n(const T n[3], const T E[3], const T H[3]) {
+    T x[3];
+    ccross(E, H, x);
+    return dot3(n, x);
+}
+template <typename T>
+__device__ __forceinline__ T fld_(T a, T *) { return a; }
+template <typename T>
+__device__ __forceinline__ cxt<T> fld_(T a, cxt<T> *) { return cxt<T>{a, T(0)}; }
+template <typename F, typename T>
+__device__ __forceinline__ F fld(T a) { return fld_(a, (F *)nullptr); }
+template <typename T>
+__device__ __forceinline__ T re_(T a) { return a; }
+template <typename T>
+__device__ __forceinline__ T re_(cxt<T> a) { return a.re; }
+template <typename T>
+__device__ __forceinline__ T im_(T) { return T(0); }
+template <typename T>
+__device__ __forceinline__ T im_(cxt<T> a) { return a.im; }
+
 // Inward wave (possibly evanescent: decaying into the medium) of the mode with tangential kt.
 template <typename T>
 __device__ __forceinline__ void inward_wave_c(int mode, T eo, T ee, const T c[3], const T n[3],
@@ -629,17 +668,17 @@ __device__ __forceinline__ void inward_wave_c(int mode, T eo, T ee, const T c[3]
 // Field directions of a plane wave of the mode (Sect. 3): D_o perpendicular to the ordinary
 // main section, D_e in the extraordinary main section and perpendicular to k; E = eps^-1 D,
 // H = k x E.  Degenerate k parallel to c: D_o along z x k (x x k if that vanishes too).
-template <typename T>
-__device__ __forceinline__ void wave_fields(int mode, T eo, T ee, const T c[3], const cxt<T> k[3],
-                                            cxt<T> E[3], cxt<T> H[3]) {
-    cxt<T> cc[3] = {C(c[0]), C(c[1]), C(c[2])}, Do[3], D[3];
+// ieo = 1/eo, dl = 1/ee - 1/eo; F: T (real k) or cxt<T>.
+template <typename T, typename F>
+__device__ __forceinline__ void wave_fields_f(int mode, T ieo, T dl, const T c[3], const F k[3], F E[3], F H[3]) {
+    F cc[3] = {fld<F>(c[0]), fld<F>(c[1]), fld<F>(c[2])}, Do[3], D[3];
     ccross(cc, k, Do);
     T kk2 = vnorm2(k);
     if (vnorm2(Do) < T(1e-20) * kk2) {
-        cxt<T> z3[3] = {C(T(0)), C(T(0)), C(T(1))};
+        F z3[3] = {fld<F>(T(0)), fld<F>(T(0)), fld<F>(T(1))};
         ccross(z3, k, Do);
         if (vnorm2(Do) < T(1e-20) * kk2) {
-            cxt<T> x3[3] = {C(T(1)), C(T(0)), C(T(0))};
+            F x3[3] = {fld<F>(T(1)), fld<F>(T(0)), fld<F>(T(0))};
             ccross(x3, k, Do);
         }
         if (mode == M_EXT) ccross(k, Do, D);
@@ -647,15 +686,21 @@ __device__ __forceinline__ void wave_fields(int mode, T eo, T ee, const T c[3], 
     } else if (mode == M_ORD) {
         for (int i = 0; i < 3; ++i) D[i] = Do[i];
     } else {
-        cxt<T> kk = cdot(k, k), ckk = cdot(cc, k);
+        F kk = cdot(k, k), ckk = cdot(cc, k);
         for (int i = 0; i < 3; ++i) D[i] = kk * cc[i] - ckk * k[i];
     }
     // eps^-1 = I/eo + (1/ee - 1/eo) c c^T
-    T ieo = T(1) / eo, dl = T(1) / ee - ieo;
-    cxt<T> cD = cdot(cc, D);
+    F cD = cdot(cc, D);
     for (int i = 0; i < 3; ++i) E[i] = ieo * D[i] + (dl * c[i]) * cD;
     ccross(k, E, H);
 }
+template <typename T>
+__device__ __forceinline__ void wave_fields(int mode, T eo, T ee, const T c[3], const cxt<T> k[3],
+                                            cxt<T> E[3], cxt<T> H[3]) {
+    T ieo = T(1) / eo, dl = T(1) / ee - ieo;
+    wave_fields_f(mode, ieo, dl, c, k, E, H);
+}
+
 
 template <typename T>
 __device__ __forceinline__ void unit_perp(const T n[3], T t[3]) {
@@ -680,60 +725,63 @@ __device__ __forceinline__ void s_basis(const T k[3], const T n[3], T s[3]) {
     else for (int i = 0; i < 3; ++i) s[i] /= l;
 }
 
-// Solve the complex 4x4 system A X = B for NR right-hand sides (Gaussian elimination, partial pivoting).
-template <int NR, typename T>
-__device__ bool csolve4(cxt<T> A[4][4], cxt<T> B[4][NR]) {
+// Solve the 4x4 system A X = B for NR right-hand sides (Gaussian elimination, partial pivoting), in
+// complex (F = cxt<T>) or real (F = T) arithmetic.
+template <int NR, typename F>
+__device__ bool csolve4(F A[4][4], F B[4][NR]) {
     for (int col = 0; col < 4; ++col) {
         int piv = col;
-        T best = cabs2(A[col][col]);
+        auto best = cabs2(A[col][col]);
         for (int r = col + 1; r < 4; ++r) {
-            T v = cabs2(A[r][col]);
+            auto v = cabs2(A[r][col]);
             if (v > best) { best = v; piv = r; }
         }
-        if (best == T(0)) return false;
+        if (best == decltype(best)(0)) return false;
         if (piv != col) {
-            for (int k = 0; k < 4; ++k) { cxt<T> t = A[col][k]; A[col][k] = A[piv][k]; A[piv][k] = t; }
-            for (int k = 0; k < NR; ++k) { cxt<T> t = B[col][k]; B[col][k] = B[piv][k]; B[piv][k] = t; }
+            for (int k = 0; k < 4; ++k) { F t = A[col][k]; A[col][k] = A[piv][k]; A[piv][k] = t; }
+            for (int k = 0; k < NR; ++k) { F t = B[col][k]; B[col][k] = B[piv][k]; B[piv][k] = t; }
         }
         for (int r = col + 1; r < 4; ++r) {
-            cxt<T> f = cdiv(A[r][col], A[col][col]);
+            F f = cdiv(A[r][col], A[col][col]);
             for (int k = col; k < 4; ++k) A[r][k] = A[r][k] - f * A[col][k];
             for (int k = 0; k < NR; ++k) B[r][k] = B[r][k] - f * B[col][k];
         }
     }
     for (int r = 3; r >= 0; --r)
         for (int k = 0; k < NR; ++k) {
-            cxt<T> s = B[r][k];
+            F s = B[r][k];
             for (int j = r + 1; j < 4; ++j) s = s - A[r][j] * B[j][k];
             B[r][k] = cdiv(s, A[r][r]);
         }
     return true;
 }
 
-// Eq. 12, vacuum -> medium, unpolarised light (mean over s and p): transmission into `mode`.
-template <typename T>
-static __device__ __noinline__ T transmission_in(int mode, T eo, T ee, const T c[3], const T n[3],
-                                               const T d[3]) {
-    T dn = dot3(d, n), kt[3], kr[3];
-    for (int i = 0; i < 3; ++i) { kt[i] = d[i] - dn * n[i]; kr[i] = d[i] - T(2) * dn * n[i]; }
-    cxt<T> ko[3], ke[3], Eo[3], Ho[3], Ee[3], He[3];
-    inward_wave_c(M_ORD, eo, ee, c, n, kt, ko);
-    inward_wave_c(M_EXT, eo, ee, c, n, kt, ke);
-    wave_fields(M_ORD, eo, ee, c, ko, Eo, Ho);
-    wave_fields(M_EXT, eo, ee, c, ke, Ee, He);
+
+// Eq. 12, vacuum -> medium, unpolarised light (mean over s and p): transmission into `mode`.  ko, ke: the
+// wave vectors of the two inward waves (F = T when both propagate, cxt<T> when one is evanescent).
+template <typename T, typename F>
+static __device__ __noinline__ T trans_in_f(int mode, T eo, T ee, const T c[3], const T n[3], const T d[3],
+                                            const F ko[3], const F ke[3]) {
+    const T ieo = T(1) / eo, dl = T(1) / ee - ieo;
+    T dn = dot3(d, n), kr[3];
+    for (int i = 0; i < 3; ++i) kr[i] = d[i] - T(2) * dn * n[i];
+    F Eo[3], Ho[3], Ee[3], He[3];
+    wave_fields_f(M_ORD, ieo, dl, c, ko, Eo, Ho);
+    wave_fields_f(M_EXT, ieo, dl, c, ke, Ee, He);
     T s[3], pi[3], pr[3], t2[3];
     s_basis(d, n, s);
     pi[0] = s[1] * d[2] - s[2] * d[1]; pi[1] = s[2] * d[0] - s[0] * d[2]; pi[2] = s[0] * d[1] - s[1] * d[0];
     pr[0] = s[1] * kr[2] - s[2] * kr[1]; pr[1] = s[2] * kr[0] - s[0] * kr[2]; pr[2] = s[0] * kr[1] - s[1] * kr[0];
     t2[0] = n[1] * s[2] - n[2] * s[1]; t2[1] = n[2] * s[0] - n[0] * s[2]; t2[2] = n[0] * s[1] - n[1] * s[0];
     // columns: reflected s, reflected p, -o, -e ; rows: E.t1, E.t2, H.t1, H.t2 with t1 = s
-    cxt<T> Ers[3] = {C(s[0]), C(s[1]), C(s[2])}, Erp[3] = {C(pr[0]), C(pr[1]), C(pr[2])}, Hrs[3], Hrp[3];
-    cxt<T> ckr[3] = {C(kr[0]), C(kr[1]), C(kr[2])};
+    F Ers[3] = {fld<F>(s[0]), fld<F>(s[1]), fld<F>(s[2])}, Erp[3] = {fld<F>(pr[0]), fld<F>(pr[1]), fld<F>(pr[2])},
+      Hrs[3], Hrp[3];
+    F ckr[3] = {fld<F>(kr[0]), fld<F>(kr[1]), fld<F>(kr[2])};
     ccross(ckr, Ers, Hrs);
     ccross(ckr, Erp, Hrp);
-    cxt<T> ct1[3] = {C(s[0]), C(s[1]), C(s[2])}, ct2[3] = {C(t2[0]), C(t2[1]), C(t2[2])};
-    const cxt<T> *colE[4] = {Ers, Erp, Eo, Ee}, *colH[4] = {Hrs, Hrp, Ho, He};
-    cxt<T> A[4][4], B[4][2];
+    F ct1[3] = {fld<F>(s[0]), fld<F>(s[1]), fld<F>(s[2])}, ct2[3] = {fld<F>(t2[0]), fld<F>(t2[1]), fld<F>(t2[2])};
+    const F *colE[4] = {Ers, Erp, Eo, Ee}, *colH[4] = {Hrs, Hrp, Ho, He};
+    F A[4][4], B[4][2];
     for (int j = 0; j < 4; ++j) {
         T sg = j < 2 ? T(1) : -T(1);
         A[0][j] = sg * cdot(colE[j], ct1);
@@ -741,11 +789,11 @@ static __device__ __noinline__ T transmission_in(int mode, T eo, T ee, const T c
         A[2][j] = sg * cdot(colH[j], ct1);
         A[3][j] = sg * cdot(colH[j], ct2);
     }
-    cxt<T> cd[3] = {C(d[0]), C(d[1]), C(d[2])};
+    F cd[3] = {fld<F>(d[0]), fld<F>(d[1]), fld<F>(d[2])};
     T fin[2];
     for (int pol = 0; pol < 2; ++pol) {
         const T *e = pol == 0 ? s : pi;
-        cxt<T> Ei[3] = {C(e[0]), C(e[1]), C(e[2])}, Hi[3];
+        F Ei[3] = {fld<F>(e[0]), fld<F>(e[1]), fld<F>(e[2])}, Hi[3];
         ccross(cd, Ei, Hi);
         B[0][pol] = -T(1) * cdot(Ei, ct1);
         B[1][pol] = -T(1) * cdot(Ei, ct2);
@@ -754,43 +802,51 @@ static __device__ __noinline__ T transmission_in(int mode, T eo, T ee, const T c
         fin[pol] = fabs(flux_n(n, Ei, Hi));
     }
     if (!csolve4<2>(A, B)) return T(0);
-    const cxt<T> *Em = mode == M_ORD ? Eo : Ee, *Hm = mode == M_ORD ? Ho : He;
+    const F *Em = mode == M_ORD ? Eo : Ee, *Hm = mode == M_ORD ? Ho : He;
     int row = mode == M_ORD ? 2 : 3;
     T fm = fabs(flux_n(n, Em, Hm));
     return T(0.5) * (cabs2(B[row][0]) * fm / fin[0] + cabs2(B[row][1]) * fm / fin[1]);
+}
+template <typename T>
+__device__ __forceinline__ T transmission_in(int mode, T eo, T ee, const T c[3], const T n[3], const T d[3]) {
+    T dn = dot3(d, n), kt[3], ko[3], ke[3], v[3];
+    for (int i = 0; i < 3; ++i) kt[i] = d[i] - dn * n[i];
+    if (refract_in(M_ORD, eo, ee, c, n, kt, ko, v) && refract_in(M_EXT, eo, ee, c, n, kt, ke, v))
+        return trans_in_f<T, T>(mode, eo, ee, c, n, d, ko, ke);
+    cxt<T> koc[3], kec[3];
+    inward_wave_c(M_ORD, eo, ee, c, n, kt, koc);
+    inward_wave_c(M_EXT, eo, ee, c, n, kt, kec);
+    return trans_in_f<T, cxt<T>>(mode, eo, ee, c, n, d, koc, kec);
 }
 
 // Eq. 12, medium -> vacuum (Sect. 3, last paragraph): fraction of the incident mode's normal
 // energy flux carried by the refracted vacuum wave.  0 for total internal reflection.
 // axis: a linear polariser the transmitted vacuum wave then meets (nullable): the result is multiplied by
-// the fraction of that wave's flux along the axis taken across the wave (Malus's law)
-template <typename T>
-static __device__ __noinline__ T transmission_out(int mode, T eo, T ee, const T c[3],
-                                                const T n[3], const T k[3], const T *axis = nullptr) {
-    T kn = dot3(k, n), kt[3];
-    for (int i = 0; i < 3; ++i) kt[i] = k[i] - kn * n[i];
-    T kt2 = dot3(kt, kt);
-    if (kt2 > T(1)) return T(0);
+// the fraction of that wave's flux along the axis taken across the wave (Malus's law).  kro, kre: the wave
+// vectors of the two reflected (inward) waves (F = T when both propagate, cxt<T> when one is evanescent).
+template <typename T, typename F>
+static __device__ __noinline__ T trans_out_f(int mode, T eo, T ee, const T c[3], const T n[3], const T k[3],
+                                             const T kt[3], T kt2, const F kro[3], const F kre[3], const T *axis) {
+    const T ieo = T(1) / eo, dl = T(1) / ee - ieo;
     T kv[3], s[3], pv[3], t2[3];
     T qn = sqrt(T(1) - kt2);
     for (int i = 0; i < 3; ++i) kv[i] = fma(qn, n[i], kt[i]);
     s_basis(kv, n, s);
     pv[0] = s[1] * kv[2] - s[2] * kv[1]; pv[1] = s[2] * kv[0] - s[0] * kv[2]; pv[2] = s[0] * kv[1] - s[1] * kv[0];
     t2[0] = n[1] * s[2] - n[2] * s[1]; t2[1] = n[2] * s[0] - n[0] * s[2]; t2[2] = n[0] * s[1] - n[1] * s[0];
-    cxt<T> ckv[3] = {C(kv[0]), C(kv[1]), C(kv[2])};
-    cxt<T> Es[3] = {C(s[0]), C(s[1]), C(s[2])}, Ep[3] = {C(pv[0]), C(pv[1]), C(pv[2])}, Hs[3], Hp[3];
+    F ckv[3] = {fld<F>(kv[0]), fld<F>(kv[1]), fld<F>(kv[2])};
+    F Es[3] = {fld<F>(s[0]), fld<F>(s[1]), fld<F>(s[2])}, Ep[3] = {fld<F>(pv[0]), fld<F>(pv[1]), fld<F>(pv[2])},
+      Hs[3], Hp[3];
     ccross(ckv, Es, Hs);
     ccross(ckv, Ep, Hp);
-    cxt<T> kro[3], kre[3], Ero[3], Hro[3], Ere[3], Hre[3], Em[3], Hm[3];
-    inward_wave_c(M_ORD, eo, ee, c, n, kt, kro);
-    inward_wave_c(M_EXT, eo, ee, c, n, kt, kre);
-    wave_fields(M_ORD, eo, ee, c, kro, Ero, Hro);
-    wave_fields(M_EXT, eo, ee, c, kre, Ere, Hre);
-    cxt<T> ck3[3] = {C(k[0]), C(k[1]), C(k[2])};
-    wave_fields(mode, eo, ee, c, ck3, Em, Hm);
-    cxt<T> ct1[3] = {C(s[0]), C(s[1]), C(s[2])}, ct2[3] = {C(t2[0]), C(t2[1]), C(t2[2])};
-    const cxt<T> *colE[4] = {Es, Ep, Ero, Ere}, *colH[4] = {Hs, Hp, Hro, Hre};
-    cxt<T> A[4][4], B[4][1];
+    F Ero[3], Hro[3], Ere[3], Hre[3], Em[3], Hm[3];
+    wave_fields_f(M_ORD, ieo, dl, c, kro, Ero, Hro);
+    wave_fields_f(M_EXT, ieo, dl, c, kre, Ere, Hre);
+    F ck3[3] = {fld<F>(k[0]), fld<F>(k[1]), fld<F>(k[2])};
+    wave_fields_f(mode, ieo, dl, c, ck3, Em, Hm);
+    F ct1[3] = {fld<F>(s[0]), fld<F>(s[1]), fld<F>(s[2])}, ct2[3] = {fld<F>(t2[0]), fld<F>(t2[1]), fld<F>(t2[2])};
+    const F *colE[4] = {Es, Ep, Ero, Ere}, *colH[4] = {Hs, Hp, Hro, Hre};
+    F A[4][4], B[4][1];
     for (int j = 0; j < 4; ++j) {
         T sg = j < 2 ? T(1) : -T(1);
         A[0][j] = sg * cdot(colE[j], ct1);
@@ -804,7 +860,7 @@ static __device__ __noinline__ T transmission_out(int mode, T eo, T ee, const T 
     B[3][0] = cdot(Hm, ct2);
     T fm = fabs(flux_n(n, Em, Hm));
     if (!csolve4<1>(A, B)) return T(0);
-    cxt<T> Et[3], Ht[3];
+    F Et[3], Ht[3];
     for (int i = 0; i < 3; ++i) { Et[i] = B[0][0] * Es[i] + B[1][0] * Ep[i]; Ht[i] = B[0][0] * Hs[i] + B[1][0] * Hp[i]; }
     const T Tr = fabs(flux_n(n, Et, Ht)) / fm;
     if (!axis) return Tr;
@@ -815,12 +871,28 @@ static __device__ __noinline__ T transmission_out(int mode, T eo, T ee, const T 
     const T al2 = dot3(a, a);
     T er = T(0), ei = T(0), e2 = T(0);
     for (int i = 0; i < 3; ++i) {
-        er += Et[i].re * a[i];
-        ei += Et[i].im * a[i];
-        e2 += Et[i].re * Et[i].re + Et[i].im * Et[i].im;
+        er += re_(Et[i]) * a[i];
+        ei += im_(Et[i]) * a[i];
+        e2 += re_(Et[i]) * re_(Et[i]) + im_(Et[i]) * im_(Et[i]);
     }
     return al2 > T(0) && e2 > T(0) ? Tr * (er * er + ei * ei) / (al2 * e2) : T(0);
 }
+template <typename T>
+__device__ __forceinline__ T transmission_out(int mode, T eo, T ee, const T c[3], const T n[3], const T k[3],
+                                              const T *axis = nullptr) {
+    T kn = dot3(k, n), kt[3];
+    for (int i = 0; i < 3; ++i) kt[i] = k[i] - kn * n[i];
+    T kt2 = dot3(kt, kt);
+    if (kt2 > T(1)) return T(0);
+    T kro[3], kre[3], v[3];
+    if (refract_in(M_ORD, eo, ee, c, n, kt, kro, v) && refract_in(M_EXT, eo, ee, c, n, kt, kre, v))
+        return trans_out_f<T, T>(mode, eo, ee, c, n, k, kt, kt2, kro, kre, axis);
+    cxt<T> kroc[3], krec[3];
+    inward_wave_c(M_ORD, eo, ee, c, n, kt, kroc);
+    inward_wave_c(M_EXT, eo, ee, c, n, kt, krec);
+    return trans_out_f<T, cxt<T>>(mode, eo, ee, c, n, k, kt, kt2, kroc, krec, axis);
+}
+
 
 // First-order reflections (Sect. 3 last paragraphs, Sect. 4).
 // Reflection coefficients of a wave of `mode` (real wave vector k, travelling towards the face with outward
