@@ -61,7 +61,7 @@ __device__ __forceinline__ void sur_gate_one(const Params &p, int mode, const Qu
     // the height moves monotonically along the ray: a predicted exit inside the lateral surface means
     // no cap was crossed -- with a margin of twice the exit-point error the confidence allows
     // (predicted log10 error c bounds the exit-point error by 10 R2 10^c)
-    const double margin = 20.0 * p.R2 * exp10((double)y[4]);
+    const double margin = 20.0 * p.R2 * (double)exp10f(y[4]);
     if (!(fabs(P[2] + 2.0 * p.R2 * (double)y[0]) < p.halfH - margin)) return;
     double pos[3], dout[3], tof;
     sur_reconstruct(p.R2, p.H, P, d, y, pos, dout, tof);

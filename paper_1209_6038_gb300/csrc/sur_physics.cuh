@@ -47,6 +47,18 @@ __device__ __forceinline__ double sur_local(const double P[3], const double d[3]
     return phi;
 }
 
+// The same local components with the frame taken from the position itself (r-hat = (x, y) / r), without
+// the azimuth: no FP64 transcendental, which the render-side kernels avoid (the GPU's FP64 unit is scarce).
+__device__ __forceinline__ void sur_local_frame(const double P[3], const double d[3], double rh[2], double &dr,
+                                                double &dt, double &dz) {
+    const double ir = rsqrt_nr(fma(P[0], P[0], P[1] * P[1]));
+    rh[0] = P[0] * ir;
+    rh[1] = P[1] * ir;
+    dr = fma(d[0], rh[0], d[1] * rh[1]);
+    dt = fma(d[1], rh[0], -d[0] * rh[1]);
+    dz = d[2];
+}
+
 // training ray i: entry point uniform on the lateral surface, direction cosine-weighted about the
 // inward normal (a uniform point of the unit disc lifted onto the hemisphere), mode and variant uniform
 __device__ __forceinline__ void sur_sample(unsigned long long seed, unsigned long long i, double R2, double H,
@@ -69,15 +81,18 @@ __device__ __forceinline__ void sur_sample(unsigned long long seed, unsigned lon
 }
 
 // network inputs: z / (H/2), phi / pi - 1, asin(d_z) / (pi/2), atan2(d_theta, -d_r) / (pi/2),
-// 2 mode - 1, 2 variant - 1, R1 / R2
+// 2 mode - 1, 2 variant - 1, R1 / R2.  The angles in FP32: an input enters the network as a pair of
+// BF16 or FP16 numbers (16 or 22 significant bits), below FP32's 24.
 __device__ __forceinline__ void sur_features(double R1, double R2, double H, int variant, int mode, const double P[3],
                                              const double d[3], float x[SUR_IN]) {
-    double dr, dt, dz;
-    const double phi = sur_local(P, d, dr, dt, dz);
+    double rh[2], dr, dt, dz;
+    sur_local_frame(P, d, rh, dr, dt, dz);
+    float phi = atan2f((float)P[1], (float)P[0]);
+    if (phi < 0.f) phi += 2.f * (float)M_PI;
     x[0] = (float)(P[2] / (0.5 * H));
-    x[1] = (float)(phi / M_PI - 1.0);
-    x[2] = (float)(asin(fmin(fmax(dz, -1.0), 1.0)) / (0.5 * M_PI));
-    x[3] = (float)(atan2(dt, -dr) / (0.5 * M_PI));
+    x[1] = phi * (float)M_1_PI - 1.f;
+    x[2] = asinf(fminf(fmaxf((float)dz, -1.f), 1.f)) * (float)M_2_PI;
+    x[3] = atan2f((float)dt, (float)-dr) * (float)M_2_PI;
     x[4] = (float)(2 * mode - 1);
     x[5] = (float)(2 * variant - 1);
     x[6] = (float)(R1 / R2);
@@ -104,14 +119,24 @@ __device__ __forceinline__ bool sur_targets(double R2, double H, const double P[
     return true;
 }
 
-// exit point on r = R2, vacuum exit direction (k_z, L_z conserved) and time of flight from y[0..3]
+// exit point on r = R2, vacuum exit direction (k_z, L_z conserved) and time of flight from y[0..3]: the exit
+// azimuth is phi + pi - 2 alpha + psi (alpha = atan2(d_theta, -d_r), psi = atan2(y2, y1)), composed as a
+// product of unit complex numbers, e^{i phe} = -e^{i phi} conj(e^{i alpha})^2 e^{i psi}, in FP64 algebra
 __device__ __forceinline__ void sur_reconstruct(double R2, double H, const double P[3], const double d[3],
                                                 const float y[4], double pos[3], double dir[3], double &tof) {
-    double dr, dt, dz;
-    const double phi = sur_local(P, d, dr, dt, dz);
-    const double phe = phi + M_PI - 2.0 * atan2(dt, -dr) + atan2((double)y[2], (double)y[1]);
+    double e[2], dr, dt, dz;
+    sur_local_frame(P, d, e, dr, dt, dz);
+    const double ia = rsqrt_nr(fma(dr, dr, dt * dt)), ac = -dr * ia, as = dt * ia;  // e^{i alpha}
+    const double bc = fma(ac, ac, -as * as), bs = -2.0 * ac * as;                  // conj(e^{i alpha})^2
+    const double y1 = (double)y[1], y2 = (double)y[2], yy = fma(y1, y1, y2 * y2);
+    const double ip = yy > 0.0 ? rsqrt_nr(yy) : 0.0;
+    const double pc = yy > 0.0 ? y1 * ip : 1.0, ps = y2 * ip;                      // e^{i psi} (psi = 0 at y = 0)
+    const double qc = fma(bc, pc, -bs * ps), qs = fma(bc, ps, bs * pc);
     double rh[3], th[3];
-    sur_frame(phe, rh, th);
+    rh[0] = -fma(e[0], qc, -e[1] * qs);
+    rh[1] = -fma(e[0], qs, e[1] * qc);
+    rh[2] = 0.0;
+    th[0] = -rh[1]; th[1] = rh[0]; th[2] = 0.0;
     pos[0] = R2 * rh[0];
     pos[1] = R2 * rh[1];
     pos[2] = P[2] + (double)y[0] * 2.0 * R2;
