@@ -185,11 +185,17 @@ __device__ __noinline__ df3 accel_df_call(df R1, df x, df y, df vx, df vy, df vz
     accel<VAR, MODE, df>(R1, unused, unused, x, y, vx, vy, vz, a.x, a.y, a.z, vm);
     return a;
 }
+// one medium: inline; the batch's any-medium form: one out-of-line copy with the switch inside
 template <int VAR, int MODE>
 __device__ __forceinline__ void rhs_df(df R1, const df y[6], df d[6], int vm) {
     d[0] = y[3]; d[1] = y[4]; d[2] = y[5];
-    const df3 a = accel_df_call<VAR, MODE>(R1, y[0], y[1], y[3], y[4], y[5], vm);
-    d[3] = a.x; d[4] = a.y; d[5] = a.z;
+    if (VAR != V_ANY) {
+        const df unused;  // K and 1/K: the simplified accelerations of accel_fixed do not read them
+        accel_fixed<VAR, MODE, df>(R1, unused, unused, y[0], y[1], y[3], y[4], y[5], d[3], d[4], d[5]);
+    } else {
+        const df3 a = accel_df_call<VAR, MODE>(R1, y[0], y[1], y[3], y[4], y[5], vm);
+        d[3] = a.x; d[4] = a.y; d[5] = a.z;
+    }
 }
 template <int VAR, int MODE>
 __device__ __forceinline__ void dp45_step_df(df R1, const df y[6], const df k1[6], df h, df out[6], df err[6],
@@ -274,9 +280,26 @@ __device__ __noinline__ void band_step_f64(const Params &p, const double *y, dou
         dp45_step<VAR, MODE>(p, y, k1, s, yo, e, k7, vm);
     }
 }
+template <int VAR, int MODE>
+__device__ __forceinline__ void dp45_band_df(df R1, const df *y, df hs, df *yo, df *e, df *k7, int vm) {
+    df k1[6];
+    rhs_df<VAR, MODE>(R1, y, k1, vm);
+    dp45_step_df<VAR, MODE>(R1, y, k1, hs, yo, e, k7, vm);
+}
 template <int VAR, int MODE, int INTEG>
 __device__ __noinline__ void band_step_df(float R1h, float R1l, const df *y, float s, df *yo, df *e, df *k7, int vm) {
     const df R1(R1h, R1l), hs(s, 0.f);
+    if (VAR == V_ANY && INTEG == I_DP45) {
+        // the batch's medium chosen once per step: each medium's step with its right-hand sides inline
+        // (a call per stage cost the double-float step 5 % of its integration)
+        switch (vm) {
+        case 0: dp45_band_df<V_RADIAL, M_ORD>(R1, y, hs, yo, e, k7, vm); break;
+        case 1: dp45_band_df<V_RADIAL, M_EXT>(R1, y, hs, yo, e, k7, vm); break;
+        case 2: dp45_band_df<V_AZIMUTHAL, M_ORD>(R1, y, hs, yo, e, k7, vm); break;
+        default: dp45_band_df<V_AZIMUTHAL, M_EXT>(R1, y, hs, yo, e, k7, vm); break;
+        }
+        return;
+    }
     if (INTEG == I_RK4) {
         rk4_step_df<VAR, MODE>(R1, y, hs, yo, vm);
     } else {
