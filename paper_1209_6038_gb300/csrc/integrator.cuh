@@ -172,7 +172,6 @@ __device__ __forceinline__ void rhs_f32(const Params &p, const float t[6], const
                                d[3], d[4], d[5]);
 }
 
-
 // ------------------------------------------------------------------ double-float steps (the band near R1)
 // The same right-hand side and the same Dormand-Prince / RK4 updates as the FP64 path, in double-float.
 struct df3 {
